@@ -1,0 +1,47 @@
+"""Writes the stored expected eigenvalues under tests/golden/ by calling only the oracle.
+
+For each workload, the discrete eigenvalues of A(k) strictly inside its contour (the plain
+definition of the method's output, Section 1: all k inside the contour with T(k)u = 0),
+found by the oracle's successive-linear-problems refinement started from the closed-form
+continuum eigenvalues inside the contour (unit sphere: zeros of spherical Bessel functions,
+Table 3; unit cube: pi sqrt(n1^2 + n2^2 + n3^2), Table 1) and from every neighbour that the
+refinement reveals. Usage: python tests/golden/make_golden.py [sphere320] [cube3072]
+"""
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import synth                      # noqa: E402
+from oracle import refine, contour  # noqa: E402
+
+STARTS = {
+    "sphere320": [3.141593, 4.493409],
+    "cube3072": [5.441398, 7.695299],
+}
+
+
+def main(names):
+    for name in names:
+        prob = synth.workload(name).problems[0]
+        mesh = prob.mesh()
+        spec = prob.contour
+        found = refine.discrete_eigs(mesh, STARTS[name], radius=0.2,
+                                     keep=lambda l: bool(contour.inside(l, spec, -0.05)))
+        path = os.path.join(HERE, f"eigs_{name}.txt")
+        with open(path, "w") as f:
+            f.write(f"# discrete eigenvalues of A(k) inside the contour of {name}\n")
+            f.write(f"# mesh {mesh.name} (n = {mesh.n}), contour {spec}\n")
+            f.write("# written by tests/golden/make_golden.py (oracle only)\n")
+            f.write("# re im multiplicity inside\n")
+            for lam, mult in found:
+                ins = int(bool(contour.inside(lam, spec)))
+                f.write(f"{lam.real:.17g} {lam.imag:.17g} {mult} {ins}\n")
+        print(name, found)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:] or list(STARTS))

@@ -1,0 +1,59 @@
+"""Pins of the oracle's discrete eigenvalues (the plain definition of the method's output:
+the k inside the contour where A(k) is singular) against facts that use none of its
+machinery: the smallest singular value of A at the eigenvalue, the argument-principle
+count of det A(z) around the contour, and the closed-form Dirichlet eigenvalues of the
+unit sphere (zeros of spherical Bessel functions, Table 3 of the paper) and unit cube
+(pi sqrt(n1^2 + n2^2 + n3^2), Table 1 of the paper) approached at O(h^2)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import refine
+
+SPHERE = [3.141593, 4.493409]        # j_0 and j_1 first zeros (multiplicity 1, 3)
+CUBE = [5.441398, 7.695299]          # pi sqrt(3) (x1), pi sqrt(6) (x3)
+
+
+def test_sphere320_eigs_singular_and_counted(oracle_mod):
+    m = synth.icosphere(2)
+    spec = synth.workload("sphere320").problems[0].contour
+    found = refine.discrete_eigs(m, SPHERE, radius=0.2)
+    lams = [l for l, _ in found]
+    mults = [k for _, k in found]
+    assert mults == [1, 3]
+    for l, k in found:
+        s = np.linalg.svd(oracle_mod.assembly.matrix(m, l), compute_uv=False)
+        assert np.all(s[-k:] / s[0] < 1e-12)          # k-fold singular
+        assert s[-k - 1] / s[0] > 1e-4                  # and not more
+    count = refine.winding_count(m, spec, M=128)
+    assert abs(count - sum(mults)) < 1e-6
+    # discrete values sit a little above the continuum ones on the inscribed mesh
+    assert 0 < lams[0].real - SPHERE[0] < 0.06 and 0 < lams[1].real - SPHERE[1] < 0.08
+
+
+@pytest.mark.slow
+def test_sphere_richardson_to_bessel_zeros(oracle_mod):
+    ground, second = [], []
+    for L in (1, 2, 3):
+        f = refine.discrete_eigs(synth.icosphere(L), [SPHERE[0] * 1.02, SPHERE[1] * 1.02],
+                                 radius=0.05)
+        ground.append(f[0][0].real)
+        second.append(f[-1][0].real)
+        assert f[-1][1] == 3
+    for vals, exact in ((ground, SPHERE[0]), (second, SPHERE[1])):
+        e = [v - exact for v in vals]
+        assert 3.0 < e[0] / e[1] < 5.0 and 3.0 < e[1] / e[2] < 5.0      # O(h^2)
+        rich = vals[2] + (vals[2] - vals[1]) / 3.0
+        assert abs(rich - exact) < 1e-3 * exact
+
+
+@pytest.mark.slow
+def test_cube_richardson_to_closed_form(oracle_mod):
+    vals = []
+    for m in (4, 8):
+        f = refine.discrete_eigs(synth.cube_grid(m), [CUBE[0]], radius=0.01)
+        vals.append(f[0][0].real)
+    e = [CUBE[0] - v for v in vals]
+    assert 3.0 < e[0] / e[1] < 6.0
+    rich = vals[1] + (vals[1] - vals[0]) / 3.0
+    assert abs(rich - CUBE[0]) < 2e-3 * CUBE[0]
