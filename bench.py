@@ -1,0 +1,319 @@
+"""Benchmark of the fused BEM assembly + Rayleigh-Ritz projection on one GB300 per rank.
+
+One step is one pass of the hot path over the unit-cube workload (3072 triangles, 16 x 16
+squares per face; ellipse contour centre 6.5, semi-axes 1.5 and 0.4, N = 32 trapezoid
+nodes; Ritz basis of 64 complex Gaussian columns):
+  geometry set-up -> contour nodes, weights and self terms -> CholeskyQR2 of the basis ->
+  fused assembly + projection Bhat_j = w_j V^H A(z_j) V for all 32 nodes.
+The metric counts n^2 N matrix entries assembled and projected per step.
+
+Ranks (torchrun) run independent replicas of the step (the path has no exchange step) and
+the reported value is the sum over ranks (weak scaling). ``--impl reference`` times the
+CPU FP64 oracle on a bounded row sample of the same workload instead (rank 0 only).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BEM entries assembled+projected/s at eig rel err ≤1e-8; % of roofline"
+UNIT = "entries/s"
+WORKLOAD = "cube3072"
+L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def problem():
+    import synth
+    prob = synth.workload(WORKLOAD).problems[0]
+    mesh = prob.mesh()
+    V = synth.complex_gaussian(mesh.n, prob.nu, prob.seed)
+    return prob, mesh, V
+
+
+def oracle_sample(prob, mesh, V, target_s=12.0):
+    """Times the oracle's assembly + projection on a row sample sized to ~target_s."""
+    import oracle
+    from oracle import contour as ocon, rr as orr
+    oracle.build()
+    z, w = ocon.from_spec(prob.contour, prob.N)
+    rows = 16
+    while True:
+        t0 = time.perf_counter()
+        orr.project(mesh, z, V, rows=(0, rows))
+        dt = time.perf_counter() - t0
+        if dt >= target_s or rows >= mesh.n:
+            break
+        rows = min(mesh.n, max(2 * rows, int(rows * target_s / max(dt, 1e-3))))
+    entries = rows * mesh.n * prob.N
+    cores = oracle.lib().oracle_max_threads()
+    return {"value": entries / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"rows 0..{rows} of {mesh.n} (all {mesh.n} columns, all {prob.N} "
+                      f"nodes, nu={prob.nu}): {entries:.3e} entries in {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    prob, mesh, V = problem()
+    times = []
+    base = None
+    for it in range(args.warmup + args.steps):
+        b = oracle_sample(prob, mesh, V, target_s=8.0 if it >= args.warmup else 1.0)
+        if it >= args.warmup:
+            times.append(b["value"])
+            base = b
+    value = statistics.median(times)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "n": mesh.n, "N": prob.N, "nu": prob.nu,
+                       "sample": base["sample"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"],
+                             "kind": "oracle", "sample": base["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import paper_1906_03938_gb300 as bem
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prob, mesh, V = problem()
+    n, N, nu = mesh.n, prob.N, prob.nu
+    prec = bem.PREC_MIXED if args.precision == "mixed" else bem.PREC_FP64
+    c = prob.contour
+    ctx = bem.Context(local)
+    stream = torch.cuda.current_stream()
+
+    V_host = torch.from_numpy(np.asfortranarray(V)).pin_memory()   # column-major host copy
+    V_res = bem.fortran(V_host.to(dev))                              # resident input
+    V_work = bem.fortran(torch.empty_like(V_res))
+    B_dev = torch.empty((N, nu, nu), dtype=torch.complex128, device=dev)
+    B_host = torch.empty((N, nu, nu), dtype=torch.complex128).pin_memory()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(src):
+        ctx.set_mesh(mesh.xyz, mesh.tri)
+        ctx.set_contour(c.kind, c.centre, c.a, c.b, N)
+        V_work.copy_(src, non_blocking=True)
+        ctx.cholqr2(V_work, want_R=False)
+        ctx.project(V_work, prec, Bhat=B_dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    for _ in range(args.warmup):
+        step(V_res)
+    barrier()
+
+    # device-resident timing (value) with L2 flushed between steps, per-step events
+    ctx.set_timing(True)
+    launches0 = ctx.launches
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        step(V_res)
+        ev[k][1].record(stream)
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    launches = ctx.launches - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    kern_ms = list(ctx.kernel_times())
+    ctx.set_timing(False)
+    t_total = sum(step_ms) / 1e3
+
+    # end to end through the public API with host buffers: H2D of V and the mesh each
+    # step, D2H of the projected matrices
+    barrier()
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e2e_ev[k][0].record(stream)
+        step(V_host)
+        B_host.copy_(B_dev, non_blocking=True)
+        e2e_ev[k][1].record(stream)
+    barrier()
+    e2e_total = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3
+
+    # max over ranks
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_total, e2e_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total, e2e_total = float(t[0]), float(t[1])
+
+    entries = float(n) * n * N
+    value = world * entries * args.steps / t_total
+    e2e_value = world * entries * args.steps / e2e_total
+
+    if rank != 0:
+        ctx.close()
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel
+    kern_avg = statistics.mean(kern_ms) if kern_ms else float("nan")
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if prec == bem.PREC_FP64:
+        # plain path: FP64 pipe; algorithmic work = the complex MAC of every entry with
+        # every basis column, 8 nu flops per entry
+        flops = entries * 8 * nu
+        peak = ctx.microbench("fp64_fma")
+        roof = {"bound": "alu", "pipe": "fp64", "achieved": flops / (kern_avg * 1e-3) / 1e12,
+                "peak": peak / 1e12, "unit": "TFLOP/s",
+                "peak_source": "measured FP64 FMA microbenchmark (bem_microbench)"}
+    else:
+        ex2 = ctx.microbench("ex2")
+        ops = entries * 7 * 3   # ex2, sin, cos per quadrature point
+        roof = {"bound": "alu", "pipe": "mufu", "achieved": ops / (kern_avg * 1e-3) / 1e12,
+                "peak": ex2 / 1e12, "unit": "Tops/s",
+                "peak_source": "measured MUFU ex2 microbenchmark (bem_microbench)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel_ms"] = kern_avg
+    roof["launches_timed"] = len(kern_ms)
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = oracle_sample(prob, mesh, V)
+
+    bi = V.nbytes + mesh.xyz.nbytes + mesh.tri.nbytes
+    bo = N * nu * nu * 16
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == bem.PREC_FP64 else "f32+bf16x3", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "mesh": mesh.name, "n": n, "N": N, "nu": nu,
+                   "contour": "ellipse c=6.5 a=1.5 b=0.4", "precision": args.precision,
+                   "parallelism": f"replicas{world}", "l2": "flushed between steps (512 MB write)",
+                   "wall_s_timed": wall},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
+                "d2h_bytes_per_step": bo},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,151 @@
+/*
+ * bem_gb300.h -- C ABI of the GB300 hot path of the Cauchy rational-approximation /
+ * Rayleigh-Ritz method for the acoustic BEM nonlinear eigenvalue problem A(k) x = 0
+ * (El-Guide, Miedlar, Saad, "A rational approximation method for solving acoustic
+ * nonlinear eigenvalue problems").
+ *
+ * Operator. A(k) is the constant-element collocation matrix of the single-layer part of
+ * the boundary integral equation (Section 1, Eq. HelmBIM, Eq. GreenFun): for triangles
+ * i != l, A_il(k) = sum_q W_lq exp(i k r) / (4 pi r), r = |x_i - y_lq|, with x_i the
+ * centroid of triangle i and (y_lq, W_lq) Radon's 7-point degree-5 rule on triangle l;
+ * A_ii(k) is the exact integral of the kernel over triangle i, taken in polar
+ * coordinates about x_i (radial part in closed form, angular part by 16-point
+ * Gauss-Legendre in u = asinh(s/d) on each side of the foot of each edge).
+ *
+ * Conventions for every entry point:
+ *  - Complex numbers are interleaved (re, im) doubles. Matrices are column-major.
+ *  - "_dev" pointers are CUDA device pointers on the context's device; "_host" pointers
+ *    are host memory. The caller owns every buffer it passes; the context owns only its
+ *    internal workspaces (geometry, contour, self-term table, reduction partials).
+ *  - Work is enqueued on the given stream (a cudaStream_t passed as void*, NULL = legacy
+ *    default stream) and returns without synchronising unless stated otherwise.
+ *  - Every call returns a bem_status; on failure bem_last_error() describes it. No C++
+ *    exception crosses the ABI. There is no CPU fallback: a missing or failing GPU is an
+ *    error (BEM_ECUDA).
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef BEM_GB300_H
+#define BEM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bem_ctx bem_ctx;
+
+typedef enum {
+    BEM_OK = 0,
+    BEM_EINVAL = -1,    /* invalid argument (null pointer, bad size, degenerate mesh) */
+    BEM_ENOMEM = -2,    /* device workspace allocation failed */
+    BEM_ECUDA = -3,     /* CUDA runtime error (launch failure, no device, ...) */
+    BEM_EKERNEL = -4,   /* a kernel reported an error through its status word */
+    BEM_ETIMEOUT = -5,  /* a bounded device wait ran out */
+    BEM_ENOCONV = -6,   /* an iteration did not converge */
+    BEM_ESTATE = -7     /* call out of order (no mesh / no contour set yet) */
+} bem_status;
+
+typedef enum {
+    BEM_PREC_FP64 = 0,  /* plain path: FP64 evaluation and FP64 contraction */
+    BEM_PREC_MIXED = 1  /* FP32 evaluation, BF16x3 split-precision tcgen05 contraction */
+} bem_precision;
+
+typedef enum { BEM_CONTOUR_CIRCLE = 0, BEM_CONTOUR_ELLIPSE = 1 } bem_contour_kind;
+
+/* Create a context on CUDA device `device`. */
+bem_status bem_create(bem_ctx** out, int device);
+void bem_destroy(bem_ctx* ctx);
+/* Message of the last failing call on this context (never NULL). */
+const char* bem_last_error(const bem_ctx* ctx);
+/* Library version string. */
+const char* bem_version(void);
+
+/*
+ * Geometry set-up (the mesh is the discretisation of Section 1; Eq. NEVPHelmholtz).
+ * Copies nv vertices (xyz_host: 3*nv doubles, x y z per vertex) and nt triangles
+ * (tri_host: 3*nt int32 vertex indices, outward orientation) to the device and computes
+ * per-triangle centroids, areas and the 7 quadrature points and weights. n = nt is the
+ * number of unknowns. Fails with BEM_EINVAL on an index out of range or a triangle of
+ * zero area. Synchronises the stream before returning.
+ */
+bem_status bem_set_mesh(bem_ctx* ctx, int64_t nv, const double* xyz_host, int64_t nt,
+                        const int32_t* tri_host, void* stream);
+
+/*
+ * Contour set-up (Section 2, Eq. Tz, Eq. TzApp). Trapezoid nodes in the angle,
+ * theta_j = 2 pi (j + 1/2) / N, j = 0..N-1, on z(theta) = c + a cos(theta) + i b sin(theta)
+ * (kind CIRCLE uses b = a):
+ *     z_j = c + a cos(theta_j) + i b sin(theta_j),
+ *     w_j = (b cos(theta_j) + i a sin(theta_j)) / N,
+ * so that A(z) ~ sum_j w_j A(z_j) / (z_j - z) inside the contour. Also evaluates the
+ * self-term table A_ii(z_j) for the current mesh. z_host / w_host (2*N doubles each) may
+ * be NULL; if given they receive the nodes / weights. Requires a mesh. N in [1, 4096],
+ * a > 0, b > 0. Synchronises the stream before returning.
+ */
+bem_status bem_set_contour(bem_ctx* ctx, int kind, double c_re, double c_im, double a,
+                           double b, int N, double* z_host, double* w_host, void* stream);
+
+/*
+ * Fused assembly + Rayleigh-Ritz projection (Section 3, Eq. RR_approx; Algorithm 3,
+ * "use U to compute B^_i"): for every contour node z_j,
+ *     Bhat_j = w_j * V^H A(z_j) V                                   (nu x nu)
+ * without storing A(z_j): its entries are evaluated tile by tile and contracted at once.
+ *   V_dev    n x nu complex, column-major, leading dimension ldv >= n.
+ *   Bhat_dev N x (nu x nu) complex: node j at offset j*nu*nu, column-major.
+ *   AV_dev   optional (NULL to skip): N x (n x nu) complex, node j at offset j*n*nu,
+ *            column-major with leading dimension n: Y_j = A(z_j) V (unweighted), the
+ *            products the stopping test and the residuals use.
+ *   precision  BEM_PREC_FP64 or BEM_PREC_MIXED.
+ * 1 <= nu <= 256. Requires a mesh and a contour. Asynchronous on `stream`.
+ */
+bem_status bem_project(bem_ctx* ctx, const double* V_dev, int64_t ldv, int nu,
+                       double* Bhat_dev, double* AV_dev, int precision, void* stream);
+
+/*
+ * CholeskyQR2 orthonormalisation of a basis (the paper orthonormalises U before the
+ * projection, Section 4, Example 1): G = V^H V, R1 = chol(G), V <- V R1^{-1}, repeated
+ * once; on return V (n x nu, column-major, leading dimension ldv) has orthonormal
+ * columns and, if R_dev is not NULL, R_dev (nu x nu, column-major) holds R = R2 R1 with
+ * V_in = V_out R. FP64 throughout. Fails with BEM_EKERNEL if a Gram matrix is not
+ * numerically positive definite (rank-deficient V). Synchronises the stream.
+ */
+bem_status bem_cholqr2(bem_ctx* ctx, double* V_dev, int64_t n, int64_t ldv, int nu,
+                       double* R_dev, void* stream);
+
+/*
+ * Residuals of approximate eigenpairs (Section 4: ||T(lambda) u||_2 / ||u||_2), matrix-
+ * free in FP64: for each column c, r_c = A(lam_c) x_c.
+ *   lam_host   2*m doubles (lambda_c interleaved)
+ *   X_dev      n x m complex, column-major, leading dimension ldx
+ *   R_dev      optional n x m complex output (leading dimension n), may be NULL
+ *   relres_host m doubles receiving ||r_c|| / ||x_c||
+ * Synchronises the stream.
+ */
+bem_status bem_residual(bem_ctx* ctx, int m, const double* lam_host, const double* X_dev,
+                        int64_t ldx, double* R_dev, double* relres_host, void* stream);
+
+/* Number of CUDA kernels this context has launched since creation (diagnostics). */
+int64_t bem_kernel_launches(const bem_ctx* ctx);
+
+/*
+ * Diagnostics for roofline accounting (no counterpart in the paper).
+ * bem_set_timing: when enable != 0, every bem_project records CUDA events on its stream
+ *   around its main kernel (the fused evaluation + contraction); resets the record.
+ * bem_kernel_times: durations in ms of up to max_out recorded launches (in call order),
+ *   synchronising on their stop events; *count receives how many; resets the record.
+ *   At most 256 launches are kept between resets.
+ * bem_microbench: measured throughput (operations per second over the whole device) of
+ *   one pipe: kind 0 FP64 FMA (2 flops each), 1 FP32 FMA (2 flops each), 2 MUFU ex2,
+ *   3 MUFU sin, 4 MUFU cos. Synchronous; runs on the legacy default stream.
+ */
+bem_status bem_set_timing(bem_ctx* ctx, int enable);
+bem_status bem_kernel_times(bem_ctx* ctx, double* ms_out, int max_out, int* count);
+bem_status bem_microbench(bem_ctx* ctx, int kind, double* ops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BEM_GB300_H */

@@ -1,0 +1,218 @@
+"""Python binding of the GB300 BEM eigen-solver hot path (C ABI in include/bem_gb300.h).
+
+Argument marshalling only: every step runs in the CUDA library ``_build/libbem_gb300.so``.
+The raw entry points keep their C names (``bem_create``, ``bem_set_mesh``, ...); the
+``Context`` class wraps them for torch tensors (device memory, streams) and numpy arrays
+(host inputs). Importing this package does not touch the GPU; loading the library fails
+loudly if it has not been built: there is no CPU fallback.
+
+Layouts: complex arrays are complex128 (interleaved re, im). An n x nu basis is a device
+tensor whose memory is column-major, i.e. ``V.stride() == (1, ld)`` with ``ld >= n``
+(``fortran(V)`` makes one). Projected matrices come back as a (N, nu, nu) tensor whose
+[j] slice is the matrix Bhat_j itself.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbem_gb300.so")
+
+BEM_OK = 0
+STATUS = {0: "BEM_OK", -1: "BEM_EINVAL", -2: "BEM_ENOMEM", -3: "BEM_ECUDA", -4: "BEM_EKERNEL",
+          -5: "BEM_ETIMEOUT", -6: "BEM_ENOCONV", -7: "BEM_ESTATE"}
+PREC_FP64 = 0
+PREC_MIXED = 1
+CONTOUR_CIRCLE = 0
+CONTOUR_ELLIPSE = 1
+
+# name -> (restype, argtypes) of every symbol declared in include/bem_gb300.h
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I = ctypes.c_int
+_D = ctypes.c_double
+SIGNATURES = {
+    "bem_create": (_I, [ctypes.POINTER(_P), _I]),
+    "bem_destroy": (None, [_P]),
+    "bem_last_error": (ctypes.c_char_p, [_P]),
+    "bem_version": (ctypes.c_char_p, []),
+    "bem_set_mesh": (_I, [_P, _I64, _P, _I64, _P, _P]),
+    "bem_set_contour": (_I, [_P, _I, _D, _D, _D, _D, _I, _P, _P, _P]),
+    "bem_project": (_I, [_P, _P, _I64, _I, _P, _P, _I, _P]),
+    "bem_cholqr2": (_I, [_P, _P, _I64, _I64, _I, _P, _P]),
+    "bem_residual": (_I, [_P, _I, _P, _P, _I64, _P, _P, _P]),
+    "bem_kernel_launches": (_I64, [_P]),
+    "bem_set_timing": (_I, [_P, _I]),
+    "bem_kernel_times": (_I, [_P, _P, _I, ctypes.POINTER(_I)]),
+    "bem_microbench": (_I, [_P, _I, ctypes.POINTER(_D)]),
+}
+
+_lib = None
+
+
+class BemError(RuntimeError):
+    def __init__(self, name, status, msg):
+        super().__init__(f"{name} failed with {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it is missing: build it with ``build.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} (run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`)")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def __getattr__(name):
+    # raw C entry points under their own names: paper_1906_03938_gb300.bem_project(...)
+    if name in SIGNATURES:
+        return getattr(load(), name)
+    raise AttributeError(name)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(_P)
+    return _P(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return _P(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return _P(stream)
+    return _P(stream.cuda_stream)
+
+
+def fortran(t):
+    """Column-major copy of a 2-D tensor (stride (1, rows))."""
+    return t.transpose(0, 1).contiguous().transpose(0, 1)
+
+
+def _check_fortran(V, name):
+    if V.dim() != 2 or V.stride(0) != 1 or V.stride(1) < V.shape[0]:
+        raise ValueError(f"{name} must be a column-major 2-D tensor (use fortran())")
+
+
+class Context:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._lib = load()
+        h = _P()
+        st = self._lib.bem_create(ctypes.byref(h), int(device))
+        if st != BEM_OK:
+            raise BemError("bem_create", st, "no usable CUDA device")
+        self._h = h
+        self.device = device
+        self.n = 0
+        self.N = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.bem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, name, st):
+        if st != BEM_OK:
+            raise BemError(name, st, self._lib.bem_last_error(self._h).decode())
+
+    @property
+    def launches(self) -> int:
+        return int(self._lib.bem_kernel_launches(self._h))
+
+    def set_timing(self, enable=True):
+        self._chk("bem_set_timing", self._lib.bem_set_timing(self._h, int(bool(enable))))
+
+    def kernel_times(self, max_out=256):
+        ms = np.zeros(max_out)
+        cnt = _I(0)
+        self._chk("bem_kernel_times", self._lib.bem_kernel_times(self._h, _ptr(ms), max_out,
+                                                                  ctypes.byref(cnt)))
+        return ms[:cnt.value]
+
+    def microbench(self, kind):
+        """Measured device throughput in ops/s: 'fp64_fma', 'fp32_fma' (flops), 'ex2',
+        'sin', 'cos' (MUFU operations)."""
+        kinds = {"fp64_fma": 0, "fp32_fma": 1, "ex2": 2, "sin": 3, "cos": 4}
+        r = _D(0.0)
+        self._chk("bem_microbench", self._lib.bem_microbench(self._h, kinds[kind], ctypes.byref(r)))
+        return r.value
+
+    def set_mesh(self, xyz, tri, stream=None):
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+        self._chk("bem_set_mesh", self._lib.bem_set_mesh(self._h, xyz.shape[0], _ptr(xyz),
+                                                          tri.shape[0], _ptr(tri),
+                                                          _stream(stream)))
+        self.n = int(tri.shape[0])
+
+    def set_contour(self, kind, centre, a, b, N, stream=None):
+        kinds = {"circle": CONTOUR_CIRCLE, "ellipse": CONTOUR_ELLIPSE}
+        k = kinds[kind] if isinstance(kind, str) else int(kind)
+        z = np.zeros(2 * N)
+        w = np.zeros(2 * N)
+        c = complex(centre)
+        self._chk("bem_set_contour", self._lib.bem_set_contour(
+            self._h, k, c.real, c.imag, float(a), float(b), int(N), _ptr(z), _ptr(w),
+            _stream(stream)))
+        self.N = int(N)
+        return z.view(np.complex128), w.view(np.complex128)
+
+    def project(self, V, precision=PREC_FP64, AV=False, Bhat=None, stream=None):
+        """Bhat_j = w_j V^H A(z_j) V for all nodes; optionally Y_j = A(z_j) V."""
+        import torch
+        _check_fortran(V, "V")
+        n, nu = V.shape
+        if Bhat is None:
+            Bhat = torch.empty((self.N, nu, nu), dtype=torch.complex128, device=V.device)
+        Y = None
+        if AV is True:
+            Y = torch.empty((self.N, nu, n), dtype=torch.complex128, device=V.device)
+        elif AV is not False and AV is not None:
+            Y = AV
+        self._chk("bem_project", self._lib.bem_project(
+            self._h, _ptr(V), V.stride(1), nu, _ptr(Bhat), _ptr(Y), int(precision),
+            _stream(stream)))
+        Bm = Bhat.transpose(1, 2)
+        return (Bm, Y.transpose(1, 2)) if Y is not None else Bm
+
+    def cholqr2(self, V, want_R=True, stream=None):
+        import torch
+        _check_fortran(V, "V")
+        n, nu = V.shape
+        R = torch.empty((nu, nu), dtype=torch.complex128, device=V.device) if want_R else None
+        self._chk("bem_cholqr2", self._lib.bem_cholqr2(self._h, _ptr(V), n, V.stride(1), nu,
+                                                        _ptr(R), _stream(stream)))
+        return R.transpose(0, 1) if R is not None else None
+
+    def residual(self, lam, X, want_R=False, stream=None):
+        import torch
+        _check_fortran(X, "X")
+        n, m = X.shape
+        lam = np.ascontiguousarray(np.asarray(lam, dtype=np.complex128).reshape(m))
+        rel = np.zeros(m)
+        R = torch.empty((m, n), dtype=torch.complex128, device=X.device) if want_R else None
+        self._chk("bem_residual", self._lib.bem_residual(
+            self._h, m, _ptr(lam.view(np.float64)), _ptr(X), X.stride(1), _ptr(R), _ptr(rel),
+            _stream(stream)))
+        return (rel, R.transpose(0, 1)) if want_R else rel

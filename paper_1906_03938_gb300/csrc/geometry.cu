@@ -1,0 +1,145 @@
+// Geometry, contour and self-term kernels (FP64).
+//
+// * Panel geometry (the constant-element discretisation of Section 1): centroid x_l,
+//   area |T_l| and Radon's 7-point degree-5 rule mapped onto each triangle. Weights are
+//   stored as W_lq / (4 pi) so that an off-diagonal entry is sum_q qw * exp(i k r) / r.
+// * Contour (Section 2, Eq. Tz, Eq. TzApp): trapezoid nodes theta_j = 2 pi (j + 1/2) / N.
+// * Self terms A_ll(z_j) for every panel and node (see selfterm.cuh).
+#include <math.h>
+
+#include "internal.h"
+#include "selfterm.cuh"
+
+namespace bem {
+namespace {
+
+struct Rule7 {
+  double bary[7][3];
+  double w[7];
+};
+
+// Radon's rule from its closed-form constants: the centroid with weight 9/40 and two
+// orbits of three points (alpha, alpha, 1 - 2 alpha), alpha = (6 -+ sqrt 15) / 21, with
+// weights (155 -+ sqrt 15) / 1200.
+Rule7 make_rule7() {
+  Rule7 r;
+  const double s = sqrt(15.0);
+  const double al[2] = {(6.0 - s) / 21.0, (6.0 + s) / 21.0};
+  const double wt[2] = {(155.0 - s) / 1200.0, (155.0 + s) / 1200.0};
+  r.bary[0][0] = r.bary[0][1] = r.bary[0][2] = 1.0 / 3.0;
+  r.w[0] = 9.0 / 40.0;
+  for (int o = 0; o < 2; ++o) {
+    for (int p = 0; p < 3; ++p) {
+      const int q = 1 + 3 * o + p;
+      for (int c = 0; c < 3; ++c) r.bary[q][c] = (c == p) ? 1.0 - 2.0 * al[o] : al[o];
+      r.w[q] = wt[o];
+    }
+  }
+  return r;
+}
+
+__global__ void geometry_kernel(Geometry g, Rule7 rule, int* status) {
+  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= g.n) return;
+  const int32_t i0 = g.tri[3 * l], i1 = g.tri[3 * l + 1], i2 = g.tri[3 * l + 2];
+  if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= g.nv || i1 >= g.nv || i2 >= g.nv) {
+    atomicOr(status, kStatusBadIndex);
+    return;
+  }
+  double v[3][3];
+  for (int c = 0; c < 3; ++c) {
+    v[0][c] = g.xyz[3 * (int64_t)i0 + c];
+    v[1][c] = g.xyz[3 * (int64_t)i1 + c];
+    v[2][c] = g.xyz[3 * (int64_t)i2 + c];
+  }
+  const double e1[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
+  const double e2[3] = {v[2][0] - v[0][0], v[2][1] - v[0][1], v[2][2] - v[0][2]};
+  const double nx = e1[1] * e2[2] - e1[2] * e2[1];
+  const double ny = e1[2] * e2[0] - e1[0] * e2[2];
+  const double nz = e1[0] * e2[1] - e1[1] * e2[0];
+  const double area = 0.5 * sqrt(nx * nx + ny * ny + nz * nz);
+  // degenerate: area below 1e-12 of the squared longest edge (an exact zero can come out
+  // of the cross product as a rounding residue once products are fused)
+  const double e3[3] = {v[2][0] - v[1][0], v[2][1] - v[1][1], v[2][2] - v[1][2]};
+  const double l2 = fmax(fmax(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2],
+                              e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2]),
+                         e3[0] * e3[0] + e3[1] * e3[1] + e3[2] * e3[2]);
+  if (!(area > 1e-12 * l2) || !isfinite(area)) atomicOr(status, kStatusZeroArea);
+  const int64_t n = g.n;
+  for (int c = 0; c < 3; ++c) {
+    const double x = (v[0][c] + v[1][c] + v[2][c]) / 3.0;
+    g.cx[c * n + l] = x;
+    g.cx32[c * n + l] = (float)x;
+  }
+  for (int q = 0; q < 7; ++q) {
+    for (int c = 0; c < 3; ++c) {
+      const double p = rule.bary[q][0] * v[0][c] + rule.bary[q][1] * v[1][c] +
+                       rule.bary[q][2] * v[2][c];
+      g.qp[(7 * c + q) * n + l] = p;
+      g.qp32[(7 * c + q) * n + l] = (float)p;
+    }
+    const double w = rule.w[q] * area / (4.0 * kPiD);
+    g.qw[q * n + l] = w;
+    g.qw32[q * n + l] = (float)w;
+  }
+}
+
+__global__ void contour_kernel(int N, int kind, double c_re, double c_im, double a, double b,
+                               double* z, double* w) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  if (kind == BEM_CONTOUR_CIRCLE) b = a;
+  double s, c;
+  sincospi((2.0 * j + 1.0) / N, &s, &c);   // theta_j = pi (2 j + 1) / N
+  z[2 * j] = c_re + a * c;
+  z[2 * j + 1] = c_im + b * s;
+  w[2 * j] = b * c / N;
+  w[2 * j + 1] = a * s / N;
+}
+
+// One thread per (panel l, node j).
+__global__ void self_term_kernel(Geometry g, int N, const double* z, GL16 gl, double* self) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= g.n * (int64_t)N) return;
+  const int64_t l = t % g.n;
+  const int j = (int)(t / g.n);
+  double v[3][3], x[3];
+  for (int e = 0; e < 3; ++e) {
+    const int32_t vi = g.tri[3 * l + e];
+    for (int c = 0; c < 3; ++c) v[e][c] = g.xyz[3 * (int64_t)vi + c];
+  }
+  for (int c = 0; c < 3; ++c) x[c] = g.cx[c * g.n + l];
+  const double2 a = self_term(v, x, make_double2(z[2 * j], z[2 * j + 1]), gl);
+  self[2 * (j * g.n + l)] = a.x;
+  self[2 * (j * g.n + l) + 1] = a.y;
+}
+
+}  // namespace
+
+cudaError_t launch_geometry(bem_ctx* ctx, cudaStream_t s) {
+  static const Rule7 rule = make_rule7();
+  const int64_t n = ctx->geo.n;
+  geometry_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctx->geo, rule, ctx->d_status);
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_contour(bem_ctx* ctx, cudaStream_t s) {
+  const Contour& c = ctx->con;
+  contour_kernel<<<(c.N + 127) / 128, 128, 0, s>>>(c.N, c.kind, c.c_re, c.c_im, c.a, c.b, c.z,
+                                                   c.w);
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_self_terms(bem_ctx* ctx, cudaStream_t s) {
+  static const GL16 gl = make_gl16();
+  const int64_t total = ctx->geo.n * (int64_t)ctx->con.N;
+  self_term_kernel<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(ctx->geo, ctx->con.N,
+                                                                   ctx->con.z, gl,
+                                                                   ctx->con.self);
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace bem

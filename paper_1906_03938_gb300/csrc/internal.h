@@ -1,0 +1,114 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "bem_gb300.h"
+
+namespace bem {
+
+// Maximum sizes the kernels are written for.
+constexpr int kMaxNu = 256;
+constexpr int kMaxNodes = 4096;
+// Launches of the projection's main kernel whose duration is kept when timing is on.
+constexpr int kMaxTimed = 256;
+
+// Bits of the device status word.
+enum : int {
+  kStatusBadIndex = 1,     // a triangle references a vertex out of range
+  kStatusZeroArea = 2,     // a triangle of zero area
+  kStatusNotSPD = 4,       // a Gram matrix that is not numerically positive definite
+  kStatusNonFinite = 8,    // a non-finite value where a finite one is required
+};
+
+// Device geometry, structure-of-arrays, FP64 (plain path) and FP32 (mixed path).
+// Quadrature arrays are q-major: element (q, l) at q * n + l, so that consecutive
+// panels are consecutive in memory.
+struct Geometry {
+  int64_t n = 0;           // triangles = unknowns
+  int64_t nv = 0;          // vertices
+  int64_t cap_n = 0;       // allocated sizes (buffers are reused by same-size meshes)
+  int64_t cap_nv = 0;
+  double* xyz = nullptr;   // 3 nv
+  int32_t* tri = nullptr;  // 3 n
+  double* cx = nullptr;    // centroids, 3 n: x[0..n), y[n..2n), z[2n..3n)
+  double* qp = nullptr;    // 21 n: x of point q at q*n + l, y at (7+q)*n + l, z at (14+q)*n + l
+  double* qw = nullptr;    // 7 n: W_lq / (4 pi) at q*n + l
+  float* cx32 = nullptr;   // FP32 copies of the above for the mixed path
+  float* qp32 = nullptr;
+  float* qw32 = nullptr;
+};
+
+struct Contour {
+  int N = 0;
+  int kind = 0;
+  double c_re = 0, c_im = 0, a = 0, b = 0;
+  double* z = nullptr;     // 2 N, device
+  double* w = nullptr;     // 2 N, device
+  double* self = nullptr;  // 2 n N, device: A_ll(z_j) at j * n + l (complex)
+  int cap_N = 0;           // allocated sizes
+  int64_t cap_self = 0;
+  double z_host[2 * kMaxNodes];
+  double w_host[2 * kMaxNodes];
+};
+
+}  // namespace bem
+
+struct bem_ctx {
+  int device = 0;
+  std::string err;
+  bem::Geometry geo;
+  bem::Contour con;
+  int* d_status = nullptr;       // device status word
+  double* d_scratch = nullptr;   // reusable FP64 workspace
+  size_t scratch_bytes = 0;
+  double* d_small = nullptr;     // small FP64 workspace (Gram / Cholesky / norms)
+  size_t small_bytes = 0;
+  int64_t launches = 0;
+  int64_t mesh_version = 0;         // bumped by every successful bem_set_mesh
+  int64_t contour_version = 0;      // bumped by every successful bem_set_contour
+  bool timing = false;              // record events around the main projection kernel
+  std::vector<cudaEvent_t> ev;      // 2 * kMaxTimed events (start, stop)
+  int n_timed = 0;
+};
+
+namespace bem {
+
+// Set the context's error message and return `st`.
+bem_status fail(bem_ctx* ctx, bem_status st, const std::string& msg);
+// Map a CUDA error to BEM_ECUDA with a message; BEM_OK if `e` is cudaSuccess.
+bem_status cuda_check(bem_ctx* ctx, cudaError_t e, const char* what);
+// Make sure the context's scratch holds at least `bytes`.
+bem_status ensure_scratch(bem_ctx* ctx, size_t bytes);
+bem_status ensure_small(bem_ctx* ctx, size_t bytes);
+// Events around the main kernel of a projection (no-ops unless timing is enabled).
+inline void timing_begin(bem_ctx* ctx, cudaStream_t s) {
+  if (ctx->timing && ctx->n_timed < kMaxTimed) cudaEventRecord(ctx->ev[2 * ctx->n_timed], s);
+}
+inline void timing_end(bem_ctx* ctx, cudaStream_t s) {
+  if (ctx->timing && ctx->n_timed < kMaxTimed) cudaEventRecord(ctx->ev[2 * ctx->n_timed++ + 1], s);
+}
+// Read and clear the device status word (synchronises `stream`).
+bem_status take_status(bem_ctx* ctx, cudaStream_t stream, const char* where);
+
+// Kernel launchers (each returns the launch error, if any).
+cudaError_t launch_geometry(bem_ctx* ctx, cudaStream_t s);
+cudaError_t launch_contour(bem_ctx* ctx, cudaStream_t s);
+cudaError_t launch_self_terms(bem_ctx* ctx, cudaStream_t s);
+// Y_j = A(z_j) V for all nodes (FP64), Y node-major with leading dimension n.
+cudaError_t launch_apply_fp64(bem_ctx* ctx, const double* V, int64_t ldv, int nu, double* Y,
+                              cudaStream_t s);
+// C_j = scale_j * X^H Y_j for a batch of nb right-hand blocks (FP64, deterministic).
+// X: n x p (ldx), Y_j at Y + j * strideY (ldy), C_j at C + j * p * q (p x q, col-major).
+// scale: nullptr (1) or 2 nb doubles (complex, device).
+cudaError_t launch_xhy_fp64(bem_ctx* ctx, const double* X, int64_t ldx, int p, const double* Y,
+                            int64_t ldy, int64_t strideY, int q, int64_t n, int nb,
+                            const double* scale, double* C, cudaStream_t s);
+// mixed-precision fused projection (tcgen05); defined in project_mixed.cu
+bem_status project_mixed(bem_ctx* ctx, const double* V, int64_t ldv, int nu, double* Bhat,
+                         double* AV, cudaStream_t s);
+
+}  // namespace bem

@@ -1,0 +1,116 @@
+// FP64 device helpers shared by the kernels that evaluate the singular self term
+// A_ll(k) = integral over triangle l of exp(i k r) / (4 pi r) about its centroid.
+//
+// Polar coordinates about the centroid x in the plane of the triangle: the radial
+// integral is R h(i k R) with h(w) = (e^w - 1) / w; along each edge (d the distance from
+// x to the edge's line, s the position along the edge from the foot of the perpendicular)
+// the angle is traded for u = asinh(s / d), so R = d cosh(u), d(phi) = du / cosh(u) and
+// the integrand d h(i k d cosh u) is entire in u; 16-point Gauss-Legendre on each side of
+// u = 0.
+#pragma once
+
+#include <math.h>
+
+namespace bem {
+
+constexpr double kPiD = 3.141592653589793238462643383279502884;
+
+struct GL16 {
+  double x[16];
+  double w[16];
+};
+
+// Gauss-Legendre nodes as the roots of P_16 by Newton's method (three-term recurrence).
+inline GL16 make_gl16() {
+  GL16 g;
+  const int n = 16;
+  for (int i = 0; i < n; ++i) {
+    double x = cos(kPiD * (4.0 * i + 3.0) / (4.0 * n + 2.0));
+    double dp = 1.0;
+    for (int it = 0; it < 60; ++it) {
+      double pm = 1.0, p = x;
+      for (int k = 1; k < n; ++k) {
+        const double pn = ((2 * k + 1) * x * p - k * pm) / (k + 1);
+        pm = p;
+        p = pn;
+      }
+      dp = n * (pm - x * p) / (1.0 - x * x);
+      const double step = p / dp;
+      x -= step;
+      if (fabs(step) <= 4e-17) break;
+    }
+    double pm = 1.0, p = x;
+    for (int k = 1; k < n; ++k) {
+      const double pn = ((2 * k + 1) * x * p - k * pm) / (k + 1);
+      pm = p;
+      p = pn;
+    }
+    dp = n * (pm - x * p) / (1.0 - x * x);
+    g.x[i] = x;
+    g.w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+  return g;
+}
+
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// h(w) = (e^w - 1) / w; Taylor series sum_m w^m / (m + 1)! for |w| < 1/2.
+__device__ inline double2 h_fun(double2 w) {
+  if (w.x * w.x + w.y * w.y < 0.25) {
+    double2 s = make_double2(0.0, 0.0), t = make_double2(1.0, 0.0);
+    for (int m = 0; m < 24; ++m) {
+      s.x += t.x;
+      s.y += t.y;
+      t = zmul(t, w);
+      t.x /= (m + 2.0);
+      t.y /= (m + 2.0);
+    }
+    return s;
+  }
+  double sn, cs;
+  sincos(w.y, &sn, &cs);
+  const double e = exp(w.x);
+  const double2 num = make_double2(e * cs - 1.0, e * sn);
+  const double d = w.x * w.x + w.y * w.y;
+  return make_double2((num.x * w.x + num.y * w.y) / d, (num.y * w.x - num.x * w.y) / d);
+}
+
+// Self term of the triangle with vertices v[0..2] about the point x, at wavenumber k.
+__device__ inline double2 self_term(const double v[3][3], const double x[3], double2 k,
+                                    const GL16& gl) {
+  double2 total = make_double2(0.0, 0.0);
+  for (int e = 0; e < 3; ++e) {
+    const double* p = v[e];
+    const double* q = v[(e + 1) % 3];
+    double tx = q[0] - p[0], ty = q[1] - p[1], tz = q[2] - p[2];
+    const double len = sqrt(tx * tx + ty * ty + tz * tz);
+    tx /= len;
+    ty /= len;
+    tz /= len;
+    const double px = p[0] - x[0], py = p[1] - x[1], pz = p[2] - x[2];
+    const double qx = q[0] - x[0], qy = q[1] - x[1], qz = q[2] - x[2];
+    const double sp = px * tx + py * ty + pz * tz;
+    const double sq = qx * tx + qy * ty + qz * tz;
+    const double ox = px - sp * tx, oy = py - sp * ty, oz = pz - sp * tz;
+    const double d = sqrt(ox * ox + oy * oy + oz * oz);
+    const double up = asinh(sp / d), uq = asinh(sq / d);
+    const bool split = up < 0.0 && uq > 0.0;
+    for (int s = 0; s < (split ? 2 : 1); ++s) {
+      const double lo = split ? (s == 0 ? up : 0.0) : up;
+      const double hi = split ? (s == 0 ? 0.0 : uq) : uq;
+      const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
+      for (int gi = 0; gi < 16; ++gi) {
+        const double R = d * cosh(mid + half * gl.x[gi]);
+        const double2 h = h_fun(make_double2(-k.y * R, k.x * R));   // h(i k R)
+        const double f = half * gl.w[gi] * d;
+        total.x += f * h.x;
+        total.y += f * h.y;
+      }
+    }
+  }
+  return make_double2(total.x / (4.0 * kPiD), total.y / (4.0 * kPiD));
+}
+
+}  // namespace bem
