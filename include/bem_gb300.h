@@ -144,6 +144,30 @@ bem_status bem_set_timing(bem_ctx* ctx, int enable);
 bem_status bem_kernel_times(bem_ctx* ctx, double* ms_out, int max_out, int* count);
 bem_status bem_microbench(bem_ctx* ctx, int kind, double* ops_per_s);
 
+/*
+ * Allocation-free projection (the paper has no counterpart: this serves callers that
+ * cannot call cudaMalloc, such as code running under a locked or externally owned memory
+ * pool, or a process whose device footprint must not grow after start-up).
+ * Computes the same Bhat_j = w_j V^H A(z_j) V as bem_project with BEM_PREC_FP64, without a
+ * context: the caller passes the mesh already on the device (xyz_dev: 3*nv doubles,
+ * tri_dev: 3*nt int32), the contour parameters (as bem_set_contour), V_dev (nt x nu,
+ * column-major, ldv >= nt) and Bhat_dev (N x nu x nu, as bem_project). Every intermediate
+ * lives in one 64 MiB device array inside the library, which each GPU that loads the
+ * library holds until the process exits; nothing is allocated or freed by this call.
+ * Limit: 372*nt + 16*nt*N + 16*nt*nu + 32*N bytes (plus alignment) must fit in 64 MiB,
+ * otherwise BEM_EINVAL (e.g. nt = 3072, N = 32, nu = 64 fits; the nodes are processed in
+ * groups that fit). The first call on a device looks up the array's device address (with
+ * that device current); make that first call before any stream capture. All calls share
+ * the array and it keeps the last call's contents: calls that overlap on the GPU (other
+ * streams or threads) race and must be serialised by the caller. Returns BEM_EINVAL for a
+ * bad argument or a vertex index out of range, BEM_ECUDA on a CUDA error. Synchronises the
+ * stream once (after the geometry checks); the rest is asynchronous on `stream`.
+ */
+bem_status bem_project_fp64_noalloc(int device, int64_t nv, const double* xyz_dev, int64_t nt,
+                                    const int32_t* tri_dev, int kind, double c_re, double c_im,
+                                    double a, double b, int N, const double* V_dev,
+                                    int64_t ldv, int nu, double* Bhat_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -46,6 +46,8 @@ SIGNATURES = {
     "bem_set_timing": (_I, [_P, _I]),
     "bem_kernel_times": (_I, [_P, _P, _I, ctypes.POINTER(_I)]),
     "bem_microbench": (_I, [_P, _I, ctypes.POINTER(_D)]),
+    "bem_project_fp64_noalloc": (_I, [_I, _I64, _P, _I64, _P, _I, _D, _D, _D, _D, _I, _P,
+                                      _I64, _I, _P, _P]),
 }
 
 _lib = None
