@@ -126,6 +126,15 @@ bem_status bem_cholqr2(bem_ctx* ctx, double* V_dev, int64_t n, int64_t ldv, int 
 bem_status bem_residual(bem_ctx* ctx, int m, const double* lam_host, const double* X_dev,
                         int64_t ldx, double* R_dev, double* relres_host, void* stream);
 
+/*
+ * Synchronise `stream` and report errors that kernels recorded in the context's device
+ * status word since the last check (asynchronous calls such as bem_project report device-
+ * side failures here): BEM_ETIMEOUT if a bounded wait inside a kernel gave up (the kernel
+ * then stopped cleanly and its outputs are invalid), BEM_EKERNEL / BEM_EINVAL for other
+ * recorded failures, BEM_ECUDA for a CUDA error. Clears the status word.
+ */
+bem_status bem_check(bem_ctx* ctx, void* stream);
+
 /* Number of CUDA kernels this context has launched since creation (diagnostics). */
 int64_t bem_kernel_launches(const bem_ctx* ctx);
 

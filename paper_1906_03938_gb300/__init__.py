@@ -43,6 +43,7 @@ SIGNATURES = {
     "bem_cholqr2": (_I, [_P, _P, _I64, _I64, _I, _P, _P]),
     "bem_residual": (_I, [_P, _I, _P, _P, _I64, _P, _P, _P]),
     "bem_kernel_launches": (_I64, [_P]),
+    "bem_check": (_I, [_P, _P]),
     "bem_set_timing": (_I, [_P, _I]),
     "bem_kernel_times": (_I, [_P, _P, _I, ctypes.POINTER(_I)]),
     "bem_microbench": (_I, [_P, _I, ctypes.POINTER(_D)]),
@@ -137,6 +138,10 @@ class Context:
     def _chk(self, name, st):
         if st != BEM_OK:
             raise BemError(name, st, self._lib.bem_last_error(self._h).decode())
+
+    def check(self, stream=None):
+        """Synchronise and raise if a kernel recorded a device-side failure."""
+        self._chk("bem_check", self._lib.bem_check(self._h, _stream(stream)))
 
     @property
     def launches(self) -> int:

@@ -59,6 +59,8 @@ bem_status take_status(bem_ctx* ctx, cudaStream_t stream, const char* where) {
   if (h & kStatusZeroArea) m += " zero-area-triangle";
   if (h & kStatusNotSPD) m += " Gram-matrix-not-positive-definite";
   if (h & kStatusNonFinite) m += " non-finite-value";
+  if (h & kStatusTimeout) m += " wait-timeout";
+  if (h & kStatusTimeout) return fail(ctx, BEM_ETIMEOUT, m);
   return fail(ctx, (h & (kStatusBadIndex | kStatusZeroArea)) ? BEM_EINVAL : BEM_EKERNEL, m);
 }
 
@@ -123,6 +125,15 @@ const char* bem_last_error(const bem_ctx* ctx) {
 }
 
 int64_t bem_kernel_launches(const bem_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+bem_status bem_check(bem_ctx* ctx, void* stream) {
+  if (!ctx) return BEM_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  bem_status st = cuda_check(ctx, cudaGetLastError(), "bem_check");
+  if (st != BEM_OK) return st;
+  return take_status(ctx, s, "bem_check");
+}
 
 bem_status bem_set_mesh(bem_ctx* ctx, int64_t nv, const double* xyz_host, int64_t nt,
                         const int32_t* tri_host, void* stream) {

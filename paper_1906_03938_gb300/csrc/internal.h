@@ -22,6 +22,7 @@ enum : int {
   kStatusZeroArea = 2,     // a triangle of zero area
   kStatusNotSPD = 4,       // a Gram matrix that is not numerically positive definite
   kStatusNonFinite = 8,    // a non-finite value where a finite one is required
+  kStatusTimeout = 16,     // a bounded device wait gave up (the kernel aborted cleanly)
 };
 
 // Device geometry, structure-of-arrays, FP64 (plain path) and FP32 (mixed path).

@@ -1,11 +1,619 @@
-// Mixed-precision fused assembly + projection (FP32 evaluation, BF16x3 tcgen05 contraction).
+// Mixed-precision fused assembly + projection (Section 3, Eq. RR_approx) on GB300.
+//
+// mixed_apply_kernel computes Y_j = A(z_j) V without storing A(z_j):
+//  * a work unit is one 128-row tile of A, a group of G <= 4 contour nodes and a range of
+//    16-column K-blocks (the column range is split when that balances the grid);
+//  * 8 evaluation warps compute each 128 x 16 block of entries in FP32 for the G nodes
+//    (7-point rule: one rsqrt per quadrature point shared by the nodes, then ex2, sin and
+//    cos on the MUFU unit per node; the self term from the FP64 table on the diagonal),
+//    with coordinates taken relative to the tile's first centroid, and write them as four
+//    BF16 planes (Re/Im x hi/lo) into shared memory in the tensor core's canonical K-major
+//    layout;
+//  * one producer warp copies the matching K-block of the prepared BF16 basis planes
+//    (four planes [Vr|Vi], [Vr_lo|Vi_lo], [-Vi|Vr], [-Vi_lo|Vr_lo]) with a bulk TMA copy;
+//  * one MMA warp issues, per node, six tcgen05 BF16 MMAs (M = 128, N = 2 C, K = 16)
+//    that add Ar_hi[Vr|Vi] + Ar_hi[Vr_lo|Vi_lo] + Ar_lo[Vr|Vi] + Ai_hi[-Vi|Vr]
+//    + Ai_hi[-Vi_lo|Vr_lo] + Ai_lo[-Vi|Vr] into an FP32 accumulator [Yr | Yi] in TMEM
+//    (the split-precision "BF16x3" complex product);
+//  * two shared-memory stages overlap evaluation, copies and MMAs (mbarriers; every wait
+//    is bounded and a timeout aborts the block cleanly with an error status);
+//  * the evaluation warps finally read the accumulators from TMEM and store the FP32
+//    partial Y of the unit.
+// mixed_vhy_kernel then forms Bhat_j = w_j V^H (sum over column splits of Y_j) in FP64
+// with a fixed summation order.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <algorithm>
+
 #include "internal.h"
+#include "sm100.cuh"
 
 namespace bem {
+namespace {
 
-bem_status project_mixed(bem_ctx* ctx, const double*, int64_t, int, double*, double*,
-                         cudaStream_t) {
-  return fail(ctx, BEM_EINVAL, "bem_project: mixed precision path not available in this build");
+using namespace sm100;
+
+constexpr int kBM = 128;            // rows per tile (MMA M)
+constexpr int kBK = 16;             // columns per K-block (MMA K)
+constexpr int kStages = 2;
+constexpr int kEvalWarps = 8;
+constexpr int kEvalThreads = 32 * kEvalWarps;
+constexpr int kThreads = 32 * (2 + kEvalWarps);
+constexpr int kMaxG = 4;
+constexpr int kPlaneBytes = kBM * kBK * 2;   // one BF16 plane of a 128 x 16 block: 4 KB
+constexpr uint32_t kWaitLimit = 1u << 24;    // polls (with 64 ns sleeps) before giving up
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kInv2Pi = 0.15915494309189535f;
+constexpr float kTwoPiHi = 6.28318548202514648f;      // float nearest 2 pi
+constexpr float kTwoPiLo = -1.7484555314695172e-7f;   // 2 pi - kTwoPiHi
+
+struct MixedParams {
+  int64_t n;          // unknowns
+  int N;              // nodes
+  int nu;             // basis columns
+  int nup;            // nu rounded up to a multiple of 8
+  int C;              // basis columns per MMA chunk (N of the MMA = 2 C)
+  int nchunks;        // nup / C
+  int G;              // nodes per unit
+  int nG;             // node groups
+  int nK;             // K-blocks
+  int S;              // column splits
+  int n_pad;          // rows rounded up to 128
+  const double* cx;   // FP64 centroids, SoA
+  const double* qp;   // FP64 quadrature points, q-major SoA
+  const double* qw;   // FP64 weights / 4 pi
+  const double* self; // FP64 complex self terms, node-major
+  const double* z;    // FP64 complex nodes
+  const __nv_bfloat16* Bp;   // prepared basis planes, tile-native
+  float* Yp;          // FP32 partial products [S][N][2 nup][n_pad]
+  int* status;
+};
+
+struct SmemLayout {
+  uint32_t a_off, b_off, row_off, col_off, bar_off, misc_off, total;
+  uint32_t a_stage_bytes, b_stage_bytes;
+};
+
+__host__ __device__ inline SmemLayout smem_layout(int G, int nup) {
+  SmemLayout L;
+  L.a_stage_bytes = (uint32_t)G * 4 * kPlaneBytes;
+  L.b_stage_bytes = (uint32_t)256 * nup;     // 4 planes x 2 nup rows x 16 k x 2 B
+  L.a_off = 0;
+  L.b_off = L.a_off + kStages * L.a_stage_bytes;
+  L.row_off = L.b_off + kStages * L.b_stage_bytes;
+  L.col_off = L.row_off + kBM * 4 * 4;           // 128 rows x (x, y, z, valid)
+  L.bar_off = L.col_off + kBK * 28 * 4;          // 16 columns x (21 coords + 7 weights)
+  L.misc_off = L.bar_off + 8 * 8;                // 7 mbarriers (+1 pad)
+  L.total = L.misc_off + 16;                     // tmem slot, abort flag
+  return L;
+}
+
+__device__ __forceinline__ float ex2f(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sinf_mufu(float x) {
+  float r;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float cosf_mufu(float x) {
+  float r;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsqrtf_mufu(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(lo_elem, hi_elem);   // .x -> low 16 bits
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// OR of v over the evaluation threads (named barrier 1): a block-uniform decision
+__device__ __forceinline__ int eval_barrier_or(int v) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.s32 q, %1, 0;\n\t"
+      "bar.red.or.pred p, 1, %2, q;\n\t"
+      "selp.s32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(r)
+      : "r"(v), "n"(kEvalThreads)
+      : "memory");
+  return r;
+}
+
+// bounded wait that also watches the block's abort flag
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
+                                              volatile int* abort_flag, int* status) {
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (it > 64) __nanosleep(64);
+  }
+  atomicOr(status, kStatusTimeout);
+  *abort_flag = 1;
+  return false;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const SmemLayout L = smem_layout(p.G, p.nup);
+  unsigned char* sA = smem + L.a_off;
+  unsigned char* sB = smem + L.b_off;
+  float4* sRow = reinterpret_cast<float4*>(smem + L.row_off);
+  float* sCol = reinterpret_cast<float*>(smem + L.col_off);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
+  uint64_t* afull = bars;        // [2] evaluation warps -> MMA
+  uint64_t* bfull = bars + 2;    // [2] bulk copy -> MMA
+  uint64_t* empty = bars + 4;    // [2] MMA done with the stage
+  uint64_t* accfull = bars + 6;  // accumulators final
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.misc_off);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.misc_off + 4);
+
+  const int warp = threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+
+  // unit -> (row tile, node group, column split)
+  const int u = blockIdx.x;
+  const int split = u % p.S;
+  const int t = u / p.S;
+  const int gg = t % p.nG;
+  const int rt = t / p.nG;
+  const int64_t row0 = (int64_t)rt * kBM;
+  const int kb0 = (int)((int64_t)p.nK * split / p.S);
+  const int kb1 = (int)((int64_t)p.nK * (split + 1) / p.S);
+  const int nkb = kb1 - kb0;
+  const int j0 = gg * p.G;
+  const int Gv = min(p.G, p.N - j0);
+  const uint32_t acc_cols = 2u * p.nup;                 // TMEM columns per node
+  uint32_t tmem_cols = 32;
+  while (tmem_cols < (uint32_t)p.G * acc_cols) tmem_cols <<= 1;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&afull[s], kEvalThreads);
+      mbar_init(&bfull[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accfull, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, tmem_cols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- producer: basis planes by bulk copy ----------------
+    if (lane == 0) {
+      int issued = 0;
+      for (int it = 0; it < nkb; ++it) {
+        const int s = it % kStages;
+        const uint32_t par = (it / kStages) & 1;
+        if (!wait_or_abort(&empty[s], par ^ 1, abort_flag, p.status)) break;
+        mbar_arrive_expect_tx(&bfull[s], L.b_stage_bytes);
+        bulk_g2s(sB + s * L.b_stage_bytes,
+                 reinterpret_cast<const unsigned char*>(p.Bp) +
+                     (size_t)(kb0 + it) * L.b_stage_bytes,
+                 L.b_stage_bytes, &bfull[s]);
+        ++issued;
+      }
+      if (*abort_flag) {
+        // let copies in flight land before the block exits (bounded)
+        for (int it = max(0, issued - kStages); it < issued; ++it)
+          mbar_wait(&bfull[it % kStages], (it / kStages) & 1, kWaitLimit);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(kBM, 2 * p.C);
+      // (A plane, B plane) pairs of the split-precision complex product
+      const int pa[6] = {0, 0, 1, 2, 2, 3};   // Ar_hi, Ar_hi, Ar_lo, Ai_hi, Ai_hi, Ai_lo
+      const int pb[6] = {0, 1, 0, 2, 3, 2};   // [Vr|Vi], [Vr_lo|Vi_lo], [-Vi|Vr], [-Vi_lo|Vr_lo]
+      const uint32_t bplane = 2u * p.C * kBK * 2;   // bytes of one basis plane per chunk
+      for (int it = 0; it < nkb; ++it) {
+        const int s = it % kStages;
+        const uint32_t par = (it / kStages) & 1;
+        if (!wait_or_abort(&afull[s], par, abort_flag, p.status)) break;
+        if (!wait_or_abort(&bfull[s], par, abort_flag, p.status)) break;
+        tc_fence_after();
+        const uint32_t a_base = smem_u32(sA + s * L.a_stage_bytes);
+        const uint32_t b_base = smem_u32(sB + s * L.b_stage_bytes);
+        for (int g = 0; g < Gv; ++g) {
+          for (int c = 0; c < p.nchunks; ++c) {
+            const uint32_t d = tmem_base + g * acc_cols + c * 2 * p.C;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+              const uint64_t ad = smem_desc(a_base + (g * 4 + pa[q]) * kPlaneBytes, 128, 256);
+              const uint64_t bd = smem_desc(b_base + (c * 4 + pb[q]) * bplane, 128, 256);
+              mma_bf16(d, ad, bd, idesc, (it > 0 || q > 0) ? 1u : 0u);
+            }
+          }
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(accfull);
+    }
+  } else {
+    // ---------------- evaluation warps ----------------
+    const int e = warp - 2;               // 0..7
+    const int et = threadIdx.x - 64;      // 0..255
+    // origin of this tile's relative coordinates
+    const int64_t i_org = row0 < p.n ? row0 : p.n - 1;
+    const double ox = p.cx[i_org], oy = p.cx[p.n + i_org], oz = p.cx[2 * p.n + i_org];
+    if (et < kBM) {
+      const int64_t i = row0 + et;
+      float4 v = make_float4(2.0f, 2.0f, 2.0f, 0.f);   // padding rows: zeroed after evaluation
+      if (i < p.n)
+        v = make_float4((float)(p.cx[i] - ox), (float)(p.cx[p.n + i] - oy),
+                        (float)(p.cx[2 * p.n + i] - oz), 1.f);
+      sRow[et] = v;
+    }
+    // node constants
+    float kr[kMaxG], kmi[kMaxG];
+#pragma unroll
+    for (int g = 0; g < kMaxG; ++g) {
+      const int j = j0 + (g < Gv ? g : 0);
+      kr[g] = (float)p.z[2 * j];
+      kmi[g] = (float)(-p.z[2 * j + 1]) * kLog2e;
+    }
+    // this thread's 2 x 4 entries: rows 16 e + {0, 8} + r8, columns 8 kg + 2 kp + {0, 1}
+    const int r8 = lane / 4, kp = lane % 4;
+
+    for (int it = 0; it < nkb; ++it) {
+      const int s = it % kStages;
+      const uint32_t par = (it / kStages) & 1;
+      const int kb = kb0 + it;
+      // every evaluation thread takes the same exit decision here (this is also the
+      // barrier that protects the column geometry of the previous K-block)
+      if (eval_barrier_or(*abort_flag)) break;
+      // stage the K-block's column geometry (all evaluation threads)
+      for (int x = et; x < kBK * 28; x += kEvalThreads) {
+        const int k = x / 28, f = x % 28;
+        const int64_t l = (int64_t)kb * kBK + k;
+        // padding columns: finite placeholders; their entries are zeroed after evaluation
+        float val = f < 21 ? 1.0f : 0.f;
+        if (l < p.n) {
+          if (f < 21) {
+            const int c = f / 7, q = f % 7;
+            const double o = c == 0 ? ox : (c == 1 ? oy : oz);
+            val = (float)(p.qp[(7 * c + q) * p.n + l] - o);
+          } else {
+            val = (float)p.qw[(f - 21) * p.n + l];
+          }
+        }
+        sCol[k * 28 + f] = val;
+      }
+      asm volatile("bar.sync 1, %0;" ::"n"(kEvalThreads) : "memory");
+      const bool ready = wait_or_abort(&empty[s], par ^ 1, abort_flag, p.status);
+      unsigned char* a_stage = sA + s * L.a_stage_bytes;
+#pragma unroll 1
+      for (int cm = 0; cm < (ready ? 4 : 0); ++cm) {
+        const int rg = 2 * e + (cm >> 1);
+        const int kg = cm & 1;
+        const int row = 8 * rg + r8;
+        const int k0 = 8 * kg + 2 * kp;
+        const float4 xr = sRow[row];
+        const int64_t i = row0 + row;
+        const int64_t l0 = (int64_t)kb * kBK + k0;
+        float rr[2][7], am[2][7];
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+          const float* col = sCol + (k0 + d) * 28;
+#pragma unroll
+          for (int q = 0; q < 7; ++q) {
+            const float dx = xr.x - col[q], dy = xr.y - col[7 + q], dz = xr.z - col[14 + q];
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float rs = rsqrtf_mufu(r2);
+            rr[d][q] = r2 * rs;
+            am[d][q] = col[21 + q] * rs;
+          }
+        }
+        const uint32_t off = rg * 256 + kg * 128 + r8 * 16 + kp * 4;
+#pragma unroll
+        for (int g = 0; g < kMaxG; ++g) {
+          if (g >= Gv) break;
+          float re[2], im[2];
+#pragma unroll
+          for (int d = 0; d < 2; ++d) {
+            float sr = 0.f, si = 0.f;
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+              const float a = am[d][q] * ex2f(kmi[g] * rr[d][q]);
+              const float ph = kr[g] * rr[d][q];
+              const float nrot = fmaf(ph, kInv2Pi, 12582912.0f) - 12582912.0f;
+              const float red = fmaf(-nrot, kTwoPiLo, fmaf(-nrot, kTwoPiHi, ph));
+              sr = fmaf(a, cosf_mufu(red), sr);
+              si = fmaf(a, sinf_mufu(red), si);
+            }
+            if (i == l0 + d && i < p.n) {   // diagonal: the self term
+              const double2 sv = reinterpret_cast<const double2*>(p.self)[(int64_t)(j0 + g) * p.n + i];
+              sr = (float)sv.x;
+              si = (float)sv.y;
+            }
+            if (i >= p.n || l0 + d >= p.n) {   // padding rows / columns of the tile
+              sr = 0.f;
+              si = 0.f;
+            }
+            re[d] = sr;
+            im[d] = si;
+          }
+          const uint32_t hr = pack_bf16(re[0], re[1]);
+          const uint32_t hi = pack_bf16(im[0], im[1]);
+          const uint32_t lr = pack_bf16(re[0] - __uint_as_float(hr << 16),
+                                        re[1] - __uint_as_float(hr & 0xFFFF0000u));
+          const uint32_t li = pack_bf16(im[0] - __uint_as_float(hi << 16),
+                                        im[1] - __uint_as_float(hi & 0xFFFF0000u));
+          unsigned char* ag = a_stage + g * 4 * kPlaneBytes + off;
+          *reinterpret_cast<uint32_t*>(ag + 0 * kPlaneBytes) = hr;
+          *reinterpret_cast<uint32_t*>(ag + 1 * kPlaneBytes) = lr;
+          *reinterpret_cast<uint32_t*>(ag + 2 * kPlaneBytes) = hi;
+          *reinterpret_cast<uint32_t*>(ag + 3 * kPlaneBytes) = li;
+        }
+      }
+      fence_proxy_async_smem();
+      mbar_arrive(&afull[s]);
+    }
+
+    // ---------------- epilogue: TMEM -> FP32 partial Y ----------------
+    const bool ok = !*abort_flag && wait_or_abort(accfull, 0, abort_flag, p.status);
+    if (__all_sync(0xffffffffu, ok)) {   // tcgen05.ld is warp-collective
+      tc_fence_after();
+      const int quarter = warp % 4;              // TMEM lanes this warp may read
+      const int half = (warp - 2) / 4;           // two warps per quarter split the columns
+      const int row = quarter * 32 + lane;
+      const int64_t i = row0 + row;
+      const uint32_t cols_total = (uint32_t)Gv * acc_cols;
+      for (uint32_t c0 = half * 16; c0 < cols_total; c0 += 32) {
+        float v[16];
+        tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + c0, v);
+        const int g = c0 / acc_cols;
+        const int col = c0 % acc_cols;
+        float* dst = p.Yp + (((size_t)split * p.N + (j0 + g)) * acc_cols + col) * p.n_pad + i;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) dst[(size_t)k * p.n_pad] = v[k];
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    // the accumulators may only be released once every MMA has completed (bounded wait:
+    // immediate on the normal path, where the epilogue has already seen it)
+    if (lane == 0) mbar_wait(accfull, 0, kWaitLimit);
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem_base, tmem_cols);
+  }
+}
+
+// Basis planes in the tile-native layout the kernel copies per K-block: for K-block kb,
+// chunk c, plane pl, the 2C x 16 block in core matrices (row group ng, k group kg) of
+// 8 rows x 8 bf16, row stride 16 B, at ng * 256 + kg * 128 bytes.
+__global__ void prep_basis_planes_kernel(const double* __restrict__ V, int64_t ldv, int64_t n,
+                                         int nu, int nup, int C, int nK,
+                                         __nv_bfloat16* __restrict__ Bp) {
+  const int64_t total = (int64_t)nK * 4 * 2 * nup * kBK;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  // decode in the order of the layout
+  int64_t x = t;
+  const int k8 = (int)(x % 8); x /= 8;
+  const int r8 = (int)(x % 8); x /= 8;
+  const int kg = (int)(x % 2); x /= 2;
+  const int ngroups = 2 * C / 8;
+  const int ng = (int)(x % ngroups); x /= ngroups;
+  const int pl = (int)(x % 4); x /= 4;
+  const int nchunks = nup / C;
+  const int c = (int)(x % nchunks); x /= nchunks;
+  const int kb = (int)x;
+  const int rowN = ng * 8 + r8;                 // 0 .. 2C
+  const int halfim = rowN >= C;                 // 0: feeds Yr, 1: feeds Yi
+  const int col = c * C + (rowN % C);
+  const int64_t l = (int64_t)kb * kBK + kg * 8 + k8;
+  double vr = 0.0, vi = 0.0;
+  if (l < n && col < nu) {
+    const double2 v = reinterpret_cast<const double2*>(V)[(int64_t)col * ldv + l];
+    vr = v.x;
+    vi = v.y;
+  }
+  const __nv_bfloat16 vr_hi = __double2bfloat16(vr);
+  const __nv_bfloat16 vi_hi = __double2bfloat16(vi);
+  const __nv_bfloat16 vr_lo = __double2bfloat16(vr - (double)__bfloat162float(vr_hi));
+  const __nv_bfloat16 vi_lo = __double2bfloat16(vi - (double)__bfloat162float(vi_hi));
+  __nv_bfloat16 out;
+  switch (pl) {
+    case 0: out = halfim ? vi_hi : vr_hi; break;                    // [Vr | Vi]
+    case 1: out = halfim ? vi_lo : vr_lo; break;                    // [Vr_lo | Vi_lo]
+    case 2: out = halfim ? vr_hi : __hneg(vi_hi); break;            // [-Vi | Vr]
+    default: out = halfim ? vr_lo : __hneg(vi_lo); break;           // [-Vi_lo | Vr_lo]
+  }
+  Bp[t] = out;
+}
+
+// Bhat_j = w_j V^H Y_j with Y_j = sum over splits of the FP32 partials (FP64 sums in a
+// fixed order); optionally AV_j = Y_j in FP64.
+constexpr int kT = 32;
+__global__ void __launch_bounds__(256)
+mixed_vhy_kernel(const double* __restrict__ V, int64_t ldv, int nu, int64_t n, int n_pad,
+                 int N, int S, int acc_cols, int C, const float* __restrict__ Yp,
+                 const double* __restrict__ w, double* __restrict__ Bhat) {
+  __shared__ double2 sX[kT][kT + 1];
+  __shared__ double2 sY[kT][kT + 1];
+  const int tiles_a = (nu + kT - 1) / kT;
+  const int ta = blockIdx.x % tiles_a, tb = blockIdx.x / tiles_a;
+  const int j = blockIdx.y;
+  const int tid = threadIdx.x;
+  const int oa = tid % kT, ob0 = tid / kT;
+  double2 acc[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) acc[m] = make_double2(0.0, 0.0);
+  const double2* Vc = reinterpret_cast<const double2*>(V);
+  for (int64_t r0 = 0; r0 < n; r0 += kT) {
+    __syncthreads();
+    for (int x = tid; x < kT * kT; x += 256) {
+      const int rr = x % kT, cc = x / kT;
+      const int64_t r = r0 + rr;
+      const int a = ta * kT + cc, b = tb * kT + cc;
+      sX[rr][cc] = (r < n && a < nu) ? Vc[(int64_t)a * ldv + r] : make_double2(0.0, 0.0);
+      double2 y = make_double2(0.0, 0.0);
+      if (r < n && b < nu) {
+        const int colr = (b / C) * 2 * C + (b % C);
+        for (int s = 0; s < S; ++s) {
+          const float* base = Yp + ((size_t)s * N + j) * acc_cols * (size_t)n_pad;
+          y.x += base[(size_t)colr * n_pad + r];
+          y.y += base[(size_t)(colr + C) * n_pad + r];
+        }
+      }
+      sY[rr][cc] = y;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < kT; ++rr) {
+      const double2 x = sX[rr][oa];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const double2 y = sY[rr][ob0 + 8 * m];
+        acc[m].x = fma(x.x, y.x, fma(x.y, y.y, acc[m].x));
+        acc[m].y = fma(x.x, y.y, fma(-x.y, y.x, acc[m].y));
+      }
+    }
+  }
+  const double2 s = reinterpret_cast<const double2*>(w)[j];
+  const int a = ta * kT + oa;
+  if (a < nu) {
+    double2* Bj = reinterpret_cast<double2*>(Bhat) + (int64_t)j * nu * nu;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int b = tb * kT + ob0 + 8 * m;
+      if (b < nu)
+        Bj[(int64_t)b * nu + a] = make_double2(s.x * acc[m].x - s.y * acc[m].y,
+                                              s.x * acc[m].y + s.y * acc[m].x);
+    }
+  }
+}
+
+__global__ void mixed_av_kernel(int64_t n, int n_pad, int nu, int N, int S, int acc_cols, int C,
+                                const float* __restrict__ Yp, double* __restrict__ AV) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)N * nu * n) return;
+  const int64_t i = t % n;
+  const int b = (int)((t / n) % nu);
+  const int j = (int)(t / (n * (int64_t)nu));
+  const int colr = (b / C) * 2 * C + (b % C);
+  double re = 0.0, im = 0.0;
+  for (int s = 0; s < S; ++s) {
+    const float* base = Yp + ((size_t)s * N + j) * acc_cols * (size_t)n_pad;
+    re += base[(size_t)colr * n_pad + i];
+    im += base[(size_t)(colr + C) * n_pad + i];
+  }
+  reinterpret_cast<double2*>(AV)[t] = make_double2(re, im);
+}
+
+// Column splits: the fewest that fill whole waves of the device to >= 90 %.
+int choose_splits(int64_t units1, int nK, int sms) {
+  int best = 1;
+  double best_eff = 0.0;
+  const int smax = std::max(1, std::min(8, nK / 4));
+  for (int S = 1; S <= smax; ++S) {
+    const int64_t u = units1 * S;
+    const int64_t waves = (u + sms - 1) / sms;
+    const double eff = (double)u / (double)(waves * sms);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = S;
+    }
+    if (eff >= 0.9) break;
+  }
+  return best;
+}
+
+}  // namespace
+
+bem_status project_mixed(bem_ctx* ctx, const double* V, int64_t ldv, int nu, double* Bhat,
+                         double* AV, cudaStream_t s) {
+  const int64_t n = ctx->geo.n;
+  const int N = ctx->con.N;
+  MixedParams p{};
+  p.n = n;
+  p.N = N;
+  p.nu = nu;
+  p.nup = (nu + 7) / 8 * 8;
+  p.C = p.nup <= 128 ? p.nup : 128;
+  if (p.nup % p.C != 0) p.nup = (p.nup + p.C - 1) / p.C * p.C;
+  p.nchunks = p.nup / p.C;
+  const int acc_cols = 2 * p.nup;
+  p.G = std::max(1, std::min(std::min(N, kMaxG), 512 / acc_cols));
+  p.nG = (N + p.G - 1) / p.G;
+  p.nK = (int)((n + kBK - 1) / kBK);
+  p.n_pad = (int)((n + kBM - 1) / kBM * kBM);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  const int64_t rtiles = p.n_pad / kBM;
+  p.S = choose_splits(rtiles * p.nG, p.nK, std::max(1, sms));
+
+  // scratch: basis planes, then the FP32 partials
+  const size_t bp_bytes = (size_t)p.nK * 256 * p.nup;
+  const size_t bp_off = 0;
+  const size_t yp_off = (bp_bytes + 255) / 256 * 256;
+  const size_t yp_bytes = (size_t)p.S * N * acc_cols * p.n_pad * sizeof(float);
+  bem_status st = ensure_scratch(ctx, yp_off + yp_bytes);
+  if (st != BEM_OK) return st;
+  unsigned char* scr = reinterpret_cast<unsigned char*>(ctx->d_scratch);
+  p.Bp = reinterpret_cast<const __nv_bfloat16*>(scr + bp_off);
+  p.Yp = reinterpret_cast<float*>(scr + yp_off);
+  p.cx = ctx->geo.cx;
+  p.qp = ctx->geo.qp;
+  p.qw = ctx->geo.qw;
+  p.self = ctx->con.self;
+  p.z = ctx->con.z;
+  p.status = ctx->d_status;
+
+  const int64_t prep_total = (int64_t)p.nK * 4 * 2 * p.nup * kBK;
+  prep_basis_planes_kernel<<<(unsigned)((prep_total + 255) / 256), 256, 0, s>>>(
+      V, ldv, n, nu, p.nup, p.C, p.nK,
+      reinterpret_cast<__nv_bfloat16*>(scr + bp_off));
+  ctx->launches++;
+
+  const SmemLayout L = smem_layout(p.G, p.nup);
+  st = cuda_check(ctx, cudaFuncSetAttribute(mixed_apply_kernel,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)L.total),
+                  "mixed kernel attribute");
+  if (st != BEM_OK) return st;
+  const int64_t units = rtiles * p.nG * p.S;
+  timing_begin(ctx, s);
+  mixed_apply_kernel<<<(unsigned)units, kThreads, L.total, s>>>(p);
+  timing_end(ctx, s);
+  ctx->launches++;
+  st = cuda_check(ctx, cudaGetLastError(), "mixed apply kernel");
+  if (st != BEM_OK) return st;
+
+  const int tiles = ((nu + kT - 1) / kT) * ((nu + kT - 1) / kT);
+  mixed_vhy_kernel<<<dim3((unsigned)tiles, (unsigned)N), 256, 0, s>>>(
+      V, ldv, nu, n, p.n_pad, N, p.S, acc_cols, p.C, p.Yp, ctx->con.w, Bhat);
+  ctx->launches++;
+  if (AV) {
+    const int64_t tot = (int64_t)N * nu * n;
+    mixed_av_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, p.n_pad, nu, N, p.S,
+                                                                  acc_cols, p.C, p.Yp, AV);
+    ctx->launches++;
+  }
+  return cuda_check(ctx, cudaGetLastError(), "mixed projection kernels");
 }
 
 }  // namespace bem
