@@ -37,7 +37,9 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    p.add_argument("--plain-steps", type=int, default=2,
+                   help="steps of the plain FP64 path timed for the speedup (0: skip)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -258,7 +260,6 @@ def run_ours(args):
 
     # roofline of the dominant kernel
     kern_avg = statistics.mean(kern_ms) if kern_ms else float("nan")
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if prec == bem.PREC_FP64:
         # plain path: FP64 pipe; algorithmic work = the complex MAC of every entry with
         # every basis column, 8 nu flops per entry
@@ -268,15 +269,43 @@ def run_ours(args):
                 "peak": peak / 1e12, "unit": "TFLOP/s",
                 "peak_source": "measured FP64 FMA microbenchmark (bem_microbench)"}
     else:
-        ex2 = ctx.microbench("ex2")
-        ops = entries * 7 * 3   # ex2, sin, cos per quadrature point
-        roof = {"bound": "alu", "pipe": "mufu", "achieved": ops / (kern_avg * 1e-3) / 1e12,
-                "peak": ex2 / 1e12, "unit": "Tops/s",
-                "peak_source": "measured MUFU ex2 microbenchmark (bem_microbench)"}
+        # mixed path: the MUFU unit binds. Per entry and node the method needs one complex
+        # exponential per quadrature point (ex2, sin, cos) and, shared by the G nodes of a
+        # unit, one rsqrt per quadrature point. Roof = entries/s if the MUFU unit did only
+        # that work at its measured rates.
+        rates = {k: ctx.microbench(k) for k in ("ex2", "sin", "cos", "rsqrt")}
+        G = min(N, 4, max(1, 512 // (2 * ((nu + 7) // 8 * 8))))
+        t_entry = 7 * (1 / rates["ex2"] + 1 / rates["sin"] + 1 / rates["cos"]) + \
+            7 / (G * rates["rsqrt"])
+        roof = {"bound": "alu", "pipe": "mufu", "achieved": entries / (kern_avg * 1e-3),
+                "peak": 1.0 / t_entry, "unit": "entries/s",
+                "peak_source": "measured MUFU rates (bem_microbench): "
+                               + ", ".join(f"{k} {v:.3e}/s" for k, v in rates.items())
+                               + f"; 21 MUFU ops per entry-node + 7 rsqrt per entry / G={G}"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
     roof["kernel_ms"] = kern_avg
     roof["launches_timed"] = len(kern_ms)
+
+    plain = None
+    if prec != bem.PREC_FP64 and args.plain_steps > 0:
+        # the plain FP64 GPU path on the same workload, for the speedup of the mixed form
+        ms = []
+        for _ in range(args.plain_steps):
+            flush.fill_(0.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.set_mesh(mesh.xyz, mesh.tri)
+            ctx.set_contour(c.kind, c.centre, c.a, c.b, N)
+            V_work.copy_(V_res, non_blocking=True)
+            ctx.cholqr2(V_work, want_R=False)
+            ctx.project(V_work, bem.PREC_FP64, Bhat=B_dev)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        plain = {"value": entries / (statistics.mean(ms) * 1e-3), "unit": UNIT,
+                 "ms_per_step": statistics.mean(ms), "steps": len(ms),
+                 "speedup_of_mixed": statistics.mean(ms) / (1e3 * t_total / args.steps)}
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -299,6 +328,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": bo},
         "gpu_launches": launches,
         "clocks": clk,
+        "plain_fp64": plain,
     }
     print(json.dumps(line), flush=True)
     ctx.close()

@@ -79,8 +79,10 @@ bem_status bem_set_mesh(bem_ctx* ctx, int64_t nv, const double* xyz_host, int64_
  * (kind CIRCLE uses b = a):
  *     z_j = c + a cos(theta_j) + i b sin(theta_j),
  *     w_j = (b cos(theta_j) + i a sin(theta_j)) / N,
- * so that A(z) ~ sum_j w_j A(z_j) / (z_j - z) inside the contour. Also evaluates the
- * self-term table A_ii(z_j) for the current mesh. z_host / w_host (2*N doubles each) may
+ * so that A(z) ~ sum_j w_j A(z_j) / (z_j - z) inside the contour. The self terms A_ii(z_j)
+ * of the current mesh are evaluated by the first bem_project after this call (in the
+ * precision that projection uses) and kept until the mesh or contour changes. z_host /
+ * w_host (2*N doubles each) may
  * be NULL; if given they receive the nodes / weights. Requires a mesh. N in [1, 4096],
  * a > 0, b > 0. Synchronises the stream before returning.
  */
@@ -147,7 +149,7 @@ int64_t bem_kernel_launches(const bem_ctx* ctx);
  *   At most 256 launches are kept between resets.
  * bem_microbench: measured throughput (operations per second over the whole device) of
  *   one pipe: kind 0 FP64 FMA (2 flops each), 1 FP32 FMA (2 flops each), 2 MUFU ex2,
- *   3 MUFU sin, 4 MUFU cos. Synchronous; runs on the legacy default stream.
+ *   3 MUFU sin, 4 MUFU cos, 5 MUFU rsqrt. Synchronous; runs on the legacy default stream.
  */
 bem_status bem_set_timing(bem_ctx* ctx, int enable);
 bem_status bem_kernel_times(bem_ctx* ctx, double* ms_out, int max_out, int* count);

@@ -159,8 +159,8 @@ class Context:
 
     def microbench(self, kind):
         """Measured device throughput in ops/s: 'fp64_fma', 'fp32_fma' (flops), 'ex2',
-        'sin', 'cos' (MUFU operations)."""
-        kinds = {"fp64_fma": 0, "fp32_fma": 1, "ex2": 2, "sin": 3, "cos": 4}
+        'sin', 'cos', 'rsqrt' (MUFU operations)."""
+        kinds = {"fp64_fma": 0, "fp32_fma": 1, "ex2": 2, "sin": 3, "cos": 4, "rsqrt": 5}
         r = _D(0.0)
         self._chk("bem_microbench", self._lib.bem_microbench(self._h, kinds[kind], ctypes.byref(r)))
         return r.value

@@ -71,11 +71,27 @@ static void free_geometry(Geometry& g) {
 }
 
 static void free_contour(Contour& c) {
-  cudaFree(c.z); cudaFree(c.w); cudaFree(c.self);
+  cudaFree(c.z); cudaFree(c.w); cudaFree(c.self); cudaFree(c.self32);
   c.z = c.w = c.self = nullptr;
+  c.self32 = nullptr;
+  c.self64_ready = c.self32_ready = false;
   c.N = 0;
   c.cap_N = 0;
   c.cap_self = 0;
+}
+
+bem_status ensure_self64(bem_ctx* ctx, cudaStream_t s) {
+  if (ctx->con.self64_ready) return BEM_OK;
+  bem_status st = cuda_check(ctx, launch_self_terms(ctx, s), "self-term kernel");
+  if (st == BEM_OK) ctx->con.self64_ready = true;
+  return st;
+}
+
+bem_status ensure_self32(bem_ctx* ctx, cudaStream_t s) {
+  if (ctx->con.self32_ready) return BEM_OK;
+  bem_status st = cuda_check(ctx, launch_self_terms32(ctx, s), "self-term kernel");
+  if (st == BEM_OK) ctx->con.self32_ready = true;
+  return st;
 }
 
 }  // namespace bem
@@ -206,7 +222,8 @@ bem_status bem_set_contour(bem_ctx* ctx, int kind, double c_re, double c_im, dou
     free_contour(c);
     bool ok = cudaMalloc(&c.z, 2 * N * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&c.w, 2 * N * sizeof(double)) == cudaSuccess &&
-              cudaMalloc(&c.self, 2 * need_self * sizeof(double)) == cudaSuccess;
+              cudaMalloc(&c.self, 2 * need_self * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&c.self32, 2 * need_self * sizeof(float)) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       free_contour(c);
@@ -216,8 +233,8 @@ bem_status bem_set_contour(bem_ctx* ctx, int kind, double c_re, double c_im, dou
     c.cap_self = need_self;
   }
   c.N = N; c.kind = kind; c.c_re = c_re; c.c_im = c_im; c.a = a; c.b = b;
+  c.self64_ready = c.self32_ready = false;   // filled by the first projection that needs them
   bem_status st = cuda_check(ctx, launch_contour(ctx, s), "contour kernel");
-  if (st == BEM_OK) st = cuda_check(ctx, launch_self_terms(ctx, s), "self-term kernel");
   if (st == BEM_OK)
     st = cuda_check(ctx, cudaMemcpyAsync(c.z_host, c.z, 2 * N * sizeof(double),
                                          cudaMemcpyDeviceToHost, s), "contour copy");
@@ -250,6 +267,8 @@ bem_status bem_project(bem_ctx* ctx, const double* V_dev, int64_t ldv, int nu,
   const int N = ctx->con.N;
   if (precision == BEM_PREC_MIXED) return project_mixed(ctx, V_dev, ldv, nu, Bhat_dev, AV_dev, s);
   if (precision != BEM_PREC_FP64) return fail(ctx, BEM_EINVAL, "bem_project: unknown precision");
+  bem_status st0 = ensure_self64(ctx, s);
+  if (st0 != BEM_OK) return st0;
   double* Y = AV_dev;
   if (!Y) {
     bem_status st = ensure_scratch(ctx, (size_t)N * n * nu * 2 * sizeof(double));

@@ -6,6 +6,8 @@
 // precision for well-conditioned V. All steps are deterministic (fixed-order sums).
 #include <math.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace bem {
@@ -62,20 +64,90 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(double2* G, int nu, int*
   }
 }
 
-// Rinv = R^{-1} for upper-triangular R; one thread per column (back substitution).
+constexpr int kGT = 32;   // Gram output tile
+
+// Partial Gram matrices: block (tile, r) sums conj(V[i][a]) V[i][b] over its row range.
+__global__ void __launch_bounds__(256)
+gram_partial_kernel(const double2* __restrict__ V, int64_t ldv, int64_t n, int nu,
+                    int64_t rows_per_part, double2* __restrict__ part) {
+  __shared__ double2 sX[kGT][kGT + 1];
+  __shared__ double2 sY[kGT][kGT + 1];
+  const int tiles_a = (nu + kGT - 1) / kGT;
+  const int ta = blockIdx.x % tiles_a, tb = blockIdx.x / tiles_a;
+  const int64_t r_begin = (int64_t)blockIdx.y * rows_per_part;
+  const int64_t r_end = min(n, r_begin + rows_per_part);
+  const int tid = threadIdx.x;
+  const int oa = tid % kGT, ob0 = tid / kGT;
+  double2 acc[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) acc[m] = make_double2(0.0, 0.0);
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += kGT) {
+    __syncthreads();
+    for (int x = tid; x < kGT * kGT; x += 256) {
+      const int rr = x % kGT, cc = x / kGT;
+      const int64_t r = r0 + rr;
+      const int a = ta * kGT + cc, b = tb * kGT + cc;
+      sX[rr][cc] = (r < r_end && a < nu) ? V[(int64_t)a * ldv + r] : make_double2(0.0, 0.0);
+      sY[rr][cc] = (r < r_end && b < nu) ? V[(int64_t)b * ldv + r] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < kGT; ++rr) {
+      const double2 x = sX[rr][oa];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const double2 y = sY[rr][ob0 + 8 * m];
+        acc[m].x = fma(x.x, y.x, fma(x.y, y.y, acc[m].x));
+        acc[m].y = fma(x.x, y.y, fma(-x.y, y.x, acc[m].y));
+      }
+    }
+  }
+  const int a = ta * kGT + oa;
+  if (a < nu) {
+    double2* P = part + (int64_t)blockIdx.y * nu * nu;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int b = tb * kGT + ob0 + 8 * m;
+      if (b < nu) P[(int64_t)b * nu + a] = acc[m];
+    }
+  }
+}
+
+// G = sum of the partials in part order (deterministic).
+__global__ void sum_parts_kernel(const double2* __restrict__ part, int parts, int64_t count,
+                                 double2* __restrict__ G) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  double2 s = make_double2(0.0, 0.0);
+  for (int r = 0; r < parts; ++r) {
+    const double2 v = part[(int64_t)r * count + t];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  G[t] = s;
+}
+
+// Rinv = R^{-1} for upper-triangular R; one thread per column (back substitution), with R
+// staged in shared memory when it fits (dynamic size nu * nu * 16 bytes, else 0).
 __global__ void triangular_inverse_kernel(const double2* R, int nu, double2* Rinv) {
+  extern __shared__ double2 sR[];
+  const bool staged = (R != nullptr) && blockDim.x >= nu && nu <= 64;
+  if (staged)
+    for (int t = threadIdx.x; t < nu * nu; t += blockDim.x) sR[t] = R[t];
+  __syncthreads();
+  const double2* Rm = staged ? sR : R;
   const int jcol = blockIdx.x * blockDim.x + threadIdx.x;
   if (jcol >= nu) return;
   for (int i = nu - 1; i >= 0; --i) {
     double2 s = make_double2(i == jcol ? 1.0 : 0.0, 0.0);
     if (i <= jcol) {
       for (int m = i + 1; m <= jcol; ++m) {
-        const double2 r = R[(int64_t)m * nu + i];
+        const double2 r = Rm[(int64_t)m * nu + i];
         const double2 x = Rinv[(int64_t)jcol * nu + m];
         s.x -= r.x * x.x - r.y * x.y;
         s.y -= r.x * x.y + r.y * x.x;
       }
-      const double2 d = R[(int64_t)i * nu + i];   // real positive
+      const double2 d = Rm[(int64_t)i * nu + i];   // real positive
       Rinv[(int64_t)jcol * nu + i] = make_double2(s.x / d.x, s.y / d.x);
     } else {
       Rinv[(int64_t)jcol * nu + i] = make_double2(0.0, 0.0);
@@ -138,19 +210,40 @@ extern "C" bem_status bem_cholqr2(bem_ctx* ctx, double* V_dev, int64_t n, int64_
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   const size_t mat = (size_t)nu * nu * 2;
-  bem_status st = ensure_small(ctx, 4 * mat * sizeof(double));
+  // Gram partials: enough row ranges to occupy the device, at least 64 rows each
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  const int tiles = ((nu + kGT - 1) / kGT) * ((nu + kGT - 1) / kGT);
+  int64_t parts = std::max<int64_t>(1, std::min<int64_t>((n + 63) / 64,
+                                                         (2 * (int64_t)sms + tiles - 1) / tiles));
+  const int64_t rows_per_part = (n + parts - 1) / parts;
+  parts = (n + rows_per_part - 1) / rows_per_part;
+  bem_status st = ensure_small(ctx, (4 + (size_t)parts) * mat * sizeof(double));
   if (st != BEM_OK) return st;
   double2* G = reinterpret_cast<double2*>(ctx->d_small);
   double2* Rinv = G + (size_t)nu * nu;
   double2* R1 = Rinv + (size_t)nu * nu;
   double2* R2 = R1 + (size_t)nu * nu;
+  double2* part = R2 + (size_t)nu * nu;
+  const int inv_threads = 64;   // one block (R staged in shared memory) when nu <= 64
+  const size_t inv_smem = nu <= 64 ? (size_t)nu * nu * sizeof(double2) : 0;
+  if (inv_smem > 48 * 1024) {
+    st = cuda_check(ctx, cudaFuncSetAttribute(triangular_inverse_kernel,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)inv_smem),
+                    "cholqr attribute");
+    if (st != BEM_OK) return st;
+  }
   for (int pass = 0; pass < 2; ++pass) {
     double2* R = pass == 0 ? R1 : R2;
-    st = cuda_check(ctx, launch_xhy_fp64(ctx, V_dev, ldv, nu, V_dev, ldv, 0, nu, n, 1, nullptr,
-                                         reinterpret_cast<double*>(R), s), "gram kernel");
-    if (st != BEM_OK) return st;
+    gram_partial_kernel<<<dim3((unsigned)tiles, (unsigned)parts), 256, 0, s>>>(
+        reinterpret_cast<const double2*>(V_dev), ldv, n, nu, rows_per_part, part);
+    sum_parts_kernel<<<(unsigned)(((int64_t)nu * nu + 255) / 256), 256, 0, s>>>(
+        part, (int)parts, (int64_t)nu * nu, R);
     cholesky_kernel<<<1, 1024, 0, s>>>(R, nu, ctx->d_status);
-    triangular_inverse_kernel<<<(nu + 63) / 64, 64, 0, s>>>(R, nu, Rinv);
+    triangular_inverse_kernel<<<(nu + inv_threads - 1) / inv_threads, inv_threads, inv_smem, s>>>(
+        R, nu, Rinv);
+    ctx->launches += 2;
     right_multiply_kernel<<<(unsigned)((n + kRows - 1) / kRows), 256, 0, s>>>(
         reinterpret_cast<double2*>(V_dev), ldv, n, nu, Rinv);
     ctx->launches += 3;

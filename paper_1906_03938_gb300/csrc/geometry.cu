@@ -4,7 +4,8 @@
 //   area |T_l| and Radon's 7-point degree-5 rule mapped onto each triangle. Weights are
 //   stored as W_lq / (4 pi) so that an off-diagonal entry is sum_q qw * exp(i k r) / r.
 // * Contour (Section 2, Eq. Tz, Eq. TzApp): trapezoid nodes theta_j = 2 pi (j + 1/2) / N.
-// * Self terms A_ll(z_j) for every panel and node (see selfterm.cuh).
+// * Self terms A_ll(z_j) for every panel and node (see selfterm.cuh), in FP64 for the plain
+//   path and in FP32 for the mixed path.
 #include <math.h>
 
 #include "internal.h"
@@ -114,6 +115,22 @@ __global__ void self_term_kernel(Geometry g, int N, const double* z, GL16 gl, do
   self[2 * (j * g.n + l) + 1] = a.y;
 }
 
+// FP32 table for the mixed path, one thread per (panel l, node j).
+__global__ void self_term32_kernel(Geometry g, int N, const double* z, GL16 gl, float* self32) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= g.n * (int64_t)N) return;
+  const int64_t l = t % g.n;
+  const int j = (int)(t / g.n);
+  double v[3][3], x[3];
+  for (int e = 0; e < 3; ++e) {
+    const int32_t vi = g.tri[3 * l + e];
+    for (int c = 0; c < 3; ++c) v[e][c] = g.xyz[3 * (int64_t)vi + c];
+  }
+  for (int c = 0; c < 3; ++c) x[c] = g.cx[c * g.n + l];
+  const float2 a = self_term32(v, x, (float)z[2 * j], (float)z[2 * j + 1], gl);
+  reinterpret_cast<float2*>(self32)[(int64_t)j * g.n + l] = a;
+}
+
 }  // namespace
 
 cudaError_t launch_geometry(bem_ctx* ctx, cudaStream_t s) {
@@ -128,6 +145,16 @@ cudaError_t launch_contour(bem_ctx* ctx, cudaStream_t s) {
   const Contour& c = ctx->con;
   contour_kernel<<<(c.N + 127) / 128, 128, 0, s>>>(c.N, c.kind, c.c_re, c.c_im, c.a, c.b, c.z,
                                                    c.w);
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_self_terms32(bem_ctx* ctx, cudaStream_t s) {
+  static const GL16 gl = make_gl16();
+  const int64_t total = ctx->geo.n * (int64_t)ctx->con.N;
+  self_term32_kernel<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(ctx->geo, ctx->con.N,
+                                                                     ctx->con.z, gl,
+                                                                     ctx->con.self32);
   ctx->launches++;
   return cudaGetLastError();
 }

@@ -50,6 +50,9 @@ struct Contour {
   double* z = nullptr;     // 2 N, device
   double* w = nullptr;     // 2 N, device
   double* self = nullptr;  // 2 n N, device: A_ll(z_j) at j * n + l (complex)
+  float* self32 = nullptr; // 2 n N, device: the same in FP32 (mixed path)
+  bool self64_ready = false;   // tables are filled on first use after bem_set_contour
+  bool self32_ready = false;
   int cap_N = 0;           // allocated sizes
   int64_t cap_self = 0;
   double z_host[2 * kMaxNodes];
@@ -99,6 +102,10 @@ bem_status take_status(bem_ctx* ctx, cudaStream_t stream, const char* where);
 cudaError_t launch_geometry(bem_ctx* ctx, cudaStream_t s);
 cudaError_t launch_contour(bem_ctx* ctx, cudaStream_t s);
 cudaError_t launch_self_terms(bem_ctx* ctx, cudaStream_t s);
+cudaError_t launch_self_terms32(bem_ctx* ctx, cudaStream_t s);
+// Fill the FP64 / FP32 self-term table of the current contour if not done yet.
+bem_status ensure_self64(bem_ctx* ctx, cudaStream_t s);
+bem_status ensure_self32(bem_ctx* ctx, cudaStream_t s);
 // Y_j = A(z_j) V for all nodes (FP64), Y node-major with leading dimension n.
 cudaError_t launch_apply_fp64(bem_ctx* ctx, const double* V, int64_t ldv, int nu, double* Y,
                               cudaStream_t s);

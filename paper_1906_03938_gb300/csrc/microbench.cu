@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kThreads) fma32_kernel(float* out, float seed)
   if (s == 12345.678f) out[0] = s;
 }
 
-// kind 0: ex2.approx, 1: sin.approx, 2: cos.approx (one MUFU operation each)
+// kind 0: ex2.approx, 1: sin.approx, 2: cos.approx, 3: rsqrt.approx (one MUFU op each)
 template <int kKind>
 __global__ void __launch_bounds__(kThreads) mufu_kernel(float* out, float seed) {
   float a[8];
@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(kThreads) mufu_kernel(float* out, float seed) 
       if (kKind == 0) asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a[k]));
       if (kKind == 1) asm volatile("sin.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a[k]));
       if (kKind == 2) asm volatile("cos.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a[k]));
+      if (kKind == 3) asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a[k]));
       a[k] = r;
     }
   }
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(kThreads) mufu_kernel(float* out, float seed) 
 using namespace bem;
 
 extern "C" bem_status bem_microbench(bem_ctx* ctx, int kind, double* ops_per_s) {
-  if (!ctx || !ops_per_s || kind < 0 || kind > 4) return fail(ctx, BEM_EINVAL, "bem_microbench: bad argument");
+  if (!ctx || !ops_per_s || kind < 0 || kind > 5) return fail(ctx, BEM_EINVAL, "bem_microbench: bad argument");
   cudaSetDevice(ctx->device);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
@@ -91,7 +92,8 @@ extern "C" bem_status bem_microbench(bem_ctx* ctx, int kind, double* ops_per_s) 
       case 1: fma32_kernel<<<blocks, kThreads>>>(reinterpret_cast<float*>(ctx->d_small), 1.0f); break;
       case 2: mufu_kernel<0><<<blocks, kThreads>>>(reinterpret_cast<float*>(ctx->d_small), 1.0f); break;
       case 3: mufu_kernel<1><<<blocks, kThreads>>>(reinterpret_cast<float*>(ctx->d_small), 1.0f); break;
-      default: mufu_kernel<2><<<blocks, kThreads>>>(reinterpret_cast<float*>(ctx->d_small), 1.0f); break;
+      case 4: mufu_kernel<2><<<blocks, kThreads>>>(reinterpret_cast<float*>(ctx->d_small), 1.0f); break;
+      default: mufu_kernel<3><<<blocks, kThreads>>>(reinterpret_cast<float*>(ctx->d_small), 1.0f); break;
     }
     cudaEventRecord(e1, 0);
     ctx->launches++;

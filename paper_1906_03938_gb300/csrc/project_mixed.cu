@@ -3,14 +3,15 @@
 // mixed_apply_kernel computes Y_j = A(z_j) V without storing A(z_j):
 //  * a work unit is one 128-row tile of A, a group of G <= 4 contour nodes and a range of
 //    16-column K-blocks (the column range is split when that balances the grid);
-//  * 8 evaluation warps compute each 128 x 16 block of entries in FP32 for the G nodes
+//  * 16 evaluation warps compute each 128 x 16 block of entries in FP32 for the G nodes
 //    (7-point rule: one rsqrt per quadrature point shared by the nodes, then ex2, sin and
-//    cos on the MUFU unit per node; the self term from the FP64 table on the diagonal),
+//    cos on the MUFU unit per node; the self term from the FP32 table on the diagonal),
 //    with coordinates taken relative to the tile's first centroid, and write them as four
 //    BF16 planes (Re/Im x hi/lo) into shared memory in the tensor core's canonical K-major
 //    layout;
 //  * one producer warp copies the matching K-block of the prepared BF16 basis planes
-//    (four planes [Vr|Vi], [Vr_lo|Vi_lo], [-Vi|Vr], [-Vi_lo|Vr_lo]) with a bulk TMA copy;
+//    (four planes [Vr|Vi], [Vr_lo|Vi_lo], [-Vi|Vr], [-Vi_lo|Vr_lo]) with a bulk TMA copy
+//    and stages the block's column geometry (FP64 -> tile-relative FP32) and self terms;
 //  * one MMA warp issues, per node, six tcgen05 BF16 MMAs (M = 128, N = 2 C, K = 16)
 //    that add Ar_hi[Vr|Vi] + Ar_hi[Vr_lo|Vi_lo] + Ar_lo[Vr|Vi] + Ai_hi[-Vi|Vr]
 //    + Ai_hi[-Vi_lo|Vr_lo] + Ai_lo[-Vi|Vr] into an FP32 accumulator [Yr | Yi] in TMEM
@@ -19,8 +20,8 @@
 //    is bounded and a timeout aborts the block cleanly with an error status);
 //  * the evaluation warps finally read the accumulators from TMEM and store the FP32
 //    partial Y of the unit.
-// mixed_vhy_kernel then forms Bhat_j = w_j V^H (sum over column splits of Y_j) in FP64
-// with a fixed summation order.
+// mixed_vhy_part_kernel / mixed_vhy_reduce_kernel then form
+// Bhat_j = w_j V^H (sum over column splits of Y_j) with a fixed summation order.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -37,7 +38,7 @@ using namespace sm100;
 constexpr int kBM = 128;            // rows per tile (MMA M)
 constexpr int kBK = 16;             // columns per K-block (MMA K)
 constexpr int kStages = 2;
-constexpr int kEvalWarps = 8;
+constexpr int kEvalWarps = 16;
 constexpr int kEvalThreads = 32 * kEvalWarps;
 constexpr int kThreads = 32 * (2 + kEvalWarps);
 constexpr int kMaxG = 4;
@@ -63,7 +64,7 @@ struct MixedParams {
   const double* cx;   // FP64 centroids, SoA
   const double* qp;   // FP64 quadrature points, q-major SoA
   const double* qw;   // FP64 weights / 4 pi
-  const double* self; // FP64 complex self terms, node-major
+  const float2* self32;   // FP32 complex self terms, node-major
   const double* z;    // FP64 complex nodes
   const __nv_bfloat16* Bp;   // prepared basis planes, tile-native
   float* Yp;          // FP32 partial products [S][N][2 nup][n_pad]
@@ -71,7 +72,7 @@ struct MixedParams {
 };
 
 struct SmemLayout {
-  uint32_t a_off, b_off, row_off, col_off, bar_off, misc_off, total;
+  uint32_t a_off, b_off, row_off, col_off, self_off, bar_off, misc_off, total;
   uint32_t a_stage_bytes, b_stage_bytes;
 };
 
@@ -83,8 +84,9 @@ __host__ __device__ inline SmemLayout smem_layout(int G, int nup) {
   L.b_off = L.a_off + kStages * L.a_stage_bytes;
   L.row_off = L.b_off + kStages * L.b_stage_bytes;
   L.col_off = L.row_off + kBM * 4 * 4;           // 128 rows x (x, y, z, valid)
-  L.bar_off = L.col_off + kBK * 28 * 4;          // 16 columns x (21 coords + 7 weights)
-  L.misc_off = L.bar_off + 8 * 8;                // 7 mbarriers (+1 pad)
+  L.self_off = L.col_off + kStages * kBK * 28 * 4;   // per stage 16 x (21 coords + 7 weights)
+  L.bar_off = L.self_off + kStages * kBK * kMaxG * 8;  // per stage 16 x G complex self terms
+  L.misc_off = L.bar_off + 10 * 8;               // 9 mbarriers (+1 pad)
   L.total = L.misc_off + 16;                     // tmem slot, abort flag
   return L;
 }
@@ -115,20 +117,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// OR of v over the evaluation threads (named barrier 1): a block-uniform decision
-__device__ __forceinline__ int eval_barrier_or(int v) {
-  int r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\t"
-      "setp.ne.s32 q, %1, 0;\n\t"
-      "bar.red.or.pred p, 1, %2, q;\n\t"
-      "selp.s32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(r)
-      : "r"(v), "n"(kEvalThreads)
-      : "memory");
-  return r;
-}
-
 // bounded wait that also watches the block's abort flag
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
                                               volatile int* abort_flag, int* status) {
@@ -148,12 +136,14 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
   unsigned char* sA = smem + L.a_off;
   unsigned char* sB = smem + L.b_off;
   float4* sRow = reinterpret_cast<float4*>(smem + L.row_off);
-  float* sCol = reinterpret_cast<float*>(smem + L.col_off);
+  float* sColAll = reinterpret_cast<float*>(smem + L.col_off);      // [stage][16][28]
+  float2* sSelfAll = reinterpret_cast<float2*>(smem + L.self_off);  // [stage][16][kMaxG]
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
   uint64_t* afull = bars;        // [2] evaluation warps -> MMA
   uint64_t* bfull = bars + 2;    // [2] bulk copy -> MMA
   uint64_t* empty = bars + 4;    // [2] MMA done with the stage
   uint64_t* accfull = bars + 6;  // accumulators final
+  uint64_t* gfull = bars + 7;    // [2] column geometry / self terms staged -> evaluation
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.misc_off);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.misc_off + 4);
 
@@ -181,6 +171,7 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
       mbar_init(&afull[s], kEvalThreads);
       mbar_init(&bfull[s], 1);
       mbar_init(&empty[s], 1);
+      mbar_init(&gfull[s], 32);
     }
     mbar_init(accfull, 1);
     *abort_flag = 0;
@@ -196,25 +187,67 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
   const uint32_t tmem_base = *tmem_slot;
 
   if (warp == 0) {
-    // ---------------- producer: basis planes by bulk copy ----------------
-    if (lane == 0) {
-      int issued = 0;
-      for (int it = 0; it < nkb; ++it) {
-        const int s = it % kStages;
-        const uint32_t par = (it / kStages) & 1;
-        if (!wait_or_abort(&empty[s], par ^ 1, abort_flag, p.status)) break;
+    // ---------------- producer: basis planes (bulk copy), column geometry, self terms ----
+    // origin of this tile's relative coordinates: its first centroid
+    const int64_t i_org = row0 < p.n ? row0 : p.n - 1;
+    const double ox = p.cx[i_org], oy = p.cx[p.n + i_org], oz = p.cx[2 * p.n + i_org];
+    for (int r = lane; r < kBM; r += 32) {
+      const int64_t i = row0 + r;
+      float4 v = make_float4(2.0f, 2.0f, 2.0f, 0.f);   // padding rows: zeroed after evaluation
+      if (i < p.n)
+        v = make_float4((float)(p.cx[i] - ox), (float)(p.cx[p.n + i] - oy),
+                        (float)(p.cx[2 * p.n + i] - oz), 1.f);
+      sRow[r] = v;
+    }
+    int issued = 0;
+    for (int it = 0; it < nkb; ++it) {
+      const int s = it % kStages;
+      const uint32_t par = (it / kStages) & 1;
+      const int kb = kb0 + it;
+      int ok = 1;
+      if (lane == 0) ok = wait_or_abort(&empty[s], par ^ 1, abort_flag, p.status);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      if (lane == 0) {
         mbar_arrive_expect_tx(&bfull[s], L.b_stage_bytes);
         bulk_g2s(sB + s * L.b_stage_bytes,
                  reinterpret_cast<const unsigned char*>(p.Bp) +
-                     (size_t)(kb0 + it) * L.b_stage_bytes,
+                     (size_t)kb * L.b_stage_bytes,
                  L.b_stage_bytes, &bfull[s]);
-        ++issued;
       }
-      if (*abort_flag) {
-        // let copies in flight land before the block exits (bounded)
-        for (int it = max(0, issued - kStages); it < issued; ++it)
-          mbar_wait(&bfull[it % kStages], (it / kStages) & 1, kWaitLimit);
+      ++issued;
+      float* sCol = sColAll + s * (kBK * 28);
+      for (int x = lane; x < kBK * 28; x += 32) {
+        const int k = x / 28, f = x % 28;
+        const int64_t l = (int64_t)kb * kBK + k;
+        // padding columns: finite placeholders; their entries are zeroed after evaluation
+        float val = f < 21 ? 1.0f : 0.f;
+        if (l < p.n) {
+          if (f < 21) {
+            const int c = f / 7, q = f % 7;
+            const double o = c == 0 ? ox : (c == 1 ? oy : oz);
+            val = (float)(p.qp[(7 * c + q) * p.n + l] - o);
+          } else {
+            val = (float)p.qw[(f - 21) * p.n + l];
+          }
+        }
+        sCol[k * 28 + f] = val;
       }
+      float2* sSelf = sSelfAll + s * (kBK * kMaxG);
+      for (int x = lane; x < kBK * kMaxG; x += 32) {
+        const int k = x / kMaxG, g = x % kMaxG;
+        const int64_t l = (int64_t)kb * kBK + k;
+        float2 v = make_float2(0.f, 0.f);
+        if (l < p.n && g < Gv && l >= row0 && l < row0 + kBM)
+          v = p.self32[(int64_t)(j0 + g) * p.n + l];
+        sSelf[x] = v;
+      }
+      mbar_arrive(&gfull[s]);   // release: the staged values are visible to the waiters
+    }
+    if (lane == 0 && *abort_flag) {
+      // let copies in flight land before the block exits (bounded)
+      for (int it = max(0, issued - kStages); it < issued; ++it)
+        mbar_wait(&bfull[it % kStages], (it / kStages) & 1, kWaitLimit);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -249,19 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
     }
   } else {
     // ---------------- evaluation warps ----------------
-    const int e = warp - 2;               // 0..7
-    const int et = threadIdx.x - 64;      // 0..255
-    // origin of this tile's relative coordinates
-    const int64_t i_org = row0 < p.n ? row0 : p.n - 1;
-    const double ox = p.cx[i_org], oy = p.cx[p.n + i_org], oz = p.cx[2 * p.n + i_org];
-    if (et < kBM) {
-      const int64_t i = row0 + et;
-      float4 v = make_float4(2.0f, 2.0f, 2.0f, 0.f);   // padding rows: zeroed after evaluation
-      if (i < p.n)
-        v = make_float4((float)(p.cx[i] - ox), (float)(p.cx[p.n + i] - oy),
-                        (float)(p.cx[2 * p.n + i] - oz), 1.f);
-      sRow[et] = v;
-    }
+    const int e = warp - 2;               // 0..15: row group of the 128 x 16 block
     // node constants
     float kr[kMaxG], kmi[kMaxG];
 #pragma unroll
@@ -270,44 +291,23 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
       kr[g] = (float)p.z[2 * j];
       kmi[g] = (float)(-p.z[2 * j + 1]) * kLog2e;
     }
-    // this thread's 2 x 4 entries: rows 16 e + {0, 8} + r8, columns 8 kg + 2 kp + {0, 1}
+    // this thread's entries: row 8 e + r8, columns 8 kg + 2 kp + {0, 1} for kg = 0, 1
     const int r8 = lane / 4, kp = lane % 4;
+    const int row = 8 * e + r8;
+    const int64_t i = row0 + row;
 
     for (int it = 0; it < nkb; ++it) {
       const int s = it % kStages;
       const uint32_t par = (it / kStages) & 1;
       const int kb = kb0 + it;
-      // every evaluation thread takes the same exit decision here (this is also the
-      // barrier that protects the column geometry of the previous K-block)
-      if (eval_barrier_or(*abort_flag)) break;
-      // stage the K-block's column geometry (all evaluation threads)
-      for (int x = et; x < kBK * 28; x += kEvalThreads) {
-        const int k = x / 28, f = x % 28;
-        const int64_t l = (int64_t)kb * kBK + k;
-        // padding columns: finite placeholders; their entries are zeroed after evaluation
-        float val = f < 21 ? 1.0f : 0.f;
-        if (l < p.n) {
-          if (f < 21) {
-            const int c = f / 7, q = f % 7;
-            const double o = c == 0 ? ox : (c == 1 ? oy : oz);
-            val = (float)(p.qp[(7 * c + q) * p.n + l] - o);
-          } else {
-            val = (float)p.qw[(f - 21) * p.n + l];
-          }
-        }
-        sCol[k * 28 + f] = val;
-      }
-      asm volatile("bar.sync 1, %0;" ::"n"(kEvalThreads) : "memory");
-      const bool ready = wait_or_abort(&empty[s], par ^ 1, abort_flag, p.status);
+      const bool ready = wait_or_abort(&gfull[s], par, abort_flag, p.status);
+      const float* sCol = sColAll + s * (kBK * 28);
+      const float2* sSelf = sSelfAll + s * (kBK * kMaxG);
       unsigned char* a_stage = sA + s * L.a_stage_bytes;
+      const float4 xr = sRow[row];
 #pragma unroll 1
-      for (int cm = 0; cm < (ready ? 4 : 0); ++cm) {
-        const int rg = 2 * e + (cm >> 1);
-        const int kg = cm & 1;
-        const int row = 8 * rg + r8;
+      for (int kg = 0; kg < (ready ? 2 : 0); ++kg) {
         const int k0 = 8 * kg + 2 * kp;
-        const float4 xr = sRow[row];
-        const int64_t i = row0 + row;
         const int64_t l0 = (int64_t)kb * kBK + k0;
         float rr[2][7], am[2][7];
 #pragma unroll
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
             am[d][q] = col[21 + q] * rs;
           }
         }
-        const uint32_t off = rg * 256 + kg * 128 + r8 * 16 + kp * 4;
+        const uint32_t off = e * 256 + kg * 128 + r8 * 16 + kp * 4;
 #pragma unroll
         for (int g = 0; g < kMaxG; ++g) {
           if (g >= Gv) break;
@@ -339,10 +339,10 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
               sr = fmaf(a, cosf_mufu(red), sr);
               si = fmaf(a, sinf_mufu(red), si);
             }
-            if (i == l0 + d && i < p.n) {   // diagonal: the self term
-              const double2 sv = reinterpret_cast<const double2*>(p.self)[(int64_t)(j0 + g) * p.n + i];
-              sr = (float)sv.x;
-              si = (float)sv.y;
+            if (i == l0 + d) {   // diagonal: the self term
+              const float2 sv = sSelf[(k0 + d) * kMaxG + g];
+              sr = sv.x;
+              si = sv.y;
             }
             if (i >= p.n || l0 + d >= p.n) {   // padding rows / columns of the tile
               sr = 0.f;
@@ -366,6 +366,7 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
       }
       fence_proxy_async_smem();
       mbar_arrive(&afull[s]);
+      if (!ready) break;
     }
 
     // ---------------- epilogue: TMEM -> FP32 partial Y ----------------
@@ -373,16 +374,16 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
     if (__all_sync(0xffffffffu, ok)) {   // tcgen05.ld is warp-collective
       tc_fence_after();
       const int quarter = warp % 4;              // TMEM lanes this warp may read
-      const int half = (warp - 2) / 4;           // two warps per quarter split the columns
-      const int row = quarter * 32 + lane;
-      const int64_t i = row0 + row;
+      const int part = (warp - 2) / 4;           // four warps per quarter split the columns
+      const int erow = quarter * 32 + lane;
+      const int64_t ei = row0 + erow;
       const uint32_t cols_total = (uint32_t)Gv * acc_cols;
-      for (uint32_t c0 = half * 16; c0 < cols_total; c0 += 32) {
+      for (uint32_t c0 = part * 16; c0 < cols_total; c0 += 64) {
         float v[16];
         tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + c0, v);
         const int g = c0 / acc_cols;
         const int col = c0 % acc_cols;
-        float* dst = p.Yp + (((size_t)split * p.N + (j0 + g)) * acc_cols + col) * p.n_pad + i;
+        float* dst = p.Yp + (((size_t)split * p.N + (j0 + g)) * acc_cols + col) * p.n_pad + ei;
 #pragma unroll
         for (int k = 0; k < 16; ++k) dst[(size_t)k * p.n_pad] = v[k];
       }
@@ -445,33 +446,42 @@ __global__ void prep_basis_planes_kernel(const double* __restrict__ V, int64_t l
   Bp[t] = out;
 }
 
-// Bhat_j = w_j V^H Y_j with Y_j = sum over splits of the FP32 partials (FP64 sums in a
-// fixed order); optionally AV_j = Y_j in FP64.
+// Partial products P_r,j = V^H Y_j over the row range of part r, Y_j = sum over column
+// splits of the FP32 partials: FP32 products summed over 32-row chunks, chunk sums added
+// in FP64 (the inputs carry ~1e-5 relative error, so FP32 products lose nothing; the FP64
+// pipe of this GPU is ~70x slower than its FP32 pipe).
 constexpr int kT = 32;
 __global__ void __launch_bounds__(256)
-mixed_vhy_kernel(const double* __restrict__ V, int64_t ldv, int nu, int64_t n, int n_pad,
-                 int N, int S, int acc_cols, int C, const float* __restrict__ Yp,
-                 const double* __restrict__ w, double* __restrict__ Bhat) {
-  __shared__ double2 sX[kT][kT + 1];
-  __shared__ double2 sY[kT][kT + 1];
+mixed_vhy_part_kernel(const double* __restrict__ V, int64_t ldv, int nu, int64_t n, int n_pad,
+                      int N, int S, int acc_cols, int C, const float* __restrict__ Yp,
+                      int64_t rows_per_part, double* __restrict__ part) {
+  __shared__ float2 sX[kT][kT + 1];
+  __shared__ float2 sY[kT][kT + 1];
   const int tiles_a = (nu + kT - 1) / kT;
   const int ta = blockIdx.x % tiles_a, tb = blockIdx.x / tiles_a;
   const int j = blockIdx.y;
+  const int64_t r_begin = (int64_t)blockIdx.z * rows_per_part;
+  const int64_t r_end = min(n, r_begin + rows_per_part);
   const int tid = threadIdx.x;
   const int oa = tid % kT, ob0 = tid / kT;
   double2 acc[4];
 #pragma unroll
   for (int m = 0; m < 4; ++m) acc[m] = make_double2(0.0, 0.0);
   const double2* Vc = reinterpret_cast<const double2*>(V);
-  for (int64_t r0 = 0; r0 < n; r0 += kT) {
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += kT) {
     __syncthreads();
     for (int x = tid; x < kT * kT; x += 256) {
       const int rr = x % kT, cc = x / kT;
       const int64_t r = r0 + rr;
       const int a = ta * kT + cc, b = tb * kT + cc;
-      sX[rr][cc] = (r < n && a < nu) ? Vc[(int64_t)a * ldv + r] : make_double2(0.0, 0.0);
-      double2 y = make_double2(0.0, 0.0);
-      if (r < n && b < nu) {
+      float2 v = make_float2(0.f, 0.f);
+      if (r < r_end && a < nu) {
+        const double2 vd = Vc[(int64_t)a * ldv + r];
+        v = make_float2((float)vd.x, (float)vd.y);
+      }
+      sX[rr][cc] = v;
+      float2 y = make_float2(0.f, 0.f);
+      if (r < r_end && b < nu) {
         const int colr = (b / C) * 2 * C + (b % C);
         for (int s = 0; s < S; ++s) {
           const float* base = Yp + ((size_t)s * N + j) * acc_cols * (size_t)n_pad;
@@ -482,29 +492,52 @@ mixed_vhy_kernel(const double* __restrict__ V, int64_t ldv, int nu, int64_t n, i
       sY[rr][cc] = y;
     }
     __syncthreads();
+    float2 c[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) c[m] = make_float2(0.f, 0.f);
 #pragma unroll 8
     for (int rr = 0; rr < kT; ++rr) {
-      const double2 x = sX[rr][oa];
+      const float2 x = sX[rr][oa];   // conj(x) * y
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
-        const double2 y = sY[rr][ob0 + 8 * m];
-        acc[m].x = fma(x.x, y.x, fma(x.y, y.y, acc[m].x));
-        acc[m].y = fma(x.x, y.y, fma(-x.y, y.x, acc[m].y));
+        const float2 y = sY[rr][ob0 + 8 * m];
+        c[m].x = fmaf(x.x, y.x, fmaf(x.y, y.y, c[m].x));
+        c[m].y = fmaf(x.x, y.y, fmaf(-x.y, y.x, c[m].y));
       }
     }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      acc[m].x += c[m].x;
+      acc[m].y += c[m].y;
+    }
   }
-  const double2 s = reinterpret_cast<const double2*>(w)[j];
   const int a = ta * kT + oa;
   if (a < nu) {
-    double2* Bj = reinterpret_cast<double2*>(Bhat) + (int64_t)j * nu * nu;
+    double2* P = reinterpret_cast<double2*>(part) + ((int64_t)blockIdx.z * N + j) * nu * nu;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       const int b = tb * kT + ob0 + 8 * m;
-      if (b < nu)
-        Bj[(int64_t)b * nu + a] = make_double2(s.x * acc[m].x - s.y * acc[m].y,
-                                              s.x * acc[m].y + s.y * acc[m].x);
+      if (b < nu) P[(int64_t)b * nu + a] = acc[m];
     }
   }
+}
+
+// Bhat_j = w_j sum_r P_r,j (parts added in order: deterministic).
+__global__ void mixed_vhy_reduce_kernel(const double* __restrict__ part, int parts, int N, int nu,
+                                        const double* __restrict__ w, double* __restrict__ Bhat) {
+  const int64_t per = (int64_t)nu * nu;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= per * N) return;
+  const int j = (int)(t / per);
+  const double2* P = reinterpret_cast<const double2*>(part);
+  double2 s = make_double2(0.0, 0.0);
+  for (int r = 0; r < parts; ++r) {
+    const double2 v = P[(int64_t)r * per * N + t];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  const double2 wj = reinterpret_cast<const double2*>(w)[j];
+  reinterpret_cast<double2*>(Bhat)[t] = make_double2(wj.x * s.x - wj.y * s.y, wj.x * s.y + wj.y * s.x);
 }
 
 __global__ void mixed_av_kernel(int64_t n, int n_pad, int nu, int N, int S, int acc_cols, int C,
@@ -571,7 +604,18 @@ bem_status project_mixed(bem_ctx* ctx, const double* V, int64_t ldv, int nu, dou
   const size_t bp_off = 0;
   const size_t yp_off = (bp_bytes + 255) / 256 * 256;
   const size_t yp_bytes = (size_t)p.S * N * acc_cols * p.n_pad * sizeof(float);
-  bem_status st = ensure_scratch(ctx, yp_off + yp_bytes);
+  // V^H Y partials: enough row ranges to fill the device, at least 256 rows each
+  const int vtiles = ((nu + kT - 1) / kT) * ((nu + kT - 1) / kT);
+  int64_t vparts = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256,
+                                                          (2 * (int64_t)sms + vtiles * N - 1) /
+                                                              ((int64_t)vtiles * N)));
+  const int64_t rows_per_vpart = (n + vparts - 1) / vparts;
+  vparts = (n + rows_per_vpart - 1) / rows_per_vpart;
+  const size_t vp_off = (yp_off + yp_bytes + 255) / 256 * 256;
+  const size_t vp_bytes = (size_t)vparts * N * nu * nu * 2 * sizeof(double);
+  bem_status st = ensure_self32(ctx, s);
+  if (st != BEM_OK) return st;
+  st = ensure_scratch(ctx, vp_off + vp_bytes);
   if (st != BEM_OK) return st;
   unsigned char* scr = reinterpret_cast<unsigned char*>(ctx->d_scratch);
   p.Bp = reinterpret_cast<const __nv_bfloat16*>(scr + bp_off);
@@ -579,7 +623,7 @@ bem_status project_mixed(bem_ctx* ctx, const double* V, int64_t ldv, int nu, dou
   p.cx = ctx->geo.cx;
   p.qp = ctx->geo.qp;
   p.qw = ctx->geo.qw;
-  p.self = ctx->con.self;
+  p.self32 = reinterpret_cast<const float2*>(ctx->con.self32);
   p.z = ctx->con.z;
   p.status = ctx->d_status;
 
@@ -603,10 +647,13 @@ bem_status project_mixed(bem_ctx* ctx, const double* V, int64_t ldv, int nu, dou
   st = cuda_check(ctx, cudaGetLastError(), "mixed apply kernel");
   if (st != BEM_OK) return st;
 
-  const int tiles = ((nu + kT - 1) / kT) * ((nu + kT - 1) / kT);
-  mixed_vhy_kernel<<<dim3((unsigned)tiles, (unsigned)N), 256, 0, s>>>(
-      V, ldv, nu, n, p.n_pad, N, p.S, acc_cols, p.C, p.Yp, ctx->con.w, Bhat);
-  ctx->launches++;
+  double* vpart = reinterpret_cast<double*>(scr + vp_off);
+  mixed_vhy_part_kernel<<<dim3((unsigned)vtiles, (unsigned)N, (unsigned)vparts), 256, 0, s>>>(
+      V, ldv, nu, n, p.n_pad, N, p.S, acc_cols, p.C, p.Yp, rows_per_vpart, vpart);
+  const int64_t outs = (int64_t)N * nu * nu;
+  mixed_vhy_reduce_kernel<<<(unsigned)((outs + 255) / 256), 256, 0, s>>>(vpart, (int)vparts, N, nu,
+                                                                         ctx->con.w, Bhat);
+  ctx->launches += 2;
   if (AV) {
     const int64_t tot = (int64_t)N * nu * n;
     mixed_av_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, p.n_pad, nu, N, p.S,
