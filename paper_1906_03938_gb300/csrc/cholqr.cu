@@ -15,15 +15,23 @@ namespace {
 
 // In-place Cholesky of the Hermitian nu x nu matrix G (column-major, upper triangle used):
 // on exit the upper triangle holds R with G = R^H R, the strict lower triangle is zero.
-// A pivot below 1e-13 of the largest diagonal entry of G counts as loss of rank.
-__global__ void __launch_bounds__(1024) cholesky_kernel(double2* G, int nu, int* status) {
+// A pivot below 1e-13 of the largest diagonal entry of G counts as loss of rank. One block;
+// G is staged in shared memory when the dynamic allocation holds it (nu <= 64).
+__global__ void __launch_bounds__(1024) cholesky_kernel(double2* Gg, int nu, int* status) {
+  extern __shared__ double2 sG[];
   __shared__ double rkk, dmax;
+  const bool staged = nu <= 64;
+  double2* G = staged ? sG : Gg;
   const int tid = threadIdx.x;
+  if (staged)
+    for (int t = tid; t < nu * nu; t += blockDim.x) sG[t] = Gg[t];
+  __syncthreads();
   if (tid == 0) {
     dmax = 0.0;
     for (int k = 0; k < nu; ++k) dmax = fmax(dmax, G[(int64_t)k * nu + k].x);
   }
   __syncthreads();
+  bool failed = false;
   for (int k = 0; k < nu; ++k) {
     if (tid == 0) {
       const double d = G[(int64_t)k * nu + k].x;
@@ -36,7 +44,10 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(double2* G, int nu, int*
       G[(int64_t)k * nu + k] = make_double2(rkk, 0.0);
     }
     __syncthreads();
-    if (rkk == 0.0) return;
+    if (rkk == 0.0) {
+      failed = true;
+      break;
+    }
     for (int jj = k + 1 + tid; jj < nu; jj += blockDim.x) {
       double2 g = G[(int64_t)jj * nu + k];
       G[(int64_t)jj * nu + k] = make_double2(g.x / rkk, g.y / rkk);
@@ -60,7 +71,8 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(double2* G, int nu, int*
   }
   for (int64_t t = tid; t < (int64_t)nu * nu; t += blockDim.x) {
     const int i = (int)(t % nu), jj = (int)(t / nu);
-    if (i > jj) G[t] = make_double2(0.0, 0.0);
+    const double2 v = (i > jj) ? make_double2(0.0, 0.0) : G[t];
+    Gg[t] = failed ? make_double2(NAN, NAN) : v;
   }
 }
 
@@ -127,37 +139,51 @@ __global__ void sum_parts_kernel(const double2* __restrict__ part, int parts, in
   G[t] = s;
 }
 
-// Rinv = R^{-1} for upper-triangular R; one thread per column (back substitution), with R
-// staged in shared memory when it fits (dynamic size nu * nu * 16 bytes, else 0).
-__global__ void triangular_inverse_kernel(const double2* R, int nu, double2* Rinv) {
-  extern __shared__ double2 sR[];
-  const bool staged = (R != nullptr) && blockDim.x >= nu && nu <= 64;
-  if (staged)
-    for (int t = threadIdx.x; t < nu * nu; t += blockDim.x) sR[t] = R[t];
+// Rinv = R^{-1} for upper-triangular R: one block per column j, back substitution
+// x_i = (delta_ij - sum_{m=i+1..j} R_im x_m) / R_ii for i = j..0, each sum split over the
+// block's threads and combined in a fixed order (deterministic). The column lives in
+// shared memory; R is read through the cache.
+__global__ void __launch_bounds__(128)
+triangular_inverse_kernel(const double2* __restrict__ R, int nu, double2* __restrict__ Rinv) {
+  __shared__ double2 x[kMaxNu];
+  __shared__ double2 red[4];
+  const int j = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid % 32, w = tid / 32;
+  for (int i = tid; i < nu; i += blockDim.x) x[i] = make_double2(0.0, 0.0);
   __syncthreads();
-  const double2* Rm = staged ? sR : R;
-  const int jcol = blockIdx.x * blockDim.x + threadIdx.x;
-  if (jcol >= nu) return;
-  for (int i = nu - 1; i >= 0; --i) {
-    double2 s = make_double2(i == jcol ? 1.0 : 0.0, 0.0);
-    if (i <= jcol) {
-      for (int m = i + 1; m <= jcol; ++m) {
-        const double2 r = Rm[(int64_t)m * nu + i];
-        const double2 x = Rinv[(int64_t)jcol * nu + m];
-        s.x -= r.x * x.x - r.y * x.y;
-        s.y -= r.x * x.y + r.y * x.x;
-      }
-      const double2 d = Rm[(int64_t)i * nu + i];   // real positive
-      Rinv[(int64_t)jcol * nu + i] = make_double2(s.x / d.x, s.y / d.x);
-    } else {
-      Rinv[(int64_t)jcol * nu + i] = make_double2(0.0, 0.0);
+  for (int i = j; i >= 0; --i) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int m = i + 1 + tid; m <= j; m += blockDim.x) {
+      const double2 r = R[(int64_t)m * nu + i];
+      const double2 xm = x[m];
+      acc.x += r.x * xm.x - r.y * xm.y;
+      acc.y += r.x * xm.y + r.y * xm.x;
     }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    }
+    if (lane == 0) red[w] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      double2 s = make_double2(i == j ? 1.0 : 0.0, 0.0);
+      for (int k = 0; k < 4; ++k) {
+        s.x -= red[k].x;
+        s.y -= red[k].y;
+      }
+      const double d = R[(int64_t)i * nu + i].x;   // real positive
+      x[i] = make_double2(s.x / d, s.y / d);
+    }
+    __syncthreads();
   }
+  for (int i = tid; i < nu; i += blockDim.x) Rinv[(int64_t)j * nu + i] = x[i];
 }
 
 constexpr int kRows = 8;
 
-// V <- V * M in place, M nu x nu (column-major); each block owns kRows rows of V.
+// V <- V * M in place, M nu x nu upper triangular (column-major); each block owns kRows
+// rows of V.
 __global__ void __launch_bounds__(256)
 right_multiply_kernel(double2* V, int64_t ldv, int64_t n, int nu, const double2* __restrict__ M) {
   __shared__ double2 sV[kRows][kMaxNu];
@@ -172,7 +198,7 @@ right_multiply_kernel(double2* V, int64_t ldv, int64_t n, int nu, const double2*
     const int rr = t % kRows, c = t / kRows;
     const int64_t r = r0 + rr;
     double2 acc = make_double2(0.0, 0.0);
-    for (int k = 0; k <= c; ++k) {   // M is upper triangular
+    for (int k = 0; k <= c; ++k) {
       const double2 a = sV[rr][k];
       const double2 b = M[(int64_t)c * nu + k];
       acc.x += a.x * b.x - a.y * b.y;
@@ -225,28 +251,26 @@ extern "C" bem_status bem_cholqr2(bem_ctx* ctx, double* V_dev, int64_t n, int64_
   double2* R1 = Rinv + (size_t)nu * nu;
   double2* R2 = R1 + (size_t)nu * nu;
   double2* part = R2 + (size_t)nu * nu;
-  const int inv_threads = 64;   // one block (R staged in shared memory) when nu <= 64
-  const size_t inv_smem = nu <= 64 ? (size_t)nu * nu * sizeof(double2) : 0;
-  if (inv_smem > 48 * 1024) {
-    st = cuda_check(ctx, cudaFuncSetAttribute(triangular_inverse_kernel,
+  const size_t chol_smem = nu <= 64 ? (size_t)nu * nu * sizeof(double2) : 0;
+  if (chol_smem > 48 * 1024) {
+    st = cuda_check(ctx, cudaFuncSetAttribute(cholesky_kernel,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)inv_smem),
+                                              (int)chol_smem),
                     "cholqr attribute");
     if (st != BEM_OK) return st;
   }
+
   for (int pass = 0; pass < 2; ++pass) {
     double2* R = pass == 0 ? R1 : R2;
     gram_partial_kernel<<<dim3((unsigned)tiles, (unsigned)parts), 256, 0, s>>>(
         reinterpret_cast<const double2*>(V_dev), ldv, n, nu, rows_per_part, part);
     sum_parts_kernel<<<(unsigned)(((int64_t)nu * nu + 255) / 256), 256, 0, s>>>(
         part, (int)parts, (int64_t)nu * nu, R);
-    cholesky_kernel<<<1, 1024, 0, s>>>(R, nu, ctx->d_status);
-    triangular_inverse_kernel<<<(nu + inv_threads - 1) / inv_threads, inv_threads, inv_smem, s>>>(
-        R, nu, Rinv);
-    ctx->launches += 2;
+    cholesky_kernel<<<1, 1024, chol_smem, s>>>(R, nu, ctx->d_status);
+    triangular_inverse_kernel<<<nu, 128, 0, s>>>(R, nu, Rinv);
     right_multiply_kernel<<<(unsigned)((n + kRows - 1) / kRows), 256, 0, s>>>(
         reinterpret_cast<double2*>(V_dev), ldv, n, nu, Rinv);
-    ctx->launches += 3;
+    ctx->launches += 5;
     st = cuda_check(ctx, cudaGetLastError(), "cholqr kernels");
     if (st != BEM_OK) return st;
   }

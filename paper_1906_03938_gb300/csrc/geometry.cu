@@ -83,6 +83,18 @@ __global__ void geometry_kernel(Geometry g, Rule7 rule, int* status) {
     g.qw[q * n + l] = w;
     g.qw32[q * n + l] = (float)w;
   }
+  if (g.edge32) {
+    // node-independent edge data of the self term, once per panel
+    double x[3];
+    for (int c = 0; c < 3; ++c) x[c] = (v[0][c] + v[1][c] + v[2][c]) / 3.0;
+    for (int e = 0; e < 3; ++e) {
+      double d, up, uq;
+      self_edge(v, x, e, d, up, uq);
+      g.edge32[(3 * e + 0) * n + l] = (float)d;
+      g.edge32[(3 * e + 1) * n + l] = (float)up;
+      g.edge32[(3 * e + 2) * n + l] = (float)uq;
+    }
+  }
 }
 
 __global__ void contour_kernel(int N, int kind, double c_re, double c_im, double a, double b,
@@ -115,20 +127,28 @@ __global__ void self_term_kernel(Geometry g, int N, const double* z, GL16 gl, do
   self[2 * (j * g.n + l) + 1] = a.y;
 }
 
-// FP32 table for the mixed path, one thread per (panel l, node j).
+// FP32 table for the mixed path, one warp per (panel l, node j): the 96 angular nodes
+// (3 edges x 2 sides x 16) are spread over the lanes and summed by a fixed shuffle tree.
 __global__ void self_term32_kernel(Geometry g, int N, const double* z, GL16 gl, float* self32) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= g.n * (int64_t)N) return;
-  const int64_t l = t % g.n;
-  const int j = (int)(t / g.n);
-  double v[3][3], x[3];
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x % 32;
+  if (wid >= g.n * (int64_t)N) return;
+  const int64_t l = wid % g.n;
+  const int j = (int)(wid / g.n);
+  float d3[3], up3[3], uq3[3];
+#pragma unroll
   for (int e = 0; e < 3; ++e) {
-    const int32_t vi = g.tri[3 * l + e];
-    for (int c = 0; c < 3; ++c) v[e][c] = g.xyz[3 * (int64_t)vi + c];
+    d3[e] = g.edge32[(3 * e + 0) * g.n + l];
+    up3[e] = g.edge32[(3 * e + 1) * g.n + l];
+    uq3[e] = g.edge32[(3 * e + 2) * g.n + l];
   }
-  for (int c = 0; c < 3; ++c) x[c] = g.cx[c * g.n + l];
-  const float2 a = self_term32(v, x, (float)z[2 * j], (float)z[2 * j + 1], gl);
-  reinterpret_cast<float2*>(self32)[(int64_t)j * g.n + l] = a;
+  float2 a = self_term32_part(d3, up3, uq3, (float)z[2 * j], (float)z[2 * j + 1], gl, lane, 32);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    a.x += __shfl_xor_sync(0xffffffffu, a.x, off);
+    a.y += __shfl_xor_sync(0xffffffffu, a.y, off);
+  }
+  if (lane == 0) reinterpret_cast<float2*>(self32)[(int64_t)j * g.n + l] = a;
 }
 
 }  // namespace
@@ -152,7 +172,7 @@ cudaError_t launch_contour(bem_ctx* ctx, cudaStream_t s) {
 cudaError_t launch_self_terms32(bem_ctx* ctx, cudaStream_t s) {
   static const GL16 gl = make_gl16();
   const int64_t total = ctx->geo.n * (int64_t)ctx->con.N;
-  self_term32_kernel<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(ctx->geo, ctx->con.N,
+  self_term32_kernel<<<(unsigned)((32 * total + 255) / 256), 256, 0, s>>>(ctx->geo, ctx->con.N,
                                                                      ctx->con.z, gl,
                                                                      ctx->con.self32);
   ctx->launches++;

@@ -41,6 +41,8 @@ struct Geometry {
   float* cx32 = nullptr;   // FP32 copies of the above for the mixed path
   float* qp32 = nullptr;
   float* qw32 = nullptr;
+  float* edge32 = nullptr; // 9 n, optional: self-term edge data (d, u_p, u_q per edge) at
+                           // (3 e + f) * n + l, for the FP32 self terms of the mixed path
 };
 
 struct Contour {

@@ -450,74 +450,100 @@ __global__ void prep_basis_planes_kernel(const double* __restrict__ V, int64_t l
 // splits of the FP32 partials: FP32 products summed over 32-row chunks, chunk sums added
 // in FP64 (the inputs carry ~1e-5 relative error, so FP32 products lose nothing; the FP64
 // pipe of this GPU is ~70x slower than its FP32 pipe).
-constexpr int kT = 32;
+constexpr int kT = 64;    // output tile (64 x 64 of the nu x nu matrix)
+constexpr int kTR = 32;   // rows per chunk
 __global__ void __launch_bounds__(256)
 mixed_vhy_part_kernel(const double* __restrict__ V, int64_t ldv, int nu, int64_t n, int n_pad,
                       int N, int S, int acc_cols, int C, const float* __restrict__ Yp,
                       int64_t rows_per_part, double* __restrict__ part) {
-  __shared__ float2 sX[kT][kT + 1];
-  __shared__ float2 sY[kT][kT + 1];
+  __shared__ float2 sX[kTR][kT + 1];   // +1: the row-major fill below is then 2-way at most
+  __shared__ float2 sY[kTR][kT + 1];
   const int tiles_a = (nu + kT - 1) / kT;
   const int ta = blockIdx.x % tiles_a, tb = blockIdx.x / tiles_a;
   const int j = blockIdx.y;
   const int64_t r_begin = (int64_t)blockIdx.z * rows_per_part;
   const int64_t r_end = min(n, r_begin + rows_per_part);
   const int tid = threadIdx.x;
-  const int oa = tid % kT, ob0 = tid / kT;
-  double2 acc[4];
+  const int oa = tid % 16, ob = tid / 16;   // outputs (oa + 16 i, ob + 16 m)
+  double2 acc[4][4];
 #pragma unroll
-  for (int m = 0; m < 4; ++m) acc[m] = make_double2(0.0, 0.0);
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int m = 0; m < 4; ++m) acc[i][m] = make_double2(0.0, 0.0);
   const double2* Vc = reinterpret_cast<const double2*>(V);
-  for (int64_t r0 = r_begin; r0 < r_end; r0 += kT) {
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += kTR) {
     __syncthreads();
-    for (int x = tid; x < kT * kT; x += 256) {
-      const int rr = x % kT, cc = x / kT;
+    for (int x = tid; x < kTR * kT; x += 256) {
+      const int rr = x % kTR, cc = x / kTR;
       const int64_t r = r0 + rr;
-      const int a = ta * kT + cc, b = tb * kT + cc;
+      const int a = ta * kT + cc;
       float2 v = make_float2(0.f, 0.f);
       if (r < r_end && a < nu) {
         const double2 vd = Vc[(int64_t)a * ldv + r];
         v = make_float2((float)vd.x, (float)vd.y);
       }
       sX[rr][cc] = v;
-      float2 y = make_float2(0.f, 0.f);
+    }
+    // Y rows four at a time (rows_per_part and the chunk start are multiples of 4; rows
+    // past n are the zero padding rows of the last tile, rows past r_end are masked)
+    for (int x = tid; x < (kTR / 4) * kT; x += 256) {
+      const int q4 = x % (kTR / 4), cc = x / (kTR / 4);
+      const int64_t r = r0 + 4 * q4;
+      const int b = tb * kT + cc;
+      float4 yr = make_float4(0.f, 0.f, 0.f, 0.f), yi = yr;
       if (r < r_end && b < nu) {
         const int colr = (b / C) * 2 * C + (b % C);
         for (int s = 0; s < S; ++s) {
           const float* base = Yp + ((size_t)s * N + j) * acc_cols * (size_t)n_pad;
-          y.x += base[(size_t)colr * n_pad + r];
-          y.y += base[(size_t)(colr + C) * n_pad + r];
+          const float4 a4 = *reinterpret_cast<const float4*>(base + (size_t)colr * n_pad + r);
+          const float4 b4 = *reinterpret_cast<const float4*>(base + (size_t)(colr + C) * n_pad + r);
+          yr.x += a4.x; yr.y += a4.y; yr.z += a4.z; yr.w += a4.w;
+          yi.x += b4.x; yi.y += b4.y; yi.z += b4.z; yi.w += b4.w;
         }
       }
-      sY[rr][cc] = y;
+      sY[4 * q4 + 0][cc] = (r + 0 < r_end) ? make_float2(yr.x, yi.x) : make_float2(0.f, 0.f);
+      sY[4 * q4 + 1][cc] = (r + 1 < r_end) ? make_float2(yr.y, yi.y) : make_float2(0.f, 0.f);
+      sY[4 * q4 + 2][cc] = (r + 2 < r_end) ? make_float2(yr.z, yi.z) : make_float2(0.f, 0.f);
+      sY[4 * q4 + 3][cc] = (r + 3 < r_end) ? make_float2(yr.w, yi.w) : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    float2 c[4];
+    float2 c[4][4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) c[m] = make_float2(0.f, 0.f);
-#pragma unroll 8
-    for (int rr = 0; rr < kT; ++rr) {
-      const float2 x = sX[rr][oa];   // conj(x) * y
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) c[i][m] = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (int rr = 0; rr < kTR; ++rr) {
+      float2 x[4], y[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) x[i] = sX[rr][oa + 16 * i];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) y[m] = sY[rr][ob + 16 * m];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {   // conj(x) * y
+          c[i][m].x = fmaf(x[i].x, y[m].x, fmaf(x[i].y, y[m].y, c[i][m].x));
+          c[i][m].y = fmaf(x[i].x, y[m].y, fmaf(-x[i].y, y[m].x, c[i][m].y));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
-        const float2 y = sY[rr][ob0 + 8 * m];
-        c[m].x = fmaf(x.x, y.x, fmaf(x.y, y.y, c[m].x));
-        c[m].y = fmaf(x.x, y.y, fmaf(-x.y, y.x, c[m].y));
+        acc[i][m].x += c[i][m].x;
+        acc[i][m].y += c[i][m].y;
       }
-    }
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      acc[m].x += c[m].x;
-      acc[m].y += c[m].y;
-    }
   }
-  const int a = ta * kT + oa;
-  if (a < nu) {
-    double2* P = reinterpret_cast<double2*>(part) + ((int64_t)blockIdx.z * N + j) * nu * nu;
+  double2* P = reinterpret_cast<double2*>(part) + ((int64_t)blockIdx.z * N + j) * nu * nu;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int a = ta * kT + oa + 16 * i;
+    if (a >= nu) continue;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      const int b = tb * kT + ob0 + 8 * m;
-      if (b < nu) P[(int64_t)b * nu + a] = acc[m];
+      const int b = tb * kT + ob + 16 * m;
+      if (b < nu) P[(int64_t)b * nu + a] = acc[i][m];
     }
   }
 }
@@ -604,12 +630,12 @@ bem_status project_mixed(bem_ctx* ctx, const double* V, int64_t ldv, int nu, dou
   const size_t bp_off = 0;
   const size_t yp_off = (bp_bytes + 255) / 256 * 256;
   const size_t yp_bytes = (size_t)p.S * N * acc_cols * p.n_pad * sizeof(float);
-  // V^H Y partials: enough row ranges to fill the device, at least 256 rows each
+  // V^H Y partials: enough row ranges to fill the device, at least 128 rows each
   const int vtiles = ((nu + kT - 1) / kT) * ((nu + kT - 1) / kT);
-  int64_t vparts = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256,
-                                                          (2 * (int64_t)sms + vtiles * N - 1) /
+  int64_t vparts = std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128,
+                                                          (4 * (int64_t)sms + vtiles * N - 1) /
                                                               ((int64_t)vtiles * N)));
-  const int64_t rows_per_vpart = (n + vparts - 1) / vparts;
+  const int64_t rows_per_vpart = ((n + vparts - 1) / vparts + kTR - 1) / kTR * kTR;
   vparts = (n + rows_per_vpart - 1) / rows_per_vpart;
   const size_t vp_off = (yp_off + yp_bytes + 255) / 256 * 256;
   const size_t vp_bytes = (size_t)vparts * N * nu * nu * 2 * sizeof(double);

@@ -113,62 +113,78 @@ __device__ inline double2 self_term(const double v[3][3], const double x[3], dou
   return make_double2(total.x / (4.0 * kPiD), total.y / (4.0 * kPiD));
 }
 
-// FP32 version for the mixed path: the edge geometry (d, u range) in FP64, the angular
-// quadrature and h(i k R) in FP32 (relative accuracy ~1e-6, the level of the mixed path).
-__device__ inline float2 self_term32(const double v[3][3], const double x[3], float kr, float ki,
-                                     const GL16& gl) {
+// Edge data of the self term, FP64: for edge e = (v[e], v[e+1]) about the point x, the
+// distance d from x to the edge's line and the u = asinh(s / d) range of the edge.
+__device__ inline void self_edge(const double v[3][3], const double x[3], int e, double& d,
+                                 double& up, double& uq) {
+  const double* p = v[e];
+  const double* q = v[(e + 1) % 3];
+  double tx = q[0] - p[0], ty = q[1] - p[1], tz = q[2] - p[2];
+  const double len = sqrt(tx * tx + ty * ty + tz * tz);
+  tx /= len;
+  ty /= len;
+  tz /= len;
+  const double px = p[0] - x[0], py = p[1] - x[1], pz = p[2] - x[2];
+  const double qx = q[0] - x[0], qy = q[1] - x[1], qz = q[2] - x[2];
+  const double sp = px * tx + py * ty + pz * tz;
+  const double sq = qx * tx + qy * ty + qz * tz;
+  const double ox = px - sp * tx, oy = py - sp * ty, oz = pz - sp * tz;
+  d = sqrt(ox * ox + oy * oy + oz * oz);
+  up = asinh(sp / d);
+  uq = asinh(sq / d);
+}
+
+// FP32 version for the mixed path: given the edge data (d, u range per edge, computed in
+// FP64), the angular quadrature and h(i k R) in FP32 (relative accuracy ~1e-6, the level
+// of the mixed path). Returns the part of the sum over the angular nodes t = part,
+// part + nparts, ... of the 96 = 3 edges x 2 sides x 16 nodes.
+__device__ inline float2 self_term32_part(const float d3[3], const float up3[3],
+                                          const float uq3[3], float kr, float ki,
+                                          const GL16& gl, int part, int nparts) {
   float tr = 0.f, ti = 0.f;
-  for (int e = 0; e < 3; ++e) {
-    const double* p = v[e];
-    const double* q = v[(e + 1) % 3];
-    double tx = q[0] - p[0], ty = q[1] - p[1], tz = q[2] - p[2];
-    const double len = sqrt(tx * tx + ty * ty + tz * tz);
-    tx /= len;
-    ty /= len;
-    tz /= len;
-    const double px = p[0] - x[0], py = p[1] - x[1], pz = p[2] - x[2];
-    const double qx = q[0] - x[0], qy = q[1] - x[1], qz = q[2] - x[2];
-    const double sp = px * tx + py * ty + pz * tz;
-    const double sq = qx * tx + qy * ty + qz * tz;
-    const double ox = px - sp * tx, oy = py - sp * ty, oz = pz - sp * tz;
-    const float d = (float)sqrt(ox * ox + oy * oy + oz * oz);
-    const float up = (float)asinh(sp / (double)d), uq = (float)asinh(sq / (double)d);
+  for (int t = part; t < 96; t += nparts) {
+    const int e = t / 32, side = (t / 16) % 2, gi = t % 16;
+    const float d = d3[e], up = up3[e], uq = uq3[e];
+    // the two sides of u = 0 when the foot lies inside the edge, else the whole range once
     const bool split = up < 0.f && uq > 0.f;
-    for (int s = 0; s < (split ? 2 : 1); ++s) {
-      const float lo = split ? (s == 0 ? up : 0.f) : up;
-      const float hi = split ? (s == 0 ? 0.f : uq) : uq;
-      const float half = 0.5f * (hi - lo), mid = 0.5f * (hi + lo);
-      for (int gi = 0; gi < 16; ++gi) {
-        const float R = d * coshf(mid + half * (float)gl.x[gi]);
-        const float wr = -ki * R, wi = kr * R;   // w = i k R
-        float hr, hi2;
-        if (wr * wr + wi * wi < 0.25f) {
-          // sum_m w^m / (m + 1)!, 10 terms
-          float sr = 0.f, si = 0.f, cr = 1.f, ci = 0.f;
-          for (int m = 0; m < 10; ++m) {
-            sr += cr;
-            si += ci;
-            const float nr = (cr * wr - ci * wi) / (m + 2.0f);
-            const float ni = (cr * wi + ci * wr) / (m + 2.0f);
-            cr = nr;
-            ci = ni;
-          }
-          hr = sr;
-          hi2 = si;
-        } else {
-          float sn, cs;
-          sincosf(wi, &sn, &cs);
-          const float ex = expf(wr);
-          const float nr = ex * cs - 1.f, ni = ex * sn;
-          const float dd = wr * wr + wi * wi;
-          hr = (nr * wr + ni * wi) / dd;
-          hi2 = (ni * wr - nr * wi) / dd;
-        }
-        const float f = half * (float)gl.w[gi] * d;
-        tr += f * hr;
-        ti += f * hi2;
-      }
+    float lo, hi;
+    if (split) {
+      lo = side == 0 ? up : 0.f;
+      hi = side == 0 ? 0.f : uq;
+    } else {
+      if (side == 1) continue;
+      lo = up;
+      hi = uq;
     }
+    const float half = 0.5f * (hi - lo), mid = 0.5f * (hi + lo);
+    const float R = d * coshf(mid + half * (float)gl.x[gi]);
+    const float wr = -ki * R, wi = kr * R;   // w = i k R
+    float hr, hi2;
+    if (wr * wr + wi * wi < 0.25f) {
+      // sum_m w^m / (m + 1)!, 10 terms
+      float sr = 0.f, si = 0.f, cr = 1.f, ci = 0.f;
+      for (int m = 0; m < 10; ++m) {
+        sr += cr;
+        si += ci;
+        const float nr = (cr * wr - ci * wi) / (m + 2.0f);
+        const float ni = (cr * wi + ci * wr) / (m + 2.0f);
+        cr = nr;
+        ci = ni;
+      }
+      hr = sr;
+      hi2 = si;
+    } else {
+      float sn, cs;
+      sincosf(wi, &sn, &cs);
+      const float ex = expf(wr);
+      const float nr = ex * cs - 1.f, ni = ex * sn;
+      const float dd = wr * wr + wi * wi;
+      hr = (nr * wr + ni * wi) / dd;
+      hi2 = (ni * wr - nr * wi) / dd;
+    }
+    const float f = half * (float)gl.w[gi] * d;
+    tr += f * hr;
+    ti += f * hi2;
   }
   const float inv4pi = (float)(1.0 / (4.0 * kPiD));
   return make_float2(tr * inv4pi, ti * inv4pi);
