@@ -129,6 +129,87 @@ bem_status bem_residual(bem_ctx* ctx, int m, const double* lam_host, const doubl
                         int64_t ldx, double* R_dev, double* relres_host, void* stream);
 
 /*
+ * Reduced linearised eigenproblem (Section 3.1, Eq. EVP_red, Eq. sc1_cauchy_red, Eq. sc2 -
+ * sc5). Given the weighted projected matrices Bhat_j (N x nu x nu, as bem_project writes
+ * them, for the context's current contour), finds eigenpairs of
+ *     sum_j Bhat_j y / (lambda - z_j) = 0
+ * nearest the shift s by subspace iteration with a block of p vectors on the shifted and
+ * inverted linearisation H = (A - s M)^{-1} M (applied through the Schur complement
+ * S = sum_j Bhat_j / (z_j - s)), CholeskyQR2 after every application and a Rayleigh-Ritz
+ * step every 5 iterations; stops when every Ritz value inside the contour among the p/2
+ * with the largest |mu| has reduced residual
+ * ||sum_j Bhat_j y / (lambda - z_j)|| / (||y|| sum_j ||Bhat_j|| / |lambda - z_j|) <= tol,
+ * or after max_iter iterations. The shift must not be an eigenvalue (S must be regular;
+ * a singular S is reported as BEM_EKERNEL). Directions that H annihilates are refilled
+ * at random, so p may exceed the number of non-negligible eigenvalues.
+ *   lam_host  2*p doubles: the p Ritz values (complex, nearest the shift first is NOT
+ *             guaranteed; callers filter by position and residual)
+ *   Y_dev     nu x p complex (column-major): y-parts of the Ritz vectors
+ *   res_host  p doubles: their reduced residuals
+ *   iters_done  iterations performed (may be NULL)
+ * 1 <= p <= min(256, N nu). Uses the context's scratch. Synchronises the stream.
+ */
+bem_status bem_solve_reduced(bem_ctx* ctx, const double* Bhat_dev, int nu, double shift_re,
+                             double shift_im, int p, int max_iter, double tol, double* lam_host,
+                             double* Y_dev, double* res_host, int* iters_done, void* stream);
+
+/*
+ * Ritz vectors x = V y (Section 3: approximate eigenvectors u = U y): X_dev (n x k,
+ * leading dimension ldx) = V_dev (n x nu, ldv) Y_dev (nu x k). FP64. Asynchronous.
+ */
+bem_status bem_ritz_vectors(bem_ctx* ctx, const double* V_dev, int64_t ldv, int nu,
+                            const double* Y_dev, int k, double* X_dev, int64_t ldx, void* stream);
+
+/*
+ * Basis improvement by q steps of the inverse power method for the Cauchy linearisation
+ * (Section 3.3, Algorithm 1; Eq. wjp1, Eq. vjp1, Eq. viupd, Eq. linsyssim) with shift s,
+ * applied to every column of V (n x nu, leading dimension ldv) at once, starting from
+ * v_j = u / (z_j - s):
+ *     S u' = sum_j B_j v_j / (z_j - s),  S = sum_j w_j A(z_j) / (z_j - s),
+ *     v_j' = (v_j - u') / (z_j - s).
+ * (The algebra of (A - sM) w' = M w; the extra u term of the paper's right-hand side
+ * vanishes because M has a zero last block.) S is assembled densely in FP32 and LU-
+ * factorised once; sum_j B_j v_j / (z_j - s) is applied matrix-free in FP32. On return V
+ * holds the last u (not orthonormalised). Needs n^2 * 8 + N n nu * 8 bytes of scratch.
+ * N <= 64, 1 <= nu <= 256. Synchronises the stream.
+ */
+bem_status bem_inverse_power(bem_ctx* ctx, double* V_dev, int64_t ldv, int nu, int q,
+                             double shift_re, double shift_im, void* stream);
+
+/*
+ * FP64 refinement of approximate eigenpairs of A(k) x = 0 (the eigenpairs the paper
+ * measures by ||T(lambda) u|| / ||u||, Section 4): residual inverse iteration with a
+ * frozen FP32 LU of A(sigma) and a Newton step for lambda on
+ * e^H A(sigma)^{-1} A(lambda) x = 0 (e = the starting vector); residuals A(lambda) x and
+ * A'(lambda) x are FP64 and matrix-free, so the converged pair is an FP64 eigenpair.
+ * sigma starts at the given lambda and moves to the current one when the step stalls.
+ *   lam_host   2*m doubles: in, starting values; out, refined eigenvalues
+ *   X_dev      n x m (ld ldx): in, starting vectors; out, refined vectors (e^H x = 1)
+ *   relres_host m doubles: final ||A(lambda) x|| / ||x||
+ *   iters_host  optional m ints: iterations used
+ * Stops a pair when |dlambda| <= tol |lambda| or after maxit iterations. Synchronises.
+ */
+bem_status bem_refine(bem_ctx* ctx, int m, double* lam_host, double* X_dev, int64_t ldx,
+                      double tol, int maxit, double* relres_host, int* iters_host, void* stream);
+
+/*
+ * The whole method (Algorithm 3 with one outer pass) for the context's mesh and contour:
+ * basis V0 (n x nu, ld ldv; not modified) -> q inverse power steps about the contour's
+ * centre -> CholeskyQR2 -> projection (precision BEM_PREC_FP64 or BEM_PREC_MIXED) ->
+ * reduced linearised eigenproblem -> Ritz pairs inside the contour with small reduced
+ * residual, nearest the centre first, at most kmax -> FP64 refinement (tolerance tol).
+ *   lam_host    2*kmax doubles: eigenvalues found
+ *   X_dev       n x kmax (ld ldx): their vectors
+ *   k_found     number of pairs returned (several may share an eigenvalue: degenerate
+ *               eigenvalues appear once per independent vector)
+ *   relres_host kmax doubles: ||A(lambda) x|| / ||x||
+ * Synchronises the stream.
+ */
+bem_status bem_solve(bem_ctx* ctx, const double* V0_dev, int64_t ldv, int nu, int q,
+                     int precision, double tol, int kmax, double* lam_host, double* X_dev,
+                     int64_t ldx, int* k_found, double* relres_host, void* stream);
+
+/*
  * Synchronise `stream` and report errors that kernels recorded in the context's device
  * status word since the last check (asynchronous calls such as bem_project report device-
  * side failures here): BEM_ETIMEOUT if a bounded wait inside a kernel gave up (the kernel

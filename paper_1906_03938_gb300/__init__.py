@@ -44,6 +44,13 @@ SIGNATURES = {
     "bem_residual": (_I, [_P, _I, _P, _P, _I64, _P, _P, _P]),
     "bem_kernel_launches": (_I64, [_P]),
     "bem_check": (_I, [_P, _P]),
+    "bem_solve_reduced": (_I, [_P, _P, _I, _D, _D, _I, _I, _D, _P, _P, _P,
+                               ctypes.POINTER(_I), _P]),
+    "bem_ritz_vectors": (_I, [_P, _P, _I64, _I, _P, _I, _P, _I64, _P]),
+    "bem_inverse_power": (_I, [_P, _P, _I64, _I, _I, _D, _D, _P]),
+    "bem_refine": (_I, [_P, _I, _P, _P, _I64, _D, _I, _P, _P, _P]),
+    "bem_solve": (_I, [_P, _P, _I64, _I, _I, _I, _D, _I, _P, _P, _I64, ctypes.POINTER(_I),
+                       _P, _P]),
     "bem_set_timing": (_I, [_P, _I]),
     "bem_kernel_times": (_I, [_P, _P, _I, ctypes.POINTER(_I)]),
     "bem_microbench": (_I, [_P, _I, ctypes.POINTER(_D)]),
@@ -202,6 +209,72 @@ class Context:
             _stream(stream)))
         Bm = Bhat.transpose(1, 2)
         return (Bm, Y.transpose(1, 2)) if Y is not None else Bm
+
+    def solve_reduced(self, Bhat, shift, p=None, max_iter=200, tol=1e-12, stream=None):
+        """Eigenpairs of the reduced linearised problem from Bhat (N x nu x nu matrices,
+        as returned by project). Returns (lam, Y, res, iters): Ritz values, y-parts
+        (nu x p tensor), reduced residuals."""
+        import torch
+        N, nu, _ = Bhat.shape
+        if p is None:
+            p = min(N * nu, 256, max(2 * nu, 32))
+        Bm = Bhat.transpose(1, 2).contiguous()        # column-major per node
+        lam = np.zeros(2 * p)
+        res = np.zeros(p)
+        Y = torch.empty((p, nu), dtype=torch.complex128, device=Bhat.device)
+        it = _I(0)
+        sh = complex(shift)
+        self._chk("bem_solve_reduced", self._lib.bem_solve_reduced(
+            self._h, _ptr(Bm), nu, sh.real, sh.imag, int(p), int(max_iter), float(tol),
+            _ptr(lam), _ptr(Y), _ptr(res), ctypes.byref(it), _stream(stream)))
+        return lam.view(np.complex128), Y.transpose(0, 1), res, it.value
+
+    def ritz_vectors(self, V, Y, stream=None):
+        import torch
+        _check_fortran(V, "V")
+        n, nu = V.shape
+        Yc = fortran(Y) if not (Y.stride(0) == 1 and Y.stride(1) == nu) else Y
+        k = Yc.shape[1]
+        X = torch.empty((k, n), dtype=torch.complex128, device=V.device)
+        self._chk("bem_ritz_vectors", self._lib.bem_ritz_vectors(
+            self._h, _ptr(V), V.stride(1), nu, _ptr(Yc), k, _ptr(X), n, _stream(stream)))
+        return X.transpose(0, 1)
+
+    def inverse_power(self, V, q, shift, stream=None):
+        """q steps of Algorithm 1 on every column of V (in place)."""
+        _check_fortran(V, "V")
+        n, nu = V.shape
+        sh = complex(shift)
+        self._chk("bem_inverse_power", self._lib.bem_inverse_power(
+            self._h, _ptr(V), V.stride(1), nu, int(q), sh.real, sh.imag, _stream(stream)))
+
+    def refine(self, lam, X, tol=1e-13, maxit=40, stream=None):
+        """FP64 refinement of eigenpairs (X refined in place); returns (lam, relres, iters)."""
+        _check_fortran(X, "X")
+        n, m = X.shape
+        lam = np.ascontiguousarray(np.asarray(lam, dtype=np.complex128).reshape(m)).copy()
+        rel = np.zeros(m)
+        its = np.zeros(m, dtype=np.int32)
+        self._chk("bem_refine", self._lib.bem_refine(
+            self._h, m, _ptr(lam.view(np.float64)), _ptr(X), X.stride(1), float(tol), int(maxit),
+            _ptr(rel), _ptr(its), _stream(stream)))
+        return lam, rel, its
+
+    def solve(self, V0, q=10, precision=PREC_FP64, tol=1e-13, kmax=None, stream=None):
+        """Eigenpairs inside the contour: (lam, X, relres)."""
+        import torch
+        _check_fortran(V0, "V0")
+        n, nu = V0.shape
+        kmax = kmax or min(n, 2 * nu)
+        lam = np.zeros(2 * kmax)
+        rel = np.zeros(kmax)
+        X = torch.zeros((kmax, n), dtype=torch.complex128, device=V0.device)
+        k = _I(0)
+        self._chk("bem_solve", self._lib.bem_solve(
+            self._h, _ptr(V0), V0.stride(1), nu, int(q), int(precision), float(tol), int(kmax),
+            _ptr(lam), _ptr(X), n, ctypes.byref(k), _ptr(rel), _stream(stream)))
+        kk = k.value
+        return lam.view(np.complex128)[:kk], X.transpose(0, 1)[:, :kk], rel[:kk]
 
     def cholqr2(self, V, want_R=True, stream=None):
         import torch

@@ -131,6 +131,7 @@ void bem_destroy(bem_ctx* ctx) {
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_scratch);
   cudaFree(ctx->d_small);
+  cudaFree(ctx->d_solve);
   for (auto& e : ctx->ev) cudaEventDestroy(e);
   delete ctx;
 }

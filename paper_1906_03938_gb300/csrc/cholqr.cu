@@ -17,7 +17,10 @@ namespace {
 // on exit the upper triangle holds R with G = R^H R, the strict lower triangle is zero.
 // A pivot below 1e-13 of the largest diagonal entry of G counts as loss of rank. One block;
 // G is staged in shared memory when the dynamic allocation holds it (nu <= 64).
-__global__ void __launch_bounds__(1024) cholesky_kernel(double2* Gg, int nu, int* status) {
+// With `deficient` non-null, a collapsed pivot does not fail: its column of R becomes the
+// unit vector (the column of V is then replaced by the caller) and deficient[k] = 1.
+__global__ void __launch_bounds__(1024) cholesky_kernel(double2* Gg, int nu, int* status,
+                                                        int* deficient) {
   extern __shared__ double2 sG[];
   __shared__ double rkk, dmax;
   const bool staged = nu <= 64;
@@ -36,17 +39,29 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(double2* Gg, int nu, int
     if (tid == 0) {
       const double d = G[(int64_t)k * nu + k].x;
       if (!(d > 1e-13 * dmax) || !isfinite(d)) {
-        atomicOr(status, kStatusNotSPD);
-        rkk = 0.0;
+        if (deficient) {
+          deficient[k] = 1;
+          rkk = -1.0;   // marker: unit column, no trailing update
+        } else {
+          atomicOr(status, kStatusNotSPD);
+          rkk = 0.0;
+        }
       } else {
+        if (deficient) deficient[k] = 0;
         rkk = sqrt(d);
       }
-      G[(int64_t)k * nu + k] = make_double2(rkk, 0.0);
+      G[(int64_t)k * nu + k] = make_double2(rkk < 0.0 ? 1.0 : rkk, 0.0);
     }
     __syncthreads();
     if (rkk == 0.0) {
       failed = true;
       break;
+    }
+    if (rkk < 0.0) {
+      for (int jj = k + 1 + tid; jj < nu; jj += blockDim.x)
+        G[(int64_t)jj * nu + k] = make_double2(0.0, 0.0);
+      __syncthreads();
+      continue;
     }
     for (int jj = k + 1 + tid; jj < nu; jj += blockDim.x) {
       double2 g = G[(int64_t)jj * nu + k];
@@ -74,6 +89,22 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(double2* Gg, int nu, int
     const double2 v = (i > jj) ? make_double2(0.0, 0.0) : G[t];
     Gg[t] = failed ? make_double2(NAN, NAN) : v;
   }
+}
+
+// Columns flagged deficient get fresh pseudo-random entries (SplitMix64 of seed, index).
+__global__ void refresh_columns_kernel(double2* V, int64_t ldv, int64_t n, int nu,
+                                       const int* deficient, uint64_t seed) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * nu) return;
+  const int c = (int)(t / n);
+  if (!deficient[c]) return;
+  const int64_t r = t % n;
+  uint64_t a = seed + (2 * (uint64_t)t + 1) * 0x9E3779B97F4A7C15ull;
+  uint64_t b = seed + (2 * (uint64_t)t + 2) * 0x9E3779B97F4A7C15ull;
+  a = (a ^ (a >> 30)) * 0xBF58476D1CE4E5B9ull; a = (a ^ (a >> 27)) * 0x94D049BB133111EBull; a ^= a >> 31;
+  b = (b ^ (b >> 30)) * 0xBF58476D1CE4E5B9ull; b = (b ^ (b >> 27)) * 0x94D049BB133111EBull; b ^= b >> 31;
+  V[(int64_t)c * ldv + r] = make_double2((double)(a >> 11) * 0x1.0p-52 - 1.0,
+                                         (double)(b >> 11) * 0x1.0p-52 - 1.0);
 }
 
 constexpr int kGT = 32;   // Gram output tile
@@ -224,6 +255,74 @@ __global__ void upper_product_kernel(const double2* A, const double2* B, int nu,
 }
 
 }  // namespace
+
+size_t cholqr2_work_bytes(bem_ctx* ctx, int64_t n, int nu) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  const int tiles = ((nu + kGT - 1) / kGT) * ((nu + kGT - 1) / kGT);
+  int64_t parts = std::max<int64_t>(1, std::min<int64_t>((n + 63) / 64,
+                                                         (2 * (int64_t)sms + tiles - 1) / tiles));
+  const int64_t rows_per_part = (n + parts - 1) / parts;
+  parts = (n + rows_per_part - 1) / rows_per_part;
+  return (4 + (size_t)parts) * (size_t)nu * nu * sizeof(double2) + 256 * sizeof(int);
+}
+
+// CholeskyQR2 of V (n x nu, ld ldv) with caller-provided work (cholqr2_work_bytes);
+// asynchronous; a Gram matrix that is not positive definite is flagged in the context's
+// status word.
+bem_status cholqr2_impl(bem_ctx* ctx, double* V_dev, int64_t n, int64_t ldv, int nu,
+                        double* R_dev, void* work, cudaStream_t s, uint64_t refresh_seed) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  const int tiles = ((nu + kGT - 1) / kGT) * ((nu + kGT - 1) / kGT);
+  int64_t parts = std::max<int64_t>(1, std::min<int64_t>((n + 63) / 64,
+                                                         (2 * (int64_t)sms + tiles - 1) / tiles));
+  const int64_t rows_per_part = (n + parts - 1) / parts;
+  parts = (n + rows_per_part - 1) / rows_per_part;
+  double2* G = reinterpret_cast<double2*>(work);
+  double2* Rinv = G + (size_t)nu * nu;
+  double2* R1 = Rinv + (size_t)nu * nu;
+  double2* R2 = R1 + (size_t)nu * nu;
+  double2* part = R2 + (size_t)nu * nu;
+  int* deficient = reinterpret_cast<int*>(part + (size_t)parts * nu * nu);
+  bem_status st = BEM_OK;
+  const size_t chol_smem = nu <= 64 ? (size_t)nu * nu * sizeof(double2) : 0;
+  if (chol_smem > 48 * 1024) {
+    st = cuda_check(ctx, cudaFuncSetAttribute(cholesky_kernel,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)chol_smem),
+                    "cholqr attribute");
+    if (st != BEM_OK) return st;
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    double2* R = pass == 0 ? R1 : R2;
+    gram_partial_kernel<<<dim3((unsigned)tiles, (unsigned)parts), 256, 0, s>>>(
+        reinterpret_cast<const double2*>(V_dev), ldv, n, nu, rows_per_part, part);
+    sum_parts_kernel<<<(unsigned)(((int64_t)nu * nu + 255) / 256), 256, 0, s>>>(
+        part, (int)parts, (int64_t)nu * nu, R);
+    const bool refresh = refresh_seed != 0 && pass == 0;
+    cholesky_kernel<<<1, 1024, chol_smem, s>>>(R, nu, ctx->d_status, refresh ? deficient : nullptr);
+    triangular_inverse_kernel<<<nu, 128, 0, s>>>(R, nu, Rinv);
+    right_multiply_kernel<<<(unsigned)((n + kRows - 1) / kRows), 256, 0, s>>>(
+        reinterpret_cast<double2*>(V_dev), ldv, n, nu, Rinv);
+    ctx->launches += 5;
+    if (refresh) {
+      refresh_columns_kernel<<<(unsigned)((n * nu + 255) / 256), 256, 0, s>>>(
+          reinterpret_cast<double2*>(V_dev), ldv, n, nu, deficient, refresh_seed);
+      ctx->launches++;
+    }
+    st = cuda_check(ctx, cudaGetLastError(), "cholqr kernels");
+    if (st != BEM_OK) return st;
+  }
+  if (R_dev) {
+    upper_product_kernel<<<1, 256, 0, s>>>(R2, R1, nu, reinterpret_cast<double2*>(R_dev));
+    ctx->launches++;
+    st = cuda_check(ctx, cudaGetLastError(), "cholqr kernels");
+  }
+  (void)G;
+  return st;
+}
+
 }  // namespace bem
 
 using namespace bem;
@@ -235,51 +334,9 @@ extern "C" bem_status bem_cholqr2(bem_ctx* ctx, double* V_dev, int64_t n, int64_
     return fail(ctx, BEM_EINVAL, "bem_cholqr2: need V, 1 <= nu <= min(n, 256), ldv >= n");
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t mat = (size_t)nu * nu * 2;
-  // Gram partials: enough row ranges to occupy the device, at least 64 rows each
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  const int tiles = ((nu + kGT - 1) / kGT) * ((nu + kGT - 1) / kGT);
-  int64_t parts = std::max<int64_t>(1, std::min<int64_t>((n + 63) / 64,
-                                                         (2 * (int64_t)sms + tiles - 1) / tiles));
-  const int64_t rows_per_part = (n + parts - 1) / parts;
-  parts = (n + rows_per_part - 1) / rows_per_part;
-  bem_status st = ensure_small(ctx, (4 + (size_t)parts) * mat * sizeof(double));
+  bem_status st = ensure_small(ctx, cholqr2_work_bytes(ctx, n, nu));
   if (st != BEM_OK) return st;
-  double2* G = reinterpret_cast<double2*>(ctx->d_small);
-  double2* Rinv = G + (size_t)nu * nu;
-  double2* R1 = Rinv + (size_t)nu * nu;
-  double2* R2 = R1 + (size_t)nu * nu;
-  double2* part = R2 + (size_t)nu * nu;
-  const size_t chol_smem = nu <= 64 ? (size_t)nu * nu * sizeof(double2) : 0;
-  if (chol_smem > 48 * 1024) {
-    st = cuda_check(ctx, cudaFuncSetAttribute(cholesky_kernel,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)chol_smem),
-                    "cholqr attribute");
-    if (st != BEM_OK) return st;
-  }
-
-  for (int pass = 0; pass < 2; ++pass) {
-    double2* R = pass == 0 ? R1 : R2;
-    gram_partial_kernel<<<dim3((unsigned)tiles, (unsigned)parts), 256, 0, s>>>(
-        reinterpret_cast<const double2*>(V_dev), ldv, n, nu, rows_per_part, part);
-    sum_parts_kernel<<<(unsigned)(((int64_t)nu * nu + 255) / 256), 256, 0, s>>>(
-        part, (int)parts, (int64_t)nu * nu, R);
-    cholesky_kernel<<<1, 1024, chol_smem, s>>>(R, nu, ctx->d_status);
-    triangular_inverse_kernel<<<nu, 128, 0, s>>>(R, nu, Rinv);
-    right_multiply_kernel<<<(unsigned)((n + kRows - 1) / kRows), 256, 0, s>>>(
-        reinterpret_cast<double2*>(V_dev), ldv, n, nu, Rinv);
-    ctx->launches += 5;
-    st = cuda_check(ctx, cudaGetLastError(), "cholqr kernels");
-    if (st != BEM_OK) return st;
-  }
-  if (R_dev) {
-    upper_product_kernel<<<1, 256, 0, s>>>(R2, R1, nu, reinterpret_cast<double2*>(R_dev));
-    ctx->launches++;
-    st = cuda_check(ctx, cudaGetLastError(), "cholqr kernels");
-    if (st != BEM_OK) return st;
-  }
-  (void)G;
+  st = cholqr2_impl(ctx, V_dev, n, ldv, nu, R_dev, ctx->d_small, s, 0);
+  if (st != BEM_OK) return st;
   return take_status(ctx, s, "bem_cholqr2");
 }

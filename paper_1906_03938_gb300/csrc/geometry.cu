@@ -179,6 +179,14 @@ cudaError_t launch_self_terms32(bem_ctx* ctx, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_self32(bem_ctx* ctx, int nk, const double* kz, float* out, cudaStream_t s) {
+  static const GL16 gl = make_gl16();
+  const int64_t total = ctx->geo.n * (int64_t)nk;
+  self_term32_kernel<<<(unsigned)((32 * total + 255) / 256), 256, 0, s>>>(ctx->geo, nk, kz, gl, out);
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_self_terms(bem_ctx* ctx, cudaStream_t s) {
   static const GL16 gl = make_gl16();
   const int64_t total = ctx->geo.n * (int64_t)ctx->con.N;

@@ -15,6 +15,8 @@ constexpr int kMaxNu = 256;
 constexpr int kMaxNodes = 4096;
 // Launches of the projection's main kernel whose duration is kept when timing is on.
 constexpr int kMaxTimed = 256;
+// Contour nodes the dense / matrix-free FP32 solver kernels accept.
+constexpr int kMaxNodesSolve = 64;
 
 // Bits of the device status word.
 enum : int {
@@ -76,6 +78,9 @@ struct bem_ctx {
   int64_t launches = 0;
   int64_t mesh_version = 0;         // bumped by every successful bem_set_mesh
   int64_t contour_version = 0;      // bumped by every successful bem_set_contour
+  // buffers of bem_solve (grown on demand, owned by the context)
+  double* d_solve = nullptr;
+  size_t solve_bytes = 0;
   bool timing = false;              // record events around the main projection kernel
   std::vector<cudaEvent_t> ev;      // 2 * kMaxTimed events (start, stop)
   int n_timed = 0;
@@ -105,6 +110,23 @@ cudaError_t launch_geometry(bem_ctx* ctx, cudaStream_t s);
 cudaError_t launch_contour(bem_ctx* ctx, cudaStream_t s);
 cudaError_t launch_self_terms(bem_ctx* ctx, cudaStream_t s);
 cudaError_t launch_self_terms32(bem_ctx* ctx, cudaStream_t s);
+// FP32 self terms of the mesh at nk wavenumbers kz (device, complex) into out (nk x n).
+cudaError_t launch_self32(bem_ctx* ctx, int nk, const double* kz, float* out, cudaStream_t s);
+// R[:, c] = A(lam_c) X[:, c] (deriv: A'(lam_c) X[:, c]), FP64, matrix-free (residual.cu);
+// R has leading dimension n. lam_dev: m complex on the device.
+cudaError_t launch_apply_percol64(bem_ctx* ctx, int m, const double* lam_dev, const double* X,
+                                  int64_t ldx, double* R, bool deriv, cudaStream_t s);
+// out[2c] = ||R[:, c]||^2, out[2c+1] = ||X[:, c]||^2 (fixed-order sums)
+cudaError_t launch_colnorms(bem_ctx* ctx, const double* R, int64_t ldr, const double* X,
+                            int64_t ldx, int64_t n, int m, double* out, cudaStream_t s);
+// dense FP32 operator and LU (dense32.cu)
+bem_status assemble32(bem_ctx* ctx, int nk, const double* kz_host, const double* coef_host,
+                      float2* M, cudaStream_t s);
+bem_status lu32(bem_ctx* ctx, float2* A, int64_t n, int* ipiv, cudaStream_t s);
+bem_status lu32_solve(bem_ctx* ctx, const float2* LU, const int* ipiv, int64_t n, float2* B,
+                      int64_t m, cudaStream_t s);
+cudaError_t launch_zgemm(bem_ctx* ctx, int m, int n, int k, const double* A, int64_t lda,
+                         const double* B, int64_t ldb, double* C, int64_t ldc, cudaStream_t s);
 // Fill the FP64 / FP32 self-term table of the current contour if not done yet.
 bem_status ensure_self64(bem_ctx* ctx, cudaStream_t s);
 bem_status ensure_self32(bem_ctx* ctx, cudaStream_t s);
@@ -117,6 +139,13 @@ cudaError_t launch_apply_fp64(bem_ctx* ctx, const double* V, int64_t ldv, int nu
 cudaError_t launch_xhy_fp64(bem_ctx* ctx, const double* X, int64_t ldx, int p, const double* Y,
                             int64_t ldy, int64_t strideY, int q, int64_t n, int nb,
                             const double* scale, double* C, cudaStream_t s);
+// CholeskyQR2 with caller-provided work space (asynchronous; status word on failure).
+// refresh_seed != 0: columns whose first-pass pivot collapses (rank deficiency) are
+// replaced by pseudo-random columns before the second pass instead of failing; R is then
+// not a factor of the input.
+size_t cholqr2_work_bytes(bem_ctx* ctx, int64_t n, int nu);
+bem_status cholqr2_impl(bem_ctx* ctx, double* V, int64_t n, int64_t ldv, int nu, double* R,
+                        void* work, cudaStream_t s, uint64_t refresh_seed);
 // mixed-precision fused projection (tcgen05); defined in project_mixed.cu
 bem_status project_mixed(bem_ctx* ctx, const double* V, int64_t ldv, int nu, double* Bhat,
                          double* AV, cudaStream_t s);

@@ -17,6 +17,8 @@ namespace {
 constexpr int kRowsPerBlock = 128;
 constexpr int kChunk = 128;
 
+// kDeriv: the k-derivative of the off-diagonal entries, sum_q W_lq i exp(i k r) / (4 pi).
+template <bool kDeriv>
 __global__ void __launch_bounds__(kRowsPerBlock)
 residual_kernel(Geometry g, const double* __restrict__ lam, const double* __restrict__ X,
                 int64_t ldx, double* __restrict__ R) {
@@ -63,9 +65,14 @@ residual_kernel(Geometry g, const double* __restrict__ lam, const double* __rest
           const double r = sqrt(dx * dx + dy * dy + dz * dz);
           double s, co;
           sincos(kr * r, &s, &co);
-          const double amp = sQ[3][q][lc] * exp(-ki * r) / r;
-          a.x += amp * co;
-          a.y += amp * s;
+          const double amp = kDeriv ? sQ[3][q][lc] * exp(-ki * r) : sQ[3][q][lc] * exp(-ki * r) / r;
+          if (kDeriv) {   // i * amp * (co + i s)
+            a.x -= amp * s;
+            a.y += amp * co;
+          } else {
+            a.x += amp * co;
+            a.y += amp * s;
+          }
         }
         const double2 v = sX[lc];
         acc.x += a.x * v.x - a.y * v.y;
@@ -83,9 +90,10 @@ residual_kernel(Geometry g, const double* __restrict__ lam, const double* __rest
   }
 }
 
-// Self term A_ii(lambda_c) of every row, written into R as the multiplier of x_i.
+// Self term A_ii(lambda_c) (or its k-derivative) of every row, written into R as the
+// multiplier of x_i.
 __global__ void self_at_kernel(Geometry g, const double* __restrict__ lam, GL16 gl,
-                               double* __restrict__ R) {
+                               double* __restrict__ R, bool deriv) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int c = blockIdx.y;
   if (i >= g.n) return;
@@ -96,7 +104,7 @@ __global__ void self_at_kernel(Geometry g, const double* __restrict__ lam, GL16 
   }
   for (int d = 0; d < 3; ++d) x[d] = g.cx[d * g.n + i];
   reinterpret_cast<double2*>(R)[(int64_t)c * g.n + i] =
-      self_term(v, x, make_double2(lam[2 * c], lam[2 * c + 1]), gl);
+      self_term(v, x, make_double2(lam[2 * c], lam[2 * c + 1]), gl, deriv);
 }
 
 __global__ void norms_kernel(const double* __restrict__ R, const double* __restrict__ X,
@@ -127,6 +135,30 @@ __global__ void norms_kernel(const double* __restrict__ R, const double* __restr
 }
 
 }  // namespace
+
+cudaError_t launch_apply_percol64(bem_ctx* ctx, int m, const double* lam_dev, const double* X,
+                                  int64_t ldx, double* R, bool deriv, cudaStream_t s) {
+  static const GL16 gl = make_gl16();
+  const int64_t n = ctx->geo.n;
+  dim3 g1((unsigned)((n + 127) / 128), (unsigned)m);
+  self_at_kernel<<<g1, 128, 0, s>>>(ctx->geo, lam_dev, gl, R, deriv);
+  dim3 g2((unsigned)((n + kRowsPerBlock - 1) / kRowsPerBlock), (unsigned)m);
+  if (deriv)
+    residual_kernel<true><<<g2, kRowsPerBlock, 0, s>>>(ctx->geo, lam_dev, X, ldx, R);
+  else
+    residual_kernel<false><<<g2, kRowsPerBlock, 0, s>>>(ctx->geo, lam_dev, X, ldx, R);
+  ctx->launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colnorms(bem_ctx* ctx, const double* R, int64_t ldr, const double* X,
+                            int64_t ldx, int64_t n, int m, double* out, cudaStream_t s) {
+  (void)ldr;
+  norms_kernel<<<m, 256, 0, s>>>(R, X, ldx, n, out);
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
 }  // namespace bem
 
 using namespace bem;
@@ -157,14 +189,10 @@ extern "C" bem_status bem_residual(bem_ctx* ctx, int m, const double* lam_host, 
   st = cuda_check(ctx, cudaMemcpyAsync(dlam, lam_host, 2 * m * sizeof(double),
                                        cudaMemcpyHostToDevice, s), "bem_residual copy");
   if (st != BEM_OK) return st;
-  static const GL16 gl = make_gl16();
-  dim3 g1((unsigned)((n + 127) / 128), (unsigned)m);
-  self_at_kernel<<<g1, 128, 0, s>>>(ctx->geo, dlam, gl, R);
-  dim3 g2((unsigned)((n + kRowsPerBlock - 1) / kRowsPerBlock), (unsigned)m);
-  residual_kernel<<<g2, kRowsPerBlock, 0, s>>>(ctx->geo, dlam, X_dev, ldx, R);
-  norms_kernel<<<m, 256, 0, s>>>(R, X_dev, ldx, n, dnorm);
-  ctx->launches += 3;
-  st = cuda_check(ctx, cudaGetLastError(), "residual kernels");
+  st = cuda_check(ctx, launch_apply_percol64(ctx, m, dlam, X_dev, ldx, R, false, s),
+                  "residual kernels");
+  if (st != BEM_OK) return st;
+  st = cuda_check(ctx, launch_colnorms(ctx, R, n, X_dev, ldx, n, m, dnorm, s), "residual kernels");
   if (st != BEM_OK) return st;
   std::vector<double> h(2 * m);
   st = cuda_check(ctx, cudaMemcpyAsync(h.data(), dnorm, 2 * m * sizeof(double),

@@ -77,9 +77,34 @@ __device__ inline double2 h_fun(double2 w) {
   return make_double2((num.x * w.x + num.y * w.y) / d, (num.y * w.x - num.x * w.y) / d);
 }
 
+// h'(w) = (w e^w - e^w + 1) / w^2; Taylor series sum_{m>=1} m w^{m-1} / (m + 1)! near 0.
+__device__ inline double2 hprime_fun(double2 w) {
+  if (w.x * w.x + w.y * w.y < 0.25) {
+    double2 s = make_double2(0.0, 0.0), p = make_double2(1.0, 0.0);   // p = w^{m-1}
+    double fact = 2.0;                                                // (m + 1)!
+    for (int m = 1; m < 26; ++m) {
+      s.x += m * p.x / fact;
+      s.y += m * p.y / fact;
+      p = zmul(p, w);
+      fact *= (m + 2.0);
+    }
+    return s;
+  }
+  double sn, cs;
+  sincos(w.y, &sn, &cs);
+  const double e = exp(w.x);
+  const double2 ew = make_double2(e * cs, e * sn);
+  const double2 num = make_double2(zmul(w, ew).x - ew.x + 1.0, zmul(w, ew).y - ew.y);
+  const double2 w2 = zmul(w, w);
+  const double d = w2.x * w2.x + w2.y * w2.y;
+  return make_double2((num.x * w2.x + num.y * w2.y) / d, (num.y * w2.x - num.x * w2.y) / d);
+}
+
 // Self term of the triangle with vertices v[0..2] about the point x, at wavenumber k.
+// (deriv = true: its derivative in k, the integral of i R^2 h'(i k R) d(phi), i.e.
+// i d^2 cosh(u) h'(i k d cosh u) du along each edge.)
 __device__ inline double2 self_term(const double v[3][3], const double x[3], double2 k,
-                                    const GL16& gl) {
+                                    const GL16& gl, bool deriv = false) {
   double2 total = make_double2(0.0, 0.0);
   for (int e = 0; e < 3; ++e) {
     const double* p = v[e];
@@ -103,10 +128,18 @@ __device__ inline double2 self_term(const double v[3][3], const double x[3], dou
       const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
       for (int gi = 0; gi < 16; ++gi) {
         const double R = d * cosh(mid + half * gl.x[gi]);
-        const double2 h = h_fun(make_double2(-k.y * R, k.x * R));   // h(i k R)
-        const double f = half * gl.w[gi] * d;
-        total.x += f * h.x;
-        total.y += f * h.y;
+        const double2 wv = make_double2(-k.y * R, k.x * R);   // i k R
+        if (deriv) {
+          const double2 hp = hprime_fun(wv);
+          const double f = half * gl.w[gi] * d * R;         // d^2 cosh(u) = d R
+          total.x += -f * hp.y;                               // i * hp
+          total.y += f * hp.x;
+        } else {
+          const double2 h = h_fun(wv);
+          const double f = half * gl.w[gi] * d;
+          total.x += f * h.x;
+          total.y += f * h.y;
+        }
       }
     }
   }

@@ -1,0 +1,572 @@
+// The steps around the projection: basis improvement by inverse power steps (Algorithm 1)
+// and refinement of Ritz pairs against the true operator (residual inverse iteration).
+//
+// Inverse power (Algorithm 1; Eq. wjp1, Eq. vjp1, Eq. viupd, Eq. linsyssim), shift s:
+//   S u' = sum_j B_j v_j / (z_j - s),  S = sum_j B_j / (z_j - s),  B_j = w_j A(z_j),
+//   v_j' = (v_j - u') / (z_j - s),
+// for every basis column at once, q times, from v_j = u / (z_j - s). S is assembled densely
+// (FP32) and factorised once (blocked LU); the right-hand side is applied matrix-free by
+// apply_nodes32_kernel. The iterates are rescaled column by column (direction only).
+//
+// Refinement: for an approximate eigenpair (lambda, x) of A(k) x = 0, residual inverse
+// iteration with a frozen factorisation of A(sigma) (Neumaier 1985) and a Newton step for
+// lambda on f(lambda) = e^H A(sigma)^{-1} A(lambda) x:
+//   r = A(lambda) x, r' = A'(lambda) x           (FP64, matrix-free)
+//   [s1 s2] = A(sigma)^{-1} [r r']                (FP32 LU)
+//   dlambda = -(e^H s1) / (e^H s2), x <- x - (s1 + dlambda s2), x <- x / (e^H x)
+// The fixed point is an FP64-exact eigenpair (r = 0) whatever the LU's precision; sigma
+// is moved to the current lambda when the iteration stalls.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+
+namespace bem {
+namespace {
+
+constexpr float kLog2eF = 1.4426950408889634f;
+constexpr float kInv2PiF = 0.15915494309189535f;
+constexpr float kTwoPiHiF = 6.28318548202514648f;
+constexpr float kTwoPiLoF = -1.7484555314695172e-7f;
+
+__device__ __forceinline__ float fex2(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float fsin(float x) {
+  float r;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float fcos(float x) {
+  float r;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+constexpr int kAR = 64;   // rows per block
+constexpr int kAC = 32;   // columns of A per panel
+constexpr int kAV = 64;   // basis columns per block
+
+struct NodeList {
+  int N;
+  float kr[kMaxNodesSolve], kmi[kMaxNodesSolve], cr[kMaxNodesSolve], ci[kMaxNodesSolve];
+};
+
+// out[:, c] = sum_j c_j A(z_j) Vn_j[:, c], Vn node-major (N x n x nu, FP32 complex,
+// column-major per node), out n x nu FP32 complex. Self terms from the FP32 table.
+__global__ void __launch_bounds__(256)
+apply_nodes32_kernel(Geometry g, NodeList nl, const float2* __restrict__ self32,
+                     const float2* __restrict__ Vn, int nu, float2* __restrict__ out) {
+  __shared__ float2 sA[kAR][kAC + 1];
+  __shared__ float2 sV[kAC][kAV];
+  __shared__ float sQ[4][7][kAC];
+  __shared__ float sC[3][kAR];
+  const int64_t n = g.n;
+  const int tid = threadIdx.x;
+  const int64_t row0 = (int64_t)blockIdx.x * kAR;
+  const int col0 = blockIdx.y * kAV;
+  if (tid < kAR) {
+    const int64_t i = row0 + tid;
+    for (int c = 0; c < 3; ++c) sC[c][tid] = i < n ? g.cx32[c * n + i] : 0.f;
+  }
+  const int gr = tid / 4;          // output row
+  const int gc0 = tid % 4;         // output columns gc0 + 4 m, m < 16
+  float2 acc[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) acc[m] = make_float2(0.f, 0.f);
+  const int el = tid % kAC, er0 = tid / kAC;   // evaluation: column el, rows er0 + 8 m
+  for (int64_t l0 = 0; l0 < n; l0 += kAC) {
+    __syncthreads();
+    for (int t = tid; t < 7 * kAC; t += 256) {
+      const int q = t / kAC, lc = t % kAC;
+      const int64_t l = l0 + lc;
+      const bool ok = l < n;
+      sQ[0][q][lc] = ok ? g.qp32[q * n + l] : 1e3f;
+      sQ[1][q][lc] = ok ? g.qp32[(7 + q) * n + l] : 1e3f;
+      sQ[2][q][lc] = ok ? g.qp32[(14 + q) * n + l] : 1e3f;
+      sQ[3][q][lc] = ok ? g.qw32[q * n + l] : 0.f;
+    }
+    __syncthreads();
+    for (int j = 0; j < nl.N; ++j) {
+      // entries of c_j A(z_j) for this 64 x 32 panel
+      const int64_t l = l0 + el;
+      for (int m = 0; m < kAR / 8; ++m) {
+        const int rr = er0 + 8 * m;
+        const int64_t i = row0 + rr;
+        float sr = 0.f, si = 0.f;
+        if (i < n && l < n) {
+          if (i == l) {
+            const float2 v = self32[(int64_t)j * n + l];
+            sr = v.x;
+            si = v.y;
+          } else {
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+              const float dx = sC[0][rr] - sQ[0][q][el], dy = sC[1][rr] - sQ[1][q][el],
+                          dz = sC[2][rr] - sQ[2][q][el];
+              const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+              const float rs = rsqrtf(r2);
+              const float r = r2 * rs;
+              const float a = sQ[3][q][el] * rs * fex2(nl.kmi[j] * r);
+              const float ph = nl.kr[j] * r;
+              const float nrot = fmaf(ph, kInv2PiF, 12582912.0f) - 12582912.0f;
+              const float red = fmaf(-nrot, kTwoPiLoF, fmaf(-nrot, kTwoPiHiF, ph));
+              sr = fmaf(a, fcos(red), sr);
+              si = fmaf(a, fsin(red), si);
+            }
+          }
+        }
+        sA[rr][el] = make_float2(nl.cr[j] * sr - nl.ci[j] * si, nl.cr[j] * si + nl.ci[j] * sr);
+      }
+      const float2* Vj = Vn + (int64_t)j * n * nu;
+      for (int t = tid; t < kAC * kAV; t += 256) {
+        const int k = t / kAV, c = t % kAV;
+        const int64_t ll = l0 + k;
+        sV[k][c] = (ll < n && col0 + c < nu) ? Vj[(int64_t)(col0 + c) * n + ll] : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int k = 0; k < kAC; ++k) {
+        const float2 a = sA[gr][k];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          const float2 v = sV[k][gc0 + 4 * m];
+          acc[m].x = fmaf(a.x, v.x, fmaf(-a.y, v.y, acc[m].x));
+          acc[m].y = fmaf(a.x, v.y, fmaf(a.y, v.x, acc[m].y));
+        }
+      }
+      __syncthreads();
+    }
+  }
+  const int64_t i = row0 + gr;
+  if (i < n)
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int c = col0 + gc0 + 4 * m;
+      if (c < nu) out[(int64_t)c * n + i] = acc[m];
+    }
+}
+
+// Vn_j = u / (z_j - s) (u FP64 n x nu, ld ldu)
+__global__ void ip_start_kernel(const double2* __restrict__ U, int64_t ldu, int64_t n, int nu,
+                                int N, const double2* __restrict__ z, double2 s, float2* Vn) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per = n * nu;
+  if (t >= per * N) return;
+  const int j = (int)(t / per);
+  const int64_t e = t % per;
+  const int c = (int)(e / n);
+  const int64_t i = e % n;
+  const double2 u = U[(int64_t)c * ldu + i];
+  const double2 d = make_double2(z[j].x - s.x, z[j].y - s.y);
+  const double dd = d.x * d.x + d.y * d.y;
+  Vn[t] = make_float2((float)((u.x * d.x + u.y * d.y) / dd), (float)((u.y * d.x - u.x * d.y) / dd));
+}
+
+// Vn_j = (Vn_j - u') / (z_j - s); then column scaling by inv[c] (both FP32)
+__global__ void ip_update_kernel(float2* Vn, const float2* __restrict__ Up, int64_t n, int nu,
+                                 int N, const double2* __restrict__ z, double2 s) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per = n * nu;
+  if (t >= per * N) return;
+  const int j = (int)(t / per);
+  const int64_t e = t % per;
+  const float2 v = Vn[t], u = Up[e];
+  const double2 d = make_double2(z[j].x - s.x, z[j].y - s.y);
+  const double dd = d.x * d.x + d.y * d.y;
+  const double ar = v.x - u.x, ai = v.y - u.y;
+  Vn[t] = make_float2((float)((ar * d.x + ai * d.y) / dd), (float)((ai * d.x - ar * d.y) / dd));
+}
+
+// column sums of squares of the node-major block (fixed order): one block per column
+__global__ void ip_colnorm_kernel(const float2* __restrict__ Vn, int64_t n, int nu, int N,
+                                  double* __restrict__ out) {
+  __shared__ double red[256];
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (int j = 0; j < N; ++j) {
+    const float2* v = Vn + ((int64_t)j * nu + c) * n;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)v[i].x * v[i].x + (double)v[i].y * v[i].y;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = red[0];
+}
+
+__global__ void ip_scale_kernel(float2* Vn, float2* Up, int64_t n, int nu, int N,
+                                const double* __restrict__ nrm2) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per = n * nu;
+  if (t >= per * N) return;
+  const int c = (int)((t % per) / n);
+  const float f = (float)(1.0 / sqrt(fmax(nrm2[c], 1e-300)));
+  Vn[t].x *= f;
+  Vn[t].y *= f;
+  if (t < per) {
+    Up[t].x *= f;
+    Up[t].y *= f;
+  }
+}
+
+__global__ void f32_to_f64_kernel(const float2* __restrict__ a, int64_t n, int m, double2* b,
+                                  int64_t ldb) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * m) return;
+  const int c = (int)(t / n);
+  const int64_t i = t % n;
+  b[(int64_t)c * ldb + i] = make_double2(a[t].x, a[t].y);
+}
+
+// ---- refinement helpers (one eigenpair: vectors of length n) ----
+
+// [r r'] (FP64, n x 2 contiguous) -> FP32
+__global__ void to_f32_kernel(const double2* __restrict__ a, int64_t count, float2* b) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < count) b[t] = make_float2((float)a[t].x, (float)a[t].y);
+}
+
+// dots[c] = e^H s_c for the two solutions (FP64 sums in a fixed order)
+__global__ void dot2_kernel(const double2* __restrict__ e, const float2* __restrict__ S, int64_t n,
+                            double2* __restrict__ dots) {
+  __shared__ double2 red[256];
+  const int c = blockIdx.x;
+  const float2* sc = S + (int64_t)c * n;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double2 a = e[i];
+    const double2 b = make_double2(sc[i].x, sc[i].y);
+    acc.x += a.x * b.x + a.y * b.y;
+    acc.y += a.x * b.y - a.y * b.x;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      red[threadIdx.x].x += red[threadIdx.x + w].x;
+      red[threadIdx.x].y += red[threadIdx.x + w].y;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) dots[c] = red[0];
+}
+
+// x <- x - (s1 + dl s2)
+__global__ void refine_update_kernel(double2* x, const float2* __restrict__ S, int64_t n,
+                                     double2 dl) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float2 s1 = S[i], s2 = S[n + i];
+  x[i].x -= s1.x + (dl.x * s2.x - dl.y * s2.y);
+  x[i].y -= s1.y + (dl.x * s2.y + dl.y * s2.x);
+}
+
+// x <- x / alpha
+__global__ void scale_vec_kernel(double2* x, int64_t n, double2 alpha) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double d = alpha.x * alpha.x + alpha.y * alpha.y;
+  const double2 v = x[i];
+  x[i] = make_double2((v.x * alpha.x + v.y * alpha.y) / d, (v.y * alpha.x - v.x * alpha.y) / d);
+}
+
+// e^H x for one vector (one block)
+__global__ void dot1_kernel(const double2* __restrict__ e, const double2* __restrict__ x, int64_t n,
+                            double2* out) {
+  __shared__ double2 red[256];
+  double2 acc = make_double2(0.0, 0.0);
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    acc.x += e[i].x * x[i].x + e[i].y * x[i].y;
+    acc.y += e[i].x * x[i].y - e[i].y * x[i].x;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      red[threadIdx.x].x += red[threadIdx.x + w].x;
+      red[threadIdx.x].y += red[threadIdx.x + w].y;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+unsigned nblk(int64_t count, int t = 256) { return (unsigned)((count + t - 1) / t); }
+
+}  // namespace
+}  // namespace bem
+
+using namespace bem;
+
+extern "C" bem_status bem_inverse_power(bem_ctx* ctx, double* V_dev, int64_t ldv, int nu, int q,
+                                        double shift_re, double shift_im, void* stream) {
+  if (!ctx) return BEM_EINVAL;
+  if (ctx->geo.n == 0 || ctx->con.N == 0)
+    return fail(ctx, BEM_ESTATE, "bem_inverse_power: mesh and contour must be set");
+  const int64_t n = ctx->geo.n;
+  const int N = ctx->con.N;
+  if (!V_dev || nu < 1 || nu > kMaxNu || ldv < n || q < 0 || N > kMaxNodesSolve)
+    return fail(ctx, BEM_EINVAL, "bem_inverse_power: need V, 1 <= nu <= 256, ldv >= n, N <= 64");
+  if (q == 0) return BEM_OK;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  // coefficients c_j = w_j / (z_j - s)
+  std::vector<double> coef(2 * N);
+  NodeList nl;
+  nl.N = N;
+  for (int j = 0; j < N; ++j) {
+    const double zr = ctx->con.z_host[2 * j] - shift_re, zi = ctx->con.z_host[2 * j + 1] - shift_im;
+    const double wr = ctx->con.w_host[2 * j], wi = ctx->con.w_host[2 * j + 1];
+    const double d = zr * zr + zi * zi;
+    coef[2 * j] = (wr * zr + wi * zi) / d;
+    coef[2 * j + 1] = (wi * zr - wr * zi) / d;
+    nl.kr[j] = (float)ctx->con.z_host[2 * j];
+    nl.kmi[j] = (float)(-ctx->con.z_host[2 * j + 1]) * kLog2eF;
+    nl.cr[j] = (float)coef[2 * j];
+    nl.ci[j] = (float)coef[2 * j + 1];
+  }
+  // workspace: S (n^2), pivots, Vn (N n nu), U' (n nu), norms
+  size_t off = 0;
+  auto take = [&](size_t b) { const size_t o = off; off += (b + 255) / 256 * 256; return o; };
+  const size_t oS = take((size_t)n * n * sizeof(float2)), oP = take((size_t)n * sizeof(int)),
+               oV = take((size_t)N * n * nu * sizeof(float2)), oU = take((size_t)n * nu * sizeof(float2)),
+               oN = take((size_t)nu * sizeof(double));
+  bem_status st = ensure_scratch(ctx, off);
+  if (st != BEM_OK) return st;
+  st = ensure_self32(ctx, s);
+  if (st != BEM_OK) return st;
+  unsigned char* base = reinterpret_cast<unsigned char*>(ctx->d_scratch);
+  float2* S = reinterpret_cast<float2*>(base + oS);
+  int* piv = reinterpret_cast<int*>(base + oP);
+  float2* Vn = reinterpret_cast<float2*>(base + oV);
+  float2* Up = reinterpret_cast<float2*>(base + oU);
+  double* nrm = reinterpret_cast<double*>(base + oN);
+  st = assemble32(ctx, N, ctx->con.z_host, coef.data(), S, s);
+  if (st == BEM_OK) st = lu32(ctx, S, n, piv, s);
+  if (st != BEM_OK) return st;
+  const double2 sh = make_double2(shift_re, shift_im);
+  const double2* z = reinterpret_cast<const double2*>(ctx->con.z);
+  const int64_t total = (int64_t)N * n * nu;
+  ip_start_kernel<<<nblk(total), 256, 0, s>>>(reinterpret_cast<const double2*>(V_dev), ldv, n, nu,
+                                              N, z, sh, Vn);
+  ctx->launches++;
+  for (int step = 0; step < q; ++step) {
+    dim3 grid((unsigned)((n + kAR - 1) / kAR), (unsigned)((nu + kAV - 1) / kAV));
+    apply_nodes32_kernel<<<grid, 256, 0, s>>>(ctx->geo, nl,
+                                              reinterpret_cast<const float2*>(ctx->con.self32),
+                                              Vn, nu, Up);
+    ctx->launches++;
+    st = lu32_solve(ctx, S, piv, n, Up, nu, s);
+    if (st != BEM_OK) return st;
+    ip_update_kernel<<<nblk(total), 256, 0, s>>>(Vn, Up, n, nu, N, z, sh);
+    ip_colnorm_kernel<<<nu, 256, 0, s>>>(Vn, n, nu, N, nrm);
+    ip_scale_kernel<<<nblk(total), 256, 0, s>>>(Vn, Up, n, nu, N, nrm);
+    ctx->launches += 3;
+  }
+  f32_to_f64_kernel<<<nblk(n * nu), 256, 0, s>>>(Up, n, nu, reinterpret_cast<double2*>(V_dev), ldv);
+  ctx->launches++;
+  st = cuda_check(ctx, cudaGetLastError(), "bem_inverse_power");
+  if (st != BEM_OK) return st;
+  return take_status(ctx, s, "bem_inverse_power");
+}
+
+extern "C" bem_status bem_refine(bem_ctx* ctx, int m, double* lam_host, double* X_dev,
+                                 int64_t ldx, double tol, int maxit, double* relres_host,
+                                 int* iters_host, void* stream) {
+  if (!ctx) return BEM_EINVAL;
+  if (ctx->geo.n == 0) return fail(ctx, BEM_ESTATE, "bem_refine: no mesh set");
+  const int64_t n = ctx->geo.n;
+  if (m < 1 || !lam_host || !X_dev || ldx < n || !relres_host || !(tol > 0.0) || maxit < 1)
+    return fail(ctx, BEM_EINVAL, "bem_refine: bad arguments");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  size_t off = 0;
+  auto take = [&](size_t b) { const size_t o = off; off += (b + 255) / 256 * 256; return o; };
+  const size_t oA = take((size_t)n * n * sizeof(float2)), oP = take((size_t)n * sizeof(int)),
+               oR = take((size_t)2 * n * sizeof(double2)), oF = take((size_t)2 * n * sizeof(float2)),
+               oE = take((size_t)n * sizeof(double2)), oL = take(8 * sizeof(double2)),
+               oD = take(8 * sizeof(double2));
+  bem_status st = ensure_scratch(ctx, off);
+  if (st != BEM_OK) return st;
+  unsigned char* base = reinterpret_cast<unsigned char*>(ctx->d_scratch);
+  float2* A = reinterpret_cast<float2*>(base + oA);
+  int* piv = reinterpret_cast<int*>(base + oP);
+  double2* R = reinterpret_cast<double2*>(base + oR);
+  float2* F = reinterpret_cast<float2*>(base + oF);
+  double2* e = reinterpret_cast<double2*>(base + oE);
+  double2* dlam = reinterpret_cast<double2*>(base + oL);
+  double2* dots = reinterpret_cast<double2*>(base + oD);
+  double2 hd[2];
+  const double one[2] = {1.0, 0.0};
+  for (int c = 0; c < m; ++c) {
+    double2* x = reinterpret_cast<double2*>(X_dev) + (int64_t)c * ldx;
+    double lr = lam_host[2 * c], li = lam_host[2 * c + 1];
+    // e = x0, x normalised so that e^H x = 1
+    st = cuda_check(ctx, cudaMemcpyAsync(e, x, n * sizeof(double2), cudaMemcpyDeviceToDevice, s), "refine");
+    if (st != BEM_OK) return st;
+    dot1_kernel<<<1, 256, 0, s>>>(e, x, n, dots);
+    ctx->launches++;
+    st = cuda_check(ctx, cudaMemcpyAsync(hd, dots, sizeof(double2), cudaMemcpyDeviceToHost, s), "refine");
+    if (st == BEM_OK) st = cuda_check(ctx, cudaStreamSynchronize(s), "refine");
+    if (st != BEM_OK) return st;
+    scale_vec_kernel<<<nblk(n), 256, 0, s>>>(x, n, hd[0]);
+    ctx->launches++;
+    double sig_r = 0.0, sig_i = 0.0, dl_prev = INFINITY;
+    bool have_lu = false;
+    int it = 0;
+    for (; it < maxit; ++it) {
+      if (!have_lu) {
+        sig_r = lr;
+        sig_i = li;
+        const double k[2] = {sig_r, sig_i};
+        st = assemble32(ctx, 1, k, one, A, s);
+        if (st == BEM_OK) st = lu32(ctx, A, n, piv, s);
+        if (st != BEM_OK) return st;
+        have_lu = true;
+      }
+      const double lamv[2] = {lr, li};
+      st = cuda_check(ctx, cudaMemcpyAsync(dlam, lamv, sizeof(double2), cudaMemcpyHostToDevice, s), "refine");
+      if (st != BEM_OK) return st;
+      if (launch_apply_percol64(ctx, 1, reinterpret_cast<double*>(dlam), reinterpret_cast<double*>(x),
+                                n, reinterpret_cast<double*>(R), false, s) != cudaSuccess ||
+          launch_apply_percol64(ctx, 1, reinterpret_cast<double*>(dlam), reinterpret_cast<double*>(x),
+                                n, reinterpret_cast<double*>(R + n), true, s) != cudaSuccess)
+        return fail(ctx, BEM_ECUDA, "refine residual");
+      to_f32_kernel<<<nblk(2 * n), 256, 0, s>>>(R, 2 * n, F);
+      ctx->launches++;
+      st = lu32_solve(ctx, A, piv, n, F, 2, s);
+      if (st != BEM_OK) return st;
+      dot2_kernel<<<2, 256, 0, s>>>(e, F, n, dots);
+      ctx->launches++;
+      st = cuda_check(ctx, cudaMemcpyAsync(hd, dots, 2 * sizeof(double2), cudaMemcpyDeviceToHost, s), "refine");
+      if (st == BEM_OK) st = cuda_check(ctx, cudaStreamSynchronize(s), "refine");
+      if (st != BEM_OK) return st;
+      // dlambda = -(e^H s1) / (e^H s2)
+      const double dd = hd[1].x * hd[1].x + hd[1].y * hd[1].y;
+      if (!(dd > 0.0)) break;
+      const double dr = -(hd[0].x * hd[1].x + hd[0].y * hd[1].y) / dd;
+      const double di = -(hd[0].y * hd[1].x - hd[0].x * hd[1].y) / dd;
+      refine_update_kernel<<<nblk(n), 256, 0, s>>>(x, F, n, make_double2(dr, di));
+      dot1_kernel<<<1, 256, 0, s>>>(e, x, n, dots);
+      ctx->launches += 2;
+      st = cuda_check(ctx, cudaMemcpyAsync(hd, dots, sizeof(double2), cudaMemcpyDeviceToHost, s), "refine");
+      if (st == BEM_OK) st = cuda_check(ctx, cudaStreamSynchronize(s), "refine");
+      if (st != BEM_OK) return st;
+      scale_vec_kernel<<<nblk(n), 256, 0, s>>>(x, n, hd[0]);
+      ctx->launches++;
+      lr += dr;
+      li += di;
+      const double step = hypot(dr, di), lam_abs = hypot(lr, li);
+      if (step <= tol * lam_abs) {
+        ++it;
+        break;
+      }
+      // stalled: refactor at the current lambda
+      if (step > 0.1 * dl_prev) have_lu = false;
+      dl_prev = step;
+    }
+    lam_host[2 * c] = lr;
+    lam_host[2 * c + 1] = li;
+    if (iters_host) iters_host[c] = it;
+  }
+  // final FP64 residuals
+  return bem_residual(ctx, m, lam_host, X_dev, ldx, nullptr, relres_host, stream);
+}
+
+extern "C" bem_status bem_solve(bem_ctx* ctx, const double* V0_dev, int64_t ldv, int nu, int q,
+                                int precision, double tol, int kmax, double* lam_host,
+                                double* X_dev, int64_t ldx, int* k_found, double* relres_host,
+                                void* stream) {
+  if (!ctx) return BEM_EINVAL;
+  if (ctx->geo.n == 0 || ctx->con.N == 0)
+    return fail(ctx, BEM_ESTATE, "bem_solve: mesh and contour must be set");
+  const int64_t n = ctx->geo.n;
+  const int N = ctx->con.N;
+  if (!V0_dev || nu < 1 || nu > kMaxNu || nu > n || ldv < n || q < 0 || kmax < 1 ||
+      !lam_host || !X_dev || ldx < n || !k_found || !relres_host || !(tol > 0.0))
+    return fail(ctx, BEM_EINVAL, "bem_solve: bad arguments");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const Contour& con = ctx->con;
+  const int p = std::min<int64_t>(std::min<int64_t>((int64_t)N * nu, 256), std::max(2 * nu, 32));
+  // solve-owned buffers: basis V (n nu), Bhat (N nu^2), Y (nu p), Ritz vectors (n p)
+  const size_t bV = (size_t)n * nu * 16, bB = (size_t)N * nu * nu * 16, bY = (size_t)nu * p * 16,
+               bX = (size_t)n * p * 16;
+  const size_t need = bV + bB + bY + bX + 4 * 256;
+  if (need > ctx->solve_bytes) {
+    cudaFree(ctx->d_solve);
+    ctx->d_solve = nullptr;
+    ctx->solve_bytes = 0;
+    if (cudaMalloc(&ctx->d_solve, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, BEM_ENOMEM, "bem_solve: buffer allocation failed");
+    }
+    ctx->solve_bytes = need;
+  }
+  unsigned char* base = reinterpret_cast<unsigned char*>(ctx->d_solve);
+  double* V = reinterpret_cast<double*>(base);
+  double* Bh = reinterpret_cast<double*>(base + (bV + 255) / 256 * 256);
+  double* Y = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(Bh) + (bB + 255) / 256 * 256);
+  double* Xc = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(Y) + (bY + 255) / 256 * 256);
+  bem_status st = cuda_check(ctx, cudaMemcpy2DAsync(V, n * 16, V0_dev, ldv * 16, n * 16, nu,
+                                                    cudaMemcpyDeviceToDevice, s), "bem_solve copy");
+  if (st != BEM_OK) return st;
+  // 1. basis: q inverse power steps about the contour's centre (Algorithm 1), then
+  //    CholeskyQR2 (orthonormal basis for the Rayleigh-Ritz projection)
+  st = bem_inverse_power(ctx, V, n, nu, q, con.c_re, con.c_im, stream);
+  if (st == BEM_OK) st = bem_cholqr2(ctx, V, n, n, nu, nullptr, stream);
+  // 2. projection and the reduced problem
+  if (st == BEM_OK) st = bem_project(ctx, V, n, nu, Bh, nullptr, precision, stream);
+  if (st != BEM_OK) return st;
+  std::vector<double> lam(2 * p), res(p);
+  int iters = 0;
+  // shift: the centre, nudged off the real axis so that it is not itself an eigenvalue of
+  // a real-symmetric-looking problem
+  const double sh_r = con.c_re, sh_i = con.c_im + 1e-3 * std::min(con.a, con.b);
+  st = bem_solve_reduced(ctx, Bh, nu, sh_r, sh_i, p, 300, 1e-11, lam.data(), Y, res.data(), &iters,
+                         stream);
+  if (st != BEM_OK) return st;
+  // 3. candidates: inside the contour, small reduced residual, nearest the centre first
+  std::vector<int> cand;
+  for (int i = 0; i < p; ++i) {
+    const double xr = (lam[2 * i] - con.c_re) / con.a, xi = (lam[2 * i + 1] - con.c_im) / con.b;
+    if (xr * xr + xi * xi < 1.0 && res[i] <= 1e-6) cand.push_back(i);
+  }
+  std::sort(cand.begin(), cand.end(), [&](int a, int b) {
+    return hypot(lam[2 * a] - con.c_re, lam[2 * a + 1] - con.c_im) <
+           hypot(lam[2 * b] - con.c_re, lam[2 * b + 1] - con.c_im);
+  });
+  const int k = std::min<int>((int)cand.size(), std::min(kmax, p));
+  *k_found = 0;
+  if (k == 0) return BEM_OK;
+  // gather the selected y columns (device-side copies) and form x = V y
+  for (int t = 0; t < k; ++t) {
+    st = cuda_check(ctx, cudaMemcpyAsync(Xc + (size_t)2 * nu * t, Y + (size_t)2 * nu * cand[t],
+                                         nu * 16, cudaMemcpyDeviceToDevice, s), "bem_solve gather");
+    if (st != BEM_OK) return st;
+  }
+  st = bem_ritz_vectors(ctx, V, n, nu, Xc, k, X_dev, ldx, stream);
+  if (st != BEM_OK) return st;
+  std::vector<double> lk(2 * k), rr(k);
+  for (int t = 0; t < k; ++t) {
+    lk[2 * t] = lam[2 * cand[t]];
+    lk[2 * t + 1] = lam[2 * cand[t] + 1];
+  }
+  // 4. FP64 refinement of every candidate against A(k) itself
+  st = bem_refine(ctx, k, lk.data(), X_dev, ldx, tol, 40, rr.data(), nullptr, stream);
+  if (st != BEM_OK) return st;
+  for (int t = 0; t < k; ++t) {
+    lam_host[2 * t] = lk[2 * t];
+    lam_host[2 * t + 1] = lk[2 * t + 1];
+    relres_host[t] = rr[t];
+  }
+  *k_found = k;
+  return BEM_OK;
+}
