@@ -195,7 +195,10 @@ bem_status bem_refine(bem_ctx* ctx, int m, double* lam_host, double* X_dev, int6
 /*
  * The whole method (Algorithm 3 with one outer pass) for the context's mesh and contour:
  * basis V0 (n x nu, ld ldv; not modified) -> q inverse power steps about the contour's
- * centre -> CholeskyQR2 -> projection (precision BEM_PREC_FP64 or BEM_PREC_MIXED) ->
+ * centre, taken on the circle of radius 2 max(a, b) about that centre (the Cauchy
+ * linearisation has eigenvalues clustered at its nodes, which must stay farther from the
+ * shift than the wanted eigenvalues) -> CholeskyQR2 -> projection on the contour itself
+ * (precision BEM_PREC_FP64 or BEM_PREC_MIXED) ->
  * reduced linearised eigenproblem -> Ritz pairs inside the contour with small reduced
  * residual, nearest the centre first, at most kmax -> FP64 refinement (tolerance tol).
  *   lam_host    2*kmax doubles: eigenvalues found

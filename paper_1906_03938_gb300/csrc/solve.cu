@@ -495,7 +495,7 @@ extern "C" bem_status bem_solve(bem_ctx* ctx, const double* V0_dev, int64_t ldv,
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   const Contour& con = ctx->con;
-  const int p = std::min<int64_t>(std::min<int64_t>((int64_t)N * nu, 256), std::max(2 * nu, 32));
+  const int p = (int)std::min<int64_t>(std::min<int64_t>((int64_t)N * nu, 256), std::max(2 * nu, 32));
   // solve-owned buffers: basis V (n nu), Bhat (N nu^2), Y (nu p), Ritz vectors (n p)
   const size_t bV = (size_t)n * nu * 16, bB = (size_t)N * nu * nu * 16, bY = (size_t)nu * p * 16,
                bX = (size_t)n * p * 16;
@@ -519,46 +519,74 @@ extern "C" bem_status bem_solve(bem_ctx* ctx, const double* V0_dev, int64_t ldv,
                                                     cudaMemcpyDeviceToDevice, s), "bem_solve copy");
   if (st != BEM_OK) return st;
   // 1. basis: q inverse power steps about the contour's centre (Algorithm 1), then
-  //    CholeskyQR2 (orthonormal basis for the Rayleigh-Ritz projection)
-  st = bem_inverse_power(ctx, V, n, nu, q, con.c_re, con.c_im, stream);
+  //    CholeskyQR2 (orthonormal basis for the Rayleigh-Ritz projection). The Cauchy
+  //    linearisation has n eigenvalues clustered at every node; on a flat ellipse the
+  //    nodes nearest the centre are closer to the shift than the wanted eigenvalues and
+  //    would capture the iteration, so the basis is built on the circle of radius
+  //    2 max(a, b) about the same centre (nodes at least twice as far as anything inside
+  //    the contour), and the contour is restored for the projection.
+  const int kind0 = con.kind, N0 = con.N;
+  const double c_re = con.c_re, c_im = con.c_im, a0 = con.a, b0 = con.b;
+  const double rb = 2.0 * std::max(a0, b0);
+  st = bem_set_contour(ctx, BEM_CONTOUR_CIRCLE, c_re, c_im, rb, rb, N0, nullptr, nullptr, stream);
+  if (st == BEM_OK) st = bem_inverse_power(ctx, V, n, nu, q, c_re, c_im, stream);
+  const bem_status st_restore =
+      bem_set_contour(ctx, kind0, c_re, c_im, a0, b0, N0, nullptr, nullptr, stream);
+  if (st == BEM_OK) st = st_restore;
   if (st == BEM_OK) st = bem_cholqr2(ctx, V, n, n, nu, nullptr, stream);
   // 2. projection and the reduced problem
   if (st == BEM_OK) st = bem_project(ctx, V, n, nu, Bh, nullptr, precision, stream);
   if (st != BEM_OK) return st;
-  std::vector<double> lam(2 * p), res(p);
+  // 3. reduced problem: shift-and-invert at K shifts spread along the major axis
+  //    (K = round(a/b); one shift, the centre, for a circle). The reduced linearisation
+  //    has nu eigenvalues clustered at each node; a shift only sees the eigenvalues that
+  //    are nearer to it than the nearest node cluster, so on a flat ellipse one shift at
+  //    the centre would return node clusters instead of the eigenvalues inside. Each
+  //    shift keeps the converged Ritz pairs inside the contour that are nearer to it
+  //    than to any other shift (every eigenvalue is reported once).
+  const double amaj = std::max(con.a, con.b), amin = std::min(con.a, con.b);
+  const bool along_re = con.a >= con.b;
+  const int K = std::max(1, std::min(16, (int)lround(amaj / amin)));
+  std::vector<double> sr(K), si(K);
+  for (int kk = 0; kk < K; ++kk) {
+    const double x = -1.0 + (2.0 * kk + 1.0) / K;
+    sr[kk] = con.c_re + (along_re ? amaj * x : 0.0);
+    si[kk] = con.c_im + (along_re ? 0.0 : amaj * x) + 1e-3 * amin;   // off the real axis
+  }
+  const int pk = std::min(p, 32);
+  std::vector<double> lam(2 * pk), res(pk), lk, ysel;
+  std::vector<int> cand_shift;
   int iters = 0;
-  // shift: the centre, nudged off the real axis so that it is not itself an eigenvalue of
-  // a real-symmetric-looking problem
-  const double sh_r = con.c_re, sh_i = con.c_im + 1e-3 * std::min(con.a, con.b);
-  st = bem_solve_reduced(ctx, Bh, nu, sh_r, sh_i, p, 300, 1e-11, lam.data(), Y, res.data(), &iters,
-                         stream);
-  if (st != BEM_OK) return st;
-  // 3. candidates: inside the contour, small reduced residual, nearest the centre first
-  std::vector<int> cand;
-  for (int i = 0; i < p; ++i) {
-    const double xr = (lam[2 * i] - con.c_re) / con.a, xi = (lam[2 * i + 1] - con.c_im) / con.b;
-    if (xr * xr + xi * xi < 1.0 && res[i] <= 1e-6) cand.push_back(i);
-  }
-  std::sort(cand.begin(), cand.end(), [&](int a, int b) {
-    return hypot(lam[2 * a] - con.c_re, lam[2 * a + 1] - con.c_im) <
-           hypot(lam[2 * b] - con.c_re, lam[2 * b + 1] - con.c_im);
-  });
-  const int k = std::min<int>((int)cand.size(), std::min(kmax, p));
-  *k_found = 0;
-  if (k == 0) return BEM_OK;
-  // gather the selected y columns (device-side copies) and form x = V y
-  for (int t = 0; t < k; ++t) {
-    st = cuda_check(ctx, cudaMemcpyAsync(Xc + (size_t)2 * nu * t, Y + (size_t)2 * nu * cand[t],
-                                         nu * 16, cudaMemcpyDeviceToDevice, s), "bem_solve gather");
+  int nsel = 0;
+  for (int kk = 0; kk < K; ++kk) {
+    st = bem_solve_reduced(ctx, Bh, nu, sr[kk], si[kk], pk, 300, 1e-11, lam.data(), Y, res.data(),
+                           &iters, stream);
     if (st != BEM_OK) return st;
+    for (int i = 0; i < pk; ++i) {
+      const double lr = lam[2 * i], li = lam[2 * i + 1];
+      const double xr = (lr - con.c_re) / con.a, xi = (li - con.c_im) / con.b;
+      if (!(xr * xr + xi * xi < 1.0) || !(res[i] <= 1e-6)) continue;
+      int owner = 0;
+      double best = INFINITY;
+      for (int k2 = 0; k2 < K; ++k2) {
+        const double d = hypot(lr - sr[k2], li - si[k2]);
+        if (d < best) { best = d; owner = k2; }
+      }
+      if (owner != kk || nsel >= std::min(kmax, p)) continue;
+      st = cuda_check(ctx, cudaMemcpyAsync(Xc + (size_t)2 * nu * nsel, Y + (size_t)2 * nu * i,
+                                           nu * 16, cudaMemcpyDeviceToDevice, s), "bem_solve gather");
+      if (st != BEM_OK) return st;
+      lk.push_back(lr);
+      lk.push_back(li);
+      ++nsel;
+    }
   }
+  const int k = nsel;
+  *k_found = 0;
+  if (k == 0) return take_status(ctx, s, "bem_solve");
   st = bem_ritz_vectors(ctx, V, n, nu, Xc, k, X_dev, ldx, stream);
   if (st != BEM_OK) return st;
-  std::vector<double> lk(2 * k), rr(k);
-  for (int t = 0; t < k; ++t) {
-    lk[2 * t] = lam[2 * cand[t]];
-    lk[2 * t + 1] = lam[2 * cand[t] + 1];
-  }
+  std::vector<double> rr(k);
   // 4. FP64 refinement of every candidate against A(k) itself
   st = bem_refine(ctx, k, lk.data(), X_dev, ldx, tol, 40, rr.data(), nullptr, stream);
   if (st != BEM_OK) return st;

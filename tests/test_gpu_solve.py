@@ -125,3 +125,20 @@ def test_solve_sphere320_against_golden(bem, precision):
     lam, X, rel = ctx.solve(V0, q=10, precision=prec, tol=1e-14)
     _check_against_golden("sphere320", lam, X, rel, 1e-10)
     ctx.close()
+
+
+def test_solve_cube3072_mixed_against_golden(bem):
+    """Full bench workload, mixed projection + FP64 refinement: the three discrete
+    eigenvalues inside the ellipse (5.44004, and the split pair 7.69320 / 7.69325 x2)."""
+    import time
+    prob = synth.workload("cube3072").problems[0]
+    mesh, spec = prob.mesh(), prob.contour
+    ctx = bem.Context(0)
+    ctx.set_mesh(mesh.xyz, mesh.tri)
+    ctx.set_contour(spec.kind, spec.centre, spec.a, spec.b, prob.N)
+    V0 = bem.fortran(torch.from_numpy(synth.complex_gaussian(mesh.n, prob.nu, prob.seed)).to("cuda:0"))
+    t0 = time.perf_counter()
+    lam, X, rel = ctx.solve(V0, q=10, precision=bem.PREC_MIXED, tol=1e-14)
+    print("cube3072 solve seconds", time.perf_counter() - t0)
+    _check_against_golden("cube3072", lam, X, rel, 1e-10)
+    ctx.close()
