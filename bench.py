@@ -41,6 +41,7 @@ def parse():
     p.add_argument("--plain-steps", type=int, default=2,
                    help="steps of the plain FP64 path timed for the speedup (0: skip)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-eig-check", action="store_true")
     return p.parse_args()
 
 
@@ -307,6 +308,37 @@ def run_ours(args):
                  "ms_per_step": statistics.mean(ms), "steps": len(ms),
                  "speedup_of_mixed": statistics.mean(ms) / (1e3 * t_total / args.steps)}
 
+    # accuracy qualifier of the metric: the eigenvalues inside the contour from this
+    # projection (Algorithm 1 basis, reduced solve, FP64 refinement), untimed, against the
+    # oracle's discrete eigenvalues stored under tests/golden
+    eig = None
+    if not args.no_eig_check:
+        t0 = time.perf_counter()
+        lam, X, rel = ctx.solve(V_res, q=10, precision=prec, tol=1e-14)
+        torch.cuda.synchronize()
+        t_solve = time.perf_counter() - t0
+        gold = []
+        for line in open(os.path.join(ROOT, "tests", "golden", f"eigs_{WORKLOAD}.txt")):
+            if not line.startswith("#"):
+                re_, im_, mult, ins = line.split()
+                if int(ins):
+                    gold.append((complex(float(re_), float(im_)), int(mult)))
+        errs = [float(np.min(np.abs(lam - g)) / abs(g)) if len(lam) else float("inf") for g, _ in gold]
+        Xh = X.cpu().numpy()
+        mult_ok = True
+        for g, m in gold:
+            near = np.where(np.abs(lam - g) <= 1e-8 * abs(g))[0]
+            if len(near) == 0:
+                mult_ok = False
+                continue
+            sv = np.linalg.svd(Xh[:, near] / np.linalg.norm(Xh[:, near], axis=0), compute_uv=False)
+            mult_ok = mult_ok and int(np.sum(sv > 1e-6)) >= m
+        eig = {"eig_rel_err_max": max(errs) if errs else None, "relres_max": float(np.max(rel)) if len(rel) else None,
+               "found": [[l.real, l.imag] for l in lam], "expected": [[g.real, g.imag, m] for g, m in gold],
+               "multiplicities_ok": mult_ok, "solve_s": t_solve,
+               "pipeline": "Algorithm 1 (q=10) + CholeskyQR2 + projection (" + args.precision +
+                           ") + reduced solve + FP64 refinement"}
+
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = oracle_sample(prob, mesh, V)
@@ -329,6 +361,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
         "plain_fp64": plain,
+        "eig_check": eig,
     }
     print(json.dumps(line), flush=True)
     ctx.close()

@@ -66,7 +66,7 @@ bem_status take_status(bem_ctx* ctx, cudaStream_t stream, const char* where) {
 
 static void free_geometry(Geometry& g) {
   cudaFree(g.xyz); cudaFree(g.tri); cudaFree(g.cx); cudaFree(g.qp); cudaFree(g.qw);
-  cudaFree(g.cx32); cudaFree(g.qp32); cudaFree(g.qw32); cudaFree(g.edge32);
+  cudaFree(g.cx32); cudaFree(g.qp32); cudaFree(g.qw32); cudaFree(g.edge32); cudaFree(g.pack32);
   g = Geometry();
 }
 
@@ -173,7 +173,8 @@ bem_status bem_set_mesh(bem_ctx* ctx, int64_t nv, const double* xyz_host, int64_
               cudaMalloc(&g.cx32, 3 * nt * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&g.qp32, 21 * nt * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&g.qw32, 7 * nt * sizeof(float)) == cudaSuccess &&
-              cudaMalloc(&g.edge32, 9 * nt * sizeof(float)) == cudaSuccess;
+              cudaMalloc(&g.edge32, 9 * nt * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&g.pack32, (nt + 15) / 16 * 16 * 64 * sizeof(float)) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       free_geometry(g);

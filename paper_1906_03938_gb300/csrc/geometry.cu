@@ -41,6 +41,11 @@ Rule7 make_rule7() {
 
 __global__ void geometry_kernel(Geometry g, Rule7 rule, int* status) {
   const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g.pack32 && l >= g.n && l < (g.n + 15) / 16 * 16) {
+    // padding panels of the packed array: finite placeholders, zero weights
+    for (int t = 0; t < 64; ++t) g.pack32[l * 64 + t] = (t < 28 && t % 4 != 3) ? 1.0f : 0.0f;
+    return;
+  }
   if (l >= g.n) return;
   const int32_t i0 = g.tri[3 * l], i1 = g.tri[3 * l + 1], i2 = g.tri[3 * l + 2];
   if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= g.nv || i1 >= g.nv || i2 >= g.nv) {
@@ -82,6 +87,18 @@ __global__ void geometry_kernel(Geometry g, Rule7 rule, int* status) {
     const double w = rule.w[q] * area / (4.0 * kPiD);
     g.qw[q * n + l] = w;
     g.qw32[q * n + l] = (float)w;
+    if (g.pack32) {
+      float* pk = g.pack32 + (int64_t)l * 64;
+      for (int c = 0; c < 3; ++c) {
+        const double pt = rule.bary[q][0] * v[0][c] + rule.bary[q][1] * v[1][c] +
+                          rule.bary[q][2] * v[2][c];
+        const float hi = (float)pt;
+        pk[4 * q + c] = hi;
+        pk[28 + 4 * q + c] = (float)(pt - (double)hi);
+      }
+      pk[4 * q + 3] = (float)w;
+      pk[28 + 4 * q + 3] = 0.f;
+    }
   }
   if (g.edge32) {
     // node-independent edge data of the self term, once per panel
@@ -155,7 +172,7 @@ __global__ void self_term32_kernel(Geometry g, int N, const double* z, GL16 gl, 
 
 cudaError_t launch_geometry(bem_ctx* ctx, cudaStream_t s) {
   static const Rule7 rule = make_rule7();
-  const int64_t n = ctx->geo.n;
+  const int64_t n = (ctx->geo.n + 15) / 16 * 16;   // padding panels of the packed array too
   geometry_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctx->geo, rule, ctx->d_status);
   ctx->launches++;
   return cudaGetLastError();

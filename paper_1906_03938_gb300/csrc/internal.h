@@ -45,6 +45,9 @@ struct Geometry {
   float* qw32 = nullptr;
   float* edge32 = nullptr; // 9 n, optional: self-term edge data (d, u_p, u_q per edge) at
                            // (3 e + f) * n + l, for the FP32 self terms of the mixed path
+  float* pack32 = nullptr; // optional, 64 floats per panel, rows padded to a multiple of 16
+                           // panels: 7 x (x_hi, y_hi, z_hi, w) then 7 x (x_lo, y_lo, z_lo, 0)
+                           // (hi + lo = the FP64 quadrature point; w = W_lq / 4 pi)
 };
 
 struct Contour {

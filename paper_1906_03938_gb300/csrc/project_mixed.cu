@@ -65,6 +65,7 @@ struct MixedParams {
   const double* qp;   // FP64 quadrature points, q-major SoA
   const double* qw;   // FP64 weights / 4 pi
   const float2* self32;   // FP32 complex self terms, node-major
+  const float* pack32;    // packed FP32 hi/lo panel geometry (64 floats per panel)
   const double* z;    // FP64 complex nodes
   const __nv_bfloat16* Bp;   // prepared basis planes, tile-native
   float* Yp;          // FP32 partial products [S][N][2 nup][n_pad]
@@ -72,9 +73,10 @@ struct MixedParams {
 };
 
 struct SmemLayout {
-  uint32_t a_off, b_off, row_off, col_off, self_off, bar_off, misc_off, total;
+  uint32_t a_off, b_off, graw_off, row_off, col_off, self_off, bar_off, misc_off, total;
   uint32_t a_stage_bytes, b_stage_bytes;
 };
+constexpr uint32_t kGeoBlockBytes = kBK * 64 * 4;   // packed geometry of one K-block
 
 __host__ __device__ inline SmemLayout smem_layout(int G, int nup) {
   SmemLayout L;
@@ -82,11 +84,12 @@ __host__ __device__ inline SmemLayout smem_layout(int G, int nup) {
   L.b_stage_bytes = (uint32_t)256 * nup;     // 4 planes x 2 nup rows x 16 k x 2 B
   L.a_off = 0;
   L.b_off = L.a_off + kStages * L.a_stage_bytes;
-  L.row_off = L.b_off + kStages * L.b_stage_bytes;
+  L.graw_off = L.b_off + kStages * L.b_stage_bytes;    // per stage: packed geometry copy
+  L.row_off = L.graw_off + kStages * kGeoBlockBytes;
   L.col_off = L.row_off + kBM * 4 * 4;           // 128 rows x (x, y, z, valid)
-  L.self_off = L.col_off + kStages * kBK * 28 * 4;   // per stage 16 x (21 coords + 7 weights)
+  L.self_off = L.col_off + kStages * kBK * 7 * 16;   // per stage 16 x 7 float4 (x, y, z, w)
   L.bar_off = L.self_off + kStages * kBK * kMaxG * 8;  // per stage 16 x G complex self terms
-  L.misc_off = L.bar_off + 10 * 8;               // 9 mbarriers (+1 pad)
+  L.misc_off = L.bar_off + 12 * 8;               // 11 mbarriers (+1 pad)
   L.total = L.misc_off + 16;                     // tmem slot, abort flag
   return L;
 }
@@ -136,7 +139,8 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
   unsigned char* sA = smem + L.a_off;
   unsigned char* sB = smem + L.b_off;
   float4* sRow = reinterpret_cast<float4*>(smem + L.row_off);
-  float* sColAll = reinterpret_cast<float*>(smem + L.col_off);      // [stage][16][28]
+  const float* sGraw = reinterpret_cast<const float*>(smem + L.graw_off);  // [stage][16][64]
+  float4* sColAll = reinterpret_cast<float4*>(smem + L.col_off);    // [stage][16][7]
   float2* sSelfAll = reinterpret_cast<float2*>(smem + L.self_off);  // [stage][16][kMaxG]
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
   uint64_t* afull = bars;        // [2] evaluation warps -> MMA
@@ -144,6 +148,7 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
   uint64_t* empty = bars + 4;    // [2] MMA done with the stage
   uint64_t* accfull = bars + 6;  // accumulators final
   uint64_t* gfull = bars + 7;    // [2] column geometry / self terms staged -> evaluation
+  uint64_t* gready = bars + 9;   // [2] packed geometry bulk copy landed -> producer
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.misc_off);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.misc_off + 4);
 
@@ -172,6 +177,7 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
       mbar_init(&bfull[s], 1);
       mbar_init(&empty[s], 1);
       mbar_init(&gfull[s], 32);
+      mbar_init(&gready[s], 1);
     }
     mbar_init(accfull, 1);
     *abort_flag = 0;
@@ -191,6 +197,8 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
     // origin of this tile's relative coordinates: its first centroid
     const int64_t i_org = row0 < p.n ? row0 : p.n - 1;
     const double ox = p.cx[i_org], oy = p.cx[p.n + i_org], oz = p.cx[2 * p.n + i_org];
+    const float oxh = (float)ox, oyh = (float)oy, ozh = (float)oz;
+    const float oxl = (float)(ox - oxh), oyl = (float)(oy - oyh), ozl = (float)(oz - ozh);
     for (int r = lane; r < kBM; r += 32) {
       const int64_t i = row0 + r;
       float4 v = make_float4(2.0f, 2.0f, 2.0f, 0.f);   // padding rows: zeroed after evaluation
@@ -214,24 +222,21 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
                  reinterpret_cast<const unsigned char*>(p.Bp) +
                      (size_t)kb * L.b_stage_bytes,
                  L.b_stage_bytes, &bfull[s]);
+        mbar_arrive_expect_tx(&gready[s], kGeoBlockBytes);
+        bulk_g2s(smem + L.graw_off + s * kGeoBlockBytes, p.pack32 + (size_t)kb * kBK * 64,
+                 kGeoBlockBytes, &gready[s]);
       }
       ++issued;
-      float* sCol = sColAll + s * (kBK * 28);
-      for (int x = lane; x < kBK * 28; x += 32) {
-        const int k = x / 28, f = x % 28;
-        const int64_t l = (int64_t)kb * kBK + k;
-        // padding columns: finite placeholders; their entries are zeroed after evaluation
-        float val = f < 21 ? 1.0f : 0.f;
-        if (l < p.n) {
-          if (f < 21) {
-            const int c = f / 7, q = f % 7;
-            const double o = c == 0 ? ox : (c == 1 ? oy : oz);
-            val = (float)(p.qp[(7 * c + q) * p.n + l] - o);
-          } else {
-            val = (float)p.qw[(f - 21) * p.n + l];
-          }
-        }
-        sCol[k * 28 + f] = val;
+      // tile-relative FP32 coordinates from the hi/lo pairs: (y_hi - o_hi) + (y_lo - o_lo)
+      if (!wait_or_abort(&gready[s], par, abort_flag, p.status)) break;
+      const float* graw = sGraw + s * (kBK * 64);
+      float4* sCol = sColAll + s * (kBK * 7);
+      for (int x = lane; x < kBK * 7; x += 32) {
+        const int k = x / 7, q = x % 7;
+        const float4 hi = *reinterpret_cast<const float4*>(graw + k * 64 + 4 * q);
+        const float4 lo = *reinterpret_cast<const float4*>(graw + k * 64 + 28 + 4 * q);
+        sCol[x] = make_float4((hi.x - oxh) + (lo.x - oxl), (hi.y - oyh) + (lo.y - oyl),
+                              (hi.z - ozh) + (lo.z - ozl), hi.w);
       }
       float2* sSelf = sSelfAll + s * (kBK * kMaxG);
       for (int x = lane; x < kBK * kMaxG; x += 32) {
@@ -246,8 +251,10 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
     }
     if (lane == 0 && *abort_flag) {
       // let copies in flight land before the block exits (bounded)
-      for (int it = max(0, issued - kStages); it < issued; ++it)
+      for (int it = max(0, issued - kStages); it < issued; ++it) {
         mbar_wait(&bfull[it % kStages], (it / kStages) & 1, kWaitLimit);
+        mbar_wait(&gready[it % kStages], (it / kStages) & 1, kWaitLimit);
+      }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -301,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
       const uint32_t par = (it / kStages) & 1;
       const int kb = kb0 + it;
       const bool ready = wait_or_abort(&gfull[s], par, abort_flag, p.status);
-      const float* sCol = sColAll + s * (kBK * 28);
+      const float4* sCol = sColAll + s * (kBK * 7);
       const float2* sSelf = sSelfAll + s * (kBK * kMaxG);
       unsigned char* a_stage = sA + s * L.a_stage_bytes;
       const float4 xr = sRow[row];
@@ -312,14 +319,15 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
         float rr[2][7], am[2][7];
 #pragma unroll
         for (int d = 0; d < 2; ++d) {
-          const float* col = sCol + (k0 + d) * 28;
+          const float4* col = sCol + (k0 + d) * 7;
 #pragma unroll
           for (int q = 0; q < 7; ++q) {
-            const float dx = xr.x - col[q], dy = xr.y - col[7 + q], dz = xr.z - col[14 + q];
+            const float4 y = col[q];
+            const float dx = xr.x - y.x, dy = xr.y - y.y, dz = xr.z - y.z;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const float rs = rsqrtf_mufu(r2);
             rr[d][q] = r2 * rs;
-            am[d][q] = col[21 + q] * rs;
+            am[d][q] = y.w * rs;
           }
         }
         const uint32_t off = e * 256 + kg * 128 + r8 * 16 + kp * 4;
@@ -650,6 +658,7 @@ bem_status project_mixed(bem_ctx* ctx, const double* V, int64_t ldv, int nu, dou
   p.qp = ctx->geo.qp;
   p.qw = ctx->geo.qw;
   p.self32 = reinterpret_cast<const float2*>(ctx->con.self32);
+  p.pack32 = ctx->geo.pack32;
   p.z = ctx->con.z;
   p.status = ctx->d_status;
 
