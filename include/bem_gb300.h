@@ -110,7 +110,10 @@ bem_status bem_project(bem_ctx* ctx, const double* V_dev, int64_t ldv, int nu,
  * projection, Section 4, Example 1): G = V^H V, R1 = chol(G), V <- V R1^{-1}, repeated
  * once; on return V (n x nu, column-major, leading dimension ldv) has orthonormal
  * columns and, if R_dev is not NULL, R_dev (nu x nu, column-major) holds R = R2 R1 with
- * V_in = V_out R. FP64 throughout. Fails with BEM_EKERNEL if a Gram matrix is not
+ * V_in = V_out R. The second pass is FP64 throughout and sets the final orthogonality;
+ * when R_dev is NULL and nu <= 128 the first pass (whose only job is to make V well
+ * conditioned) runs its Gram matrix, Cholesky factor and triangular inverse in FP32 and
+ * applies the inverse to V in FP64. Fails with BEM_EKERNEL if a Gram matrix is not
  * numerically positive definite (rank-deficient V). Synchronises the stream.
  */
 bem_status bem_cholqr2(bem_ctx* ctx, double* V_dev, int64_t n, int64_t ldv, int nu,

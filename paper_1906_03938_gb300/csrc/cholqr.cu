@@ -20,7 +20,8 @@ namespace {
 // With `deficient` non-null, a collapsed pivot does not fail: its column of R becomes the
 // unit vector (the column of V is then replaced by the caller) and deficient[k] = 1.
 __global__ void __launch_bounds__(1024) cholesky_kernel(double2* Gg, int nu, int* status,
-                                                        int* deficient) {
+                                                        int* deficient, const int* gate) {
+  if (gate && *gate == 0) return;   // gated pass not needed
   extern __shared__ double2 sG[];
   __shared__ double rkk, dmax;
   const bool staged = nu <= 64;
@@ -112,7 +113,8 @@ constexpr int kGT = 32;   // Gram output tile
 // Partial Gram matrices: block (tile, r) sums conj(V[i][a]) V[i][b] over its row range.
 __global__ void __launch_bounds__(256)
 gram_partial_kernel(const double2* __restrict__ V, int64_t ldv, int64_t n, int nu,
-                    int64_t rows_per_part, double2* __restrict__ part) {
+                    int64_t rows_per_part, double2* __restrict__ part, const int* gate) {
+  if (gate && *gate == 0) return;
   __shared__ double2 sX[kGT][kGT + 1];
   __shared__ double2 sY[kGT][kGT + 1];
   const int tiles_a = (nu + kGT - 1) / kGT;
@@ -158,7 +160,8 @@ gram_partial_kernel(const double2* __restrict__ V, int64_t ldv, int64_t n, int n
 
 // G = sum of the partials in part order (deterministic).
 __global__ void sum_parts_kernel(const double2* __restrict__ part, int parts, int64_t count,
-                                 double2* __restrict__ G) {
+                                 double2* __restrict__ G, const int* gate) {
+  if (gate && *gate == 0) return;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= count) return;
   double2 s = make_double2(0.0, 0.0);
@@ -175,7 +178,9 @@ __global__ void sum_parts_kernel(const double2* __restrict__ part, int parts, in
 // block's threads and combined in a fixed order (deterministic). The column lives in
 // shared memory; R is read through the cache.
 __global__ void __launch_bounds__(128)
-triangular_inverse_kernel(const double2* __restrict__ R, int nu, double2* __restrict__ Rinv) {
+triangular_inverse_kernel(const double2* __restrict__ R, int nu, double2* __restrict__ Rinv,
+                          const int* gate) {
+  if (gate && *gate == 0) return;
   __shared__ double2 x[kMaxNu];
   __shared__ double2 red[4];
   const int j = blockIdx.x;
@@ -215,8 +220,11 @@ constexpr int kRows = 8;
 
 // V <- V * M in place, M nu x nu upper triangular (column-major); each block owns kRows
 // rows of V.
+// gate: skip unless *gate == 1; skip_if: skip when *skip_if != 0
 __global__ void __launch_bounds__(256)
-right_multiply_kernel(double2* V, int64_t ldv, int64_t n, int nu, const double2* __restrict__ M) {
+right_multiply_kernel(double2* V, int64_t ldv, int64_t n, int nu, const double2* __restrict__ M,
+                      const int* gate, const int* skip_if) {
+  if ((gate && *gate == 0) || (skip_if && *skip_if != 0)) return;
   __shared__ double2 sV[kRows][kMaxNu];
   const int64_t r0 = (int64_t)blockIdx.x * kRows;
   for (int t = threadIdx.x; t < kRows * nu; t += blockDim.x) {
@@ -237,6 +245,153 @@ right_multiply_kernel(double2* V, int64_t ldv, int64_t n, int nu, const double2*
     }
     if (r < n) V[(int64_t)c * ldv + r] = acc;
   }
+}
+
+// ---- FP32 first pass (nu <= 128): Gram, Cholesky and triangular inverse in FP32 ----
+
+__global__ void __launch_bounds__(256)
+gram_partial32_kernel(const double2* __restrict__ V, int64_t ldv, int64_t n, int nu,
+                      int64_t rows_per_part, double2* __restrict__ part) {
+  __shared__ float2 sX[kGT][kGT + 1];
+  __shared__ float2 sY[kGT][kGT + 1];
+  const int tiles_a = (nu + kGT - 1) / kGT;
+  const int ta = blockIdx.x % tiles_a, tb = blockIdx.x / tiles_a;
+  const int64_t r_begin = (int64_t)blockIdx.y * rows_per_part;
+  const int64_t r_end = min(n, r_begin + rows_per_part);
+  const int tid = threadIdx.x;
+  const int oa = tid % kGT, ob0 = tid / kGT;
+  float2 acc[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) acc[m] = make_float2(0.f, 0.f);
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += kGT) {
+    __syncthreads();
+    for (int x = tid; x < kGT * kGT; x += 256) {
+      const int rr = x % kGT, cc = x / kGT;
+      const int64_t r = r0 + rr;
+      const int a = ta * kGT + cc, b = tb * kGT + cc;
+      double2 va = make_double2(0.0, 0.0), vb = va;
+      if (r < r_end && a < nu) va = V[(int64_t)a * ldv + r];
+      if (r < r_end && b < nu) vb = V[(int64_t)b * ldv + r];
+      sX[rr][cc] = make_float2((float)va.x, (float)va.y);
+      sY[rr][cc] = make_float2((float)vb.x, (float)vb.y);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < kGT; ++rr) {
+      const float2 x = sX[rr][oa];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const float2 y = sY[rr][ob0 + 8 * m];
+        acc[m].x = fmaf(x.x, y.x, fmaf(x.y, y.y, acc[m].x));
+        acc[m].y = fmaf(x.x, y.y, fmaf(-x.y, y.x, acc[m].y));
+      }
+    }
+  }
+  const int a = ta * kGT + oa;
+  if (a < nu) {
+    double2* P = part + (int64_t)blockIdx.y * nu * nu;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int b = tb * kGT + ob0 + 8 * m;
+      if (b < nu) P[(int64_t)b * nu + a] = make_double2(acc[m].x, acc[m].y);
+    }
+  }
+}
+
+// FP32 Cholesky in shared memory (nu <= 128); output R (upper, as double2), lower zeroed.
+// A pivot below 1e-6 of the largest diagonal entry (V too ill-conditioned for an FP32
+// first pass) sets *fallback: the pass then leaves V alone and an FP64 pass is added.
+__global__ void __launch_bounds__(1024) cholesky32_kernel(double2* Gg, int nu, int* fallback) {
+  extern __shared__ float2 sG32[];
+  __shared__ float rkk, dmax;
+  const int tid = threadIdx.x;
+  for (int t = tid; t < nu * nu; t += blockDim.x) sG32[t] = make_float2((float)Gg[t].x, (float)Gg[t].y);
+  __syncthreads();
+  if (tid == 0) {
+    dmax = 0.f;
+    for (int k = 0; k < nu; ++k) dmax = fmaxf(dmax, sG32[k * nu + k].x);
+  }
+  __syncthreads();
+  bool failed = false;
+  for (int k = 0; k < nu; ++k) {
+    if (tid == 0) {
+      const float d = sG32[k * nu + k].x;
+      if (!(d > 1e-6f * dmax) || !isfinite(d)) {
+        *fallback = 1;
+        rkk = 0.f;
+      } else {
+        rkk = sqrtf(d);
+      }
+      sG32[k * nu + k] = make_float2(rkk, 0.f);
+    }
+    __syncthreads();
+    if (rkk == 0.f) {
+      failed = true;
+      break;
+    }
+    for (int jj = k + 1 + tid; jj < nu; jj += blockDim.x) {
+      const float2 g = sG32[jj * nu + k];
+      sG32[jj * nu + k] = make_float2(g.x / rkk, g.y / rkk);
+    }
+    __syncthreads();
+    const int m = nu - k - 1;
+    for (int t = tid; t < m * m; t += blockDim.x) {
+      const int i = k + 1 + t % m, jj = k + 1 + t / m;
+      if (i > jj) continue;
+      const float2 a = sG32[i * nu + k], b = sG32[jj * nu + k];
+      float2 g = sG32[jj * nu + i];
+      g.x -= a.x * b.x + a.y * b.y;
+      g.y -= a.x * b.y - a.y * b.x;
+      sG32[jj * nu + i] = g;
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < nu * nu; t += blockDim.x) {
+    const int i = t % nu, jj = t / nu;
+    const float2 v = (i > jj) ? make_float2(0.f, 0.f) : sG32[t];
+    Gg[t] = failed ? make_double2(NAN, NAN) : make_double2(v.x, v.y);
+  }
+}
+
+// FP32 triangular inverse, one block per column (as triangular_inverse_kernel).
+__global__ void __launch_bounds__(128)
+triangular_inverse32_kernel(const double2* __restrict__ R, int nu, double2* __restrict__ Rinv,
+                            const int* skip_if) {
+  if (*skip_if != 0) return;
+  __shared__ float2 x[kMaxNu];
+  __shared__ float2 red[4];
+  const int j = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid % 32, w = tid / 32;
+  for (int i = tid; i < nu; i += blockDim.x) x[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  for (int i = j; i >= 0; --i) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int m = i + 1 + tid; m <= j; m += blockDim.x) {
+      const double2 rd = R[(int64_t)m * nu + i];
+      const float2 r = make_float2((float)rd.x, (float)rd.y);
+      const float2 xm = x[m];
+      acc.x += r.x * xm.x - r.y * xm.y;
+      acc.y += r.x * xm.y + r.y * xm.x;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    }
+    if (lane == 0) red[w] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      float2 sum = make_float2(i == j ? 1.f : 0.f, 0.f);
+      for (int k = 0; k < 4; ++k) {
+        sum.x -= red[k].x;
+        sum.y -= red[k].y;
+      }
+      const float d = (float)R[(int64_t)i * nu + i].x;
+      x[i] = make_float2(sum.x / d, sum.y / d);
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < nu; i += blockDim.x) Rinv[(int64_t)j * nu + i] = make_double2(x[i].x, x[i].y);
 }
 
 // C = A * B for upper-triangular nu x nu A, B (one block).
@@ -264,7 +419,7 @@ size_t cholqr2_work_bytes(bem_ctx* ctx, int64_t n, int nu) {
                                                          (2 * (int64_t)sms + tiles - 1) / tiles));
   const int64_t rows_per_part = (n + parts - 1) / parts;
   parts = (n + rows_per_part - 1) / rows_per_part;
-  return (4 + (size_t)parts) * (size_t)nu * nu * sizeof(double2) + 256 * sizeof(int);
+  return (4 + (size_t)parts) * (size_t)nu * nu * sizeof(double2) + 257 * sizeof(int);
 }
 
 // CholeskyQR2 of V (n x nu, ld ldv) with caller-provided work (cholqr2_work_bytes);
@@ -294,17 +449,47 @@ bem_status cholqr2_impl(bem_ctx* ctx, double* V_dev, int64_t n, int64_t ldv, int
                     "cholqr attribute");
     if (st != BEM_OK) return st;
   }
-  for (int pass = 0; pass < 2; ++pass) {
+  // first pass in FP32 when its factor is not needed: it only has to make V well
+  // conditioned; the FP64 second pass sets the final orthogonality. If V is too ill-
+  // conditioned for FP32 the FP32 pass leaves V alone (device flag) and a third, FP64,
+  // pass runs in its place (its kernels return at once otherwise).
+  const bool fp32_first = R_dev == nullptr && refresh_seed == 0 && nu <= 128;
+  int* fallback = deficient + 256;
+  if (fp32_first) {
+    st = cuda_check(ctx, cudaFuncSetAttribute(cholesky32_kernel,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)(nu * nu * sizeof(float2))),
+                    "cholqr attribute");
+    if (st != BEM_OK) return st;
+    st = cuda_check(ctx, cudaMemsetAsync(fallback, 0, sizeof(int), s), "cholqr flag");
+    if (st != BEM_OK) return st;
+  }
+  const int passes = fp32_first ? 3 : 2;
+  for (int pass = 0; pass < passes; ++pass) {
+    // FP32 pass (fp32_first, pass 0); FP64 passes; the third pass only if flagged
     double2* R = pass == 0 ? R1 : R2;
-    gram_partial_kernel<<<dim3((unsigned)tiles, (unsigned)parts), 256, 0, s>>>(
-        reinterpret_cast<const double2*>(V_dev), ldv, n, nu, rows_per_part, part);
+    const bool low = fp32_first && pass == 0;
+    const int* gate = (fp32_first && pass == 2) ? fallback : nullptr;
+    const dim3 ggrid((unsigned)tiles, (unsigned)parts);
+    if (low)
+      gram_partial32_kernel<<<ggrid, 256, 0, s>>>(reinterpret_cast<const double2*>(V_dev), ldv, n,
+                                                  nu, rows_per_part, part);
+    else
+      gram_partial_kernel<<<ggrid, 256, 0, s>>>(reinterpret_cast<const double2*>(V_dev), ldv, n,
+                                                nu, rows_per_part, part, gate);
     sum_parts_kernel<<<(unsigned)(((int64_t)nu * nu + 255) / 256), 256, 0, s>>>(
-        part, (int)parts, (int64_t)nu * nu, R);
+        part, (int)parts, (int64_t)nu * nu, R, gate);
     const bool refresh = refresh_seed != 0 && pass == 0;
-    cholesky_kernel<<<1, 1024, chol_smem, s>>>(R, nu, ctx->d_status, refresh ? deficient : nullptr);
-    triangular_inverse_kernel<<<nu, 128, 0, s>>>(R, nu, Rinv);
+    if (low) {
+      cholesky32_kernel<<<1, 1024, nu * nu * sizeof(float2), s>>>(R, nu, fallback);
+      triangular_inverse32_kernel<<<nu, 128, 0, s>>>(R, nu, Rinv, fallback);
+    } else {
+      cholesky_kernel<<<1, 1024, chol_smem, s>>>(R, nu, ctx->d_status,
+                                                 refresh ? deficient : nullptr, gate);
+      triangular_inverse_kernel<<<nu, 128, 0, s>>>(R, nu, Rinv, gate);
+    }
     right_multiply_kernel<<<(unsigned)((n + kRows - 1) / kRows), 256, 0, s>>>(
-        reinterpret_cast<double2*>(V_dev), ldv, n, nu, Rinv);
+        reinterpret_cast<double2*>(V_dev), ldv, n, nu, Rinv, gate, low ? fallback : nullptr);
     ctx->launches += 5;
     if (refresh) {
       refresh_columns_kernel<<<(unsigned)((n * nu + 255) / 256), 256, 0, s>>>(

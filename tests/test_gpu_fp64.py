@@ -181,3 +181,20 @@ def test_invalid_arguments_are_rejected(bem):
     with pytest.raises(bem.BemError):
         ctx.project(_dev(np.ones((20, 300), complex)))   # nu > 256
     ctx.close()
+
+
+def test_cholqr2_fp32_first_pass_orthonormal(bem):
+    """Without R the first pass runs in FP32; the FP64 second pass must still give
+    orthonormal columns spanning the input."""
+    V = synth.complex_gaussian(3072, 64, 8)
+    V[:, 5] = V[:, 5] + 30.0 * V[:, 4]
+    ctx = bem.Context(0)
+    Vd = _dev(V)
+    ctx.cholqr2(Vd, want_R=False)
+    Q = Vd.cpu().numpy()
+    assert np.max(np.abs(Q.conj().T @ Q - np.eye(64))) < 1e-13
+    assert np.max(np.abs(Q @ (Q.conj().T @ V) - V)) < 1e-12 * np.max(np.abs(V))
+    Qo, _ = orr.orthonormalize(V)
+    # same basis up to a unitary diagonal (both are the positive-diagonal QR factor)
+    assert _relerr(Q, Qo) < 1e-10
+    ctx.close()
