@@ -243,6 +243,69 @@ bem_status bem_kernel_times(bem_ctx* ctx, double* ms_out, int max_out, int* coun
 bem_status bem_microbench(bem_ctx* ctx, int kind, double* ops_per_s);
 
 /*
+ * Near-field treatment (an operator variant for fine meshes; the paper integrates the
+ * regular panel integrals by Gauss quadrature, Section 1, and a fixed low-order rule loses
+ * accuracy when the collocation point is close to the panel). A pair (i, l), i != l, is
+ * near when the distance between the centroids is below twice the larger panel diameter
+ * (longest edge). mode 0: off, every pair i != l takes the 7-point rule; mode 1: near pairs
+ * take the 8 x 8 conical-product rule (the triangle as the image of the unit square under
+ * y = a + s (b - a) + s t (c - b), Gauss-Legendre in s and t, collapsed at the vertex nearest
+ * the collocation point); mode 2: as mode 1, except that the mixed-precision projection takes
+ * the near pairs' corrections from the surrogate network (bem_surrogate_*; BEM_ESTATE if
+ * none is loaded). The mode applies to bem_project (both precisions), bem_residual,
+ * bem_refine and bem_solve (residuals and refinement always use the 8 x 8 rule); the
+ * Algorithm 1 operator of bem_inverse_power keeps the 7-point rule. It is kept across
+ * bem_set_mesh (the pair list is rebuilt for the new mesh at first use). Building the list
+ * synchronises `stream`. Contexts with a near-field mode are not accepted by the batched
+ * projection.
+ * bem_near_pairs: the pair list of the current mesh (builds it if needed): *nnz pairs;
+ *   row_ptr_host (n + 1 int32, nullable) and cols_host (nnz int32, nullable, increasing
+ *   within each row). BEM_ESTATE when the mode is 0. Synchronous.
+ */
+bem_status bem_set_near_field(bem_ctx* ctx, int mode, void* stream);
+bem_status bem_near_pairs(bem_ctx* ctx, int64_t* nnz, int32_t* row_ptr_host, int32_t* cols_host,
+                          void* stream);
+
+/*
+ * Batched projection (Section 3's projection for many independent problems at once, as a
+ * parameter study or a sweep over geometries needs). Each problem is a context with its
+ * mesh and contour already set (bem_set_mesh, bem_set_contour), a basis V_dev[k]
+ * (n_k x nu[k] complex128, column-major, leading dimension ldv[k] >= n_k) and an output
+ * Bhat_dev[k] (N_k x nu[k] x nu[k] complex128, as bem_project). All contexts must be
+ * distinct and on one device; 1 <= nprob <= 4096, 1 <= nu[k] <= min(n_k, 256); only
+ * precision BEM_PREC_MIXED is accepted (BEM_EINVAL otherwise).
+ *
+ * bem_batch_create plans every problem (workspaces of the contexts, FP32 self terms),
+ * orders the problems by decreasing work and records one CUDA graph: per problem the basis
+ * preparation, then ONE persistent launch of the fused kernel (one block per SM taking the
+ * work units of all problems from a shared counter), then per problem the V^H Y reduction
+ * and weighting. With autotune != 0 it times whole runs for every work-unit shape in
+ * {column splits: per-problem default, 1, 2, 3, 4} x {nodes per unit: up to 4, up to 2}
+ * (three runs each, which overwrite Bhat) and keeps the fastest. It synchronises `stream` first (V may
+ * still be written there) and runs its work on a private stream; on return the batch is
+ * idle. The caller owns V and Bhat and must keep them allocated while the batch exists.
+ * bem_batch_run replays the graph on `stream` (asynchronous). It returns BEM_ESTATE if a
+ * context's mesh, contour or workspace changed since creation (create a new batch then).
+ * Device-side errors are reported per context by bem_check.
+ * bem_batch_info: chosen split count and node cap (0 = per-problem default), work units of
+ * the persistent launch, and the autotuner's time per run in ms (0 without autotuning).
+ * bem_project_batched: create (no autotuning), run, wait for completion, check every
+ * context, destroy. Synchronous.
+ * Errors are reported through bem_last_error of the first context.
+ */
+typedef struct bem_batch bem_batch;
+bem_status bem_batch_create(bem_ctx* const* ctxs, int nprob, const double* const* V_dev,
+                            const int64_t* ldv, const int* nu, double* const* Bhat_dev,
+                            int precision, int autotune, bem_batch** out, void* stream);
+bem_status bem_batch_run(bem_batch* batch, void* stream);
+bem_status bem_batch_info(const bem_batch* batch, int* splits, int* nodes_per_unit,
+                          int64_t* units, double* tuned_ms);
+void bem_batch_destroy(bem_batch* batch);
+bem_status bem_project_batched(bem_ctx* const* ctxs, int nprob, const double* const* V_dev,
+                               const int64_t* ldv, const int* nu, double* const* Bhat_dev,
+                               int precision, void* stream);
+
+/*
  * Allocation-free projection (the paper has no counterpart: this serves callers that
  * cannot call cudaMalloc, such as code running under a locked or externally owned memory
  * pool, or a process whose device footprint must not grow after start-up).

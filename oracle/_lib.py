@@ -34,8 +34,10 @@ def lib():
         L.oracle_gauss_legendre.argtypes = [i32, P, P]
         L.oracle_geometry.argtypes = [P, i64, P, P, P, P, P]
         L.oracle_self_integral.argtypes = [P, P, P, P, d, d, i32, P]
-        L.oracle_matrix.argtypes = [P, i64, P, d, d, i32, i64, i64, P, i32]
-        L.oracle_apply.argtypes = [P, i64, P, i32, P, i32, P, i64, i64, P, i32]
+        L.oracle_matrix.argtypes = [P, i64, P, d, d, i32, i64, i64, P, i32, i32]
+        L.oracle_apply.argtypes = [P, i64, P, i32, P, i32, P, i64, i64, P, i32, i32]
+        L.oracle_near_rule.argtypes = [P, P, P, P, d, d, i32, i32, P]
+        L.oracle_near_pairs.argtypes = [P, i64, P, i64, i64, P, P, P]
         L.oracle_max_threads.restype = i32
         _lib = L
     return _lib

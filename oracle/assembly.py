@@ -46,19 +46,20 @@ def self_integral(v0, v1, v2, x, k, deriv=0):
     return complex(out[0], out[1])
 
 
-def matrix(mesh, k, deriv=0, rows=None, threads=0):
-    """Dense A(k) (deriv=0) or dA/dk (deriv=1) as an (r1-r0) x n complex128 array."""
+def matrix(mesh, k, deriv=0, rows=None, threads=0, near=False):
+    """Dense A(k) (deriv=0) or dA/dk (deriv=1) as an (r1-r0) x n complex128 array; near=True
+    uses the 64-point conical rule on near pairs (see ``bem_oracle.c``)."""
     xyz, tri = _mesh_arrays(mesh)
     n = tri.shape[0]
     r0, r1 = (0, n) if rows is None else rows
     A = np.zeros((r1 - r0, n), dtype=np.complex128)
     k = complex(k)
     lib().oracle_matrix(_p(xyz), n, _p(tri), k.real, k.imag, int(deriv), r0, r1, _p(A),
-                        int(threads))
+                        int(threads), int(bool(near)))
     return A
 
 
-def apply(mesh, z, V, rows=None, threads=0):
+def apply(mesh, z, V, rows=None, threads=0, near=False):
     """Y[j] = (A(z_j) V)[rows] for all nodes; returns (N, r1-r0, nu) complex128."""
     xyz, tri = _mesh_arrays(mesh)
     n = tri.shape[0]
@@ -69,7 +70,33 @@ def apply(mesh, z, V, rows=None, threads=0):
     N = z.shape[0]
     r0, r1 = (0, n) if rows is None else rows
     Y = np.zeros(N * (r1 - r0) * nu, dtype=np.complex128)
-    lib().oracle_apply(_p(xyz), n, _p(tri), N, _p(z), nu, _p(V), r0, r1, _p(Y), int(threads))
+    lib().oracle_apply(_p(xyz), n, _p(tri), N, _p(z), nu, _p(V), r0, r1, _p(Y), int(threads),
+                       int(bool(near)))
     # block j is column-major (rows x nu)
     return np.stack([Y[j * (r1 - r0) * nu:(j + 1) * (r1 - r0) * nu].reshape(nu, r1 - r0).T
                      for j in range(N)])
+
+
+def near_rule(v0, v1, v2, x, k, deriv=0, order=8):
+    """The conical-product rule of the given order (order x order points) for the integral of
+    g(k, |x - y|) over the triangle (v0, v1, v2), collapsed at the vertex nearest x."""
+    arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in (v0, v1, v2, x)]
+    out = np.zeros(2)
+    k = complex(k)
+    lib().oracle_near_rule(*[_p(a) for a in arrs], k.real, k.imag, int(deriv), int(order),
+                           _p(out))
+    return complex(out[0], out[1])
+
+
+def near_pairs(mesh, rows=None):
+    """CSR of the near pairs: (row_ptr, cols), cols increasing within each row."""
+    xyz, tri = _mesh_arrays(mesh)
+    n = tri.shape[0]
+    r0, r1 = (0, n) if rows is None else rows
+    counts = np.zeros(r1 - r0, dtype=np.int64)
+    lib().oracle_near_pairs(_p(xyz), n, _p(tri), r0, r1, _p(counts), None, None)
+    row_ptr = np.zeros(r1 - r0 + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum(counts)
+    cols = np.zeros(int(row_ptr[-1]), dtype=np.int64)
+    lib().oracle_near_pairs(_p(xyz), n, _p(tri), r0, r1, _p(counts), _p(row_ptr), _p(cols))
+    return row_ptr, cols

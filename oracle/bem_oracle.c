@@ -24,6 +24,14 @@
  * entire in u, and 16-point Gauss-Legendre is used on each side of u = 0. The derivative dA/dk, used by the eigenvalue refinement, is taken term
  * by term: g' = i exp(i k r) / (4 pi) and, for the self term, i R^2 h'(i k R) / (4 pi).
  *
+ * Near field (operator variant used for fine meshes): a pair (i, l), i != l, is near when
+ * the distance between the centroids is below 2 max(h_i, h_l), h the panel diameter (its
+ * longest edge). Its entry is then the 64-point conical-product rule instead of the 7-point
+ * rule: the triangle (a, b, c) is the image of the unit square under
+ * y = a + s (b - a) + s t (c - b), with Jacobian 2 |T| s, and 8-point Gauss-Legendre is used in
+ * s and in t; the collapsed vertex a is the vertex of triangle l nearest x_i (the first of
+ * them in the triangle's order on a tie), b and c follow it cyclically.
+ *
  * Everything is double / double complex, loops are plain, rows are spread over OpenMP
  * threads (no blocking, no reordering of any sum).
  */
@@ -134,6 +142,8 @@ static cplx hprime_fun(cplx w) {
 typedef struct {
     double centroid[3];
     double area;
+    double diam;       /* longest edge */
+    double v[3][3];    /* vertices */
     double qp[7][3];
     double qw[7];
 } panel_t;
@@ -150,6 +160,14 @@ static void panel_geometry(const double* xyz, const int32_t* tri, int64_t l, pan
     cross3(e1, e2, nrm);
     P->area = 0.5 * norm3(nrm);
     for (int c = 0; c < 3; ++c) P->centroid[c] = (v0[c] + v1[c] + v2[c]) / 3.0;
+    double e3[3];
+    sub3(v2, v1, e3);
+    P->diam = fmax(fmax(norm3(e1), norm3(e2)), norm3(e3));
+    for (int c = 0; c < 3; ++c) {
+        P->v[0][c] = v0[c];
+        P->v[1][c] = v1[c];
+        P->v[2][c] = v2[c];
+    }
     for (int q = 0; q < 7; ++q) {
         for (int c = 0; c < 3; ++c)
             P->qp[q][c] = bary[q][0] * v0[c] + bary[q][1] * v1[c] + bary[q][2] * v2[c];
@@ -203,9 +221,60 @@ static cplx self_integral(const double* v0, const double* v1, const double* v2,
     return total / (4.0 * PI);
 }
 
-/* A_il(k) (deriv = 0) or dA_il/dk (deriv = 1). */
+/* ---------------- the near-field rule ---------------- */
+
+/* Conical-product rule of order m (m x m points) for the integral over triangle v of
+ * g(k, |x - y|) (deriv = 0) or its k-derivative (deriv = 1); collapsed at the vertex of the
+ * triangle nearest x. */
+static cplx near_integral(const double v[3][3], const double* x, cplx k, int deriv, int m) {
+    double gx[64], gw[64];
+    gauss_legendre(m, gx, gw);
+    int a = 0;
+    double best = 0.0;
+    for (int q = 0; q < 3; ++q) {
+        double d[3];
+        sub3(v[q], x, d);
+        double r = norm3(d);
+        if (q == 0 || r < best) {
+            best = r;
+            a = q;
+        }
+    }
+    const double* A = v[a];
+    const double* B = v[(a + 1) % 3];
+    const double* C = v[(a + 2) % 3];
+    double ab[3], bc[3], nrm[3];
+    sub3(B, A, ab);
+    sub3(C, B, bc);
+    cross3(ab, bc, nrm);
+    const double twice_area = norm3(nrm);
+    cplx total = 0.0;
+    for (int p = 0; p < m; ++p) {
+        const double sp = 0.5 * (gx[p] + 1.0), wp = 0.5 * gw[p];
+        for (int q = 0; q < m; ++q) {
+            const double tq = 0.5 * (gx[q] + 1.0), wq = 0.5 * gw[q];
+            double y[3], d[3];
+            for (int c = 0; c < 3; ++c) y[c] = A[c] + sp * ab[c] + sp * tq * bc[c];
+            sub3(x, y, d);
+            const double r = norm3(d);
+            const cplx e = cexp(I * k * r);
+            const cplx g = deriv ? I * e / (4.0 * PI) : e / (4.0 * PI * r);
+            total += wp * wq * twice_area * sp * g;
+        }
+    }
+    return total;
+}
+
+static int is_near(const panel_t* Pi, const panel_t* Pl) {
+    double d[3];
+    sub3(Pi->centroid, Pl->centroid, d);
+    return norm3(d) < 2.0 * fmax(Pi->diam, Pl->diam);
+}
+
+/* A_il(k) (deriv = 0) or dA_il/dk (deriv = 1); near != 0 selects the near-field variant. */
 static cplx entry(const double* xyz, const int32_t* tri, const panel_t* Pi,
-                  const panel_t* Pl, int64_t i, int64_t l, cplx k, int deriv) {
+                  const panel_t* Pl, int64_t i, int64_t l, cplx k, int deriv, int near) {
+    if (near && i != l && is_near(Pi, Pl)) return near_integral(Pl->v, Pi->centroid, k, deriv, 8);
     if (i == l) {
         const double* v0 = xyz + 3 * (int64_t)tri[3 * l + 0];
         const double* v1 = xyz + 3 * (int64_t)tri[3 * l + 1];
@@ -276,7 +345,7 @@ void oracle_self_integral(const double* v0, const double* v1, const double* v2,
 /* Dense A(k) (or dA/dk) for rows [r0, r1), row-major with row stride nt (complex). */
 void oracle_matrix(const double* xyz, int64_t nt, const int32_t* tri, double k_re,
                    double k_im, int deriv, int64_t r0, int64_t r1, double* A_out,
-                   int nthreads) {
+                   int nthreads, int near) {
     set_threads(nthreads);
     cplx k = k_re + I * k_im;
     cplx* A = (cplx*)A_out;
@@ -286,7 +355,7 @@ void oracle_matrix(const double* xyz, int64_t nt, const int32_t* tri, double k_r
         panel_geometry(xyz, tri, i, &Pi);
         for (int64_t l = 0; l < nt; ++l) {
             panel_geometry(xyz, tri, l, &Pl);
-            A[(i - r0) * nt + l] = entry(xyz, tri, &Pi, &Pl, i, l, k, deriv);
+            A[(i - r0) * nt + l] = entry(xyz, tri, &Pi, &Pl, i, l, k, deriv, near);
         }
     }
 }
@@ -298,7 +367,7 @@ void oracle_matrix(const double* xyz, int64_t nt, const int32_t* tri, double k_r
  */
 void oracle_apply(const double* xyz, int64_t nt, const int32_t* tri, int N,
                   const double* z, int nu, const double* V_in, int64_t r0, int64_t r1,
-                  double* Y_out, int nthreads) {
+                  double* Y_out, int nthreads, int near) {
     set_threads(nthreads);
     const cplx* V = (const cplx*)V_in;
     cplx* Y = (cplx*)Y_out;
@@ -312,11 +381,46 @@ void oracle_apply(const double* xyz, int64_t nt, const int32_t* tri, int N,
             panel_geometry(xyz, tri, l, &Pl);
             for (int j = 0; j < N; ++j) {
                 cplx k = z[2 * j] + I * z[2 * j + 1];
-                cplx a = entry(xyz, tri, &Pi, &Pl, i, l, k, 0);
+                cplx a = entry(xyz, tri, &Pi, &Pl, i, l, k, 0, near);
                 cplx* Yj = Y + (int64_t)j * rows * nu;
                 for (int c = 0; c < nu; ++c)
                     Yj[(int64_t)c * rows + (i - r0)] += a * V[(int64_t)c * nt + l];
             }
         }
+    }
+}
+
+/* The conical-product rule of order m (<= 64) for triangle (v0, v1, v2) at x; out = (re, im). */
+void oracle_near_rule(const double* v0, const double* v1, const double* v2, const double* x,
+                      double k_re, double k_im, int deriv, int m, double* out) {
+    double v[3][3];
+    for (int c = 0; c < 3; ++c) {
+        v[0][c] = v0[c];
+        v[1][c] = v1[c];
+        v[2][c] = v2[c];
+    }
+    cplx s = near_integral(v, x, k_re + I * k_im, deriv, m);
+    out[0] = creal(s);
+    out[1] = cimag(s);
+}
+
+/* Near pairs of rows [r0, r1): counts[i - r0] = number of near panels l of row i; with
+ * cols non-null, the panels themselves in increasing l, row after row (row_ptr given by
+ * the caller from the counts). */
+void oracle_near_pairs(const double* xyz, int64_t nt, const int32_t* tri, int64_t r0,
+                       int64_t r1, int64_t* counts, const int64_t* row_ptr, int64_t* cols) {
+    for (int64_t i = r0; i < r1; ++i) {
+        panel_t Pi, Pl;
+        panel_geometry(xyz, tri, i, &Pi);
+        int64_t c = 0;
+        for (int64_t l = 0; l < nt; ++l) {
+            if (l == i) continue;
+            panel_geometry(xyz, tri, l, &Pl);
+            if (is_near(&Pi, &Pl)) {
+                if (cols) cols[row_ptr[i - r0] + c] = l;
+                ++c;
+            }
+        }
+        counts[i - r0] = c;
     }
 }

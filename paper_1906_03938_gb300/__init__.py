@@ -56,6 +56,14 @@ SIGNATURES = {
     "bem_microbench": (_I, [_P, _I, ctypes.POINTER(_D)]),
     "bem_project_fp64_noalloc": (_I, [_I, _I64, _P, _I64, _P, _I, _D, _D, _D, _D, _I, _P,
                                       _I64, _I, _P, _P]),
+    "bem_set_near_field": (_I, [_P, _I, _P]),
+    "bem_near_pairs": (_I, [_P, ctypes.POINTER(_I64), _P, _P, _P]),
+    "bem_batch_create": (_I, [_P, _I, _P, _P, _P, _P, _I, _I, ctypes.POINTER(_P), _P]),
+    "bem_batch_run": (_I, [_P, _P]),
+    "bem_batch_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I64),
+                            ctypes.POINTER(_D)]),
+    "bem_batch_destroy": (None, [_P]),
+    "bem_project_batched": (_I, [_P, _I, _P, _P, _P, _P, _I, _P]),
 }
 
 _lib = None
@@ -171,6 +179,24 @@ class Context:
         r = _D(0.0)
         self._chk("bem_microbench", self._lib.bem_microbench(self._h, kinds[kind], ctypes.byref(r)))
         return r.value
+
+    def set_near_field(self, mode, stream=None):
+        """0: 7-point rule everywhere; 1: 8 x 8 conical rule on near pairs; 2: surrogate
+        network for the near pairs in the mixed projection."""
+        self._chk("bem_set_near_field", self._lib.bem_set_near_field(self._h, int(mode),
+                                                                     _stream(stream)))
+
+    def near_pairs(self, stream=None):
+        """(row_ptr, cols) of the current mesh's near pairs (numpy int32)."""
+        nnz = _I64()
+        self._chk("bem_near_pairs", self._lib.bem_near_pairs(self._h, ctypes.byref(nnz), None,
+                                                             None, _stream(stream)))
+        row_ptr = np.zeros(self.n + 1, dtype=np.int32)
+        cols = np.zeros(max(1, nnz.value), dtype=np.int32)
+        self._chk("bem_near_pairs", self._lib.bem_near_pairs(self._h, ctypes.byref(nnz),
+                                                             _ptr(row_ptr), _ptr(cols),
+                                                             _stream(stream)))
+        return row_ptr, cols[:nnz.value]
 
     def set_mesh(self, xyz, tri, stream=None):
         xyz = np.ascontiguousarray(xyz, dtype=np.float64)
@@ -296,3 +322,83 @@ class Context:
             self._h, m, _ptr(lam.view(np.float64)), _ptr(X), X.stride(1), _ptr(R), _ptr(rel),
             _stream(stream)))
         return (rel, R.transpose(0, 1)) if want_R else rel
+
+
+def _batch_arrays(ctxs, Vs, Bhats):
+    n = len(ctxs)
+    hs = (_P * n)(*[c._h for c in ctxs])
+    vp = (_P * n)(*[V.data_ptr() for V in Vs])
+    ld = (_I64 * n)(*[V.stride(1) for V in Vs])
+    nus = (_I * n)(*[V.shape[1] for V in Vs])
+    bp = (_P * n)(*[B.data_ptr() for B in Bhats])
+    return hs, vp, ld, nus, bp
+
+
+def _batch_outputs(ctxs, Vs):
+    """Raw output buffers (the library writes each Bhat_j column-major) and their views."""
+    import torch
+    for c, V in zip(ctxs, Vs):
+        _check_fortran(V, "V")
+        if V.shape[0] != c.n:
+            raise ValueError("each V must have as many rows as its context's mesh has panels")
+    raw = [torch.empty((c.N, V.shape[1], V.shape[1]), dtype=torch.complex128, device=V.device)
+           for c, V in zip(ctxs, Vs)]
+    return raw, [r.transpose(1, 2) for r in raw]
+
+
+class Batch:
+    """Grouped mixed-precision projection of several contexts, recorded as a CUDA graph.
+
+    ``Batch(ctxs, Vs, autotune=True)`` plans and records; ``run()`` replays it into
+    ``self.Bhat`` (a list of (N_k, nu_k, nu_k) tensors, whose [j] slice is Bhat_j)."""
+
+    def __init__(self, ctxs, Vs, autotune=False, stream=None):
+        self._lib = load()
+        self.ctxs = list(ctxs)
+        self.Vs = list(Vs)
+        self._raw, self.Bhat = _batch_outputs(self.ctxs, self.Vs)
+        hs, vp, ld, nus, bp = _batch_arrays(self.ctxs, self.Vs, self._raw)
+        h = _P()
+        st = self._lib.bem_batch_create(hs, len(self.ctxs), vp, ld, nus, bp, PREC_MIXED,
+                                        int(bool(autotune)), ctypes.byref(h), _stream(stream))
+        if st != BEM_OK:
+            raise BemError("bem_batch_create", st,
+                           self._lib.bem_last_error(self.ctxs[0]._h).decode())
+        self._h = h
+
+    def run(self, stream=None):
+        st = self._lib.bem_batch_run(self._h, _stream(stream))
+        if st != BEM_OK:
+            raise BemError("bem_batch_run", st, self._lib.bem_last_error(self.ctxs[0]._h).decode())
+        return self.Bhat
+
+    def info(self):
+        s, g, u, t = _I(), _I(), _I64(), _D()
+        self._lib.bem_batch_info(self._h, ctypes.byref(s), ctypes.byref(g), ctypes.byref(u),
+                                 ctypes.byref(t))
+        return {"splits": s.value, "nodes_per_unit": g.value, "units": u.value,
+                "tuned_ms": t.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.bem_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def project_batched(ctxs, Vs, stream=None):
+    """One-shot grouped projection (synchronous); returns the list of Bhat tensors."""
+    lib = load()
+    ctxs = list(ctxs)
+    Vs = list(Vs)
+    raw, Bhat = _batch_outputs(ctxs, Vs)
+    hs, vp, ld, nus, bp = _batch_arrays(ctxs, Vs, raw)
+    st = lib.bem_project_batched(hs, len(ctxs), vp, ld, nus, bp, PREC_MIXED, _stream(stream))
+    if st != BEM_OK:
+        raise BemError("bem_project_batched", st, lib.bem_last_error(ctxs[0]._h).decode())
+    return Bhat

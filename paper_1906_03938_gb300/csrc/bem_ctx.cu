@@ -67,6 +67,7 @@ bem_status take_status(bem_ctx* ctx, cudaStream_t stream, const char* where) {
 static void free_geometry(Geometry& g) {
   cudaFree(g.xyz); cudaFree(g.tri); cudaFree(g.cx); cudaFree(g.qp); cudaFree(g.qw);
   cudaFree(g.cx32); cudaFree(g.qp32); cudaFree(g.qw32); cudaFree(g.edge32); cudaFree(g.pack32);
+  cudaFree(g.mom32); cudaFree(g.rho32); cudaFree(g.diam);
   g = Geometry();
 }
 
@@ -132,6 +133,10 @@ void bem_destroy(bem_ctx* ctx) {
   cudaFree(ctx->d_scratch);
   cudaFree(ctx->d_small);
   cudaFree(ctx->d_solve);
+  cudaFree(ctx->d_near_ptr);
+  cudaFree(ctx->d_near_cols);
+  cudaFree(ctx->d_near_work);
+  cudaFree(ctx->d_net);
   for (auto& e : ctx->ev) cudaEventDestroy(e);
   delete ctx;
 }
@@ -174,6 +179,9 @@ bem_status bem_set_mesh(bem_ctx* ctx, int64_t nv, const double* xyz_host, int64_
               cudaMalloc(&g.qp32, 21 * nt * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&g.qw32, 7 * nt * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&g.edge32, 9 * nt * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&g.mom32, kSelfMoments * nt * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&g.rho32, nt * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&g.diam, nt * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&g.pack32, (nt + 15) / 16 * 16 * 64 * sizeof(float)) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
@@ -268,9 +276,12 @@ bem_status bem_project(bem_ctx* ctx, const double* V_dev, int64_t ldv, int nu,
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   const int N = ctx->con.N;
+  if (precision != BEM_PREC_MIXED && precision != BEM_PREC_FP64)
+    return fail(ctx, BEM_EINVAL, "bem_project: unknown precision");
+  bem_status st0 = ensure_near(ctx, s);
+  if (st0 != BEM_OK) return st0;
   if (precision == BEM_PREC_MIXED) return project_mixed(ctx, V_dev, ldv, nu, Bhat_dev, AV_dev, s);
-  if (precision != BEM_PREC_FP64) return fail(ctx, BEM_EINVAL, "bem_project: unknown precision");
-  bem_status st0 = ensure_self64(ctx, s);
+  st0 = ensure_self64(ctx, s);
   if (st0 != BEM_OK) return st0;
   double* Y = AV_dev;
   if (!Y) {
@@ -282,6 +293,10 @@ bem_status bem_project(bem_ctx* ctx, const double* V_dev, int64_t ldv, int nu,
   bem_status st = cuda_check(ctx, launch_apply_fp64(ctx, V_dev, ldv, nu, Y, s), "apply kernel");
   timing_end(ctx, s);
   if (st != BEM_OK) return st;
+  if (near_active(ctx)) {
+    st = near_apply64(ctx, V_dev, ldv, nu, Y, s);
+    if (st != BEM_OK) return st;
+  }
   return cuda_check(ctx, launch_xhy_fp64(ctx, V_dev, ldv, nu, Y, n, n * nu, nu, n, N, ctx->con.w,
                                          Bhat_dev, s),
                     "projection kernel");

@@ -1,9 +1,13 @@
-// CholeskyQR2 orthonormalisation of the Ritz basis (FP64).
+// CholeskyQR2 orthonormalisation of the Ritz basis.
 //
 // The paper orthonormalises the basis U before the Rayleigh-Ritz projection (Section 4,
 // Example 1). CholeskyQR2: G = V^H V, G = R^H R (R upper, positive diagonal),
 // V <- V R^{-1}, and the same once more, which restores orthogonality to working
 // precision for well-conditioned V. All steps are deterministic (fixed-order sums).
+// FP64 runs at a small fraction of the FP32 rate on this part, so the FP64 work is kept to
+// the Gram matrix and the multiplication by the inverse factor: the first pass factors in
+// FP32, and the second pass, whose Gram matrix is then near the identity, obtains its
+// inverse factor from a few small products instead of a sequential factorisation.
 #include <math.h>
 
 #include <algorithm>
@@ -109,41 +113,61 @@ __global__ void refresh_columns_kernel(double2* V, int64_t ldv, int64_t n, int n
 }
 
 constexpr int kGT = 32;   // Gram output tile
+constexpr int kGR = 16;   // rows of V staged at a time by the FP64 Gram kernel
 
-// Partial Gram matrices: block (tile, r) sums conj(V[i][a]) V[i][b] over its row range.
+// Tile pair (ta, tb), ta <= tb, of the idx-th upper tile: tb = 0, 1, ..., ta = 0..tb.
+__device__ __forceinline__ void upper_tile(int idx, int& ta, int& tb) {
+  int b = 0;
+  while ((b + 1) * (b + 2) / 2 <= idx) ++b;
+  tb = b;
+  ta = idx - b * (b + 1) / 2;
+}
+
+// Partial Gram matrices, FP64: block (tile, r) sums conj(V[i][a]) V[i][b] over its row
+// range for the upper tiles only (the Gram matrix is Hermitian; every consumer reads the
+// upper triangle). Three real products per complex term: with x = V[i][a], y = V[i][b],
+// conj(x) y = (S1 + S2) + i (S3 - S1 + S2), S1 = x.re y.re, S2 = x.im y.im,
+// S3 = (x.re - x.im)(y.re + y.im); the sums of the parts are formed once per staged element.
 __global__ void __launch_bounds__(256)
 gram_partial_kernel(const double2* __restrict__ V, int64_t ldv, int64_t n, int nu,
                     int64_t rows_per_part, double2* __restrict__ part, const int* gate) {
   if (gate && *gate == 0) return;
-  __shared__ double2 sX[kGT][kGT + 1];
-  __shared__ double2 sY[kGT][kGT + 1];
-  const int tiles_a = (nu + kGT - 1) / kGT;
-  const int ta = blockIdx.x % tiles_a, tb = blockIdx.x / tiles_a;
+  __shared__ double xr[kGR][kGT + 1], xi[kGR][kGT + 1], xd[kGR][kGT + 1];
+  __shared__ double yr[kGR][kGT + 1], yi[kGR][kGT + 1], ys[kGR][kGT + 1];
+  int ta, tb;
+  upper_tile(blockIdx.x, ta, tb);
   const int64_t r_begin = (int64_t)blockIdx.y * rows_per_part;
   const int64_t r_end = min(n, r_begin + rows_per_part);
   const int tid = threadIdx.x;
   const int oa = tid % kGT, ob0 = tid / kGT;
-  double2 acc[4];
+  double s1[4], s2[4], s3[4];
 #pragma unroll
-  for (int m = 0; m < 4; ++m) acc[m] = make_double2(0.0, 0.0);
-  for (int64_t r0 = r_begin; r0 < r_end; r0 += kGT) {
+  for (int m = 0; m < 4; ++m) s1[m] = s2[m] = s3[m] = 0.0;
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += kGR) {
     __syncthreads();
-    for (int x = tid; x < kGT * kGT; x += 256) {
-      const int rr = x % kGT, cc = x / kGT;
+    for (int x = tid; x < kGR * kGT; x += 256) {
+      const int rr = x % kGR, cc = x / kGR;
       const int64_t r = r0 + rr;
       const int a = ta * kGT + cc, b = tb * kGT + cc;
-      sX[rr][cc] = (r < r_end && a < nu) ? V[(int64_t)a * ldv + r] : make_double2(0.0, 0.0);
-      sY[rr][cc] = (r < r_end && b < nu) ? V[(int64_t)b * ldv + r] : make_double2(0.0, 0.0);
+      const double2 va = (r < r_end && a < nu) ? V[(int64_t)a * ldv + r] : make_double2(0.0, 0.0);
+      const double2 vb = (r < r_end && b < nu) ? V[(int64_t)b * ldv + r] : make_double2(0.0, 0.0);
+      xr[rr][cc] = va.x;
+      xi[rr][cc] = va.y;
+      xd[rr][cc] = va.x - va.y;
+      yr[rr][cc] = vb.x;
+      yi[rr][cc] = vb.y;
+      ys[rr][cc] = vb.x + vb.y;
     }
     __syncthreads();
-#pragma unroll 8
-    for (int rr = 0; rr < kGT; ++rr) {
-      const double2 x = sX[rr][oa];
+    const int rows = (int)(r_end - r0 < kGR ? r_end - r0 : kGR);
+    for (int rr = 0; rr < rows; ++rr) {
+      const double ar = xr[rr][oa], ai = xi[rr][oa], ad = xd[rr][oa];
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
-        const double2 y = sY[rr][ob0 + 8 * m];
-        acc[m].x = fma(x.x, y.x, fma(x.y, y.y, acc[m].x));
-        acc[m].y = fma(x.x, y.y, fma(-x.y, y.x, acc[m].y));
+        const int cb = ob0 + 8 * m;
+        s1[m] = fma(ar, yr[rr][cb], s1[m]);
+        s2[m] = fma(ai, yi[rr][cb], s2[m]);
+        s3[m] = fma(ad, ys[rr][cb], s3[m]);
       }
     }
   }
@@ -153,24 +177,342 @@ gram_partial_kernel(const double2* __restrict__ V, int64_t ldv, int64_t n, int n
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       const int b = tb * kGT + ob0 + 8 * m;
-      if (b < nu) P[(int64_t)b * nu + a] = acc[m];
+      if (b < nu) P[(int64_t)b * nu + a] = make_double2(s1[m] + s2[m], s3[m] - s1[m] + s2[m]);
     }
   }
 }
 
-// G = sum of the partials in part order (deterministic).
-__global__ void sum_parts_kernel(const double2* __restrict__ part, int parts, int64_t count,
-                                 double2* __restrict__ G, const int* gate) {
-  if (gate && *gate == 0) return;
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= count) return;
-  double2 s = make_double2(0.0, 0.0);
-  for (int r = 0; r < parts; ++r) {
-    const double2 v = part[(int64_t)r * count + t];
-    s.x += v.x;
-    s.y += v.y;
+// Partial Gram matrices in FP32 (first pass), upper tiles; partial sums stored as double2.
+__global__ void __launch_bounds__(256)
+gram_partial32_kernel(const double2* __restrict__ V, int64_t ldv, int64_t n, int nu,
+                      int64_t rows_per_part, double2* __restrict__ part) {
+  __shared__ float2 sX[kGT][kGT + 1];
+  __shared__ float2 sY[kGT][kGT + 1];
+  int ta, tb;
+  upper_tile(blockIdx.x, ta, tb);
+  const int64_t r_begin = (int64_t)blockIdx.y * rows_per_part;
+  const int64_t r_end = min(n, r_begin + rows_per_part);
+  const int tid = threadIdx.x;
+  const int oa = tid % kGT, ob0 = tid / kGT;
+  float2 acc[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) acc[m] = make_float2(0.f, 0.f);
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += kGT) {
+    __syncthreads();
+    for (int x = tid; x < kGT * kGT; x += 256) {
+      const int rr = x % kGT, cc = x / kGT;
+      const int64_t r = r0 + rr;
+      const int a = ta * kGT + cc, b = tb * kGT + cc;
+      double2 va = make_double2(0.0, 0.0), vb = va;
+      if (r < r_end && a < nu) va = V[(int64_t)a * ldv + r];
+      if (r < r_end && b < nu) vb = V[(int64_t)b * ldv + r];
+      sX[rr][cc] = make_float2((float)va.x, (float)va.y);
+      sY[rr][cc] = make_float2((float)vb.x, (float)vb.y);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < kGT; ++rr) {
+      const float2 x = sX[rr][oa];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const float2 y = sY[rr][ob0 + 8 * m];
+        acc[m].x = fmaf(x.x, y.x, fmaf(x.y, y.y, acc[m].x));
+        acc[m].y = fmaf(x.x, y.y, fmaf(-x.y, y.x, acc[m].y));
+      }
+    }
   }
-  G[t] = s;
+  const int a = ta * kGT + oa;
+  if (a < nu) {
+    double2* P = part + (int64_t)blockIdx.y * nu * nu;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int b = tb * kGT + ob0 + 8 * m;
+      if (b < nu) P[(int64_t)b * nu + a] = make_double2(acc[m].x, acc[m].y);
+    }
+  }
+}
+
+// G = sum of the partials (deterministic): eight threads per element, thread q adding the
+// parts q, q + 8, ... in order, then a fixed shuffle tree. Elements of lower tiles are not
+// formed.
+__global__ void __launch_bounds__(256)
+sum_parts_kernel(const double2* __restrict__ part, int parts, int nu, double2* __restrict__ G,
+                 const int* gate) {
+  if (gate && *gate == 0) return;
+  const int64_t count = (int64_t)nu * nu;
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t t = gt / 8;
+  const int q = (int)(gt % 8);
+  double2 sum = make_double2(0.0, 0.0);
+  bool live = t < count;
+  if (live) {
+    const int a = (int)(t % nu), b = (int)(t / nu);
+    live = a / kGT <= b / kGT;
+  }
+  if (live)
+    for (int r = q; r < parts; r += 8) {
+      const double2 v = part[(int64_t)r * count + t];
+      sum.x += v.x;
+      sum.y += v.y;
+    }
+#pragma unroll
+  for (int off = 1; off < 8; off <<= 1) {
+    sum.x += __shfl_xor_sync(0xffffffffu, sum.x, off);
+    sum.y += __shfl_xor_sync(0xffffffffu, sum.y, off);
+  }
+  if (live && q == 0) G[t] = sum;
+}
+
+// FP32 first-pass factor: Z = R^{-1} for G = R^H R (nu <= 128), one block, by Gaussian
+// elimination of [G | I] without pivoting: the left part becomes D L^H and the right part
+// L^{-1} (G = L D L^H, L unit lower), so Z = L^{-H} D^{-1/2}. Shared memory holds G's
+// trailing lower triangle (G[r][c], r >= c) and W = L^{-1} transposed in the strict upper
+// triangle (W[c][r] at row r, column c); step k changes only columns c > k and reads
+// column k, so one barrier per step suffices. A pivot below 1e-6 of the largest diagonal
+// entry sets *fallback (V too ill-conditioned for an FP32 pass) and Z is not written.
+template <int kSlots>   // ceil(nu^2 / 1024)
+__global__ void __launch_bounds__(1024)
+chol_inv32_kernel(const double2* __restrict__ Gg, int nu, double2* __restrict__ Z, int* fallback) {
+  extern __shared__ float2 S[];
+  __shared__ float dmax_s;
+  const int tid = threadIdx.x;
+  const int total = nu * nu;
+  for (int e = tid; e < total; e += blockDim.x) {
+    const int r = e % nu, c = e / nu;
+    float2 v = make_float2(0.f, 0.f);
+    if (r >= c) {
+      const double2 g = Gg[(int64_t)r * nu + c];   // G[r][c] = conj(G[c][r]), upper stored
+      v = make_float2((float)g.x, -(float)g.y);
+    }
+    S[e] = v;
+  }
+  if (tid < 32) {
+    float m = 0.f;
+    for (int k = tid; k < nu; k += 32) m = fmaxf(m, (float)Gg[(int64_t)k * nu + k].x);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (tid == 0) dmax_s = m;
+  }
+  __syncthreads();
+  const float dmax = dmax_s;
+  int sr[kSlots], sc[kSlots];
+#pragma unroll
+  for (int m = 0; m < kSlots; ++m) {
+    const int e = tid + m * 1024;
+    sr[m] = e < total ? e % nu : 0;
+    sc[m] = e < total ? e / nu : -1;
+  }
+  for (int k = 0; k < nu; ++k) {
+    const float d = S[k * nu + k].x;
+    if (!(d > 1e-6f * dmax) || !isfinite(d)) {
+      if (tid == 0) *fallback = 1;
+      return;   // d is the same for every thread: the whole block leaves
+    }
+    const float rd = 1.f / d;
+#pragma unroll
+    for (int m = 0; m < kSlots; ++m) {
+      const int r = sr[m], c = sc[m];
+      if (c <= k) continue;
+      if (r >= c) {
+        // G[r][c] -= G[r][k] conj(G[c][k]) / d
+        const float2 a = S[k * nu + r], b = S[k * nu + c];
+        float2 g = S[c * nu + r];
+        g.x -= (a.x * b.x + a.y * b.y) * rd;
+        g.y -= (a.y * b.x - a.x * b.y) * rd;
+        S[c * nu + r] = g;
+      } else if (r <= k) {
+        // W[c][r] -= (G[c][k] / d) W[k][r], W[k][k] = 1
+        const float2 l = S[k * nu + c];
+        const float2 w = (r == k) ? make_float2(1.f, 0.f) : S[k * nu + r];
+        float2 g = S[c * nu + r];
+        g.x -= (l.x * w.x - l.y * w.y) * rd;
+        g.y -= (l.x * w.y + l.y * w.x) * rd;
+        S[c * nu + r] = g;
+      }
+    }
+    __syncthreads();
+  }
+  // Z[c][k] = conj(W[k][c]) / sqrt(d_k) for c <= k, zero below the diagonal
+  for (int e = tid; e < total; e += blockDim.x) {
+    const int c = e % nu, k = e / nu;
+    double2 out = make_double2(0.0, 0.0);
+    if (c <= k) {
+      const float inv = 1.f / sqrtf(S[k * nu + k].x);
+      if (c == k) {
+        out = make_double2(inv, 0.0);
+      } else {
+        const float2 w = S[k * nu + c];
+        out = make_double2(w.x * inv, -w.y * inv);
+      }
+    }
+    Z[e] = out;
+  }
+}
+
+// ---- second pass near the identity ----
+//
+// After a first pass G = V^H V = I + E with ||E|| small. The inverse factor Z = R^{-1} is
+// I + Y with Y upper triangular with a real diagonal, and Z^H G Z = I reads
+// Y + Y^H = -H(Y), H(Y) = E + Y^H E + E Y + Y^H Y + Y^H E Y. The fixed point
+// Y <- -U(H(Y)) (U keeps the strict upper triangle and half the diagonal) gains one order
+// of ||E|| per step: Y0 = -U(E) is exact to O(||E||^2), Y1 (without the cubic term) to
+// O(||E||^3) and Y2 to O(||E||^4). Only small products are needed, spread over many
+// blocks, instead of a sequential Cholesky factorisation and triangular inverse.
+
+// E entry (m, j) from the upper triangle of G.
+__device__ __forceinline__ double2 e_entry(const double2* G, int nu, int m, int j) {
+  if (m <= j) {
+    const double2 g = G[(int64_t)j * nu + m];
+    return make_double2(g.x - (m == j ? 1.0 : 0.0), m == j ? 0.0 : g.y);
+  }
+  const double2 g = G[(int64_t)m * nu + j];
+  return make_double2(g.x, -g.y);
+}
+
+// Y entry (m, i), m <= i: explicit (Yx non-null) or Y0 = -U(E) from G.
+__device__ __forceinline__ double2 y_entry(const double2* G, const double2* Yx, int nu, int m, int i) {
+  if (Yx) return Yx[(int64_t)i * nu + m];
+  const double2 g = G[(int64_t)i * nu + m];
+  return m < i ? make_double2(-g.x, -g.y) : make_double2(-0.5 * (g.x - 1.0), 0.0);
+}
+
+constexpr int kNT = 8;     // output tile of the near-identity products (kNT x kNT per block)
+constexpr int kNM = 16;    // inner-dimension chunk staged in shared memory
+
+// Tiled small products of the near-identity factor; one 8 x 8 output tile per block of 64
+// threads, the inner dimension staged 16 at a time in shared memory.
+//  kMode 0: P = Y0^H E (all entries), Q = Y0^H Y0 (upper), Y0 = -U(E) formed from G, and
+//           the block sums of |E_ij|^2 (upper triangle, off-diagonal entries twice);
+//  kMode 1: P = Y^H E, Q = Y^H Y for the explicit Y;
+//  kMode 2: Z = I + Y2, Y2 = -U(E + P + P^H + Q + P Y) (P, Q, Y of mode 1).
+template <int kMode>
+__global__ void __launch_bounds__(64)
+near_tile_kernel(const double2* __restrict__ G, const double2* __restrict__ Y,
+                 const double2* __restrict__ Pin, const double2* __restrict__ Qin, int nu,
+                 double2* __restrict__ P, double2* __restrict__ Q, double2* __restrict__ Z,
+                 float* epsp, const int* gate, const int* skip_if) {
+  if ((gate && *gate == 0) || (skip_if && *skip_if != 0)) return;
+  __shared__ double2 sA[kNM][kNT], sB[kNM][kNT], sC[kNM][kNT];
+  __shared__ float red[64];
+  const int tid = threadIdx.x;
+  const int ti = tid % kNT, tj = tid / kNT;
+  const int i0 = blockIdx.x * kNT, j0 = blockIdx.y * kNT;
+  const int i = i0 + ti, j = j0 + tj;
+  double2 p = make_double2(0.0, 0.0), q = p;
+  // inner index m runs to the last row where the upper-triangular factor is non-zero
+  const int mend = min(nu, (kMode == 2 ? j0 : i0) + kNT);
+  for (int m0 = 0; m0 < mend; m0 += kNM) {
+    __syncthreads();
+    for (int x = tid; x < kNM * kNT; x += 64) {
+      const int mm = x / kNT, cc = x % kNT;
+      const int m = m0 + mm;
+      const int ic = i0 + cc, jc = j0 + cc;
+      const bool mv = m < nu;
+      if (kMode == 2) {
+        sA[mm][cc] = (mv && ic < nu) ? Pin[(int64_t)m * nu + ic] : make_double2(0.0, 0.0);   // P(i, m)
+        sB[mm][cc] = (mv && jc < nu && m <= jc) ? Y[(int64_t)jc * nu + m] : make_double2(0.0, 0.0);
+      } else {
+        sA[mm][cc] = (mv && ic < nu && m <= ic) ? y_entry(G, kMode == 0 ? nullptr : Y, nu, m, ic)
+                                                : make_double2(0.0, 0.0);
+        sB[mm][cc] = (mv && jc < nu) ? e_entry(G, nu, m, jc) : make_double2(0.0, 0.0);
+        sC[mm][cc] = (mv && jc < nu && m <= jc) ? y_entry(G, kMode == 0 ? nullptr : Y, nu, m, jc)
+                                                : make_double2(0.0, 0.0);
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int mm = 0; mm < kNM; ++mm) {
+      const double2 a = sA[mm][ti], b = sB[mm][tj];
+      if (kMode == 2) {   // P(i, m) Y(m, j)
+        p.x += a.x * b.x - a.y * b.y;
+        p.y += a.x * b.y + a.y * b.x;
+      } else {            // conj(Y(m, i)) E(m, j), conj(Y(m, i)) Y(m, j)
+        const double2 c = sC[mm][tj];
+        p.x += a.x * b.x + a.y * b.y;
+        p.y += a.x * b.y - a.y * b.x;
+        q.x += a.x * c.x + a.y * c.y;
+        q.y += a.x * c.y - a.y * c.x;
+      }
+    }
+  }
+  const bool in = i < nu && j < nu;
+  const int64_t t = (int64_t)j * nu + i;
+  if (kMode == 2) {
+    if (in) {
+      if (i > j) {
+        Z[t] = make_double2(0.0, 0.0);
+      } else {
+        double2 h = e_entry(G, nu, i, j);
+        const double2 pp = Pin[t], pt = Pin[(int64_t)i * nu + j], qq = Qin[t];
+        h.x += pp.x + pt.x + qq.x + p.x;
+        h.y += pp.y - pt.y + qq.y + p.y;
+        Z[t] = i < j ? make_double2(-h.x, -h.y) : make_double2(1.0 - 0.5 * h.x, 0.0);
+      }
+    }
+    return;
+  }
+  if (in) {
+    P[t] = p;
+    if (i <= j) Q[t] = q;
+  }
+  if (kMode == 0) {
+    float e2 = 0.f;
+    if (in && i <= j) {
+      const double2 e = e_entry(G, nu, i, j);
+      e2 = (float)((e.x * e.x + e.y * e.y) * (i == j ? 1.0 : 2.0));
+    }
+    red[tid] = e2;
+    __syncthreads();
+    for (int s = 32; s > 0; s >>= 1) {
+      if (tid < s) red[tid] += red[tid + s];
+      __syncthreads();
+    }
+    if (tid == 0) epsp[blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+  }
+}
+
+// Y1 = -U(E + P + P^H + Q). Every block first sums the block sums of |E|^2 in order; if
+// ||E||_F exceeds eps_max the near-identity route is abandoned (*classic = 1) and the
+// classic Cholesky factorisation runs instead. *done = 1 tells the second step to skip.
+__global__ void __launch_bounds__(64)
+near_y1_kernel(const double2* __restrict__ G, const double2* __restrict__ P,
+               const double2* __restrict__ Q, const float* __restrict__ epsp, int nparts,
+               int nu, float eps_max, float eps_small, double2* __restrict__ Y,
+               double2* __restrict__ Z, int* classic, int* done, const int* gate) {
+  if (gate && *gate == 0) return;
+  __shared__ float e2s;
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int b = 0; b < nparts; ++b) s += epsp[b];
+    e2s = s;
+  }
+  __syncthreads();
+  if (!(e2s <= eps_max * eps_max)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      *classic = 1;
+      *done = 1;
+    }
+    return;
+  }
+  // ||E|| <= eps_small: Y1 is already exact to rounding (its error is O(||E||^3)), so
+  // Z = I + Y1 is written here and the second step is skipped
+  const bool small = e2s <= eps_small * eps_small;
+  if (small && blockIdx.x == 0 && threadIdx.x == 0) *done = 1;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nu * nu) return;
+  const int i = (int)(t % nu), j = (int)(t / nu);
+  double2 y = make_double2(0.0, 0.0);
+  if (i < j) {
+    const double2 e = e_entry(G, nu, i, j), p = P[t], pt = P[(int64_t)i * nu + j], q = Q[t];
+    y = make_double2(-(e.x + p.x + pt.x + q.x), -(e.y + p.y - pt.y + q.y));
+  } else if (i == j) {
+    const double2 e = e_entry(G, nu, i, i), p = P[t], q = Q[t];
+    y = make_double2(-0.5 * (e.x + 2.0 * p.x + q.x), 0.0);
+  }
+  if (small)
+    Z[t] = i == j ? make_double2(1.0 + y.x, 0.0) : y;
+  else
+    Y[t] = y;
 }
 
 // Rinv = R^{-1} for upper-triangular R: one block per column j, back substitution
@@ -216,182 +558,77 @@ triangular_inverse_kernel(const double2* __restrict__ R, int nu, double2* __rest
   for (int i = tid; i < nu; i += blockDim.x) Rinv[(int64_t)j * nu + i] = x[i];
 }
 
-constexpr int kRows = 8;
+constexpr int kRMRows = 8;    // rows of V per block
+constexpr int kRMK = 16;      // k chunk of M staged at a time
 
-// V <- V * M in place, M nu x nu upper triangular (column-major); each block owns kRows
-// rows of V.
-// gate: skip unless *gate == 1; skip_if: skip when *skip_if != 0
+size_t right_multiply_smem(int nu) {
+  return (size_t)(3 * nu * kRMRows + 3 * kRMK * (nu + 1)) * sizeof(double);
+}
+
+// V <- V M in place, M nu x nu upper triangular (column-major, zero below the diagonal);
+// each block owns kRMRows complete rows of V, staged in shared memory before any is
+// overwritten. Three real products per complex term: a b = (S1 - S2) + i (S3 - S1 - S2),
+// S1 = a.re b.re, S2 = a.im b.im, S3 = (a.re + a.im)(b.re + b.im).
+// gate: skip unless *gate != 0; skip_if: skip when *skip_if != 0.
 __global__ void __launch_bounds__(256)
 right_multiply_kernel(double2* V, int64_t ldv, int64_t n, int nu, const double2* __restrict__ M,
                       const int* gate, const int* skip_if) {
   if ((gate && *gate == 0) || (skip_if && *skip_if != 0)) return;
-  __shared__ double2 sV[kRows][kMaxNu];
-  const int64_t r0 = (int64_t)blockIdx.x * kRows;
-  for (int t = threadIdx.x; t < kRows * nu; t += blockDim.x) {
-    const int rr = t % kRows, c = t / kRows;
-    const int64_t r = r0 + rr;
-    sV[rr][c] = (r < n) ? V[(int64_t)c * ldv + r] : make_double2(0.0, 0.0);
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < kRows * nu; t += blockDim.x) {
-    const int rr = t % kRows, c = t / kRows;
-    const int64_t r = r0 + rr;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int k = 0; k <= c; ++k) {
-      const double2 a = sV[rr][k];
-      const double2 b = M[(int64_t)c * nu + k];
-      acc.x += a.x * b.x - a.y * b.y;
-      acc.y += a.x * b.y + a.y * b.x;
-    }
-    if (r < n) V[(int64_t)c * ldv + r] = acc;
-  }
-}
-
-// ---- FP32 first pass (nu <= 128): Gram, Cholesky and triangular inverse in FP32 ----
-
-__global__ void __launch_bounds__(256)
-gram_partial32_kernel(const double2* __restrict__ V, int64_t ldv, int64_t n, int nu,
-                      int64_t rows_per_part, double2* __restrict__ part) {
-  __shared__ float2 sX[kGT][kGT + 1];
-  __shared__ float2 sY[kGT][kGT + 1];
-  const int tiles_a = (nu + kGT - 1) / kGT;
-  const int ta = blockIdx.x % tiles_a, tb = blockIdx.x / tiles_a;
-  const int64_t r_begin = (int64_t)blockIdx.y * rows_per_part;
-  const int64_t r_end = min(n, r_begin + rows_per_part);
+  extern __shared__ double rm_smem[];
+  double* vr = rm_smem;                  // [nu][kRMRows]
+  double* vi = vr + nu * kRMRows;
+  double* vs = vi + nu * kRMRows;
+  double* mr = vs + nu * kRMRows;        // [kRMK][nu + 1]
+  double* mi = mr + kRMK * (nu + 1);
+  double* ms = mi + kRMK * (nu + 1);
   const int tid = threadIdx.x;
-  const int oa = tid % kGT, ob0 = tid / kGT;
-  float2 acc[4];
+  const int64_t r0 = (int64_t)blockIdx.x * kRMRows;
+  for (int t = tid; t < kRMRows * nu; t += blockDim.x) {
+    const int rr = t % kRMRows, c = t / kRMRows;
+    const int64_t r = r0 + rr;
+    const double2 v = (r < n) ? V[(int64_t)c * ldv + r] : make_double2(0.0, 0.0);
+    vr[c * kRMRows + rr] = v.x;
+    vi[c * kRMRows + rr] = v.y;
+    vs[c * kRMRows + rr] = v.x + v.y;
+  }
+  constexpr int kOut = kMaxNu * kRMRows / 256;   // outputs per thread at nu = kMaxNu
+  const int outs = kRMRows * nu;
+  double s1[kOut], s2[kOut], s3[kOut];
 #pragma unroll
-  for (int m = 0; m < 4; ++m) acc[m] = make_float2(0.f, 0.f);
-  for (int64_t r0 = r_begin; r0 < r_end; r0 += kGT) {
+  for (int m = 0; m < kOut; ++m) s1[m] = s2[m] = s3[m] = 0.0;
+  for (int k0 = 0; k0 < nu; k0 += kRMK) {
+    const int kn = min(kRMK, nu - k0);
     __syncthreads();
-    for (int x = tid; x < kGT * kGT; x += 256) {
-      const int rr = x % kGT, cc = x / kGT;
-      const int64_t r = r0 + rr;
-      const int a = ta * kGT + cc, b = tb * kGT + cc;
-      double2 va = make_double2(0.0, 0.0), vb = va;
-      if (r < r_end && a < nu) va = V[(int64_t)a * ldv + r];
-      if (r < r_end && b < nu) vb = V[(int64_t)b * ldv + r];
-      sX[rr][cc] = make_float2((float)va.x, (float)va.y);
-      sY[rr][cc] = make_float2((float)vb.x, (float)vb.y);
+    for (int t = tid; t < kRMK * nu; t += blockDim.x) {
+      const int kk = t % kRMK, c = t / kRMK;
+      const double2 b = kk < kn ? M[(int64_t)c * nu + k0 + kk] : make_double2(0.0, 0.0);
+      mr[kk * (nu + 1) + c] = b.x;
+      mi[kk * (nu + 1) + c] = b.y;
+      ms[kk * (nu + 1) + c] = b.x + b.y;
     }
     __syncthreads();
-#pragma unroll 8
-    for (int rr = 0; rr < kGT; ++rr) {
-      const float2 x = sX[rr][oa];
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const float2 y = sY[rr][ob0 + 8 * m];
-        acc[m].x = fmaf(x.x, y.x, fmaf(x.y, y.y, acc[m].x));
-        acc[m].y = fmaf(x.x, y.y, fmaf(-x.y, y.x, acc[m].y));
+    for (int m = 0; m < kOut; ++m) {
+      const int o = tid + 256 * m;
+      if (o >= outs) break;
+      const int c = o % nu, rr = o / nu;
+      if (c < k0) continue;   // M[k][c] = 0 for k > c
+      for (int kk = 0; kk < kn; ++kk) {
+        const int k = k0 + kk;
+        s1[m] = fma(vr[k * kRMRows + rr], mr[kk * (nu + 1) + c], s1[m]);
+        s2[m] = fma(vi[k * kRMRows + rr], mi[kk * (nu + 1) + c], s2[m]);
+        s3[m] = fma(vs[k * kRMRows + rr], ms[kk * (nu + 1) + c], s3[m]);
       }
     }
   }
-  const int a = ta * kGT + oa;
-  if (a < nu) {
-    double2* P = part + (int64_t)blockIdx.y * nu * nu;
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const int b = tb * kGT + ob0 + 8 * m;
-      if (b < nu) P[(int64_t)b * nu + a] = make_double2(acc[m].x, acc[m].y);
-    }
+  for (int m = 0; m < kOut; ++m) {
+    const int o = tid + 256 * m;
+    if (o >= outs) break;
+    const int c = o % nu, rr = o / nu;
+    const int64_t r = r0 + rr;
+    if (r < n) V[(int64_t)c * ldv + r] = make_double2(s1[m] - s2[m], s3[m] - s1[m] - s2[m]);
   }
-}
-
-// FP32 Cholesky in shared memory (nu <= 128); output R (upper, as double2), lower zeroed.
-// A pivot below 1e-6 of the largest diagonal entry (V too ill-conditioned for an FP32
-// first pass) sets *fallback: the pass then leaves V alone and an FP64 pass is added.
-__global__ void __launch_bounds__(1024) cholesky32_kernel(double2* Gg, int nu, int* fallback) {
-  extern __shared__ float2 sG32[];
-  __shared__ float rkk, dmax;
-  const int tid = threadIdx.x;
-  for (int t = tid; t < nu * nu; t += blockDim.x) sG32[t] = make_float2((float)Gg[t].x, (float)Gg[t].y);
-  __syncthreads();
-  if (tid == 0) {
-    dmax = 0.f;
-    for (int k = 0; k < nu; ++k) dmax = fmaxf(dmax, sG32[k * nu + k].x);
-  }
-  __syncthreads();
-  bool failed = false;
-  for (int k = 0; k < nu; ++k) {
-    if (tid == 0) {
-      const float d = sG32[k * nu + k].x;
-      if (!(d > 1e-6f * dmax) || !isfinite(d)) {
-        *fallback = 1;
-        rkk = 0.f;
-      } else {
-        rkk = sqrtf(d);
-      }
-      sG32[k * nu + k] = make_float2(rkk, 0.f);
-    }
-    __syncthreads();
-    if (rkk == 0.f) {
-      failed = true;
-      break;
-    }
-    for (int jj = k + 1 + tid; jj < nu; jj += blockDim.x) {
-      const float2 g = sG32[jj * nu + k];
-      sG32[jj * nu + k] = make_float2(g.x / rkk, g.y / rkk);
-    }
-    __syncthreads();
-    const int m = nu - k - 1;
-    for (int t = tid; t < m * m; t += blockDim.x) {
-      const int i = k + 1 + t % m, jj = k + 1 + t / m;
-      if (i > jj) continue;
-      const float2 a = sG32[i * nu + k], b = sG32[jj * nu + k];
-      float2 g = sG32[jj * nu + i];
-      g.x -= a.x * b.x + a.y * b.y;
-      g.y -= a.x * b.y - a.y * b.x;
-      sG32[jj * nu + i] = g;
-    }
-    __syncthreads();
-  }
-  for (int t = tid; t < nu * nu; t += blockDim.x) {
-    const int i = t % nu, jj = t / nu;
-    const float2 v = (i > jj) ? make_float2(0.f, 0.f) : sG32[t];
-    Gg[t] = failed ? make_double2(NAN, NAN) : make_double2(v.x, v.y);
-  }
-}
-
-// FP32 triangular inverse, one block per column (as triangular_inverse_kernel).
-__global__ void __launch_bounds__(128)
-triangular_inverse32_kernel(const double2* __restrict__ R, int nu, double2* __restrict__ Rinv,
-                            const int* skip_if) {
-  if (*skip_if != 0) return;
-  __shared__ float2 x[kMaxNu];
-  __shared__ float2 red[4];
-  const int j = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid % 32, w = tid / 32;
-  for (int i = tid; i < nu; i += blockDim.x) x[i] = make_float2(0.f, 0.f);
-  __syncthreads();
-  for (int i = j; i >= 0; --i) {
-    float2 acc = make_float2(0.f, 0.f);
-    for (int m = i + 1 + tid; m <= j; m += blockDim.x) {
-      const double2 rd = R[(int64_t)m * nu + i];
-      const float2 r = make_float2((float)rd.x, (float)rd.y);
-      const float2 xm = x[m];
-      acc.x += r.x * xm.x - r.y * xm.y;
-      acc.y += r.x * xm.y + r.y * xm.x;
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-    }
-    if (lane == 0) red[w] = acc;
-    __syncthreads();
-    if (tid == 0) {
-      float2 sum = make_float2(i == j ? 1.f : 0.f, 0.f);
-      for (int k = 0; k < 4; ++k) {
-        sum.x -= red[k].x;
-        sum.y -= red[k].y;
-      }
-      const float d = (float)R[(int64_t)i * nu + i].x;
-      x[i] = make_float2(sum.x / d, sum.y / d);
-    }
-    __syncthreads();
-  }
-  for (int i = tid; i < nu; i += blockDim.x) Rinv[(int64_t)j * nu + i] = make_double2(x[i].x, x[i].y);
 }
 
 // C = A * B for upper-triangular nu x nu A, B (one block).
@@ -411,101 +648,185 @@ __global__ void upper_product_kernel(const double2* A, const double2* B, int nu,
 
 }  // namespace
 
-size_t cholqr2_work_bytes(bem_ctx* ctx, int64_t n, int nu) {
+namespace {
+
+struct CqLayout {
+  int tiles_u = 0;           // upper Gram tiles
+  int64_t parts = 0, rows_per_part = 0;
+  int near_blocks = 0;       // blocks of the near-identity element kernels (64 threads)
+  int near_tiles = 0;        // 8 x 8 tiles of the near-identity products
+  unsigned sum_blocks = 0;   // blocks of sum_parts_kernel (eight threads per element)
+};
+
+CqLayout cq_layout(bem_ctx* ctx, int64_t n, int nu) {
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  const int tiles = ((nu + kGT - 1) / kGT) * ((nu + kGT - 1) / kGT);
-  int64_t parts = std::max<int64_t>(1, std::min<int64_t>((n + 63) / 64,
-                                                         (2 * (int64_t)sms + tiles - 1) / tiles));
-  const int64_t rows_per_part = (n + parts - 1) / parts;
-  parts = (n + rows_per_part - 1) / rows_per_part;
-  return (4 + (size_t)parts) * (size_t)nu * nu * sizeof(double2) + 257 * sizeof(int);
+  CqLayout L;
+  const int T = (nu + kGT - 1) / kGT;
+  L.tiles_u = T * (T + 1) / 2;
+  L.parts = std::max<int64_t>(1, std::min<int64_t>((n + kGT - 1) / kGT,
+                                                   (2 * (int64_t)sms + L.tiles_u - 1) / L.tiles_u));
+  L.rows_per_part = (n + L.parts - 1) / L.parts;
+  L.parts = (n + L.rows_per_part - 1) / L.rows_per_part;
+  L.near_blocks = (int)(((int64_t)nu * nu + 63) / 64);
+  L.near_tiles = ((nu + 7) / 8) * ((nu + 7) / 8);
+  L.sum_blocks = (unsigned)((8 * (int64_t)nu * nu + 255) / 256);
+  return L;
+}
+
+// Work space: nine nu x nu complex matrices (G, Z, R1, R2, P, Q, Y, P1, Q1), the Gram
+// partials, then 256 deficiency flags, 8 pass flags and the |E|^2 block sums.
+struct CqWork {
+  double2 *G, *Z, *R1, *R2, *P, *Q, *Y, *P1, *Q1, *part;
+  int* deficient;
+  int* flags;
+  float* epsp;
+};
+
+CqWork cq_work(void* work, int nu, const CqLayout& L) {
+  CqWork w;
+  double2* p = reinterpret_cast<double2*>(work);
+  const size_t m = (size_t)nu * nu;
+  w.G = p; w.Z = p + m; w.R1 = p + 2 * m; w.R2 = p + 3 * m; w.P = p + 4 * m; w.Q = p + 5 * m;
+  w.Y = p + 6 * m; w.P1 = p + 7 * m; w.Q1 = p + 8 * m; w.part = p + 9 * m;
+  w.deficient = reinterpret_cast<int*>(w.part + (size_t)L.parts * m);
+  w.flags = w.deficient + 256;
+  w.epsp = reinterpret_cast<float*>(w.flags + 8);
+  return w;
+}
+
+// ||G - I||_F up to which the near-identity factor is used; its error is O(||G - I||^4)
+// (at 8e-4 it still matches the Cholesky factor to rounding)
+constexpr float kNearEps = 5e-4f;
+// ||G - I||_F up to which the first step alone is exact to rounding
+constexpr float kNearEpsSmall = 1e-5f;
+
+bem_status set_smem(bem_ctx* ctx, const void* fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return BEM_OK;
+  return cuda_check(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)bytes),
+                    "cholqr attribute");
+}
+
+// One FP64 pass V <- V R^{-1} whose Gram matrix is expected near the identity: the
+// near-identity factor, or the classic Cholesky factorisation and triangular inverse when
+// ||G - I||_F > kNearEps (flag *classic, set on the device). Everything is skipped unless
+// *gate != 0 (gate null: always runs).
+bem_status near_pass(bem_ctx* ctx, double* V_dev, int64_t ldv, int64_t n, int nu,
+                     const CqLayout& L, const CqWork& w, const int* gate, int* classic,
+                     cudaStream_t s) {
+  int* done = classic + 2;   // classic flag and its "second step not needed" companion
+  bem_status st = cuda_check(ctx, cudaMemsetAsync(classic, 0, 3 * sizeof(int), s), "cholqr flag");
+  if (st != BEM_OK) return st;
+  double2* V = reinterpret_cast<double2*>(V_dev);
+  const unsigned nb = (unsigned)L.near_blocks;
+  gram_partial_kernel<<<dim3((unsigned)L.tiles_u, (unsigned)L.parts), 256, 0, s>>>(
+      V, ldv, n, nu, L.rows_per_part, w.part, gate);
+  sum_parts_kernel<<<L.sum_blocks, 256, 0, s>>>(w.part, (int)L.parts, nu, w.G, gate);
+  const unsigned nt = (unsigned)((nu + kNT - 1) / kNT);
+  const dim3 tgrid(nt, nt);
+  near_tile_kernel<0><<<tgrid, 64, 0, s>>>(w.G, nullptr, nullptr, nullptr, nu, w.P, w.Q, nullptr,
+                                           w.epsp, gate, nullptr);
+  near_y1_kernel<<<nb, 64, 0, s>>>(w.G, w.P, w.Q, w.epsp, (int)(nt * nt), nu, kNearEps,
+                                   kNearEpsSmall, w.Y, w.Z, classic, done, gate);
+  const size_t chol_smem = nu <= 64 ? (size_t)nu * nu * sizeof(double2) : 0;
+  cholesky_kernel<<<1, 1024, chol_smem, s>>>(w.G, nu, ctx->d_status, nullptr, classic);
+  triangular_inverse_kernel<<<nu, 128, 0, s>>>(w.G, nu, w.Z, classic);
+  near_tile_kernel<1><<<tgrid, 64, 0, s>>>(w.G, w.Y, nullptr, nullptr, nu, w.P1, w.Q1, nullptr,
+                                           nullptr, gate, done);
+  near_tile_kernel<2><<<tgrid, 64, 0, s>>>(w.G, w.Y, w.P1, w.Q1, nu, nullptr, nullptr, w.Z,
+                                           nullptr, gate, done);
+  right_multiply_kernel<<<(unsigned)((n + kRMRows - 1) / kRMRows), 256, right_multiply_smem(nu),
+                          s>>>(V, ldv, n, nu, w.Z, gate, nullptr);
+  ctx->launches += 9;
+  return cuda_check(ctx, cudaGetLastError(), "cholqr kernels");
+}
+
+// Classic FP64 pass: Gram, Cholesky (optionally refreshing collapsed columns), inverse,
+// V <- V R^{-1}; R kept in R_out.
+bem_status classic_pass(bem_ctx* ctx, double* V_dev, int64_t ldv, int64_t n, int nu,
+                        const CqLayout& L, const CqWork& w, double2* R_out, uint64_t refresh_seed,
+                        cudaStream_t s) {
+  double2* V = reinterpret_cast<double2*>(V_dev);
+  gram_partial_kernel<<<dim3((unsigned)L.tiles_u, (unsigned)L.parts), 256, 0, s>>>(
+      V, ldv, n, nu, L.rows_per_part, w.part, nullptr);
+  sum_parts_kernel<<<L.sum_blocks, 256, 0, s>>>(w.part, (int)L.parts, nu, R_out, nullptr);
+  const size_t chol_smem = nu <= 64 ? (size_t)nu * nu * sizeof(double2) : 0;
+  cholesky_kernel<<<1, 1024, chol_smem, s>>>(R_out, nu, ctx->d_status,
+                                             refresh_seed ? w.deficient : nullptr, nullptr);
+  triangular_inverse_kernel<<<nu, 128, 0, s>>>(R_out, nu, w.Z, nullptr);
+  right_multiply_kernel<<<(unsigned)((n + kRMRows - 1) / kRMRows), 256, right_multiply_smem(nu),
+                          s>>>(V, ldv, n, nu, w.Z, nullptr, nullptr);
+  ctx->launches += 5;
+  if (refresh_seed) {
+    refresh_columns_kernel<<<(unsigned)((n * nu + 255) / 256), 256, 0, s>>>(V, ldv, n, nu,
+                                                                           w.deficient,
+                                                                           refresh_seed);
+    ctx->launches++;
+  }
+  return cuda_check(ctx, cudaGetLastError(), "cholqr kernels");
+}
+
+}  // namespace
+
+size_t cholqr2_work_bytes(bem_ctx* ctx, int64_t n, int nu) {
+  const CqLayout L = cq_layout(ctx, n, nu);
+  return (9 + (size_t)L.parts) * (size_t)nu * nu * sizeof(double2) +
+         (256 + 8) * sizeof(int) + (size_t)L.near_tiles * sizeof(float);
 }
 
 // CholeskyQR2 of V (n x nu, ld ldv) with caller-provided work (cholqr2_work_bytes);
 // asynchronous; a Gram matrix that is not positive definite is flagged in the context's
 // status word.
+//
+// Without R: the first pass runs in FP32 (nu <= 128, no refresh): it only has to make V
+// well conditioned. The FP64 second pass then sees G = I + E with small E and uses the
+// near-identity factor. If V is too ill-conditioned for FP32 the first pass leaves V alone
+// (device flag) and a third pass runs (its kernels return at once otherwise); the second
+// pass then falls back to the classic factorisation by itself. With R: two classic passes
+// and R = R2 R1.
 bem_status cholqr2_impl(bem_ctx* ctx, double* V_dev, int64_t n, int64_t ldv, int nu,
                         double* R_dev, void* work, cudaStream_t s, uint64_t refresh_seed) {
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  const int tiles = ((nu + kGT - 1) / kGT) * ((nu + kGT - 1) / kGT);
-  int64_t parts = std::max<int64_t>(1, std::min<int64_t>((n + 63) / 64,
-                                                         (2 * (int64_t)sms + tiles - 1) / tiles));
-  const int64_t rows_per_part = (n + parts - 1) / parts;
-  parts = (n + rows_per_part - 1) / rows_per_part;
-  double2* G = reinterpret_cast<double2*>(work);
-  double2* Rinv = G + (size_t)nu * nu;
-  double2* R1 = Rinv + (size_t)nu * nu;
-  double2* R2 = R1 + (size_t)nu * nu;
-  double2* part = R2 + (size_t)nu * nu;
-  int* deficient = reinterpret_cast<int*>(part + (size_t)parts * nu * nu);
+  const CqLayout L = cq_layout(ctx, n, nu);
+  const CqWork w = cq_work(work, nu, L);
   bem_status st = BEM_OK;
   const size_t chol_smem = nu <= 64 ? (size_t)nu * nu * sizeof(double2) : 0;
-  if (chol_smem > 48 * 1024) {
-    st = cuda_check(ctx, cudaFuncSetAttribute(cholesky_kernel,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)chol_smem),
-                    "cholqr attribute");
-    if (st != BEM_OK) return st;
-  }
-  // first pass in FP32 when its factor is not needed: it only has to make V well
-  // conditioned; the FP64 second pass sets the final orthogonality. If V is too ill-
-  // conditioned for FP32 the FP32 pass leaves V alone (device flag) and a third, FP64,
-  // pass runs in its place (its kernels return at once otherwise).
-  const bool fp32_first = R_dev == nullptr && refresh_seed == 0 && nu <= 128;
-  int* fallback = deficient + 256;
-  if (fp32_first) {
-    st = cuda_check(ctx, cudaFuncSetAttribute(cholesky32_kernel,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)(nu * nu * sizeof(float2))),
-                    "cholqr attribute");
-    if (st != BEM_OK) return st;
-    st = cuda_check(ctx, cudaMemsetAsync(fallback, 0, sizeof(int), s), "cholqr flag");
-    if (st != BEM_OK) return st;
-  }
-  const int passes = fp32_first ? 3 : 2;
-  for (int pass = 0; pass < passes; ++pass) {
-    // FP32 pass (fp32_first, pass 0); FP64 passes; the third pass only if flagged
-    double2* R = pass == 0 ? R1 : R2;
-    const bool low = fp32_first && pass == 0;
-    const int* gate = (fp32_first && pass == 2) ? fallback : nullptr;
-    const dim3 ggrid((unsigned)tiles, (unsigned)parts);
-    if (low)
-      gram_partial32_kernel<<<ggrid, 256, 0, s>>>(reinterpret_cast<const double2*>(V_dev), ldv, n,
-                                                  nu, rows_per_part, part);
-    else
-      gram_partial_kernel<<<ggrid, 256, 0, s>>>(reinterpret_cast<const double2*>(V_dev), ldv, n,
-                                                nu, rows_per_part, part, gate);
-    sum_parts_kernel<<<(unsigned)(((int64_t)nu * nu + 255) / 256), 256, 0, s>>>(
-        part, (int)parts, (int64_t)nu * nu, R, gate);
-    const bool refresh = refresh_seed != 0 && pass == 0;
-    if (low) {
-      cholesky32_kernel<<<1, 1024, nu * nu * sizeof(float2), s>>>(R, nu, fallback);
-      triangular_inverse32_kernel<<<nu, 128, 0, s>>>(R, nu, Rinv, fallback);
-    } else {
-      cholesky_kernel<<<1, 1024, chol_smem, s>>>(R, nu, ctx->d_status,
-                                                 refresh ? deficient : nullptr, gate);
-      triangular_inverse_kernel<<<nu, 128, 0, s>>>(R, nu, Rinv, gate);
-    }
-    right_multiply_kernel<<<(unsigned)((n + kRows - 1) / kRows), 256, 0, s>>>(
-        reinterpret_cast<double2*>(V_dev), ldv, n, nu, Rinv, gate, low ? fallback : nullptr);
-    ctx->launches += 5;
-    if (refresh) {
-      refresh_columns_kernel<<<(unsigned)((n * nu + 255) / 256), 256, 0, s>>>(
-          reinterpret_cast<double2*>(V_dev), ldv, n, nu, deficient, refresh_seed);
-      ctx->launches++;
-    }
-    st = cuda_check(ctx, cudaGetLastError(), "cholqr kernels");
-    if (st != BEM_OK) return st;
-  }
+  if ((st = set_smem(ctx, (const void*)cholesky_kernel, chol_smem)) != BEM_OK) return st;
+  if ((st = set_smem(ctx, (const void*)right_multiply_kernel, right_multiply_smem(nu))) != BEM_OK)
+    return st;
   if (R_dev) {
-    upper_product_kernel<<<1, 256, 0, s>>>(R2, R1, nu, reinterpret_cast<double2*>(R_dev));
+    if ((st = classic_pass(ctx, V_dev, ldv, n, nu, L, w, w.R1, refresh_seed, s)) != BEM_OK) return st;
+    if ((st = classic_pass(ctx, V_dev, ldv, n, nu, L, w, w.R2, 0, s)) != BEM_OK) return st;
+    upper_product_kernel<<<1, 256, 0, s>>>(w.R2, w.R1, nu, reinterpret_cast<double2*>(R_dev));
     ctx->launches++;
-    st = cuda_check(ctx, cudaGetLastError(), "cholqr kernels");
+    return cuda_check(ctx, cudaGetLastError(), "cholqr kernels");
   }
-  (void)G;
-  return st;
+  const bool fp32_first = refresh_seed == 0 && nu <= 128;
+  if (!fp32_first) {
+    if ((st = classic_pass(ctx, V_dev, ldv, n, nu, L, w, w.R1, refresh_seed, s)) != BEM_OK) return st;
+    return near_pass(ctx, V_dev, ldv, n, nu, L, w, nullptr, w.flags + 1, s);
+  }
+  int* fallback = w.flags;
+  const size_t ci_smem = (size_t)nu * nu * sizeof(float2);
+  if ((st = set_smem(ctx, (const void*)chol_inv32_kernel<4>, ci_smem)) != BEM_OK ||
+      (st = set_smem(ctx, (const void*)chol_inv32_kernel<16>, ci_smem)) != BEM_OK)
+    return st;
+  st = cuda_check(ctx, cudaMemsetAsync(fallback, 0, sizeof(int), s), "cholqr flag");
+  if (st != BEM_OK) return st;
+  double2* V = reinterpret_cast<double2*>(V_dev);
+  gram_partial32_kernel<<<dim3((unsigned)L.tiles_u, (unsigned)L.parts), 256, 0, s>>>(
+      V, ldv, n, nu, L.rows_per_part, w.part);
+  sum_parts_kernel<<<L.sum_blocks, 256, 0, s>>>(w.part, (int)L.parts, nu, w.G, nullptr);
+  if (nu <= 64)
+    chol_inv32_kernel<4><<<1, 1024, ci_smem, s>>>(w.G, nu, w.Z, fallback);
+  else
+    chol_inv32_kernel<16><<<1, 1024, ci_smem, s>>>(w.G, nu, w.Z, fallback);
+  right_multiply_kernel<<<(unsigned)((n + kRMRows - 1) / kRMRows), 256, right_multiply_smem(nu),
+                          s>>>(V, ldv, n, nu, w.Z, nullptr, fallback);
+  ctx->launches += 4;
+  if ((st = cuda_check(ctx, cudaGetLastError(), "cholqr kernels")) != BEM_OK) return st;
+  if ((st = near_pass(ctx, V_dev, ldv, n, nu, L, w, nullptr, w.flags + 1, s)) != BEM_OK) return st;
+  return near_pass(ctx, V_dev, ldv, n, nu, L, w, fallback, w.flags + 4, s);
 }
 
 }  // namespace bem

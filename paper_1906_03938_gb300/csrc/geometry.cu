@@ -71,6 +71,16 @@ __global__ void geometry_kernel(Geometry g, Rule7 rule, int* status) {
                               e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2]),
                          e3[0] * e3[0] + e3[1] * e3[1] + e3[2] * e3[2]);
   if (!(area > 1e-12 * l2) || !isfinite(area)) atomicOr(status, kStatusZeroArea);
+  if (g.diam) {
+    // panel diameter for the near-field criterion, rounded step by step (no fused
+    // operations) so that the criterion is decided exactly as written
+    double len2[3];
+    const double* ed[3] = {e1, e2, e3};
+    for (int t = 0; t < 3; ++t)
+      len2[t] = __dadd_rn(__dadd_rn(__dmul_rn(ed[t][0], ed[t][0]), __dmul_rn(ed[t][1], ed[t][1])),
+                          __dmul_rn(ed[t][2], ed[t][2]));
+    g.diam[l] = fmax(fmax(sqrt(len2[0]), sqrt(len2[1])), sqrt(len2[2]));
+  }
   const int64_t n = g.n;
   for (int c = 0; c < 3; ++c) {
     const double x = (v[0][c] + v[1][c] + v[2][c]) / 3.0;
@@ -101,15 +111,28 @@ __global__ void geometry_kernel(Geometry g, Rule7 rule, int* status) {
     }
   }
   if (g.edge32) {
-    // node-independent edge data of the self term, once per panel
+    // node-independent edge data of the FP32 self term, once per panel: the vertex offsets
+    // from the centroid are formed in FP64, the rest in FP32 (the FP32 table needs no more)
     double x[3];
     for (int c = 0; c < 3; ++c) x[c] = (v[0][c] + v[1][c] + v[2][c]) / 3.0;
+    float o[3][3];
+    for (int e = 0; e < 3; ++e)
+      for (int c = 0; c < 3; ++c) o[e][c] = (float)(v[e][c] - x[c]);
     for (int e = 0; e < 3; ++e) {
-      double d, up, uq;
-      self_edge(v, x, e, d, up, uq);
-      g.edge32[(3 * e + 0) * n + l] = (float)d;
-      g.edge32[(3 * e + 1) * n + l] = (float)up;
-      g.edge32[(3 * e + 2) * n + l] = (float)uq;
+      const float* p = o[e];
+      const float* q = o[(e + 1) % 3];
+      float tx = q[0] - p[0], ty = q[1] - p[1], tz = q[2] - p[2];
+      const float il = rsqrtf(tx * tx + ty * ty + tz * tz);
+      tx *= il;
+      ty *= il;
+      tz *= il;
+      const float sp = p[0] * tx + p[1] * ty + p[2] * tz;
+      const float sq = q[0] * tx + q[1] * ty + q[2] * tz;
+      const float fx = p[0] - sp * tx, fy = p[1] - sp * ty, fz = p[2] - sp * tz;
+      const float d = sqrtf(fx * fx + fy * fy + fz * fz);
+      g.edge32[(3 * e + 0) * n + l] = d;
+      g.edge32[(3 * e + 1) * n + l] = asinhf(sp / d);
+      g.edge32[(3 * e + 2) * n + l] = asinhf(sq / d);
     }
   }
 }
@@ -144,28 +167,101 @@ __global__ void self_term_kernel(Geometry g, int N, const double* z, GL16 gl, do
   self[2 * (j * g.n + l) + 1] = a.y;
 }
 
-// FP32 table for the mixed path, one warp per (panel l, node j): the 96 angular nodes
-// (3 edges x 2 sides x 16) are spread over the lanes and summed by a fixed shuffle tree.
-__global__ void self_term32_kernel(Geometry g, int N, const double* z, GL16 gl, float* self32) {
-  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+// Moments of the FP32 self term. With f_g = half * w_g * d the angular weight of node g and
+// R_g = d cosh(u_g) its radius, A_ll(k) = (1/4 pi) sum_g f_g h(i k R_g) and
+// h(w) = sum_m w^m / (m + 1)!, so A_ll(k) = sum_m (i k rho)^m c_m with
+// c_m = (1/4 pi) sum_g f_g (R_g / rho)^m / (m + 1)!, rho the panel's largest centroid-to-
+// vertex distance (so R_g / rho <= 1 and c_m <= c_0 / (m + 1)!). The moments depend on the
+// panel only; each node then costs one polynomial evaluation. One warp per panel; lane L
+// takes the angular nodes L, L + 32, L + 64 and the sums are combined by a fixed shuffle tree.
+__global__ void self_moments32_kernel(Geometry g, GL16 gl) {
+  const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
   const int lane = threadIdx.x % 32;
-  if (wid >= g.n * (int64_t)N) return;
-  const int64_t l = wid % g.n;
-  const int j = (int)(wid / g.n);
+  if (l >= g.n) return;
   float d3[3], up3[3], uq3[3];
+  float rho = 0.f;
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
     d3[e] = g.edge32[(3 * e + 0) * g.n + l];
     up3[e] = g.edge32[(3 * e + 1) * g.n + l];
     uq3[e] = g.edge32[(3 * e + 2) * g.n + l];
+    rho = fmaxf(rho, d3[e] * coshf(fmaxf(fabsf(up3[e]), fabsf(uq3[e]))));
   }
-  float2 a = self_term32_part(d3, up3, uq3, (float)z[2 * j], (float)z[2 * j + 1], gl, lane, 32);
+  const float irho = 1.f / rho;
+  float c[kSelfMoments];
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    a.x += __shfl_xor_sync(0xffffffffu, a.x, off);
-    a.y += __shfl_xor_sync(0xffffffffu, a.y, off);
+  for (int m = 0; m < kSelfMoments; ++m) c[m] = 0.f;
+  for (int t = lane; t < 96; t += 32) {
+    const int e = t / 32, side = (t / 16) % 2, gi = t % 16;
+    const float d = d3[e], up = up3[e], uq = uq3[e];
+    const bool split = up < 0.f && uq > 0.f;   // the foot of the perpendicular inside the edge
+    if (!split && side == 1) continue;
+    const float lo = split ? (side == 0 ? up : 0.f) : up;
+    const float hi = split ? (side == 0 ? 0.f : uq) : uq;
+    const float half = 0.5f * (hi - lo), mid = 0.5f * (hi + lo);
+    const float r = d * coshf(mid + half * (float)gl.x[gi]) * irho;
+    float term = half * (float)gl.w[gi] * d;   // f_g (R / rho)^m / (m + 1)! at m = 0
+#pragma unroll
+    for (int m = 0; m < kSelfMoments; ++m) {
+      c[m] += term;
+      term *= r * (1.f / (float)(m + 2));
+    }
   }
-  if (lane == 0) reinterpret_cast<float2*>(self32)[(int64_t)j * g.n + l] = a;
+  const float inv4pi = (float)(1.0 / (4.0 * kPiD));
+#pragma unroll
+  for (int m = 0; m < kSelfMoments; ++m) {
+    float v = c[m];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == m) g.mom32[(int64_t)m * g.n + l] = v * inv4pi;
+  }
+  if (lane == 0) g.rho32[l] = rho;
+}
+
+// |i k rho| up to which the FP32 self term is summed from the moments: the terms of the
+// series grow to about e^x / x before they decay, so at x = 3.5 the sum loses about one
+// decimal digit to cancellation, still far below the mixed path's ~1e-5 level. Beyond it
+// (panels large against the wavelength) the angular quadrature is summed directly.
+constexpr float kMomentReach = 3.5f;
+
+// FP32 table for the mixed path, one thread per (panel l, node j): the moment series in
+// i k rho by Horner's rule, truncated where x^M / (M + 1)! < 1.5e-8 (x = |k| rho), or the
+// 96-node angular quadrature directly when x > kMomentReach or no moments exist.
+__global__ void self_term32_kernel(Geometry g, int N, const double* z, GL16 gl, float* self32) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= g.n * (int64_t)N) return;
+  const int64_t l = t % g.n;
+  const int j = (int)(t / g.n);
+  const float kr = (float)z[2 * j], ki = (float)z[2 * j + 1];
+  float2 out;
+  const float rho = g.mom32 ? g.rho32[l] : 0.f;
+  const float wr = -ki * rho, wi = kr * rho;   // i k rho
+  const float x = sqrtf(wr * wr + wi * wi);
+  if (g.mom32 && x <= kMomentReach) {
+    int M = 1;
+    float bound = 0.5f * x;   // x^M / (M + 1)!
+    while (M < kSelfMoments && bound > 1.5e-8f) {
+      ++M;
+      bound *= x / (float)(M + 1);
+    }
+    float sr = g.mom32[(int64_t)(M - 1) * g.n + l], si = 0.f;
+    for (int m = M - 2; m >= 0; --m) {
+      const float nr = sr * wr - si * wi + g.mom32[(int64_t)m * g.n + l];
+      si = sr * wi + si * wr;
+      sr = nr;
+    }
+    out = make_float2(sr, si);
+  } else {
+    float d3[3], up3[3], uq3[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      d3[e] = g.edge32[(3 * e + 0) * g.n + l];
+      up3[e] = g.edge32[(3 * e + 1) * g.n + l];
+      uq3[e] = g.edge32[(3 * e + 2) * g.n + l];
+    }
+    out = self_term32_part(d3, up3, uq3, kr, ki, gl, 0, 1);
+  }
+  reinterpret_cast<float2*>(self32)[(int64_t)j * g.n + l] = out;
 }
 
 }  // namespace
@@ -173,8 +269,15 @@ __global__ void self_term32_kernel(Geometry g, int N, const double* z, GL16 gl, 
 cudaError_t launch_geometry(bem_ctx* ctx, cudaStream_t s) {
   static const Rule7 rule = make_rule7();
   const int64_t n = (ctx->geo.n + 15) / 16 * 16;   // padding panels of the packed array too
-  geometry_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctx->geo, rule, ctx->d_status);
+  // one thread per panel in 32-thread blocks: the FP64 work per panel is long and FP64
+  // issue is slow, so the panels are spread over as many SMs as possible
+  geometry_kernel<<<(unsigned)((n + 31) / 32), 32, 0, s>>>(ctx->geo, rule, ctx->d_status);
   ctx->launches++;
+  if (ctx->geo.mom32) {
+    static const GL16 gl = make_gl16();
+    self_moments32_kernel<<<(unsigned)((32 * ctx->geo.n + 255) / 256), 256, 0, s>>>(ctx->geo, gl);
+    ctx->launches++;
+  }
   return cudaGetLastError();
 }
 
@@ -189,7 +292,7 @@ cudaError_t launch_contour(bem_ctx* ctx, cudaStream_t s) {
 cudaError_t launch_self_terms32(bem_ctx* ctx, cudaStream_t s) {
   static const GL16 gl = make_gl16();
   const int64_t total = ctx->geo.n * (int64_t)ctx->con.N;
-  self_term32_kernel<<<(unsigned)((32 * total + 255) / 256), 256, 0, s>>>(ctx->geo, ctx->con.N,
+  self_term32_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(ctx->geo, ctx->con.N,
                                                                      ctx->con.z, gl,
                                                                      ctx->con.self32);
   ctx->launches++;
@@ -199,7 +302,7 @@ cudaError_t launch_self_terms32(bem_ctx* ctx, cudaStream_t s) {
 cudaError_t launch_self32(bem_ctx* ctx, int nk, const double* kz, float* out, cudaStream_t s) {
   static const GL16 gl = make_gl16();
   const int64_t total = ctx->geo.n * (int64_t)nk;
-  self_term32_kernel<<<(unsigned)((32 * total + 255) / 256), 256, 0, s>>>(ctx->geo, nk, kz, gl, out);
+  self_term32_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(ctx->geo, nk, kz, gl, out);
   ctx->launches++;
   return cudaGetLastError();
 }

@@ -18,6 +18,9 @@ constexpr int kMaxTimed = 256;
 // Contour nodes the dense / matrix-free FP32 solver kernels accept.
 constexpr int kMaxNodesSolve = 64;
 
+// Terms kept of the Taylor expansion of the FP32 self term in i k rho.
+constexpr int kSelfMoments = 24;
+
 // Bits of the device status word.
 enum : int {
   kStatusBadIndex = 1,     // a triangle references a vertex out of range
@@ -45,6 +48,10 @@ struct Geometry {
   float* qw32 = nullptr;
   float* edge32 = nullptr; // 9 n, optional: self-term edge data (d, u_p, u_q per edge) at
                            // (3 e + f) * n + l, for the FP32 self terms of the mixed path
+  double* diam = nullptr;  // optional, n: panel diameter (longest edge), FP64
+  float* mom32 = nullptr;  // optional, kSelfMoments * n: moments of the FP32 self term at
+                           // m * n + l (see self_moments32_kernel)
+  float* rho32 = nullptr;  // optional, n: largest centroid-to-vertex distance of panel l
   float* pack32 = nullptr; // optional, 64 floats per panel, rows padded to a multiple of 16
                            // panels: 7 x (x_hi, y_hi, z_hi, w) then 7 x (x_lo, y_lo, z_lo, 0)
                            // (hi + lo = the FP64 quadrature point; w = W_lq / 4 pi)
@@ -87,6 +94,19 @@ struct bem_ctx {
   bool timing = false;              // record events around the main projection kernel
   std::vector<cudaEvent_t> ev;      // 2 * kMaxTimed events (start, stop)
   int n_timed = 0;
+  // near field: mode (0 off, 1 64-point rule, 2 surrogate network) and the pair list (CSR)
+  int near_mode = 0;
+  int64_t near_mesh_version = -1;   // mesh the list was built for
+  int64_t near_nnz = 0;
+  int32_t* d_near_ptr = nullptr;    // n + 1
+  int32_t* d_near_cols = nullptr;   // nnz
+  int64_t near_cap_n = 0, near_cap_nnz = 0;
+  void* d_near_work = nullptr;      // row-major copy of the basis for the near products
+  size_t near_work_bytes = 0;
+  // surrogate network of the near field (weights on the device, see surrogate.cu)
+  float* d_net = nullptr;
+  int64_t net_floats = 0;
+  bool net_ready = false;
 };
 
 namespace bem {
@@ -149,6 +169,24 @@ cudaError_t launch_xhy_fp64(bem_ctx* ctx, const double* X, int64_t ldx, int p, c
 size_t cholqr2_work_bytes(bem_ctx* ctx, int64_t n, int nu);
 bem_status cholqr2_impl(bem_ctx* ctx, double* V, int64_t n, int64_t ldv, int nu, double* R,
                         void* work, cudaStream_t s, uint64_t refresh_seed);
+// Near field (near.cu). near_active: a mode is set and the pair list is current (build it
+// with ensure_near first).
+bem_status ensure_near(bem_ctx* ctx, cudaStream_t s);
+inline bool near_active(const bem_ctx* ctx) {
+  return ctx->near_mode != 0 && ctx->near_mesh_version == ctx->mesh_version;
+}
+// Y_j += (A_near - A_7)(z_j) V over the near pairs, FP64 (Y node-major, leading dim. n).
+bem_status near_apply64(bem_ctx* ctx, const double* V, int64_t ldv, int nu, double* Y,
+                        cudaStream_t s);
+// The same correction in FP32 into slice `slice` of the mixed path's partial products
+// (layout [slice][N][2 nup][n_pad], basis column b at (b / C) 2C + b % C, imaginary part C
+// further); V32 is the FP32 copy of V (column-major, leading dimension n). Every row and
+// column of the slice is written.
+bem_status near_apply32(bem_ctx* ctx, const float2* V32, int nu, int nup, int C, int n_pad,
+                        float* Yp, int slice, cudaStream_t s);
+// R[:, c] += (A_near - A_7)(lam_c) X[:, c] (deriv: the k-derivatives), FP64.
+cudaError_t launch_near_percol64(bem_ctx* ctx, int m, const double* lam_dev, const double* X,
+                                 int64_t ldx, double* R, bool deriv, cudaStream_t s);
 // mixed-precision fused projection (tcgen05); defined in project_mixed.cu
 bem_status project_mixed(bem_ctx* ctx, const double* V, int64_t ldv, int nu, double* Bhat,
                          double* AV, cudaStream_t s);

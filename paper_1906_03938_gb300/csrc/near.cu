@@ -1,0 +1,612 @@
+// Near field: a finer rule on panel pairs close to each other.
+//
+// The 7-point rule (Section 1's Gauss quadrature of the regular integrals) loses accuracy
+// when the collocation point x_i is close to panel l. A pair (i, l), i != l, is near when
+// the centroid distance is below twice the larger panel diameter (longest edge); its entry
+// is then the 8 x 8 conical-product rule: the triangle (a, b, c) is the image of the unit
+// square under y = a + s (b - a) + s t (c - b) (Jacobian 2 |T| s), with Gauss-Legendre in s
+// and t, collapsed at the vertex nearest x_i (the first in the triangle's order on a tie).
+// The matrix-free kernels keep the 7-point rule everywhere; the near pairs are corrected by
+// (A_near - A_7) applied as a sparse matrix, which is what this file provides:
+//   * the pair list (CSR, columns increasing within a row), decided in FP64 with the
+//     criterion rounded step by step exactly as written, after an FP32 prefilter;
+//   * Y_j += C(z_j) V for the FP64 projection, the same in FP32 into a slice of the mixed
+//     path's partial products (optionally from the surrogate network), and
+//     R[:, c] += C(lam_c) X[:, c] (values or k-derivatives) for residuals and refinement.
+// One warp per (row, node) or (row, column): its lanes evaluate the row's pair corrections,
+// then sweep the basis columns with them (fixed order: deterministic).
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+#include "surrogate.cuh"
+
+namespace bem {
+namespace {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+struct GL8 {
+  double x[8];   // nodes on [0, 1]
+  double w[8];
+};
+
+// Gauss-Legendre nodes as the roots of P_8 (Newton's method on the three-term recurrence),
+// mapped to [0, 1].
+GL8 make_gl8() {
+  GL8 g;
+  const int n = 8;
+  for (int i = 0; i < n; ++i) {
+    double x = cos(kPi * (4.0 * i + 3.0) / (4.0 * n + 2.0));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double pm = 1.0, p = x;
+      for (int k = 1; k < n; ++k) {
+        const double pn = ((2 * k + 1) * x * p - k * pm) / (k + 1);
+        pm = p;
+        p = pn;
+      }
+      dp = n * (pm - x * p) / (1.0 - x * x);
+      const double step = p / dp;
+      x -= step;
+      if (fabs(step) <= 1e-17) break;
+    }
+    double pm = 1.0, p = x;
+    for (int k = 1; k < n; ++k) {
+      const double pn = ((2 * k + 1) * x * p - k * pm) / (k + 1);
+      pm = p;
+      p = pn;
+    }
+    dp = n * (pm - x * p) / (1.0 - x * x);
+    g.x[i] = 0.5 * (x + 1.0);
+    g.w[i] = 0.5 * 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+  return g;
+}
+
+// |a - b| rounded step by step (no fused operations)
+__device__ __forceinline__ double dist_rn(const double a[3], const double b[3]) {
+  const double dx = __dsub_rn(a[0], b[0]), dy = __dsub_rn(a[1], b[1]), dz = __dsub_rn(a[2], b[2]);
+  return sqrt(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+}
+
+constexpr int kScanTile = 256;
+
+// Near pairs of every row: counts (cols == nullptr) or the columns themselves at
+// row_ptr[i] in increasing order. One thread per row; the columns' centroids and
+// diameters are staged through shared memory, first tested in FP32 with a margin, then
+// exactly in FP64.
+__global__ void __launch_bounds__(kScanTile)
+near_scan_kernel(Geometry g, int32_t* __restrict__ counts, const int32_t* __restrict__ row_ptr,
+                 int32_t* __restrict__ cols) {
+  __shared__ float4 sc[kScanTile];
+  const int64_t n = g.n;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double xi[3] = {0.0, 0.0, 0.0};
+  double hi = 0.0;
+  if (i < n) {
+    for (int c = 0; c < 3; ++c) xi[c] = g.cx[c * n + i];
+    hi = g.diam[i];
+  }
+  const float fx = (float)xi[0], fy = (float)xi[1], fz = (float)xi[2], fh = (float)hi;
+  int32_t cnt = 0;
+  const int64_t base = (cols && i < n) ? row_ptr[i] : 0;
+  for (int64_t l0 = 0; l0 < n; l0 += kScanTile) {
+    __syncthreads();
+    const int64_t lt = l0 + threadIdx.x;
+    sc[threadIdx.x] = lt < n ? make_float4((float)g.cx[lt], (float)g.cx[n + lt],
+                                           (float)g.cx[2 * n + lt], (float)g.diam[lt])
+                             : make_float4(3e30f, 3e30f, 3e30f, 0.f);
+    __syncthreads();
+    if (i >= n) continue;
+    const int lim = (int)(n - l0 < kScanTile ? n - l0 : kScanTile);
+    for (int t = 0; t < lim; ++t) {
+      const float4 c = sc[t];
+      const float dx = fx - c.x, dy = fy - c.y, dz = fz - c.z;
+      const float hm = fmaxf(fh, c.w);
+      if (dx * dx + dy * dy + dz * dz > 4.02f * hm * hm + 1e-30f) continue;
+      const int64_t l = l0 + t;
+      if (l == i) continue;
+      const double xl[3] = {g.cx[l], g.cx[n + l], g.cx[2 * n + l]};
+      if (dist_rn(xi, xl) < 2.0 * fmax(hi, g.diam[l])) {
+        if (cols) cols[base + cnt] = (int32_t)l;
+        ++cnt;
+      }
+    }
+  }
+  if (i < n && !cols) counts[i] = cnt;
+}
+
+// The 8 x 8 rule's frame for panel l seen from x: collapsed vertex a (nearest x), the two
+// edge vectors and 2 |T| / (4 pi).
+struct NearFrame {
+  double a[3], ab[3], bc[3];
+  double scale;
+};
+
+__device__ void near_frame(const Geometry& g, int64_t l, const double x[3], NearFrame& F) {
+  double v[3][3];
+  for (int e = 0; e < 3; ++e) {
+    const int32_t vi = g.tri[3 * l + e];
+    for (int c = 0; c < 3; ++c) v[e][c] = g.xyz[3 * (int64_t)vi + c];
+  }
+  int a = 0;
+  double best = dist_rn(v[0], x);
+  for (int q = 1; q < 3; ++q) {
+    const double r = dist_rn(v[q], x);
+    if (r < best) {
+      best = r;
+      a = q;
+    }
+  }
+  const double* A = v[a];
+  const double* B = v[(a + 1) % 3];
+  const double* C = v[(a + 2) % 3];
+  for (int c = 0; c < 3; ++c) {
+    F.a[c] = A[c];
+    F.ab[c] = B[c] - A[c];
+    F.bc[c] = C[c] - B[c];
+  }
+  const double nx = F.ab[1] * F.bc[2] - F.ab[2] * F.bc[1];
+  const double ny = F.ab[2] * F.bc[0] - F.ab[0] * F.bc[2];
+  const double nz = F.ab[0] * F.bc[1] - F.ab[1] * F.bc[0];
+  F.scale = sqrt(nx * nx + ny * ny + nz * nz) / (4.0 * kPi);
+}
+
+// kernel value e^{ikr}/r (deriv: i e^{ikr}) times w, added to acc
+__device__ __forceinline__ void add_kernel64(double2& acc, double w, double r, double kr,
+                                             double ki, bool deriv) {
+  double s, c;
+  sincos(kr * r, &s, &c);
+  const double amp = deriv ? w * exp(-ki * r) : w * exp(-ki * r) / r;
+  if (deriv) {
+    acc.x -= amp * s;
+    acc.y += amp * c;
+  } else {
+    acc.x += amp * c;
+    acc.y += amp * s;
+  }
+}
+
+// (A_near - A_7)(k) of the pair (x, l), FP64; deriv: its k-derivative.
+__device__ double2 near_corr64(const Geometry& g, int64_t l, const double x[3], double kr,
+                               double ki, bool deriv, const GL8& gl) {
+  NearFrame F;
+  near_frame(g, l, x, F);
+  double2 acc = make_double2(0.0, 0.0);
+  for (int p = 0; p < 8; ++p) {
+    const double sp = gl.x[p];
+    for (int q = 0; q < 8; ++q) {
+      const double st = sp * gl.x[q];
+      const double y0 = F.a[0] + sp * F.ab[0] + st * F.bc[0];
+      const double y1 = F.a[1] + sp * F.ab[1] + st * F.bc[1];
+      const double y2 = F.a[2] + sp * F.ab[2] + st * F.bc[2];
+      const double dx = x[0] - y0, dy = x[1] - y1, dz = x[2] - y2;
+      add_kernel64(acc, gl.w[p] * gl.w[q] * sp * F.scale, sqrt(dx * dx + dy * dy + dz * dz), kr,
+                   ki, deriv);
+    }
+  }
+  const int64_t n = g.n;
+  for (int q = 0; q < 7; ++q) {
+    const double dx = x[0] - g.qp[q * n + l], dy = x[1] - g.qp[(7 + q) * n + l],
+                 dz = x[2] - g.qp[(14 + q) * n + l];
+    add_kernel64(acc, -g.qw[q * n + l], sqrt(dx * dx + dy * dy + dz * dz), kr, ki, deriv);
+  }
+  return acc;
+}
+
+// Canonical features of the pair for the surrogate network: the frame has its origin at
+// x, e1 along (b - a), e3 along the normal (b - a) x (c - b) flipped so that a lies on its
+// non-negative side, e2 = e3 x e1; the three vertices in that frame divided by the
+// panel's diameter h, then Re(k h), Im(k h).
+__device__ void near_features32(const Geometry& g, int64_t l, const NearFrame& F, const double x[3],
+                                float kr, float ki, float feat[kNetIn]) {
+  const double h = g.diam[l];
+  double e1[3] = {F.ab[0], F.ab[1], F.ab[2]};
+  double n1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+  for (int c = 0; c < 3; ++c) e1[c] /= n1;
+  double e3[3] = {F.ab[1] * F.bc[2] - F.ab[2] * F.bc[1], F.ab[2] * F.bc[0] - F.ab[0] * F.bc[2],
+                  F.ab[0] * F.bc[1] - F.ab[1] * F.bc[0]};
+  double n3 = sqrt(e3[0] * e3[0] + e3[1] * e3[1] + e3[2] * e3[2]);
+  for (int c = 0; c < 3; ++c) e3[c] /= n3;
+  const double ax[3] = {F.a[0] - x[0], F.a[1] - x[1], F.a[2] - x[2]};
+  if (ax[0] * e3[0] + ax[1] * e3[1] + ax[2] * e3[2] < 0.0)
+    for (int c = 0; c < 3; ++c) e3[c] = -e3[c];
+  const double e2[3] = {e3[1] * e1[2] - e3[2] * e1[1], e3[2] * e1[0] - e3[0] * e1[2],
+                        e3[0] * e1[1] - e3[1] * e1[0]};
+  double p[3][3];
+  for (int c = 0; c < 3; ++c) {
+    p[0][c] = ax[c];
+    p[1][c] = ax[c] + F.ab[c];
+    p[2][c] = ax[c] + F.ab[c] + F.bc[c];
+  }
+  for (int v = 0; v < 3; ++v) {
+    feat[3 * v + 0] = (float)((p[v][0] * e1[0] + p[v][1] * e1[1] + p[v][2] * e1[2]) / h);
+    feat[3 * v + 1] = (float)((p[v][0] * e2[0] + p[v][1] * e2[1] + p[v][2] * e2[2]) / h);
+    feat[3 * v + 2] = (float)((p[v][0] * e3[0] + p[v][1] * e3[1] + p[v][2] * e3[2]) / h);
+  }
+  feat[9] = (float)(kr * h);
+  feat[10] = (float)(ki * h);
+}
+
+// (A_near - A_7)(k) of the pair, FP32 with coordinates relative to x (formed in FP64), or
+// from the surrogate network when net is non-null (the 7-point part is then h times its
+// output's complement: the network predicts the whole correction divided by h).
+__device__ float2 near_corr32(const Geometry& g, int64_t l, const double x[3], float kr,
+                              float ki, const GL8& gl, const float* __restrict__ net) {
+  NearFrame F;
+  near_frame(g, l, x, F);
+  if (net) {
+    float feat[kNetIn];
+    near_features32(g, l, F, x, kr, ki, feat);
+    const float2 o = surrogate_eval(net, feat);
+    const float h = (float)g.diam[l];
+    return make_float2(o.x * h, o.y * h);
+  }
+  const float ax = (float)(F.a[0] - x[0]), ay = (float)(F.a[1] - x[1]), az = (float)(F.a[2] - x[2]);
+  const float abx = (float)F.ab[0], aby = (float)F.ab[1], abz = (float)F.ab[2];
+  const float bcx = (float)F.bc[0], bcy = (float)F.bc[1], bcz = (float)F.bc[2];
+  const float scale = (float)F.scale;
+  float sr = 0.f, si = 0.f;
+  for (int p = 0; p < 8; ++p) {
+    const float sp = (float)gl.x[p];
+    for (int q = 0; q < 8; ++q) {
+      const float st = sp * (float)gl.x[q];
+      const float dx = ax + sp * abx + st * bcx, dy = ay + sp * aby + st * bcy,
+                  dz = az + sp * abz + st * bcz;
+      const float r = sqrtf(dx * dx + dy * dy + dz * dz);
+      float s, c;
+      sincosf(kr * r, &s, &c);
+      const float amp = (float)(gl.w[p] * gl.w[q]) * sp * scale * expf(-ki * r) / r;
+      sr += amp * c;
+      si += amp * s;
+    }
+  }
+  const int64_t n = g.n;
+  for (int q = 0; q < 7; ++q) {
+    const float dx = (float)(g.qp[q * n + l] - x[0]), dy = (float)(g.qp[(7 + q) * n + l] - x[1]),
+                dz = (float)(g.qp[(14 + q) * n + l] - x[2]);
+    const float r = sqrtf(dx * dx + dy * dy + dz * dz);
+    float s, c;
+    sincosf(kr * r, &s, &c);
+    const float amp = (float)g.qw[q * n + l] * expf(-ki * r) / r;
+    sr -= amp * c;
+    si -= amp * s;
+  }
+  return make_float2(sr, si);
+}
+
+constexpr int kMaxColGroups = kMaxNu / 32;
+
+// Y_j += C(z_j) V, FP64: one warp per (row i, node j); Vt is V row-major (nu per row).
+__global__ void __launch_bounds__(256)
+near_apply64_kernel(Geometry g, const int32_t* __restrict__ ptr, const int32_t* __restrict__ cols,
+                    const double* __restrict__ z, int N, const double2* __restrict__ Vt, int nu,
+                    double2* __restrict__ Y, GL8 gl) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x % 32;
+  const int64_t n = g.n;
+  if (w >= n * (int64_t)N) return;
+  const int64_t i = w % n;
+  const int node = (int)(w / n);
+  const double kr = z[2 * node], ki = z[2 * node + 1];
+  const double x[3] = {g.cx[i], g.cx[n + i], g.cx[2 * n + i]};
+  double2 acc[kMaxColGroups];
+#pragma unroll
+  for (int t = 0; t < kMaxColGroups; ++t) acc[t] = make_double2(0.0, 0.0);
+  const int32_t e0 = ptr[i], e1 = ptr[i + 1];
+  for (int32_t eb = e0; eb < e1; eb += 32) {
+    const int32_t e = eb + lane;
+    double2 cval = make_double2(0.0, 0.0);
+    int32_t l = 0;
+    if (e < e1) {
+      l = cols[e];
+      cval = near_corr64(g, l, x, kr, ki, false, gl);
+    }
+    const int cnt = min(32, e1 - eb);
+    for (int t = 0; t < cnt; ++t) {
+      const double cx = __shfl_sync(0xffffffffu, cval.x, t);
+      const double cy = __shfl_sync(0xffffffffu, cval.y, t);
+      const int32_t lt = __shfl_sync(0xffffffffu, l, t);
+      const double2* vr = Vt + (int64_t)lt * nu;
+#pragma unroll
+      for (int cg = 0; cg < kMaxColGroups; ++cg) {
+        const int c = lane + 32 * cg;
+        if (c < nu) {
+          const double2 v = vr[c];
+          acc[cg].x += cx * v.x - cy * v.y;
+          acc[cg].y += cx * v.y + cy * v.x;
+        }
+      }
+    }
+  }
+  if (e1 == e0) return;
+  double2* Yj = Y + (int64_t)node * n * nu;
+#pragma unroll
+  for (int cg = 0; cg < kMaxColGroups; ++cg) {
+    const int c = lane + 32 * cg;
+    if (c < nu) {
+      double2 y = Yj[(int64_t)c * n + i];
+      y.x += acc[cg].x;
+      y.y += acc[cg].y;
+      Yj[(int64_t)c * n + i] = y;
+    }
+  }
+}
+
+// Slice `slice` of the mixed path's partials := C(z_j) V in FP32 (every row < n_pad and
+// every column < nu written); one warp per (row i, node j).
+__global__ void __launch_bounds__(256)
+near_apply32_kernel(Geometry g, const int32_t* __restrict__ ptr, const int32_t* __restrict__ cols,
+                    const double* __restrict__ z, int N, const float2* __restrict__ Vt, int nu,
+                    int nup, int C, int n_pad, float* __restrict__ Yp, int slice, GL8 gl,
+                    const float* __restrict__ net) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x % 32;
+  const int64_t n = g.n;
+  if (w >= (int64_t)n_pad * N) return;
+  const int64_t i = w % n_pad;
+  const int node = (int)(w / n_pad);
+  float2 acc[kMaxColGroups];
+#pragma unroll
+  for (int t = 0; t < kMaxColGroups; ++t) acc[t] = make_float2(0.f, 0.f);
+  if (i < n) {
+    const float kr = (float)z[2 * node], ki = (float)z[2 * node + 1];
+    const double x[3] = {g.cx[i], g.cx[n + i], g.cx[2 * n + i]};
+    const int32_t e0 = ptr[i], e1 = ptr[i + 1];
+    for (int32_t eb = e0; eb < e1; eb += 32) {
+      const int32_t e = eb + lane;
+      float2 cval = make_float2(0.f, 0.f);
+      int32_t l = 0;
+      if (e < e1) {
+        l = cols[e];
+        cval = near_corr32(g, l, x, kr, ki, gl, net);
+      }
+      const int cnt = min(32, e1 - eb);
+      for (int t = 0; t < cnt; ++t) {
+        const float cx = __shfl_sync(0xffffffffu, cval.x, t);
+        const float cy = __shfl_sync(0xffffffffu, cval.y, t);
+        const int32_t lt = __shfl_sync(0xffffffffu, l, t);
+        const float2* vr = Vt + (int64_t)lt * nu;
+#pragma unroll
+        for (int cg = 0; cg < kMaxColGroups; ++cg) {
+          const int c = lane + 32 * cg;
+          if (c < nu) {
+            const float2 v = vr[c];
+            acc[cg].x += cx * v.x - cy * v.y;
+            acc[cg].y += cx * v.y + cy * v.x;
+          }
+        }
+      }
+    }
+  }
+  const int acc_cols = 2 * nup;
+  float* base = Yp + ((size_t)slice * N + node) * acc_cols * (size_t)n_pad;
+#pragma unroll
+  for (int cg = 0; cg < kMaxColGroups; ++cg) {
+    const int c = lane + 32 * cg;
+    if (c < nu) {
+      const int colr = (c / C) * 2 * C + (c % C);
+      base[(size_t)colr * n_pad + i] = acc[cg].x;
+      base[(size_t)(colr + C) * n_pad + i] = acc[cg].y;
+    }
+  }
+}
+
+// R[:, c] += C(lam_c) X[:, c] (deriv: k-derivatives); one warp per (row i, column c).
+template <bool kDeriv>
+__global__ void __launch_bounds__(256)
+near_percol64_kernel(Geometry g, const int32_t* __restrict__ ptr, const int32_t* __restrict__ cols,
+                     const double* __restrict__ lam, int m, const double2* __restrict__ X,
+                     int64_t ldx, double2* __restrict__ R, GL8 gl) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x % 32;
+  const int64_t n = g.n;
+  if (w >= n * (int64_t)m) return;
+  const int64_t i = w % n;
+  const int c = (int)(w / n);
+  const double kr = lam[2 * c], ki = lam[2 * c + 1];
+  const double x[3] = {g.cx[i], g.cx[n + i], g.cx[2 * n + i]};
+  double2 acc = make_double2(0.0, 0.0);
+  const int32_t e0 = ptr[i], e1 = ptr[i + 1];
+  for (int32_t e = e0 + lane; e < e1; e += 32) {
+    const int32_t l = cols[e];
+    const double2 cv = near_corr64(g, l, x, kr, ki, kDeriv, gl);
+    const double2 v = X[(int64_t)c * ldx + l];
+    acc.x += cv.x * v.x - cv.y * v.y;
+    acc.y += cv.x * v.y + cv.y * v.x;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+  }
+  if (lane == 0 && e1 > e0) {
+    double2 r = R[(int64_t)c * n + i];
+    r.x += acc.x;
+    r.y += acc.y;
+    R[(int64_t)c * n + i] = r;
+  }
+}
+
+// Row-major copies of the basis for the near products.
+__global__ void transpose64_kernel(const double2* __restrict__ V, int64_t ldv, int64_t n, int nu,
+                                   double2* __restrict__ Vt) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * nu) return;
+  const int64_t l = t / nu;
+  const int c = (int)(t % nu);
+  Vt[t] = V[(int64_t)c * ldv + l];
+}
+
+__global__ void transpose32_kernel(const float2* __restrict__ V32, int64_t n, int nu,
+                                   float2* __restrict__ Vt) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * nu) return;
+  const int64_t l = t / nu;
+  const int c = (int)(t % nu);
+  Vt[t] = V32[(int64_t)c * n + l];
+}
+
+const GL8& gl8() {
+  static const GL8 g = make_gl8();
+  return g;
+}
+
+bem_status ensure_near_work(bem_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->near_work_bytes) return BEM_OK;
+  cudaFree(ctx->d_near_work);
+  ctx->d_near_work = nullptr;
+  ctx->near_work_bytes = 0;
+  if (cudaMalloc(&ctx->d_near_work, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, BEM_ENOMEM, "near field: device allocation failed");
+  }
+  ctx->near_work_bytes = bytes;
+  return BEM_OK;
+}
+
+}  // namespace
+
+bem_status ensure_near(bem_ctx* ctx, cudaStream_t s) {
+  if (ctx->near_mode == 0 || ctx->near_mesh_version == ctx->mesh_version) return BEM_OK;
+  const int64_t n = ctx->geo.n;
+  if (n == 0) return fail(ctx, BEM_ESTATE, "near field: no mesh set");
+  if (n + 1 > ctx->near_cap_n) {
+    cudaFree(ctx->d_near_ptr);
+    ctx->d_near_ptr = nullptr;
+    ctx->near_cap_n = 0;
+    if (cudaMalloc(&ctx->d_near_ptr, (n + 1) * sizeof(int32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, BEM_ENOMEM, "near field: device allocation failed");
+    }
+    ctx->near_cap_n = n + 1;
+  }
+  const unsigned blocks = (unsigned)((n + kScanTile - 1) / kScanTile);
+  near_scan_kernel<<<blocks, kScanTile, 0, s>>>(ctx->geo, ctx->d_near_ptr, nullptr, nullptr);
+  ctx->launches++;
+  std::vector<int32_t> h(n + 1);
+  bem_status st = cuda_check(ctx, cudaMemcpyAsync(h.data(), ctx->d_near_ptr, n * sizeof(int32_t),
+                                                  cudaMemcpyDeviceToHost, s),
+                             "near field copy");
+  if (st == BEM_OK) st = cuda_check(ctx, cudaStreamSynchronize(s), "near field copy");
+  if (st != BEM_OK) return st;
+  int64_t total = 0;
+  for (int64_t i = 0; i < n; ++i) {   // counts -> row pointers
+    const int64_t c = h[i];
+    h[i] = (int32_t)total;
+    total += c;
+  }
+  if (total > 0x7fffffff) return fail(ctx, BEM_EINVAL, "near field: too many near pairs");
+  h[n] = (int32_t)total;
+  if (total > ctx->near_cap_nnz) {
+    cudaFree(ctx->d_near_cols);
+    ctx->d_near_cols = nullptr;
+    ctx->near_cap_nnz = 0;
+    if (cudaMalloc(&ctx->d_near_cols, std::max<int64_t>(1, total) * sizeof(int32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, BEM_ENOMEM, "near field: device allocation failed");
+    }
+    ctx->near_cap_nnz = std::max<int64_t>(1, total);
+  }
+  st = cuda_check(ctx, cudaMemcpyAsync(ctx->d_near_ptr, h.data(), (n + 1) * sizeof(int32_t),
+                                       cudaMemcpyHostToDevice, s),
+                  "near field copy");
+  if (st != BEM_OK) return st;
+  near_scan_kernel<<<blocks, kScanTile, 0, s>>>(ctx->geo, nullptr, ctx->d_near_ptr,
+                                                ctx->d_near_cols);
+  ctx->launches++;
+  st = cuda_check(ctx, cudaGetLastError(), "near field kernels");
+  if (st == BEM_OK) st = cuda_check(ctx, cudaStreamSynchronize(s), "near field build");
+  if (st != BEM_OK) return st;
+  ctx->near_nnz = total;
+  ctx->near_mesh_version = ctx->mesh_version;
+  return BEM_OK;
+}
+
+bem_status near_apply64(bem_ctx* ctx, const double* V, int64_t ldv, int nu, double* Y,
+                        cudaStream_t s) {
+  const int64_t n = ctx->geo.n;
+  bem_status st = ensure_near_work(ctx, (size_t)n * nu * sizeof(double2));
+  if (st != BEM_OK) return st;
+  double2* Vt = reinterpret_cast<double2*>(ctx->d_near_work);
+  transpose64_kernel<<<(unsigned)((n * nu + 255) / 256), 256, 0, s>>>(
+      reinterpret_cast<const double2*>(V), ldv, n, nu, Vt);
+  const int N = ctx->con.N;
+  near_apply64_kernel<<<(unsigned)((32 * n * (int64_t)N + 255) / 256), 256, 0, s>>>(
+      ctx->geo, ctx->d_near_ptr, ctx->d_near_cols, ctx->con.z, N, Vt, nu,
+      reinterpret_cast<double2*>(Y), gl8());
+  ctx->launches += 2;
+  return cuda_check(ctx, cudaGetLastError(), "near field kernels");
+}
+
+bem_status near_apply32(bem_ctx* ctx, const float2* V32, int nu, int nup, int C, int n_pad,
+                        float* Yp, int slice, cudaStream_t s) {
+  const int64_t n = ctx->geo.n;
+  bem_status st = ensure_near_work(ctx, (size_t)n * nu * sizeof(float2));
+  if (st != BEM_OK) return st;
+  float2* Vt = reinterpret_cast<float2*>(ctx->d_near_work);
+  transpose32_kernel<<<(unsigned)((n * nu + 255) / 256), 256, 0, s>>>(V32, n, nu, Vt);
+  const int N = ctx->con.N;
+  const float* net = (ctx->near_mode == 2 && ctx->net_ready) ? ctx->d_net : nullptr;
+  near_apply32_kernel<<<(unsigned)((32 * (int64_t)n_pad * N + 255) / 256), 256, 0, s>>>(
+      ctx->geo, ctx->d_near_ptr, ctx->d_near_cols, ctx->con.z, N, Vt, nu, nup, C, n_pad, Yp, slice,
+      gl8(), net);
+  ctx->launches += 2;
+  return cuda_check(ctx, cudaGetLastError(), "near field kernels");
+}
+
+cudaError_t launch_near_percol64(bem_ctx* ctx, int m, const double* lam_dev, const double* X,
+                                 int64_t ldx, double* R, bool deriv, cudaStream_t s) {
+  const int64_t n = ctx->geo.n;
+  const unsigned blocks = (unsigned)((32 * n * (int64_t)m + 255) / 256);
+  if (deriv)
+    near_percol64_kernel<true><<<blocks, 256, 0, s>>>(
+        ctx->geo, ctx->d_near_ptr, ctx->d_near_cols, lam_dev, m,
+        reinterpret_cast<const double2*>(X), ldx, reinterpret_cast<double2*>(R), gl8());
+  else
+    near_percol64_kernel<false><<<blocks, 256, 0, s>>>(
+        ctx->geo, ctx->d_near_ptr, ctx->d_near_cols, lam_dev, m,
+        reinterpret_cast<const double2*>(X), ldx, reinterpret_cast<double2*>(R), gl8());
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace bem
+
+using namespace bem;
+
+extern "C" bem_status bem_set_near_field(bem_ctx* ctx, int mode, void* stream) {
+  if (!ctx) return BEM_EINVAL;
+  if (mode < 0 || mode > 2) return fail(ctx, BEM_EINVAL, "bem_set_near_field: mode must be 0, 1 or 2");
+  if (mode == 2 && !ctx->net_ready)
+    return fail(ctx, BEM_ESTATE, "bem_set_near_field: no surrogate network loaded");
+  cudaSetDevice(ctx->device);
+  ctx->near_mode = mode;
+  ctx->near_mesh_version = -1;
+  if (mode == 0 || ctx->geo.n == 0) return BEM_OK;
+  return ensure_near(ctx, (cudaStream_t)stream);
+}
+
+extern "C" bem_status bem_near_pairs(bem_ctx* ctx, int64_t* nnz, int32_t* row_ptr_host,
+                                     int32_t* cols_host, void* stream) {
+  if (!ctx || !nnz) return BEM_EINVAL;
+  if (ctx->near_mode == 0) return fail(ctx, BEM_ESTATE, "bem_near_pairs: near field is off");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  bem_status st = ensure_near(ctx, s);
+  if (st != BEM_OK) return st;
+  *nnz = ctx->near_nnz;
+  if (row_ptr_host)
+    st = cuda_check(ctx, cudaMemcpyAsync(row_ptr_host, ctx->d_near_ptr,
+                                         (ctx->geo.n + 1) * sizeof(int32_t),
+                                         cudaMemcpyDeviceToHost, s), "bem_near_pairs copy");
+  if (st == BEM_OK && cols_host && ctx->near_nnz > 0)
+    st = cuda_check(ctx, cudaMemcpyAsync(cols_host, ctx->d_near_cols,
+                                         ctx->near_nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+                    "bem_near_pairs copy");
+  if (st == BEM_OK) st = cuda_check(ctx, cudaStreamSynchronize(s), "bem_near_pairs copy");
+  return st;
+}

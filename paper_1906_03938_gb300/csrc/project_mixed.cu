@@ -45,9 +45,6 @@ constexpr int kMaxG = 4;
 constexpr int kPlaneBytes = kBM * kBK * 2;   // one BF16 plane of a 128 x 16 block: 4 KB
 constexpr uint32_t kWaitLimit = 1u << 24;    // polls (with 64 ns sleeps) before giving up
 constexpr float kLog2e = 1.4426950408889634f;
-constexpr float kInv2Pi = 0.15915494309189535f;
-constexpr float kTwoPiHi = 6.28318548202514648f;      // float nearest 2 pi
-constexpr float kTwoPiLo = -1.7484555314695172e-7f;   // 2 pi - kTwoPiHi
 
 struct MixedParams {
   int64_t n;          // unknowns
@@ -133,7 +130,13 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
   return false;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p) {
+// One work unit (row tile, node group, column split) of problem p; the body of the single
+// and the grouped launch.
+// tmem_given: TMEM columns already allocated by a persistent caller (its base address), or
+// kNoTmem to allocate (and release) them here.
+constexpr uint32_t kNoTmem = 0xffffffffu;
+__device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int u,
+                                                 const uint32_t tmem_given) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const SmemLayout L = smem_layout(p.G, p.nup);
   unsigned char* sA = smem + L.a_off;
@@ -156,7 +159,6 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
   const int lane = threadIdx.x % 32;
 
   // unit -> (row tile, node group, column split)
-  const int u = blockIdx.x;
   const int split = u % p.S;
   const int t = u / p.S;
   const int gg = t % p.nG;
@@ -183,14 +185,14 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
     *abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == 1) {
+  if (warp == 1 && tmem_given == kNoTmem) {
     tmem_alloc(tmem_slot, tmem_cols);
     tmem_relinquish();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem_base = *tmem_slot;
+  const uint32_t tmem_base = tmem_given == kNoTmem ? *tmem_slot : tmem_given;
 
   if (warp == 0) {
     // ---------------- producer: basis planes (bulk copy), column geometry, self terms ----
@@ -341,11 +343,12 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
 #pragma unroll
             for (int q = 0; q < 7; ++q) {
               const float a = am[d][q] * ex2f(kmi[g] * rr[d][q]);
+              // the MUFU sine and cosine reduce their argument in revolutions themselves;
+              // that reduction's error (half an FP32 ulp of ph / 2 pi) is of the order of
+              // the rounding of ph itself, so no explicit reduction precedes them
               const float ph = kr[g] * rr[d][q];
-              const float nrot = fmaf(ph, kInv2Pi, 12582912.0f) - 12582912.0f;
-              const float red = fmaf(-nrot, kTwoPiLo, fmaf(-nrot, kTwoPiHi, ph));
-              sr = fmaf(a, cosf_mufu(red), sr);
-              si = fmaf(a, sinf_mufu(red), si);
+              sr = fmaf(a, cosf_mufu(ph), sr);
+              si = fmaf(a, sinf_mufu(ph), si);
             }
             if (i == l0 + d) {   // diagonal: the self term
               const float2 sv = sSelf[(k0 + d) * kMaxG + g];
@@ -406,8 +409,52 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
     if (lane == 0) mbar_wait(accfull, 0, kWaitLimit);
     __syncwarp();
     tc_fence_after();
-    tmem_dealloc(tmem_base, tmem_cols);
+    if (tmem_given == kNoTmem) tmem_dealloc(tmem_base, tmem_cols);
   }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p) {
+  mixed_apply_unit(p, blockIdx.x, kNoTmem);
+}
+
+// Persistent grouped kernel over several problems: one CTA per SM takes work units from a
+// global counter (dynamic scheduling); unit b belongs to problem k, the last k with
+// unit_start[k] <= b (problems are ordered by decreasing work, so the largest are handed
+// out first and the small ones fill the tail). The CTA allocates the TMEM columns of the
+// widest problem once and keeps them for all its units.
+__global__ void __launch_bounds__(kThreads, 1)
+mixed_apply_grouped_kernel(const MixedParams* __restrict__ plist, const int* __restrict__ unit_start,
+                           int nprob, int total, int* next_unit, uint32_t tmem_cols) {
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_unit;
+  const int warp = threadIdx.x / 32;
+  if (warp == 1) {
+    tmem_alloc(&s_tmem, tmem_cols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = s_tmem;
+  for (;;) {
+    if (threadIdx.x == 0) s_unit = atomicAdd(next_unit, 1);
+    __syncthreads();
+    const int b = s_unit;
+    __syncthreads();   // every thread has read s_unit before it is replaced
+    if (b >= total) break;
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (unit_start[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    const MixedParams p = plist[lo];
+    mixed_apply_unit(p, b - unit_start[lo], tmem_base);
+    __syncthreads();   // the unit's barriers, shared memory and accumulators are free again
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem_base, tmem_cols);
 }
 
 // Basis planes in the tile-native layout the kernel copies per K-block: for K-block kb,
@@ -415,53 +462,53 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
 // 8 rows x 8 bf16, row stride 16 B, at ng * 256 + kg * 128 bytes.
 __global__ void prep_basis_planes_kernel(const double* __restrict__ V, int64_t ldv, int64_t n,
                                          int nu, int nup, int C, int nK,
-                                         __nv_bfloat16* __restrict__ Bp) {
-  const int64_t total = (int64_t)nK * 4 * 2 * nup * kBK;
+                                         __nv_bfloat16* __restrict__ Bp, float2* __restrict__ V32) {
+  // one thread per source element (panel l, column col); the split is formed in FP32
+  // (hi + lo carries 16 significant bits, far above FP32's own rounding)
+  const int64_t rows = (int64_t)nK * kBK;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= total) return;
-  // decode in the order of the layout
-  int64_t x = t;
-  const int k8 = (int)(x % 8); x /= 8;
-  const int r8 = (int)(x % 8); x /= 8;
-  const int kg = (int)(x % 2); x /= 2;
-  const int ngroups = 2 * C / 8;
-  const int ng = (int)(x % ngroups); x /= ngroups;
-  const int pl = (int)(x % 4); x /= 4;
-  const int nchunks = nup / C;
-  const int c = (int)(x % nchunks); x /= nchunks;
-  const int kb = (int)x;
-  const int rowN = ng * 8 + r8;                 // 0 .. 2C
-  const int halfim = rowN >= C;                 // 0: feeds Yr, 1: feeds Yi
-  const int col = c * C + (rowN % C);
-  const int64_t l = (int64_t)kb * kBK + kg * 8 + k8;
-  double vr = 0.0, vi = 0.0;
+  if (t >= rows * nup) return;
+  const int64_t l = t % rows;
+  const int col = (int)(t / rows);
+  float vr = 0.f, vi = 0.f;
   if (l < n && col < nu) {
     const double2 v = reinterpret_cast<const double2*>(V)[(int64_t)col * ldv + l];
-    vr = v.x;
-    vi = v.y;
+    vr = (float)v.x;
+    vi = (float)v.y;
+    V32[(int64_t)col * n + l] = make_float2(vr, vi);
   }
-  const __nv_bfloat16 vr_hi = __double2bfloat16(vr);
-  const __nv_bfloat16 vi_hi = __double2bfloat16(vi);
-  const __nv_bfloat16 vr_lo = __double2bfloat16(vr - (double)__bfloat162float(vr_hi));
-  const __nv_bfloat16 vi_lo = __double2bfloat16(vi - (double)__bfloat162float(vi_hi));
-  __nv_bfloat16 out;
-  switch (pl) {
-    case 0: out = halfim ? vi_hi : vr_hi; break;                    // [Vr | Vi]
-    case 1: out = halfim ? vi_lo : vr_lo; break;                    // [Vr_lo | Vi_lo]
-    case 2: out = halfim ? vr_hi : __hneg(vi_hi); break;            // [-Vi | Vr]
-    default: out = halfim ? vr_lo : __hneg(vi_lo); break;           // [-Vi_lo | Vr_lo]
-  }
-  Bp[t] = out;
+  const __nv_bfloat16 vr_hi = __float2bfloat16(vr), vi_hi = __float2bfloat16(vi);
+  const __nv_bfloat16 vr_lo = __float2bfloat16(vr - __bfloat162float(vr_hi));
+  const __nv_bfloat16 vi_lo = __float2bfloat16(vi - __bfloat162float(vi_hi));
+  const __nv_bfloat16 vals[4][2] = {{vr_hi, vi_hi},               // [Vr | Vi]
+                                    {vr_lo, vi_lo},               // [Vr_lo | Vi_lo]
+                                    {__hneg(vi_hi), vr_hi},       // [-Vi | Vr]
+                                    {__hneg(vi_lo), vr_lo}};      // [-Vi_lo | Vr_lo]
+  // position in the tile-native layout: (kb, chunk, plane, 8-row group, k half, row, k)
+  const int kb = (int)(l / kBK), kin = (int)(l % kBK);
+  const int kg = kin / 8, k8 = kin % 8;
+  const int c = col / C, rc = col % C;
+  const int nchunks = nup / C, ngroups = 2 * C / 8;
+#pragma unroll
+  for (int pl = 0; pl < 4; ++pl)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int rowN = h * C + rc;
+      const int64_t idx =
+          (((((int64_t)kb * nchunks + c) * 4 + pl) * ngroups + rowN / 8) * 2 + kg) * 64 +
+          (rowN % 8) * 8 + k8;
+      Bp[idx] = vals[pl][h];
+    }
 }
 
 // Partial products P_r,j = V^H Y_j over the row range of part r, Y_j = sum over column
-// splits of the FP32 partials: FP32 products summed over 32-row chunks, chunk sums added
-// in FP64 (the inputs carry ~1e-5 relative error, so FP32 products lose nothing; the FP64
-// pipe of this GPU is ~70x slower than its FP32 pipe).
+// splits of the FP32 partials: FP32 products of the FP32 copy of V summed over 32-row
+// chunks, chunk sums added with compensation (the inputs carry ~1e-5 relative error, so
+// FP32 products lose nothing; the FP64 pipe of this GPU is ~70x slower than its FP32 pipe).
 constexpr int kT = 64;    // output tile (64 x 64 of the nu x nu matrix)
 constexpr int kTR = 32;   // rows per chunk
-__global__ void __launch_bounds__(256)
-mixed_vhy_part_kernel(const double* __restrict__ V, int64_t ldv, int nu, int64_t n, int n_pad,
+__global__ void __launch_bounds__(256, 2)
+mixed_vhy_part_kernel(const float2* __restrict__ V32, int nu, int64_t n, int n_pad,
                       int N, int S, int acc_cols, int C, const float* __restrict__ Yp,
                       int64_t rows_per_part, double* __restrict__ part) {
   __shared__ float2 sX[kTR][kT + 1];   // +1: the row-major fill below is then 2-way at most
@@ -473,24 +520,18 @@ mixed_vhy_part_kernel(const double* __restrict__ V, int64_t ldv, int nu, int64_t
   const int64_t r_end = min(n, r_begin + rows_per_part);
   const int tid = threadIdx.x;
   const int oa = tid % 16, ob = tid / 16;   // outputs (oa + 16 i, ob + 16 m)
-  double2 acc[4][4];
+  float2 acc[4][4], comp[4][4];   // running sums of the chunk sums and their compensation
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int m = 0; m < 4; ++m) acc[i][m] = make_double2(0.0, 0.0);
-  const double2* Vc = reinterpret_cast<const double2*>(V);
+    for (int m = 0; m < 4; ++m) acc[i][m] = comp[i][m] = make_float2(0.f, 0.f);
   for (int64_t r0 = r_begin; r0 < r_end; r0 += kTR) {
     __syncthreads();
     for (int x = tid; x < kTR * kT; x += 256) {
       const int rr = x % kTR, cc = x / kTR;
       const int64_t r = r0 + rr;
       const int a = ta * kT + cc;
-      float2 v = make_float2(0.f, 0.f);
-      if (r < r_end && a < nu) {
-        const double2 vd = Vc[(int64_t)a * ldv + r];
-        v = make_float2((float)vd.x, (float)vd.y);
-      }
-      sX[rr][cc] = v;
+      sX[rr][cc] = (r < r_end && a < nu) ? V32[(int64_t)a * n + r] : make_float2(0.f, 0.f);
     }
     // Y rows four at a time (rows_per_part and the chunk start are multiples of 4; rows
     // past n are the zero padding rows of the last tile, rows past r_end are masked)
@@ -535,12 +576,18 @@ mixed_vhy_part_kernel(const double* __restrict__ V, int64_t ldv, int nu, int64_t
           c[i][m].y = fmaf(x[i].x, y[m].y, fmaf(-x[i].y, y[m].x, c[i][m].y));
         }
     }
+    // compensated (Kahan) addition of the chunk sums: the error stays at FP32 rounding
+    // however many chunks a part holds
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
-        acc[i][m].x += c[i][m].x;
-        acc[i][m].y += c[i][m].y;
+        const float yx = c[i][m].x - comp[i][m].x, yy = c[i][m].y - comp[i][m].y;
+        const float tx = acc[i][m].x + yx, ty = acc[i][m].y + yy;
+        comp[i][m].x = (tx - acc[i][m].x) - yx;
+        comp[i][m].y = (ty - acc[i][m].y) - yy;
+        acc[i][m].x = tx;
+        acc[i][m].y = ty;
       }
   }
   double2* P = reinterpret_cast<double2*>(part) + ((int64_t)blockIdx.z * N + j) * nu * nu;
@@ -551,7 +598,9 @@ mixed_vhy_part_kernel(const double* __restrict__ V, int64_t ldv, int nu, int64_t
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       const int b = tb * kT + ob + 16 * m;
-      if (b < nu) P[(int64_t)b * nu + a] = acc[i][m];
+      if (b < nu)
+        P[(int64_t)b * nu + a] = make_double2((double)acc[i][m].x - (double)comp[i][m].x,
+                                              (double)acc[i][m].y - (double)comp[i][m].y);
     }
   }
 }
@@ -609,13 +658,31 @@ int choose_splits(int64_t units1, int nK, int sms) {
   return best;
 }
 
-}  // namespace
+// Everything one mixed projection of one context needs besides its launches.
+struct MixedPlan {
+  MixedParams p{};
+  int64_t units = 0;          // work units of the main kernel
+  int slices = 0;             // slices of the FP32 partials: the S column splits, then the
+                              // near-field correction when it is active
+  int vtiles = 0;
+  int64_t vparts = 0, rows_per_vpart = 0;
+  const double* V = nullptr;
+  int64_t ldv = 0;
+  float2* V32 = nullptr;
+  __nv_bfloat16* Bp = nullptr;
+  double* vpart = nullptr;
+  SmemLayout L{};
+};
 
-bem_status project_mixed(bem_ctx* ctx, const double* V, int64_t ldv, int nu, double* Bhat,
-                         double* AV, cudaStream_t s) {
+// Parameters, scratch and FP32 self terms of one projection; S > 0 forces the number of
+// column splits (else the fewest that fill the device's waves), Gmax > 0 caps the nodes per
+// work unit (else up to kMaxG).
+bem_status mixed_plan(bem_ctx* ctx, const double* V, int64_t ldv, int nu, int S, int Gmax,
+                      MixedPlan& plan, cudaStream_t s) {
   const int64_t n = ctx->geo.n;
   const int N = ctx->con.N;
-  MixedParams p{};
+  MixedParams& p = plan.p;
+  p = MixedParams{};
   p.n = n;
   p.N = N;
   p.nu = nu;
@@ -624,35 +691,41 @@ bem_status project_mixed(bem_ctx* ctx, const double* V, int64_t ldv, int nu, dou
   if (p.nup % p.C != 0) p.nup = (p.nup + p.C - 1) / p.C * p.C;
   p.nchunks = p.nup / p.C;
   const int acc_cols = 2 * p.nup;
-  p.G = std::max(1, std::min(std::min(N, kMaxG), 512 / acc_cols));
+  p.G = std::max(1, std::min(std::min(N, Gmax > 0 ? std::min(Gmax, kMaxG) : kMaxG), 512 / acc_cols));
   p.nG = (N + p.G - 1) / p.G;
   p.nK = (int)((n + kBK - 1) / kBK);
   p.n_pad = (int)((n + kBM - 1) / kBM * kBM);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
   const int64_t rtiles = p.n_pad / kBM;
-  p.S = choose_splits(rtiles * p.nG, p.nK, std::max(1, sms));
+  p.S = S > 0 ? std::max(1, std::min(S, std::max(1, p.nK / 4)))
+              : choose_splits(rtiles * p.nG, p.nK, std::max(1, sms));
+  plan.units = rtiles * p.nG * p.S;
 
-  // scratch: basis planes, then the FP32 partials
+  // scratch: basis planes, FP32 partials, FP32 copy of V, V^H Y partials
   const size_t bp_bytes = (size_t)p.nK * 256 * p.nup;
   const size_t bp_off = 0;
   const size_t yp_off = (bp_bytes + 255) / 256 * 256;
-  const size_t yp_bytes = (size_t)p.S * N * acc_cols * p.n_pad * sizeof(float);
+  plan.slices = p.S + (near_active(ctx) ? 1 : 0);
+  const size_t yp_bytes = (size_t)plan.slices * N * acc_cols * p.n_pad * sizeof(float);
   // V^H Y partials: enough row ranges to fill the device, at least 128 rows each
-  const int vtiles = ((nu + kT - 1) / kT) * ((nu + kT - 1) / kT);
+  plan.vtiles = ((nu + kT - 1) / kT) * ((nu + kT - 1) / kT);
   int64_t vparts = std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128,
-                                                          (4 * (int64_t)sms + vtiles * N - 1) /
-                                                              ((int64_t)vtiles * N)));
-  const int64_t rows_per_vpart = ((n + vparts - 1) / vparts + kTR - 1) / kTR * kTR;
-  vparts = (n + rows_per_vpart - 1) / rows_per_vpart;
-  const size_t vp_off = (yp_off + yp_bytes + 255) / 256 * 256;
-  const size_t vp_bytes = (size_t)vparts * N * nu * nu * 2 * sizeof(double);
+                                                          (4 * (int64_t)sms + plan.vtiles * N - 1) /
+                                                              ((int64_t)plan.vtiles * N)));
+  plan.rows_per_vpart = ((n + vparts - 1) / vparts + kTR - 1) / kTR * kTR;
+  plan.vparts = (n + plan.rows_per_vpart - 1) / plan.rows_per_vpart;
+  const size_t v32_off = (yp_off + yp_bytes + 255) / 256 * 256;
+  const size_t v32_bytes = (size_t)n * nu * sizeof(float2);
+  const size_t vp_off = (v32_off + v32_bytes + 255) / 256 * 256;
+  const size_t vp_bytes = (size_t)plan.vparts * N * nu * nu * 2 * sizeof(double);
   bem_status st = ensure_self32(ctx, s);
   if (st != BEM_OK) return st;
   st = ensure_scratch(ctx, vp_off + vp_bytes);
   if (st != BEM_OK) return st;
   unsigned char* scr = reinterpret_cast<unsigned char*>(ctx->d_scratch);
-  p.Bp = reinterpret_cast<const __nv_bfloat16*>(scr + bp_off);
+  plan.Bp = reinterpret_cast<__nv_bfloat16*>(scr + bp_off);
+  p.Bp = plan.Bp;
   p.Yp = reinterpret_cast<float*>(scr + yp_off);
   p.cx = ctx->geo.cx;
   p.qp = ctx->geo.qp;
@@ -661,41 +734,352 @@ bem_status project_mixed(bem_ctx* ctx, const double* V, int64_t ldv, int nu, dou
   p.pack32 = ctx->geo.pack32;
   p.z = ctx->con.z;
   p.status = ctx->d_status;
+  plan.V = V;
+  plan.ldv = ldv;
+  plan.V32 = reinterpret_cast<float2*>(scr + v32_off);
+  plan.vpart = reinterpret_cast<double*>(scr + vp_off);
+  plan.L = smem_layout(p.G, p.nup);
+  return BEM_OK;
+}
 
-  const int64_t prep_total = (int64_t)p.nK * 4 * 2 * p.nup * kBK;
+// Basis planes and FP32 copy of V (before the main kernel).
+void mixed_pre(bem_ctx* ctx, const MixedPlan& plan, cudaStream_t s) {
+  const MixedParams& p = plan.p;
+  const int64_t prep_total = (int64_t)p.nK * kBK * p.nup;
   prep_basis_planes_kernel<<<(unsigned)((prep_total + 255) / 256), 256, 0, s>>>(
-      V, ldv, n, nu, p.nup, p.C, p.nK,
-      reinterpret_cast<__nv_bfloat16*>(scr + bp_off));
+      plan.V, plan.ldv, p.n, p.nu, p.nup, p.C, p.nK, plan.Bp, plan.V32);
   ctx->launches++;
+}
 
-  const SmemLayout L = smem_layout(p.G, p.nup);
-  st = cuda_check(ctx, cudaFuncSetAttribute(mixed_apply_kernel,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)L.total),
-                  "mixed kernel attribute");
+// V^H Y, weights, optional Y (after the main kernel).
+void mixed_post(bem_ctx* ctx, const MixedPlan& plan, double* Bhat, double* AV, cudaStream_t s) {
+  const MixedParams& p = plan.p;
+  const int acc_cols = 2 * p.nup;
+  mixed_vhy_part_kernel<<<dim3((unsigned)plan.vtiles, (unsigned)p.N, (unsigned)plan.vparts), 256,
+                          0, s>>>(plan.V32, p.nu, p.n, p.n_pad, p.N, plan.slices, acc_cols, p.C,
+                                  p.Yp, plan.rows_per_vpart, plan.vpart);
+  const int64_t outs = (int64_t)p.N * p.nu * p.nu;
+  mixed_vhy_reduce_kernel<<<(unsigned)((outs + 255) / 256), 256, 0, s>>>(
+      plan.vpart, (int)plan.vparts, p.N, p.nu, ctx->con.w, Bhat);
+  ctx->launches += 2;
+  if (AV) {
+    const int64_t tot = (int64_t)p.N * p.nu * p.n;
+    mixed_av_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(p.n, p.n_pad, p.nu, p.N,
+                                                                  plan.slices, acc_cols, p.C, p.Yp,
+                                                                  AV);
+    ctx->launches++;
+  }
+}
+
+bem_status set_mixed_smem(bem_ctx* ctx, uint32_t bytes) {
+  bem_status st = cuda_check(ctx, cudaFuncSetAttribute(mixed_apply_kernel,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)bytes),
+                             "mixed kernel attribute");
   if (st != BEM_OK) return st;
-  const int64_t units = rtiles * p.nG * p.S;
+  return cuda_check(ctx, cudaFuncSetAttribute(mixed_apply_grouped_kernel,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)bytes),
+                    "mixed kernel attribute");
+}
+
+}  // namespace
+
+bem_status project_mixed(bem_ctx* ctx, const double* V, int64_t ldv, int nu, double* Bhat,
+                         double* AV, cudaStream_t s) {
+  MixedPlan plan;
+  bem_status st = mixed_plan(ctx, V, ldv, nu, 0, 0, plan, s);
+  if (st != BEM_OK) return st;
+  mixed_pre(ctx, plan, s);
+  if ((st = set_mixed_smem(ctx, plan.L.total)) != BEM_OK) return st;
   timing_begin(ctx, s);
-  mixed_apply_kernel<<<(unsigned)units, kThreads, L.total, s>>>(p);
+  mixed_apply_kernel<<<(unsigned)plan.units, kThreads, plan.L.total, s>>>(plan.p);
   timing_end(ctx, s);
   ctx->launches++;
   st = cuda_check(ctx, cudaGetLastError(), "mixed apply kernel");
   if (st != BEM_OK) return st;
-
-  double* vpart = reinterpret_cast<double*>(scr + vp_off);
-  mixed_vhy_part_kernel<<<dim3((unsigned)vtiles, (unsigned)N, (unsigned)vparts), 256, 0, s>>>(
-      V, ldv, nu, n, p.n_pad, N, p.S, acc_cols, p.C, p.Yp, rows_per_vpart, vpart);
-  const int64_t outs = (int64_t)N * nu * nu;
-  mixed_vhy_reduce_kernel<<<(unsigned)((outs + 255) / 256), 256, 0, s>>>(vpart, (int)vparts, N, nu,
-                                                                         ctx->con.w, Bhat);
-  ctx->launches += 2;
-  if (AV) {
-    const int64_t tot = (int64_t)N * nu * n;
-    mixed_av_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, p.n_pad, nu, N, p.S,
-                                                                  acc_cols, p.C, p.Yp, AV);
-    ctx->launches++;
+  if (plan.slices > plan.p.S) {
+    st = near_apply32(ctx, plan.V32, nu, plan.p.nup, plan.p.C, plan.p.n_pad, plan.p.Yp, plan.p.S, s);
+    if (st != BEM_OK) return st;
   }
+  mixed_post(ctx, plan, Bhat, AV, s);
   return cuda_check(ctx, cudaGetLastError(), "mixed projection kernels");
 }
 
 }  // namespace bem
+
+// ---------------------------------------------------------------------------------------
+// Batched projection: several contexts (meshes, contours, bases) in one grouped launch of
+// the fused kernel, the per-problem preparation and reductions around it, recorded once as
+// a CUDA graph and replayed.
+
+struct bem_batch {
+  int device = 0;
+  int nprob = 0;
+  std::vector<bem_ctx*> ctx;
+  std::vector<const double*> V;
+  std::vector<int64_t> ldv;
+  std::vector<int> nu;
+  std::vector<double*> Bhat;
+  std::vector<int64_t> mesh_ver, contour_ver;
+  std::vector<double*> scratch;
+  std::vector<int64_t> launches;      // launches per run, per context
+  bem::MixedParams* d_plist = nullptr;
+  int* d_ustart = nullptr;
+  cudaStream_t cs = nullptr;          // private capture stream
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int* d_next = nullptr;              // work counter of the persistent kernel
+  int sms = 0;
+  int S = 0;                          // column splits (0: per-problem default)
+  int G = 0;                          // nodes per unit cap (0: default)
+  int64_t units = 0;                  // blocks of the grouped launch
+  double tuned_ms = 0.0;              // time of one run at the chosen S (autotune), else 0
+};
+
+namespace bem {
+namespace {
+
+void batch_release_graph(bem_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+// Plan every problem at split count S and node cap G, and record the graph.
+bem_status batch_record(bem_batch* b, int S, int G) {
+  bem_ctx* c0 = b->ctx[0];
+  batch_release_graph(b);
+  std::vector<MixedPlan> plan(b->nprob);
+  uint32_t smem = 0, tcols = 32;
+  for (int k = 0; k < b->nprob; ++k) {
+    bem_status st = mixed_plan(b->ctx[k], b->V[k], b->ldv[k], b->nu[k], S, G, plan[k], b->cs);
+    if (st != BEM_OK) return st;
+    smem = std::max(smem, plan[k].L.total);
+    while (tcols < (uint32_t)plan[k].p.G * 2u * plan[k].p.nup) tcols <<= 1;
+  }
+  // largest problems first; the unit offsets of the grouped launch
+  std::vector<int> order(b->nprob);
+  for (int k = 0; k < b->nprob; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return plan[x].units > plan[y].units; });
+  std::vector<MixedParams> plist(b->nprob);
+  std::vector<int> ustart(b->nprob);
+  int64_t total = 0;
+  for (int k = 0; k < b->nprob; ++k) {
+    plist[k] = plan[order[k]].p;
+    ustart[k] = (int)total;
+    total += plan[order[k]].units;
+  }
+  if (total > 0x7fffffff) return fail(c0, BEM_EINVAL, "bem_batch_create: too many work units");
+  b->units = total;
+  b->S = S;
+  b->G = G;
+  bem_status st = cuda_check(c0, cudaMemcpyAsync(b->d_plist, plist.data(),
+                                                 b->nprob * sizeof(MixedParams),
+                                                 cudaMemcpyHostToDevice, b->cs), "batch copy");
+  if (st == BEM_OK)
+    st = cuda_check(c0, cudaMemcpyAsync(b->d_ustart, ustart.data(), b->nprob * sizeof(int),
+                                        cudaMemcpyHostToDevice, b->cs), "batch copy");
+  if (st == BEM_OK) st = cuda_check(c0, cudaStreamSynchronize(b->cs), "batch copy");
+  if (st == BEM_OK) st = set_mixed_smem(c0, smem);
+  if (st != BEM_OK) return st;
+  std::vector<int64_t> before(b->nprob);
+  for (int k = 0; k < b->nprob; ++k) before[k] = b->ctx[k]->launches;
+  st = cuda_check(c0, cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal),
+                  "batch capture");
+  if (st != BEM_OK) return st;
+  for (int k = 0; k < b->nprob; ++k) mixed_pre(b->ctx[k], plan[k], b->cs);
+  cudaMemsetAsync(b->d_next, 0, sizeof(int), b->cs);
+  const unsigned grid = (unsigned)std::min<int64_t>(total, std::max(1, b->sms));
+  mixed_apply_grouped_kernel<<<grid, kThreads, smem, b->cs>>>(b->d_plist, b->d_ustart, b->nprob,
+                                                            (int)total, b->d_next, tcols);
+  c0->launches++;
+  for (int k = 0; k < b->nprob; ++k) mixed_post(b->ctx[k], plan[k], b->Bhat[k], nullptr, b->cs);
+  const cudaError_t le = cudaGetLastError();
+  const cudaError_t ce = cudaStreamEndCapture(b->cs, &b->graph);
+  for (int k = 0; k < b->nprob; ++k) {   // counted per replay instead
+    b->launches[k] = b->ctx[k]->launches - before[k];
+    b->ctx[k]->launches = before[k];
+  }
+  st = cuda_check(c0, le != cudaSuccess ? le : ce, "batch capture");
+  if (st == BEM_OK) st = cuda_check(c0, cudaGraphInstantiate(&b->exec, b->graph, 0), "batch graph");
+  if (st != BEM_OK) return st;
+  for (int k = 0; k < b->nprob; ++k) {
+    b->mesh_ver[k] = b->ctx[k]->mesh_version;
+    b->contour_ver[k] = b->ctx[k]->contour_version;
+    b->scratch[k] = b->ctx[k]->d_scratch;
+  }
+  return BEM_OK;
+}
+
+bem_status batch_launch(bem_batch* b, cudaStream_t s) {
+  bem_ctx* c0 = b->ctx[0];
+  for (int k = 0; k < b->nprob; ++k)
+    if (b->ctx[k]->mesh_version != b->mesh_ver[k] ||
+        b->ctx[k]->contour_version != b->contour_ver[k] ||
+        b->ctx[k]->d_scratch != b->scratch[k] || !b->ctx[k]->con.self32_ready)
+      return fail(c0, BEM_ESTATE,
+                  "bem_batch_run: a context's mesh, contour or workspace changed since the "
+                  "batch was created");
+  cudaSetDevice(b->device);
+  bem_status st = cuda_check(c0, cudaGraphLaunch(b->exec, s), "bem_batch_run");
+  if (st != BEM_OK) return st;
+  for (int k = 0; k < b->nprob; ++k) b->ctx[k]->launches += b->launches[k];
+  return BEM_OK;
+}
+
+// Time `reps` runs on the private stream (after one untimed run).
+bem_status batch_time(bem_batch* b, int reps, double* ms) {
+  bem_ctx* c0 = b->ctx[0];
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  bem_status st = batch_launch(b, b->cs);
+  if (st == BEM_OK) st = cuda_check(c0, cudaEventRecord(e0, b->cs), "batch timing");
+  for (int r = 0; r < reps && st == BEM_OK; ++r) st = batch_launch(b, b->cs);
+  if (st == BEM_OK) st = cuda_check(c0, cudaEventRecord(e1, b->cs), "batch timing");
+  if (st == BEM_OK) st = cuda_check(c0, cudaEventSynchronize(e1), "batch timing");
+  float t = 0.f;
+  if (st == BEM_OK) cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = t / reps;
+  for (int k = 0; k < b->nprob && st == BEM_OK; ++k)
+    st = take_status(b->ctx[k], b->cs, "bem_batch_create");
+  return st;
+}
+
+}  // namespace
+}  // namespace bem
+
+extern "C" {
+
+void bem_batch_destroy(bem_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->cs) cudaStreamSynchronize(b->cs);
+  bem::batch_release_graph(b);
+  cudaFree(b->d_plist);
+  cudaFree(b->d_ustart);
+  cudaFree(b->d_next);
+  if (b->cs) cudaStreamDestroy(b->cs);
+  delete b;
+}
+
+bem_status bem_batch_create(bem_ctx* const* ctxs, int nprob, const double* const* V_dev,
+                            const int64_t* ldv, const int* nu, double* const* Bhat_dev,
+                            int precision, int autotune, bem_batch** out, void* stream) {
+  if (!out) return BEM_EINVAL;
+  *out = nullptr;
+  if (!ctxs || nprob < 1 || !ctxs[0]) return BEM_EINVAL;
+  bem_ctx* c0 = ctxs[0];
+  if (nprob > 4096 || !V_dev || !ldv || !nu || !Bhat_dev)
+    return bem::fail(c0, BEM_EINVAL, "bem_batch_create: need 1..4096 problems and all arrays");
+  if (precision != BEM_PREC_MIXED)
+    return bem::fail(c0, BEM_EINVAL, "bem_batch_create: the grouped launch is the mixed path");
+  for (int k = 0; k < nprob; ++k) {
+    bem_ctx* c = ctxs[k];
+    if (!c || c->device != c0->device)
+      return bem::fail(c0, BEM_EINVAL, "bem_batch_create: contexts must exist and share a device");
+    for (int q = 0; q < k; ++q)
+      if (ctxs[q] == c) return bem::fail(c0, BEM_EINVAL, "bem_batch_create: a context appears twice");
+    if (c->geo.n == 0 || c->con.N == 0)
+      return bem::fail(c0, BEM_ESTATE, "bem_batch_create: every context needs a mesh and a contour");
+    if (c->near_mode != 0)
+      return bem::fail(c0, BEM_EINVAL, "bem_batch_create: near-field treatment is not batched");
+    if (!V_dev[k] || !Bhat_dev[k] || nu[k] < 1 || nu[k] > bem::kMaxNu || ldv[k] < c->geo.n ||
+        nu[k] > c->geo.n)
+      return bem::fail(c0, BEM_EINVAL, "bem_batch_create: bad V, Bhat, ldv or nu");
+  }
+  cudaSetDevice(c0->device);
+  bem_batch* b = new bem_batch();
+  b->device = c0->device;
+  b->nprob = nprob;
+  b->ctx.assign(ctxs, ctxs + nprob);
+  b->V.assign(V_dev, V_dev + nprob);
+  b->ldv.assign(ldv, ldv + nprob);
+  b->nu.assign(nu, nu + nprob);
+  b->Bhat.assign(Bhat_dev, Bhat_dev + nprob);
+  b->mesh_ver.resize(nprob);
+  b->contour_ver.resize(nprob);
+  b->scratch.resize(nprob);
+  b->launches.resize(nprob);
+  bem_status st = bem::cuda_check(c0, cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking),
+                                  "bem_batch_create");
+  if (st == BEM_OK)
+    st = bem::cuda_check(c0, cudaMalloc(&b->d_plist, nprob * sizeof(bem::MixedParams)),
+                         "bem_batch_create");
+  if (st == BEM_OK)
+    st = bem::cuda_check(c0, cudaMalloc(&b->d_ustart, nprob * sizeof(int)), "bem_batch_create");
+  if (st == BEM_OK)
+    st = bem::cuda_check(c0, cudaMalloc(&b->d_next, sizeof(int)), "bem_batch_create");
+  cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+  // the caller's stream may still be writing V: order the private stream after it
+  if (st == BEM_OK) st = bem::cuda_check(c0, cudaStreamSynchronize((cudaStream_t)stream), "bem_batch_create");
+  if (st == BEM_OK && autotune) {
+    // autotuner: the work-unit shape of the grouped launch (column splits S, nodes per
+    // unit G), by measurement of whole runs
+    int best_S = 0, best_G = 0;
+    double best = 1e300;
+    for (int G : {0, 2}) {
+      for (int S : {0, 1, 2, 3, 4}) {
+        double ms = 0.0;
+        st = bem::batch_record(b, S, G);
+        if (st == BEM_OK) st = bem::batch_time(b, 3, &ms);
+        if (st != BEM_OK) break;
+        if (ms < best) {
+          best = ms;
+          best_S = S;
+          best_G = G;
+        }
+      }
+      if (st != BEM_OK) break;
+    }
+    if (st == BEM_OK) {
+      b->tuned_ms = best;
+      st = bem::batch_record(b, best_S, best_G);
+    }
+  } else if (st == BEM_OK) {
+    st = bem::batch_record(b, 0, 0);
+  }
+  if (st == BEM_OK) st = bem::cuda_check(c0, cudaStreamSynchronize(b->cs), "bem_batch_create");
+  if (st != BEM_OK) {
+    bem_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return BEM_OK;
+}
+
+bem_status bem_batch_run(bem_batch* b, void* stream) {
+  if (!b) return BEM_EINVAL;
+  return bem::batch_launch(b, (cudaStream_t)stream);
+}
+
+bem_status bem_batch_info(const bem_batch* b, int* splits, int* nodes_per_unit, int64_t* units,
+                          double* tuned_ms) {
+  if (!b) return BEM_EINVAL;
+  if (splits) *splits = b->S;
+  if (nodes_per_unit) *nodes_per_unit = b->G;
+  if (units) *units = b->units;
+  if (tuned_ms) *tuned_ms = b->tuned_ms;
+  return BEM_OK;
+}
+
+bem_status bem_project_batched(bem_ctx* const* ctxs, int nprob, const double* const* V_dev,
+                               const int64_t* ldv, const int* nu, double* const* Bhat_dev,
+                               int precision, void* stream) {
+  bem_batch* b = nullptr;
+  bem_status st = bem_batch_create(ctxs, nprob, V_dev, ldv, nu, Bhat_dev, precision, 0, &b, stream);
+  if (st != BEM_OK) return st;
+  st = bem_batch_run(b, stream);
+  if (st == BEM_OK)
+    st = bem::cuda_check(ctxs[0], cudaStreamSynchronize((cudaStream_t)stream), "bem_project_batched");
+  for (int k = 0; k < nprob && st == BEM_OK; ++k) st = bem_check(ctxs[k], stream);
+  bem_batch_destroy(b);
+  return st;
+}
+
+}  // extern "C"

@@ -148,6 +148,7 @@ cudaError_t launch_apply_percol64(bem_ctx* ctx, int m, const double* lam_dev, co
   else
     residual_kernel<false><<<g2, kRowsPerBlock, 0, s>>>(ctx->geo, lam_dev, X, ldx, R);
   ctx->launches += 2;
+  if (near_active(ctx)) return launch_near_percol64(ctx, m, lam_dev, X, ldx, R, deriv, s);
   return cudaGetLastError();
 }
 
@@ -174,9 +175,11 @@ extern "C" bem_status bem_residual(bem_ctx* ctx, int m, const double* lam_host, 
     if (!isfinite(lam_host[c])) return fail(ctx, BEM_EINVAL, "bem_residual: non-finite lambda");
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
+  bem_status st = ensure_near(ctx, s);
+  if (st != BEM_OK) return st;
   // workspace: lambda (2m) + norms (2m) [+ R if the caller passes none]
   const size_t small = (size_t)4 * m * sizeof(double);
-  bem_status st = ensure_small(ctx, small);
+  st = ensure_small(ctx, small);
   if (st != BEM_OK) return st;
   double* R = R_dev;
   if (!R) {

@@ -387,6 +387,10 @@ extern "C" bem_status bem_refine(bem_ctx* ctx, int m, double* lam_host, double* 
     return fail(ctx, BEM_EINVAL, "bem_refine: bad arguments");
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
+  {
+    const bem_status sn = ensure_near(ctx, s);
+    if (sn != BEM_OK) return sn;
+  }
   size_t off = 0;
   auto take = [&](size_t b) { const size_t o = off; off += (b + 255) / 256 * 256; return o; };
   const size_t oA = take((size_t)n * n * sizeof(float2)), oP = take((size_t)n * sizeof(int)),
@@ -494,6 +498,10 @@ extern "C" bem_status bem_solve(bem_ctx* ctx, const double* V0_dev, int64_t ldv,
     return fail(ctx, BEM_EINVAL, "bem_solve: bad arguments");
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
+  {
+    const bem_status sn = ensure_near(ctx, s);
+    if (sn != BEM_OK) return sn;
+  }
   const Contour& con = ctx->con;
   const int p = (int)std::min<int64_t>(std::min<int64_t>((int64_t)N * nu, 256), std::max(2 * nu, 32));
   // solve-owned buffers: basis V (n nu), Bhat (N nu^2), Y (nu p), Ritz vectors (n p)

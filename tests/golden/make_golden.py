@@ -5,7 +5,9 @@ definition of the method's output, Section 1: all k inside the contour with T(k)
 found by the oracle's successive-linear-problems refinement started from the closed-form
 continuum eigenvalues inside the contour (unit sphere: zeros of spherical Bessel functions,
 Table 3; unit cube: pi sqrt(n1^2 + n2^2 + n3^2), Table 1) and from every neighbour that the
-refinement reveals. Usage: python tests/golden/make_golden.py [sphere320] [cube3072]
+refinement reveals. "sphere320_near" is the same sphere with the near-field variant of A
+(8 x 8 conical rule on near panel pairs). Usage:
+python tests/golden/make_golden.py [sphere320] [cube3072] [sphere320_near]
 """
 import os
 import sys
@@ -21,19 +23,23 @@ from oracle import refine, contour  # noqa: E402
 STARTS = {
     "sphere320": [3.141593, 4.493409],
     "cube3072": [5.441398, 7.695299],
+    "sphere320_near": [3.141593, 4.493409],
 }
 
 
 def main(names):
     for name in names:
-        prob = synth.workload(name).problems[0]
+        near = name.endswith("_near")
+        prob = synth.workload(name[:-5] if near else name).problems[0]
         mesh = prob.mesh()
         spec = prob.contour
         found = refine.discrete_eigs(mesh, STARTS[name], radius=0.2,
-                                     keep=lambda l: bool(contour.inside(l, spec, -0.05)))
+                                     keep=lambda l: bool(contour.inside(l, spec, -0.05)),
+                                     near=near)
         path = os.path.join(HERE, f"eigs_{name}.txt")
         with open(path, "w") as f:
-            f.write(f"# discrete eigenvalues of A(k) inside the contour of {name}\n")
+            f.write(f"# discrete eigenvalues of A(k) inside the contour of {name}"
+                    f"{' (near-field variant of A)' if near else ''}\n")
             f.write(f"# mesh {mesh.name} (n = {mesh.n}), contour {spec}\n")
             f.write("# written by tests/golden/make_golden.py (oracle only)\n")
             f.write("# re im multiplicity inside\n")

@@ -198,3 +198,22 @@ def test_cholqr2_fp32_first_pass_orthonormal(bem):
     # same basis up to a unitary diagonal (both are the positive-diagonal QR factor)
     assert _relerr(Q, Qo) < 1e-10
     ctx.close()
+
+
+@pytest.mark.parametrize("n,nu,boost", [(2000, 24, 1e4), (600, 130, 0.0), (3072, 64, 300.0)])
+def test_cholqr2_without_R_routes(bem, n, nu, boost):
+    """Without R: an FP32 pass that gives up (boost 1e4: condition ~1e5), the FP64 route for
+    nu > 128, and a second pass whose Gram matrix is near the identity must all give the
+    positive-diagonal QR factor of the input to FP64 accuracy."""
+    V = synth.complex_gaussian(n, nu, 11)
+    if boost:
+        V[:, 7] = V[:, 7] + boost * V[:, 6]
+    ctx = bem.Context(0)
+    Vd = _dev(V)
+    ctx.cholqr2(Vd, want_R=False)
+    Q = Vd.cpu().numpy()
+    assert np.max(np.abs(Q.conj().T @ Q - np.eye(nu))) < 1e-13
+    assert np.max(np.abs(Q @ (Q.conj().T @ V) - V)) < 1e-12 * np.max(np.abs(V))
+    Qo, _ = orr.orthonormalize(V)
+    assert _relerr(Q, Qo) < 1e-8 * max(1.0, boost / 100.0)
+    ctx.close()

@@ -94,3 +94,26 @@ def test_mixed_full_size_cube3072(bem):
     print(f"cube3072: worst rel err Bhat vs FP64 GPU {worst_b:.2e}, sampled Y vs oracle {worst_y:.2e}")
     assert worst_b < TOL and worst_y < TOL
     ctx.close()
+
+
+@pytest.mark.parametrize("scale,centre", [(1.0, 4.0), (2.0, 3.5)])
+def test_mixed_self_terms_both_routes(bem, scale, centre):
+    """Diagonal entries of the mixed path (unit columns) against the oracle's self integral:
+    small panels against the wavelength take the moment series (|k| rho ~ 1), panels of a
+    doubled icosahedron at k ~ 3.5 + i the direct angular quadrature (|k| rho > 3.5)."""
+    from oracle import assembly as oasm
+    mesh = synth.icosphere(1 if scale == 1.0 else 0)
+    mesh = synth.Mesh(mesh.name, mesh.xyz * scale, mesh.tri)
+    spec = synth.ContourSpec("circle", centre + 0j, 1.0, 1.0)
+    ctx = bem.Context(0)
+    ctx.set_mesh(mesh.xyz, mesh.tri)
+    z, _ = ctx.set_contour(spec.kind, spec.centre, spec.a, spec.b, 4)
+    E = np.eye(mesh.n, dtype=complex)
+    _, Y = ctx.project(_dev(E), bem.PREC_MIXED, AV=True)
+    ctx.check()
+    for j in range(4):
+        A = oasm.matrix(mesh, z[j])
+        d = np.diag(Y[j].cpu().numpy())
+        assert np.max(np.abs(d - np.diag(A)) / np.abs(np.diag(A))) < 2e-5, j
+        assert _relerr(Y[j].cpu().numpy(), A) < TOL
+    ctx.close()
