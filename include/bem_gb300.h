@@ -267,6 +267,58 @@ bem_status bem_near_pairs(bem_ctx* ctx, int64_t* nnz, int32_t* row_ptr_host, int
                           void* stream);
 
 /*
+ * Surrogate network of the near-field correction (a learned replacement for the 8 x 8 rule
+ * of near pairs in the mixed projection; the paper has no counterpart). A multilayer
+ * perceptron 11 -> 64 -> 64 -> 64 -> 2 (tanh) maps a near pair's canonical features to
+ * (A_near - A_7) / h, h the panel diameter. Features (11 floats per sample): the triangle's
+ * vertices in a frame with origin at the collocation point x, e1 along (b - a), e3 along the
+ * normal (b - a) x (c - b) turned so that a lies on its non-negative side, e2 = e3 x e1
+ * (a the vertex nearest x, b and c following it), divided by h; then Re(k h), Im(k h).
+ * Parameters (bem_surrogate_size() floats): in_shift[11], in_scale[11], W1[64][11], b1[64],
+ * W2[64][64], b2[64], W3[64][64], b3[64], W4[2][64], b4[2], out_scale[2]; the output is
+ * out_scale * (W4 h3 + b4) on features standardised as (f - in_shift) * in_scale.
+ * The context keeps FP32 master weights (trained) and an inference copy with the weights
+ * rounded to BF16 (used by bem_surrogate_forward and by the mixed projection in near-field
+ * mode 2). Device arrays are row-major: features count x 11, targets and outputs count x 2.
+ *
+ * bem_surrogate_init: Xavier-uniform weights from `seed`, zero biases, identity scalings.
+ * bem_surrogate_set / _get: copy the parameters from / to the host (which: 0 master, 1
+ *   inference copy); synchronous.
+ * bem_surrogate_samples: `count` training samples from the current mesh's near pairs
+ *   (near-field mode >= 1 required): pair and k drawn uniformly (k in [kr_lo, kr_hi] x
+ *   [ki_lo, ki_hi], FP32-rounded) by SplitMix64 of `seed`; features, target (A_near - A_7)/h
+ *   from the FP64 8 x 8 rule; optionally pairs_dev (count x 2 int32: row, panel) and k_dev
+ *   (count complex). Asynchronous.
+ * bem_surrogate_forward: outputs of the inference copy. Asynchronous.
+ * bem_surrogate_grad: mean over the samples of the squared error summed over the outputs
+ *   (*loss_host) and its gradient with respect to the master parameters (grad_dev,
+ *   bem_surrogate_size() floats; zero for the scalings), FP32 forward and backward kernels
+ *   of the library. Synchronous.
+ * bem_surrogate_train: `epochs` passes of Adam (lr, betas 0.9 / 0.999) over the samples in
+ *   batches of `batch`, each epoch in an affine permutation of the samples; fit_scaling != 0
+ *   first sets the standardisation and output scale from the samples' means and standard
+ *   deviations. loss_host (nullable, epochs doubles): mean batch loss per epoch. Refreshes
+ *   the inference copy. Synchronous.
+ * Errors: BEM_EINVAL for bad arguments, BEM_ESTATE without a network (init or set first).
+ */
+int bem_surrogate_size(void);
+bem_status bem_surrogate_init(bem_ctx* ctx, uint64_t seed, void* stream);
+bem_status bem_surrogate_set(bem_ctx* ctx, const float* params_host, int64_t count, void* stream);
+bem_status bem_surrogate_get(bem_ctx* ctx, int which, float* params_host, int64_t count,
+                             void* stream);
+bem_status bem_surrogate_samples(bem_ctx* ctx, double kr_lo, double kr_hi, double ki_lo,
+                                 double ki_hi, int64_t count, uint64_t seed, float* feat_dev,
+                                 float* target_dev, int32_t* pairs_dev, double* k_dev,
+                                 void* stream);
+bem_status bem_surrogate_forward(bem_ctx* ctx, const float* feat_dev, int64_t count,
+                                 float* out_dev, void* stream);
+bem_status bem_surrogate_grad(bem_ctx* ctx, const float* feat_dev, const float* target_dev,
+                              int64_t count, float* grad_dev, double* loss_host, void* stream);
+bem_status bem_surrogate_train(bem_ctx* ctx, const float* feat_dev, const float* target_dev,
+                               int64_t count, int epochs, int batch, double lr, int fit_scaling,
+                               uint64_t seed, double* loss_host, void* stream);
+
+/*
  * Batched projection (Section 3's projection for many independent problems at once, as a
  * parameter study or a sweep over geometries needs). Each problem is a context with its
  * mesh and contour already set (bem_set_mesh, bem_set_contour), a basis V_dev[k]

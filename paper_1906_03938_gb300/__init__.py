@@ -58,6 +58,15 @@ SIGNATURES = {
                                       _I64, _I, _P, _P]),
     "bem_set_near_field": (_I, [_P, _I, _P]),
     "bem_near_pairs": (_I, [_P, ctypes.POINTER(_I64), _P, _P, _P]),
+    "bem_surrogate_size": (_I, []),
+    "bem_surrogate_init": (_I, [_P, ctypes.c_uint64, _P]),
+    "bem_surrogate_set": (_I, [_P, _P, _I64, _P]),
+    "bem_surrogate_get": (_I, [_P, _I, _P, _I64, _P]),
+    "bem_surrogate_samples": (_I, [_P, _D, _D, _D, _D, _I64, ctypes.c_uint64, _P, _P, _P, _P,
+                                   _P]),
+    "bem_surrogate_forward": (_I, [_P, _P, _I64, _P, _P]),
+    "bem_surrogate_grad": (_I, [_P, _P, _P, _I64, _P, ctypes.POINTER(_D), _P]),
+    "bem_surrogate_train": (_I, [_P, _P, _P, _I64, _I, _I, _D, _I, ctypes.c_uint64, _P, _P]),
     "bem_batch_create": (_I, [_P, _I, _P, _P, _P, _P, _I, _I, ctypes.POINTER(_P), _P]),
     "bem_batch_run": (_I, [_P, _P]),
     "bem_batch_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I64),
@@ -197,6 +206,58 @@ class Context:
                                                              _ptr(row_ptr), _ptr(cols),
                                                              _stream(stream)))
         return row_ptr, cols[:nnz.value]
+
+    # ---- surrogate network of the near-field correction ----
+    def surrogate_init(self, seed=1, stream=None):
+        self._chk("bem_surrogate_init", self._lib.bem_surrogate_init(self._h, int(seed),
+                                                                     _stream(stream)))
+
+    def surrogate_params(self, which=0):
+        out = np.zeros(self._lib.bem_surrogate_size(), dtype=np.float32)
+        self._chk("bem_surrogate_get", self._lib.bem_surrogate_get(self._h, int(which), _ptr(out),
+                                                                   out.size, None))
+        return out
+
+    def surrogate_set(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        self._chk("bem_surrogate_set", self._lib.bem_surrogate_set(self._h, _ptr(p), p.size, None))
+
+    def surrogate_samples(self, count, k_re, k_im, seed=1, with_pairs=False, stream=None):
+        """(features (count, 11), targets (count, 2)[, pairs (count, 2), k (count,)])."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        feat = torch.empty((count, 11), dtype=torch.float32, device=dev)
+        targ = torch.empty((count, 2), dtype=torch.float32, device=dev)
+        pairs = torch.empty((count, 2), dtype=torch.int32, device=dev) if with_pairs else None
+        ks = torch.empty((count,), dtype=torch.complex128, device=dev) if with_pairs else None
+        self._chk("bem_surrogate_samples", self._lib.bem_surrogate_samples(
+            self._h, float(k_re[0]), float(k_re[1]), float(k_im[0]), float(k_im[1]), int(count),
+            int(seed), _ptr(feat), _ptr(targ), _ptr(pairs), _ptr(ks), _stream(stream)))
+        return (feat, targ, pairs, ks) if with_pairs else (feat, targ)
+
+    def surrogate_forward(self, feat, stream=None):
+        import torch
+        out = torch.empty((feat.shape[0], 2), dtype=torch.float32, device=feat.device)
+        self._chk("bem_surrogate_forward", self._lib.bem_surrogate_forward(
+            self._h, _ptr(feat), feat.shape[0], _ptr(out), _stream(stream)))
+        return out
+
+    def surrogate_grad(self, feat, targ, stream=None):
+        import torch
+        g = torch.empty(self._lib.bem_surrogate_size(), dtype=torch.float32, device=feat.device)
+        loss = _D()
+        self._chk("bem_surrogate_grad", self._lib.bem_surrogate_grad(
+            self._h, _ptr(feat), _ptr(targ), feat.shape[0], _ptr(g), ctypes.byref(loss),
+            _stream(stream)))
+        return loss.value, g
+
+    def surrogate_train(self, feat, targ, epochs, batch=4096, lr=1e-3, fit_scaling=True, seed=1,
+                        stream=None):
+        losses = np.zeros(int(epochs))
+        self._chk("bem_surrogate_train", self._lib.bem_surrogate_train(
+            self._h, _ptr(feat), _ptr(targ), feat.shape[0], int(epochs), int(batch), float(lr),
+            int(bool(fit_scaling)), int(seed), _ptr(losses), _stream(stream)))
+        return losses
 
     def set_mesh(self, xyz, tri, stream=None):
         xyz = np.ascontiguousarray(xyz, dtype=np.float64)

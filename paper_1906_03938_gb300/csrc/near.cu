@@ -450,6 +450,58 @@ __global__ void transpose32_kernel(const float2* __restrict__ V32, int64_t n, in
   Vt[t] = V32[(int64_t)c * n + l];
 }
 
+__device__ __forceinline__ double u01(uint64_t seed, uint64_t idx) {
+  uint64_t z = seed + (idx + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * 0x1.0p-53;
+}
+
+// Training samples of the surrogate network: sample t takes the near pair
+// e = floor(u * nnz) of the current mesh and k uniform in the box, u from SplitMix64 of
+// (seed, 3t, 3t+1, 3t+2); features as near_features32, target (A_near - A_7)(k) / h from
+// the FP64 8 x 8 rule (the plain quadrature judges the network). Optionally the pair
+// (row, column) and k of each sample.
+__global__ void surrogate_samples_kernel(Geometry g, const int32_t* __restrict__ ptr,
+                                         const int32_t* __restrict__ cols, int64_t nnz,
+                                         int64_t count, uint64_t seed, double kr_lo, double kr_hi,
+                                         double ki_lo, double ki_hi, float* __restrict__ feat,
+                                         float* __restrict__ target, int32_t* __restrict__ pairs,
+                                         double* __restrict__ ks, GL8 gl) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  int64_t e = (int64_t)(u01(seed, 3 * t) * (double)nnz);
+  if (e > nnz - 1) e = nnz - 1;
+  const double kr = kr_lo + (kr_hi - kr_lo) * u01(seed, 3 * t + 1);
+  const double ki = ki_lo + (ki_hi - ki_lo) * u01(seed, 3 * t + 2);
+  int64_t lo = 0, hi = g.n - 1;   // row: the last i with ptr[i] <= e
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) / 2;
+    if (ptr[mid] <= e) lo = mid; else hi = mid - 1;
+  }
+  const int64_t i = lo, l = cols[e], n = g.n;
+  const double x[3] = {g.cx[i], g.cx[n + i], g.cx[2 * n + i]};
+  NearFrame F;
+  near_frame(g, l, x, F);
+  float f[kNetIn];
+  near_features32(g, l, F, x, (float)kr, (float)ki, f);
+  // the features take k h from the float k; the target uses the same rounded k
+  const double2 c = near_corr64(g, l, x, (double)(float)kr, (double)(float)ki, false, gl);
+  const double h = g.diam[l];
+  for (int q = 0; q < kNetIn; ++q) feat[t * kNetIn + q] = f[q];
+  target[2 * t] = (float)(c.x / h);
+  target[2 * t + 1] = (float)(c.y / h);
+  if (pairs) {
+    pairs[2 * t] = (int32_t)i;
+    pairs[2 * t + 1] = (int32_t)l;
+  }
+  if (ks) {
+    ks[2 * t] = (double)(float)kr;
+    ks[2 * t + 1] = (double)(float)ki;
+  }
+}
+
 const GL8& gl8() {
   static const GL8 g = make_gl8();
   return g;
@@ -550,7 +602,8 @@ bem_status near_apply32(bem_ctx* ctx, const float2* V32, int nu, int nup, int C,
   float2* Vt = reinterpret_cast<float2*>(ctx->d_near_work);
   transpose32_kernel<<<(unsigned)((n * nu + 255) / 256), 256, 0, s>>>(V32, n, nu, Vt);
   const int N = ctx->con.N;
-  const float* net = (ctx->near_mode == 2 && ctx->net_ready) ? ctx->d_net : nullptr;
+  // the inference copy of the network (BF16-rounded weights) follows the master weights
+  const float* net = (ctx->near_mode == 2 && ctx->net_ready) ? ctx->d_net + kNetFloats : nullptr;
   near_apply32_kernel<<<(unsigned)((32 * (int64_t)n_pad * N + 255) / 256), 256, 0, s>>>(
       ctx->geo, ctx->d_near_ptr, ctx->d_near_cols, ctx->con.z, N, Vt, nu, nup, C, n_pad, Yp, slice,
       gl8(), net);
@@ -609,4 +662,24 @@ extern "C" bem_status bem_near_pairs(bem_ctx* ctx, int64_t* nnz, int32_t* row_pt
                     "bem_near_pairs copy");
   if (st == BEM_OK) st = cuda_check(ctx, cudaStreamSynchronize(s), "bem_near_pairs copy");
   return st;
+}
+
+extern "C" bem_status bem_surrogate_samples(bem_ctx* ctx, double kr_lo, double kr_hi, double ki_lo,
+                                            double ki_hi, int64_t count, uint64_t seed,
+                                            float* feat_dev, float* target_dev, int32_t* pairs_dev,
+                                            double* k_dev, void* stream) {
+  if (!ctx) return BEM_EINVAL;
+  if (count < 1 || !feat_dev || !target_dev || !(kr_hi >= kr_lo) || !(ki_hi >= ki_lo))
+    return fail(ctx, BEM_EINVAL, "bem_surrogate_samples: bad arguments");
+  if (ctx->near_mode == 0) return fail(ctx, BEM_ESTATE, "bem_surrogate_samples: near field is off");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  bem_status st = ensure_near(ctx, s);
+  if (st != BEM_OK) return st;
+  if (ctx->near_nnz == 0) return fail(ctx, BEM_ESTATE, "bem_surrogate_samples: mesh has no near pairs");
+  surrogate_samples_kernel<<<(unsigned)((count + 127) / 128), 128, 0, s>>>(
+      ctx->geo, ctx->d_near_ptr, ctx->d_near_cols, ctx->near_nnz, count, seed, kr_lo, kr_hi, ki_lo,
+      ki_hi, feat_dev, target_dev, pairs_dev, k_dev, gl8());
+  ctx->launches++;
+  return cuda_check(ctx, cudaGetLastError(), "bem_surrogate_samples");
 }

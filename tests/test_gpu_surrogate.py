@@ -1,0 +1,141 @@
+"""The learned near-field correction: training data, forward and backward kernels against the
+oracle, training on the GPU, and what the trained network gains.
+
+Bars: features to 1e-6 and targets to 1e-5 (FP32 storage of FP64 values) against the oracle's
+features and 8 x 8 rule; the GPU loss and gradient (FP32 kernels) against the oracle's FP64
+backward pass to 1e-4 relative; the GPU forward pass of the BF16-rounded inference copy against
+the oracle forward with the same parameters to 1e-4. Training must cut the loss by 20x, and on
+held-out pairs of a finer mesh the network-corrected entries must be at least 5x closer (median)
+to the 8 x 8 rule than the plain 7-point entries; the mixed projection with the network must
+land closer to the near-field oracle than the projection without any near-field treatment."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import assembly as oasm, surrogate as osur, rr as orr
+
+pytestmark = pytest.mark.gpu
+K_RE, K_IM = (5.5, 10.5), (-1.5, 1.5)
+
+
+@pytest.fixture(scope="module")
+def bem():
+    import paper_1906_03938_gb300 as b
+    from paper_1906_03938_gb300 import build
+    build.build()
+    return b
+
+
+def _ctx(bem, mesh):
+    ctx = bem.Context(0)
+    ctx.set_mesh(mesh.xyz, mesh.tri)
+    ctx.set_near_field(1)
+    return ctx
+
+
+def _diam(v):
+    return max(np.linalg.norm(v[1] - v[0]), np.linalg.norm(v[2] - v[0]), np.linalg.norm(v[2] - v[1]))
+
+
+def test_samples_match_oracle(bem):
+    mesh = synth.icosphere(3)
+    ctx = _ctx(bem, mesh)
+    feat, targ, pairs, ks = ctx.surrogate_samples(300, K_RE, K_IM, seed=7, with_pairs=True)
+    feat, targ = feat.cpu().numpy(), targ.cpu().numpy()
+    pairs, ks = pairs.cpu().numpy(), ks.cpu().numpy()
+    c, _, qp, qw = oasm.geometry(mesh)
+    row_ptr, cols = oasm.near_pairs(mesh)
+    for t in range(300):
+        i, l = pairs[t]
+        assert l in cols[row_ptr[i]:row_ptr[i + 1]]
+        v = mesh.xyz[mesh.tri[l]]
+        h = _diam(v)
+        f = osur.features(v, c[i], ks[t], h)
+        assert np.max(np.abs(feat[t] - f)) < 1e-6 * max(1.0, np.max(np.abs(f)))
+        r = np.linalg.norm(qp[l] - c[i], axis=1)
+        a7 = np.sum(qw[l] * np.exp(1j * ks[t] * r) / (4 * np.pi * r))
+        corr = (oasm.near_rule(v[0], v[1], v[2], c[i], ks[t], order=8) - a7) / h
+        assert abs(complex(targ[t, 0], targ[t, 1]) - corr) < 1e-5 * abs(corr) + 1e-12
+    ctx.close()
+
+
+def test_grad_and_forward_match_oracle(bem):
+    mesh = synth.icosphere(3)
+    ctx = _ctx(bem, mesh)
+    feat, targ = ctx.surrogate_samples(1000, K_RE, K_IM, seed=3)
+    rng = np.random.default_rng(11)
+    parts = {}
+    for name, shape in osur._SHAPES:
+        parts[name] = rng.normal(scale=0.3, size=shape)
+    fh = feat.cpu().numpy().astype(np.float64)
+    parts["in_shift"] = fh.mean(axis=0)
+    parts["in_scale"] = 1.0 / np.maximum(fh.std(axis=0), 1e-6)
+    parts["out_scale"] = np.abs(targ.cpu().numpy()).std(axis=0) + 1e-3
+    params = osur.pack(parts).astype(np.float32)
+    ctx.surrogate_set(params)
+    loss, g = ctx.surrogate_grad(feat, targ)
+    lo, go = osur.loss_and_grad(params.astype(np.float64), fh, targ.cpu().numpy().astype(np.float64))
+    g = g.cpu().numpy()
+    assert abs(loss - lo) < 1e-5 * lo
+    assert np.max(np.abs(g - go)) < 1e-4 * np.max(np.abs(go))
+    # forward of the inference copy (weights rounded to BF16)
+    inf = ctx.surrogate_params(which=1)
+    u = osur.unpack(np.arange(osur.SIZE))
+    w = np.concatenate([u[n].ravel() for n in osur.TRAINED])
+    assert np.max(np.abs(inf[w] - params[w])) <= 2.0 ** -8 * np.max(np.abs(params[w]))
+    out = ctx.surrogate_forward(feat).cpu().numpy()
+    ref, _ = osur.forward(inf.astype(np.float64), fh)
+    assert np.max(np.abs(out - ref)) < 1e-4 * np.max(np.abs(ref))
+    ctx.close()
+
+
+def test_training_and_gain_on_held_out_mesh(bem):
+    # training pairs: two spheres and an ellipsoid of different resolution
+    feats, targs = [], []
+    for seed, mesh in ((21, synth.icosphere(3)), (22, synth.icosphere(4)),
+                       (23, synth.tetrakis_sphere(3, (1.0, 0.7, 0.5)))):
+        ctx = _ctx(bem, mesh)
+        f, t = ctx.surrogate_samples(80000, K_RE, K_IM, seed=seed)
+        feats.append(f)
+        targs.append(t)
+        ctx.close()
+    feat, targ = torch.cat(feats), torch.cat(targs)
+    trainer = bem.Context(0)
+    trainer.surrogate_init(seed=5)
+    losses = trainer.surrogate_train(feat, targ, epochs=60, batch=4096, lr=2e-3)
+    assert np.all(np.isfinite(losses)) and losses[-1] < losses[0] / 20, losses
+    params = trainer.surrogate_params(which=0)
+    trainer.close()
+    # held out: pairs of a finer sphere; the network against the 8 x 8 rule (the judge)
+    mesh = synth.icosphere(5)
+    ctx = _ctx(bem, mesh)
+    ctx.surrogate_set(params)
+    f, t = ctx.surrogate_samples(20000, K_RE, K_IM, seed=99)
+    pred = ctx.surrogate_forward(f).cpu().numpy()
+    t = t.cpu().numpy()
+    err_net = np.hypot(*(pred - t).T)          # |A7 + C_net - A_near| / h
+    err_7 = np.hypot(*t.T)                     # |A7 - A_near| / h
+    gain = np.median(err_7) / np.median(err_net)
+    print("held-out median |C|", np.median(err_7), "median error", np.median(err_net), "gain", gain)
+    assert gain > 5.0
+    ctx.close()
+    # the mixed projection with the network (mode 2) against the near-field oracle
+    m = synth.icosphere(2)
+    spec = synth.ContourSpec("circle", 7.0 + 0j, 1.0, 1.0)
+    V = synth.complex_gaussian(m.n, 8, 4)
+    ctx = bem.Context(0)
+    ctx.set_mesh(m.xyz, m.tri)
+    z, w = ctx.set_contour(spec.kind, spec.centre, spec.a, spec.b, 6)
+    ctx.surrogate_set(params)
+    Vd = bem.fortran(torch.from_numpy(V).to("cuda:0"))
+    ctx.set_near_field(2)
+    _, Y2 = ctx.project(Vd, bem.PREC_MIXED, AV=True)
+    ctx.set_near_field(0)
+    _, Y0 = ctx.project(Vd, bem.PREC_MIXED, AV=True)
+    _, Yo = orr.project(m, z, V, near=True)
+    e2 = max(np.max(np.abs(Y2[j].cpu().numpy() - Yo[j])) for j in range(6))
+    e0 = max(np.max(np.abs(Y0[j].cpu().numpy() - Yo[j])) for j in range(6))
+    print("mixed A V error vs near-field oracle: with network", e2, "without near field", e0)
+    assert e2 < e0 / 3
+    ctx.close()
