@@ -7,6 +7,13 @@ nodes; Ritz basis of 64 complex Gaussian columns):
   fused assembly + projection Bhat_j = w_j V^H A(z_j) V for all 32 nodes.
 The metric counts n^2 N matrix entries assembled and projected per step.
 
+``--workload`` selects another of the synthetic workloads for a separate line (the
+default line is the unit cube): ``sphere20480`` (icosphere level 5, circle centre 7 radius
+1, N = 32, nu = 128; ``--near`` 0/1/2 selects no near-field treatment, the 8 x 8 rule, or
+the surrogate network, trained beforehand, untimed), ``ellipsoid98304`` (98304 triangles,
+circle centre 9 radius 1.5, N = 64, nu = 256) and ``batch48`` (48 ellipsoids of uneven size
+through the grouped persistent launch replayed as a CUDA graph; a step is one replay).
+
 Ranks (torchrun) run independent replicas of the step (the path has no exchange step) and
 the reported value is the sum over ranks (weak scaling). ``--impl reference`` times the
 CPU FP64 oracle on a bounded row sample of the same workload instead (rank 0 only).
@@ -42,6 +49,10 @@ def parse():
                    help="steps of the plain FP64 path timed for the speedup (0: skip)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-eig-check", action="store_true")
+    p.add_argument("--workload", default=WORKLOAD,
+                   choices=["cube3072", "sphere20480", "ellipsoid98304", "batch48"])
+    p.add_argument("--near", type=int, default=None, choices=[0, 1, 2],
+                   help="near-field mode (default: 1 for sphere20480 and ellipsoid98304, else 0)")
     return p.parse_args()
 
 
@@ -105,9 +116,9 @@ def dist_env():
     return rank, world, local
 
 
-def problem():
+def problem(name=WORKLOAD):
     import synth
-    prob = synth.workload(WORKLOAD).problems[0]
+    prob = synth.workload(name).problems[0]
     mesh = prob.mesh()
     V = synth.complex_gaussian(mesh.n, prob.nu, prob.seed)
     return prob, mesh, V
@@ -138,7 +149,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    prob, mesh, V = problem()
+    prob, mesh, V = problem(args.workload if args.workload != "batch48" else WORKLOAD)
     times = []
     base = None
     for it in range(args.warmup + args.steps):
@@ -151,13 +162,166 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "n": mesh.n, "N": prob.N, "nu": prob.nu,
-                       "sample": base["sample"]},
+            "config": {"workload": args.workload if args.workload != "batch48" else WORKLOAD,
+                       "n": mesh.n, "N": prob.N, "nu": prob.nu, "sample": base["sample"]},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"],
                              "kind": "oracle", "sample": base["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def measured_traffic(workload, precision):
+    """DRAM bytes (read + write) per launch of the fused kernel from the committed ncu
+    summary of this workload, or None when there is none or the kernel's source has changed
+    since the counters were taken (the summary records the source's SHA-256)."""
+    import hashlib
+    if precision != "mixed":
+        return None
+    path = os.path.join(ROOT, "profiles", f"mixed_apply_{workload}_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    src = os.path.join(ROOT, "paper_1906_03938_gb300", "csrc", "project_mixed.cu")
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    if rec.get("source_sha256") != sha:
+        return None
+    return rec["dram_bytes_read"] + rec["dram_bytes_write"]
+
+
+def train_surrogate(bem, device, epochs=200):
+    """Training data from the near pairs of two spheres and an ellipsoid (k over the
+    contours' range), then training with the library's own kernels; returns the parameters
+    and the loss history."""
+    import torch
+    import synth
+    t0 = time.perf_counter()
+    feats, targs = [], []
+    for seed, mesh in ((21, synth.icosphere(3)), (22, synth.icosphere(4)),
+                       (23, synth.tetrakis_sphere(3, (1.0, 0.7, 0.5)))):
+        c = bem.Context(device)
+        c.set_mesh(mesh.xyz, mesh.tri)
+        c.set_near_field(1)
+        f, t = c.surrogate_samples(300000, (5.5, 10.5), (-1.5, 1.5), seed=seed)
+        feats.append(f)
+        targs.append(t)
+        c.close()
+    feat, targ = torch.cat(feats), torch.cat(targs)
+    tr = bem.Context(device)
+    tr.surrogate_init(seed=5)
+    losses = tr.surrogate_train(feat, targ, epochs=epochs, batch=4096, lr=3e-3)
+    params = tr.surrogate_params(which=0)
+    tr.close()
+    return {"params": params, "samples": int(feat.shape[0]), "epochs": epochs,
+            "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+            "train_s": time.perf_counter() - t0}
+
+
+def run_batch(args):
+    """The 48-ellipsoid sweep through the grouped persistent launch (CUDA graph)."""
+    import torch
+    import paper_1906_03938_gb300 as bem
+    import synth
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    probs = synth.workload("batch48").problems
+    ctxs, Vh, Vd, meshes = [], [], [], []
+    for prob in probs:
+        mesh = prob.mesh()
+        c = bem.Context(local)
+        c.set_mesh(mesh.xyz, mesh.tri)
+        c.set_contour(prob.contour.kind, prob.contour.centre, prob.contour.a, prob.contour.b, prob.N)
+        V = synth.complex_gaussian(mesh.n, prob.nu, prob.seed)
+        Vh.append(torch.from_numpy(np.asfortranarray(V)).pin_memory())
+        Vd.append(bem.fortran(Vh[-1].to(dev)))
+        ctxs.append(c)
+        meshes.append(mesh)
+    t0 = time.perf_counter()
+    batch = bem.Batch(ctxs, Vd, autotune=True)
+    tune_s = time.perf_counter() - t0
+    info = batch.info()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        batch.run()
+    torch.cuda.synchronize()
+    launches0 = sum(c.launches for c in ctxs)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        batch.run()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_total = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    launches = sum(c.launches for c in ctxs) - launches0
+    # end to end: host bases in, projected matrices out, every step
+    Bh = [torch.empty(B.shape, dtype=B.dtype).pin_memory() for B in batch.Bhat]
+    e2e = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e2e[k][0].record(stream)
+        for a, b in zip(Vd, Vh):
+            a.copy_(b, non_blocking=True)
+        batch.run()
+        for a, b in zip(Bh, batch.Bhat):
+            a.copy_(b, non_blocking=True)
+        e2e[k][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_total = sum(a.elapsed_time(b) for a, b in e2e) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_total, e2e_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total, e2e_total = float(t[0]), float(t[1])
+    entries = float(sum(m.n * m.n * p.N for m, p in zip(meshes, probs)))
+    value = world * entries * args.steps / t_total
+    if rank != 0:
+        return 0
+    rates = {k: ctxs[0].microbench(k) for k in ("ex2", "sin", "cos", "rsqrt")}
+    t_entry = 7 * (1 / rates["ex2"] + 1 / rates["sin"] + 1 / rates["cos"]) + 7 / (4 * rates["rsqrt"])
+    step_s = t_total / args.steps
+    roof = {"bound": "alu", "pipe": "mufu", "achieved": entries / step_s, "peak": 1.0 / t_entry,
+            "unit": "entries/s", "frac": entries / step_s * t_entry, "traffic": None,
+            "kernel_ms": 1e3 * step_s,
+            "peak_source": "measured MUFU rates (bem_microbench); achieved over the whole graph "
+                           "replay (preparation, grouped kernel, reductions), not the kernel alone"}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = oracle_sample(probs[0], meshes[0], synth.complex_gaussian(meshes[0].n, probs[0].nu,
+                                                                        probs[0].seed))
+    bi = sum(v.numel() * 16 for v in Vh)
+    bo = sum(b.numel() * 16 for b in Bh)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16x3", "data": "synthetic",
+            "config": {"workload": "batch48", "problems": len(probs),
+                       "n_range": [min(m.n for m in meshes), max(m.n for m in meshes)],
+                       "entries_per_step": entries, "precision": "mixed",
+                       "launch": "grouped persistent kernel in a CUDA graph",
+                       "autotuned": info, "autotune_s": tune_s,
+                       "parallelism": f"replicas{world}", "l2": "flushed between steps (512 MB write)"},
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": world * entries * args.steps / e2e_total, "unit": UNIT,
+                    "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
+            "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    batch.close()
+    for c in ctxs:
+        c.close()
     return 0
 
 
@@ -171,12 +335,20 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    prob, mesh, V = problem()
+    prob, mesh, V = problem(args.workload)
     n, N, nu = mesh.n, prob.N, prob.nu
     prec = bem.PREC_MIXED if args.precision == "mixed" else bem.PREC_FP64
     c = prob.contour
     ctx = bem.Context(local)
     stream = torch.cuda.current_stream()
+    near = args.near if args.near is not None else (1 if n > 10000 else 0)
+    surrogate = None
+    if near == 2:
+        surrogate = train_surrogate(bem, local)      # untimed: data generation and training
+        ctx.surrogate_set(surrogate["params"])
+    if near:
+        ctx.set_mesh(mesh.xyz, mesh.tri)
+        ctx.set_near_field(near)
 
     V_host = torch.from_numpy(np.asfortranarray(V)).pin_memory()   # column-major host copy
     V_res = bem.fortran(V_host.to(dev))                              # resident input
@@ -284,12 +456,12 @@ def run_ours(args):
                                + ", ".join(f"{k} {v:.3e}/s" for k, v in rates.items())
                                + f"; 21 MUFU ops per entry-node + 7 rsqrt per entry / G={G}"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = measured_traffic(args.workload, args.precision)
     roof["kernel_ms"] = kern_avg
     roof["launches_timed"] = len(kern_ms)
 
     plain = None
-    if prec != bem.PREC_FP64 and args.plain_steps > 0:
+    if prec != bem.PREC_FP64 and args.plain_steps > 0 and args.workload == "cube3072":
         # the plain FP64 GPU path on the same workload, for the speedup of the mixed form
         ms = []
         for _ in range(args.plain_steps):
@@ -312,13 +484,14 @@ def run_ours(args):
     # projection (Algorithm 1 basis, reduced solve, FP64 refinement), untimed, against the
     # oracle's discrete eigenvalues stored under tests/golden
     eig = None
-    if not args.no_eig_check:
+    golden = os.path.join(ROOT, "tests", "golden", f"eigs_{args.workload}.txt")
+    if not args.no_eig_check and os.path.exists(golden) and not near:
         t0 = time.perf_counter()
         lam, X, rel = ctx.solve(V_res, q=10, precision=prec, tol=1e-14)
         torch.cuda.synchronize()
         t_solve = time.perf_counter() - t0
         gold = []
-        for line in open(os.path.join(ROOT, "tests", "golden", f"eigs_{WORKLOAD}.txt")):
+        for line in open(golden):
             if not line.startswith("#"):
                 re_, im_, mult, ins = line.split()
                 if int(ins):
@@ -350,8 +523,10 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == bem.PREC_FP64 else "f32+bf16x3", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "mesh": mesh.name, "n": n, "N": N, "nu": nu,
-                   "contour": "ellipse c=6.5 a=1.5 b=0.4", "precision": args.precision,
+        "config": {"workload": args.workload, "mesh": mesh.name, "n": n, "N": N, "nu": nu,
+                   "contour": f"{c.kind} c={c.centre.real:g} a={c.a:g} b={c.b:g}",
+                   "precision": args.precision,
+                   "near_field": ["off", "8x8 rule", "surrogate network"][near],
                    "parallelism": f"replicas{world}", "l2": "flushed between steps (512 MB write)",
                    "wall_s_timed": wall},
         "roofline": roof,
@@ -363,6 +538,8 @@ def run_ours(args):
         "plain_fp64": plain,
         "eig_check": eig,
     }
+    if surrogate is not None:
+        line["surrogate"] = {k: v for k, v in surrogate.items() if k != "params"}
     print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -375,6 +552,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch48":
+        return run_batch(args)
     return run_ours(args)
 
 

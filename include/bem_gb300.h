@@ -290,11 +290,12 @@ bem_status bem_near_pairs(bem_ctx* ctx, int64_t* nnz, int32_t* row_ptr_host, int
  *   from the FP64 8 x 8 rule; optionally pairs_dev (count x 2 int32: row, panel) and k_dev
  *   (count complex). Asynchronous.
  * bem_surrogate_forward: outputs of the inference copy. Asynchronous.
- * bem_surrogate_grad: mean over the samples of the squared error summed over the outputs
- *   (*loss_host) and its gradient with respect to the master parameters (grad_dev,
+ * bem_surrogate_grad: mean over the samples of the squared error in units of out_scale,
+ *   summed over the outputs (*loss_host), and its gradient with respect to the master parameters (grad_dev,
  *   bem_surrogate_size() floats; zero for the scalings), FP32 forward and backward kernels
  *   of the library. Synchronous.
- * bem_surrogate_train: `epochs` passes of Adam (lr, betas 0.9 / 0.999) over the samples in
+ * bem_surrogate_train: `epochs` passes of Adam (betas 0.9 / 0.999; the step size decays
+ *   geometrically from lr to lr / 100 over the run) over the samples in
  *   batches of `batch`, each epoch in an affine permutation of the samples; fit_scaling != 0
  *   first sets the standardisation and output scale from the samples' means and standard
  *   deviations. loss_host (nullable, epochs doubles): mean batch loss per epoch. Refreshes
@@ -317,6 +318,34 @@ bem_status bem_surrogate_grad(bem_ctx* ctx, const float* feat_dev, const float* 
 bem_status bem_surrogate_train(bem_ctx* ctx, const float* feat_dev, const float* target_dev,
                                int64_t count, int epochs, int batch, double lr, int fit_scaling,
                                uint64_t seed, double* loss_host, void* stream);
+
+/*
+ * Context statistics and checkpoints (operational support; the paper has no counterpart).
+ * bem_stats: the context's sizes and counters: device, panels n, vertices nv, contour nodes N
+ *   (0 before bem_set_contour), near-field mode and its pair count (-1 while the list is not
+ *   built for the current mesh), kernel launches so far, bytes of device workspace held,
+ *   whether a surrogate network is loaded. Host only, no synchronisation.
+ * bem_save_state: writes a checkpoint of what defines the operator and the contour (mesh,
+ *   contour, near-field mode, surrogate network master parameters) into buf (host). With
+ *   buf == NULL it only sets *len to the size needed; with *len too small it fails with
+ *   BEM_EINVAL and sets *len. Synchronous. BEM_ESTATE without a mesh.
+ * bem_load_state: restores such a checkpoint into a context (any device): sets the mesh,
+ *   the network, the contour and the near-field mode as the corresponding calls would.
+ *   BEM_EINVAL for a buffer that is not a checkpoint, truncated or inconsistent.
+ */
+typedef struct {
+  int device;
+  int64_t n, nv;
+  int N;
+  int near_mode;
+  int64_t near_pairs;
+  int64_t launches;
+  int64_t workspace_bytes;
+  int surrogate_ready;
+} bem_stats_t;
+bem_status bem_stats(const bem_ctx* ctx, bem_stats_t* out);
+bem_status bem_save_state(bem_ctx* ctx, void* buf, size_t* len, void* stream);
+bem_status bem_load_state(bem_ctx* ctx, const void* buf, size_t len, void* stream);
 
 /*
  * Batched projection (Section 3's projection for many independent problems at once, as a

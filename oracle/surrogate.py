@@ -7,8 +7,9 @@ frame with its origin at the collocation point x, e1 along (b - a), e3 along the
 (b - a) x (c - b) flipped so that a lies on its non-negative side, e2 = e3 x e1 (a the vertex
 nearest x, b and c following it in the triangle's order), each divided by h; then Re(k h),
 Im(k h). Network: standardisation (f - shift) * scale, then 11 -> 64 -> 64 -> 64 -> 2 with
-tanh on the hidden layers, the output multiplied by out_scale. Loss: mean over samples of
-the squared error summed over the two outputs.
+tanh on the hidden layers; the prediction is out_scale * z / (d/h)^7, z the last layer's
+output and d/h the distance from x to the triangle's centroid read off the features.
+Loss: mean over samples of sum_o (z_o - target_o (d/h)^7 / out_scale_o)^2.
 
 Parameter layout (one flat array, the same order as the library's):
 in_shift[11], in_scale[11], W1[64][11], b1[64], W2[64][64], b2[64], W3[64][64], b3[64],
@@ -40,26 +41,34 @@ def pack(parts):
                            for name, _ in _SHAPES])
 
 
+def decay(feat):
+    """(d/h)^7 per sample, d/h the norm of the mean of the three vertex features."""
+    f = np.asarray(feat, dtype=np.float64)
+    c = (f[:, 0:3] + f[:, 3:6] + f[:, 6:9]) / 3.0
+    return np.sum(c * c, axis=1) ** 3.5
+
+
 def forward(params, feat):
-    """Network output (n, 2) and the activations needed by the backward pass."""
+    """Prediction (n, 2) and the activations needed by the backward pass."""
     p = unpack(np.asarray(params, dtype=np.float64))
     x = (np.asarray(feat, dtype=np.float64) - p["in_shift"]) * p["in_scale"]
     h1 = np.tanh(x @ p["W1"].T + p["b1"])
     h2 = np.tanh(h1 @ p["W2"].T + p["b2"])
     h3 = np.tanh(h2 @ p["W3"].T + p["b3"])
     z = h3 @ p["W4"].T + p["b4"]
-    return z * p["out_scale"], (x, h1, h2, h3)
+    return z * p["out_scale"] / decay(feat)[:, None], (x, h1, h2, h3, z)
 
 
 def loss_and_grad(params, feat, target):
-    """Mean over samples of sum_o (pred_o - target_o)^2 and its gradient with respect to the
-    flat parameter array (zero for the standardisation and output scaling)."""
+    """Mean over samples of sum_o (z_o - target_o (d/h)^7 / out_scale_o)^2 and its gradient
+    with respect to the flat parameter array (zero for the standardisation and output
+    scaling)."""
     p = unpack(np.asarray(params, dtype=np.float64))
-    pred, (x, h1, h2, h3) = forward(params, feat)
+    pred, (x, h1, h2, h3, z) = forward(params, feat)
     n = pred.shape[0]
-    diff = pred - np.asarray(target, dtype=np.float64)
+    diff = z - np.asarray(target, dtype=np.float64) * decay(feat)[:, None] / p["out_scale"]
     loss = np.sum(diff * diff) / n
-    dz = 2.0 * diff * p["out_scale"] / n                  # dL/dz, z the pre-scaling output
+    dz = 2.0 * diff / n                                   # dL/dz, z the pre-scaling output
     g = {name: np.zeros(shape) for name, shape in _SHAPES}
     g["W4"] = dz.T @ h3
     g["b4"] = dz.sum(axis=0)

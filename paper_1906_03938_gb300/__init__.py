@@ -75,6 +75,20 @@ SIGNATURES = {
     "bem_project_batched": (_I, [_P, _I, _P, _P, _P, _P, _I, _P]),
 }
 
+class Stats(ctypes.Structure):
+    """bem_stats_t"""
+    _fields_ = [("device", ctypes.c_int), ("n", ctypes.c_int64), ("nv", ctypes.c_int64),
+                ("N", ctypes.c_int), ("near_mode", ctypes.c_int), ("near_pairs", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
+                ("surrogate_ready", ctypes.c_int)]
+
+
+SIGNATURES.update({
+    "bem_stats": (_I, [_P, ctypes.POINTER(Stats)]),
+    "bem_save_state": (_I, [_P, _P, ctypes.POINTER(ctypes.c_size_t), _P]),
+    "bem_load_state": (_I, [_P, _P, ctypes.c_size_t, _P]),
+})
+
 _lib = None
 
 
@@ -258,6 +272,25 @@ class Context:
             self._h, _ptr(feat), _ptr(targ), feat.shape[0], int(epochs), int(batch), float(lr),
             int(bool(fit_scaling)), int(seed), _ptr(losses), _stream(stream)))
         return losses
+
+    def stats(self):
+        st = Stats()
+        self._chk("bem_stats", self._lib.bem_stats(self._h, ctypes.byref(st)))
+        return {name: getattr(st, name) for name, _ in Stats._fields_}
+
+    def save_state(self):
+        """Checkpoint (bytes) of the mesh, contour, near-field mode and network."""
+        n = ctypes.c_size_t(0)
+        self._chk("bem_save_state", self._lib.bem_save_state(self._h, None, ctypes.byref(n), None))
+        buf = ctypes.create_string_buffer(n.value)
+        self._chk("bem_save_state", self._lib.bem_save_state(self._h, buf, ctypes.byref(n), None))
+        return buf.raw[:n.value]
+
+    def load_state(self, data):
+        buf = ctypes.create_string_buffer(bytes(data), len(data))
+        self._chk("bem_load_state", self._lib.bem_load_state(self._h, buf, len(data), None))
+        st = self.stats()
+        self.n, self.N = int(st["n"]), int(st["N"])
 
     def set_mesh(self, xyz, tri, stream=None):
         xyz = np.ascontiguousarray(xyz, dtype=np.float64)

@@ -2,8 +2,9 @@
 // with the library's own forward and backward kernels (FP32) and Adam.
 //
 // The network (layout in surrogate.cuh) maps a near pair's canonical features to
-// (A_near - A_7) / h. Training minimises the mean over samples of the squared error summed
-// over the two outputs. One block handles 64 samples: the forward pass keeps the three
+// (A_near - A_7) / h. Training minimises the mean over samples of the squared error at the
+// network's output, i.e. in units of out_scale / (d / h)^7 (relative to the size the
+// correction has at that distance), summed over the two outputs. One block handles 64 samples: the forward pass keeps the three
 // hidden layers in shared memory, the backward pass forms the block's gradient with sums
 // over its samples in a fixed order; block gradients are then added in block order and
 // Adam updates the trained parameters (deterministic). The standardisation of the features
@@ -73,16 +74,24 @@ __global__ void forward_kernel(const float* __restrict__ net, const float* __res
   out[2 * t + 1] = o.y;
 }
 
-// Mean and standard deviation of column c of the features (c < 11) or the targets
-// (c = 11, 12): one block per column, fixed-order FP64 sums. Sets in_shift / in_scale
-// (1 / std, or 1 for a constant column) and out_scale (std, or 1).
+// Mean and standard deviation of column c of the features (c < 11) or of the network's
+// targets (c = 11, 12: target times (d / h)^7): one block per column, fixed-order FP64
+// sums. Sets in_shift / in_scale (1 / std, or 1 for a constant column) and out_scale (std,
+// or 1).
 __global__ void fit_scaling_kernel(const float* __restrict__ feat, const float* __restrict__ target,
                                    int64_t count, float* __restrict__ net) {
   __shared__ double s1[256], s2[256];
   const int c = blockIdx.x;
   double a = 0.0, b = 0.0;
   for (int64_t t = threadIdx.x; t < count; t += blockDim.x) {
-    const double v = c < kNetIn ? feat[t * kNetIn + c] : target[t * kNetOut + (c - kNetIn)];
+    double v;
+    if (c < kNetIn) {
+      v = feat[t * kNetIn + c];
+    } else {   // the network's own target: (A_near - A_7) / h times (d / h)^7
+      float f[kNetIn];
+      for (int q = 0; q < kNetIn; ++q) f[q] = feat[t * kNetIn + q];
+      v = (double)target[t * kNetOut + (c - kNetIn)] * (double)surrogate_decay(f);
+    }
     a += v;
     b += v * v;
   }
@@ -136,6 +145,7 @@ grad_kernel(const float* __restrict__ net, const float* __restrict__ feat,
   float* W3 = W2 + kNetHid * kNetHid;
   float* W4 = W3 + kNetHid * kNetHid;          // [2][64]
   __shared__ float red[256];
+  __shared__ float sdec[kGS];                  // (d / h)^7 of each sample
   const int tid = threadIdx.x;
   const int64_t first = start + (int64_t)blockIdx.x * kGS;
   const int64_t left = end - first;
@@ -155,6 +165,17 @@ grad_kernel(const float* __restrict__ net, const float* __restrict__ feat,
       v = (feat[idx * kNetIn + i] - net[kOffInShift + i]) * net[kOffInScale + i];
     }
     xs[t] = v;
+  }
+  if (tid < kGS) {
+    float dec = 1.f;
+    if (tid < ns) {
+      const int64_t idx = (int64_t)(((uint64_t)perm_a * (uint64_t)(first + tid) + (uint64_t)perm_c) %
+                                    (uint64_t)count);
+      float f[kNetIn];
+      for (int q = 0; q < kNetIn; ++q) f[q] = feat[idx * kNetIn + q];
+      dec = surrogate_decay(f);
+    }
+    sdec[tid] = dec;
   }
   __syncthreads();
   const int s = tid % kGS, og = tid / kGS;   // lanes over samples, 4 groups of outputs
@@ -186,10 +207,12 @@ grad_kernel(const float* __restrict__ net, const float* __restrict__ feat,
     if (s < ns) {
       const int64_t idx = (int64_t)(((uint64_t)perm_a * (uint64_t)(first + s) + (uint64_t)perm_c) %
                                     (uint64_t)count);
+      // the error at the network's output, in units of out_scale / (d/h)^7:
+      // (pred - t) (d/h)^7 / osc = z - t (d/h)^7 / osc
       const float osc = net[kOffOutScale + o];
-      const float diff = a * osc - target[idx * kNetOut + o];
+      const float diff = a - target[idx * kNetOut + o] * sdec[s] / osc;
       lsum = diff * diff;
-      d = 2.f * diff * osc * inv_n;
+      d = 2.f * diff * inv_n;
     }
     dz[s * kNetOut + o] = d;
   }
@@ -512,8 +535,10 @@ bem_status bem_surrogate_train(bem_ctx* ctx, const float* feat_dev, const float*
       if (st != BEM_OK) break;
       ++t_adam;
       const float bc1 = 1.f - powf(0.9f, (float)t_adam), bc2 = 1.f - powf(0.999f, (float)t_adam);
+      // learning rate decayed geometrically from lr to lr / 100 over the run
+      const float lr_t = (float)(lr * pow(0.01, (double)(t_adam - 1) / (double)(epochs * steps)));
       adam_kernel<<<(kOffTrainEnd - kOffTrainBegin + 255) / 256, 256, 0, s>>>(
-          b.master, b.m, b.v, b.grad, (float)lr, bc1, bc2);
+          b.master, b.m, b.v, b.grad, lr_t, bc1, bc2);
       ctx->launches++;
     }
     if (st == BEM_OK)

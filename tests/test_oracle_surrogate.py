@@ -1,6 +1,6 @@
 """Pins of the surrogate network's oracle (oracle/surrogate.py): the backward pass against
 central finite differences of the forward pass in FP64, the forward pass in a case with a
-closed form, and the invariances of the canonical features and of the normalised target
+closed form (including the (d/h)^7 decay factor), and the invariances of the canonical features and of the normalised target
 (rigid motions, cyclic vertex order, joint scaling of geometry and wavelength)."""
 import numpy as np
 
@@ -44,8 +44,12 @@ def test_forward_constant_when_hidden_weights_vanish():
     p = osur.unpack(_random_params(rng))
     p = {k: v.copy() for k, v in p.items()}
     p["W4"][:] = 0.0
-    out, _ = osur.forward(osur.pack(p), rng.normal(size=(5, osur.IN)))
-    assert np.allclose(out, p["b4"] * p["out_scale"], rtol=0, atol=0)
+    feat = rng.normal(size=(5, osur.IN))
+    out, _ = osur.forward(osur.pack(p), feat)
+    # the prediction is out_scale * b4 / (d/h)^7, d/h the norm of the vertices' mean
+    c = (feat[:, 0:3] + feat[:, 3:6] + feat[:, 6:9]) / 3.0
+    dh = np.sqrt(np.sum(c * c, axis=1))
+    assert np.allclose(out * dh[:, None] ** 7, p["b4"] * p["out_scale"], rtol=1e-13, atol=0)
 
 
 def _rotation(rng):
