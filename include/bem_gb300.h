@@ -52,7 +52,11 @@ typedef enum {
     BEM_PREC_MIXED = 1  /* FP32 evaluation, BF16x3 split-precision tcgen05 contraction */
 } bem_precision;
 
-typedef enum { BEM_CONTOUR_CIRCLE = 0, BEM_CONTOUR_ELLIPSE = 1 } bem_contour_kind;
+typedef enum {
+    BEM_CONTOUR_CIRCLE = 0,
+    BEM_CONTOUR_ELLIPSE = 1,
+    BEM_CONTOUR_CHEBYSHEV = 2   /* Chebyshev points of a real interval (Eq. Chebyshev) */
+} bem_contour_kind;
 
 /* Create a context on CUDA device `device`. */
 bem_status bem_create(bem_ctx** out, int device);
@@ -85,6 +89,9 @@ bem_status bem_set_mesh(bem_ctx* ctx, int64_t nv, const double* xyz_host, int64_
  * w_host (2*N doubles each) may
  * be NULL; if given they receive the nodes / weights. Requires a mesh. N in [1, 4096],
  * a > 0, b > 0. Synchronises the stream before returning.
+ * Kind CHEBYSHEV (Section 2, Eq. Chebyshev): the Chebyshev points of the first kind of the
+ * interval [c_re - a, c_re + a] shifted by i c_im, z_k = c + a cos(pi (k + 1/2) / N), and
+ * unit weights (bem_project then returns the unweighted V^H A(z_k) V); b is ignored.
  */
 bem_status bem_set_contour(bem_ctx* ctx, int kind, double c_re, double c_im, double a,
                            double b, int N, double* z_host, double* w_host, void* stream);
@@ -241,6 +248,30 @@ int64_t bem_kernel_launches(const bem_ctx* ctx);
 bem_status bem_set_timing(bem_ctx* ctx, int enable);
 bem_status bem_kernel_times(bem_ctx* ctx, double* ms_out, int max_out, int* count);
 bem_status bem_microbench(bem_ctx* ctx, int kind, double* ops_per_s);
+
+/*
+ * Chebyshev variant (Section 2, Eq. Chebyshev; Section 3, Eq. sc1_chebyshev_red; the
+ * setting of Algorithm 2), for eigenvalues near a real interval. Requires a contour of kind
+ * CHEBYSHEV with N >= 4 points (interpolation degree m = N - 1).
+ * bem_chebyshev_coeffs: from P_dev = the unweighted projections V^H A(z_k) V of bem_project
+ *   (N x nu x nu, as Bhat), the coefficients of the interpolant in the Chebyshev basis,
+ *   B_i = (2 - delta_i0) / N sum_k cos(i pi (k + 1/2) / N) P_k, i = 0..N-1 (B_dev, same
+ *   layout). Asynchronous.
+ * bem_solve_chebyshev: eigenpairs of sum_i B_i T_i(zeta) y = 0, zeta = (z - c) / a, nearest
+ *   the shift (in z units), by subspace iteration of block size p with the shift-and-invert
+ *   operator of the colleague linearisation (A - sigma M)^{-1} M, A w = zeta M w,
+ *   w = [T_0 y; ..; T_{m-1} y]; each application solves the block system by the three-term
+ *   recurrence and one nu x nu system (Algorithm 2 at sigma = 0). Outputs as
+ *   bem_solve_reduced: lam_host (2p doubles, z units), Y_dev (nu x p, the y-parts), res_host
+ *   (p reduced residuals ||sum_i T_i(zeta) B_i y|| / (||y|| sum_i |T_i(zeta)| ||B_i||_1)).
+ *   Stops when the dominant half of the Ritz values with |Re zeta| < 1 and |Im zeta| < 0.25
+ *   has residuals <= tol, or after max_iter steps. Synchronises the stream.
+ */
+bem_status bem_chebyshev_coeffs(bem_ctx* ctx, const double* P_dev, int nu, double* B_dev,
+                                void* stream);
+bem_status bem_solve_chebyshev(bem_ctx* ctx, const double* B_dev, int nu, double shift_re,
+                               double shift_im, int p, int max_iter, double tol, double* lam_host,
+                               double* Y_dev, double* res_host, int* iters_done, void* stream);
 
 /*
  * Near-field treatment (an operator variant for fine meshes; the paper integrates the

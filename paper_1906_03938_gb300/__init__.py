@@ -26,6 +26,7 @@ PREC_FP64 = 0
 PREC_MIXED = 1
 CONTOUR_CIRCLE = 0
 CONTOUR_ELLIPSE = 1
+CONTOUR_CHEBYSHEV = 2
 
 # name -> (restype, argtypes) of every symbol declared in include/bem_gb300.h
 _P = ctypes.c_void_p
@@ -56,6 +57,9 @@ SIGNATURES = {
     "bem_microbench": (_I, [_P, _I, ctypes.POINTER(_D)]),
     "bem_project_fp64_noalloc": (_I, [_I, _I64, _P, _I64, _P, _I, _D, _D, _D, _D, _I, _P,
                                       _I64, _I, _P, _P]),
+    "bem_chebyshev_coeffs": (_I, [_P, _P, _I, _P, _P]),
+    "bem_solve_chebyshev": (_I, [_P, _P, _I, _D, _D, _I, _I, _D, _P, _P, _P, ctypes.POINTER(_I),
+                                 _P]),
     "bem_set_near_field": (_I, [_P, _I, _P]),
     "bem_near_pairs": (_I, [_P, ctypes.POINTER(_I64), _P, _P, _P]),
     "bem_surrogate_size": (_I, []),
@@ -301,7 +305,8 @@ class Context:
         self.n = int(tri.shape[0])
 
     def set_contour(self, kind, centre, a, b, N, stream=None):
-        kinds = {"circle": CONTOUR_CIRCLE, "ellipse": CONTOUR_ELLIPSE}
+        kinds = {"circle": CONTOUR_CIRCLE, "ellipse": CONTOUR_ELLIPSE,
+                 "chebyshev": CONTOUR_CHEBYSHEV}
         k = kinds[kind] if isinstance(kind, str) else int(kind)
         z = np.zeros(2 * N)
         w = np.zeros(2 * N)
@@ -345,6 +350,34 @@ class Context:
         it = _I(0)
         sh = complex(shift)
         self._chk("bem_solve_reduced", self._lib.bem_solve_reduced(
+            self._h, _ptr(Bm), nu, sh.real, sh.imag, int(p), int(max_iter), float(tol),
+            _ptr(lam), _ptr(Y), _ptr(res), ctypes.byref(it), _stream(stream)))
+        return lam.view(np.complex128), Y.transpose(0, 1), res, it.value
+
+    def chebyshev_coeffs(self, P, stream=None):
+        """Chebyshev coefficients B_0..B_{N-1} of the reduced interpolant from the projections
+        P (N x nu x nu, as returned by project on a Chebyshev contour)."""
+        import torch
+        N, nu, _ = P.shape
+        Pm = P.transpose(1, 2).contiguous()
+        Bm = torch.empty_like(Pm)
+        self._chk("bem_chebyshev_coeffs", self._lib.bem_chebyshev_coeffs(
+            self._h, _ptr(Pm), nu, _ptr(Bm), _stream(stream)))
+        return Bm.transpose(1, 2)
+
+    def solve_chebyshev(self, B, shift, p=None, max_iter=200, tol=1e-12, stream=None):
+        """Eigenpairs of sum_i B_i T_i(zeta) y = 0 nearest shift: (lam, Y, res, iters)."""
+        import torch
+        N, nu, _ = B.shape
+        if p is None:
+            p = min((N - 1) * nu, 256, max(2 * nu, 32))
+        Bm = B.transpose(1, 2).contiguous()
+        lam = np.zeros(2 * p)
+        res = np.zeros(p)
+        Y = torch.empty((p, nu), dtype=torch.complex128, device=B.device)
+        it = _I(0)
+        sh = complex(shift)
+        self._chk("bem_solve_chebyshev", self._lib.bem_solve_chebyshev(
             self._h, _ptr(Bm), nu, sh.real, sh.imag, int(p), int(max_iter), float(tol),
             _ptr(lam), _ptr(Y), _ptr(res), ctypes.byref(it), _stream(stream)))
         return lam.view(np.complex128), Y.transpose(0, 1), res, it.value

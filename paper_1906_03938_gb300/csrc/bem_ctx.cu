@@ -218,9 +218,9 @@ bem_status bem_set_contour(bem_ctx* ctx, int kind, double c_re, double c_im, dou
                            double b, int N, double* z_host, double* w_host, void* stream) {
   if (!ctx) return BEM_EINVAL;
   if (ctx->geo.n == 0) return fail(ctx, BEM_ESTATE, "bem_set_contour: no mesh set");
-  if (kind != BEM_CONTOUR_CIRCLE && kind != BEM_CONTOUR_ELLIPSE)
+  if (kind != BEM_CONTOUR_CIRCLE && kind != BEM_CONTOUR_ELLIPSE && kind != BEM_CONTOUR_CHEBYSHEV)
     return fail(ctx, BEM_EINVAL, "bem_set_contour: unknown contour kind");
-  if (kind == BEM_CONTOUR_CIRCLE) b = a;
+  if (kind == BEM_CONTOUR_CIRCLE || kind == BEM_CONTOUR_CHEBYSHEV) b = a;
   if (!(a > 0.0) || !(b > 0.0) || !isfinite(a) || !isfinite(b) || !isfinite(c_re) ||
       !isfinite(c_im))
     return fail(ctx, BEM_EINVAL, "bem_set_contour: semi-axes must be positive and finite");

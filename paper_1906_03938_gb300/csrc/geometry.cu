@@ -3,7 +3,8 @@
 // * Panel geometry (the constant-element discretisation of Section 1): centroid x_l,
 //   area |T_l| and Radon's 7-point degree-5 rule mapped onto each triangle. Weights are
 //   stored as W_lq / (4 pi) so that an off-diagonal entry is sum_q qw * exp(i k r) / r.
-// * Contour (Section 2, Eq. Tz, Eq. TzApp): trapezoid nodes theta_j = 2 pi (j + 1/2) / N.
+// * Contour (Section 2, Eq. Tz, Eq. TzApp): trapezoid nodes theta_j = 2 pi (j + 1/2) / N;
+//   or the Chebyshev points of a real interval (Eq. Chebyshev) with unit weights.
 // * Self terms A_ll(z_j) for every panel and node (see selfterm.cuh), in FP64 for the plain
 //   path and in FP32 for the mixed path.
 #include <math.h>
@@ -141,6 +142,13 @@ __global__ void contour_kernel(int N, int kind, double c_re, double c_im, double
                                double* z, double* w) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= N) return;
+  if (kind == BEM_CONTOUR_CHEBYSHEV) {   // Chebyshev points of [c - a, c + a], unit weights
+    z[2 * j] = c_re + a * cospi((j + 0.5) / N);
+    z[2 * j + 1] = c_im;
+    w[2 * j] = 1.0;
+    w[2 * j + 1] = 0.0;
+    return;
+  }
   if (kind == BEM_CONTOUR_CIRCLE) b = a;
   double s, c;
   sincospi((2.0 * j + 1.0) / N, &s, &c);   // theta_j = pi (2 j + 1) / N

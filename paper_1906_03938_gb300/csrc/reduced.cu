@@ -268,6 +268,180 @@ __global__ void small_eig_kernel(int m, double2* A, double2* w, double2* V, doub
   if (rc != 0) atomicOr(status, kStatusNonFinite);
 }
 
+// ---- Chebyshev variant (Eq. Chebyshev, Eq. sc1_chebyshev_red, Algorithm 2's setting) ----
+//
+// With projected samples P_k = V^H T(x_k) V at the Chebyshev points of [c - a, c + a], the
+// reduced interpolant is sum_i B^_i T_i(zeta), zeta = (z - c) / a, and its colleague
+// linearisation A w = zeta M w, w = [v_0; ..; v_{m-1}], v_i = T_i(zeta) y. Shift-and-invert
+// about sigma (zeta units): (A - sigma M) w' = M w is solved by the three-term recurrence
+// of the first m - 1 block rows, v'_i = e_i + T_i(sigma) u with e_0 = 0, e_1 = y_0,
+// e_{i+1} = y_i - e_{i-1} + 2 sigma e_i (y = M w), and the last block row, which leaves the
+// nu x nu system G u = b, G = sum_i T_i(sigma) L_i, b = y_{m-1} - sum_i L_i e_i, where
+// L_i = -B^_i (i <= m-3), L_{m-2} = B^_m - B^_{m-2}, L_{m-1} = -B^_{m-1} - 2 sigma B^_m.
+// (Algorithm 2 is this solve at sigma = 0.)
+
+// table[i N + k] = (2 - delta_i0) / N cos(i pi (k + 1/2) / N)
+__global__ void cheb_table_kernel(int N, double* table) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * N) return;
+  const int i = t / N, k = t % N;
+  table[t] = (i == 0 ? 1.0 : 2.0) / N * cospi((double)i * (k + 0.5) / N);
+}
+
+// B_i = sum_k table[i N + k] P_k (fixed order), P_k and B_i nu x nu.
+__global__ void cheb_coeff_kernel(const double2* __restrict__ P, const double* __restrict__ table,
+                                  int N, int64_t nn, double2* __restrict__ B) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)N * nn) return;
+  const int i = (int)(t / nn);
+  const int64_t e = t % nn;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int k = 0; k < N; ++k) {
+    const double c = table[i * N + k];
+    const double2 p = P[(int64_t)k * nn + e];
+    acc.x += c * p.x;
+    acc.y += c * p.y;
+  }
+  B[t] = acc;
+}
+
+// L = [L_0 .. L_{m-1}] (nu x m nu, ld nu) and G = sum_i s_i L_i, s_i = T_i(sigma).
+__global__ void cheb_setup_kernel(const double2* __restrict__ B, int m, int nu, double2 sigma,
+                                  const double2* __restrict__ sT, double2* __restrict__ L,
+                                  double2* __restrict__ G) {
+  const int64_t nn = (int64_t)nu * nu;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nn) return;
+  double2 g = make_double2(0.0, 0.0);
+  for (int i = 0; i < m; ++i) {
+    double2 l;
+    if (i <= m - 3) {
+      l = make_double2(-B[i * nn + e].x, -B[i * nn + e].y);
+    } else if (i == m - 2) {
+      l = make_double2(B[m * nn + e].x - B[(m - 2) * nn + e].x, B[m * nn + e].y - B[(m - 2) * nn + e].y);
+    } else {
+      const double2 bm = zmul_(make_double2(2.0 * sigma.x, 2.0 * sigma.y), B[m * nn + e]);
+      l = make_double2(-B[(m - 1) * nn + e].x - bm.x, -B[(m - 1) * nn + e].y - bm.y);
+    }
+    L[i * nn + e] = l;
+    const double2 sl = zmul_(sT[i], l);
+    g.x += sl.x;
+    g.y += sl.y;
+  }
+  G[e] = g;
+}
+
+// E = the u-independent parts e_0..e_{m-1} of the solve, from W (y = M W on the fly; the
+// last block row is handled separately). One thread per (row of a block, column).
+__global__ void cheb_recur_kernel(const double2* __restrict__ W, int m, int nu, int p,
+                                  double2 sigma, double2* __restrict__ E) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nu * p) return;
+  const int r = (int)(t % nu), c = (int)(t / nu);
+  const int64_t ld = (int64_t)m * nu;
+  const double2* w = W + (int64_t)c * ld + r;
+  double2* e = E + (int64_t)c * ld + r;
+  double2 em1 = make_double2(0.0, 0.0);     // e_{i-1}
+  double2 ei = w[0];                         // e_1 = y_0 = w_0
+  e[0] = em1;                                // e_0 = 0
+  if (m > 1) e[nu] = ei;
+  for (int i = 1; i + 1 < m; ++i) {
+    const double2 yi = make_double2(2.0 * w[(int64_t)i * nu].x, 2.0 * w[(int64_t)i * nu].y);
+    const double2 se = zmul_(make_double2(2.0 * sigma.x, 2.0 * sigma.y), ei);
+    const double2 en = make_double2(yi.x - em1.x + se.x, yi.y - em1.y + se.y);
+    e[(int64_t)(i + 1) * nu] = en;
+    em1 = ei;
+    ei = en;
+  }
+}
+
+// HW_i = E_i + s_i U, U nu x p; HW and E are (m nu) x p.
+__global__ void cheb_combine_kernel(const double2* __restrict__ E, const double2* __restrict__ U,
+                                    const double2* __restrict__ sT, int m, int nu, int p,
+                                    double2* __restrict__ HW) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t rows = (int64_t)m * nu;
+  if (t >= rows * p) return;
+  const int64_t r = t % rows;
+  const int c = (int)(t / rows);
+  const int i = (int)(r / nu), a = (int)(r % nu);
+  const double2 su = zmul_(sT[i], U[(int64_t)c * nu + a]);
+  HW[t] = make_double2(E[t].x + su.x, E[t].y + su.y);
+}
+
+// rhs = y_{m-1} - L E = 2 BW - LE, given BW = B_m w_{m-1} and LE = L E (nu x p each)
+__global__ void cheb_rhs_kernel(const double2* __restrict__ BW, const double2* __restrict__ LE,
+                                int64_t count, double2* __restrict__ rhs) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  rhs[t] = make_double2(2.0 * BW[t].x - LE[t].x, 2.0 * BW[t].y - LE[t].y);
+}
+
+// ||sum_i T_i(zeta) B_i y|| / (||y|| sum_i |T_i(zeta)| ||B_i||_1), one block per Ritz pair;
+// zeta[i] in zeta units.
+__global__ void cheb_residual_kernel(const double2* __restrict__ B, const double2* __restrict__ zeta,
+                                     const double2* __restrict__ Y, int N, int nu,
+                                     double* __restrict__ res) {
+  __shared__ double red[256];
+  const int q = blockIdx.x;
+  const double2 zt = zeta[q];
+  const double2* y = Y + (int64_t)q * nu;
+  const int64_t nn = (int64_t)nu * nu;
+  double part = 0.0;
+  for (int a = threadIdx.x; a < nu; a += blockDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
+    double2 tm1 = make_double2(1.0, 0.0), ti = zt;
+    for (int i = 0; i < N; ++i) {
+      const double2 T = i == 0 ? tm1 : ti;
+      double2 s = make_double2(0.0, 0.0);
+      for (int k = 0; k < nu; ++k) {
+        const double2 pr = zmul_(B[i * nn + (int64_t)k * nu + a], y[k]);
+        s.x += pr.x;
+        s.y += pr.y;
+      }
+      const double2 ts = zmul_(T, s);
+      acc.x += ts.x;
+      acc.y += ts.y;
+      if (i >= 1) {   // advance T_i -> T_{i+1}
+        const double2 z2t = zmul_(make_double2(2.0 * zt.x, 2.0 * zt.y), ti);
+        const double2 tn = make_double2(z2t.x - tm1.x, z2t.y - tm1.y);
+        tm1 = ti;
+        ti = tn;
+      }
+    }
+    part += acc.x * acc.x + acc.y * acc.y;
+  }
+  red[threadIdx.x] = part;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double yn = 0.0, den = 0.0;
+    for (int k = 0; k < nu; ++k) yn += y[k].x * y[k].x + y[k].y * y[k].y;
+    double2 tm = make_double2(1.0, 0.0), tc = zt;
+    for (int i = 0; i < N; ++i) {
+      const double2 T = i == 0 ? tm : tc;
+      double bmax = 0.0;
+      for (int k = 0; k < nu; ++k) {
+        double cs = 0.0;
+        for (int a = 0; a < nu; ++a) cs += hypot(B[i * nn + (int64_t)k * nu + a].x, B[i * nn + (int64_t)k * nu + a].y);
+        bmax = fmax(bmax, cs);
+      }
+      den += bmax * hypot(T.x, T.y);
+      if (i >= 1) {
+        const double2 z2t = zmul_(make_double2(2.0 * zt.x, 2.0 * zt.y), tc);
+        const double2 tn = make_double2(z2t.x - tm.x, z2t.y - tm.y);
+        tm = tc;
+        tc = tn;
+      }
+    }
+    const double d = den * sqrt(yn);
+    res[q] = d > 0.0 ? sqrt(red[0]) / d : INFINITY;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_zgemm(bem_ctx* ctx, int m, int n, int k, const double* A, int64_t lda,
@@ -290,6 +464,8 @@ extern "C" bem_status bem_solve_reduced(bem_ctx* ctx, const double* Bhat_dev, in
                                         double* res_host, int* iters_done, void* stream) {
   if (!ctx) return BEM_EINVAL;
   if (ctx->con.N == 0) return fail(ctx, BEM_ESTATE, "bem_solve_reduced: no contour set");
+  if (ctx->con.kind == BEM_CONTOUR_CHEBYSHEV)
+    return fail(ctx, BEM_ESTATE, "bem_solve_reduced: a Chebyshev interval needs bem_solve_chebyshev");
   const int N = ctx->con.N;
   const int64_t rows = (int64_t)N * nu;
   if (!Bhat_dev || !lam_host || !Y_dev || !res_host || nu < 1 || nu > kMaxNu || p < 1 ||
@@ -442,4 +618,182 @@ extern "C" bem_status bem_ritz_vectors(bem_ctx* ctx, const double* V_dev, int64_
   return cuda_check(ctx, launch_zgemm(ctx, (int)n, k, nu, V_dev, ldv, Y_dev, nu, X_dev, ldx,
                                       (cudaStream_t)stream),
                     "bem_ritz_vectors");
+}
+
+extern "C" bem_status bem_chebyshev_coeffs(bem_ctx* ctx, const double* P_dev, int nu, double* B_dev,
+                                           void* stream) {
+  if (!ctx) return BEM_EINVAL;
+  if (ctx->con.N == 0 || ctx->con.kind != BEM_CONTOUR_CHEBYSHEV)
+    return fail(ctx, BEM_ESTATE, "bem_chebyshev_coeffs: the contour must be a Chebyshev interval");
+  if (!P_dev || !B_dev || nu < 1 || nu > kMaxNu)
+    return fail(ctx, BEM_EINVAL, "bem_chebyshev_coeffs: need P, B and 1 <= nu <= 256");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int N = ctx->con.N;
+  bem_status st = ensure_small(ctx, (size_t)N * N * sizeof(double));
+  if (st != BEM_OK) return st;
+  cheb_table_kernel<<<(N * N + 255) / 256, 256, 0, s>>>(N, ctx->d_small);
+  const int64_t nn = (int64_t)nu * nu;
+  cheb_coeff_kernel<<<(unsigned)((N * nn + 255) / 256), 256, 0, s>>>(
+      reinterpret_cast<const double2*>(P_dev), ctx->d_small, N, nn, reinterpret_cast<double2*>(B_dev));
+  ctx->launches += 2;
+  return cuda_check(ctx, cudaGetLastError(), "bem_chebyshev_coeffs");
+}
+
+extern "C" bem_status bem_solve_chebyshev(bem_ctx* ctx, const double* B_dev, int nu,
+                                          double shift_re, double shift_im, int p, int max_iter,
+                                          double tol, double* lam_host, double* Y_dev,
+                                          double* res_host, int* iters_done, void* stream) {
+  if (!ctx) return BEM_EINVAL;
+  if (ctx->con.N == 0 || ctx->con.kind != BEM_CONTOUR_CHEBYSHEV)
+    return fail(ctx, BEM_ESTATE, "bem_solve_chebyshev: the contour must be a Chebyshev interval");
+  const int N = ctx->con.N, m = N - 1;
+  const int64_t rows = (int64_t)m * nu;
+  if (N < 4 || !B_dev || !lam_host || !Y_dev || !res_host || nu < 1 || nu > kMaxNu || p < 1 ||
+      p > 256 || p > rows || max_iter < 1 || !(tol > 0.0))
+    return fail(ctx, BEM_EINVAL,
+                "bem_solve_chebyshev: need N >= 4 coefficients, outputs, 1 <= nu <= 256, "
+                "1 <= p <= min(256, (N - 1) nu)");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const Contour& con = ctx->con;
+  const double cc = con.c_re, ci = con.c_im, ha = con.a;
+  const double2 sigma = make_double2((shift_re - cc) / ha, (shift_im - ci) / ha);
+  // T_i(sigma), i < m, on the host (three-term recurrence)
+  std::vector<double> sT(2 * m);
+  {
+    double pr = 1.0, pi = 0.0, qr = sigma.x, qi = sigma.y;
+    for (int i = 0; i < m; ++i) {
+      if (i == 0) { sT[0] = 1.0; sT[1] = 0.0; continue; }
+      sT[2 * i] = qr;
+      sT[2 * i + 1] = qi;
+      const double nr = 2.0 * (sigma.x * qr - sigma.y * qi) - pr;
+      const double ni = 2.0 * (sigma.x * qi + sigma.y * qr) - pi;
+      pr = qr; pi = qi; qr = nr; qi = ni;
+    }
+  }
+  const size_t z2 = sizeof(double2);
+  const size_t nn = (size_t)nu * nu, nW = (size_t)rows * p, nT = (size_t)nu * p, nG = (size_t)p * p;
+  const size_t cq = cholqr2_work_bytes(ctx, rows, p);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
+  const size_t oL = take((size_t)m * nn * z2), oG = take(nn * z2), oGi = take(nn * z2),
+               oW = take(nW * z2), oE = take(nW * z2), oHW = take(nW * z2), oY2 = take(nT * z2),
+               oLE = take(nT * z2), oU = take(nT * z2), oR = take(nT * z2), oS = take(nG * z2),
+               oZ = take(nG * z2), oVs = take(nG * z2), oMu = take((size_t)p * z2),
+               oRes = take((size_t)p * sizeof(double)), oST = take((size_t)m * z2), oCq = take(cq);
+  bem_status st = ensure_scratch(ctx, off);
+  if (st != BEM_OK) return st;
+  unsigned char* base = reinterpret_cast<unsigned char*>(ctx->d_scratch);
+  auto at = [&](size_t o) { return reinterpret_cast<double2*>(base + o); };
+  double2 *L = at(oL), *G = at(oG), *Gi = at(oGi), *W = at(oW), *E = at(oE), *HW = at(oHW),
+          *Y2 = at(oY2), *LE = at(oLE), *U = at(oU), *R = at(oR), *Sm = at(oS), *Zm = at(oZ),
+          *Vs = at(oVs), *mu = at(oMu), *dsT = at(oST);
+  double* res = reinterpret_cast<double*>(base + oRes);
+  void* cqw = base + oCq;
+  const double2* B = reinterpret_cast<const double2*>(B_dev);
+  st = cuda_check(ctx, cudaMemcpyAsync(dsT, sT.data(), 2 * m * sizeof(double), cudaMemcpyHostToDevice, s),
+                  "chebyshev copy");
+  if (st != BEM_OK) return st;
+  cheb_setup_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(B, m, nu, sigma, dsT, L, G);
+  gauss_jordan_kernel<<<1, 1024, 0, s>>>(G, Gi, nu, ctx->d_status);
+  random_block_kernel<<<(unsigned)((nW + 255) / 256), 256, 0, s>>>(W, (int64_t)nW, 20190609ull);
+  ctx->launches += 3;
+  st = cuda_check(ctx, cudaGetLastError(), "chebyshev setup");
+  if (st != BEM_OK) return st;
+  st = cholqr2_impl(ctx, reinterpret_cast<double*>(W), rows, rows, p, nullptr, cqw, s, 77);
+  if (st != BEM_OK) return st;
+
+  // HW = (A - sigma M)^{-1} M W
+  auto apply_H = [&]() -> bem_status {
+    const double2* Bm = B + (size_t)m * nn;
+    const double2* wlast = W + (size_t)(m - 1) * nu;
+    cheb_recur_kernel<<<(unsigned)((nT + 255) / 256), 256, 0, s>>>(W, m, nu, p, sigma, E);
+    ctx->launches++;
+    if (launch_zgemm(ctx, nu, p, nu, reinterpret_cast<const double*>(Bm), nu,
+                     reinterpret_cast<const double*>(wlast), rows, reinterpret_cast<double*>(Y2), nu,
+                     s) != cudaSuccess ||
+        launch_zgemm(ctx, nu, p, (int)rows, reinterpret_cast<const double*>(L), nu,
+                     reinterpret_cast<const double*>(E), rows, reinterpret_cast<double*>(LE), nu,
+                     s) != cudaSuccess)
+      return fail(ctx, BEM_ECUDA, "chebyshev apply");
+    // rhs = 2 B_m w_{m-1} - L E (Y2 holds B_m w_{m-1})
+    cheb_rhs_kernel<<<(unsigned)((nT + 255) / 256), 256, 0, s>>>(Y2, LE, (int64_t)nT, R);
+    ctx->launches++;
+    if (launch_zgemm(ctx, nu, p, nu, reinterpret_cast<const double*>(Gi), nu,
+                     reinterpret_cast<const double*>(R), nu, reinterpret_cast<double*>(U), nu,
+                     s) != cudaSuccess)
+      return fail(ctx, BEM_ECUDA, "chebyshev apply");
+    cheb_combine_kernel<<<(unsigned)((nW + 255) / 256), 256, 0, s>>>(E, U, dsT, m, nu, p, HW);
+    ctx->launches++;
+    return cuda_check(ctx, cudaGetLastError(), "chebyshev apply");
+  };
+
+  std::vector<double> hmu(2 * p), hres(p), zeta(2 * p);
+  const int check_every = 5;
+  int it = 0;
+  bool done = false;
+  while (!done) {
+    const bool rr = (it > 0 && it % check_every == 0) || it >= max_iter;
+    st = apply_H();
+    if (st != BEM_OK) return st;
+    if (rr) {
+      st = cuda_check(ctx, launch_xhy_fp64(ctx, reinterpret_cast<double*>(W), rows, p,
+                                           reinterpret_cast<double*>(HW), rows, 0, p, rows, 1,
+                                           nullptr, reinterpret_cast<double*>(Sm), s),
+                      "chebyshev rayleigh-ritz");
+      if (st != BEM_OK) return st;
+      small_eig_kernel<<<1, 32, 0, s>>>(p, Sm, mu, Vs, Zm, ctx->d_status);
+      ctx->launches++;
+      // y-parts of the Ritz vectors: the first block of W Vs (v_0 = T_0 y = y)
+      if (launch_zgemm(ctx, nu, p, p, reinterpret_cast<double*>(W), rows,
+                       reinterpret_cast<double*>(Vs), p, Y_dev, nu, s) != cudaSuccess)
+        return fail(ctx, BEM_ECUDA, "chebyshev ritz vectors");
+      st = cuda_check(ctx, cudaMemcpyAsync(hmu.data(), mu, 2 * p * sizeof(double),
+                                           cudaMemcpyDeviceToHost, s), "chebyshev copy");
+      if (st == BEM_OK) st = cuda_check(ctx, cudaStreamSynchronize(s), "chebyshev sync");
+      if (st != BEM_OK) return st;
+      for (int i = 0; i < p; ++i) {   // zeta = sigma + 1 / mu, lambda = c + a zeta
+        const double mr = hmu[2 * i], mi = hmu[2 * i + 1];
+        const double d = mr * mr + mi * mi;
+        zeta[2 * i] = d > 0.0 ? sigma.x + mr / d : INFINITY;
+        zeta[2 * i + 1] = d > 0.0 ? sigma.y - mi / d : INFINITY;
+        lam_host[2 * i] = cc + ha * zeta[2 * i];
+        lam_host[2 * i + 1] = ci + ha * zeta[2 * i + 1];
+      }
+      st = cuda_check(ctx, cudaMemcpyAsync(mu, zeta.data(), 2 * p * sizeof(double),
+                                           cudaMemcpyHostToDevice, s), "chebyshev copy");
+      if (st != BEM_OK) return st;
+      cheb_residual_kernel<<<p, 256, 0, s>>>(B, mu, reinterpret_cast<const double2*>(Y_dev), N, nu, res);
+      ctx->launches++;
+      st = cuda_check(ctx, cudaMemcpyAsync(hres.data(), res, p * sizeof(double),
+                                           cudaMemcpyDeviceToHost, s), "chebyshev copy");
+      if (st == BEM_OK) st = take_status(ctx, s, "bem_solve_chebyshev");
+      if (st != BEM_OK) return st;
+      // converged when every Ritz value near the interval (|Re zeta| < 1, |Im zeta| < 0.25)
+      // among the dominant half has a small reduced residual
+      std::vector<int> order(p);
+      for (int i = 0; i < p; ++i) order[i] = i;
+      std::sort(order.begin(), order.end(), [&](int a, int b) {
+        return hmu[2 * a] * hmu[2 * a] + hmu[2 * a + 1] * hmu[2 * a + 1] >
+               hmu[2 * b] * hmu[2 * b] + hmu[2 * b + 1] * hmu[2 * b + 1];
+      });
+      bool all = true;
+      for (int r = 0; r < p; ++r) {
+        const int i = order[r];
+        res_host[i] = hres[i];
+        if (r >= (p + 1) / 2) continue;
+        if (fabs(zeta[2 * i]) < 1.0 && fabs(zeta[2 * i + 1]) < 0.25 && !(hres[i] <= tol)) all = false;
+      }
+      if (all || it >= max_iter) done = true;
+    }
+    if (done) break;
+    std::swap(W, HW);
+    st = cholqr2_impl(ctx, reinterpret_cast<double*>(W), rows, rows, p, nullptr, cqw, s,
+                      1000003ull * (it + 1));
+    if (st != BEM_OK) return st;
+    ++it;
+  }
+  if (iters_done) *iters_done = it;
+  return BEM_OK;
 }

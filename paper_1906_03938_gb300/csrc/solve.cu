@@ -491,6 +491,8 @@ extern "C" bem_status bem_solve(bem_ctx* ctx, const double* V0_dev, int64_t ldv,
   if (!ctx) return BEM_EINVAL;
   if (ctx->geo.n == 0 || ctx->con.N == 0)
     return fail(ctx, BEM_ESTATE, "bem_solve: mesh and contour must be set");
+  if (ctx->con.kind == BEM_CONTOUR_CHEBYSHEV)
+    return fail(ctx, BEM_ESTATE, "bem_solve: needs a closed contour (circle or ellipse)");
   const int64_t n = ctx->geo.n;
   const int N = ctx->con.N;
   if (!V0_dev || nu < 1 || nu > kMaxNu || nu > n || ldv < n || q < 0 || kmax < 1 ||
