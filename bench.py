@@ -341,14 +341,14 @@ def run_ours(args):
     c = prob.contour
     ctx = bem.Context(local)
     stream = torch.cuda.current_stream()
-    near = args.near if args.near is not None else (1 if n > 10000 else 0)
+    near_mode = args.near if args.near is not None else (1 if n > 10000 else 0)
     surrogate = None
-    if near == 2:
+    if near_mode == 2:
         surrogate = train_surrogate(bem, local)      # untimed: data generation and training
         ctx.surrogate_set(surrogate["params"])
-    if near:
+    if near_mode:
         ctx.set_mesh(mesh.xyz, mesh.tri)
-        ctx.set_near_field(near)
+        ctx.set_near_field(near_mode)
 
     V_host = torch.from_numpy(np.asfortranarray(V)).pin_memory()   # column-major host copy
     V_res = bem.fortran(V_host.to(dev))                              # resident input
@@ -485,7 +485,7 @@ def run_ours(args):
     # oracle's discrete eigenvalues stored under tests/golden
     eig = None
     golden = os.path.join(ROOT, "tests", "golden", f"eigs_{args.workload}.txt")
-    if not args.no_eig_check and os.path.exists(golden) and not near:
+    if not args.no_eig_check and os.path.exists(golden) and not near_mode:
         t0 = time.perf_counter()
         lam, X, rel = ctx.solve(V_res, q=10, precision=prec, tol=1e-14)
         torch.cuda.synchronize()
@@ -526,7 +526,7 @@ def run_ours(args):
         "config": {"workload": args.workload, "mesh": mesh.name, "n": n, "N": N, "nu": nu,
                    "contour": f"{c.kind} c={c.centre.real:g} a={c.a:g} b={c.b:g}",
                    "precision": args.precision,
-                   "near_field": ["off", "8x8 rule", "surrogate network"][near],
+                   "near_field": ["off", "8x8 rule", "surrogate network"][near_mode],
                    "parallelism": f"replicas{world}", "l2": "flushed between steps (512 MB write)",
                    "wall_s_timed": wall},
         "roofline": roof,

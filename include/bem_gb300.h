@@ -264,11 +264,18 @@ bem_status bem_microbench(bem_ctx* ctx, int kind, double* ops_per_s);
  *   recurrence and one nu x nu system (Algorithm 2 at sigma = 0). Outputs as
  *   bem_solve_reduced: lam_host (2p doubles, z units), Y_dev (nu x p, the y-parts), res_host
  *   (p reduced residuals ||sum_i T_i(zeta) B_i y|| / (||y|| sum_i |T_i(zeta)| ||B_i||_1)).
- *   Stops when the dominant half of the Ritz values with |Re zeta| < 1 and |Im zeta| < 0.25
- *   has residuals <= tol, or after max_iter steps. Synchronises the stream.
+ *   Stops when the dominant half of the Ritz values contains values with |Re zeta| < 1 and
+ *   |Im zeta| < 0.25 and all of them have residuals <= tol, or after max_iter steps.
+ *   Synchronises the stream.
  */
 bem_status bem_chebyshev_coeffs(bem_ctx* ctx, const double* P_dev, int nu, double* B_dev,
                                 void* stream);
+/* One application of the shift-and-invert operator of bem_solve_chebyshev to p columns:
+ * HW = (A - sigma M)^{-1} M W, sigma = (shift - c) / a; W_dev and HW_dev ((N - 1) nu x p,
+ * column-major, leading dimension (N - 1) nu). Synchronises the stream. */
+bem_status bem_chebyshev_apply(bem_ctx* ctx, const double* B_dev, int nu, double shift_re,
+                               double shift_im, const double* W_dev, int p, double* HW_dev,
+                               void* stream);
 bem_status bem_solve_chebyshev(bem_ctx* ctx, const double* B_dev, int nu, double shift_re,
                                double shift_im, int p, int max_iter, double tol, double* lam_host,
                                double* Y_dev, double* res_host, int* iters_done, void* stream);

@@ -60,6 +60,7 @@ SIGNATURES = {
     "bem_chebyshev_coeffs": (_I, [_P, _P, _I, _P, _P]),
     "bem_solve_chebyshev": (_I, [_P, _P, _I, _D, _D, _I, _I, _D, _P, _P, _P, ctypes.POINTER(_I),
                                  _P]),
+    "bem_chebyshev_apply": (_I, [_P, _P, _I, _D, _D, _P, _I, _P, _P]),
     "bem_set_near_field": (_I, [_P, _I, _P]),
     "bem_near_pairs": (_I, [_P, ctypes.POINTER(_I64), _P, _P, _P]),
     "bem_surrogate_size": (_I, []),
@@ -364,6 +365,19 @@ class Context:
         self._chk("bem_chebyshev_coeffs", self._lib.bem_chebyshev_coeffs(
             self._h, _ptr(Pm), nu, _ptr(Bm), _stream(stream)))
         return Bm.transpose(1, 2)
+
+    def chebyshev_apply(self, B, shift, W, stream=None):
+        """(A - sigma M)^{-1} M W for the colleague pencil of B (W: (N-1) nu x p)."""
+        import torch
+        N, nu, _ = B.shape
+        Bm = B.transpose(1, 2).contiguous()
+        Wc = fortran(W)
+        HW = fortran(torch.empty_like(Wc))
+        sh = complex(shift)
+        self._chk("bem_chebyshev_apply", self._lib.bem_chebyshev_apply(
+            self._h, _ptr(Bm), nu, sh.real, sh.imag, _ptr(Wc), Wc.shape[1], _ptr(HW),
+            _stream(stream)))
+        return HW
 
     def solve_chebyshev(self, B, shift, p=None, max_iter=200, tol=1e-12, stream=None):
         """Eigenpairs of sum_i B_i T_i(zeta) y = 0 nearest shift: (lam, Y, res, iters)."""

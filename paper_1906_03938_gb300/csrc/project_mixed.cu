@@ -112,6 +112,35 @@ __device__ __forceinline__ float rsqrtf_mufu(float x) {
   return r;
 }
 
+// Packed FP32 pairs: the evaluation handles two entries of a row at once (its two columns
+// of the 16-wide K-block), so their identical arithmetic goes through the paired FP32
+// instructions (one instruction per two lanes' worth of work; same rounding as the scalar
+// operations).
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2(float a, float b) {
+  f2_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2split(f2_t v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2_t mul2(f2_t a, f2_t b) {
+  f2_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2_t sub2(f2_t a, f2_t b) {
+  f2_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c) {
+  f2_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
   __nv_bfloat162 h = __floats2bfloat162_rn(lo_elem, hi_elem);   // .x -> low 16 bits
   return *reinterpret_cast<uint32_t*>(&h);
@@ -318,18 +347,23 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
       for (int kg = 0; kg < (ready ? 2 : 0); ++kg) {
         const int k0 = 8 * kg + 2 * kp;
         const int64_t l0 = (int64_t)kb * kBK + k0;
-        float rr[2][7], am[2][7];
-#pragma unroll
-        for (int d = 0; d < 2; ++d) {
-          const float4* col = sCol + (k0 + d) * 7;
+        // distances and weights of the 7 points of both columns, as pairs (column k0, k0 + 1)
+        f2_t rr2[7], am2[7];
+        {
+          const float4* c0 = sCol + k0 * 7;
+          const float4* c1 = c0 + 7;
+          const f2_t xx = f2(xr.x, xr.x), xy = f2(xr.y, xr.y), xz = f2(xr.z, xr.z);
 #pragma unroll
           for (int q = 0; q < 7; ++q) {
-            const float4 y = col[q];
-            const float dx = xr.x - y.x, dy = xr.y - y.y, dz = xr.z - y.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float rs = rsqrtf_mufu(r2);
-            rr[d][q] = r2 * rs;
-            am[d][q] = y.w * rs;
+            const float4 y0 = c0[q], y1 = c1[q];
+            const f2_t dx = sub2(xx, f2(y0.x, y1.x)), dy = sub2(xy, f2(y0.y, y1.y)),
+                       dz = sub2(xz, f2(y0.z, y1.z));
+            const f2_t r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+            float r20, r21;
+            f2split(r2, r20, r21);
+            const f2_t rs = f2(rsqrtf_mufu(r20), rsqrtf_mufu(r21));
+            rr2[q] = mul2(r2, rs);
+            am2[q] = mul2(f2(y0.w, y1.w), rs);
           }
         }
         const uint32_t off = e * 256 + kg * 128 + r8 * 16 + kp * 4;
@@ -337,19 +371,26 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
         for (int g = 0; g < kMaxG; ++g) {
           if (g >= Gv) break;
           float re[2], im[2];
+          f2_t sr2 = f2(0.f, 0.f), si2 = f2(0.f, 0.f);
+          const f2_t kmi2 = f2(kmi[g], kmi[g]), kr2 = f2(kr[g], kr[g]);
+#pragma unroll
+          for (int q = 0; q < 7; ++q) {
+            float e0, e1;
+            f2split(mul2(kmi2, rr2[q]), e0, e1);
+            const f2_t a = mul2(am2[q], f2(ex2f(e0), ex2f(e1)));
+            // the MUFU sine and cosine reduce their argument in revolutions themselves;
+            // that reduction's error (half an FP32 ulp of ph / 2 pi) is of the order of
+            // the rounding of ph itself, so no explicit reduction precedes them
+            float p0, p1;
+            f2split(mul2(kr2, rr2[q]), p0, p1);
+            sr2 = fma2(a, f2(cosf_mufu(p0), cosf_mufu(p1)), sr2);
+            si2 = fma2(a, f2(sinf_mufu(p0), sinf_mufu(p1)), si2);
+          }
+          f2split(sr2, re[0], re[1]);
+          f2split(si2, im[0], im[1]);
 #pragma unroll
           for (int d = 0; d < 2; ++d) {
-            float sr = 0.f, si = 0.f;
-#pragma unroll
-            for (int q = 0; q < 7; ++q) {
-              const float a = am[d][q] * ex2f(kmi[g] * rr[d][q]);
-              // the MUFU sine and cosine reduce their argument in revolutions themselves;
-              // that reduction's error (half an FP32 ulp of ph / 2 pi) is of the order of
-              // the rounding of ph itself, so no explicit reduction precedes them
-              const float ph = kr[g] * rr[d][q];
-              sr = fmaf(a, cosf_mufu(ph), sr);
-              si = fmaf(a, sinf_mufu(ph), si);
-            }
+            float sr = re[d], si = im[d];
             if (i == l0 + d) {   // diagonal: the self term
               const float2 sv = sSelf[(k0 + d) * kMaxG + g];
               sr = sv.x;

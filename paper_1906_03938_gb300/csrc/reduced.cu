@@ -640,25 +640,28 @@ extern "C" bem_status bem_chebyshev_coeffs(bem_ctx* ctx, const double* P_dev, in
   return cuda_check(ctx, cudaGetLastError(), "bem_chebyshev_coeffs");
 }
 
-extern "C" bem_status bem_solve_chebyshev(bem_ctx* ctx, const double* B_dev, int nu,
-                                          double shift_re, double shift_im, int p, int max_iter,
-                                          double tol, double* lam_host, double* Y_dev,
-                                          double* res_host, int* iters_done, void* stream) {
-  if (!ctx) return BEM_EINVAL;
-  if (ctx->con.N == 0 || ctx->con.kind != BEM_CONTOUR_CHEBYSHEV)
-    return fail(ctx, BEM_ESTATE, "bem_solve_chebyshev: the contour must be a Chebyshev interval");
+namespace {
+
+// Work of the Chebyshev shift-and-invert operator for p columns (in the context's scratch).
+struct ChebOp {
+  int m = 0, nu = 0, p = 0;
+  int64_t rows = 0;
+  double2 sigma{};
+  const double2* B = nullptr;
+  double2 *L, *G, *Gi, *W, *E, *HW, *Y2, *LE, *U, *R, *Sm, *Zm, *Vs, *mu, *dsT;
+  double* res;
+  void* cqw;
+};
+
+bem_status cheb_prepare(bem_ctx* ctx, const double* B_dev, int nu, double2 sigma, int p,
+                        ChebOp& op, cudaStream_t s) {
   const int N = ctx->con.N, m = N - 1;
-  const int64_t rows = (int64_t)m * nu;
-  if (N < 4 || !B_dev || !lam_host || !Y_dev || !res_host || nu < 1 || nu > kMaxNu || p < 1 ||
-      p > 256 || p > rows || max_iter < 1 || !(tol > 0.0))
-    return fail(ctx, BEM_EINVAL,
-                "bem_solve_chebyshev: need N >= 4 coefficients, outputs, 1 <= nu <= 256, "
-                "1 <= p <= min(256, (N - 1) nu)");
-  cudaSetDevice(ctx->device);
-  cudaStream_t s = (cudaStream_t)stream;
-  const Contour& con = ctx->con;
-  const double cc = con.c_re, ci = con.c_im, ha = con.a;
-  const double2 sigma = make_double2((shift_re - cc) / ha, (shift_im - ci) / ha);
+  op.m = m;
+  op.nu = nu;
+  op.p = p;
+  op.rows = (int64_t)m * nu;
+  op.sigma = sigma;
+  op.B = reinterpret_cast<const double2*>(B_dev);
   // T_i(sigma), i < m, on the host (three-term recurrence)
   std::vector<double> sT(2 * m);
   {
@@ -673,8 +676,8 @@ extern "C" bem_status bem_solve_chebyshev(bem_ctx* ctx, const double* B_dev, int
     }
   }
   const size_t z2 = sizeof(double2);
-  const size_t nn = (size_t)nu * nu, nW = (size_t)rows * p, nT = (size_t)nu * p, nG = (size_t)p * p;
-  const size_t cq = cholqr2_work_bytes(ctx, rows, p);
+  const size_t nn = (size_t)nu * nu, nW = (size_t)op.rows * p, nT = (size_t)nu * p, nG = (size_t)p * p;
+  const size_t cq = cholqr2_work_bytes(ctx, op.rows, p);
   size_t off = 0;
   auto take = [&](size_t bytes) { const size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
   const size_t oL = take((size_t)m * nn * z2), oG = take(nn * z2), oGi = take(nn * z2),
@@ -686,48 +689,106 @@ extern "C" bem_status bem_solve_chebyshev(bem_ctx* ctx, const double* B_dev, int
   if (st != BEM_OK) return st;
   unsigned char* base = reinterpret_cast<unsigned char*>(ctx->d_scratch);
   auto at = [&](size_t o) { return reinterpret_cast<double2*>(base + o); };
-  double2 *L = at(oL), *G = at(oG), *Gi = at(oGi), *W = at(oW), *E = at(oE), *HW = at(oHW),
-          *Y2 = at(oY2), *LE = at(oLE), *U = at(oU), *R = at(oR), *Sm = at(oS), *Zm = at(oZ),
-          *Vs = at(oVs), *mu = at(oMu), *dsT = at(oST);
-  double* res = reinterpret_cast<double*>(base + oRes);
-  void* cqw = base + oCq;
-  const double2* B = reinterpret_cast<const double2*>(B_dev);
-  st = cuda_check(ctx, cudaMemcpyAsync(dsT, sT.data(), 2 * m * sizeof(double), cudaMemcpyHostToDevice, s),
-                  "chebyshev copy");
+  op.L = at(oL); op.G = at(oG); op.Gi = at(oGi); op.W = at(oW); op.E = at(oE); op.HW = at(oHW);
+  op.Y2 = at(oY2); op.LE = at(oLE); op.U = at(oU); op.R = at(oR); op.Sm = at(oS); op.Zm = at(oZ);
+  op.Vs = at(oVs); op.mu = at(oMu); op.dsT = at(oST);
+  op.res = reinterpret_cast<double*>(base + oRes);
+  op.cqw = base + oCq;
+  st = cuda_check(ctx, cudaMemcpyAsync(op.dsT, sT.data(), 2 * m * sizeof(double),
+                                       cudaMemcpyHostToDevice, s), "chebyshev copy");
   if (st != BEM_OK) return st;
-  cheb_setup_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(B, m, nu, sigma, dsT, L, G);
-  gauss_jordan_kernel<<<1, 1024, 0, s>>>(G, Gi, nu, ctx->d_status);
-  random_block_kernel<<<(unsigned)((nW + 255) / 256), 256, 0, s>>>(W, (int64_t)nW, 20190609ull);
-  ctx->launches += 3;
-  st = cuda_check(ctx, cudaGetLastError(), "chebyshev setup");
-  if (st != BEM_OK) return st;
-  st = cholqr2_impl(ctx, reinterpret_cast<double*>(W), rows, rows, p, nullptr, cqw, s, 77);
-  if (st != BEM_OK) return st;
+  cheb_setup_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(op.B, m, nu, sigma, op.dsT, op.L, op.G);
+  gauss_jordan_kernel<<<1, 1024, 0, s>>>(op.G, op.Gi, nu, ctx->d_status);
+  ctx->launches += 2;
+  return cuda_check(ctx, cudaGetLastError(), "chebyshev setup");
+}
 
-  // HW = (A - sigma M)^{-1} M W
-  auto apply_H = [&]() -> bem_status {
-    const double2* Bm = B + (size_t)m * nn;
-    const double2* wlast = W + (size_t)(m - 1) * nu;
-    cheb_recur_kernel<<<(unsigned)((nT + 255) / 256), 256, 0, s>>>(W, m, nu, p, sigma, E);
-    ctx->launches++;
-    if (launch_zgemm(ctx, nu, p, nu, reinterpret_cast<const double*>(Bm), nu,
-                     reinterpret_cast<const double*>(wlast), rows, reinterpret_cast<double*>(Y2), nu,
-                     s) != cudaSuccess ||
-        launch_zgemm(ctx, nu, p, (int)rows, reinterpret_cast<const double*>(L), nu,
-                     reinterpret_cast<const double*>(E), rows, reinterpret_cast<double*>(LE), nu,
-                     s) != cudaSuccess)
-      return fail(ctx, BEM_ECUDA, "chebyshev apply");
-    // rhs = 2 B_m w_{m-1} - L E (Y2 holds B_m w_{m-1})
-    cheb_rhs_kernel<<<(unsigned)((nT + 255) / 256), 256, 0, s>>>(Y2, LE, (int64_t)nT, R);
-    ctx->launches++;
-    if (launch_zgemm(ctx, nu, p, nu, reinterpret_cast<const double*>(Gi), nu,
-                     reinterpret_cast<const double*>(R), nu, reinterpret_cast<double*>(U), nu,
-                     s) != cudaSuccess)
-      return fail(ctx, BEM_ECUDA, "chebyshev apply");
-    cheb_combine_kernel<<<(unsigned)((nW + 255) / 256), 256, 0, s>>>(E, U, dsT, m, nu, p, HW);
-    ctx->launches++;
-    return cuda_check(ctx, cudaGetLastError(), "chebyshev apply");
-  };
+// HW = (A - sigma M)^{-1} M W for the op's p columns (W, HW: rows x p, leading dim rows)
+bem_status cheb_apply(bem_ctx* ctx, const ChebOp& op, const double2* W, double2* HW, cudaStream_t s) {
+  const int m = op.m, nu = op.nu, p = op.p;
+  const int64_t rows = op.rows;
+  const size_t nn = (size_t)nu * nu, nT = (size_t)nu * p, nW = (size_t)rows * p;
+  const double2* Bm = op.B + (size_t)m * nn;
+  const double2* wlast = W + (size_t)(m - 1) * nu;
+  cheb_recur_kernel<<<(unsigned)((nT + 255) / 256), 256, 0, s>>>(W, m, nu, p, op.sigma, op.E);
+  ctx->launches++;
+  if (launch_zgemm(ctx, nu, p, nu, reinterpret_cast<const double*>(Bm), nu,
+                   reinterpret_cast<const double*>(wlast), rows, reinterpret_cast<double*>(op.Y2), nu,
+                   s) != cudaSuccess ||
+      launch_zgemm(ctx, nu, p, (int)rows, reinterpret_cast<const double*>(op.L), nu,
+                   reinterpret_cast<const double*>(op.E), rows, reinterpret_cast<double*>(op.LE), nu,
+                   s) != cudaSuccess)
+    return fail(ctx, BEM_ECUDA, "chebyshev apply");
+  // rhs = 2 B_m w_{m-1} - L E (Y2 holds B_m w_{m-1})
+  cheb_rhs_kernel<<<(unsigned)((nT + 255) / 256), 256, 0, s>>>(op.Y2, op.LE, (int64_t)nT, op.R);
+  ctx->launches++;
+  if (launch_zgemm(ctx, nu, p, nu, reinterpret_cast<const double*>(op.Gi), nu,
+                   reinterpret_cast<const double*>(op.R), nu, reinterpret_cast<double*>(op.U), nu,
+                   s) != cudaSuccess)
+    return fail(ctx, BEM_ECUDA, "chebyshev apply");
+  cheb_combine_kernel<<<(unsigned)((nW + 255) / 256), 256, 0, s>>>(op.E, op.U, op.dsT, m, nu, p, HW);
+  ctx->launches++;
+  return cuda_check(ctx, cudaGetLastError(), "chebyshev apply");
+}
+
+bem_status cheb_check_args(bem_ctx* ctx, const char* who) {
+  if (ctx->con.N == 0 || ctx->con.kind != BEM_CONTOUR_CHEBYSHEV)
+    return fail(ctx, BEM_ESTATE, std::string(who) + ": the contour must be a Chebyshev interval");
+  if (ctx->con.N < 4) return fail(ctx, BEM_EINVAL, std::string(who) + ": need N >= 4 coefficients");
+  return BEM_OK;
+}
+
+}  // namespace
+
+extern "C" bem_status bem_chebyshev_apply(bem_ctx* ctx, const double* B_dev, int nu,
+                                          double shift_re, double shift_im, const double* W_dev,
+                                          int p, double* HW_dev, void* stream) {
+  if (!ctx) return BEM_EINVAL;
+  bem_status st = cheb_check_args(ctx, "bem_chebyshev_apply");
+  if (st != BEM_OK) return st;
+  const int64_t rows = (int64_t)(ctx->con.N - 1) * nu;
+  if (!B_dev || !W_dev || !HW_dev || nu < 1 || nu > kMaxNu || p < 1 || p > 256 || p > rows)
+    return fail(ctx, BEM_EINVAL, "bem_chebyshev_apply: bad arguments");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const Contour& con = ctx->con;
+  ChebOp op;
+  st = cheb_prepare(ctx, B_dev, nu, make_double2((shift_re - con.c_re) / con.a,
+                                                 (shift_im - con.c_im) / con.a), p, op, s);
+  if (st != BEM_OK) return st;
+  st = cheb_apply(ctx, op, reinterpret_cast<const double2*>(W_dev), reinterpret_cast<double2*>(HW_dev), s);
+  if (st != BEM_OK) return st;
+  return take_status(ctx, s, "bem_chebyshev_apply");
+}
+
+extern "C" bem_status bem_solve_chebyshev(bem_ctx* ctx, const double* B_dev, int nu,
+                                          double shift_re, double shift_im, int p, int max_iter,
+                                          double tol, double* lam_host, double* Y_dev,
+                                          double* res_host, int* iters_done, void* stream) {
+  if (!ctx) return BEM_EINVAL;
+  bem_status st = cheb_check_args(ctx, "bem_solve_chebyshev");
+  if (st != BEM_OK) return st;
+  const int N = ctx->con.N;
+  const int64_t rows = (int64_t)(N - 1) * nu;
+  if (!B_dev || !lam_host || !Y_dev || !res_host || nu < 1 || nu > kMaxNu || p < 1 ||
+      p > 256 || p > rows || max_iter < 1 || !(tol > 0.0))
+    return fail(ctx, BEM_EINVAL,
+                "bem_solve_chebyshev: need outputs, 1 <= nu <= 256, 1 <= p <= min(256, (N - 1) nu)");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const Contour& con = ctx->con;
+  const double cc = con.c_re, ci = con.c_im, ha = con.a;
+  const double2 sigma = make_double2((shift_re - cc) / ha, (shift_im - ci) / ha);
+  ChebOp op;
+  st = cheb_prepare(ctx, B_dev, nu, sigma, p, op, s);
+  if (st != BEM_OK) return st;
+  double2* W = op.W;
+  double2* HW = op.HW;
+  const size_t nW = (size_t)rows * p;
+  random_block_kernel<<<(unsigned)((nW + 255) / 256), 256, 0, s>>>(W, (int64_t)nW, 20190609ull);
+  ctx->launches++;
+  st = cholqr2_impl(ctx, reinterpret_cast<double*>(W), rows, rows, p, nullptr, op.cqw, s, 77);
+  if (st != BEM_OK) return st;
 
   std::vector<double> hmu(2 * p), hres(p), zeta(2 * p);
   const int check_every = 5;
@@ -735,21 +796,21 @@ extern "C" bem_status bem_solve_chebyshev(bem_ctx* ctx, const double* B_dev, int
   bool done = false;
   while (!done) {
     const bool rr = (it > 0 && it % check_every == 0) || it >= max_iter;
-    st = apply_H();
+    st = cheb_apply(ctx, op, W, HW, s);
     if (st != BEM_OK) return st;
     if (rr) {
       st = cuda_check(ctx, launch_xhy_fp64(ctx, reinterpret_cast<double*>(W), rows, p,
                                            reinterpret_cast<double*>(HW), rows, 0, p, rows, 1,
-                                           nullptr, reinterpret_cast<double*>(Sm), s),
+                                           nullptr, reinterpret_cast<double*>(op.Sm), s),
                       "chebyshev rayleigh-ritz");
       if (st != BEM_OK) return st;
-      small_eig_kernel<<<1, 32, 0, s>>>(p, Sm, mu, Vs, Zm, ctx->d_status);
+      small_eig_kernel<<<1, 32, 0, s>>>(p, op.Sm, op.mu, op.Vs, op.Zm, ctx->d_status);
       ctx->launches++;
       // y-parts of the Ritz vectors: the first block of W Vs (v_0 = T_0 y = y)
       if (launch_zgemm(ctx, nu, p, p, reinterpret_cast<double*>(W), rows,
-                       reinterpret_cast<double*>(Vs), p, Y_dev, nu, s) != cudaSuccess)
+                       reinterpret_cast<double*>(op.Vs), p, Y_dev, nu, s) != cudaSuccess)
         return fail(ctx, BEM_ECUDA, "chebyshev ritz vectors");
-      st = cuda_check(ctx, cudaMemcpyAsync(hmu.data(), mu, 2 * p * sizeof(double),
+      st = cuda_check(ctx, cudaMemcpyAsync(hmu.data(), op.mu, 2 * p * sizeof(double),
                                            cudaMemcpyDeviceToHost, s), "chebyshev copy");
       if (st == BEM_OK) st = cuda_check(ctx, cudaStreamSynchronize(s), "chebyshev sync");
       if (st != BEM_OK) return st;
@@ -761,17 +822,20 @@ extern "C" bem_status bem_solve_chebyshev(bem_ctx* ctx, const double* B_dev, int
         lam_host[2 * i] = cc + ha * zeta[2 * i];
         lam_host[2 * i + 1] = ci + ha * zeta[2 * i + 1];
       }
-      st = cuda_check(ctx, cudaMemcpyAsync(mu, zeta.data(), 2 * p * sizeof(double),
+      st = cuda_check(ctx, cudaMemcpyAsync(op.mu, zeta.data(), 2 * p * sizeof(double),
                                            cudaMemcpyHostToDevice, s), "chebyshev copy");
       if (st != BEM_OK) return st;
-      cheb_residual_kernel<<<p, 256, 0, s>>>(B, mu, reinterpret_cast<const double2*>(Y_dev), N, nu, res);
+      cheb_residual_kernel<<<p, 256, 0, s>>>(op.B, op.mu, reinterpret_cast<const double2*>(Y_dev), N,
+                                             nu, op.res);
       ctx->launches++;
-      st = cuda_check(ctx, cudaMemcpyAsync(hres.data(), res, p * sizeof(double),
+      st = cuda_check(ctx, cudaMemcpyAsync(hres.data(), op.res, p * sizeof(double),
                                            cudaMemcpyDeviceToHost, s), "chebyshev copy");
       if (st == BEM_OK) st = take_status(ctx, s, "bem_solve_chebyshev");
       if (st != BEM_OK) return st;
-      // converged when every Ritz value near the interval (|Re zeta| < 1, |Im zeta| < 0.25)
-      // among the dominant half has a small reduced residual
+      // converged when the dominant half holds at least one Ritz value near the interval
+      // (|Re zeta| < 1, |Im zeta| < 0.25) and every such value has a small reduced residual.
+      // The colleague operator is far from normal, so the first Rayleigh-Ritz values of a
+      // poorly converged block can all be spurious: an empty set is not taken as converged.
       std::vector<int> order(p);
       for (int i = 0; i < p; ++i) order[i] = i;
       std::sort(order.begin(), order.end(), [&](int a, int b) {
@@ -779,17 +843,21 @@ extern "C" bem_status bem_solve_chebyshev(bem_ctx* ctx, const double* B_dev, int
                hmu[2 * b] * hmu[2 * b] + hmu[2 * b + 1] * hmu[2 * b + 1];
       });
       bool all = true;
+      int inside = 0;
       for (int r = 0; r < p; ++r) {
         const int i = order[r];
         res_host[i] = hres[i];
         if (r >= (p + 1) / 2) continue;
-        if (fabs(zeta[2 * i]) < 1.0 && fabs(zeta[2 * i + 1]) < 0.25 && !(hres[i] <= tol)) all = false;
+        if (fabs(zeta[2 * i]) < 1.0 && fabs(zeta[2 * i + 1]) < 0.25) {
+          ++inside;
+          if (!(hres[i] <= tol)) all = false;
+        }
       }
-      if (all || it >= max_iter) done = true;
+      if ((all && inside > 0) || it >= max_iter) done = true;
     }
     if (done) break;
     std::swap(W, HW);
-    st = cholqr2_impl(ctx, reinterpret_cast<double*>(W), rows, rows, p, nullptr, cqw, s,
+    st = cholqr2_impl(ctx, reinterpret_cast<double*>(W), rows, rows, p, nullptr, op.cqw, s,
                       1000003ull * (it + 1));
     if (st != BEM_OK) return st;
     ++it;

@@ -46,6 +46,25 @@ def test_nodes_and_coefficients(bem):
     ctx.close()
 
 
+@pytest.mark.parametrize("N", [4, 5, 8, 14])
+def test_shift_invert_operator_matches_dense_solve(bem, N):
+    """The GPU's recurrence solve of (A - sigma M) w' = M w against the oracle's dense
+    solve of the colleague pencil, for coefficients that are all significant."""
+    rng = np.random.default_rng(N)
+    nu, p = 5, 7
+    c, a = 0.0, 1.0
+    ctx, _, _ = _ctx(bem, c, a, N)
+    B = np.stack([(rng.normal(size=(nu, nu)) + 1j * rng.normal(size=(nu, nu))) * 0.5 ** i
+                  for i in range(N)])
+    W = rng.normal(size=((N - 1) * nu, p)) + 1j * rng.normal(size=((N - 1) * nu, p))
+    for sigma in (0.0, 0.05, 0.3 - 0.2j):
+        HW = ctx.chebyshev_apply(torch.from_numpy(B).to("cuda:0"), c + a * sigma,
+                                 torch.from_numpy(W).to("cuda:0")).cpu().numpy()
+        ref = och.shift_invert_apply(B, sigma, W)
+        assert np.max(np.abs(HW - ref)) < 1e-12 * np.max(np.abs(ref)), (N, sigma)
+    ctx.close()
+
+
 def test_solve_matrix_polynomial(bem):
     rng = np.random.default_rng(5)
     nu = 6
