@@ -172,6 +172,31 @@ def run_reference(args):
     return 0
 
 
+def unit_nodes(N, nu, cap):
+    """Nodes per work unit of the mixed kernel: up to 4 (or the cap), within the 512 TMEM
+    accumulator columns (2 nup per node, nup = nu rounded up to 8, above 128 to 128)."""
+    nup = (nu + 7) // 8 * 8
+    if nup > 128:
+        nup = (nup + 127) // 128 * 128
+    g = min(N, min(cap, 4) if cap > 0 else 4)
+    return max(1, min(g, 512 // (2 * nup)))
+
+
+def mufu_seconds_per_entry(rates, N, G, twins):
+    """MUFU time of one entry of A for all N nodes at the measured rates: per quadrature
+    point (7) one ex2 per node, one sin and one cos per node or per twin pair evaluated
+    together (the pair in one unit, starting at an even slot), one rsqrt per unit."""
+    paired = 0
+    for P in range(twins):
+        s0 = 2 * P
+        if s0 // G == (s0 + 1) // G and (s0 // G * G) % 2 == 0:
+            paired += 1
+    phases = N - paired
+    units = -(-N // G)
+    return 7 * (N / rates["ex2"] + phases * (1 / rates["sin"] + 1 / rates["cos"]) +
+                units / rates["rsqrt"])
+
+
 def measured_traffic(workload, precision):
     """DRAM bytes (read + write) per launch of the fused kernel from the committed ncu
     summary of this workload, or None when there is none or the kernel's source has changed
@@ -298,9 +323,16 @@ def run_batch(args):
     if rank != 0:
         return 0
     rates = {k: ctxs[0].microbench(k) for k in ("ex2", "sin", "cos", "rsqrt")}
-    t_entry = 7 * (1 / rates["ex2"] + 1 / rates["sin"] + 1 / rates["cos"]) + 7 / (4 * rates["rsqrt"])
     step_s = t_total / args.steps
     mine_entries = float(sum(costs[i] for i in mine))
+    # MUFU seconds of this rank's work: each problem at its own node count, schedule and
+    # nodes per unit (the batch's cap, else 4, within the accumulator limit)
+    t_mufu = 0.0
+    for k, i in enumerate(mine):
+        Nk = probs_all[i].N
+        Gk = unit_nodes(Nk, probs_all[i].nu, batch.info()["nodes_per_unit"])
+        t_mufu += costs[i] / Nk * mufu_seconds_per_entry(rates, Nk, Gk, ctxs[k].node_order()[1])
+    t_entry = t_mufu / mine_entries
     roof = {"bound": "alu", "pipe": "mufu", "achieved": mine_entries / step_s, "peak": 1.0 / t_entry,
             "unit": "entries/s", "frac": mine_entries / step_s * t_entry, "traffic": None,
             "kernel_ms": 1e3 * step_s,
@@ -456,14 +488,16 @@ def run_ours(args):
         # unit, one rsqrt per quadrature point. Roof = entries/s if the MUFU unit did only
         # that work at its measured rates.
         rates = {k: ctx.microbench(k) for k in ("ex2", "sin", "cos", "rsqrt")}
-        G = min(N, 4, max(1, 512 // (2 * ((nu + 7) // 8 * 8))))
-        t_entry = 7 * (1 / rates["ex2"] + 1 / rates["sin"] + 1 / rates["cos"]) + \
-            7 / (G * rates["rsqrt"])
+        G = unit_nodes(N, nu, 0)
+        twins = ctx.node_order()[1]
+        t_entry = mufu_seconds_per_entry(rates, N, G, twins) / N
         roof = {"bound": "alu", "pipe": "mufu", "achieved": entries / (kern_avg * 1e-3),
                 "peak": 1.0 / t_entry, "unit": "entries/s",
                 "peak_source": "measured MUFU rates (bem_microbench): "
                                + ", ".join(f"{k} {v:.3e}/s" for k, v in rates.items())
-                               + f"; 21 MUFU ops per entry-node + 7 rsqrt per entry / G={G}"}
+                               + f"; per entry and quadrature point: ex2 per node, sin + cos "
+                               f"per node or per twin pair ({twins} of {N // 2} possible), "
+                               f"rsqrt per {G} nodes"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = measured_traffic(args.workload, args.precision)
     roof["kernel_ms"] = kern_avg

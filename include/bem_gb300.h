@@ -97,6 +97,21 @@ bem_status bem_set_contour(bem_ctx* ctx, int kind, double c_re, double c_im, dou
                            double b, int N, double* z_host, double* w_host, void* stream);
 
 /*
+ * Node schedule of the mixed projection (an implementation detail of Eq. RR_approx's
+ * evaluation; the paper has no counterpart). Nodes whose real parts round to the same FP32
+ * value evaluate the same phase Re(z_j) |x - y| at every quadrature point: the conjugate
+ * nodes z, conj(z) of a circle or ellipse centred on the real axis (the trapezoid nodes of
+ * Eq. quadrature_contour are placed mirror-symmetrically, so their real parts agree
+ * exactly). The mixed kernel takes such twins in pairs and computes one sine and one cosine
+ * for both; the results are the same as without pairing, bit for bit.
+ *   order_host  N ints (host), or NULL: slot s of the schedule holds node order[s]; twin
+ *               pairs fill slots 0 .. 2 twins - 1 (slots 2 P, 2 P + 1), the rest follow.
+ *   twins       (host), or NULL: number of twin pairs.
+ * Set by bem_set_contour; host only. BEM_ESTATE without a contour.
+ */
+bem_status bem_node_order(const bem_ctx* ctx, int* order_host, int* twins);
+
+/*
  * Fused assembly + Rayleigh-Ritz projection (Section 3, Eq. RR_approx; Algorithm 3,
  * "use U to compute B^_i"): for every contour node z_j,
  *     Bhat_j = w_j * V^H A(z_j) V                                   (nu x nu)

@@ -41,6 +41,7 @@ SIGNATURES = {
     "bem_set_mesh": (_I, [_P, _I64, _P, _I64, _P, _P]),
     "bem_set_contour": (_I, [_P, _I, _D, _D, _D, _D, _I, _P, _P, _P]),
     "bem_project": (_I, [_P, _P, _I64, _I, _P, _P, _I, _P]),
+    "bem_node_order": (_I, [_P, _P, _P]),
     "bem_cholqr2": (_I, [_P, _P, _I64, _I64, _I, _P, _P]),
     "bem_residual": (_I, [_P, _I, _P, _P, _I64, _P, _P, _P]),
     "bem_kernel_launches": (_I64, [_P]),
@@ -317,6 +318,15 @@ class Context:
             _stream(stream)))
         self.N = int(N)
         return z.view(np.complex128), w.view(np.complex128)
+
+    def node_order(self):
+        """(order, twins): the mixed kernel's node schedule (slot -> node) and the number
+        of twin pairs (nodes with equal FP32 real parts) at its front."""
+        order = np.zeros(self.N, dtype=np.int32)
+        tw = _I(0)
+        self._chk("bem_node_order", self._lib.bem_node_order(
+            self._h, order.ctypes.data_as(_P), ctypes.byref(tw)))
+        return order, int(tw.value)
 
     def project(self, V, precision=PREC_FP64, AV=False, Bhat=None, stream=None):
         """Bhat_j = w_j V^H A(z_j) V for all nodes; optionally Y_j = A(z_j) V."""

@@ -3,6 +3,7 @@
 #include <stdio.h>
 
 #include <string>
+#include <vector>
 
 #include "internal.h"
 
@@ -72,8 +73,10 @@ static void free_geometry(Geometry& g) {
 }
 
 static void free_contour(Contour& c) {
-  cudaFree(c.z); cudaFree(c.w); cudaFree(c.self); cudaFree(c.self32);
+  cudaFree(c.z); cudaFree(c.w); cudaFree(c.self); cudaFree(c.self32); cudaFree(c.order);
   c.z = c.w = c.self = nullptr;
+  c.order = nullptr;
+  c.twins = 0;
   c.self32 = nullptr;
   c.self64_ready = c.self32_ready = false;
   c.N = 0;
@@ -93,6 +96,35 @@ bem_status ensure_self32(bem_ctx* ctx, cudaStream_t s) {
   bem_status st = cuda_check(ctx, launch_self_terms32(ctx, s), "self-term kernel");
   if (st == BEM_OK) ctx->con.self32_ready = true;
   return st;
+}
+
+// Node schedule of the mixed evaluation. Nodes whose real parts round to the same FP32
+// value (the conjugate nodes of a contour symmetric about a horizontal line) evaluate the
+// same phase Re(z) r at every quadrature point, so the kernel computes its sine and cosine
+// once for both: twins first, in pairs at even slots (the first flagged), then the rest.
+static void build_node_order(Contour& c) {
+  const int N = c.N;
+  std::vector<char> used(N, 0);
+  std::vector<int> single;
+  int slot = 0;
+  c.twins = 0;
+  for (int j = 0; j < N; ++j) {
+    if (used[j]) continue;
+    used[j] = 1;
+    const float rj = (float)c.z_host[2 * j];
+    int m = -1;
+    for (int k = j + 1; k < N && m < 0; ++k)
+      if (!used[k] && (float)c.z_host[2 * k] == rj) m = k;
+    if (m < 0) {
+      single.push_back(j);
+      continue;
+    }
+    used[m] = 1;
+    c.order_host[slot++] = j | kTwinBit;
+    c.order_host[slot++] = m;
+    c.twins++;
+  }
+  for (int j : single) c.order_host[slot++] = j;
 }
 
 }  // namespace bem
@@ -234,7 +266,8 @@ bem_status bem_set_contour(bem_ctx* ctx, int kind, double c_re, double c_im, dou
     bool ok = cudaMalloc(&c.z, 2 * N * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&c.w, 2 * N * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&c.self, 2 * need_self * sizeof(double)) == cudaSuccess &&
-              cudaMalloc(&c.self32, 2 * need_self * sizeof(float)) == cudaSuccess;
+              cudaMalloc(&c.self32, 2 * need_self * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&c.order, N * sizeof(int)) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       free_contour(c);
@@ -253,6 +286,11 @@ bem_status bem_set_contour(bem_ctx* ctx, int kind, double c_re, double c_im, dou
     st = cuda_check(ctx, cudaMemcpyAsync(c.w_host, c.w, 2 * N * sizeof(double),
                                          cudaMemcpyDeviceToHost, s), "contour copy");
   if (st == BEM_OK) st = take_status(ctx, s, "bem_set_contour");
+  if (st == BEM_OK) {
+    build_node_order(c);
+    st = cuda_check(ctx, cudaMemcpyAsync(c.order, c.order_host, N * sizeof(int),
+                                         cudaMemcpyHostToDevice, s), "node order copy");
+  }
   if (st != BEM_OK) {
     free_contour(c);
     return st;
@@ -262,6 +300,15 @@ bem_status bem_set_contour(bem_ctx* ctx, int kind, double c_re, double c_im, dou
     if (z_host) z_host[t] = c.z_host[t];
     if (w_host) w_host[t] = c.w_host[t];
   }
+  return BEM_OK;
+}
+
+bem_status bem_node_order(const bem_ctx* ctx, int* order_host, int* twins) {
+  if (!ctx) return BEM_EINVAL;
+  if (ctx->con.N == 0) return BEM_ESTATE;
+  if (order_host)
+    for (int t = 0; t < ctx->con.N; ++t) order_host[t] = ctx->con.order_host[t] & kNodeMask;
+  if (twins) *twins = ctx->con.twins;
   return BEM_OK;
 }
 

@@ -150,8 +150,12 @@ __global__ void contour_kernel(int N, int kind, double c_re, double c_im, double
     return;
   }
   if (kind == BEM_CONTOUR_CIRCLE) b = a;
+  // theta_j = pi (2 j + 1) / N; the lower half mirrors the upper (theta_{N-1-j} = 2 pi -
+  // theta_j) exactly, so conjugate nodes have bit-equal real parts
+  const int m = 2 * j + 1 > N ? N - 1 - j : j;
   double s, c;
-  sincospi((2.0 * j + 1.0) / N, &s, &c);   // theta_j = pi (2 j + 1) / N
+  sincospi((2.0 * m + 1.0) / N, &s, &c);
+  if (m != j) s = -s;
   z[2 * j] = c_re + a * c;
   z[2 * j + 1] = c_im + b * s;
   w[2 * j] = b * c / N;

@@ -71,7 +71,14 @@ struct Contour {
   int64_t cap_self = 0;
   double z_host[2 * kMaxNodes];
   double w_host[2 * kMaxNodes];
+  // Node schedule of the mixed evaluation: slot -> node, twin nodes (equal FP32 real parts,
+  // which share their sine and cosine) at slots 2 P, 2 P + 1 with kTwinBit on slot 2 P.
+  int* order = nullptr;    // N, device
+  int order_host[kMaxNodes];
+  int twins = 0;           // twin pairs in the schedule
 };
+constexpr int kTwinBit = 1 << 30;
+constexpr int kNodeMask = kTwinBit - 1;
 
 }  // namespace bem
 

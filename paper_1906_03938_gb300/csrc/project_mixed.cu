@@ -64,6 +64,7 @@ struct MixedParams {
   const float2* self32;   // FP32 complex self terms, node-major
   const float* pack32;    // packed FP32 hi/lo panel geometry (64 floats per panel)
   const double* z;    // FP64 complex nodes
+  const int* order;   // node schedule: slot -> node (| kTwinBit on the first of a twin pair)
   const __nv_bfloat16* Bp;   // prepared basis planes, tile-native
   float* Yp;          // FP32 partial products [S][N][2 nup][n_pad]
   int* status;
@@ -144,6 +145,38 @@ __device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c) {
 __device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
   __nv_bfloat162 h = __floats2bfloat162_rn(lo_elem, hi_elem);   // .x -> low 16 bits
   return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// Two entries (row i, columns l0, l0 + 1) of one node: the self term on the diagonal, zero
+// in the padding, then the hi/lo BF16 split into the four planes (Re hi, Re lo, Im hi, Im lo)
+// at ag; self points at the staged self term of column l0 (that of l0 + 1 is kMaxG later).
+__device__ __forceinline__ void put_entries(f2_t sr2, f2_t si2, const float2* self, int64_t i,
+                                            int64_t l0, int64_t n, unsigned char* ag) {
+  float re[2], im[2];
+  f2split(sr2, re[0], re[1]);
+  f2split(si2, im[0], im[1]);
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    if (i == l0 + d) {   // diagonal: the self term
+      const float2 sv = self[d * kMaxG];
+      re[d] = sv.x;
+      im[d] = sv.y;
+    }
+    if (i >= n || l0 + d >= n) {   // padding rows / columns of the tile
+      re[d] = 0.f;
+      im[d] = 0.f;
+    }
+  }
+  const uint32_t hr = pack_bf16(re[0], re[1]);
+  const uint32_t hi = pack_bf16(im[0], im[1]);
+  const uint32_t lr = pack_bf16(re[0] - __uint_as_float(hr << 16),
+                                re[1] - __uint_as_float(hr & 0xFFFF0000u));
+  const uint32_t li = pack_bf16(im[0] - __uint_as_float(hi << 16),
+                                im[1] - __uint_as_float(hi & 0xFFFF0000u));
+  *reinterpret_cast<uint32_t*>(ag + 0 * kPlaneBytes) = hr;
+  *reinterpret_cast<uint32_t*>(ag + 1 * kPlaneBytes) = lr;
+  *reinterpret_cast<uint32_t*>(ag + 2 * kPlaneBytes) = hi;
+  *reinterpret_cast<uint32_t*>(ag + 3 * kPlaneBytes) = li;
 }
 
 // bounded wait that also watches the block's abort flag
@@ -275,7 +308,7 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
         const int64_t l = (int64_t)kb * kBK + k;
         float2 v = make_float2(0.f, 0.f);
         if (l < p.n && g < Gv && l >= row0 && l < row0 + kBM)
-          v = p.self32[(int64_t)(j0 + g) * p.n + l];
+          v = p.self32[(int64_t)(p.order[j0 + g] & kNodeMask) * p.n + l];
         sSelf[x] = v;
       }
       mbar_arrive(&gfull[s]);   // release: the staged values are visible to the waiters
@@ -323,11 +356,18 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
     const int e = warp - 2;               // 0..15: row group of the 128 x 16 block
     // node constants
     float kr[kMaxG], kmi[kMaxG];
+    bool twin[kMaxG / 2];
 #pragma unroll
     for (int g = 0; g < kMaxG; ++g) {
-      const int j = j0 + (g < Gv ? g : 0);
+      const int code = p.order[j0 + (g < Gv ? g : 0)];
+      const int j = code & kNodeMask;
       kr[g] = (float)p.z[2 * j];
       kmi[g] = (float)(-p.z[2 * j + 1]) * kLog2e;
+      // a twin pair sits at slots 2 P, 2 P + 1 of the schedule: inside this group when the
+      // group starts at an even slot
+      if (g % 2 == 0)
+        twin[g / 2] = (code & kTwinBit) && (j0 % 2 == 0) && g + 1 < Gv && kr[g] ==
+                      (float)p.z[2 * (p.order[j0 + g + 1] & kNodeMask)];
     }
     // this thread's entries: row 8 e + r8, columns 8 kg + 2 kp + {0, 1} for kg = 0, 1
     const int r8 = lane / 4, kp = lane % 4;
@@ -367,53 +407,55 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
           }
         }
         const uint32_t off = e * 256 + kg * 128 + r8 * 16 + kp * 4;
+        const float2* selfk = sSelf + k0 * kMaxG;
 #pragma unroll
-        for (int g = 0; g < kMaxG; ++g) {
+        for (int g = 0; g < kMaxG; g += 2) {
           if (g >= Gv) break;
-          float re[2], im[2];
-          f2_t sr2 = f2(0.f, 0.f), si2 = f2(0.f, 0.f);
-          const f2_t kmi2 = f2(kmi[g], kmi[g]), kr2 = f2(kr[g], kr[g]);
+          if (twin[g / 2]) {
+            // twin nodes: one sine and one cosine of the shared phase for both
+            f2_t sa = f2(0.f, 0.f), ia = f2(0.f, 0.f), sb = f2(0.f, 0.f), ib = f2(0.f, 0.f);
+            const f2_t kma = f2(kmi[g], kmi[g]), kmb = f2(kmi[g + 1], kmi[g + 1]);
+            const f2_t kr2 = f2(kr[g], kr[g]);
 #pragma unroll
-          for (int q = 0; q < 7; ++q) {
-            float e0, e1;
-            f2split(mul2(kmi2, rr2[q]), e0, e1);
-            const f2_t a = mul2(am2[q], f2(ex2f(e0), ex2f(e1)));
-            // the MUFU sine and cosine reduce their argument in revolutions themselves;
-            // that reduction's error (half an FP32 ulp of ph / 2 pi) is of the order of
-            // the rounding of ph itself, so no explicit reduction precedes them
-            float p0, p1;
-            f2split(mul2(kr2, rr2[q]), p0, p1);
-            sr2 = fma2(a, f2(cosf_mufu(p0), cosf_mufu(p1)), sr2);
-            si2 = fma2(a, f2(sinf_mufu(p0), sinf_mufu(p1)), si2);
-          }
-          f2split(sr2, re[0], re[1]);
-          f2split(si2, im[0], im[1]);
+            for (int q = 0; q < 7; ++q) {
+              float e0, e1, e2, e3, p0, p1;
+              f2split(mul2(kma, rr2[q]), e0, e1);
+              f2split(mul2(kmb, rr2[q]), e2, e3);
+              const f2_t aa = mul2(am2[q], f2(ex2f(e0), ex2f(e1)));
+              const f2_t ab = mul2(am2[q], f2(ex2f(e2), ex2f(e3)));
+              f2split(mul2(kr2, rr2[q]), p0, p1);
+              const f2_t cs = f2(cosf_mufu(p0), cosf_mufu(p1));
+              const f2_t sn = f2(sinf_mufu(p0), sinf_mufu(p1));
+              sa = fma2(aa, cs, sa);
+              ia = fma2(aa, sn, ia);
+              sb = fma2(ab, cs, sb);
+              ib = fma2(ab, sn, ib);
+            }
+            put_entries(sa, ia, selfk + g, i, l0, p.n, a_stage + g * 4 * kPlaneBytes + off);
+            put_entries(sb, ib, selfk + g + 1, i, l0, p.n,
+                        a_stage + (g + 1) * 4 * kPlaneBytes + off);
+          } else {
 #pragma unroll
-          for (int d = 0; d < 2; ++d) {
-            float sr = re[d], si = im[d];
-            if (i == l0 + d) {   // diagonal: the self term
-              const float2 sv = sSelf[(k0 + d) * kMaxG + g];
-              sr = sv.x;
-              si = sv.y;
+            for (int h = g; h < g + 2; ++h) {
+              if (h >= Gv) break;
+              f2_t sr2 = f2(0.f, 0.f), si2 = f2(0.f, 0.f);
+              const f2_t kmi2 = f2(kmi[h], kmi[h]), kr2 = f2(kr[h], kr[h]);
+#pragma unroll
+              for (int q = 0; q < 7; ++q) {
+                float e0, e1;
+                f2split(mul2(kmi2, rr2[q]), e0, e1);
+                const f2_t a = mul2(am2[q], f2(ex2f(e0), ex2f(e1)));
+                // the MUFU sine and cosine reduce their argument in revolutions themselves;
+                // that reduction's error (half an FP32 ulp of ph / 2 pi) is of the order of
+                // the rounding of ph itself, so no explicit reduction precedes them
+                float p0, p1;
+                f2split(mul2(kr2, rr2[q]), p0, p1);
+                sr2 = fma2(a, f2(cosf_mufu(p0), cosf_mufu(p1)), sr2);
+                si2 = fma2(a, f2(sinf_mufu(p0), sinf_mufu(p1)), si2);
+              }
+              put_entries(sr2, si2, selfk + h, i, l0, p.n, a_stage + h * 4 * kPlaneBytes + off);
             }
-            if (i >= p.n || l0 + d >= p.n) {   // padding rows / columns of the tile
-              sr = 0.f;
-              si = 0.f;
-            }
-            re[d] = sr;
-            im[d] = si;
           }
-          const uint32_t hr = pack_bf16(re[0], re[1]);
-          const uint32_t hi = pack_bf16(im[0], im[1]);
-          const uint32_t lr = pack_bf16(re[0] - __uint_as_float(hr << 16),
-                                        re[1] - __uint_as_float(hr & 0xFFFF0000u));
-          const uint32_t li = pack_bf16(im[0] - __uint_as_float(hi << 16),
-                                        im[1] - __uint_as_float(hi & 0xFFFF0000u));
-          unsigned char* ag = a_stage + g * 4 * kPlaneBytes + off;
-          *reinterpret_cast<uint32_t*>(ag + 0 * kPlaneBytes) = hr;
-          *reinterpret_cast<uint32_t*>(ag + 1 * kPlaneBytes) = lr;
-          *reinterpret_cast<uint32_t*>(ag + 2 * kPlaneBytes) = hi;
-          *reinterpret_cast<uint32_t*>(ag + 3 * kPlaneBytes) = li;
         }
       }
       fence_proxy_async_smem();
@@ -435,7 +477,8 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
         tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + c0, v);
         const int g = c0 / acc_cols;
         const int col = c0 % acc_cols;
-        float* dst = p.Yp + (((size_t)split * p.N + (j0 + g)) * acc_cols + col) * p.n_pad + ei;
+        const int j = p.order[j0 + g] & kNodeMask;
+        float* dst = p.Yp + (((size_t)split * p.N + j) * acc_cols + col) * p.n_pad + ei;
 #pragma unroll
         for (int k = 0; k < 16; ++k) dst[(size_t)k * p.n_pad] = v[k];
       }
@@ -774,6 +817,7 @@ bem_status mixed_plan(bem_ctx* ctx, const double* V, int64_t ldv, int nu, int S,
   p.self32 = reinterpret_cast<const float2*>(ctx->con.self32);
   p.pack32 = ctx->geo.pack32;
   p.z = ctx->con.z;
+  p.order = ctx->con.order;
   p.status = ctx->d_status;
   plan.V = V;
   plan.ldv = ldv;

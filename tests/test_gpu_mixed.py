@@ -44,9 +44,17 @@ def _run(bem, mesh, spec, N, nu, seed, AV=True):
     return ctx, V, z, w, out
 
 
-@pytest.mark.parametrize("case", ["sphere320", "ragged108", "nu1", "nu130"])
+@pytest.mark.parametrize("case", ["sphere320", "ragged108", "nu1", "nu130", "g3_twins",
+                                  "odd_n_twins"])
 def test_mixed_matches_oracle(bem, case):
-    if case == "sphere320":
+    if case == "g3_twins":
+        # nu = 72 leaves room for 3 nodes per work unit: twin pairs (32 ellipse nodes, all
+        # conjugate) straddle the unit boundaries and fall back to single evaluation there
+        mesh, spec, N, nu = synth.icosphere(1), synth.ContourSpec("ellipse", 6.0 + 0j, 1.5, 0.4), 32, 72
+    elif case == "odd_n_twins":
+        # 7 circle nodes: three twin pairs and the real node theta = pi on its own
+        mesh, spec, N, nu = synth.icosphere(1), synth.ContourSpec("circle", 4.0 + 0j, 1.0, 1.0), 7, 40
+    elif case == "sphere320":
         mesh, spec, N, nu = synth.icosphere(2), synth.ContourSpec("circle", 4.0 + 0j, 1.0, 1.0), 16, 16
     elif case == "ragged108":
         mesh, spec, N, nu = synth.cube_grid(3), synth.ContourSpec("ellipse", 6.5 + 0.1j, 1.5, 0.4), 7, 5
@@ -116,4 +124,24 @@ def test_mixed_self_terms_both_routes(bem, scale, centre):
         d = np.diag(Y[j].cpu().numpy())
         assert np.max(np.abs(d - np.diag(A)) / np.abs(np.diag(A))) < 2e-5, j
         assert _relerr(Y[j].cpu().numpy(), A) < TOL
+    ctx.close()
+
+
+@pytest.mark.parametrize("kind,N,twins", [("ellipse", 32, 16), ("circle", 7, 3),
+                                          ("circle", 1, 0), ("chebyshev", 12, 0)])
+def test_node_order(bem, kind, N, twins):
+    """The schedule is a permutation of the nodes; its twin pairs (at the front) have
+    bit-equal real parts, so the shared sine and cosine are exactly each node's own, and
+    for a contour symmetric about the real axis they are conjugates."""
+    mesh = synth.icosphere(0)
+    ctx = bem.Context(0)
+    ctx.set_mesh(mesh.xyz, mesh.tri)
+    z, _ = ctx.set_contour(kind, 5.0 + 0j, 1.25, 0.5, N)
+    order, tw = ctx.node_order()
+    assert sorted(order.tolist()) == list(range(N))
+    assert tw == twins
+    for P in range(tw):
+        a, b = z[order[2 * P]], z[order[2 * P + 1]]
+        assert np.float32(a.real) == np.float32(b.real)
+        assert a.real == b.real and a.imag == -b.imag
     ctx.close()
