@@ -186,6 +186,51 @@ bem_status bem_ritz_vectors(bem_ctx* ctx, const double* V_dev, int64_t ldv, int 
                             const double* Y_dev, int k, double* X_dev, int64_t ldx, void* stream);
 
 /*
+ * Node-summed operator of Algorithm 1 (Section 3.3, Eq. linsyssim): with the mesh and the
+ * contour of the context,
+ *     Y = sum_j c_j A(z_j) X_j        (per_node != 0: a block X_j per node)
+ *     Y = (sum_j c_j A(z_j)) X        (per_node == 0: one X; the Schur complement S = sum_j
+ *                                      w_j A(z_j) / (z_j - s) is the case c_j = w_j/(z_j - s))
+ * evaluated matrix-free by the fused kernel of bem_project's mixed path (FP32 entries, BF16x3
+ * tcgen05 contraction, FP32 accumulation; the entries c_j A_il(z_j) are formed in FP32).
+ * The operator is the 7-point rule with the self terms (no near-field corrections: it serves
+ * the basis construction).
+ *   coef_host  2 N doubles (host): c_j as (re, im).
+ *   X_dev      n x nu complex, column-major, leading dimension ldx >= n; with per_node, N
+ *              such blocks, block j at X_dev + 2 j ldx nu doubles.
+ *   Y_dev      n x nu complex, column-major, leading dimension n (output).
+ * 1 <= nu <= 256. Uses the context's scratch. Synchronises the stream.
+ */
+bem_status bem_apply_sum(bem_ctx* ctx, const double* coef_host, const double* X_dev,
+                         int64_t ldx, int nu, int per_node, double* Y_dev, void* stream);
+
+/*
+ * Matrix-free solve with the same operator (Section 3.3, Eq. wjp1 / Eq. linsyssim: the
+ * system S u = b of each inverse power step), never forming S:
+ *     (sum_j c_j A(z_j)) X = B
+ * by restarted GMRES (restart 40) on every column at once; each Arnoldi step applies the
+ * operator to one vector per column with the fused kernel (as bem_apply_sum), the Arnoldi
+ * vectors are FP32 and orthogonalised by classical Gram-Schmidt run twice (FP64 dot
+ * products), the Hessenberg least-squares problems are solved by Givens rotations on the
+ * host (FP64). Stops when every column's true relative residual ||B - S X|| / ||B|| is
+ * <= tol (checked at each restart, and when the rotations estimate it below tol / 2), or
+ * after max_iter Arnoldi steps in total.
+ *   coef_host   2 N doubles (host): c_j as (re, im).
+ *   B_dev       n x nu complex, column-major, leading dimension ldb >= n.
+ *   X_dev       n x nu complex, column-major, leading dimension ldx >= n (output).
+ *   iters       (host, may be NULL): Arnoldi steps taken.
+ *   relres_host (host, may be NULL): nu doubles, the final true relative residuals.
+ * The operator itself carries the split-precision error of the fused kernel (~3e-5
+ * relative), so residuals much below ~1e-5 are not reachable: tol around 1e-4 suits the
+ * inexact inverse power steps. 1 <= nu <= 256, tol > 0, max_iter >= 1. Does not fail on
+ * slow convergence: the caller reads relres_host. Uses the context's scratch. Synchronises
+ * the stream.
+ */
+bem_status bem_solve_sum(bem_ctx* ctx, const double* coef_host, const double* B_dev,
+                         int64_t ldb, int nu, double tol, int max_iter, double* X_dev,
+                         int64_t ldx, int* iters, double* relres_host, void* stream);
+
+/*
  * Basis improvement by q steps of the inverse power method for the Cauchy linearisation
  * (Section 3.3, Algorithm 1; Eq. wjp1, Eq. vjp1, Eq. viupd, Eq. linsyssim) with shift s,
  * applied to every column of V (n x nu, leading dimension ldv) at once, starting from
@@ -194,12 +239,24 @@ bem_status bem_ritz_vectors(bem_ctx* ctx, const double* V_dev, int64_t ldv, int 
  *     v_j' = (v_j - u') / (z_j - s).
  * (The algebra of (A - sM) w' = M w; the extra u term of the paper's right-hand side
  * vanishes because M has a zero last block.) S is assembled densely in FP32 and LU-
- * factorised once; sum_j B_j v_j / (z_j - s) is applied matrix-free in FP32. On return V
+ * factorised once; sum_j B_j v_j / (z_j - s) is applied matrix-free by the node-summed fused
+ * kernel (bem_apply_sum). On return V
  * holds the last u (not orthonormalised). Needs n^2 * 8 + N n nu * 8 bytes of scratch.
  * N <= 64, 1 <= nu <= 256. Synchronises the stream.
  */
 bem_status bem_inverse_power(bem_ctx* ctx, double* V_dev, int64_t ldv, int nu, int q,
                              double shift_re, double shift_im, void* stream);
+
+/*
+ * bem_inverse_power without forming S (the basis construction at sizes where the dense S,
+ * n^2 * 8 bytes, does not fit): the same q steps, each S u' = b solved by bem_solve_sum's
+ * GMRES to relative residual tol with at most max_iter Arnoldi steps. Memory: the N n nu
+ * iterates, 41 n nu FP32 Arnoldi vectors and the fused kernel's basis planes, no n^2 term.
+ * gmres_iters (host, may be NULL): Arnoldi steps over all q solves. Synchronises the stream.
+ */
+bem_status bem_inverse_power_mf(bem_ctx* ctx, double* V_dev, int64_t ldv, int nu, int q,
+                                double shift_re, double shift_im, double tol, int max_iter,
+                                int* gmres_iters, void* stream);
 
 /*
  * FP64 refinement of approximate eigenpairs of A(k) x = 0 (the eigenpairs the paper

@@ -42,6 +42,9 @@ SIGNATURES = {
     "bem_set_contour": (_I, [_P, _I, _D, _D, _D, _D, _I, _P, _P, _P]),
     "bem_project": (_I, [_P, _P, _I64, _I, _P, _P, _I, _P]),
     "bem_node_order": (_I, [_P, _P, _P]),
+    "bem_apply_sum": (_I, [_P, _P, _P, _I64, _I, _I, _P, _P]),
+    "bem_solve_sum": (_I, [_P, _P, _P, _I64, _I, _D, _I, _P, _I64, ctypes.POINTER(_I), _P, _P]),
+    "bem_inverse_power_mf": (_I, [_P, _P, _I64, _I, _I, _D, _D, _D, _I, ctypes.POINTER(_I), _P]),
     "bem_cholqr2": (_I, [_P, _P, _I64, _I64, _I, _P, _P]),
     "bem_residual": (_I, [_P, _I, _P, _P, _I64, _P, _P, _P]),
     "bem_kernel_launches": (_I64, [_P]),
@@ -319,6 +322,30 @@ class Context:
         self.N = int(N)
         return z.view(np.complex128), w.view(np.complex128)
 
+    def apply_sum(self, coef, X, per_node=True, stream=None):
+        """Y = sum_j c_j A(z_j) X_j (per_node: X of shape (N, n, nu), each block column-major)
+        or (sum_j c_j A(z_j)) X (X n x nu column-major); Y n x nu complex128 column-major."""
+        import torch
+        c = np.ascontiguousarray(np.asarray(coef, dtype=np.complex128)).view(np.float64)
+        if c.size != 2 * self.N:
+            raise ValueError("apply_sum: one coefficient per node")
+        if per_node:
+            if X.dim() != 3 or X.shape[0] != self.N or X.stride(1) != 1:
+                raise ValueError("apply_sum: X must be (N, n, nu) with column-major blocks")
+            n, nu = X.shape[1], X.shape[2]
+            ldx = X.stride(2)
+            if X.stride(0) != ldx * nu:
+                raise ValueError("apply_sum: node blocks must be ldx * nu apart")
+        else:
+            _check_fortran(X, "X")
+            n, nu = X.shape
+            ldx = X.stride(1)
+        Y = torch.empty((nu, n), dtype=torch.complex128, device=X.device).t()
+        self._chk("bem_apply_sum", self._lib.bem_apply_sum(
+            self._h, c.ctypes.data_as(_P), _P(X.data_ptr()), int(ldx), int(nu),
+            1 if per_node else 0, _P(Y.data_ptr()), _stream(stream)))
+        return Y
+
     def node_order(self):
         """(order, twins): the mixed kernel's node schedule (slot -> node) and the number
         of twin pairs (nodes with equal FP32 real parts) at its front."""
@@ -424,6 +451,34 @@ class Context:
         sh = complex(shift)
         self._chk("bem_inverse_power", self._lib.bem_inverse_power(
             self._h, _ptr(V), V.stride(1), nu, int(q), sh.real, sh.imag, _stream(stream)))
+
+    def inverse_power_mf(self, V, q, shift, tol=1e-4, max_iter=400, stream=None):
+        """q steps of Algorithm 1 with matrix-free GMRES solves (in place); returns the total
+        number of Arnoldi steps."""
+        _check_fortran(V, "V")
+        n, nu = V.shape
+        sh = complex(shift)
+        it = _I(0)
+        self._chk("bem_inverse_power_mf", self._lib.bem_inverse_power_mf(
+            self._h, _ptr(V), V.stride(1), nu, int(q), sh.real, sh.imag, float(tol),
+            int(max_iter), ctypes.byref(it), _stream(stream)))
+        return int(it.value)
+
+    def solve_sum(self, coef, B, tol=1e-4, max_iter=400, stream=None):
+        """X with (sum_j c_j A(z_j)) X = B by matrix-free GMRES; returns (X, iters, relres)."""
+        import torch
+        _check_fortran(B, "B")
+        n, nu = B.shape
+        c = np.ascontiguousarray(np.asarray(coef, dtype=np.complex128)).view(np.float64)
+        if c.size != 2 * self.N:
+            raise ValueError("solve_sum: one coefficient per node")
+        X = torch.empty((nu, n), dtype=torch.complex128, device=B.device).t()
+        it = _I(0)
+        rel = np.zeros(nu)
+        self._chk("bem_solve_sum", self._lib.bem_solve_sum(
+            self._h, c.ctypes.data_as(_P), _ptr(B), B.stride(1), nu, float(tol), int(max_iter),
+            _ptr(X), X.stride(1), ctypes.byref(it), rel.ctypes.data_as(_P), _stream(stream)))
+        return X, int(it.value), rel
 
     def refine(self, lam, X, tol=1e-13, maxit=40, stream=None):
         """FP64 refinement of eigenpairs (X refined in place); returns (lam, relres, iters)."""

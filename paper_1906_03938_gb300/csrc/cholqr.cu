@@ -569,11 +569,11 @@ size_t right_multiply_smem(int nu) {
 // each block owns kRMRows complete rows of V, staged in shared memory before any is
 // overwritten. Three real products per complex term: a b = (S1 - S2) + i (S3 - S1 - S2),
 // S1 = a.re b.re, S2 = a.im b.im, S3 = (a.re + a.im)(b.re + b.im).
-// gate: skip unless *gate != 0; skip_if: skip when *skip_if != 0.
+// gate, need: skip unless *gate != 0 and *need != 0; skip_if: skip when *skip_if != 0.
 __global__ void __launch_bounds__(256)
 right_multiply_kernel(double2* V, int64_t ldv, int64_t n, int nu, const double2* __restrict__ M,
-                      const int* gate, const int* skip_if) {
-  if ((gate && *gate == 0) || (skip_if && *skip_if != 0)) return;
+                      const int* gate, const int* skip_if, const int* need) {
+  if ((gate && *gate == 0) || (need && *need == 0) || (skip_if && *skip_if != 0)) return;
   extern __shared__ double rm_smem[];
   double* vr = rm_smem;                  // [nu][kRMRows]
   double* vi = vr + nu * kRMRows;
@@ -628,6 +628,120 @@ right_multiply_kernel(double2* V, int64_t ldv, int64_t n, int nu, const double2*
     const int c = o % nu, rr = o / nu;
     const int64_t r = r0 + rr;
     if (r < n) V[(int64_t)c * ldv + r] = make_double2(s1[m] - s2[m], s3[m] - s1[m] - s2[m]);
+  }
+}
+
+// V <- V + V (M - I) for the near-identity factor M = I + Y (upper triangular), with the
+// small product V Y in double-FP32 arithmetic on the FP32 pipe (this GPU's FP64 pipe runs at
+// ~1/65 of its rate). Each FP64 value x is carried as hi + lo, hi = fl32(x),
+// lo = fl32(x - hi); the product hi_v hi_y is formed exactly (its rounding error recovered by
+// an FMA) and added to the running sum by an error-free two-sum; the error terms and the
+// hi x lo cross products gather in an FP32 companion, whose own rounding leaves a relative
+// error of ~1e-13 of the sum of the terms' magnitudes. Since ||Y|| <= ~||G - I|| (at most
+// 5e-4 on this route, ~1e-6 after an FP32 first pass), that is ~1e-17 of |V| or less: below
+// V's own FP64 rounding, which the final FP64 addition V + V Y then sets.
+// Same blocking as right_multiply_kernel: kRMRows complete rows per block, staged first.
+// gate: skip unless *gate != 0; skip_if: skip when *skip_if != 0.
+constexpr int kDFK = 8;   // k chunk of M staged at a time
+size_t right_multiply_df_smem(int nu) {
+  return (size_t)(nu * kRMRows + kDFK * nu) * sizeof(float4);
+}
+
+// Error-free transformations, written with the _rn intrinsics so that the compiler neither
+// contracts a product into a following addition nor reorders the sums.
+__device__ __forceinline__ void two_sum(float& s, float b, float& err) {
+  const float t = __fadd_rn(s, b);
+  const float bb = __fsub_rn(t, s);
+  err = __fadd_rn(err, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(b, bb)));
+  s = t;
+}
+// s + lo += x y with the product's rounding error recovered exactly
+__device__ __forceinline__ void df_mac(float& s, float& lo, float x, float y) {
+  const float p = __fmul_rn(x, y);
+  lo = __fadd_rn(lo, __fmaf_rn(x, y, -p));
+  two_sum(s, p, lo);
+}
+
+// Y = M - I split once into FP32 (re hi, im hi, re lo, im lo) for every block of the
+// multiply (the conversions run on the FP64 pipe).
+__global__ void split_near_factor_kernel(const double2* __restrict__ M, int nu,
+                                         float4* __restrict__ Ms, const int* gate,
+                                         const int* skip_if) {
+  if ((gate && *gate == 0) || (skip_if && *skip_if != 0)) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nu * nu) return;
+  double2 b = M[t];
+  if (t % nu == t / nu) b.x -= 1.0;   // exact: the diagonal is near 1
+  const float br = (float)b.x, bi = (float)b.y;
+  Ms[t] = make_float4(br, bi, (float)(b.x - br), (float)(b.y - bi));
+}
+
+__global__ void __launch_bounds__(256)
+right_multiply_near_df_kernel(double2* V, int64_t ldv, int64_t n, int nu,
+                              const float4* __restrict__ Ms, const int* gate, const int* skip_if) {
+  if ((gate && *gate == 0) || (skip_if && *skip_if != 0)) return;
+  extern __shared__ float4 df_smem[];
+  float4* sV = df_smem;                 // [nu][kRMRows]: (re hi, im hi, re lo, im lo)
+  float4* sM = sV + nu * kRMRows;       // [kDFK][nu]
+  const int tid = threadIdx.x;
+  const int64_t r0 = (int64_t)blockIdx.x * kRMRows;
+  for (int t = tid; t < kRMRows * nu; t += blockDim.x) {
+    const int rr = t % kRMRows, c = t / kRMRows;
+    const int64_t r = r0 + rr;
+    const double2 v = (r < n) ? V[(int64_t)c * ldv + r] : make_double2(0.0, 0.0);
+    const float hr = (float)v.x, hi = (float)v.y;
+    sV[c * kRMRows + rr] = make_float4(hr, hi, (float)(v.x - hr), (float)(v.y - hi));
+  }
+  constexpr int kOut = kMaxNu * kRMRows / 256;
+  const int outs = kRMRows * nu;
+  float sr[kOut], srl[kOut], si[kOut], sil[kOut];
+#pragma unroll
+  for (int m = 0; m < kOut; ++m) sr[m] = srl[m] = si[m] = sil[m] = 0.f;
+  for (int k0 = 0; k0 < nu; k0 += kDFK) {
+    const int kn = min(kDFK, nu - k0);
+    __syncthreads();
+    for (int t = tid; t < kDFK * nu; t += blockDim.x) {
+      const int kk = t / nu, c = t % nu;
+      sM[kk * nu + c] = kk < kn ? Ms[(int64_t)c * nu + k0 + kk] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < kOut; ++m) {
+      const int o = tid + 256 * m;
+      if (o >= outs) break;
+      const int c = o % nu, rr = o / nu;
+      const int kend = min(kn, c - k0 + 1);   // M[k][c] = 0 for k > c
+      for (int kk = 0; kk < kend; ++kk) {
+        const float4 a = sV[(k0 + kk) * kRMRows + rr];
+        const float4 b = sM[kk * nu + c];
+        // real part: a.re b.re - a.im b.im, then the hi x lo cross terms
+        df_mac(sr[m], srl[m], a.x, b.x);
+        df_mac(sr[m], srl[m], -a.y, b.y);
+        srl[m] = __fmaf_rn(a.x, b.z, srl[m]);
+        srl[m] = __fmaf_rn(a.z, b.x, srl[m]);
+        srl[m] = __fmaf_rn(-a.y, b.w, srl[m]);
+        srl[m] = __fmaf_rn(-a.w, b.y, srl[m]);
+        // imaginary part: a.re b.im + a.im b.re
+        df_mac(si[m], sil[m], a.x, b.y);
+        df_mac(si[m], sil[m], a.y, b.x);
+        sil[m] = __fmaf_rn(a.x, b.w, sil[m]);
+        sil[m] = __fmaf_rn(a.z, b.y, sil[m]);
+        sil[m] = __fmaf_rn(a.y, b.z, sil[m]);
+        sil[m] = __fmaf_rn(a.w, b.x, sil[m]);
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < kOut; ++m) {
+    const int o = tid + 256 * m;
+    if (o >= outs) break;
+    const int c = o % nu, rr = o / nu;
+    const int64_t r = r0 + rr;
+    if (r >= n) continue;
+    // V + V Y: the block's own rows, still unchanged in global memory
+    const double2 v = V[(int64_t)c * ldv + r];
+    V[(int64_t)c * ldv + r] = make_double2(v.x + ((double)sr[m] + (double)srl[m]),
+                                           v.y + ((double)si[m] + (double)sil[m]));
   }
 }
 
@@ -736,9 +850,16 @@ bem_status near_pass(bem_ctx* ctx, double* V_dev, int64_t ldv, int64_t n, int nu
                                            nullptr, gate, done);
   near_tile_kernel<2><<<tgrid, 64, 0, s>>>(w.G, w.Y, w.P1, w.Q1, nu, nullptr, nullptr, w.Z,
                                            nullptr, gate, done);
-  right_multiply_kernel<<<(unsigned)((n + kRMRows - 1) / kRMRows), 256, right_multiply_smem(nu),
-                          s>>>(V, ldv, n, nu, w.Z, gate, nullptr);
-  ctx->launches += 9;
+  // V <- V Z: the classic inverse in FP64, the near-identity factor as V + V (Z - I)
+  const unsigned rb = (unsigned)((n + kRMRows - 1) / kRMRows);
+  right_multiply_kernel<<<rb, 256, right_multiply_smem(nu), s>>>(V, ldv, n, nu, w.Z, gate,
+                                                                 nullptr, classic);
+  float4* Zs = reinterpret_cast<float4*>(w.R2);   // R2 is free outside the classic passes
+  split_near_factor_kernel<<<(unsigned)((nu * nu + 255) / 256), 256, 0, s>>>(w.Z, nu, Zs, gate,
+                                                                            classic);
+  right_multiply_near_df_kernel<<<rb, 256, right_multiply_df_smem(nu), s>>>(V, ldv, n, nu, Zs,
+                                                                            gate, classic);
+  ctx->launches += 11;
   return cuda_check(ctx, cudaGetLastError(), "cholqr kernels");
 }
 
@@ -756,7 +877,7 @@ bem_status classic_pass(bem_ctx* ctx, double* V_dev, int64_t ldv, int64_t n, int
                                              refresh_seed ? w.deficient : nullptr, nullptr);
   triangular_inverse_kernel<<<nu, 128, 0, s>>>(R_out, nu, w.Z, nullptr);
   right_multiply_kernel<<<(unsigned)((n + kRMRows - 1) / kRMRows), 256, right_multiply_smem(nu),
-                          s>>>(V, ldv, n, nu, w.Z, nullptr, nullptr);
+                          s>>>(V, ldv, n, nu, w.Z, nullptr, nullptr, nullptr);
   ctx->launches += 5;
   if (refresh_seed) {
     refresh_columns_kernel<<<(unsigned)((n * nu + 255) / 256), 256, 0, s>>>(V, ldv, n, nu,
@@ -794,6 +915,9 @@ bem_status cholqr2_impl(bem_ctx* ctx, double* V_dev, int64_t n, int64_t ldv, int
   if ((st = set_smem(ctx, (const void*)cholesky_kernel, chol_smem)) != BEM_OK) return st;
   if ((st = set_smem(ctx, (const void*)right_multiply_kernel, right_multiply_smem(nu))) != BEM_OK)
     return st;
+  if ((st = set_smem(ctx, (const void*)right_multiply_near_df_kernel,
+                     right_multiply_df_smem(nu))) != BEM_OK)
+    return st;
   if (R_dev) {
     if ((st = classic_pass(ctx, V_dev, ldv, n, nu, L, w, w.R1, refresh_seed, s)) != BEM_OK) return st;
     if ((st = classic_pass(ctx, V_dev, ldv, n, nu, L, w, w.R2, 0, s)) != BEM_OK) return st;
@@ -822,7 +946,7 @@ bem_status cholqr2_impl(bem_ctx* ctx, double* V_dev, int64_t n, int64_t ldv, int
   else
     chol_inv32_kernel<16><<<1, 1024, ci_smem, s>>>(w.G, nu, w.Z, fallback);
   right_multiply_kernel<<<(unsigned)((n + kRMRows - 1) / kRMRows), 256, right_multiply_smem(nu),
-                          s>>>(V, ldv, n, nu, w.Z, nullptr, fallback);
+                          s>>>(V, ldv, n, nu, w.Z, nullptr, fallback, nullptr);
   ctx->launches += 4;
   if ((st = cuda_check(ctx, cudaGetLastError(), "cholqr kernels")) != BEM_OK) return st;
   if ((st = near_pass(ctx, V_dev, ldv, n, nu, L, w, nullptr, w.flags + 1, s)) != BEM_OK) return st;

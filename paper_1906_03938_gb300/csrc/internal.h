@@ -194,6 +194,20 @@ bem_status near_apply32(bem_ctx* ctx, const float2* V32, int nu, int nup, int C,
 // R[:, c] += (A_near - A_7)(lam_c) X[:, c] (deriv: the k-derivatives), FP64.
 cudaError_t launch_near_percol64(bem_ctx* ctx, int m, const double* lam_dev, const double* X,
                                  int64_t ldx, double* R, bool deriv, cudaStream_t s);
+// Node-summed fused apply (tcgen05; project_mixed.cu): out = sum_j c_j A(z_j) X_j, X_j at
+// X + j node_stride (per_node) or X itself, FP32 complex, column-major with leading dimension
+// ldx; out n x nu (leading dimension n). work: mixed_sum_work_bytes(ctx, nu, per_node) bytes.
+size_t mixed_sum_work_bytes(bem_ctx* ctx, int nu, bool per_node);
+bem_status mixed_sum_apply(bem_ctx* ctx, const float2* X, int64_t ldx, int64_t node_stride,
+                           bool per_node, int nu, const double* coef_host, float2* out,
+                           void* work, cudaStream_t s);
+// Restarted GMRES (gmres.cu) for (sum_j c_j A(z_j)) X = B, FP32 n x nu blocks (leading
+// dimension n), every column at once; work: gmres_sum_work_bytes(ctx, nu, restart) bytes.
+// relres_host (nu doubles, may be null): final true relative residuals.
+size_t gmres_sum_work_bytes(bem_ctx* ctx, int nu, int restart);
+bem_status gmres_sum32(bem_ctx* ctx, const double* coef_host, const float2* B, float2* X, int nu,
+                       double tol, int max_iter, int restart, void* work, cudaStream_t s,
+                       int* iters_out, double* relres_host);
 // mixed-precision fused projection (tcgen05); defined in project_mixed.cu
 bem_status project_mixed(bem_ctx* ctx, const double* V, int64_t ldv, int nu, double* Bhat,
                          double* AV, cudaStream_t s);

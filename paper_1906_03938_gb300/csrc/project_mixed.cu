@@ -20,12 +20,14 @@
 //    is bounded and a timeout aborts the block cleanly with an error status);
 //  * the evaluation warps finally read the accumulators from TMEM and store the FP32
 //    partial Y of the unit.
-// mixed_vhy_part_kernel / mixed_vhy_reduce_kernel then form
-// Bhat_j = w_j V^H (sum over column splits of Y_j) with a fixed summation order.
+// mixed_vhy_tc_kernel (one column chunk: BF16x3 on the tensor core, reading the same basis
+// planes) or mixed_vhy_part_kernel (FP32 CUDA cores, nu > 128), then mixed_vhy_reduce_kernel,
+// form Bhat_j = w_j V^H (sum over column splits of Y_j) with a fixed summation order.
 #include <cuda_bf16.h>
 #include <math.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "internal.h"
 #include "sm100.cuh"
@@ -65,6 +67,13 @@ struct MixedParams {
   const float* pack32;    // packed FP32 hi/lo panel geometry (64 floats per panel)
   const double* z;    // FP64 complex nodes
   const int* order;   // node schedule: slot -> node (| kTwinBit on the first of a twin pair)
+  // node-summed mode (sum != 0): Y = sum_j c_j A(z_j) X_j into one accumulator per unit;
+  // the FP32 partials of unit (row tile, node group gg, split) go to slice gg S + split
+  int sum;
+  const float2* coef;       // c_j (sum mode)
+  int64_t b_node_stride;    // bytes between the nodes' basis planes (0: one X for all)
+  int gchunk;               // node groups per unit (sum mode): a unit runs its K-blocks for
+  int ngc;                  // each of its groups in turn; ngc = ceil(nG / gchunk) chunks
   const __nv_bfloat16* Bp;   // prepared basis planes, tile-native
   float* Yp;          // FP32 partial products [S][N][2 nup][n_pad]
   int* status;
@@ -76,10 +85,11 @@ struct SmemLayout {
 };
 constexpr uint32_t kGeoBlockBytes = kBK * 64 * 4;   // packed geometry of one K-block
 
-__host__ __device__ inline SmemLayout smem_layout(int G, int nup) {
+// bnodes: basis plane sets per stage (G in the node-summed mode with one X per node, else 1)
+__host__ __device__ inline SmemLayout smem_layout(int G, int nup, int bnodes = 1) {
   SmemLayout L;
   L.a_stage_bytes = (uint32_t)G * 4 * kPlaneBytes;
-  L.b_stage_bytes = (uint32_t)256 * nup;     // 4 planes x 2 nup rows x 16 k x 2 B
+  L.b_stage_bytes = (uint32_t)bnodes * 256 * nup;   // 4 planes x 2 nup rows x 16 k x 2 B each
   L.a_off = 0;
   L.b_off = L.a_off + kStages * L.a_stage_bytes;
   L.graw_off = L.b_off + kStages * L.b_stage_bytes;    // per stage: packed geometry copy
@@ -151,7 +161,8 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
 // in the padding, then the hi/lo BF16 split into the four planes (Re hi, Re lo, Im hi, Im lo)
 // at ag; self points at the staged self term of column l0 (that of l0 + 1 is kMaxG later).
 __device__ __forceinline__ void put_entries(f2_t sr2, f2_t si2, const float2* self, int64_t i,
-                                            int64_t l0, int64_t n, unsigned char* ag) {
+                                            int64_t l0, int64_t n, unsigned char* ag,
+                                            bool scaled = false, float2 cf = float2()) {
   float re[2], im[2];
   f2split(sr2, re[0], re[1]);
   f2split(si2, im[0], im[1]);
@@ -161,6 +172,11 @@ __device__ __forceinline__ void put_entries(f2_t sr2, f2_t si2, const float2* se
       const float2 sv = self[d * kMaxG];
       re[d] = sv.x;
       im[d] = sv.y;
+    }
+    if (scaled) {        // node-summed mode: c_j A_il(z_j)
+      const float r = re[d] * cf.x - im[d] * cf.y;
+      im[d] = re[d] * cf.y + im[d] * cf.x;
+      re[d] = r;
     }
     if (i >= n || l0 + d >= n) {   // padding rows / columns of the tile
       re[d] = 0.f;
@@ -197,10 +213,13 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
 // tmem_given: TMEM columns already allocated by a persistent caller (its base address), or
 // kNoTmem to allocate (and release) them here.
 constexpr uint32_t kNoTmem = 0xffffffffu;
+// kSum: the node-summed mode (p.sum is set accordingly by the host)
+template <bool kSum>
 __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int u,
                                                  const uint32_t tmem_given) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  const SmemLayout L = smem_layout(p.G, p.nup);
+  const int bnodes = (kSum && p.b_node_stride) ? p.G : 1;
+  const SmemLayout L = smem_layout(p.G, p.nup, bnodes);
   unsigned char* sA = smem + L.a_off;
   unsigned char* sB = smem + L.b_off;
   float4* sRow = reinterpret_cast<float4*>(smem + L.row_off);
@@ -220,20 +239,28 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
   const int warp = threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
 
-  // unit -> (row tile, node group, column split)
+  // unit -> (row tile, node group(s), column split); the node-summed mode takes a chunk of
+  // gchunk node groups and runs the unit's K-blocks for each in turn (iteration
+  // it = group offset * nkb + K-block offset), all into one accumulator
   const int split = u % p.S;
   const int t = u / p.S;
-  const int gg = t % p.nG;
-  const int rt = t / p.nG;
+  const int ngc = kSum ? p.ngc : p.nG;
+  const int gc = t % ngc;
+  const int rt = t / ngc;
+  const int g_begin = kSum ? gc * p.gchunk : gc;
+  const int ngr = kSum ? min(p.gchunk, p.nG - g_begin) : 1;
   const int64_t row0 = (int64_t)rt * kBM;
   const int kb0 = (int)((int64_t)p.nK * split / p.S);
   const int kb1 = (int)((int64_t)p.nK * (split + 1) / p.S);
   const int nkb = kb1 - kb0;
+  const int nit = ngr * nkb;
+  const int gg = g_begin;                 // the node group (projection)
   const int j0 = gg * p.G;
   const int Gv = min(p.G, p.N - j0);
   const uint32_t acc_cols = 2u * p.nup;                 // TMEM columns per node
+  const uint32_t accs = kSum ? 1u : (uint32_t)p.G;   // accumulators (nodes, or their sum)
   uint32_t tmem_cols = 32;
-  while (tmem_cols < (uint32_t)p.G * acc_cols) tmem_cols <<= 1;
+  while (tmem_cols < accs * acc_cols) tmem_cols <<= 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -272,20 +299,27 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
       sRow[r] = v;
     }
     int issued = 0;
-    for (int it = 0; it < nkb; ++it) {
+    for (int it = 0; it < nit; ++it) {
       const int s = it % kStages;
       const uint32_t par = (it / kStages) & 1;
-      const int kb = kb0 + it;
+      const int kb = kb0 + (kSum ? it % nkb : it);
+      const int j0i = kSum ? (g_begin + it / nkb) * p.G : j0;
+      const int Gvi = kSum ? min(p.G, p.N - j0i) : Gv;
       int ok = 1;
       if (lane == 0) ok = wait_or_abort(&empty[s], par ^ 1, abort_flag, p.status);
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
       if (lane == 0) {
-        mbar_arrive_expect_tx(&bfull[s], L.b_stage_bytes);
-        bulk_g2s(sB + s * L.b_stage_bytes,
-                 reinterpret_cast<const unsigned char*>(p.Bp) +
-                     (size_t)kb * L.b_stage_bytes,
-                 L.b_stage_bytes, &bfull[s]);
+        const uint32_t bset = 256u * p.nup;   // one node's (or the shared) planes
+        const int nb = bnodes > 1 ? Gvi : 1;
+        mbar_arrive_expect_tx(&bfull[s], (uint32_t)nb * bset);
+        for (int g = 0; g < nb; ++g) {
+          const size_t node_off =
+              bnodes > 1 ? (size_t)(p.order[j0i + g] & kNodeMask) * (size_t)p.b_node_stride : 0;
+          bulk_g2s(sB + s * L.b_stage_bytes + g * bset,
+                   reinterpret_cast<const unsigned char*>(p.Bp) + node_off + (size_t)kb * bset,
+                   bset, &bfull[s]);
+        }
         mbar_arrive_expect_tx(&gready[s], kGeoBlockBytes);
         bulk_g2s(smem + L.graw_off + s * kGeoBlockBytes, p.pack32 + (size_t)kb * kBK * 64,
                  kGeoBlockBytes, &gready[s]);
@@ -307,8 +341,8 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
         const int k = x / kMaxG, g = x % kMaxG;
         const int64_t l = (int64_t)kb * kBK + k;
         float2 v = make_float2(0.f, 0.f);
-        if (l < p.n && g < Gv && l >= row0 && l < row0 + kBM)
-          v = p.self32[(int64_t)(p.order[j0 + g] & kNodeMask) * p.n + l];
+        if (l < p.n && g < Gvi && l >= row0 && l < row0 + kBM)
+          v = p.self32[(int64_t)(p.order[j0i + g] & kNodeMask) * p.n + l];
         sSelf[x] = v;
       }
       mbar_arrive(&gfull[s]);   // release: the staged values are visible to the waiters
@@ -328,7 +362,7 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
       const int pa[6] = {0, 0, 1, 2, 2, 3};   // Ar_hi, Ar_hi, Ar_lo, Ai_hi, Ai_hi, Ai_lo
       const int pb[6] = {0, 1, 0, 2, 3, 2};   // [Vr|Vi], [Vr_lo|Vi_lo], [-Vi|Vr], [-Vi_lo|Vr_lo]
       const uint32_t bplane = 2u * p.C * kBK * 2;   // bytes of one basis plane per chunk
-      for (int it = 0; it < nkb; ++it) {
+      for (int it = 0; it < nit; ++it) {
         const int s = it % kStages;
         const uint32_t par = (it / kStages) & 1;
         if (!wait_or_abort(&afull[s], par, abort_flag, p.status)) break;
@@ -336,14 +370,17 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
         tc_fence_after();
         const uint32_t a_base = smem_u32(sA + s * L.a_stage_bytes);
         const uint32_t b_base = smem_u32(sB + s * L.b_stage_bytes);
-        for (int g = 0; g < Gv; ++g) {
+        const int Gvi = kSum ? min(p.G, p.N - (g_begin + it / nkb) * p.G) : Gv;
+        for (int g = 0; g < Gvi; ++g) {
+          const uint32_t bg = b_base + (bnodes > 1 ? g * 256u * p.nup : 0u);
           for (int c = 0; c < p.nchunks; ++c) {
-            const uint32_t d = tmem_base + g * acc_cols + c * 2 * p.C;
+            const uint32_t d = tmem_base + (kSum ? 0u : g * acc_cols) + c * 2 * p.C;
+            const bool fresh = it == 0 && (!kSum || g == 0);
 #pragma unroll
             for (int q = 0; q < 6; ++q) {
               const uint64_t ad = smem_desc(a_base + (g * 4 + pa[q]) * kPlaneBytes, 128, 256);
-              const uint64_t bd = smem_desc(b_base + (c * 4 + pb[q]) * bplane, 128, 256);
-              mma_bf16(d, ad, bd, idesc, (it > 0 || q > 0) ? 1u : 0u);
+              const uint64_t bd = smem_desc(bg + (c * 4 + pb[q]) * bplane, 128, 256);
+              mma_bf16(d, ad, bd, idesc, (fresh && q == 0) ? 0u : 1u);
             }
           }
         }
@@ -356,28 +393,40 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
     const int e = warp - 2;               // 0..15: row group of the 128 x 16 block
     // node constants
     float kr[kMaxG], kmi[kMaxG];
+    float2 cf[kSum ? kMaxG : 1];
     bool twin[kMaxG / 2];
+    constexpr bool scaled = kSum;
+    int Gvc = Gv;   // nodes of the current group
+    auto load_nodes = [&](int j0x, int Gvx) {
 #pragma unroll
-    for (int g = 0; g < kMaxG; ++g) {
-      const int code = p.order[j0 + (g < Gv ? g : 0)];
-      const int j = code & kNodeMask;
-      kr[g] = (float)p.z[2 * j];
-      kmi[g] = (float)(-p.z[2 * j + 1]) * kLog2e;
-      // a twin pair sits at slots 2 P, 2 P + 1 of the schedule: inside this group when the
-      // group starts at an even slot
-      if (g % 2 == 0)
-        twin[g / 2] = (code & kTwinBit) && (j0 % 2 == 0) && g + 1 < Gv && kr[g] ==
-                      (float)p.z[2 * (p.order[j0 + g + 1] & kNodeMask)];
-    }
+      for (int g = 0; g < kMaxG; ++g) {
+        const int code = p.order[j0x + (g < Gvx ? g : 0)];
+        const int j = code & kNodeMask;
+        if (kSum) cf[kSum ? g : 0] = p.coef[j];
+        kr[g] = (float)p.z[2 * j];
+        kmi[g] = (float)(-p.z[2 * j + 1]) * kLog2e;
+        // a twin pair sits at slots 2 P, 2 P + 1 of the schedule: inside this group when
+        // the group starts at an even slot
+        if (g % 2 == 0)
+          twin[g / 2] = (code & kTwinBit) && (j0x % 2 == 0) && g + 1 < Gvx && kr[g] ==
+                        (float)p.z[2 * (p.order[j0x + g + 1] & kNodeMask)];
+      }
+    };
+    load_nodes(j0, Gv);
     // this thread's entries: row 8 e + r8, columns 8 kg + 2 kp + {0, 1} for kg = 0, 1
     const int r8 = lane / 4, kp = lane % 4;
     const int row = 8 * e + r8;
     const int64_t i = row0 + row;
 
-    for (int it = 0; it < nkb; ++it) {
+    for (int it = 0; it < nit; ++it) {
       const int s = it % kStages;
       const uint32_t par = (it / kStages) & 1;
-      const int kb = kb0 + it;
+      const int kb = kb0 + (kSum ? it % nkb : it);
+      if (kSum && it > 0 && it % nkb == 0) {   // next node group of the chunk
+        const int j0x = (g_begin + it / nkb) * p.G;
+        Gvc = min(p.G, p.N - j0x);
+        load_nodes(j0x, Gvc);
+      }
       const bool ready = wait_or_abort(&gfull[s], par, abort_flag, p.status);
       const float4* sCol = sColAll + s * (kBK * 7);
       const float2* sSelf = sSelfAll + s * (kBK * kMaxG);
@@ -410,7 +459,7 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
         const float2* selfk = sSelf + k0 * kMaxG;
 #pragma unroll
         for (int g = 0; g < kMaxG; g += 2) {
-          if (g >= Gv) break;
+          if (g >= Gvc) break;
           if (twin[g / 2]) {
             // twin nodes: one sine and one cosine of the shared phase for both
             f2_t sa = f2(0.f, 0.f), ia = f2(0.f, 0.f), sb = f2(0.f, 0.f), ib = f2(0.f, 0.f);
@@ -431,13 +480,14 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
               sb = fma2(ab, cs, sb);
               ib = fma2(ab, sn, ib);
             }
-            put_entries(sa, ia, selfk + g, i, l0, p.n, a_stage + g * 4 * kPlaneBytes + off);
+            put_entries(sa, ia, selfk + g, i, l0, p.n, a_stage + g * 4 * kPlaneBytes + off,
+                        scaled, cf[kSum ? g : 0]);
             put_entries(sb, ib, selfk + g + 1, i, l0, p.n,
-                        a_stage + (g + 1) * 4 * kPlaneBytes + off);
+                        a_stage + (g + 1) * 4 * kPlaneBytes + off, scaled, cf[kSum ? g + 1 : 0]);
           } else {
 #pragma unroll
             for (int h = g; h < g + 2; ++h) {
-              if (h >= Gv) break;
+              if (h >= Gvc) break;
               f2_t sr2 = f2(0.f, 0.f), si2 = f2(0.f, 0.f);
               const f2_t kmi2 = f2(kmi[h], kmi[h]), kr2 = f2(kr[h], kr[h]);
 #pragma unroll
@@ -453,7 +503,8 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
                 sr2 = fma2(a, f2(cosf_mufu(p0), cosf_mufu(p1)), sr2);
                 si2 = fma2(a, f2(sinf_mufu(p0), sinf_mufu(p1)), si2);
               }
-              put_entries(sr2, si2, selfk + h, i, l0, p.n, a_stage + h * 4 * kPlaneBytes + off);
+              put_entries(sr2, si2, selfk + h, i, l0, p.n, a_stage + h * 4 * kPlaneBytes + off,
+                          scaled, cf[kSum ? h : 0]);
             }
           }
         }
@@ -471,14 +522,16 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
       const int part = (warp - 2) / 4;           // four warps per quarter split the columns
       const int erow = quarter * 32 + lane;
       const int64_t ei = row0 + erow;
-      const uint32_t cols_total = (uint32_t)Gv * acc_cols;
+      const uint32_t cols_total = (kSum ? 1u : (uint32_t)Gv) * acc_cols;
       for (uint32_t c0 = part * 16; c0 < cols_total; c0 += 64) {
         float v[16];
         tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + c0, v);
         const int g = c0 / acc_cols;
         const int col = c0 % acc_cols;
-        const int j = p.order[j0 + g] & kNodeMask;
-        float* dst = p.Yp + (((size_t)split * p.N + j) * acc_cols + col) * p.n_pad + ei;
+        // projection: slice split, node j; node-summed: slice gg S + split
+        const size_t slot = kSum ? (size_t)gc * p.S + split
+                                  : (size_t)split * p.N + (p.order[j0 + g] & kNodeMask);
+        float* dst = p.Yp + (slot * acc_cols + col) * p.n_pad + ei;
 #pragma unroll
         for (int k = 0; k < 16; ++k) dst[(size_t)k * p.n_pad] = v[k];
       }
@@ -498,7 +551,13 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
 }
 
 __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p) {
-  mixed_apply_unit(p, blockIdx.x, kNoTmem);
+  mixed_apply_unit<false>(p, blockIdx.x, kNoTmem);
+}
+
+// Node-summed form: Y = sum_j c_j A(z_j) X_j (the right-hand side of an inverse power
+// step, X_j per node) or (sum_j c_j A(z_j)) X (one X: the Schur complement S applied).
+__global__ void __launch_bounds__(kThreads, 1) mixed_sum_kernel(MixedParams p) {
+  mixed_apply_unit<true>(p, blockIdx.x, kNoTmem);
 }
 
 // Persistent grouped kernel over several problems: one CTA per SM takes work units from a
@@ -532,7 +591,7 @@ mixed_apply_grouped_kernel(const MixedParams* __restrict__ plist, const int* __r
       if (unit_start[mid] <= b) lo = mid; else hi = mid - 1;
     }
     const MixedParams p = plist[lo];
-    mixed_apply_unit(p, b - unit_start[lo], tmem_base);
+    mixed_apply_unit<false>(p, b - unit_start[lo], tmem_base);
     __syncthreads();   // the unit's barriers, shared memory and accumulators are free again
   }
   tc_fence_before();
@@ -689,6 +748,260 @@ mixed_vhy_part_kernel(const float2* __restrict__ V32, int nu, int64_t n, int n_p
   }
 }
 
+// Partial products P_r,j = V^H Y_j on the tensor core (one chunk of columns, nup <= 128,
+// C = nup): a CTA takes node j and the rows of part r, 32 rows per stage.
+//  * the A operand is the prepared basis planes [Vr | Vi] (hi and lo) of the main kernel,
+//    split into two M = 128 halves (Vr rows in half 0, Vi rows in half 1, zero rows above C)
+//    so that each output's real and imaginary combinations meet in one TMEM lane;
+//  * 8 converter warps sum the FP32 partials Y of the column splits, split them into BF16
+//    hi/lo and store them as the B operand (N = 2 C = [Yr | Yi], K = rows, canonical
+//    K-major layout);
+//  * one MMA thread issues per 16-row K-block and half: A_hi B_hi + A_hi B_lo + A_lo B_hi
+//    into D_h (128 x 2 C, FP32, TMEM);
+//  * epilogue, lane a: Re = D0[a][b] + D1[a][C + b], Im = D0[a][C + b] - D1[a][b]
+//    (conj(V)^T Y = Vr^T Yr + Vi^T Yi + i (Vr^T Yi - Vi^T Yr)), written as FP64 partials.
+// Every wait is bounded; a timeout aborts the block cleanly with an error status.
+constexpr int kVStages = 2;
+constexpr int kVKB = 2;                       // 16-row K-blocks per stage
+constexpr int kVRows = 16 * kVKB;             // rows per stage
+constexpr int kVConvWarps = 8;
+constexpr int kVConvThreads = 32 * kVConvWarps;
+constexpr int kVThreads = 32 * (2 + kVConvWarps);
+constexpr uint32_t kVHalfBytes = 128 * 32;    // one 128-row x 16-k BF16 operand block
+
+struct VhyLayout {
+  uint32_t a_stage, b_stage, b_off, bar_off, misc_off, total, tmem_cols;
+};
+__host__ __device__ inline VhyLayout vhy_layout(int C) {
+  VhyLayout L;
+  L.a_stage = kVKB * 2 * 2 * kVHalfBytes;          // [kb][plane hi/lo][half]
+  L.b_stage = kVKB * 2 * (uint32_t)(2 * C) * 32;   // [kb][plane hi/lo] N = 2 C rows x 32 B
+  L.b_off = kVStages * L.a_stage;
+  L.bar_off = L.b_off + kVStages * L.b_stage;
+  L.misc_off = L.bar_off + 8 * 8;                  // 7 mbarriers (+1 pad)
+  L.total = L.misc_off + 16;
+  const uint32_t need = 4u * C + (C % 16 ? 8u : 0u);   // two halves x 2 C columns (+ overread)
+  L.tmem_cols = 32;
+  while (L.tmem_cols < need) L.tmem_cols <<= 1;
+  return L;
+}
+
+// TPT: column/row-group tasks per converter thread and stage (8 C / 256 rounded up to 1, 2, 4).
+template <int TPT>
+__global__ void __launch_bounds__(kVThreads, 2)
+mixed_vhy_tc_kernel(const __nv_bfloat16* __restrict__ Bp, const float* __restrict__ Yp,
+                    int64_t n, int n_pad, int nu, int C, int N, int nK, int slices,
+                    int64_t rows_per_part, double* __restrict__ part, int* status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const VhyLayout L = vhy_layout(C);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
+  uint64_t* afull = bars;        // [2] basis planes landed
+  uint64_t* bfull = bars + 2;    // [2] converted Y stored
+  uint64_t* empty = bars + 4;    // [2] MMAs done with the stage
+  uint64_t* accfull = bars + 6;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.misc_off);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.misc_off + 4);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int j = blockIdx.x;
+  const int64_t r_begin = (int64_t)blockIdx.y * rows_per_part;
+  const int64_t r_end = min(n, r_begin + rows_per_part);
+  const int nst = (int)((r_end - r_begin + kVRows - 1) / kVRows);
+  const int twoC = 2 * C;
+  const uint32_t plane_bytes = (uint32_t)twoC * 32;   // one prepared plane of a K-block
+  const uint32_t half_bytes = (uint32_t)C * 32;       // its Vr or Vi rows
+
+  // zero the A blocks once: rows C..127 of each half stay zero (the copies fill rows < C)
+  for (uint32_t x = threadIdx.x; x < kVStages * L.a_stage / 16; x += blockDim.x)
+    reinterpret_cast<uint4*>(smem)[x] = make_uint4(0u, 0u, 0u, 0u);
+  fence_proxy_async_smem();
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kVStages; ++st) {
+      mbar_init(&afull[st], 1);
+      mbar_init(&bfull[st], kVConvThreads);
+      mbar_init(&empty[st], 1);
+    }
+    mbar_init(accfull, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, L.tmem_cols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- basis planes: bulk copies ----------------
+    if (lane == 0) {
+      int issued = 0;
+      for (int it = 0; it < nst; ++it) {
+        const int st = it % kVStages;
+        const uint32_t par = (it / kVStages) & 1;
+        if (!wait_or_abort(&empty[st], par ^ 1, abort_flag, status)) break;
+        const int kbg0 = (int)((r_begin + (int64_t)it * kVRows) / 16);
+        const int nkb = min(kVKB, nK - kbg0);
+        mbar_arrive_expect_tx(&afull[st], (uint32_t)nkb * 4u * half_bytes);
+        unsigned char* a_st = smem + st * L.a_stage;
+        for (int kb = 0; kb < nkb; ++kb) {
+          const unsigned char* src = reinterpret_cast<const unsigned char*>(Bp) +
+                                     (size_t)(kbg0 + kb) * (2u * plane_bytes * 2u);
+          for (int pl = 0; pl < 2; ++pl)
+            for (int h = 0; h < 2; ++h)
+              bulk_g2s(a_st + ((kb * 2 + pl) * 2 + h) * kVHalfBytes,
+                       src + pl * plane_bytes + h * half_bytes, half_bytes, &afull[st]);
+        }
+        ++issued;
+      }
+      if (*abort_flag)
+        for (int it = max(0, issued - kVStages); it < issued; ++it)
+          mbar_wait(&afull[it % kVStages], (it / kVStages) & 1, kWaitLimit);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(128, (uint32_t)twoC);
+      bool first = true;
+      for (int it = 0; it < nst; ++it) {
+        const int st = it % kVStages;
+        const uint32_t par = (it / kVStages) & 1;
+        if (!wait_or_abort(&afull[st], par, abort_flag, status)) break;
+        if (!wait_or_abort(&bfull[st], par, abort_flag, status)) break;
+        tc_fence_after();
+        const int kbg0 = (int)((r_begin + (int64_t)it * kVRows) / 16);
+        const int nkb = min(kVKB, nK - kbg0);
+        const uint32_t a_st = smem_u32(smem + st * L.a_stage);
+        const uint32_t b_st = smem_u32(smem + L.b_off + st * L.b_stage);
+        for (int kb = 0; kb < nkb; ++kb) {
+          const uint64_t bh = smem_desc(b_st + (kb * 2 + 0) * plane_bytes, 128, 256);
+          const uint64_t bl = smem_desc(b_st + (kb * 2 + 1) * plane_bytes, 128, 256);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint32_t d = tmem_base + h * twoC;
+            const uint64_t ah = smem_desc(a_st + ((kb * 2 + 0) * 2 + h) * kVHalfBytes, 128, 256);
+            const uint64_t al = smem_desc(a_st + ((kb * 2 + 1) * 2 + h) * kVHalfBytes, 128, 256);
+            mma_bf16(d, ah, bh, idesc, first ? 0u : 1u);
+            mma_bf16(d, ah, bl, idesc, 1u);
+            mma_bf16(d, al, bh, idesc, 1u);
+          }
+          first = false;
+        }
+        mma_commit(&empty[st]);
+      }
+      mma_commit(accfull);
+    }
+  } else {
+    // ---------------- converters: Y (sum of the splits) -> BF16 hi/lo B operand ----------
+    const int ct = threadIdx.x - 64;
+    const int tasks = 4 * twoC;   // (column n, 8-row group g) pairs of a stage
+    constexpr int GS = 4 / TPT;   // column splits loaded together: 8 x 16 B in flight
+    for (int it = 0; it < nst; ++it) {
+      const int st = it % kVStages;
+      const uint32_t par = (it / kVStages) & 1;
+      const bool ok = wait_or_abort(&empty[st], par ^ 1, abort_flag, status);
+      const int64_t r0 = r_begin + (int64_t)it * kVRows;
+      unsigned char* b_st = smem + L.b_off + st * L.b_stage;
+      float y[TPT][8];
+#pragma unroll
+      for (int q = 0; q < TPT; ++q)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) y[q][k] = 0.f;
+      // Y of this thread's tasks, summed over the column splits in order; lanes take
+      // consecutive columns, rows r0 + 8 g .. + 7 (< n_pad: stages end by round_up(n, 32))
+      for (int s0 = 0; ok && s0 < slices; s0 += GS) {
+        float4 u[GS][TPT][2];
+#pragma unroll
+        for (int g2 = 0; g2 < GS; ++g2)
+#pragma unroll
+          for (int q = 0; q < TPT; ++q) {
+            const int t = ct + q * kVConvThreads;
+            u[g2][q][0] = u[g2][q][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (s0 + g2 < slices && t < tasks) {
+              const int nn = t % twoC, g = t / twoC;
+              const float* src =
+                  Yp + (((size_t)(s0 + g2) * N + j) * (size_t)twoC + nn) * (size_t)n_pad + r0 +
+                  8 * g;
+              u[g2][q][0] = *reinterpret_cast<const float4*>(src);
+              u[g2][q][1] = *reinterpret_cast<const float4*>(src + 4);
+            }
+          }
+#pragma unroll
+        for (int g2 = 0; g2 < GS; ++g2)
+#pragma unroll
+          for (int q = 0; q < TPT; ++q) {
+            y[q][0] += u[g2][q][0].x; y[q][1] += u[g2][q][0].y;
+            y[q][2] += u[g2][q][0].z; y[q][3] += u[g2][q][0].w;
+            y[q][4] += u[g2][q][1].x; y[q][5] += u[g2][q][1].y;
+            y[q][6] += u[g2][q][1].z; y[q][7] += u[g2][q][1].w;
+          }
+      }
+#pragma unroll
+      for (int q = 0; q < TPT; ++q) {
+        const int t = ct + q * kVConvThreads;
+        if (!ok || t >= tasks) continue;
+        const int nn = t % twoC, g = t / twoC;
+        if (r0 + 8 * g >= r_end) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) y[q][k] = 0.f;
+        }
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          hi[k] = pack_bf16(y[q][2 * k], y[q][2 * k + 1]);
+          lo[k] = pack_bf16(y[q][2 * k] - __uint_as_float(hi[k] << 16),
+                            y[q][2 * k + 1] - __uint_as_float(hi[k] & 0xFFFF0000u));
+        }
+        const int kb = g / 2, kh = g % 2;
+        const uint32_t off = (uint32_t)(nn / 8) * 256 + kh * 128 + (nn % 8) * 16;
+        *reinterpret_cast<uint4*>(b_st + (kb * 2 + 0) * plane_bytes + off) =
+            make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(b_st + (kb * 2 + 1) * plane_bytes + off) =
+            make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      }
+      fence_proxy_async_smem();
+      mbar_arrive(&bfull[st]);
+      if (!ok) break;
+    }
+    // ---------------- epilogue: TMEM -> FP64 partial ----------------
+    const bool ok = !*abort_flag && wait_or_abort(accfull, 0, abort_flag, status);
+    const int quarter = warp % 4;
+    const int a = quarter * 32 + lane;
+    if (__all_sync(0xffffffffu, ok) && quarter * 32 < C) {
+      tc_fence_after();
+      const int side = (warp - 2) / 4;   // two warps per lane quarter split the columns
+      const uint32_t lane_addr = tmem_base + ((uint32_t)(quarter * 32) << 16);
+      double2* P = reinterpret_cast<double2*>(part) + ((int64_t)blockIdx.y * N + j) * nu * nu;
+      for (int b0 = 16 * side; b0 < C; b0 += 32) {
+        float d0r[16], d0i[16], d1r[16], d1i[16];
+        tmem_ld16(lane_addr + b0, d0r);                // Vr^T Yr
+        tmem_ld16(lane_addr + C + b0, d0i);            // Vr^T Yi
+        tmem_ld16(lane_addr + twoC + b0, d1r);         // Vi^T Yr
+        tmem_ld16(lane_addr + twoC + C + b0, d1i);     // Vi^T Yi
+        if (a < nu) {
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const int b = b0 + k;
+            if (b < nu)
+              P[(int64_t)b * nu + a] = make_double2((double)d0r[k] + (double)d1i[k],
+                                                    (double)d0i[k] - (double)d1r[k]);
+          }
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    if (lane == 0) mbar_wait(accfull, 0, kWaitLimit);
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem_base, L.tmem_cols);
+  }
+}
+
 // Bhat_j = w_j sum_r P_r,j (parts added in order: deterministic).
 __global__ void mixed_vhy_reduce_kernel(const double* __restrict__ part, int parts, int N, int nu,
                                         const double* __restrict__ w, double* __restrict__ Bhat) {
@@ -750,6 +1063,7 @@ struct MixedPlan {
                               // near-field correction when it is active
   int vtiles = 0;
   int64_t vparts = 0, rows_per_vpart = 0;
+  bool vhy_tc = false;        // V^H Y on the tensor core (one column chunk)
   const double* V = nullptr;
   int64_t ldv = 0;
   float2* V32 = nullptr;
@@ -799,6 +1113,17 @@ bem_status mixed_plan(bem_ctx* ctx, const double* V, int64_t ldv, int nu, int S,
                                                               ((int64_t)plan.vtiles * N)));
   plan.rows_per_vpart = ((n + vparts - 1) / vparts + kTR - 1) / kTR * kTR;
   plan.vparts = (n + plan.rows_per_vpart - 1) / plan.rows_per_vpart;
+  plan.vhy_tc = p.nchunks == 1;
+  if (plan.vhy_tc) {
+    // one wave of (node, row part) CTAs, 32-row stages
+    // two CTAs per SM when their shared memory and TMEM columns both fit twice
+    const VhyLayout VL = vhy_layout(p.C);
+    const int per_sm = (VL.total <= 110 * 1024 && VL.tmem_cols <= 256) ? 2 : 1;
+    const int64_t slots = (int64_t)std::max(1, sms) * per_sm;
+    const int64_t tparts = std::max<int64_t>(1, slots / N);
+    plan.rows_per_vpart = ((n + tparts - 1) / tparts + kVRows - 1) / kVRows * kVRows;
+    plan.vparts = (n + plan.rows_per_vpart - 1) / plan.rows_per_vpart;
+  }
   const size_t v32_off = (yp_off + yp_bytes + 255) / 256 * 256;
   const size_t v32_bytes = (size_t)n * nu * sizeof(float2);
   const size_t vp_off = (v32_off + v32_bytes + 255) / 256 * 256;
@@ -840,9 +1165,17 @@ void mixed_pre(bem_ctx* ctx, const MixedPlan& plan, cudaStream_t s) {
 void mixed_post(bem_ctx* ctx, const MixedPlan& plan, double* Bhat, double* AV, cudaStream_t s) {
   const MixedParams& p = plan.p;
   const int acc_cols = 2 * p.nup;
-  mixed_vhy_part_kernel<<<dim3((unsigned)plan.vtiles, (unsigned)p.N, (unsigned)plan.vparts), 256,
-                          0, s>>>(plan.V32, p.nu, p.n, p.n_pad, p.N, plan.slices, acc_cols, p.C,
-                                  p.Yp, plan.rows_per_vpart, plan.vpart);
+  if (plan.vhy_tc) {
+    const dim3 grid((unsigned)p.N, (unsigned)plan.vparts);
+    const uint32_t sm = vhy_layout(p.C).total;
+    auto* kern = p.C <= 32 ? mixed_vhy_tc_kernel<1>
+                           : (p.C <= 64 ? mixed_vhy_tc_kernel<2> : mixed_vhy_tc_kernel<4>);
+    kern<<<grid, kVThreads, sm, s>>>(plan.Bp, p.Yp, p.n, p.n_pad, p.nu, p.C, p.N, p.nK,
+                                     plan.slices, plan.rows_per_vpart, plan.vpart, p.status);
+  } else
+    mixed_vhy_part_kernel<<<dim3((unsigned)plan.vtiles, (unsigned)p.N, (unsigned)plan.vparts),
+                            256, 0, s>>>(plan.V32, p.nu, p.n, p.n_pad, p.N, plan.slices, acc_cols,
+                                         p.C, p.Yp, plan.rows_per_vpart, plan.vpart);
   const int64_t outs = (int64_t)p.N * p.nu * p.nu;
   mixed_vhy_reduce_kernel<<<(unsigned)((outs + 255) / 256), 256, 0, s>>>(
       plan.vpart, (int)plan.vparts, p.N, p.nu, ctx->con.w, Bhat);
@@ -862,13 +1195,190 @@ bem_status set_mixed_smem(bem_ctx* ctx, uint32_t bytes) {
                                                        (int)bytes),
                              "mixed kernel attribute");
   if (st != BEM_OK) return st;
+  for (const void* f : {(const void*)mixed_vhy_tc_kernel<1>, (const void*)mixed_vhy_tc_kernel<2>,
+                        (const void*)mixed_vhy_tc_kernel<4>}) {
+    st = cuda_check(ctx, cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)vhy_layout(128).total),
+                    "mixed kernel attribute");
+    if (st != BEM_OK) return st;
+  }
   return cuda_check(ctx, cudaFuncSetAttribute(mixed_apply_grouped_kernel,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)bytes),
                     "mixed kernel attribute");
 }
 
+// ---------------------------------------------------------------------------------------
+// Node-summed form of the fused kernel (Algorithm 1, Eq. linsyssim): Y = sum_j c_j A(z_j) X_j
+// with one X_j per node (the right-hand side b of an inverse power step) or one X for all
+// nodes (the Schur complement S = sum_j c_j A(z_j) applied to X). Same evaluation and
+// BF16x3 tcgen05 contraction as the projection; the G nodes of a unit accumulate into one
+// TMEM accumulator, the units of node group gg and split write slice gg S + split, and the
+// slices are summed in a fixed order.
+
+// X (FP32 complex, column-major with leading dimension ldx, node blocks node_stride apart)
+// -> BF16 hi/lo basis planes, one set of nK * 256 * nup bytes per node.
+__global__ void prep_planes32_kernel(const float2* __restrict__ X, int64_t ldx,
+                                     int64_t node_stride, int64_t n, int nu, int nup, int C,
+                                     int nK, int nnodes, __nv_bfloat16* __restrict__ Bp) {
+  const int64_t rows = (int64_t)nK * kBK;
+  const int64_t per = rows * nup;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= per * nnodes) return;
+  const int node = (int)(t / per);
+  const int64_t l = (t % per) % rows;
+  const int col = (int)((t % per) / rows);
+  float vr = 0.f, vi = 0.f;
+  if (l < n && col < nu) {
+    const float2 v = X[node * node_stride + (int64_t)col * ldx + l];
+    vr = v.x;
+    vi = v.y;
+  }
+  const __nv_bfloat16 vr_hi = __float2bfloat16(vr), vi_hi = __float2bfloat16(vi);
+  const __nv_bfloat16 vr_lo = __float2bfloat16(vr - __bfloat162float(vr_hi));
+  const __nv_bfloat16 vi_lo = __float2bfloat16(vi - __bfloat162float(vi_hi));
+  const __nv_bfloat16 vals[4][2] = {{vr_hi, vi_hi}, {vr_lo, vi_lo}, {__hneg(vi_hi), vr_hi},
+                                    {__hneg(vi_lo), vr_lo}};
+  const int kb = (int)(l / kBK), kin = (int)(l % kBK);
+  const int kg = kin / 8, k8 = kin % 8;
+  const int c = col / C, rc = col % C;
+  const int nchunks = nup / C, ngroups = 2 * C / 8;
+  __nv_bfloat16* B = Bp + (size_t)node * (size_t)nK * 128 * nup;
+#pragma unroll
+  for (int pl = 0; pl < 4; ++pl)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int rowN = h * C + rc;
+      const int64_t idx =
+          (((((int64_t)kb * nchunks + c) * 4 + pl) * ngroups + rowN / 8) * 2 + kg) * 64 +
+          (rowN % 8) * 8 + k8;
+      B[idx] = vals[pl][h];
+    }
+}
+
+// out (FP32 complex, n x nu, leading dimension n) = sum over the slices, in slice order
+__global__ void sum_slices_kernel(const float* __restrict__ Yp, int slices, int acc_cols, int C,
+                                  int64_t n, int n_pad, int nu, float2* __restrict__ out) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * nu) return;
+  const int64_t i = t % n;
+  const int c = (int)(t / n);
+  const int colr = (c / C) * 2 * C + c % C;
+  float re = 0.f, im = 0.f;
+  for (int sl = 0; sl < slices; ++sl) {
+    const float* base = Yp + (size_t)sl * acc_cols * n_pad;
+    re += base[(size_t)colr * n_pad + i];
+    im += base[(size_t)(colr + C) * n_pad + i];
+  }
+  out[t] = make_float2(re, im);
+}
+
+constexpr uint32_t kSmemMax = 227 * 1024;
+
+struct SumPlan {
+  MixedParams p{};
+  int64_t units = 0;
+  int slices = 0;
+  int nnodes = 1;            // basis plane sets (N with one X per node)
+  SmemLayout L{};
+  size_t bp_off = 0, yp_off = 0, cf_off = 0, bytes = 0;
+};
+
+SumPlan sum_plan(bem_ctx* ctx, int nu, bool per_node) {
+  SumPlan plan;
+  MixedParams& p = plan.p;
+  const int64_t n = ctx->geo.n;
+  const int N = ctx->con.N;
+  p.n = n;
+  p.N = N;
+  p.nu = nu;
+  p.nup = (nu + 7) / 8 * 8;
+  p.C = p.nup <= 128 ? p.nup : 128;
+  if (p.nup % p.C != 0) p.nup = (p.nup + p.C - 1) / p.C * p.C;
+  p.nchunks = p.nup / p.C;
+  // nodes per unit: 4, else 2, else 1 (even counts keep twin pairs together), within the
+  // shared memory (per-node basis planes take a set per node and stage)
+  int G = std::min(N, kMaxG);
+  while (G > 1 && smem_layout(G, p.nup, per_node ? G : 1).total > kSmemMax) G = G > 2 ? 2 : 1;
+  p.G = G;
+  p.nG = (N + G - 1) / G;
+  p.nK = (int)((n + kBK - 1) / kBK);
+  p.n_pad = (int)((n + kBM - 1) / kBM * kBM);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  const int64_t rtiles = p.n_pad / kBM;
+  // units: row tiles x column splits, and chunks of node groups only when those are too few
+  // to fill the device (every chunk and split is a slice of FP32 partials)
+  sms = std::max(1, sms);
+  int64_t ngc = 1;
+  p.S = choose_splits(rtiles, p.nK, sms);
+  if (rtiles * p.S < sms) {
+    ngc = std::min<int64_t>(p.nG, (sms + rtiles * p.S - 1) / (rtiles * p.S));
+    p.S = choose_splits(rtiles * ngc, p.nK, sms);
+  }
+  p.gchunk = (int)((p.nG + ngc - 1) / ngc);
+  p.ngc = (p.nG + p.gchunk - 1) / p.gchunk;
+  plan.units = rtiles * p.ngc * p.S;
+  plan.slices = p.ngc * p.S;
+  plan.nnodes = per_node ? N : 1;
+  p.sum = 1;
+  const size_t set_bytes = (size_t)p.nK * 256 * p.nup;
+  p.b_node_stride = per_node ? (int64_t)set_bytes : 0;
+  plan.bp_off = 0;
+  plan.yp_off = (plan.nnodes * set_bytes + 255) / 256 * 256;
+  plan.cf_off = plan.yp_off +
+                ((size_t)plan.slices * 2 * p.nup * p.n_pad * sizeof(float) + 255) / 256 * 256;
+  plan.bytes = plan.cf_off + (size_t)N * sizeof(float2);
+  plan.L = smem_layout(G, p.nup, per_node ? G : 1);
+  return plan;
+}
+
 }  // namespace
+
+size_t mixed_sum_work_bytes(bem_ctx* ctx, int nu, bool per_node) {
+  return sum_plan(ctx, nu, per_node).bytes;
+}
+
+bem_status mixed_sum_apply(bem_ctx* ctx, const float2* X, int64_t ldx, int64_t node_stride,
+                           bool per_node, int nu, const double* coef_host, float2* out,
+                           void* work, cudaStream_t s) {
+  SumPlan plan = sum_plan(ctx, nu, per_node);
+  MixedParams& p = plan.p;
+  unsigned char* w = reinterpret_cast<unsigned char*>(work);
+  __nv_bfloat16* Bp = reinterpret_cast<__nv_bfloat16*>(w + plan.bp_off);
+  p.Bp = Bp;
+  p.Yp = reinterpret_cast<float*>(w + plan.yp_off);
+  float2* cf = reinterpret_cast<float2*>(w + plan.cf_off);
+  p.coef = cf;
+  p.cx = ctx->geo.cx;
+  p.qp = ctx->geo.qp;
+  p.qw = ctx->geo.qw;
+  p.pack32 = ctx->geo.pack32;
+  p.z = ctx->con.z;
+  p.order = ctx->con.order;
+  p.status = ctx->d_status;
+  bem_status st = ensure_self32(ctx, s);
+  if (st != BEM_OK) return st;
+  p.self32 = reinterpret_cast<const float2*>(ctx->con.self32);
+  std::vector<float2> ch(p.N);
+  for (int j = 0; j < p.N; ++j) ch[j] = make_float2((float)coef_host[2 * j], (float)coef_host[2 * j + 1]);
+  st = cuda_check(ctx, cudaMemcpyAsync(cf, ch.data(), p.N * sizeof(float2), cudaMemcpyHostToDevice, s),
+                  "coefficient copy");
+  if (st != BEM_OK) return st;
+  const int64_t prep = (int64_t)plan.nnodes * p.nK * kBK * p.nup;
+  prep_planes32_kernel<<<(unsigned)((prep + 255) / 256), 256, 0, s>>>(
+      X, ldx, node_stride, p.n, nu, p.nup, p.C, p.nK, plan.nnodes, Bp);
+  st = cuda_check(ctx, cudaFuncSetAttribute(mixed_sum_kernel,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)plan.L.total),
+                  "mixed kernel attribute");
+  if (st != BEM_OK) return st;
+  mixed_sum_kernel<<<(unsigned)plan.units, kThreads, plan.L.total, s>>>(p);
+  sum_slices_kernel<<<(unsigned)((p.n * nu + 255) / 256), 256, 0, s>>>(
+      p.Yp, plan.slices, 2 * p.nup, p.C, p.n, p.n_pad, nu, out);
+  ctx->launches += 3;
+  return cuda_check(ctx, cudaGetLastError(), "node-summed apply");
+}
 
 bem_status project_mixed(bem_ctx* ctx, const double* V, int64_t ldv, int nu, double* Bhat,
                          double* AV, cudaStream_t s) {

@@ -6,7 +6,8 @@
 //   v_j' = (v_j - u') / (z_j - s),
 // for every basis column at once, q times, from v_j = u / (z_j - s). S is assembled densely
 // (FP32) and factorised once (blocked LU); the right-hand side is applied matrix-free by
-// apply_nodes32_kernel. The iterates are rescaled column by column (direction only).
+// the node-summed fused kernel (FP32 evaluation, BF16x3 tcgen05 contraction). The iterates
+// are rescaled column by column (direction only).
 //
 // Refinement: for an approximate eigenpair (lambda, x) of A(k) x = 0, residual inverse
 // iteration with a frozen factorisation of A(sigma) (Neumaier 1985) and a Newton step for
@@ -19,137 +20,13 @@
 #include <math.h>
 
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "internal.h"
 
 namespace bem {
 namespace {
-
-constexpr float kLog2eF = 1.4426950408889634f;
-constexpr float kInv2PiF = 0.15915494309189535f;
-constexpr float kTwoPiHiF = 6.28318548202514648f;
-constexpr float kTwoPiLoF = -1.7484555314695172e-7f;
-
-__device__ __forceinline__ float fex2(float x) {
-  float r;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-__device__ __forceinline__ float fsin(float x) {
-  float r;
-  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-__device__ __forceinline__ float fcos(float x) {
-  float r;
-  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-
-constexpr int kAR = 64;   // rows per block
-constexpr int kAC = 32;   // columns of A per panel
-constexpr int kAV = 64;   // basis columns per block
-
-struct NodeList {
-  int N;
-  float kr[kMaxNodesSolve], kmi[kMaxNodesSolve], cr[kMaxNodesSolve], ci[kMaxNodesSolve];
-};
-
-// out[:, c] = sum_j c_j A(z_j) Vn_j[:, c], Vn node-major (N x n x nu, FP32 complex,
-// column-major per node), out n x nu FP32 complex. Self terms from the FP32 table.
-__global__ void __launch_bounds__(256)
-apply_nodes32_kernel(Geometry g, NodeList nl, const float2* __restrict__ self32,
-                     const float2* __restrict__ Vn, int nu, float2* __restrict__ out) {
-  __shared__ float2 sA[kAR][kAC + 1];
-  __shared__ float2 sV[kAC][kAV];
-  __shared__ float sQ[4][7][kAC];
-  __shared__ float sC[3][kAR];
-  const int64_t n = g.n;
-  const int tid = threadIdx.x;
-  const int64_t row0 = (int64_t)blockIdx.x * kAR;
-  const int col0 = blockIdx.y * kAV;
-  if (tid < kAR) {
-    const int64_t i = row0 + tid;
-    for (int c = 0; c < 3; ++c) sC[c][tid] = i < n ? g.cx32[c * n + i] : 0.f;
-  }
-  const int gr = tid / 4;          // output row
-  const int gc0 = tid % 4;         // output columns gc0 + 4 m, m < 16
-  float2 acc[16];
-#pragma unroll
-  for (int m = 0; m < 16; ++m) acc[m] = make_float2(0.f, 0.f);
-  const int el = tid % kAC, er0 = tid / kAC;   // evaluation: column el, rows er0 + 8 m
-  for (int64_t l0 = 0; l0 < n; l0 += kAC) {
-    __syncthreads();
-    for (int t = tid; t < 7 * kAC; t += 256) {
-      const int q = t / kAC, lc = t % kAC;
-      const int64_t l = l0 + lc;
-      const bool ok = l < n;
-      sQ[0][q][lc] = ok ? g.qp32[q * n + l] : 1e3f;
-      sQ[1][q][lc] = ok ? g.qp32[(7 + q) * n + l] : 1e3f;
-      sQ[2][q][lc] = ok ? g.qp32[(14 + q) * n + l] : 1e3f;
-      sQ[3][q][lc] = ok ? g.qw32[q * n + l] : 0.f;
-    }
-    __syncthreads();
-    for (int j = 0; j < nl.N; ++j) {
-      // entries of c_j A(z_j) for this 64 x 32 panel
-      const int64_t l = l0 + el;
-      for (int m = 0; m < kAR / 8; ++m) {
-        const int rr = er0 + 8 * m;
-        const int64_t i = row0 + rr;
-        float sr = 0.f, si = 0.f;
-        if (i < n && l < n) {
-          if (i == l) {
-            const float2 v = self32[(int64_t)j * n + l];
-            sr = v.x;
-            si = v.y;
-          } else {
-#pragma unroll
-            for (int q = 0; q < 7; ++q) {
-              const float dx = sC[0][rr] - sQ[0][q][el], dy = sC[1][rr] - sQ[1][q][el],
-                          dz = sC[2][rr] - sQ[2][q][el];
-              const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-              const float rs = rsqrtf(r2);
-              const float r = r2 * rs;
-              const float a = sQ[3][q][el] * rs * fex2(nl.kmi[j] * r);
-              const float ph = nl.kr[j] * r;
-              const float nrot = fmaf(ph, kInv2PiF, 12582912.0f) - 12582912.0f;
-              const float red = fmaf(-nrot, kTwoPiLoF, fmaf(-nrot, kTwoPiHiF, ph));
-              sr = fmaf(a, fcos(red), sr);
-              si = fmaf(a, fsin(red), si);
-            }
-          }
-        }
-        sA[rr][el] = make_float2(nl.cr[j] * sr - nl.ci[j] * si, nl.cr[j] * si + nl.ci[j] * sr);
-      }
-      const float2* Vj = Vn + (int64_t)j * n * nu;
-      for (int t = tid; t < kAC * kAV; t += 256) {
-        const int k = t / kAV, c = t % kAV;
-        const int64_t ll = l0 + k;
-        sV[k][c] = (ll < n && col0 + c < nu) ? Vj[(int64_t)(col0 + c) * n + ll] : make_float2(0.f, 0.f);
-      }
-      __syncthreads();
-#pragma unroll 4
-      for (int k = 0; k < kAC; ++k) {
-        const float2 a = sA[gr][k];
-#pragma unroll
-        for (int m = 0; m < 16; ++m) {
-          const float2 v = sV[k][gc0 + 4 * m];
-          acc[m].x = fmaf(a.x, v.x, fmaf(-a.y, v.y, acc[m].x));
-          acc[m].y = fmaf(a.x, v.y, fmaf(a.y, v.x, acc[m].y));
-        }
-      }
-      __syncthreads();
-    }
-  }
-  const int64_t i = row0 + gr;
-  if (i < n)
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      const int c = col0 + gc0 + 4 * m;
-      if (c < nu) out[(int64_t)c * n + i] = acc[m];
-    }
-}
 
 // Vn_j = u / (z_j - s) (u FP64 n x nu, ld ldu)
 __global__ void ip_start_kernel(const double2* __restrict__ U, int64_t ldu, int64_t n, int nu,
@@ -228,6 +105,18 @@ __global__ void f32_to_f64_kernel(const float2* __restrict__ a, int64_t n, int m
 // ---- refinement helpers (one eigenpair: vectors of length n) ----
 
 // [r r'] (FP64, n x 2 contiguous) -> FP32
+// node blocks of X (FP64, leading dimension ldx, node_stride elements apart) -> FP32,
+// node-major with leading dimension n
+__global__ void x_to_f32_kernel(const double2* __restrict__ X, int64_t ldx, int64_t node_stride,
+                                int64_t n, int nu, int nnodes, float2* __restrict__ X32) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per = n * nu;
+  if (t >= per * nnodes) return;
+  const int64_t node = t / per, i = (t % per) % n, c = (t % per) / n;
+  const double2 v = X[node * node_stride + c * ldx + i];
+  X32[t] = make_float2((float)v.x, (float)v.y);
+}
+
 __global__ void to_f32_kernel(const double2* __restrict__ a, int64_t count, float2* b) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t < count) b[t] = make_float2((float)a[t].x, (float)a[t].y);
@@ -305,39 +194,49 @@ unsigned nblk(int64_t count, int t = 256) { return (unsigned)((count + t - 1) / 
 
 using namespace bem;
 
-extern "C" bem_status bem_inverse_power(bem_ctx* ctx, double* V_dev, int64_t ldv, int nu, int q,
-                                        double shift_re, double shift_im, void* stream) {
+namespace bem {
+namespace {
+
+// q steps of Algorithm 1 on every column of V. mf = false: S assembled densely in FP32 and
+// LU-factorised once; mf = true: S applied matrix-free, each solve by restarted GMRES to
+// the relative residual tol (at most max_iter Arnoldi steps per solve).
+bem_status inverse_power_impl(bem_ctx* ctx, double* V_dev, int64_t ldv, int nu, int q,
+                              double shift_re, double shift_im, bool mf, double tol,
+                              int max_iter, int* gmres_iters, const char* name, cudaStream_t s) {
   if (!ctx) return BEM_EINVAL;
   if (ctx->geo.n == 0 || ctx->con.N == 0)
-    return fail(ctx, BEM_ESTATE, "bem_inverse_power: mesh and contour must be set");
+    return fail(ctx, BEM_ESTATE, std::string(name) + ": mesh and contour must be set");
   const int64_t n = ctx->geo.n;
   const int N = ctx->con.N;
-  if (!V_dev || nu < 1 || nu > kMaxNu || ldv < n || q < 0 || N > kMaxNodesSolve)
-    return fail(ctx, BEM_EINVAL, "bem_inverse_power: need V, 1 <= nu <= 256, ldv >= n, N <= 64");
+  if (!V_dev || nu < 1 || nu > kMaxNu || ldv < n || q < 0 || N > kMaxNodesSolve ||
+      (mf && (!(tol > 0.0) || max_iter < 1)))
+    return fail(ctx, BEM_EINVAL, std::string(name) +
+                                     ": need V, 1 <= nu <= 256, ldv >= n, N <= 64 (and tol > 0, "
+                                     "max_iter >= 1 without a factorisation)");
+  if (gmres_iters) *gmres_iters = 0;
   if (q == 0) return BEM_OK;
   cudaSetDevice(ctx->device);
-  cudaStream_t s = (cudaStream_t)stream;
   // coefficients c_j = w_j / (z_j - s)
   std::vector<double> coef(2 * N);
-  NodeList nl;
-  nl.N = N;
   for (int j = 0; j < N; ++j) {
     const double zr = ctx->con.z_host[2 * j] - shift_re, zi = ctx->con.z_host[2 * j + 1] - shift_im;
     const double wr = ctx->con.w_host[2 * j], wi = ctx->con.w_host[2 * j + 1];
     const double d = zr * zr + zi * zi;
     coef[2 * j] = (wr * zr + wi * zi) / d;
     coef[2 * j + 1] = (wi * zr - wr * zi) / d;
-    nl.kr[j] = (float)ctx->con.z_host[2 * j];
-    nl.kmi[j] = (float)(-ctx->con.z_host[2 * j + 1]) * kLog2eF;
-    nl.cr[j] = (float)coef[2 * j];
-    nl.ci[j] = (float)coef[2 * j + 1];
   }
-  // workspace: S (n^2), pivots, Vn (N n nu), U' (n nu), norms
+  const int restart = 40;
+  // workspace: S (n^2) and pivots, or the GMRES basis; Vn (N n nu), u' (n nu), b (n nu),
+  // norms, node-summed apply
   size_t off = 0;
   auto take = [&](size_t b) { const size_t o = off; off += (b + 255) / 256 * 256; return o; };
-  const size_t oS = take((size_t)n * n * sizeof(float2)), oP = take((size_t)n * sizeof(int)),
+  const size_t oS = take(mf ? 0 : (size_t)n * n * sizeof(float2)),
+               oP = take(mf ? 0 : (size_t)n * sizeof(int)),
+               oG = take(mf ? gmres_sum_work_bytes(ctx, nu, restart) : 0),
                oV = take((size_t)N * n * nu * sizeof(float2)), oU = take((size_t)n * nu * sizeof(float2)),
-               oN = take((size_t)nu * sizeof(double));
+               oB = take(mf ? (size_t)n * nu * sizeof(float2) : 0),
+               oN = take((size_t)nu * sizeof(double)),
+               oW = take(mixed_sum_work_bytes(ctx, nu, true));
   bem_status st = ensure_scratch(ctx, off);
   if (st != BEM_OK) return st;
   st = ensure_self32(ctx, s);
@@ -347,10 +246,14 @@ extern "C" bem_status bem_inverse_power(bem_ctx* ctx, double* V_dev, int64_t ldv
   int* piv = reinterpret_cast<int*>(base + oP);
   float2* Vn = reinterpret_cast<float2*>(base + oV);
   float2* Up = reinterpret_cast<float2*>(base + oU);
+  float2* Bt = reinterpret_cast<float2*>(base + oB);
   double* nrm = reinterpret_cast<double*>(base + oN);
-  st = assemble32(ctx, N, ctx->con.z_host, coef.data(), S, s);
-  if (st == BEM_OK) st = lu32(ctx, S, n, piv, s);
-  if (st != BEM_OK) return st;
+  void* sum_work = base + oW;
+  if (!mf) {
+    st = assemble32(ctx, N, ctx->con.z_host, coef.data(), S, s);
+    if (st == BEM_OK) st = lu32(ctx, S, n, piv, s);
+    if (st != BEM_OK) return st;
+  }
   const double2 sh = make_double2(shift_re, shift_im);
   const double2* z = reinterpret_cast<const double2*>(ctx->con.z);
   const int64_t total = (int64_t)N * n * nu;
@@ -358,12 +261,17 @@ extern "C" bem_status bem_inverse_power(bem_ctx* ctx, double* V_dev, int64_t ldv
                                               N, z, sh, Vn);
   ctx->launches++;
   for (int step = 0; step < q; ++step) {
-    dim3 grid((unsigned)((n + kAR - 1) / kAR), (unsigned)((nu + kAV - 1) / kAV));
-    apply_nodes32_kernel<<<grid, 256, 0, s>>>(ctx->geo, nl,
-                                              reinterpret_cast<const float2*>(ctx->con.self32),
-                                              Vn, nu, Up);
-    ctx->launches++;
-    st = lu32_solve(ctx, S, piv, n, Up, nu, s);
+    // b = sum_j c_j A(z_j) v_j (Eq. linsyssim with the sign of Algorithm 1 absorbed in c_j)
+    st = mixed_sum_apply(ctx, Vn, n, n * nu, true, nu, coef.data(), mf ? Bt : Up, sum_work, s);
+    if (st != BEM_OK) return st;
+    if (mf) {
+      int it = 0;
+      st = gmres_sum32(ctx, coef.data(), Bt, Up, nu, tol, max_iter, restart, base + oG, s, &it,
+                       nullptr);
+      if (gmres_iters) *gmres_iters += it;
+    } else {
+      st = lu32_solve(ctx, S, piv, n, Up, nu, s);
+    }
     if (st != BEM_OK) return st;
     ip_update_kernel<<<nblk(total), 256, 0, s>>>(Vn, Up, n, nu, N, z, sh);
     ip_colnorm_kernel<<<nu, 256, 0, s>>>(Vn, n, nu, N, nrm);
@@ -372,9 +280,100 @@ extern "C" bem_status bem_inverse_power(bem_ctx* ctx, double* V_dev, int64_t ldv
   }
   f32_to_f64_kernel<<<nblk(n * nu), 256, 0, s>>>(Up, n, nu, reinterpret_cast<double2*>(V_dev), ldv);
   ctx->launches++;
-  st = cuda_check(ctx, cudaGetLastError(), "bem_inverse_power");
+  st = cuda_check(ctx, cudaGetLastError(), name);
   if (st != BEM_OK) return st;
-  return take_status(ctx, s, "bem_inverse_power");
+  return take_status(ctx, s, name);
+}
+
+}  // namespace
+}  // namespace bem
+
+extern "C" bem_status bem_inverse_power(bem_ctx* ctx, double* V_dev, int64_t ldv, int nu, int q,
+                                        double shift_re, double shift_im, void* stream) {
+  return inverse_power_impl(ctx, V_dev, ldv, nu, q, shift_re, shift_im, false, 0.0, 0, nullptr,
+                            "bem_inverse_power", (cudaStream_t)stream);
+}
+
+extern "C" bem_status bem_inverse_power_mf(bem_ctx* ctx, double* V_dev, int64_t ldv, int nu,
+                                           int q, double shift_re, double shift_im, double tol,
+                                           int max_iter, int* gmres_iters, void* stream) {
+  return inverse_power_impl(ctx, V_dev, ldv, nu, q, shift_re, shift_im, true, tol, max_iter,
+                            gmres_iters, "bem_inverse_power_mf", (cudaStream_t)stream);
+}
+
+extern "C" bem_status bem_solve_sum(bem_ctx* ctx, const double* coef_host, const double* B_dev,
+                                    int64_t ldb, int nu, double tol, int max_iter,
+                                    double* X_dev, int64_t ldx, int* iters, double* relres_host,
+                                    void* stream) {
+  if (!ctx) return BEM_EINVAL;
+  if (ctx->geo.n == 0 || ctx->con.N == 0)
+    return fail(ctx, BEM_ESTATE, "bem_solve_sum: mesh and contour must be set");
+  const int64_t n = ctx->geo.n;
+  if (!coef_host || !B_dev || !X_dev || nu < 1 || nu > kMaxNu || ldb < n || ldx < n ||
+      !(tol > 0.0) || max_iter < 1)
+    return fail(ctx, BEM_EINVAL,
+                "bem_solve_sum: need coefficients, B, X, 1 <= nu <= 256, ldb, ldx >= n, tol > 0, "
+                "max_iter >= 1");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int restart = 40;
+  size_t off = 0;
+  auto take = [&](size_t b) { const size_t o = off; off += (b + 255) / 256 * 256; return o; };
+  const size_t oB = take((size_t)n * nu * sizeof(float2)), oX = take((size_t)n * nu * sizeof(float2)),
+               oG = take(gmres_sum_work_bytes(ctx, nu, restart));
+  bem_status st = ensure_scratch(ctx, off);
+  if (st != BEM_OK) return st;
+  st = ensure_self32(ctx, s);
+  if (st != BEM_OK) return st;
+  unsigned char* base = reinterpret_cast<unsigned char*>(ctx->d_scratch);
+  float2* B32 = reinterpret_cast<float2*>(base + oB);
+  float2* X32 = reinterpret_cast<float2*>(base + oX);
+  x_to_f32_kernel<<<nblk(n * nu), 256, 0, s>>>(reinterpret_cast<const double2*>(B_dev), ldb, 0,
+                                               n, nu, 1, B32);
+  ctx->launches++;
+  st = gmres_sum32(ctx, coef_host, B32, X32, nu, tol, max_iter, restart, base + oG, s, iters,
+                   relres_host);
+  if (st != BEM_OK) return st;
+  f32_to_f64_kernel<<<nblk(n * nu), 256, 0, s>>>(X32, n, nu, reinterpret_cast<double2*>(X_dev), ldx);
+  ctx->launches++;
+  st = cuda_check(ctx, cudaGetLastError(), "bem_solve_sum");
+  if (st != BEM_OK) return st;
+  return take_status(ctx, s, "bem_solve_sum");
+}
+
+extern "C" bem_status bem_apply_sum(bem_ctx* ctx, const double* coef_host, const double* X_dev,
+                                    int64_t ldx, int nu, int per_node, double* Y_dev,
+                                    void* stream) {
+  if (!ctx) return BEM_EINVAL;
+  if (ctx->geo.n == 0 || ctx->con.N == 0)
+    return fail(ctx, BEM_ESTATE, "bem_apply_sum: mesh and contour must be set");
+  const int64_t n = ctx->geo.n;
+  const int N = ctx->con.N;
+  if (!coef_host || !X_dev || !Y_dev || nu < 1 || nu > kMaxNu || ldx < n)
+    return fail(ctx, BEM_EINVAL, "bem_apply_sum: need coefficients, X, Y, 1 <= nu <= 256, ldx >= n");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nn = per_node ? N : 1;
+  size_t off = 0;
+  auto take = [&](size_t b) { const size_t o = off; off += (b + 255) / 256 * 256; return o; };
+  const size_t oX = take((size_t)nn * n * nu * sizeof(float2)),
+               oY = take((size_t)n * nu * sizeof(float2)),
+               oW = take(mixed_sum_work_bytes(ctx, nu, per_node != 0));
+  bem_status st = ensure_scratch(ctx, off);
+  if (st != BEM_OK) return st;
+  unsigned char* base = reinterpret_cast<unsigned char*>(ctx->d_scratch);
+  float2* X32 = reinterpret_cast<float2*>(base + oX);
+  float2* Y32 = reinterpret_cast<float2*>(base + oY);
+  x_to_f32_kernel<<<nblk((int64_t)nn * n * nu), 256, 0, s>>>(
+      reinterpret_cast<const double2*>(X_dev), ldx, ldx * nu, n, nu, nn, X32);
+  ctx->launches++;
+  st = mixed_sum_apply(ctx, X32, n, n * nu, per_node != 0, nu, coef_host, Y32, base + oW, s);
+  if (st != BEM_OK) return st;
+  f32_to_f64_kernel<<<nblk(n * nu), 256, 0, s>>>(Y32, n, nu, reinterpret_cast<double2*>(Y_dev), n);
+  ctx->launches++;
+  st = cuda_check(ctx, cudaGetLastError(), "bem_apply_sum");
+  if (st != BEM_OK) return st;
+  return take_status(ctx, s, "bem_apply_sum");
 }
 
 extern "C" bem_status bem_refine(bem_ctx* ctx, int m, double* lam_host, double* X_dev,

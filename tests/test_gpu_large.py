@@ -10,8 +10,10 @@ and the FP32 accumulation over the K-blocks adds ~u32 sqrt(6 n / 16) relative to
 the terms' magnitudes. So every element must satisfy
 |Y_gpu - Y_oracle| <= (2^-15 + 4 u32 sqrt(6 n / 16)) * (|A(z_j)| |V|)_(i, c), the
 magnitudes taken from the oracle's rows of A(z_j) (a factor 2 of margin on each term).
-The projected matrices must equal w_j V^H (A(z_j) V) formed from the GPU's own full
-A(z_j) V in FP64 to 1e-5 (the contraction)."""
+The projected matrices are checked against w_j V^H (A(z_j) V) formed from the GPU's own
+full A(z_j) V in FP64 by the same kind of bound: the contraction runs in BF16x3 on the
+tensor core when nu <= 128 (3 products per 16-row K-block and half of the output), so
+|B_j - ref| <= |w_j| (2^-15 + 4 u32 sqrt(3 n / 16)) (|V|^T |A(z_j) V|) elementwise."""
 import numpy as np
 import pytest
 import torch
@@ -50,14 +52,17 @@ def test_large_workload_sampled_rows(bem, name):
     B, Y = ctx.project(Vd, bem.PREC_MIXED, AV=True)
     ctx.check()
     # the contraction: Bhat_j against w_j V^H Y_j in FP64 from the returned Y
+    u32 = 2.0 ** -24
+    cbound = 2.0 ** -15 + 4 * u32 * np.sqrt(3 * mesh.n / 16)
     for j in (0, prob.N // 2, prob.N - 1):
         ref = w[j] * (Vd.conj().transpose(0, 1) @ Y[j]).cpu().numpy()
-        assert _relerr(B[j].cpu().numpy(), ref) < 1e-5, j
+        mass = abs(w[j]) * (Vd.abs().transpose(0, 1) @ Y[j].abs()).cpu().numpy()
+        r = np.max(np.abs(B[j].cpu().numpy() - ref) / (cbound * mass))
+        assert r <= 1.0, (j, r, _relerr(B[j].cpu().numpy(), ref))
     # sampled rows against the oracle (near-field variant), all nodes
     rng = np.random.default_rng(7)
     R = 16   # rows per sample block (one oracle thread per row)
     starts = sorted(rng.choice(mesh.n - R, size=2, replace=False).tolist()) + [mesh.n - R]
-    u32 = 2.0 ** -24
     coef = 2.0 ** -15 + 4 * u32 * np.sqrt(6 * mesh.n / 16)
     absV = np.abs(V)
     worst = 0.0
