@@ -53,6 +53,9 @@ def parse():
                    choices=["cube3072", "sphere20480", "ellipsoid98304", "batch48"])
     p.add_argument("--near", type=int, default=None, choices=[0, 1, 2],
                    help="near-field mode (default: 1 for sphere20480 and ellipsoid98304, else 0)")
+    p.add_argument("--inverse-power", type=int, default=0, metavar="Q",
+                   help="instead of the projection bench: time Q steps of Algorithm 1 on the "
+                        "workload, dense (FP32 LU of S) against matrix-free (GMRES)")
     return p.parse_args()
 
 
@@ -398,6 +401,10 @@ def run_ours(args):
     B_host = torch.empty((N, nu, nu), dtype=torch.complex128).pin_memory()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
+    # asynchronous pipeline: the step makes no host synchronisation; the device status of
+    # the orthonormalisation is checked after the timed loops
+    ctx.set_async(True)
+
     def step(src):
         ctx.set_mesh(mesh.xyz, mesh.tri)
         ctx.set_contour(c.kind, c.centre, c.a, c.b, N)
@@ -453,6 +460,7 @@ def run_ours(args):
         e2e_ev[k][1].record(stream)
     barrier()
     e2e_total = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3
+    ctx.check()   # device status of every step (raises on a failure)
 
     # max over ranks
     if world > 1:
@@ -591,8 +599,58 @@ def run_ours(args):
     return 0
 
 
+def run_inverse_power(args):
+    """Algorithm 1 (q steps from a random basis, shift at the contour centre) with the dense
+    Schur complement (assembled in FP32, LU-factorised once) and matrix-free (each solve by
+    GMRES to relative residual 1e-4 with the fused kernel as the operator); one JSON line with
+    both times, the Arnoldi steps, the dense method's n^2 bytes and how far the two bases
+    differ in direction."""
+    import torch
+    import paper_1906_03938_gb300 as bem
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prob, mesh, V = problem(args.workload)
+    c = prob.contour
+    q = args.inverse_power
+    ctx = bem.Context(local)
+    ctx.set_mesh(mesh.xyz, mesh.tri)
+    ctx.set_contour(c.kind, c.centre, c.a, c.b, prob.N)
+    V0 = bem.fortran(torch.from_numpy(V).to(dev))
+    out = {}
+    for mode in ("dense", "matrix_free"):
+        Vw = bem.fortran(V0.clone())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if mode == "dense":
+            ctx.inverse_power(Vw, q, c.centre)
+            its = 0
+        else:
+            its = ctx.inverse_power_mf(Vw, q, c.centre, tol=1e-4, max_iter=2000)
+        torch.cuda.synchronize()
+        out[mode] = (time.perf_counter() - t0, its, Vw)
+    Ud, Um = out["dense"][2], out["matrix_free"][2]
+    a = (Ud.conj() * Um).sum(0) / (Ud.conj() * Ud).sum(0)
+    diff = float(((Um - a[None, :] * Ud).norm(dim=0) / Um.norm(dim=0)).max())
+    n = mesh.n
+    line = {"metric": "Algorithm 1 inverse power steps", "workload": args.workload, "n": n,
+            "N": prob.N, "nu": prob.nu, "q": q,
+            "dense_s": out["dense"][0], "matrix_free_s": out["matrix_free"][0],
+            "gmres_arnoldi_steps": out["matrix_free"][1], "gmres_tol": 1e-4,
+            "dense_S_bytes": n * n * 8, "basis_direction_diff": diff,
+            "note": "wall time around each call (synchronised); dense = S assembly + FP32 LU + "
+                    "q steps; matrix-free = q steps with GMRES solves, no n^2 storage"}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.inverse_power > 0:
+        return run_inverse_power(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch48":

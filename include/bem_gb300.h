@@ -72,7 +72,9 @@ const char* bem_version(void);
  * (tri_host: 3*nt int32 vertex indices, outward orientation) to the device and computes
  * per-triangle centroids, areas and the 7 quadrature points and weights. n = nt is the
  * number of unknowns. Fails with BEM_EINVAL on an index out of range or a triangle of
- * zero area. Synchronises the stream before returning.
+ * zero area (area below 1e-12 of its squared longest edge), both checked on the host before
+ * anything changes. The arrays are copied into a pinned staging buffer of the context and
+ * uploaded asynchronously; the call returns without synchronising.
  */
 bem_status bem_set_mesh(bem_ctx* ctx, int64_t nv, const double* xyz_host, int64_t nt,
                         const int32_t* tri_host, void* stream);
@@ -88,7 +90,9 @@ bem_status bem_set_mesh(bem_ctx* ctx, int64_t nv, const double* xyz_host, int64_
  * precision that projection uses) and kept until the mesh or contour changes. z_host /
  * w_host (2*N doubles each) may
  * be NULL; if given they receive the nodes / weights. Requires a mesh. N in [1, 4096],
- * a > 0, b > 0. Synchronises the stream before returning.
+ * a > 0, b > 0. The nodes and weights are computed on the host (the lower half of the
+ * nodes as the exact mirror of the upper, so conjugate nodes have equal real parts) and
+ * uploaded asynchronously through a pinned staging buffer; no synchronisation.
  * Kind CHEBYSHEV (Section 2, Eq. Chebyshev): the Chebyshev points of the first kind of the
  * interval [c_re - a, c_re + a] shifted by i c_im, z_k = c + a cos(pi (k + 1/2) / N), and
  * unit weights (bem_project then returns the unweighted V^H A(z_k) V); b is ignored.
@@ -302,6 +306,14 @@ bem_status bem_solve(bem_ctx* ctx, const double* V0_dev, int64_t ldv, int nu, in
  * recorded failures, BEM_ECUDA for a CUDA error. Clears the status word.
  */
 bem_status bem_check(bem_ctx* ctx, void* stream);
+/*
+ * Asynchronous mode (operational; the paper has no counterpart). With on != 0,
+ * bem_cholqr2 returns without waiting for its device status word, so that a pipeline of
+ * set-up, orthonormalisation and projection runs without a host synchronisation; a Gram
+ * matrix that was not positive definite is then reported by the next bem_check (or by the
+ * next call that synchronises). Off by default.
+ */
+bem_status bem_set_async(bem_ctx* ctx, int on);
 
 /* Number of CUDA kernels this context has launched since creation (diagnostics). */
 int64_t bem_kernel_launches(const bem_ctx* ctx);

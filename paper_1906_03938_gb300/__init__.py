@@ -42,6 +42,7 @@ SIGNATURES = {
     "bem_set_contour": (_I, [_P, _I, _D, _D, _D, _D, _I, _P, _P, _P]),
     "bem_project": (_I, [_P, _P, _I64, _I, _P, _P, _I, _P]),
     "bem_node_order": (_I, [_P, _P, _P]),
+    "bem_set_async": (_I, [_P, _I]),
     "bem_apply_sum": (_I, [_P, _P, _P, _I64, _I, _I, _P, _P]),
     "bem_solve_sum": (_I, [_P, _P, _P, _I64, _I, _D, _I, _P, _I64, ctypes.POINTER(_I), _P, _P]),
     "bem_inverse_power_mf": (_I, [_P, _P, _I64, _I, _I, _D, _D, _D, _I, ctypes.POINTER(_I), _P]),
@@ -345,6 +346,10 @@ class Context:
             self._h, c.ctypes.data_as(_P), _P(X.data_ptr()), int(ldx), int(nu),
             1 if per_node else 0, _P(Y.data_ptr()), _stream(stream)))
         return Y
+
+    def set_async(self, on=True):
+        """Asynchronous mode: cholqr2 leaves its status check to check()."""
+        self._chk("bem_set_async", self._lib.bem_set_async(self._h, 1 if on else 0))
 
     def node_order(self):
         """(order, twins): the mixed kernel's node schedule (slot -> node) and the number

@@ -1,6 +1,7 @@
 // Context, error handling, mesh and contour set-up, and the projection entry point.
 #include <math.h>
 #include <stdio.h>
+#include <string.h>
 
 #include <string>
 #include <vector>
@@ -127,6 +128,53 @@ static void build_node_order(Contour& c) {
   for (int j : single) c.order_host[slot++] = j;
 }
 
+// A pinned staging buffer of at least `bytes`, free to be rewritten (the copy behind its
+// event has completed).
+static bem_status stage_buffer(bem_ctx* ctx, void*& buf, size_t& cap, cudaEvent_t& ev,
+                               size_t bytes) {
+  if (ev) cudaEventSynchronize(ev);
+  else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+    return cuda_check(ctx, cudaGetLastError(), "staging event");
+  if (bytes > cap) {
+    cudaFreeHost(buf);
+    buf = nullptr;
+    cap = 0;
+    if (cudaMallocHost(&buf, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, BEM_ENOMEM, "pinned staging allocation failed");
+    }
+    cap = bytes;
+  }
+  return BEM_OK;
+}
+
+// Nodes and weights of a contour, on the host (the device receives these values).
+// Circle / ellipse: theta_j = pi (2 j + 1) / N with the lower half the exact mirror of the
+// upper (theta_{N-1-j} = 2 pi - theta_j), so conjugate nodes have equal real parts.
+static void contour_nodes(int kind, double c_re, double c_im, double a, double b, int N,
+                          double* z, double* w) {
+  const double pi = 3.14159265358979323846;
+  for (int j = 0; j < N; ++j) {
+    if (kind == BEM_CONTOUR_CHEBYSHEV) {
+      z[2 * j] = c_re + a * cos(pi * (j + 0.5) / N);
+      z[2 * j + 1] = c_im;
+      w[2 * j] = 1.0;
+      w[2 * j + 1] = 0.0;
+      continue;
+    }
+    const int m = 2 * j + 1 > N ? N - 1 - j : j;
+    const double th = pi * (2.0 * m + 1.0) / N;
+    double sn = sin(th);
+    const double cs = cos(th);
+    if (2 * m + 1 == N) sn = 0.0;   // theta = pi exactly
+    if (m != j) sn = -sn;
+    z[2 * j] = c_re + a * cs;
+    z[2 * j + 1] = c_im + b * sn;
+    w[2 * j] = b * cs / N;
+    w[2 * j + 1] = a * sn / N;
+  }
+}
+
 }  // namespace bem
 
 using namespace bem;
@@ -170,6 +218,12 @@ void bem_destroy(bem_ctx* ctx) {
   cudaFree(ctx->d_near_work);
   cudaFree(ctx->d_net);
   for (auto& e : ctx->ev) cudaEventDestroy(e);
+  if (ctx->mesh_ev) cudaEventSynchronize(ctx->mesh_ev);
+  if (ctx->con_ev) cudaEventSynchronize(ctx->con_ev);
+  cudaFreeHost(ctx->h_mesh);
+  cudaFreeHost(ctx->h_con);
+  if (ctx->mesh_ev) cudaEventDestroy(ctx->mesh_ev);
+  if (ctx->con_ev) cudaEventDestroy(ctx->con_ev);
   delete ctx;
 }
 
@@ -179,6 +233,12 @@ const char* bem_last_error(const bem_ctx* ctx) {
 }
 
 int64_t bem_kernel_launches(const bem_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+bem_status bem_set_async(bem_ctx* ctx, int on) {
+  if (!ctx) return BEM_EINVAL;
+  ctx->async = on != 0;
+  return BEM_OK;
+}
 
 bem_status bem_check(bem_ctx* ctx, void* stream) {
   if (!ctx) return BEM_EINVAL;
@@ -196,6 +256,29 @@ bem_status bem_set_mesh(bem_ctx* ctx, int64_t nv, const double* xyz_host, int64_
     return fail(ctx, BEM_EINVAL, "bem_set_mesh: need nv >= 3, 1 <= nt <= 2^26 and non-null arrays");
   for (int64_t t = 0; t < 3 * nv; ++t)
     if (!isfinite(xyz_host[t])) return fail(ctx, BEM_EINVAL, "bem_set_mesh: non-finite vertex coordinate");
+  // validation on the host (the geometry kernel repeats it into the status word): indices in
+  // range, and no triangle whose area is below 1e-12 of its squared longest edge
+  for (int64_t l = 0; l < nt; ++l) {
+    const int32_t* t3 = tri_host + 3 * l;
+    for (int e = 0; e < 3; ++e)
+      if (t3[e] < 0 || t3[e] >= nv)
+        return fail(ctx, BEM_EINVAL, "bem_set_mesh: vertex-index-out-of-range");
+    const double* v0 = xyz_host + 3 * (int64_t)t3[0];
+    const double* v1 = xyz_host + 3 * (int64_t)t3[1];
+    const double* v2 = xyz_host + 3 * (int64_t)t3[2];
+    const double e1[3] = {v1[0] - v0[0], v1[1] - v0[1], v1[2] - v0[2]};
+    const double e2[3] = {v2[0] - v0[0], v2[1] - v0[1], v2[2] - v0[2]};
+    const double e3[3] = {v2[0] - v1[0], v2[1] - v1[1], v2[2] - v1[2]};
+    const double nx = e1[1] * e2[2] - e1[2] * e2[1];
+    const double ny = e1[2] * e2[0] - e1[0] * e2[2];
+    const double nz = e1[0] * e2[1] - e1[1] * e2[0];
+    const double area = 0.5 * sqrt(nx * nx + ny * ny + nz * nz);
+    const double l2 = fmax(fmax(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2],
+                                e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2]),
+                           e3[0] * e3[0] + e3[1] * e3[1] + e3[2] * e3[2]);
+    if (!(area > 1e-12 * l2) || !isfinite(area))
+      return fail(ctx, BEM_EINVAL, "bem_set_mesh: zero-area-triangle");
+  }
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   ctx->con.N = 0;   // self terms depend on the mesh: the contour must be set again
@@ -231,13 +314,19 @@ bem_status bem_set_mesh(bem_ctx* ctx, int64_t nv, const double* xyz_host, int64_
   }
   g.n = nt;
   g.nv = nv;
-  bem_status st = cuda_check(ctx, cudaMemcpyAsync(g.xyz, xyz_host, 3 * nv * sizeof(double),
-                                                  cudaMemcpyHostToDevice, s), "bem_set_mesh copy");
+  // asynchronous upload through the pinned staging buffer
+  const size_t xb = 3 * nv * sizeof(double), tb = 3 * nt * sizeof(int32_t);
+  bem_status st = stage_buffer(ctx, ctx->h_mesh, ctx->h_mesh_bytes, ctx->mesh_ev, xb + tb);
+  if (st != BEM_OK) return st;
+  unsigned char* hb = reinterpret_cast<unsigned char*>(ctx->h_mesh);
+  memcpy(hb, xyz_host, xb);
+  memcpy(hb + xb, tri_host, tb);
+  st = cuda_check(ctx, cudaMemcpyAsync(g.xyz, hb, xb, cudaMemcpyHostToDevice, s), "bem_set_mesh copy");
   if (st == BEM_OK)
-    st = cuda_check(ctx, cudaMemcpyAsync(g.tri, tri_host, 3 * nt * sizeof(int32_t),
-                                         cudaMemcpyHostToDevice, s), "bem_set_mesh copy");
+    st = cuda_check(ctx, cudaMemcpyAsync(g.tri, hb + xb, tb, cudaMemcpyHostToDevice, s),
+                    "bem_set_mesh copy");
+  if (st == BEM_OK) st = cuda_check(ctx, cudaEventRecord(ctx->mesh_ev, s), "bem_set_mesh event");
   if (st == BEM_OK) st = cuda_check(ctx, launch_geometry(ctx, s), "geometry kernel");
-  if (st == BEM_OK) st = take_status(ctx, s, "bem_set_mesh");
   if (st != BEM_OK) {
     free_geometry(g);
     return st;
@@ -278,19 +367,27 @@ bem_status bem_set_contour(bem_ctx* ctx, int kind, double c_re, double c_im, dou
   }
   c.N = N; c.kind = kind; c.c_re = c_re; c.c_im = c_im; c.a = a; c.b = b;
   c.self64_ready = c.self32_ready = false;   // filled by the first projection that needs them
-  bem_status st = cuda_check(ctx, launch_contour(ctx, s), "contour kernel");
-  if (st == BEM_OK)
-    st = cuda_check(ctx, cudaMemcpyAsync(c.z_host, c.z, 2 * N * sizeof(double),
-                                         cudaMemcpyDeviceToHost, s), "contour copy");
-  if (st == BEM_OK)
-    st = cuda_check(ctx, cudaMemcpyAsync(c.w_host, c.w, 2 * N * sizeof(double),
-                                         cudaMemcpyDeviceToHost, s), "contour copy");
-  if (st == BEM_OK) st = take_status(ctx, s, "bem_set_contour");
-  if (st == BEM_OK) {
-    build_node_order(c);
-    st = cuda_check(ctx, cudaMemcpyAsync(c.order, c.order_host, N * sizeof(int),
-                                         cudaMemcpyHostToDevice, s), "node order copy");
+  // nodes, weights and node schedule on the host; asynchronous upload through the pinned
+  // staging buffer
+  contour_nodes(kind, c_re, c_im, a, b, N, c.z_host, c.w_host);
+  build_node_order(c);
+  const size_t zb = 2 * N * sizeof(double), ob = N * sizeof(int);
+  bem_status st = stage_buffer(ctx, ctx->h_con, ctx->h_con_bytes, ctx->con_ev, 2 * zb + ob);
+  if (st != BEM_OK) {
+    free_contour(c);
+    return st;
   }
+  unsigned char* hb = reinterpret_cast<unsigned char*>(ctx->h_con);
+  memcpy(hb, c.z_host, zb);
+  memcpy(hb + zb, c.w_host, zb);
+  memcpy(hb + 2 * zb, c.order_host, ob);
+  st = cuda_check(ctx, cudaMemcpyAsync(c.z, hb, zb, cudaMemcpyHostToDevice, s), "contour copy");
+  if (st == BEM_OK)
+    st = cuda_check(ctx, cudaMemcpyAsync(c.w, hb + zb, zb, cudaMemcpyHostToDevice, s), "contour copy");
+  if (st == BEM_OK)
+    st = cuda_check(ctx, cudaMemcpyAsync(c.order, hb + 2 * zb, ob, cudaMemcpyHostToDevice, s),
+                    "node order copy");
+  if (st == BEM_OK) st = cuda_check(ctx, cudaEventRecord(ctx->con_ev, s), "contour event");
   if (st != BEM_OK) {
     free_contour(c);
     return st;

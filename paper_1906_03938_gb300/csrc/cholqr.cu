@@ -968,5 +968,6 @@ extern "C" bem_status bem_cholqr2(bem_ctx* ctx, double* V_dev, int64_t n, int64_
   if (st != BEM_OK) return st;
   st = cholqr2_impl(ctx, V_dev, n, ldv, nu, R_dev, ctx->d_small, s, 0);
   if (st != BEM_OK) return st;
+  if (ctx->async) return cuda_check(ctx, cudaGetLastError(), "bem_cholqr2");
   return take_status(ctx, s, "bem_cholqr2");
 }

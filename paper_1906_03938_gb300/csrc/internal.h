@@ -114,6 +114,16 @@ struct bem_ctx {
   float* d_net = nullptr;
   int64_t net_floats = 0;
   bool net_ready = false;
+  // pinned host staging of the mesh and contour uploads (asynchronous copies); a buffer is
+  // rewritten only after the event recorded behind its last copy has completed
+  void* h_mesh = nullptr;
+  size_t h_mesh_bytes = 0;
+  cudaEvent_t mesh_ev = nullptr;
+  void* h_con = nullptr;
+  size_t h_con_bytes = 0;
+  cudaEvent_t con_ev = nullptr;
+  // asynchronous mode: bem_cholqr2 does not wait for its status word (bem_check reports it)
+  bool async = false;
 };
 
 namespace bem {

@@ -217,3 +217,33 @@ def test_cholqr2_without_R_routes(bem, n, nu, boost):
     Qo, _ = orr.orthonormalize(V)
     assert _relerr(Q, Qo) < 1e-8 * max(1.0, boost / 100.0)
     ctx.close()
+
+
+def test_async_mode_same_results_and_deferred_status(bem):
+    """bem_set_async: the set-up, orthonormalisation and projection pipeline gives the same
+    bits as the synchronous calls, and a rank-deficient basis is reported by bem_check
+    instead of by bem_cholqr2."""
+    prob = synth.workload("sphere320").problems[0]
+    mesh, spec = prob.mesh(), prob.contour
+    V = synth.complex_gaussian(mesh.n, prob.nu, prob.seed)
+    out = []
+    for mode in (False, True):
+        ctx = bem.Context(0)
+        ctx.set_async(mode)
+        ctx.set_mesh(mesh.xyz, mesh.tri)
+        ctx.set_contour(spec.kind, spec.centre, spec.a, spec.b, prob.N)
+        Vd = _dev(V)
+        ctx.cholqr2(Vd, want_R=False)
+        B = ctx.project(Vd, bem.PREC_MIXED)
+        ctx.check()
+        out.append((Vd.cpu(), B.cpu()))
+        ctx.close()
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+    ctx = bem.Context(0)
+    ctx.set_async(True)
+    Vbad = V.copy()
+    Vbad[:, 3] = Vbad[:, 2]
+    ctx.cholqr2(_dev(Vbad), want_R=False)          # returns at once
+    with pytest.raises(bem.BemError):
+        ctx.check()
+    ctx.close()
