@@ -38,6 +38,9 @@ def lib():
         L.oracle_apply.argtypes = [P, i64, P, i32, P, i32, P, i64, i64, P, i32, i32]
         L.oracle_near_rule.argtypes = [P, P, P, P, d, d, i32, i32, P]
         L.oracle_near_pairs.argtypes = [P, i64, P, i64, i64, P, P, P]
+        L.oracle_matrix_op.argtypes = [P, i64, P, d, d, i32, i64, i64, P, i32, i32, P]
+        L.oracle_apply_op.argtypes = [P, i64, P, i32, P, i32, P, i64, i64, P, i32, i32, P]
+        L.oracle_near_rule_kind.argtypes = [P, P, P, P, d, d, i32, i32, i32, P]
         L.oracle_max_threads.restype = i32
         _lib = L
     return _lib

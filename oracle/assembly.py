@@ -1,5 +1,7 @@
 """Oracle wrappers for the BEM matrix A(k) (Section 1, Eq. GreenFun; the single-layer part of
-Eq. HelmBIM with constant elements collocated at centroids). See ``bem_oracle.c``."""
+Eq. HelmBIM with constant elements collocated at centroids) and its operator variant
+T = c_G G + c_H (1/2 I + K) (the double layer K with its jump; Eq. HelmBIM's general form).
+``op`` = (c_G, c_H), default (1, 0). See ``bem_oracle.c``."""
 import ctypes
 import numpy as np
 
@@ -46,7 +48,13 @@ def self_integral(v0, v1, v2, x, k, deriv=0):
     return complex(out[0], out[1])
 
 
-def matrix(mesh, k, deriv=0, rows=None, threads=0, near=False):
+def _op4(op):
+    cg, ch = (1.0, 0.0) if op is None else op
+    cg, ch = complex(cg), complex(ch)
+    return np.array([cg.real, cg.imag, ch.real, ch.imag])
+
+
+def matrix(mesh, k, deriv=0, rows=None, threads=0, near=False, op=None):
     """Dense A(k) (deriv=0) or dA/dk (deriv=1) as an (r1-r0) x n complex128 array; near=True
     uses the 64-point conical rule on near pairs (see ``bem_oracle.c``)."""
     xyz, tri = _mesh_arrays(mesh)
@@ -54,12 +62,13 @@ def matrix(mesh, k, deriv=0, rows=None, threads=0, near=False):
     r0, r1 = (0, n) if rows is None else rows
     A = np.zeros((r1 - r0, n), dtype=np.complex128)
     k = complex(k)
-    lib().oracle_matrix(_p(xyz), n, _p(tri), k.real, k.imag, int(deriv), r0, r1, _p(A),
-                        int(threads), int(bool(near)))
+    o = _op4(op)
+    lib().oracle_matrix_op(_p(xyz), n, _p(tri), k.real, k.imag, int(deriv), r0, r1, _p(A),
+                           int(threads), int(bool(near)), _p(o))
     return A
 
 
-def apply(mesh, z, V, rows=None, threads=0, near=False):
+def apply(mesh, z, V, rows=None, threads=0, near=False, op=None):
     """Y[j] = (A(z_j) V)[rows] for all nodes; returns (N, r1-r0, nu) complex128."""
     xyz, tri = _mesh_arrays(mesh)
     n = tri.shape[0]
@@ -70,21 +79,23 @@ def apply(mesh, z, V, rows=None, threads=0, near=False):
     N = z.shape[0]
     r0, r1 = (0, n) if rows is None else rows
     Y = np.zeros(N * (r1 - r0) * nu, dtype=np.complex128)
-    lib().oracle_apply(_p(xyz), n, _p(tri), N, _p(z), nu, _p(V), r0, r1, _p(Y), int(threads),
-                       int(bool(near)))
+    o = _op4(op)
+    lib().oracle_apply_op(_p(xyz), n, _p(tri), N, _p(z), nu, _p(V), r0, r1, _p(Y), int(threads),
+                          int(bool(near)), _p(o))
     # block j is column-major (rows x nu)
     return np.stack([Y[j * (r1 - r0) * nu:(j + 1) * (r1 - r0) * nu].reshape(nu, r1 - r0).T
                      for j in range(N)])
 
 
-def near_rule(v0, v1, v2, x, k, deriv=0, order=8):
+def near_rule(v0, v1, v2, x, k, deriv=0, order=8, kind=0):
     """The conical-product rule of the given order (order x order points) for the integral of
-    g(k, |x - y|) over the triangle (v0, v1, v2), collapsed at the vertex nearest x."""
+    g(k, |x - y|) (kind 0) or dg/dn_y (kind 1, normal of the triangle in its vertex order)
+    over the triangle (v0, v1, v2), collapsed at the vertex nearest x."""
     arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in (v0, v1, v2, x)]
     out = np.zeros(2)
     k = complex(k)
-    lib().oracle_near_rule(*[_p(a) for a in arrs], k.real, k.imag, int(deriv), int(order),
-                           _p(out))
+    lib().oracle_near_rule_kind(*[_p(a) for a in arrs], k.real, k.imag, int(deriv), int(order),
+                                int(kind), _p(out))
     return complex(out[0], out[1])
 
 

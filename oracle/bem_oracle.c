@@ -32,6 +32,19 @@
  * s and in t; the collapsed vertex a is the vertex of triangle l nearest x_i (the first of
  * them in the triangle's order on a tie), b and c follow it cyclically.
  *
+ * Operator variant (the paper's general T = A H - B G of Eq. HelmBIM, for Neumann and Robin
+ * conditions): with coefficients (c_G, c_H) the matrix is c_G G + c_H H, G the single layer
+ * above and H = 1/2 I + K the double layer with its jump (the unknown is then the boundary
+ * value u, Green's representation taken to the boundary from inside with outward normals):
+ *
+ *   K_il(k) = sum_q W_lq dg/dn_y(x_i, y_lq),  dg/dn_y = exp(i k r) (i k r - 1) (y - x).n_l
+ *                                                        / (4 pi r^3),             i != l
+ *   K_ii(k) = 0  (x_i lies in the plane of triangle i, so (y - x).n_i vanishes on it)
+ *
+ * n_l the unit normal of triangle l in the vertex order (outward for an outward-oriented
+ * mesh). Its k-derivative is -k exp(i k r) (y - x).n_l / (4 pi r). Near pairs take the same
+ * 64-point conical rule for this kernel. The default (c_G, c_H) = (1, 0) is the single layer.
+ *
  * Everything is double / double complex, loops are plain, rows are spread over OpenMP
  * threads (no blocking, no reordering of any sum).
  */
@@ -142,6 +155,7 @@ static cplx hprime_fun(cplx w) {
 typedef struct {
     double centroid[3];
     double area;
+    double nrm[3];     /* unit normal, vertex order */
     double diam;       /* longest edge */
     double v[3][3];    /* vertices */
     double qp[7][3];
@@ -159,6 +173,7 @@ static void panel_geometry(const double* xyz, const int32_t* tri, int64_t l, pan
     sub3(v2, v0, e2);
     cross3(e1, e2, nrm);
     P->area = 0.5 * norm3(nrm);
+    for (int c = 0; c < 3; ++c) P->nrm[c] = nrm[c] / (2.0 * P->area);
     for (int c = 0; c < 3; ++c) P->centroid[c] = (v0[c] + v1[c] + v2[c]) / 3.0;
     double e3[3];
     sub3(v2, v1, e3);
@@ -173,6 +188,23 @@ static void panel_geometry(const double* xyz, const int32_t* tri, int64_t l, pan
             P->qp[q][c] = bary[q][0] * v0[c] + bary[q][1] * v1[c] + bary[q][2] * v2[c];
         P->qw[q] = w[q] * P->area;
     }
+}
+
+/* ---------------- kernels ---------------- */
+
+/* g(k, r) (deriv = 0) or dg/dk (deriv = 1) at distance r. */
+static cplx g_kernel(cplx k, double r, int deriv) {
+    const cplx e = cexp(I * k * r);
+    return deriv ? I * e / (4.0 * PI) : e / (4.0 * PI * r);
+}
+
+/* dg/dn_y (deriv = 0) or its k-derivative (deriv = 1) for y - x = d, normal n at y. */
+static cplx dl_kernel(cplx k, const double* d, const double* n, int deriv) {
+    const double r = norm3(d);
+    const double dn = dot3(d, n);
+    const cplx e = cexp(I * k * r);
+    if (deriv) return -k * e * dn / (4.0 * PI * r);
+    return e * (I * k * r - 1.0) * dn / (4.0 * PI * r * r * r);
 }
 
 /* ---------------- the self term ---------------- */
@@ -226,7 +258,8 @@ static cplx self_integral(const double* v0, const double* v1, const double* v2,
 /* Conical-product rule of order m (m x m points) for the integral over triangle v of
  * g(k, |x - y|) (deriv = 0) or its k-derivative (deriv = 1); collapsed at the vertex of the
  * triangle nearest x. */
-static cplx near_integral(const double v[3][3], const double* x, cplx k, int deriv, int m) {
+static cplx near_integral(const double v[3][3], const double* x, cplx k, int deriv, int m,
+                          int kind) {
     double gx[64], gw[64];
     gauss_legendre(m, gx, gw);
     int a = 0;
@@ -248,6 +281,8 @@ static cplx near_integral(const double v[3][3], const double* x, cplx k, int der
     sub3(C, B, bc);
     cross3(ab, bc, nrm);
     const double twice_area = norm3(nrm);
+    double un[3];
+    for (int c = 0; c < 3; ++c) un[c] = nrm[c] / twice_area;
     cplx total = 0.0;
     for (int p = 0; p < m; ++p) {
         const double sp = 0.5 * (gx[p] + 1.0), wp = 0.5 * gw[p];
@@ -255,10 +290,8 @@ static cplx near_integral(const double v[3][3], const double* x, cplx k, int der
             const double tq = 0.5 * (gx[q] + 1.0), wq = 0.5 * gw[q];
             double y[3], d[3];
             for (int c = 0; c < 3; ++c) y[c] = A[c] + sp * ab[c] + sp * tq * bc[c];
-            sub3(x, y, d);
-            const double r = norm3(d);
-            const cplx e = cexp(I * k * r);
-            const cplx g = deriv ? I * e / (4.0 * PI) : e / (4.0 * PI * r);
+            const cplx g = kind ? (sub3(y, x, d), dl_kernel(k, d, un, deriv))
+                                : (sub3(x, y, d), g_kernel(k, norm3(d), deriv));
             total += wp * wq * twice_area * sp * g;
         }
     }
@@ -271,23 +304,43 @@ static int is_near(const panel_t* Pi, const panel_t* Pl) {
     return norm3(d) < 2.0 * fmax(Pi->diam, Pl->diam);
 }
 
-/* A_il(k) (deriv = 0) or dA_il/dk (deriv = 1); near != 0 selects the near-field variant. */
+typedef struct {
+    cplx cG, cH;   /* T = cG G + cH (1/2 I + K) */
+} op_t;
+
+static op_t op_from(const double* op4) {
+    op_t o;
+    o.cG = op4 ? op4[0] + I * op4[1] : 1.0;
+    o.cH = op4 ? op4[2] + I * op4[3] : 0.0;
+    return o;
+}
+
+/* T_il(k) (deriv = 0) or dT_il/dk (deriv = 1); near != 0 selects the near-field variant. */
 static cplx entry(const double* xyz, const int32_t* tri, const panel_t* Pi,
-                  const panel_t* Pl, int64_t i, int64_t l, cplx k, int deriv, int near) {
-    if (near && i != l && is_near(Pi, Pl)) return near_integral(Pl->v, Pi->centroid, k, deriv, 8);
+                  const panel_t* Pl, int64_t i, int64_t l, cplx k, int deriv, int near,
+                  op_t op) {
+    cplx s = 0.0;
+    if (near && i != l && is_near(Pi, Pl)) {
+        if (op.cG != 0.0) s += op.cG * near_integral(Pl->v, Pi->centroid, k, deriv, 8, 0);
+        if (op.cH != 0.0) s += op.cH * near_integral(Pl->v, Pi->centroid, k, deriv, 8, 1);
+        return s;
+    }
     if (i == l) {
         const double* v0 = xyz + 3 * (int64_t)tri[3 * l + 0];
         const double* v1 = xyz + 3 * (int64_t)tri[3 * l + 1];
         const double* v2 = xyz + 3 * (int64_t)tri[3 * l + 2];
-        return self_integral(v0, v1, v2, Pi->centroid, k, deriv);
+        if (op.cG != 0.0) s += op.cG * self_integral(v0, v1, v2, Pi->centroid, k, deriv);
+        if (op.cH != 0.0 && !deriv) s += op.cH * 0.5;   /* the jump; K_ii = 0 */
+        return s;
     }
-    cplx s = 0.0;
     for (int q = 0; q < 7; ++q) {
-        double d[3];
+        double d[3], dy[3];
         sub3(Pi->centroid, Pl->qp[q], d);
-        double r = norm3(d);
-        cplx e = cexp(I * k * r);
-        s += Pl->qw[q] * (deriv ? I * e / (4.0 * PI) : e / (4.0 * PI * r));
+        sub3(Pl->qp[q], Pi->centroid, dy);
+        cplx t = 0.0;
+        if (op.cG != 0.0) t += op.cG * g_kernel(k, norm3(d), deriv);
+        if (op.cH != 0.0) t += op.cH * dl_kernel(k, dy, Pl->nrm, deriv);
+        s += Pl->qw[q] * t;
     }
     return s;
 }
@@ -343,10 +396,11 @@ void oracle_self_integral(const double* v0, const double* v1, const double* v2,
 }
 
 /* Dense A(k) (or dA/dk) for rows [r0, r1), row-major with row stride nt (complex). */
-void oracle_matrix(const double* xyz, int64_t nt, const int32_t* tri, double k_re,
-                   double k_im, int deriv, int64_t r0, int64_t r1, double* A_out,
-                   int nthreads, int near) {
+void oracle_matrix_op(const double* xyz, int64_t nt, const int32_t* tri, double k_re,
+                      double k_im, int deriv, int64_t r0, int64_t r1, double* A_out,
+                      int nthreads, int near, const double* op4) {
     set_threads(nthreads);
+    const op_t op = op_from(op4);
     cplx k = k_re + I * k_im;
     cplx* A = (cplx*)A_out;
 #pragma omp parallel for schedule(dynamic, 4)
@@ -355,9 +409,15 @@ void oracle_matrix(const double* xyz, int64_t nt, const int32_t* tri, double k_r
         panel_geometry(xyz, tri, i, &Pi);
         for (int64_t l = 0; l < nt; ++l) {
             panel_geometry(xyz, tri, l, &Pl);
-            A[(i - r0) * nt + l] = entry(xyz, tri, &Pi, &Pl, i, l, k, deriv, near);
+            A[(i - r0) * nt + l] = entry(xyz, tri, &Pi, &Pl, i, l, k, deriv, near, op);
         }
     }
+}
+
+void oracle_matrix(const double* xyz, int64_t nt, const int32_t* tri, double k_re,
+                   double k_im, int deriv, int64_t r0, int64_t r1, double* A_out,
+                   int nthreads, int near) {
+    oracle_matrix_op(xyz, nt, tri, k_re, k_im, deriv, r0, r1, A_out, nthreads, near, 0);
 }
 
 /*
@@ -365,10 +425,11 @@ void oracle_matrix(const double* xyz, int64_t nt, const int32_t* tri, double k_r
  * z: N complex nodes (interleaved); V: n x nu complex, column-major; Y_out: for node j the
  * block Y_out + j * (r1 - r0) * nu, column-major (r1 - r0) x nu.
  */
-void oracle_apply(const double* xyz, int64_t nt, const int32_t* tri, int N,
-                  const double* z, int nu, const double* V_in, int64_t r0, int64_t r1,
-                  double* Y_out, int nthreads, int near) {
+void oracle_apply_op(const double* xyz, int64_t nt, const int32_t* tri, int N,
+                     const double* z, int nu, const double* V_in, int64_t r0, int64_t r1,
+                     double* Y_out, int nthreads, int near, const double* op4) {
     set_threads(nthreads);
+    const op_t op = op_from(op4);
     const cplx* V = (const cplx*)V_in;
     cplx* Y = (cplx*)Y_out;
     const int64_t rows = r1 - r0;
@@ -381,7 +442,7 @@ void oracle_apply(const double* xyz, int64_t nt, const int32_t* tri, int N,
             panel_geometry(xyz, tri, l, &Pl);
             for (int j = 0; j < N; ++j) {
                 cplx k = z[2 * j] + I * z[2 * j + 1];
-                cplx a = entry(xyz, tri, &Pi, &Pl, i, l, k, 0, near);
+                cplx a = entry(xyz, tri, &Pi, &Pl, i, l, k, 0, near, op);
                 cplx* Yj = Y + (int64_t)j * rows * nu;
                 for (int c = 0; c < nu; ++c)
                     Yj[(int64_t)c * rows + (i - r0)] += a * V[(int64_t)c * nt + l];
@@ -390,18 +451,30 @@ void oracle_apply(const double* xyz, int64_t nt, const int32_t* tri, int N,
     }
 }
 
+void oracle_apply(const double* xyz, int64_t nt, const int32_t* tri, int N,
+                  const double* z, int nu, const double* V_in, int64_t r0, int64_t r1,
+                  double* Y_out, int nthreads, int near) {
+    oracle_apply_op(xyz, nt, tri, N, z, nu, V_in, r0, r1, Y_out, nthreads, near, 0);
+}
+
 /* The conical-product rule of order m (<= 64) for triangle (v0, v1, v2) at x; out = (re, im). */
-void oracle_near_rule(const double* v0, const double* v1, const double* v2, const double* x,
-                      double k_re, double k_im, int deriv, int m, double* out) {
+void oracle_near_rule_kind(const double* v0, const double* v1, const double* v2,
+                           const double* x, double k_re, double k_im, int deriv, int m,
+                           int kind, double* out) {
     double v[3][3];
     for (int c = 0; c < 3; ++c) {
         v[0][c] = v0[c];
         v[1][c] = v1[c];
         v[2][c] = v2[c];
     }
-    cplx s = near_integral(v, x, k_re + I * k_im, deriv, m);
+    cplx s = near_integral(v, x, k_re + I * k_im, deriv, m, kind);
     out[0] = creal(s);
     out[1] = cimag(s);
+}
+
+void oracle_near_rule(const double* v0, const double* v1, const double* v2, const double* x,
+                      double k_re, double k_im, int deriv, int m, double* out) {
+    oracle_near_rule_kind(v0, v1, v2, x, k_re, k_im, deriv, m, 0, out);
 }
 
 /* Near pairs of rows [r0, r1): counts[i - r0] = number of near panels l of row i; with

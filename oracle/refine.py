@@ -26,18 +26,18 @@ import scipy.sparse.linalg as spla
 from . import assembly
 
 
-def residual(mesh, lam, X, near=False):
+def residual(mesh, lam, X, near=False, op=None):
     X = np.atleast_2d(np.asarray(X, dtype=np.complex128).T).T
     lam = np.atleast_1d(lam)
     out = []
     for c in range(X.shape[1]):
-        A = assembly.matrix(mesh, lam[c], near=near)
+        A = assembly.matrix(mesh, lam[c], near=near, op=op)
         out.append(np.linalg.norm(A @ X[:, c]) / np.linalg.norm(X[:, c]))
     return np.array(out)
 
 
-def sigma_min(mesh, k, near=False):
-    s = np.linalg.svd(assembly.matrix(mesh, k, near=near), compute_uv=False)
+def sigma_min(mesh, k, near=False, op=None):
+    s = np.linalg.svd(assembly.matrix(mesh, k, near=near, op=op), compute_uv=False)
     return s[-1], s[0]
 
 
@@ -57,24 +57,24 @@ def _small_thetas(A, Ad, count):
     return th[np.argsort(np.abs(th))]
 
 
-def slp(mesh, lam0, tol=1e-14, maxit=30, count=6, near=False):
+def slp(mesh, lam0, tol=1e-14, maxit=30, count=6, near=False, op=None):
     lam = complex(lam0)
     th = None
     for _ in range(maxit):
-        A = assembly.matrix(mesh, lam, near=near)
-        Ad = assembly.matrix(mesh, lam, deriv=1, near=near)
+        A = assembly.matrix(mesh, lam, near=near, op=op)
+        Ad = assembly.matrix(mesh, lam, deriv=1, near=near, op=op)
         th = _small_thetas(A, Ad, count)
         lam = lam + th[0]
         if abs(th[0]) <= tol * abs(lam):
             break
-    A = assembly.matrix(mesh, lam, near=near)
-    Ad = assembly.matrix(mesh, lam, deriv=1, near=near)
+    A = assembly.matrix(mesh, lam, near=near, op=op)
+    Ad = assembly.matrix(mesh, lam, deriv=1, near=near, op=op)
     th = _small_thetas(A, Ad, count)
     return lam, th
 
 
 def discrete_eigs(mesh, starts, radius=0.3, mult_tol=1e-9, dedup=1e-8, count=8,
-                  keep=None, near=False):
+                  keep=None, near=False, op=None):
     """Eigenvalues (with multiplicity) reached from ``starts`` and their neighbours within
     ``radius``; ``keep(lam)`` restricts which neighbours are followed."""
     found = []      # list of (lam, multiplicity)
@@ -85,7 +85,7 @@ def discrete_eigs(mesh, starts, radius=0.3, mult_tol=1e-9, dedup=1e-8, count=8,
         s = queue.pop(0)
         if any(abs(s - f) <= 1e-6 * abs(f) for f, _ in found):
             continue
-        lam, th = slp(mesh, s, count=count, near=near)
+        lam, th = slp(mesh, s, count=count, near=near, op=op)
         if any(abs(lam - f) <= dedup * abs(f) for f, _ in found):
             continue
         mult = int(np.sum(np.abs(th) <= mult_tol * abs(lam)))
@@ -99,7 +99,7 @@ def discrete_eigs(mesh, starts, radius=0.3, mult_tol=1e-9, dedup=1e-8, count=8,
     return found
 
 
-def winding_count(mesh, spec, M=256, near=False):
+def winding_count(mesh, spec, M=256, near=False, op=None):
     """(1 / 2 pi i) \\oint tr(A(z)^{-1} A'(z)) dz by the trapezoid rule on the contour:
     the number of eigenvalues inside (argument principle)."""
     theta = 2.0 * np.pi * np.arange(M) / M
@@ -108,7 +108,7 @@ def winding_count(mesh, spec, M=256, near=False):
     for t in theta:
         zz = spec.centre + a * np.cos(t) + 1j * b * np.sin(t)
         dz = -a * np.sin(t) + 1j * b * np.cos(t)
-        A = assembly.matrix(mesh, zz, near=near)
-        Ad = assembly.matrix(mesh, zz, deriv=1, near=near)
+        A = assembly.matrix(mesh, zz, near=near, op=op)
+        Ad = assembly.matrix(mesh, zz, deriv=1, near=near, op=op)
         total += np.trace(np.linalg.solve(A, Ad)) * dz
     return total * (2.0 * np.pi / M) / (2.0j * np.pi)

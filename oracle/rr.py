@@ -26,10 +26,10 @@ import scipy.linalg as sla
 from . import assembly
 
 
-def project(mesh, z, V, rows=None, threads=0, near=False):
+def project(mesh, z, V, rows=None, threads=0, near=False, op=None):
     """P_j = V^H A(z_j) V (unweighted, Eq. RR_approx) and Y_j = A(z_j) V (near=True: the
     near-field variant of A)."""
-    Y = assembly.apply(mesh, z, V, rows=rows, threads=threads, near=near)
+    Y = assembly.apply(mesh, z, V, rows=rows, threads=threads, near=near, op=op)
     Vh = np.asarray(V).conj().T
     if rows is not None:
         Vh = Vh[:, rows[0]:rows[1]]

@@ -6,8 +6,11 @@ found by the oracle's successive-linear-problems refinement started from the clo
 continuum eigenvalues inside the contour (unit sphere: zeros of spherical Bessel functions,
 Table 3; unit cube: pi sqrt(n1^2 + n2^2 + n3^2), Table 1) and from every neighbour that the
 refinement reveals. "sphere320_near" is the same sphere with the near-field variant of A
-(8 x 8 conical rule on near panel pairs). Usage:
-python tests/golden/make_golden.py [sphere320] [cube3072] [sphere320_near]
+(8 x 8 conical rule on near panel pairs). "sphere320_neumann" is the sphere with the
+operator T = 1/2 I + K (the double layer with its jump: the interior Neumann problem, the
+paper's T = A H - B G with B = 0), started from the zeros of j_1' and j_2' (2.0816,
+3.3421) inside the circle of centre 2.75 and radius 0.9. Usage:
+python tests/golden/make_golden.py [sphere320] [cube3072] [sphere320_near] [sphere320_neumann]
 """
 import os
 import sys
@@ -24,22 +27,28 @@ STARTS = {
     "sphere320": [3.141593, 4.493409],
     "cube3072": [5.441398, 7.695299],
     "sphere320_near": [3.141593, 4.493409],
+    "sphere320_neumann": [2.081576, 3.342094],
 }
+OPERATOR = {"sphere320_neumann": (0.0, 1.0)}
+CONTOUR = {"sphere320_neumann": synth.ContourSpec("circle", 2.75 + 0j, 0.9, 0.9)}
 
 
 def main(names):
     for name in names:
         near = name.endswith("_near")
-        prob = synth.workload(name[:-5] if near else name).problems[0]
+        base = name.split("_")[0]
+        prob = synth.workload(base).problems[0]
         mesh = prob.mesh()
-        spec = prob.contour
+        spec = CONTOUR.get(name, prob.contour)
+        op = OPERATOR.get(name)
         found = refine.discrete_eigs(mesh, STARTS[name], radius=0.2,
                                      keep=lambda l: bool(contour.inside(l, spec, -0.05)),
-                                     near=near)
+                                     near=near, op=op)
         path = os.path.join(HERE, f"eigs_{name}.txt")
         with open(path, "w") as f:
             f.write(f"# discrete eigenvalues of A(k) inside the contour of {name}"
-                    f"{' (near-field variant of A)' if near else ''}\n")
+                    f"{' (near-field variant of A)' if near else ''}"
+                    f"{f' (operator c_G G + c_H (I/2 + K), (c_G, c_H) = {op})' if op else ''}\n")
             f.write(f"# mesh {mesh.name} (n = {mesh.n}), contour {spec}\n")
             f.write("# written by tests/golden/make_golden.py (oracle only)\n")
             f.write("# re im multiplicity inside\n")
