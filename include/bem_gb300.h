@@ -101,6 +101,23 @@ bem_status bem_set_contour(bem_ctx* ctx, int kind, double c_re, double c_im, dou
                            double b, int N, double* z_host, double* w_host, void* stream);
 
 /*
+ * The boundary operator (Section 1, Eq. HelmBIM in its general form T = A H - B G, with
+ * constant coefficients): T(k) = c_G G(k) + c_H (1/2 I + K(k)), G the single layer
+ * (Eq. GreenFun) and K the double layer with kernel
+ *     dG/dn_y = exp(i k r) (i k r - 1) (y - x) . n_y / (4 pi r^3),
+ * n_y the unit normal of the source triangle in its vertex order (outward for an outward
+ * oriented mesh), collocated at centroids with the same 7-point rule; K vanishes on the
+ * collocation point's own (flat) panel, whose entry is c_G A_ii + c_H / 2. (c_G, c_H) =
+ * (1, 0), the default, is the single layer (Dirichlet conditions); (0, 1) the interior
+ * Neumann problem with the boundary values as unknowns; both non-zero a Robin condition.
+ * Every projection, residual, refinement, inverse power step and near-field correction
+ * uses T from the next call on; the self terms are recomputed. The near-field surrogate
+ * (mode 2) and the batched launch cover the single layer only (BEM_EINVAL). Host only.
+ */
+bem_status bem_set_operator(bem_ctx* ctx, double cg_re, double cg_im, double ch_re,
+                            double ch_im);
+
+/*
  * Node schedule of the mixed projection (an implementation detail of Eq. RR_approx's
  * evaluation; the paper has no counterpart). Nodes whose real parts round to the same FP32
  * value evaluate the same phase Re(z_j) |x - y| at every quadrature point: the conjugate

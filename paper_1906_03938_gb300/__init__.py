@@ -43,6 +43,7 @@ SIGNATURES = {
     "bem_project": (_I, [_P, _P, _I64, _I, _P, _P, _I, _P]),
     "bem_node_order": (_I, [_P, _P, _P]),
     "bem_set_async": (_I, [_P, _I]),
+    "bem_set_operator": (_I, [_P, _D, _D, _D, _D]),
     "bem_apply_sum": (_I, [_P, _P, _P, _I64, _I, _I, _P, _P]),
     "bem_solve_sum": (_I, [_P, _P, _P, _I64, _I, _D, _I, _P, _I64, ctypes.POINTER(_I), _P, _P]),
     "bem_inverse_power_mf": (_I, [_P, _P, _I64, _I, _I, _D, _D, _D, _I, ctypes.POINTER(_I), _P]),
@@ -346,6 +347,12 @@ class Context:
             self._h, c.ctypes.data_as(_P), _P(X.data_ptr()), int(ldx), int(nu),
             1 if per_node else 0, _P(Y.data_ptr()), _stream(stream)))
         return Y
+
+    def set_operator(self, c_g=1.0, c_h=0.0):
+        """T = c_G G + c_H (I/2 + K): (1, 0) single layer, (0, 1) Neumann, else Robin."""
+        cg, ch = complex(c_g), complex(c_h)
+        self._chk("bem_set_operator", self._lib.bem_set_operator(
+            self._h, cg.real, cg.imag, ch.real, ch.imag))
 
     def set_async(self, on=True):
         """Asynchronous mode: cholqr2 leaves its status check to check()."""

@@ -69,7 +69,7 @@ bem_status take_status(bem_ctx* ctx, cudaStream_t stream, const char* where) {
 static void free_geometry(Geometry& g) {
   cudaFree(g.xyz); cudaFree(g.tri); cudaFree(g.cx); cudaFree(g.qp); cudaFree(g.qw);
   cudaFree(g.cx32); cudaFree(g.qp32); cudaFree(g.qw32); cudaFree(g.edge32); cudaFree(g.pack32);
-  cudaFree(g.mom32); cudaFree(g.rho32); cudaFree(g.diam);
+  cudaFree(g.mom32); cudaFree(g.rho32); cudaFree(g.diam); cudaFree(g.nrm);
   g = Geometry();
 }
 
@@ -234,6 +234,25 @@ const char* bem_last_error(const bem_ctx* ctx) {
 
 int64_t bem_kernel_launches(const bem_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+bem_status bem_set_operator(bem_ctx* ctx, double cg_re, double cg_im, double ch_re,
+                            double ch_im) {
+  if (!ctx) return BEM_EINVAL;
+  if (!isfinite(cg_re) || !isfinite(cg_im) || !isfinite(ch_re) || !isfinite(ch_im) ||
+      (cg_re == 0.0 && cg_im == 0.0 && ch_re == 0.0 && ch_im == 0.0))
+    return fail(ctx, BEM_EINVAL, "bem_set_operator: coefficients must be finite and not both zero");
+  const bool has_h = ch_re != 0.0 || ch_im != 0.0;
+  if (has_h && ctx->near_mode == 2)
+    return fail(ctx, BEM_EINVAL,
+                "bem_set_operator: the surrogate near field (mode 2) covers the single layer only");
+  ctx->op.cgr = cg_re;
+  ctx->op.cgi = cg_im;
+  ctx->op.chr = ch_re;
+  ctx->op.chi = ch_im;
+  ctx->op_version++;
+  ctx->con.self64_ready = ctx->con.self32_ready = false;   // T's self entries change
+  return BEM_OK;
+}
+
 bem_status bem_set_async(bem_ctx* ctx, int on) {
   if (!ctx) return BEM_EINVAL;
   ctx->async = on != 0;
@@ -297,6 +316,7 @@ bem_status bem_set_mesh(bem_ctx* ctx, int64_t nv, const double* xyz_host, int64_
               cudaMalloc(&g.mom32, kSelfMoments * nt * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&g.rho32, nt * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&g.diam, nt * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&g.nrm, 3 * nt * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&g.pack32, (nt + 15) / 16 * 16 * 64 * sizeof(float)) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();

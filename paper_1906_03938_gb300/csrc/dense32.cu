@@ -49,12 +49,14 @@ constexpr int kMaxK = 64;   // wavenumbers per assembly
 struct KList {
   int nk;
   float kr[kMaxK], kmi[kMaxK];   // Re k, -Im k log2(e)
+  float ki[kMaxK];               // Im k
   float cr[kMaxK], ci[kMaxK];    // coefficients
 };
 
 // One thread per entry (i, l), i fastest (coalesced column-major writes).
 __global__ void __launch_bounds__(256)
-assemble32_kernel(Geometry g, KList K, const float2* __restrict__ self32, float2* __restrict__ M) {
+assemble32_kernel(Geometry g, KList K, const float2* __restrict__ self32, float2* __restrict__ M,
+                  OpCoef op) {
   const int64_t n = g.n;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n * n) return;
@@ -68,7 +70,14 @@ assemble32_kernel(Geometry g, KList K, const float2* __restrict__ self32, float2
     }
   } else {
     const float xi = g.cx32[i], yi = g.cx32[n + i], zi = g.cx32[2 * n + i];
-    float rr[7], am[7];
+    const bool general = !op_single(op);
+    float nx = 0.f, ny = 0.f, nz = 0.f;
+    if (general) {
+      nx = (float)g.nrm[l];
+      ny = (float)g.nrm[n + l];
+      nz = (float)g.nrm[2 * n + l];
+    }
+    float rr[7], am[7], sq[7];   // sq: (y - x) . n / r^2 (general operator)
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
       const float dx = xi - g.qp32[q * n + l], dy = yi - g.qp32[(7 + q) * n + l],
@@ -77,6 +86,7 @@ assemble32_kernel(Geometry g, KList K, const float2* __restrict__ self32, float2
       const float rs = rsqrtf(r2);
       rr[q] = r2 * rs;
       am[q] = g.qw32[q * n + l] * rs;
+      sq[q] = general ? -(dx * nx + dy * ny + dz * nz) * rs * rs : 0.f;
     }
     for (int k = 0; k < K.nk; ++k) {
       float er = 0.f, ei = 0.f;
@@ -86,8 +96,16 @@ assemble32_kernel(Geometry g, KList K, const float2* __restrict__ self32, float2
         const float ph = K.kr[k] * rr[q];
         const float nrot = fmaf(ph, kInv2PiF, 12582912.0f) - 12582912.0f;
         const float red = fmaf(-nrot, kTwoPiLoF, fmaf(-nrot, kTwoPiHiF, ph));
-        er = fmaf(a, mufu_cos(red), er);
-        ei = fmaf(a, mufu_sin(red), ei);
+        if (general) {   // T = c_G G + c_H (1/2 I + K): times F
+          float fr, fi;
+          op_factor(op, sq[q], ph, K.ki[k] * rr[q], fr, fi);
+          const float cr = a * mufu_cos(red), ci = a * mufu_sin(red);
+          er += cr * fr - ci * fi;
+          ei += cr * fi + ci * fr;
+        } else {
+          er = fmaf(a, mufu_cos(red), er);
+          ei = fmaf(a, mufu_sin(red), ei);
+        }
       }
       sr += K.cr[k] * er - K.ci[k] * ei;
       si += K.cr[k] * ei + K.ci[k] * er;
@@ -284,6 +302,7 @@ bem_status assemble32(bem_ctx* ctx, int nk, const double* kz_host, const double*
   for (int k = 0; k < nk; ++k) {
     K.kr[k] = (float)kz_host[2 * k];
     K.kmi[k] = (float)(-kz_host[2 * k + 1]) * kLog2eF;
+    K.ki[k] = (float)kz_host[2 * k + 1];
     K.cr[k] = (float)coef_host[2 * k];
     K.ci[k] = (float)coef_host[2 * k + 1];
   }
@@ -298,7 +317,7 @@ bem_status assemble32(bem_ctx* ctx, int nk, const double* kz_host, const double*
   st = cuda_check(ctx, launch_self32(ctx, nk, zd, self32, s), "assemble32 self terms");
   if (st != BEM_OK) return st;
   assemble32_kernel<<<(unsigned)((n * n + 255) / 256), 256, 0, s>>>(
-      ctx->geo, K, reinterpret_cast<const float2*>(self32), M);
+      ctx->geo, K, reinterpret_cast<const float2*>(self32), M, ctx->op);
   ctx->launches++;
   return cuda_check(ctx, cudaGetLastError(), "assemble32 kernel");
 }

@@ -88,6 +88,15 @@ __global__ void geometry_kernel(Geometry g, Rule7 rule, int* status) {
     g.cx[c * n + l] = x;
     g.cx32[c * n + l] = (float)x;
   }
+  {
+    // unit normal in the vertex order (the double-layer kernel's n_y)
+    const double inv = 1.0 / (2.0 * area);
+    const double un[3] = {nx * inv, ny * inv, nz * inv};
+    for (int c = 0; c < 3; ++c) {
+      if (g.nrm) g.nrm[c * n + l] = un[c];
+      if (g.pack32) g.pack32[(int64_t)l * 64 + 56 + c] = (float)un[c];
+    }
+  }
   for (int q = 0; q < 7; ++q) {
     for (int c = 0; c < 3; ++c) {
       const double p = rule.bary[q][0] * v[0][c] + rule.bary[q][1] * v[1][c] +
@@ -163,7 +172,9 @@ __global__ void contour_kernel(int N, int kind, double c_re, double c_im, double
 }
 
 // One thread per (panel l, node j).
-__global__ void self_term_kernel(Geometry g, int N, const double* z, GL16 gl, double* self) {
+// T's self entry: c_G times the single-layer self integral plus c_H / 2 (the jump of H).
+__global__ void self_term_kernel(Geometry g, int N, const double* z, GL16 gl, OpCoef op,
+                                 double* self) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= g.n * (int64_t)N) return;
   const int64_t l = t % g.n;
@@ -175,8 +186,8 @@ __global__ void self_term_kernel(Geometry g, int N, const double* z, GL16 gl, do
   }
   for (int c = 0; c < 3; ++c) x[c] = g.cx[c * g.n + l];
   const double2 a = self_term(v, x, make_double2(z[2 * j], z[2 * j + 1]), gl);
-  self[2 * (j * g.n + l)] = a.x;
-  self[2 * (j * g.n + l) + 1] = a.y;
+  self[2 * (j * g.n + l)] = op.cgr * a.x - op.cgi * a.y + 0.5 * op.chr;
+  self[2 * (j * g.n + l) + 1] = op.cgr * a.y + op.cgi * a.x + 0.5 * op.chi;
 }
 
 // Moments of the FP32 self term. With f_g = half * w_g * d the angular weight of node g and
@@ -239,7 +250,8 @@ constexpr float kMomentReach = 3.5f;
 // FP32 table for the mixed path, one thread per (panel l, node j): the moment series in
 // i k rho by Horner's rule, truncated where x^M / (M + 1)! < 1.5e-8 (x = |k| rho), or the
 // 96-node angular quadrature directly when x > kMomentReach or no moments exist.
-__global__ void self_term32_kernel(Geometry g, int N, const double* z, GL16 gl, float* self32) {
+__global__ void self_term32_kernel(Geometry g, int N, const double* z, GL16 gl, OpCoef op,
+                                   float* self32) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= g.n * (int64_t)N) return;
   const int64_t l = t % g.n;
@@ -273,6 +285,9 @@ __global__ void self_term32_kernel(Geometry g, int N, const double* z, GL16 gl, 
     }
     out = self_term32_part(d3, up3, uq3, kr, ki, gl, 0, 1);
   }
+  if (!op_single(op))   // T's self entry: c_G A_ll + c_H / 2
+    out = make_float2((float)op.cgr * out.x - (float)op.cgi * out.y + 0.5f * (float)op.chr,
+                      (float)op.cgr * out.y + (float)op.cgi * out.x + 0.5f * (float)op.chi);
   reinterpret_cast<float2*>(self32)[(int64_t)j * g.n + l] = out;
 }
 
@@ -305,7 +320,7 @@ cudaError_t launch_self_terms32(bem_ctx* ctx, cudaStream_t s) {
   static const GL16 gl = make_gl16();
   const int64_t total = ctx->geo.n * (int64_t)ctx->con.N;
   self_term32_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(ctx->geo, ctx->con.N,
-                                                                     ctx->con.z, gl,
+                                                                     ctx->con.z, gl, ctx->op,
                                                                      ctx->con.self32);
   ctx->launches++;
   return cudaGetLastError();
@@ -314,7 +329,8 @@ cudaError_t launch_self_terms32(bem_ctx* ctx, cudaStream_t s) {
 cudaError_t launch_self32(bem_ctx* ctx, int nk, const double* kz, float* out, cudaStream_t s) {
   static const GL16 gl = make_gl16();
   const int64_t total = ctx->geo.n * (int64_t)nk;
-  self_term32_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(ctx->geo, nk, kz, gl, out);
+  self_term32_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(ctx->geo, nk, kz, gl, ctx->op,
+                                                                     out);
   ctx->launches++;
   return cudaGetLastError();
 }
@@ -323,7 +339,7 @@ cudaError_t launch_self_terms(bem_ctx* ctx, cudaStream_t s) {
   static const GL16 gl = make_gl16();
   const int64_t total = ctx->geo.n * (int64_t)ctx->con.N;
   self_term_kernel<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(ctx->geo, ctx->con.N,
-                                                                   ctx->con.z, gl,
+                                                                   ctx->con.z, gl, ctx->op,
                                                                    ctx->con.self);
   ctx->launches++;
   return cudaGetLastError();

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "bem_gb300.h"
+#include "operator.cuh"
 
 namespace bem {
 
@@ -54,7 +55,9 @@ struct Geometry {
   float* rho32 = nullptr;  // optional, n: largest centroid-to-vertex distance of panel l
   float* pack32 = nullptr; // optional, 64 floats per panel, rows padded to a multiple of 16
                            // panels: 7 x (x_hi, y_hi, z_hi, w) then 7 x (x_lo, y_lo, z_lo, 0)
-                           // (hi + lo = the FP64 quadrature point; w = W_lq / 4 pi)
+                           // (hi + lo = the FP64 quadrature point; w = W_lq / 4 pi), then the
+                           // unit normal (nx, ny, nz) at 56..58
+  double* nrm = nullptr;   // optional, 3 n: unit normal of panel l (vertex order) at c * n + l
 };
 
 struct Contour {
@@ -124,6 +127,9 @@ struct bem_ctx {
   cudaEvent_t con_ev = nullptr;
   // asynchronous mode: bem_cholqr2 does not wait for its status word (bem_check reports it)
   bool async = false;
+  // the boundary operator T = c_G G + c_H (1/2 I + K) (single layer by default)
+  bem::OpCoef op;
+  int64_t op_version = 0;   // bumped by every bem_set_operator
 };
 
 namespace bem {

@@ -170,12 +170,32 @@ __device__ __forceinline__ void add_kernel64(double2& acc, double w, double r, d
   }
 }
 
-// (A_near - A_7)(k) of the pair (x, l), FP64; deriv: its k-derivative.
+// (T_near - T_7)(k) of the pair (x, l), FP64; deriv: its k-derivative.
 __device__ double2 near_corr64(const Geometry& g, int64_t l, const double x[3], double kr,
-                               double ki, bool deriv, const GL8& gl) {
+                               double ki, bool deriv, const GL8& gl, const OpCoef& op) {
   NearFrame F;
   near_frame(g, l, x, F);
   double2 acc = make_double2(0.0, 0.0);
+  if (!op_single(op)) {   // the general operator: both kernels at every point
+    const int64_t n = g.n;
+    const double nx = g.nrm[l], ny = g.nrm[n + l], nz = g.nrm[2 * n + l];
+    for (int p = 0; p < 8; ++p) {
+      const double sp = gl.x[p];
+      for (int q = 0; q < 8; ++q) {
+        const double st = sp * gl.x[q];
+        const double y0 = F.a[0] + sp * F.ab[0] + st * F.bc[0];
+        const double y1 = F.a[1] + sp * F.ab[1] + st * F.bc[1];
+        const double y2 = F.a[2] + sp * F.ab[2] + st * F.bc[2];
+        op_point64(acc, op, gl.w[p] * gl.w[q] * sp * F.scale, y0 - x[0], y1 - x[1], y2 - x[2],
+                   nx, ny, nz, kr, ki, deriv);
+      }
+    }
+    for (int q = 0; q < 7; ++q)
+      op_point64(acc, op, -g.qw[q * n + l], g.qp[q * n + l] - x[0],
+                 g.qp[(7 + q) * n + l] - x[1], g.qp[(14 + q) * n + l] - x[2], nx, ny, nz, kr,
+                 ki, deriv);
+    return acc;
+  }
   for (int p = 0; p < 8; ++p) {
     const double sp = gl.x[p];
     for (int q = 0; q < 8; ++q) {
@@ -235,9 +255,14 @@ __device__ void near_features32(const Geometry& g, int64_t l, const NearFrame& F
 // from the surrogate network when net is non-null (the 7-point part is then h times its
 // output's complement: the network predicts the whole correction divided by h).
 __device__ float2 near_corr32(const Geometry& g, int64_t l, const double x[3], float kr,
-                              float ki, const GL8& gl, const float* __restrict__ net) {
+                              float ki, const GL8& gl, const float* __restrict__ net,
+                              const OpCoef& op) {
   NearFrame F;
   near_frame(g, l, x, F);
+  if (!op_single(op)) {   // the general operator: the FP64 correction, rounded
+    const double2 c = near_corr64(g, l, x, (double)kr, (double)ki, false, gl, op);
+    return make_float2((float)c.x, (float)c.y);
+  }
   if (net) {
     float feat[kNetIn];
     near_features32(g, l, F, x, kr, ki, feat);
@@ -284,7 +309,7 @@ constexpr int kMaxColGroups = kMaxNu / 32;
 __global__ void __launch_bounds__(256)
 near_apply64_kernel(Geometry g, const int32_t* __restrict__ ptr, const int32_t* __restrict__ cols,
                     const double* __restrict__ z, int N, const double2* __restrict__ Vt, int nu,
-                    double2* __restrict__ Y, GL8 gl) {
+                    double2* __restrict__ Y, GL8 gl, OpCoef op) {
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
   const int lane = threadIdx.x % 32;
   const int64_t n = g.n;
@@ -303,7 +328,7 @@ near_apply64_kernel(Geometry g, const int32_t* __restrict__ ptr, const int32_t* 
     int32_t l = 0;
     if (e < e1) {
       l = cols[e];
-      cval = near_corr64(g, l, x, kr, ki, false, gl);
+      cval = near_corr64(g, l, x, kr, ki, false, gl, op);
     }
     const int cnt = min(32, e1 - eb);
     for (int t = 0; t < cnt; ++t) {
@@ -342,7 +367,7 @@ __global__ void __launch_bounds__(256)
 near_apply32_kernel(Geometry g, const int32_t* __restrict__ ptr, const int32_t* __restrict__ cols,
                     const double* __restrict__ z, int N, const float2* __restrict__ Vt, int nu,
                     int nup, int C, int n_pad, float* __restrict__ Yp, int slice, GL8 gl,
-                    const float* __restrict__ net) {
+                    const float* __restrict__ net, OpCoef op) {
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
   const int lane = threadIdx.x % 32;
   const int64_t n = g.n;
@@ -362,7 +387,7 @@ near_apply32_kernel(Geometry g, const int32_t* __restrict__ ptr, const int32_t* 
       int32_t l = 0;
       if (e < e1) {
         l = cols[e];
-        cval = near_corr32(g, l, x, kr, ki, gl, net);
+        cval = near_corr32(g, l, x, kr, ki, gl, net, op);
       }
       const int cnt = min(32, e1 - eb);
       for (int t = 0; t < cnt; ++t) {
@@ -400,7 +425,7 @@ template <bool kDeriv>
 __global__ void __launch_bounds__(256)
 near_percol64_kernel(Geometry g, const int32_t* __restrict__ ptr, const int32_t* __restrict__ cols,
                      const double* __restrict__ lam, int m, const double2* __restrict__ X,
-                     int64_t ldx, double2* __restrict__ R, GL8 gl) {
+                     int64_t ldx, double2* __restrict__ R, GL8 gl, OpCoef op) {
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
   const int lane = threadIdx.x % 32;
   const int64_t n = g.n;
@@ -413,7 +438,7 @@ near_percol64_kernel(Geometry g, const int32_t* __restrict__ ptr, const int32_t*
   const int32_t e0 = ptr[i], e1 = ptr[i + 1];
   for (int32_t e = e0 + lane; e < e1; e += 32) {
     const int32_t l = cols[e];
-    const double2 cv = near_corr64(g, l, x, kr, ki, kDeriv, gl);
+    const double2 cv = near_corr64(g, l, x, kr, ki, kDeriv, gl, op);
     const double2 v = X[(int64_t)c * ldx + l];
     acc.x += cv.x * v.x - cv.y * v.y;
     acc.y += cv.x * v.y + cv.y * v.x;
@@ -487,7 +512,7 @@ __global__ void surrogate_samples_kernel(Geometry g, const int32_t* __restrict__
   float f[kNetIn];
   near_features32(g, l, F, x, (float)kr, (float)ki, f);
   // the features take k h from the float k; the target uses the same rounded k
-  const double2 c = near_corr64(g, l, x, (double)(float)kr, (double)(float)ki, false, gl);
+  const double2 c = near_corr64(g, l, x, (double)(float)kr, (double)(float)ki, false, gl, OpCoef());
   const double h = g.diam[l];
   for (int q = 0; q < kNetIn; ++q) feat[t * kNetIn + q] = f[q];
   target[2 * t] = (float)(c.x / h);
@@ -589,7 +614,7 @@ bem_status near_apply64(bem_ctx* ctx, const double* V, int64_t ldv, int nu, doub
   const int N = ctx->con.N;
   near_apply64_kernel<<<(unsigned)((32 * n * (int64_t)N + 255) / 256), 256, 0, s>>>(
       ctx->geo, ctx->d_near_ptr, ctx->d_near_cols, ctx->con.z, N, Vt, nu,
-      reinterpret_cast<double2*>(Y), gl8());
+      reinterpret_cast<double2*>(Y), gl8(), ctx->op);
   ctx->launches += 2;
   return cuda_check(ctx, cudaGetLastError(), "near field kernels");
 }
@@ -606,7 +631,7 @@ bem_status near_apply32(bem_ctx* ctx, const float2* V32, int nu, int nup, int C,
   const float* net = (ctx->near_mode == 2 && ctx->net_ready) ? ctx->d_net + kNetFloats : nullptr;
   near_apply32_kernel<<<(unsigned)((32 * (int64_t)n_pad * N + 255) / 256), 256, 0, s>>>(
       ctx->geo, ctx->d_near_ptr, ctx->d_near_cols, ctx->con.z, N, Vt, nu, nup, C, n_pad, Yp, slice,
-      gl8(), net);
+      gl8(), net, ctx->op);
   ctx->launches += 2;
   return cuda_check(ctx, cudaGetLastError(), "near field kernels");
 }
@@ -618,11 +643,11 @@ cudaError_t launch_near_percol64(bem_ctx* ctx, int m, const double* lam_dev, con
   if (deriv)
     near_percol64_kernel<true><<<blocks, 256, 0, s>>>(
         ctx->geo, ctx->d_near_ptr, ctx->d_near_cols, lam_dev, m,
-        reinterpret_cast<const double2*>(X), ldx, reinterpret_cast<double2*>(R), gl8());
+        reinterpret_cast<const double2*>(X), ldx, reinterpret_cast<double2*>(R), gl8(), ctx->op);
   else
     near_percol64_kernel<false><<<blocks, 256, 0, s>>>(
         ctx->geo, ctx->d_near_ptr, ctx->d_near_cols, lam_dev, m,
-        reinterpret_cast<const double2*>(X), ldx, reinterpret_cast<double2*>(R), gl8());
+        reinterpret_cast<const double2*>(X), ldx, reinterpret_cast<double2*>(R), gl8(), ctx->op);
   ctx->launches++;
   return cudaGetLastError();
 }
@@ -634,6 +659,9 @@ using namespace bem;
 extern "C" bem_status bem_set_near_field(bem_ctx* ctx, int mode, void* stream) {
   if (!ctx) return BEM_EINVAL;
   if (mode < 0 || mode > 2) return fail(ctx, BEM_EINVAL, "bem_set_near_field: mode must be 0, 1 or 2");
+  if (mode == 2 && !op_single(ctx->op) && (ctx->op.chr != 0.0 || ctx->op.chi != 0.0))
+    return fail(ctx, BEM_EINVAL,
+                "bem_set_near_field: the surrogate (mode 2) covers the single layer only");
   if (mode == 2 && !ctx->net_ready)
     return fail(ctx, BEM_ESTATE, "bem_set_near_field: no surrogate network loaded");
   cudaSetDevice(ctx->device);

@@ -22,10 +22,12 @@ constexpr int kThreads = 256;
 __global__ void __launch_bounds__(kThreads)
 apply_fp64_kernel(Geometry g, const double* __restrict__ self, const double* __restrict__ z,
                   const double* __restrict__ V, int64_t ldv, int nu,
-                  double* __restrict__ Y) {
+                  double* __restrict__ Y, OpCoef op) {
   __shared__ double2 sA[kBM][kBK];
   __shared__ double2 sV[kBK][kVC];
   __shared__ double sQ[4][7][kBK];     // x, y, z, weight of the panel's quadrature points
+  __shared__ double sN[3][kBK];        // unit normals of the panel's triangles
+  const bool general = !op_single(op);
   __shared__ double sC[3][kBM];        // centroids of the tile's rows
 
   const int64_t n = g.n;
@@ -63,6 +65,10 @@ apply_fp64_kernel(Geometry g, const double* __restrict__ self, const double* __r
       sQ[2][q][lc] = ok ? g.qp[(2 * 7 + q) * n + l] : 0.0;
       sQ[3][q][lc] = ok ? g.qw[q * n + l] : 0.0;
     }
+    if (general && tid < 3 * kBK) {
+      const int c = tid / kBK, lc = tid % kBK;
+      sN[c][lc] = (l0 + lc < n) ? g.nrm[c * n + l0 + lc] : 0.0;
+    }
     // V panel (zero outside n x nu)
     for (int t = tid; t < kBK * kVC; t += kThreads) {
       const int k = t / kVC, c = t % kVC;
@@ -86,6 +92,11 @@ apply_fp64_kernel(Geometry g, const double* __restrict__ self, const double* __r
             a = reinterpret_cast<const double2*>(self)[(int64_t)j * n + l];
           } else {
             const double xi = sC[0][rr], yi = sC[1][rr], zi = sC[2][rr];
+            if (general) {   // T = c_G G + c_H (1/2 I + K)
+              for (int q = 0; q < 7; ++q)
+                op_point64(a, op, sQ[3][q][el], sQ[0][q][el] - xi, sQ[1][q][el] - yi,
+                           sQ[2][q][el] - zi, sN[0][el], sN[1][el], sN[2][el], kr, ki, false);
+            } else
             for (int q = 0; q < 7; ++q) {
               const double dx = xi - sQ[0][q][el], dy = yi - sQ[1][q][el], dz = zi - sQ[2][q][el];
               const double r = sqrt(dx * dx + dy * dy + dz * dz);
@@ -185,7 +196,8 @@ cudaError_t launch_apply_fp64(bem_ctx* ctx, const double* V, int64_t ldv, int nu
                               cudaStream_t s) {
   const int64_t n = ctx->geo.n;
   dim3 grid((unsigned)((n + kBM - 1) / kBM), (unsigned)ctx->con.N, (unsigned)((nu + kVC - 1) / kVC));
-  apply_fp64_kernel<<<grid, kThreads, 0, s>>>(ctx->geo, ctx->con.self, ctx->con.z, V, ldv, nu, Y);
+  apply_fp64_kernel<<<grid, kThreads, 0, s>>>(ctx->geo, ctx->con.self, ctx->con.z, V, ldv, nu, Y,
+                                              ctx->op);
   ctx->launches++;
   return cudaGetLastError();
 }

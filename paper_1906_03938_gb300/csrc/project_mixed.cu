@@ -74,6 +74,7 @@ struct MixedParams {
   int64_t b_node_stride;    // bytes between the nodes' basis planes (0: one X for all)
   int gchunk;               // node groups per unit (sum mode): a unit runs its K-blocks for
   int ngc;                  // each of its groups in turn; ngc = ceil(nG / gchunk) chunks
+  OpCoef op;                // T = c_G G + c_H (1/2 I + K) (the kOp instantiations)
   const __nv_bfloat16* Bp;   // prepared basis planes, tile-native
   float* Yp;          // FP32 partial products [S][N][2 nup][n_pad]
   int* status;
@@ -152,6 +153,20 @@ __device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c) {
   return r;
 }
 
+// General operator: (sr, si) += a (cs + i sn) F, F = c_G + c_H s (i k r - 1) for the two
+// columns at once; s = (y - x).n / r^2, ph = Re(k) r, kir = Im(k) r, m1 = (-1, -1).
+__device__ __forceinline__ void op_acc2(f2_t& sr, f2_t& si, f2_t a, f2_t cs, f2_t sn, f2_t s,
+                                       f2_t ph, f2_t kir, f2_t cgr2, f2_t cgi2, f2_t chr2,
+                                       f2_t chi2, f2_t nchi2, f2_t m1) {
+  const f2_t A = mul2(fma2(s, kir, s), m1);   // -s (1 + Im(k) r)
+  const f2_t B = mul2(s, ph);                 //  s Re(k) r
+  const f2_t fr = fma2(chr2, A, fma2(nchi2, B, cgr2));
+  const f2_t fi = fma2(chr2, B, fma2(chi2, A, cgi2));
+  const f2_t cr = mul2(a, cs), ci = mul2(a, sn);
+  sr = fma2(cr, fr, fma2(mul2(ci, m1), fi, sr));
+  si = fma2(cr, fi, fma2(ci, fr, si));
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
   __nv_bfloat162 h = __floats2bfloat162_rn(lo_elem, hi_elem);   // .x -> low 16 bits
   return *reinterpret_cast<uint32_t*>(&h);
@@ -213,8 +228,9 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
 // tmem_given: TMEM columns already allocated by a persistent caller (its base address), or
 // kNoTmem to allocate (and release) them here.
 constexpr uint32_t kNoTmem = 0xffffffffu;
-// kSum: the node-summed mode (p.sum is set accordingly by the host)
-template <bool kSum>
+// kSum: the node-summed mode (p.sum is set accordingly by the host); kOp: the general
+// operator c_G G + c_H (1/2 I + K) (else the single layer, c_G = 1, c_H = 0)
+template <bool kSum, bool kOp = false>
 __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int u,
                                                  const uint32_t tmem_given) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -393,6 +409,7 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
     const int e = warp - 2;               // 0..15: row group of the 128 x 16 block
     // node constants
     float kr[kMaxG], kmi[kMaxG];
+    float kim[kOp ? kMaxG : 1];   // Im z_j (general operator)
     float2 cf[kSum ? kMaxG : 1];
     bool twin[kMaxG / 2];
     constexpr bool scaled = kSum;
@@ -405,6 +422,7 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
         if (kSum) cf[kSum ? g : 0] = p.coef[j];
         kr[g] = (float)p.z[2 * j];
         kmi[g] = (float)(-p.z[2 * j + 1]) * kLog2e;
+        if (kOp) kim[kOp ? g : 0] = (float)p.z[2 * j + 1];
         // a twin pair sits at slots 2 P, 2 P + 1 of the schedule: inside this group when
         // the group starts at an even slot
         if (g % 2 == 0)
@@ -413,6 +431,11 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
       }
     };
     load_nodes(j0, Gv);
+    // operator constants (kOp): F = c_G + c_H s (i k r - 1) per point, s = (y - x).n / r^2
+    const f2_t m1 = f2(-1.f, -1.f);
+    const f2_t cgr2 = f2((float)p.op.cgr, (float)p.op.cgr), cgi2 = f2((float)p.op.cgi, (float)p.op.cgi);
+    const f2_t chr2 = f2((float)p.op.chr, (float)p.op.chr), chi2 = f2((float)p.op.chi, (float)p.op.chi);
+    const f2_t nchi2 = f2(-(float)p.op.chi, -(float)p.op.chi);
     // this thread's entries: row 8 e + r8, columns 8 kg + 2 kp + {0, 1} for kg = 0, 1
     const int r8 = lane / 4, kp = lane % 4;
     const int row = 8 * e + r8;
@@ -438,10 +461,19 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
         const int64_t l0 = (int64_t)kb * kBK + k0;
         // distances and weights of the 7 points of both columns, as pairs (column k0, k0 + 1)
         f2_t rr2[7], am2[7];
+        f2_t s2[kOp ? 7 : 1];   // (y - x) . n / r^2 of both columns (general operator)
         {
           const float4* c0 = sCol + k0 * 7;
           const float4* c1 = c0 + 7;
           const f2_t xx = f2(xr.x, xr.x), xy = f2(xr.y, xr.y), xz = f2(xr.z, xr.z);
+          // the columns' normals, negated (d = x - y here), from the staged packed geometry
+          f2_t nnx = f2(0.f, 0.f), nny = nnx, nnz = nnx;
+          if (kOp) {
+            const float* gk = sGraw + s * (kBK * 64) + k0 * 64;
+            nnx = f2(-gk[56], -gk[64 + 56]);
+            nny = f2(-gk[57], -gk[64 + 57]);
+            nnz = f2(-gk[58], -gk[64 + 58]);
+          }
 #pragma unroll
           for (int q = 0; q < 7; ++q) {
             const float4 y0 = c0[q], y1 = c1[q];
@@ -453,6 +485,8 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
             const f2_t rs = f2(rsqrtf_mufu(r20), rsqrtf_mufu(r21));
             rr2[q] = mul2(r2, rs);
             am2[q] = mul2(f2(y0.w, y1.w), rs);
+            if (kOp)
+              s2[kOp ? q : 0] = mul2(fma2(dx, nnx, fma2(dy, nny, mul2(dz, nnz))), mul2(rs, rs));
           }
         }
         const uint32_t off = e * 256 + kg * 128 + r8 * 16 + kp * 4;
@@ -472,13 +506,22 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
               f2split(mul2(kmb, rr2[q]), e2, e3);
               const f2_t aa = mul2(am2[q], f2(ex2f(e0), ex2f(e1)));
               const f2_t ab = mul2(am2[q], f2(ex2f(e2), ex2f(e3)));
-              f2split(mul2(kr2, rr2[q]), p0, p1);
+              const f2_t ph2 = mul2(kr2, rr2[q]);
+              f2split(ph2, p0, p1);
               const f2_t cs = f2(cosf_mufu(p0), cosf_mufu(p1));
               const f2_t sn = f2(sinf_mufu(p0), sinf_mufu(p1));
-              sa = fma2(aa, cs, sa);
-              ia = fma2(aa, sn, ia);
-              sb = fma2(ab, cs, sb);
-              ib = fma2(ab, sn, ib);
+              if constexpr (kOp) {
+                op_acc2(sa, ia, aa, cs, sn, s2[q], ph2,
+                        mul2(f2(kim[g], kim[g]), rr2[q]), cgr2, cgi2, chr2, chi2, nchi2, m1);
+                op_acc2(sb, ib, ab, cs, sn, s2[q], ph2,
+                        mul2(f2(kim[g + 1], kim[g + 1]), rr2[q]), cgr2, cgi2, chr2, chi2, nchi2,
+                        m1);
+              } else {
+                sa = fma2(aa, cs, sa);
+                ia = fma2(aa, sn, ia);
+                sb = fma2(ab, cs, sb);
+                ib = fma2(ab, sn, ib);
+              }
             }
             put_entries(sa, ia, selfk + g, i, l0, p.n, a_stage + g * 4 * kPlaneBytes + off,
                         scaled, cf[kSum ? g : 0]);
@@ -499,9 +542,16 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
                 // that reduction's error (half an FP32 ulp of ph / 2 pi) is of the order of
                 // the rounding of ph itself, so no explicit reduction precedes them
                 float p0, p1;
-                f2split(mul2(kr2, rr2[q]), p0, p1);
-                sr2 = fma2(a, f2(cosf_mufu(p0), cosf_mufu(p1)), sr2);
-                si2 = fma2(a, f2(sinf_mufu(p0), sinf_mufu(p1)), si2);
+                const f2_t ph2 = mul2(kr2, rr2[q]);
+                f2split(ph2, p0, p1);
+                if constexpr (kOp) {
+                  op_acc2(sr2, si2, a, f2(cosf_mufu(p0), cosf_mufu(p1)),
+                          f2(sinf_mufu(p0), sinf_mufu(p1)), s2[q], ph2,
+                          mul2(f2(kim[h], kim[h]), rr2[q]), cgr2, cgi2, chr2, chi2, nchi2, m1);
+                } else {
+                  sr2 = fma2(a, f2(cosf_mufu(p0), cosf_mufu(p1)), sr2);
+                  si2 = fma2(a, f2(sinf_mufu(p0), sinf_mufu(p1)), si2);
+                }
               }
               put_entries(sr2, si2, selfk + h, i, l0, p.n, a_stage + h * 4 * kPlaneBytes + off,
                           scaled, cf[kSum ? h : 0]);
@@ -550,14 +600,16 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
   }
 }
 
+template <bool kOp>
 __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p) {
-  mixed_apply_unit<false>(p, blockIdx.x, kNoTmem);
+  mixed_apply_unit<false, kOp>(p, blockIdx.x, kNoTmem);
 }
 
 // Node-summed form: Y = sum_j c_j A(z_j) X_j (the right-hand side of an inverse power
 // step, X_j per node) or (sum_j c_j A(z_j)) X (one X: the Schur complement S applied).
+template <bool kOp>
 __global__ void __launch_bounds__(kThreads, 1) mixed_sum_kernel(MixedParams p) {
-  mixed_apply_unit<true>(p, blockIdx.x, kNoTmem);
+  mixed_apply_unit<true, kOp>(p, blockIdx.x, kNoTmem);
 }
 
 // Persistent grouped kernel over several problems: one CTA per SM takes work units from a
@@ -1144,6 +1196,7 @@ bem_status mixed_plan(bem_ctx* ctx, const double* V, int64_t ldv, int nu, int S,
   p.z = ctx->con.z;
   p.order = ctx->con.order;
   p.status = ctx->d_status;
+  p.op = ctx->op;
   plan.V = V;
   plan.ldv = ldv;
   plan.V32 = reinterpret_cast<float2*>(scr + v32_off);
@@ -1190,10 +1243,14 @@ void mixed_post(bem_ctx* ctx, const MixedPlan& plan, double* Bhat, double* AV, c
 }
 
 bem_status set_mixed_smem(bem_ctx* ctx, uint32_t bytes) {
-  bem_status st = cuda_check(ctx, cudaFuncSetAttribute(mixed_apply_kernel,
+  bem_status st = cuda_check(ctx, cudaFuncSetAttribute(mixed_apply_kernel<false>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                        (int)bytes),
                              "mixed kernel attribute");
+  if (st != BEM_OK) return st;
+  st = cuda_check(ctx, cudaFuncSetAttribute(mixed_apply_kernel<true>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes),
+                  "mixed kernel attribute");
   if (st != BEM_OK) return st;
   for (const void* f : {(const void*)mixed_vhy_tc_kernel<1>, (const void*)mixed_vhy_tc_kernel<2>,
                         (const void*)mixed_vhy_tc_kernel<4>}) {
@@ -1357,6 +1414,7 @@ bem_status mixed_sum_apply(bem_ctx* ctx, const float2* X, int64_t ldx, int64_t n
   p.z = ctx->con.z;
   p.order = ctx->con.order;
   p.status = ctx->d_status;
+  p.op = ctx->op;
   bem_status st = ensure_self32(ctx, s);
   if (st != BEM_OK) return st;
   p.self32 = reinterpret_cast<const float2*>(ctx->con.self32);
@@ -1368,12 +1426,12 @@ bem_status mixed_sum_apply(bem_ctx* ctx, const float2* X, int64_t ldx, int64_t n
   const int64_t prep = (int64_t)plan.nnodes * p.nK * kBK * p.nup;
   prep_planes32_kernel<<<(unsigned)((prep + 255) / 256), 256, 0, s>>>(
       X, ldx, node_stride, p.n, nu, p.nup, p.C, p.nK, plan.nnodes, Bp);
-  st = cuda_check(ctx, cudaFuncSetAttribute(mixed_sum_kernel,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+  auto* sum_kern = op_single(ctx->op) ? mixed_sum_kernel<false> : mixed_sum_kernel<true>;
+  st = cuda_check(ctx, cudaFuncSetAttribute(sum_kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)plan.L.total),
                   "mixed kernel attribute");
   if (st != BEM_OK) return st;
-  mixed_sum_kernel<<<(unsigned)plan.units, kThreads, plan.L.total, s>>>(p);
+  sum_kern<<<(unsigned)plan.units, kThreads, plan.L.total, s>>>(p);
   sum_slices_kernel<<<(unsigned)((p.n * nu + 255) / 256), 256, 0, s>>>(
       p.Yp, plan.slices, 2 * p.nup, p.C, p.n, p.n_pad, nu, out);
   ctx->launches += 3;
@@ -1388,7 +1446,10 @@ bem_status project_mixed(bem_ctx* ctx, const double* V, int64_t ldv, int nu, dou
   mixed_pre(ctx, plan, s);
   if ((st = set_mixed_smem(ctx, plan.L.total)) != BEM_OK) return st;
   timing_begin(ctx, s);
-  mixed_apply_kernel<<<(unsigned)plan.units, kThreads, plan.L.total, s>>>(plan.p);
+  if (op_single(ctx->op))
+    mixed_apply_kernel<false><<<(unsigned)plan.units, kThreads, plan.L.total, s>>>(plan.p);
+  else
+    mixed_apply_kernel<true><<<(unsigned)plan.units, kThreads, plan.L.total, s>>>(plan.p);
   timing_end(ctx, s);
   ctx->launches++;
   st = cuda_check(ctx, cudaGetLastError(), "mixed apply kernel");
@@ -1514,7 +1575,8 @@ bem_status batch_launch(bem_batch* b, cudaStream_t s) {
   for (int k = 0; k < b->nprob; ++k)
     if (b->ctx[k]->mesh_version != b->mesh_ver[k] ||
         b->ctx[k]->contour_version != b->contour_ver[k] ||
-        b->ctx[k]->d_scratch != b->scratch[k] || !b->ctx[k]->con.self32_ready)
+        b->ctx[k]->d_scratch != b->scratch[k] || !b->ctx[k]->con.self32_ready ||
+        !op_single(b->ctx[k]->op))
       return fail(c0, BEM_ESTATE,
                   "bem_batch_run: a context's mesh, contour or workspace changed since the "
                   "batch was created");
@@ -1584,6 +1646,8 @@ bem_status bem_batch_create(bem_ctx* const* ctxs, int nprob, const double* const
       return bem::fail(c0, BEM_ESTATE, "bem_batch_create: every context needs a mesh and a contour");
     if (c->near_mode != 0)
       return bem::fail(c0, BEM_EINVAL, "bem_batch_create: near-field treatment is not batched");
+    if (!bem::op_single(c->op))
+      return bem::fail(c0, BEM_EINVAL, "bem_batch_create: the batched launch covers the single layer");
     if (!V_dev[k] || !Bhat_dev[k] || nu[k] < 1 || nu[k] > bem::kMaxNu || ldv[k] < c->geo.n ||
         nu[k] > c->geo.n)
       return bem::fail(c0, BEM_EINVAL, "bem_batch_create: bad V, Bhat, ldv or nu");

@@ -21,8 +21,10 @@ constexpr int kChunk = 128;
 template <bool kDeriv>
 __global__ void __launch_bounds__(kRowsPerBlock)
 residual_kernel(Geometry g, const double* __restrict__ lam, const double* __restrict__ X,
-                int64_t ldx, double* __restrict__ R) {
+                int64_t ldx, double* __restrict__ R, OpCoef op) {
   __shared__ double sQ[4][7][kChunk];
+  __shared__ double sN[3][kChunk];
+  const bool general = !op_single(op);
   __shared__ double2 sX[kChunk];
   const int64_t n = g.n;
   const int c = blockIdx.y;
@@ -49,6 +51,8 @@ residual_kernel(Geometry g, const double* __restrict__ lam, const double* __rest
     for (int t = threadIdx.x; t < kChunk; t += blockDim.x) {
       const int64_t l = l0 + t;
       sX[t] = (l < n) ? x[l] : make_double2(0.0, 0.0);
+      if (general)
+        for (int c2 = 0; c2 < 3; ++c2) sN[c2][t] = (l < n) ? g.nrm[c2 * n + l] : 0.0;
     }
     __syncthreads();
     if (i < n) {
@@ -60,6 +64,11 @@ residual_kernel(Geometry g, const double* __restrict__ lam, const double* __rest
           continue;
         }
         double2 a = make_double2(0.0, 0.0);
+        if (general) {   // T = c_G G + c_H (1/2 I + K), or its k-derivative
+          for (int q = 0; q < 7; ++q)
+            op_point64(a, op, sQ[3][q][lc], sQ[0][q][lc] - xi, sQ[1][q][lc] - yi,
+                       sQ[2][q][lc] - zi, sN[0][lc], sN[1][lc], sN[2][lc], kr, ki, kDeriv);
+        } else
         for (int q = 0; q < 7; ++q) {
           const double dx = xi - sQ[0][q][lc], dy = yi - sQ[1][q][lc], dz = zi - sQ[2][q][lc];
           const double r = sqrt(dx * dx + dy * dy + dz * dz);
@@ -93,7 +102,7 @@ residual_kernel(Geometry g, const double* __restrict__ lam, const double* __rest
 // Self term A_ii(lambda_c) (or its k-derivative) of every row, written into R as the
 // multiplier of x_i.
 __global__ void self_at_kernel(Geometry g, const double* __restrict__ lam, GL16 gl,
-                               double* __restrict__ R, bool deriv) {
+                               double* __restrict__ R, bool deriv, OpCoef op) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int c = blockIdx.y;
   if (i >= g.n) return;
@@ -103,8 +112,11 @@ __global__ void self_at_kernel(Geometry g, const double* __restrict__ lam, GL16 
     for (int d = 0; d < 3; ++d) v[e][d] = g.xyz[3 * (int64_t)vi + d];
   }
   for (int d = 0; d < 3; ++d) x[d] = g.cx[d * g.n + i];
+  // T's self entry: c_G A_ii (+ c_H / 2, whose k-derivative is 0)
+  const double2 a = self_term(v, x, make_double2(lam[2 * c], lam[2 * c + 1]), gl, deriv);
   reinterpret_cast<double2*>(R)[(int64_t)c * g.n + i] =
-      self_term(v, x, make_double2(lam[2 * c], lam[2 * c + 1]), gl, deriv);
+      make_double2(op.cgr * a.x - op.cgi * a.y + (deriv ? 0.0 : 0.5 * op.chr),
+                   op.cgr * a.y + op.cgi * a.x + (deriv ? 0.0 : 0.5 * op.chi));
 }
 
 __global__ void norms_kernel(const double* __restrict__ R, const double* __restrict__ X,
@@ -141,12 +153,12 @@ cudaError_t launch_apply_percol64(bem_ctx* ctx, int m, const double* lam_dev, co
   static const GL16 gl = make_gl16();
   const int64_t n = ctx->geo.n;
   dim3 g1((unsigned)((n + 127) / 128), (unsigned)m);
-  self_at_kernel<<<g1, 128, 0, s>>>(ctx->geo, lam_dev, gl, R, deriv);
+  self_at_kernel<<<g1, 128, 0, s>>>(ctx->geo, lam_dev, gl, R, deriv, ctx->op);
   dim3 g2((unsigned)((n + kRowsPerBlock - 1) / kRowsPerBlock), (unsigned)m);
   if (deriv)
-    residual_kernel<true><<<g2, kRowsPerBlock, 0, s>>>(ctx->geo, lam_dev, X, ldx, R);
+    residual_kernel<true><<<g2, kRowsPerBlock, 0, s>>>(ctx->geo, lam_dev, X, ldx, R, ctx->op);
   else
-    residual_kernel<false><<<g2, kRowsPerBlock, 0, s>>>(ctx->geo, lam_dev, X, ldx, R);
+    residual_kernel<false><<<g2, kRowsPerBlock, 0, s>>>(ctx->geo, lam_dev, X, ldx, R, ctx->op);
   ctx->launches += 2;
   if (near_active(ctx)) return launch_near_percol64(ctx, m, lam_dev, X, ldx, R, deriv, s);
   return cudaGetLastError();

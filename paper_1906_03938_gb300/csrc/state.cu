@@ -1,11 +1,13 @@
 // Context state: statistics, and a checkpoint of everything that defines the operator and
 // the contour (mesh, contour, near-field mode, surrogate network) for resuming elsewhere.
 //
-// Checkpoint layout (little-endian host bytes): the 8-byte tag "BEMSTAT1", then int64 nv,
+// Checkpoint layout (little-endian host bytes): the 8-byte tag "BEMSTAT2", then int64 nv,
 // int64 nt, int64 N, int64 contour kind, int64 near-field mode, int64 network floats (0 or
-// the network size), double c_re, c_im, a, b; then xyz (3 nv doubles), tri (3 nt int32),
-// the network's master parameters (floats). Workspaces, self-term tables, pair lists and
-// timing records are rebuilt, not stored.
+// the network size), double c_re, c_im, a, b, double c_G (re, im), c_H (re, im) of the
+// operator; then xyz (3 nv doubles), tri (3 nt int32), the network's master parameters
+// (floats). States written before the operator existed ("BEMSTAT1": the same without the
+// operator's four doubles) load as the single layer. Workspaces, self-term tables, pair
+// lists and timing records are rebuilt, not stored.
 #include <string.h>
 
 #include <vector>
@@ -17,12 +19,19 @@ using namespace bem;
 
 namespace {
 
-constexpr char kTag[8] = {'B', 'E', 'M', 'S', 'T', 'A', 'T', '1'};
+constexpr char kTag[8] = {'B', 'E', 'M', 'S', 'T', 'A', 'T', '2'};
+constexpr char kTag1[8] = {'B', 'E', 'M', 'S', 'T', 'A', 'T', '1'};
 
+struct Header1 {
+  char tag[8];
+  int64_t nv, nt, N, kind, near_mode, net_floats;
+  double c_re, c_im, a, b;
+};
 struct Header {
   char tag[8];
   int64_t nv, nt, N, kind, near_mode, net_floats;
   double c_re, c_im, a, b;
+  double op[4];   // c_G (re, im), c_H (re, im)
 };
 
 }  // namespace
@@ -73,6 +82,10 @@ bem_status bem_save_state(bem_ctx* ctx, void* buf, size_t* len, void* stream) {
   h.c_im = ctx->con.c_im;
   h.a = ctx->con.a;
   h.b = ctx->con.b;
+  h.op[0] = ctx->op.cgr;
+  h.op[1] = ctx->op.cgi;
+  h.op[2] = ctx->op.chr;
+  h.op[3] = ctx->op.chi;
   unsigned char* p = static_cast<unsigned char*>(buf);
   memcpy(p, &h, sizeof(h));
   p += sizeof(h);
@@ -93,18 +106,29 @@ bem_status bem_save_state(bem_ctx* ctx, void* buf, size_t* len, void* stream) {
 
 bem_status bem_load_state(bem_ctx* ctx, const void* buf, size_t len, void* stream) {
   if (!ctx) return BEM_EINVAL;
-  if (!buf || len < sizeof(Header)) return fail(ctx, BEM_EINVAL, "bem_load_state: truncated state");
+  if (!buf || len < sizeof(Header1)) return fail(ctx, BEM_EINVAL, "bem_load_state: truncated state");
   Header h;
-  memcpy(&h, buf, sizeof(h));
-  if (memcmp(h.tag, kTag, 8) != 0) return fail(ctx, BEM_EINVAL, "bem_load_state: not a saved state");
+  size_t hsize = sizeof(Header);
+  if (memcmp(buf, kTag1, 8) == 0) {   // written before the operator existed: single layer
+    Header1 h1;
+    memcpy(&h1, buf, sizeof(h1));
+    memcpy(&h, &h1, sizeof(h1));
+    h.op[0] = 1.0;
+    h.op[1] = h.op[2] = h.op[3] = 0.0;
+    hsize = sizeof(Header1);
+  } else {
+    if (len < sizeof(Header)) return fail(ctx, BEM_EINVAL, "bem_load_state: truncated state");
+    memcpy(&h, buf, sizeof(h));
+    if (memcmp(h.tag, kTag, 8) != 0) return fail(ctx, BEM_EINVAL, "bem_load_state: not a saved state");
+  }
   if (h.nv < 3 || h.nt < 1 || h.nv > (int64_t)1 << 31 || h.nt > (int64_t)1 << 31 || h.N < 0 ||
       h.N > kMaxNodes || h.near_mode < 0 || h.near_mode > 2 ||
       (h.net_floats != 0 && h.net_floats != kNetFloats))
     return fail(ctx, BEM_EINVAL, "bem_load_state: corrupt header");
-  const size_t need = sizeof(Header) + (size_t)3 * h.nv * sizeof(double) +
+  const size_t need = hsize + (size_t)3 * h.nv * sizeof(double) +
                       (size_t)3 * h.nt * sizeof(int32_t) + (size_t)h.net_floats * sizeof(float);
   if (len < need) return fail(ctx, BEM_EINVAL, "bem_load_state: truncated state");
-  const unsigned char* p = static_cast<const unsigned char*>(buf) + sizeof(Header);
+  const unsigned char* p = static_cast<const unsigned char*>(buf) + hsize;
   std::vector<double> xyz(3 * h.nv);
   std::vector<int32_t> tri(3 * h.nt);
   memcpy(xyz.data(), p, xyz.size() * sizeof(double));
@@ -113,6 +137,12 @@ bem_status bem_load_state(bem_ctx* ctx, const void* buf, size_t len, void* strea
   p += tri.size() * sizeof(int32_t);
   // the mesh first (this clears the contour), then the network, contour and near field
   bem_status st = bem_set_mesh(ctx, h.nv, xyz.data(), h.nt, tri.data(), stream);
+  if (st != BEM_OK) return st;
+  if (ctx->near_mode == 2) {   // mode 2 would refuse a double-layer operator: reset it first
+    st = bem_set_near_field(ctx, 0, stream);
+    if (st != BEM_OK) return st;
+  }
+  st = bem_set_operator(ctx, h.op[0], h.op[1], h.op[2], h.op[3]);
   if (st != BEM_OK) return st;
   if (h.net_floats) {
     std::vector<float> net(h.net_floats);
