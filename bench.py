@@ -53,6 +53,9 @@ def parse():
                    choices=["cube3072", "sphere20480", "ellipsoid98304", "batch48"])
     p.add_argument("--near", type=int, default=None, choices=[0, 1, 2],
                    help="near-field mode (default: 1 for sphere20480 and ellipsoid98304, else 0)")
+    p.add_argument("--operator", default="single", choices=["single", "neumann", "robin"],
+                   help="boundary operator: single layer (default), double layer with its jump "
+                        "(Neumann), or Robin 0.5 G + (1/2 I + K)")
     p.add_argument("--inverse-power", type=int, default=0, metavar="Q",
                    help="instead of the projection bench: time Q steps of Algorithm 1 on the "
                         "workload, dense (FP32 LU of S) against matrix-free (GMRES)")
@@ -390,6 +393,8 @@ def run_ours(args):
     if near_mode == 2:
         surrogate = train_surrogate(bem, local)      # untimed: data generation and training
         ctx.surrogate_set(surrogate["params"])
+    OPS = {"single": (1.0, 0.0), "neumann": (0.0, 1.0), "robin": (0.5, 1.0)}
+    ctx.set_operator(*OPS[args.operator])
     if near_mode:
         ctx.set_mesh(mesh.xyz, mesh.tri)
         ctx.set_near_field(near_mode)
@@ -536,7 +541,8 @@ def run_ours(args):
     # oracle's discrete eigenvalues stored under tests/golden
     eig = None
     golden = os.path.join(ROOT, "tests", "golden", f"eigs_{args.workload}.txt")
-    if not args.no_eig_check and os.path.exists(golden) and not near_mode:
+    if not args.no_eig_check and os.path.exists(golden) and not near_mode and \
+            args.operator == "single":
         t0 = time.perf_counter()
         lam, X, rel = ctx.solve(V_res, q=10, precision=prec, tol=1e-14)
         torch.cuda.synchronize()
@@ -564,7 +570,7 @@ def run_ours(args):
                            ") + reduced solve + FP64 refinement"}
 
     cpu = None
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and args.operator == "single":
         cpu = oracle_sample(prob, mesh, V)
 
     bi = V.nbytes + mesh.xyz.nbytes + mesh.tri.nbytes
@@ -578,6 +584,7 @@ def run_ours(args):
                    "contour": f"{c.kind} c={c.centre.real:g} a={c.a:g} b={c.b:g}",
                    "precision": args.precision,
                    "near_field": ["off", "8x8 rule", "surrogate network"][near_mode],
+                   "operator": args.operator,
                    "parallelism": f"replicas{world}", "l2": "flushed between steps (512 MB write)",
                    "wall_s_timed": wall},
         "roofline": roof,
