@@ -314,7 +314,12 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
                         (float)(p.cx[2 * p.n + i] - oz), 1.f);
       sRow[r] = v;
     }
-    int issued = 0;
+    // per iteration, with fewer than kMaxG nodes per unit (a short evaluation per K-block):
+    // the column geometry as soon as the evaluation warps are done with the stage (afull of
+    // the previous round), the basis planes once the MMAs are (empty); with kMaxG nodes both
+    // once the MMAs are done (the evaluation is long enough to hide the copies)
+    const bool early = p.G < kMaxG;
+    int issued_g = 0, issued_b = 0;
     for (int it = 0; it < nit; ++it) {
       const int s = it % kStages;
       const uint32_t par = (it / kStages) & 1;
@@ -322,25 +327,33 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
       const int j0i = kSum ? (g_begin + it / nkb) * p.G : j0;
       const int Gvi = kSum ? min(p.G, p.N - j0i) : Gv;
       int ok = 1;
-      if (lane == 0) ok = wait_or_abort(&empty[s], par ^ 1, abort_flag, p.status);
+      if (lane == 0)
+        ok = early ? wait_or_abort(&afull[s], par ^ 1, abort_flag, p.status)
+                   : wait_or_abort(&empty[s], par ^ 1, abort_flag, p.status);
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
-      if (lane == 0) {
-        const uint32_t bset = 256u * p.nup;   // one node's (or the shared) planes
-        const int nb = bnodes > 1 ? Gvi : 1;
-        mbar_arrive_expect_tx(&bfull[s], (uint32_t)nb * bset);
-        for (int g = 0; g < nb; ++g) {
-          const size_t node_off =
-              bnodes > 1 ? (size_t)(p.order[j0i + g] & kNodeMask) * (size_t)p.b_node_stride : 0;
-          bulk_g2s(sB + s * L.b_stage_bytes + g * bset,
-                   reinterpret_cast<const unsigned char*>(p.Bp) + node_off + (size_t)kb * bset,
-                   bset, &bfull[s]);
+      auto issue_b = [&]() {
+        if (lane == 0) {
+          const uint32_t bset = 256u * p.nup;   // one node's (or the shared) planes
+          const int nb = bnodes > 1 ? Gvi : 1;
+          mbar_arrive_expect_tx(&bfull[s], (uint32_t)nb * bset);
+          for (int g = 0; g < nb; ++g) {
+            const size_t node_off =
+                bnodes > 1 ? (size_t)(p.order[j0i + g] & kNodeMask) * (size_t)p.b_node_stride : 0;
+            bulk_g2s(sB + s * L.b_stage_bytes + g * bset,
+                     reinterpret_cast<const unsigned char*>(p.Bp) + node_off + (size_t)kb * bset,
+                     bset, &bfull[s]);
+          }
         }
+        ++issued_b;
+      };
+      if (!early) issue_b();   // the stage is free of the MMAs already
+      if (lane == 0) {
         mbar_arrive_expect_tx(&gready[s], kGeoBlockBytes);
         bulk_g2s(smem + L.graw_off + s * kGeoBlockBytes, p.pack32 + (size_t)kb * kBK * 64,
                  kGeoBlockBytes, &gready[s]);
       }
-      ++issued;
+      ++issued_g;
       // tile-relative FP32 coordinates from the hi/lo pairs: (y_hi - o_hi) + (y_lo - o_lo)
       if (!wait_or_abort(&gready[s], par, abort_flag, p.status)) break;
       const float* graw = sGraw + s * (kBK * 64);
@@ -362,13 +375,19 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
         sSelf[x] = v;
       }
       mbar_arrive(&gfull[s]);   // release: the staged values are visible to the waiters
+      if (early) {
+        if (lane == 0) ok = wait_or_abort(&empty[s], par ^ 1, abort_flag, p.status);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        issue_b();
+      }
     }
     if (lane == 0 && *abort_flag) {
       // let copies in flight land before the block exits (bounded)
-      for (int it = max(0, issued - kStages); it < issued; ++it) {
+      for (int it = max(0, issued_b - kStages); it < issued_b; ++it)
         mbar_wait(&bfull[it % kStages], (it / kStages) & 1, kWaitLimit);
+      for (int it = max(0, issued_g - kStages); it < issued_g; ++it)
         mbar_wait(&gready[it % kStages], (it / kStages) & 1, kWaitLimit);
-      }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -450,7 +469,12 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
         Gvc = min(p.G, p.N - j0x);
         load_nodes(j0x, Gvc);
       }
-      const bool ready = wait_or_abort(&gfull[s], par, abort_flag, p.status);
+      // the column geometry, and the stage's A planes free of the MMAs of its last round
+      // (one lane per warp observes the MMAs' completion; the warp synchronises on it)
+      int free_ok = 1;
+      if (p.G < kMaxG && lane == 0) free_ok = wait_or_abort(&empty[s], par ^ 1, abort_flag, p.status);
+      free_ok = __shfl_sync(0xffffffffu, free_ok, 0);
+      const bool ready = wait_or_abort(&gfull[s], par, abort_flag, p.status) && free_ok;
       const float4* sCol = sColAll + s * (kBK * 7);
       const float2* sSelf = sSelfAll + s * (kBK * kMaxG);
       unsigned char* a_stage = sA + s * L.a_stage_bytes;
