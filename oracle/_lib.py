@@ -41,6 +41,7 @@ def lib():
         L.oracle_matrix_op.argtypes = [P, i64, P, d, d, i32, i64, i64, P, i32, i32, P]
         L.oracle_apply_op.argtypes = [P, i64, P, i32, P, i32, P, i64, i64, P, i32, i32, P]
         L.oracle_near_rule_kind.argtypes = [P, P, P, P, d, d, i32, i32, i32, P]
+        L.oracle_entries.argtypes = [P, i64, P, d, d, P, P, i64, P, i32, P]
         L.oracle_max_threads.restype = i32
         _lib = L
     return _lib

@@ -111,3 +111,18 @@ def near_pairs(mesh, rows=None):
     cols = np.zeros(int(row_ptr[-1]), dtype=np.int64)
     lib().oracle_near_pairs(_p(xyz), n, _p(tri), r0, r1, _p(counts), _p(row_ptr), _p(cols))
     return row_ptr, cols
+
+
+def entries(mesh, k, rows, cols, near=False, op=None):
+    """T_il(k) for the pairs (rows[t], cols[t]) (complex128 array)."""
+    xyz, tri = _mesh_arrays(mesh)
+    n = tri.shape[0]
+    r = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+    c = np.ascontiguousarray(np.asarray(cols, dtype=np.int64))
+    assert r.shape == c.shape
+    out = np.zeros(r.size, dtype=np.complex128)
+    k = complex(k)
+    o = _op4(op)
+    lib().oracle_entries(_p(xyz), n, _p(tri), k.real, k.imag, _p(r), _p(c), r.size, _p(out),
+                         int(bool(near)), _p(o))
+    return out

@@ -477,6 +477,21 @@ void oracle_near_rule(const double* v0, const double* v1, const double* v2, cons
     oracle_near_rule_kind(v0, v1, v2, x, k_re, k_im, deriv, m, 0, out);
 }
 
+/* Entries T_il(k) for count (i, l) pairs (rows[t], cols[t]); out: 2 count doubles. */
+void oracle_entries(const double* xyz, int64_t nt, const int32_t* tri, double k_re,
+                    double k_im, const int64_t* rows, const int64_t* cols, int64_t count,
+                    double* out, int near, const double* op4) {
+    const op_t op = op_from(op4);
+    const cplx k = k_re + I * k_im;
+    cplx* o = (cplx*)out;
+    for (int64_t t = 0; t < count; ++t) {
+        panel_t Pi, Pl;
+        panel_geometry(xyz, tri, rows[t], &Pi);
+        panel_geometry(xyz, tri, cols[t], &Pl);
+        o[t] = entry(xyz, tri, &Pi, &Pl, rows[t], cols[t], k, 0, near, op);
+    }
+}
+
 /* Near pairs of rows [r0, r1): counts[i - r0] = number of near panels l of row i; with
  * cols non-null, the panels themselves in increasing l, row after row (row_ptr given by
  * the caller from the counts). */

@@ -1,0 +1,55 @@
+"""Pins of the oracle's low-rank far field (oracle/hmatrix.py), against what the definitions
+fix independently of its code:
+
+* the block partition covers every (i, l) exactly once, and every far block satisfies the
+  admissibility condition it was chosen by;
+* adaptive cross approximation recovers an exactly rank-3 matrix to rounding in 3 steps
+  (plus at most the one that finds the zero residual);
+* the assembled H-matrix differs from the dense A(k) by less than the requested tolerance
+  (relative Frobenius norm), for the single layer and the double layer, and the error falls
+  with the tolerance.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import assembly as oasm, hmatrix as hm
+
+
+def test_partition_covers_every_entry_once():
+    mesh = synth.icosphere(2)
+    cl = hm.cluster_tree(mesh, leaf=16)
+    bl = hm.blocks(cl, eta=1.0)
+    count = np.zeros((mesh.n, mesh.n), int)
+    for t, s, far in bl:
+        count[np.ix_(cl[t][0], cl[s][0])] += 1
+        if far:
+            assert max(hm._diam(cl[t]), hm._diam(cl[s])) <= hm._dist(cl[t], cl[s])
+    assert np.all(count == 1)
+    assert any(f for _, _, f in bl) and any(not f for _, _, f in bl)
+
+
+def test_aca_recovers_a_rank3_matrix():
+    rng = np.random.default_rng(2)
+    m, n = 40, 33
+    P = rng.normal(size=(m, 3)) + 1j * rng.normal(size=(m, 3))
+    Q = rng.normal(size=(n, 3)) + 1j * rng.normal(size=(n, 3))
+    M = P @ Q.T
+    U, W = hm.aca(lambda i: M[i].copy(), lambda j: M[:, j].copy(), m, n, 1e-12, 20)
+    assert U.shape[1] <= 4
+    assert np.max(np.abs(U @ W.T - M)) < 1e-12 * np.max(np.abs(M))
+
+
+@pytest.mark.parametrize("op", [None, (0.0, 1.0)], ids=["single", "double"])
+def test_hmatrix_within_tolerance(op):
+    mesh = synth.icosphere(3)
+    k = 3.0 + 0.1j
+    cl = hm.cluster_tree(mesh, leaf=32)
+    bl = hm.blocks(cl, eta=1.0)
+    A = oasm.matrix(mesh, k, op=op)
+    errs = []
+    for eps in (1e-4, 1e-7):
+        AH = hm.dense(cl, bl, hm.compress(mesh, k, cl, bl, eps=eps, op=op), mesh.n)
+        errs.append(np.linalg.norm(A - AH) / np.linalg.norm(A))
+        assert errs[-1] < eps
+    assert errs[1] < errs[0] / 100
