@@ -49,7 +49,8 @@ typedef enum {
 
 typedef enum {
     BEM_PREC_FP64 = 0,  /* plain path: FP64 evaluation and FP64 contraction */
-    BEM_PREC_MIXED = 1  /* FP32 evaluation, BF16x3 split-precision tcgen05 contraction */
+    BEM_PREC_MIXED = 1, /* FP32 evaluation, BF16x3 split-precision tcgen05 contraction */
+    BEM_PREC_HMATRIX = 2 /* low-rank far field (bem_set_hmatrix): FP32 entries and products */
 } bem_precision;
 
 typedef enum {
@@ -118,6 +119,32 @@ bem_status bem_set_operator(bem_ctx* ctx, double cg_re, double cg_im, double ch_
                             double ch_im);
 
 /*
+ * Low-rank far field (the H-matrix route of Section 4, Example 3, where the samples are
+ * stored as H-matrices compressed by adaptive cross approximation; the paper does not give
+ * its parameters). bem_set_hmatrix configures it; bem_project with precision
+ * BEM_PREC_HMATRIX then forms B_j = w_j V^H T(z_j) V with T(z_j) replaced by its
+ * H-matrix:
+ *   cluster tree: panels split at the middle of their order along the longest axis of
+ *     their centroids' box (ties by index) down to `leaf` panels (1..32); a cluster's
+ *     geometry is the box of its panels' vertices;
+ *   blocks from (root, root): far when max(diam) <= eta dist of the two boxes, dense when
+ *     both clusters are leaves, else split into the children's pairs;
+ *   far blocks: adaptive cross approximation with partial pivoting on FP32 entries, per
+ *     node, to relative accuracy eps (stop at ||u_k|| ||w_k|| <= eps ||S_k||_F, at most
+ *     rmax terms, 1..128); dense blocks evaluated in FP32; products in FP32; the near-field
+ *     corrections (bem_set_near_field) and V^H Y in FP64.
+ * The structure is built on the host at the first projection after a mesh change (from a
+ * host copy of the mesh kept by bem_set_mesh) and reused; the compression runs at every
+ * projection. The AV output holds the H-matrix products. Synchronises the stream (once per
+ * node). bem_hmatrix_stats: far and dense block counts, the fraction of entries in far
+ * blocks, mean and largest rank of the last projection (host; BEM_ESTATE before
+ * bem_set_hmatrix).
+ */
+bem_status bem_set_hmatrix(bem_ctx* ctx, int leaf, double eta, double eps, int rmax);
+bem_status bem_hmatrix_stats(const bem_ctx* ctx, int64_t* far_blocks, int64_t* dense_blocks,
+                             double* far_fraction, double* mean_rank, int* max_rank);
+
+/*
  * Node schedule of the mixed projection (an implementation detail of Eq. RR_approx's
  * evaluation; the paper has no counterpart). Nodes whose real parts round to the same FP32
  * value evaluate the same phase Re(z_j) |x - y| at every quadrature point: the conjugate
@@ -142,7 +169,7 @@ bem_status bem_node_order(const bem_ctx* ctx, int* order_host, int* twins);
  *   AV_dev   optional (NULL to skip): N x (n x nu) complex, node j at offset j*n*nu,
  *            column-major with leading dimension n: Y_j = A(z_j) V (unweighted), the
  *            products the stopping test and the residuals use.
- *   precision  BEM_PREC_FP64 or BEM_PREC_MIXED.
+ *   precision  BEM_PREC_FP64, BEM_PREC_MIXED or BEM_PREC_HMATRIX (after bem_set_hmatrix).
  * 1 <= nu <= 256. Requires a mesh and a contour. Asynchronous on `stream`.
  */
 bem_status bem_project(bem_ctx* ctx, const double* V_dev, int64_t ldv, int nu,

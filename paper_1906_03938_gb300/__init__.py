@@ -24,6 +24,7 @@ STATUS = {0: "BEM_OK", -1: "BEM_EINVAL", -2: "BEM_ENOMEM", -3: "BEM_ECUDA", -4: 
           -5: "BEM_ETIMEOUT", -6: "BEM_ENOCONV", -7: "BEM_ESTATE"}
 PREC_FP64 = 0
 PREC_MIXED = 1
+PREC_HMATRIX = 2
 CONTOUR_CIRCLE = 0
 CONTOUR_ELLIPSE = 1
 CONTOUR_CHEBYSHEV = 2
@@ -44,6 +45,8 @@ SIGNATURES = {
     "bem_node_order": (_I, [_P, _P, _P]),
     "bem_set_async": (_I, [_P, _I]),
     "bem_set_operator": (_I, [_P, _D, _D, _D, _D]),
+    "bem_set_hmatrix": (_I, [_P, _I, _D, _D, _I]),
+    "bem_hmatrix_stats": (_I, [_P, _P, _P, _P, _P, _P]),
     "bem_apply_sum": (_I, [_P, _P, _P, _I64, _I, _I, _P, _P]),
     "bem_solve_sum": (_I, [_P, _P, _P, _I64, _I, _D, _I, _P, _I64, ctypes.POINTER(_I), _P, _P]),
     "bem_inverse_power_mf": (_I, [_P, _P, _I64, _I, _I, _D, _D, _D, _I, ctypes.POINTER(_I), _P]),
@@ -353,6 +356,21 @@ class Context:
         cg, ch = complex(c_g), complex(c_h)
         self._chk("bem_set_operator", self._lib.bem_set_operator(
             self._h, cg.real, cg.imag, ch.real, ch.imag))
+
+    def set_hmatrix(self, leaf=32, eta=1.0, eps=1e-6, rmax=48):
+        """Low-rank far field for projections with precision PREC_HMATRIX."""
+        self._chk("bem_set_hmatrix", self._lib.bem_set_hmatrix(
+            self._h, int(leaf), float(eta), float(eps), int(rmax)))
+
+    def hmatrix_stats(self):
+        fb, db = _I64(0), _I64(0)
+        ff, mr = ctypes.c_double(0), ctypes.c_double(0)
+        xr = _I(0)
+        self._chk("bem_hmatrix_stats", self._lib.bem_hmatrix_stats(
+            self._h, ctypes.byref(fb), ctypes.byref(db), ctypes.byref(ff), ctypes.byref(mr),
+            ctypes.byref(xr)))
+        return {"far_blocks": fb.value, "dense_blocks": db.value, "far_fraction": ff.value,
+                "mean_rank": mr.value, "max_rank": xr.value}
 
     def set_async(self, on=True):
         """Asynchronous mode: cholqr2 leaves its status check to check()."""

@@ -217,6 +217,7 @@ void bem_destroy(bem_ctx* ctx) {
   cudaFree(ctx->d_near_cols);
   cudaFree(ctx->d_near_work);
   cudaFree(ctx->d_net);
+  free_hmatrix(ctx);
   for (auto& e : ctx->ev) cudaEventDestroy(e);
   if (ctx->mesh_ev) cudaEventSynchronize(ctx->mesh_ev);
   if (ctx->con_ev) cudaEventSynchronize(ctx->con_ev);
@@ -334,6 +335,8 @@ bem_status bem_set_mesh(bem_ctx* ctx, int64_t nv, const double* xyz_host, int64_
   }
   g.n = nt;
   g.nv = nv;
+  ctx->h_xyz.assign(xyz_host, xyz_host + 3 * nv);
+  ctx->h_tri.assign(tri_host, tri_host + 3 * nt);
   // asynchronous upload through the pinned staging buffer
   const size_t xb = 3 * nv * sizeof(double), tb = 3 * nt * sizeof(int32_t);
   bem_status st = stage_buffer(ctx, ctx->h_mesh, ctx->h_mesh_bytes, ctx->mesh_ev, xb + tb);
@@ -440,11 +443,13 @@ bem_status bem_project(bem_ctx* ctx, const double* V_dev, int64_t ldv, int nu,
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   const int N = ctx->con.N;
-  if (precision != BEM_PREC_MIXED && precision != BEM_PREC_FP64)
+  if (precision != BEM_PREC_MIXED && precision != BEM_PREC_FP64 && precision != BEM_PREC_HMATRIX)
     return fail(ctx, BEM_EINVAL, "bem_project: unknown precision");
   bem_status st0 = ensure_near(ctx, s);
   if (st0 != BEM_OK) return st0;
   if (precision == BEM_PREC_MIXED) return project_mixed(ctx, V_dev, ldv, nu, Bhat_dev, AV_dev, s);
+  if (precision == BEM_PREC_HMATRIX)
+    return project_hmatrix(ctx, V_dev, ldv, nu, Bhat_dev, AV_dev, s);
   st0 = ensure_self64(ctx, s);
   if (st0 != BEM_OK) return st0;
   double* Y = AV_dev;

@@ -1,0 +1,766 @@
+// Low-rank far field of T(z_j) (the H-matrix route of the paper's largest problems,
+// Section 4, Example 3: the samples are stored as H-matrices compressed by adaptive cross
+// approximation), applied in the projection of Eq. RR_approx.
+//
+// Host: a cluster tree of the panels (split at the middle of their order along the longest
+// axis of the centroids' box, ties by index, down to `leaf` panels; a cluster's geometry is
+// the box of its panels' vertices) and the block partition from (root, root): a pair is far
+// when max(diam tau, diam sigma) <= eta dist(tau, sigma), a pair of leaves that is not far
+// is dense, any other pair splits into its children's pairs.
+// Device, node by node:
+//   hm_aca_kernel        one CTA per far block: adaptive cross approximation with partial
+//                        pivoting on FP32 entries (block ~ U W^T, ranks up to rmax, stop at
+//                        ||u_k|| ||w_k|| <= eps ||S_k||_F with the exact norm update);
+//   hm_wtv_kernel        T_b = W_b^T V_sigma (rank x nu) per far block;
+//   hm_leaf_kernel       per leaf row range and 64 basis columns: the dense blocks of the
+//                        leaf evaluated and multiplied at once, then U_b T_b of every far
+//                        block above the leaf, in a fixed order (no atomics), into Y_j (FP64).
+// Then the near-field corrections (if enabled) and B_j = w_j V^H Y_j in FP64.
+#include <math.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "internal.h"
+
+namespace bem {
+
+struct HMatrix {
+  int leaf = 32;
+  double eta = 1.0, eps = 1e-6;
+  int rmax = 48;
+  int64_t mesh_version = -1;
+  // structure (host)
+  std::vector<int32_t> perm;   // cluster order -> panel
+  struct Cl {
+    int32_t b, e, c0, c1;      // panel range in `perm`, children (-1: leaf)
+    double lo[3], hi[3];
+  };
+  std::vector<Cl> cl;
+  std::vector<int4> far;       // far blocks: tau range, sigma range
+  std::vector<int64_t> uw_off; // per far block: offset of U (m x rmax), then W (n x rmax)
+  int64_t uw_total = 0;        // complex elements per node
+  int64_t used_total = 0;      // row flags per node (bytes)
+  std::vector<int64_t> used_off;
+  std::vector<int4> leaves;    // leaf row range, then [near_begin, near_end) in `near`
+  std::vector<int32_t> leaf_far_ptr, leaf_far;   // CSR: far blocks above each leaf
+  std::vector<int2> near;      // dense blocks of a leaf: sigma range
+  std::vector<int32_t> near_ptr;
+  // device copies
+  int32_t* d_perm = nullptr;
+  int4* d_far = nullptr;
+  int64_t* d_uw_off = nullptr;
+  int64_t* d_used_off = nullptr;
+  int4* d_leaves = nullptr;
+  int32_t* d_leaf_far_ptr = nullptr;
+  int32_t* d_leaf_far = nullptr;
+  int2* d_near = nullptr;
+  int32_t* d_near_ptr = nullptr;
+  // per-node work (grown on demand)
+  float2* d_uw = nullptr;
+  size_t uw_bytes = 0;
+  uint8_t* d_used = nullptr;
+  size_t used_bytes = 0;
+  int32_t* d_rank = nullptr;
+  int64_t* d_toff = nullptr;
+  size_t rank_cap = 0;
+  float2* d_t = nullptr;
+  size_t t_bytes = 0;
+  float2* d_vp = nullptr;      // V in cluster order, row-major (nu per panel), FP32
+  size_t vp_bytes = 0;
+  double* d_y = nullptr;       // Y_j, FP64, column-major per node
+  size_t y_bytes = 0;
+  // statistics of the last projection
+  double mean_rank = 0.0;
+  int max_rank = 0;
+  double far_fraction = 0.0;
+};
+
+namespace {
+
+void free_dev(HMatrix& h) {
+  cudaFree(h.d_perm); cudaFree(h.d_far); cudaFree(h.d_uw_off); cudaFree(h.d_used_off);
+  cudaFree(h.d_leaves); cudaFree(h.d_leaf_far_ptr); cudaFree(h.d_leaf_far); cudaFree(h.d_near);
+  cudaFree(h.d_near_ptr);
+  h.d_perm = nullptr; h.d_far = nullptr; h.d_uw_off = nullptr; h.d_used_off = nullptr;
+  h.d_leaves = nullptr; h.d_leaf_far_ptr = nullptr; h.d_leaf_far = nullptr; h.d_near = nullptr;
+  h.d_near_ptr = nullptr;
+}
+
+void free_work(HMatrix& h) {
+  cudaFree(h.d_uw); cudaFree(h.d_used); cudaFree(h.d_rank); cudaFree(h.d_toff); cudaFree(h.d_t);
+  cudaFree(h.d_vp); cudaFree(h.d_y);
+  h.d_uw = nullptr; h.d_used = nullptr; h.d_rank = nullptr; h.d_toff = nullptr; h.d_t = nullptr;
+  h.d_vp = nullptr; h.d_y = nullptr;
+  h.uw_bytes = h.used_bytes = h.rank_cap = h.t_bytes = h.vp_bytes = h.y_bytes = 0;
+}
+
+double box_diam(const HMatrix::Cl& c) {
+  double s = 0.0;
+  for (int d = 0; d < 3; ++d) s += (c.hi[d] - c.lo[d]) * (c.hi[d] - c.lo[d]);
+  return sqrt(s);
+}
+
+double box_dist(const HMatrix::Cl& a, const HMatrix::Cl& b) {
+  double s = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    const double g = std::max(0.0, std::max(a.lo[d] - b.hi[d], b.lo[d] - a.hi[d]));
+    s += g * g;
+  }
+  return sqrt(s);
+}
+
+// Cluster tree over perm[b, e); returns the cluster's number.
+int build_cluster(HMatrix& h, const std::vector<double>& cen, const std::vector<double>& xyz,
+                  const std::vector<int32_t>& tri, int32_t b, int32_t e) {
+  const int me = (int)h.cl.size();
+  HMatrix::Cl c;
+  c.b = b;
+  c.e = e;
+  c.c0 = c.c1 = -1;
+  for (int d = 0; d < 3; ++d) {
+    c.lo[d] = 1e300;
+    c.hi[d] = -1e300;
+  }
+  double clo[3] = {1e300, 1e300, 1e300}, chi[3] = {-1e300, -1e300, -1e300};
+  for (int32_t t = b; t < e; ++t) {
+    const int32_t l = h.perm[t];
+    for (int v = 0; v < 3; ++v)
+      for (int d = 0; d < 3; ++d) {
+        const double x = xyz[3 * (int64_t)tri[3 * (int64_t)l + v] + d];
+        c.lo[d] = std::min(c.lo[d], x);
+        c.hi[d] = std::max(c.hi[d], x);
+      }
+    for (int d = 0; d < 3; ++d) {
+      clo[d] = std::min(clo[d], cen[3 * (int64_t)l + d]);
+      chi[d] = std::max(chi[d], cen[3 * (int64_t)l + d]);
+    }
+  }
+  h.cl.push_back(c);
+  if (e - b > h.leaf) {
+    int axis = 0;
+    for (int d = 1; d < 3; ++d)
+      if (chi[d] - clo[d] > chi[axis] - clo[axis]) axis = d;
+    std::sort(h.perm.begin() + b, h.perm.begin() + e, [&](int32_t p, int32_t q) {
+      const double xp = cen[3 * (int64_t)p + axis], xq = cen[3 * (int64_t)q + axis];
+      return xp < xq || (xp == xq && p < q);
+    });
+    const int32_t mid = b + (e - b) / 2;
+    const int c0 = build_cluster(h, cen, xyz, tri, b, mid);
+    const int c1 = build_cluster(h, cen, xyz, tri, mid, e);
+    h.cl[me].c0 = c0;
+    h.cl[me].c1 = c1;
+  }
+  return me;
+}
+
+void build_blocks(HMatrix& h, int t, int s, std::vector<int2>& far_cl,
+                  std::vector<int2>& near_cl) {
+  const HMatrix::Cl& A = h.cl[t];
+  const HMatrix::Cl& B = h.cl[s];
+  if (std::max(box_diam(A), box_diam(B)) <= h.eta * box_dist(A, B)) {
+    far_cl.push_back(make_int2(t, s));
+    return;
+  }
+  const bool la = A.c0 < 0, lb = B.c0 < 0;
+  if (la && lb) {
+    near_cl.push_back(make_int2(t, s));
+    return;
+  }
+  const int ta[2] = {la ? t : A.c0, la ? -1 : A.c1};
+  const int sb[2] = {lb ? s : B.c0, lb ? -1 : B.c1};
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j)
+      if (ta[i] >= 0 && sb[j] >= 0) build_blocks(h, ta[i], sb[j], far_cl, near_cl);
+}
+
+}  // namespace
+
+namespace {
+
+__device__ __forceinline__ float hm_ex2(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// T_il(z) in FP32 for i != l (7-point rule; the general operator's factor when op is not
+// the single layer); coordinates relative to x_i.
+__device__ __forceinline__ float2 hm_entry(const Geometry& g, int64_t i, int64_t l, float kr,
+                                           float ki, const OpCoef& op, bool general) {
+  const int64_t n = g.n;
+  const float xi = g.cx32[i], yi = g.cx32[n + i], zi = g.cx32[2 * n + i];
+  float nx = 0.f, ny = 0.f, nz = 0.f;
+  if (general) {
+    const float* pk = g.pack32 + l * 64;
+    nx = pk[56];
+    ny = pk[57];
+    nz = pk[58];
+  }
+  const float kmi = -ki * 1.4426950408889634f;
+  float sr = 0.f, si = 0.f;
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    const float dx = g.qp32[q * n + l] - xi, dy = g.qp32[(7 + q) * n + l] - yi,
+                dz = g.qp32[(14 + q) * n + l] - zi;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float rs = rsqrtf(r2);
+    const float r = r2 * rs;
+    const float a = g.qw32[q * n + l] * rs * hm_ex2(kmi * r);
+    float sn, cs;
+    __sincosf(kr * r, &sn, &cs);
+    if (general) {
+      float fr, fi;
+      op_factor(op, (dx * nx + dy * ny + dz * nz) * rs * rs, kr * r, ki * r, fr, fi);
+      sr += a * (cs * fr - sn * fi);
+      si += a * (cs * fi + sn * fr);
+    } else {
+      sr = fmaf(a, cs, sr);
+      si = fmaf(a, sn, si);
+    }
+  }
+  return make_float2(sr, si);
+}
+
+constexpr int kAcaThreads = 128;
+constexpr int kMaxRank = 128;
+
+// Block-wide argmax of (v, i): the largest v, the smallest i among equals.
+__device__ __forceinline__ void block_argmax(float& v, int& idx, float* sv, int* si) {
+  for (int off = 16; off > 0; off >>= 1) {
+    const float ov = __shfl_down_sync(0xffffffffu, v, off);
+    const int oi = __shfl_down_sync(0xffffffffu, idx, off);
+    if (ov > v || (ov == v && oi < idx)) {
+      v = ov;
+      idx = oi;
+    }
+  }
+  const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (lane == 0) {
+    sv[w] = v;
+    si[w] = idx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < kAcaThreads / 32; ++k)
+      if (sv[k] > sv[0] || (sv[k] == sv[0] && si[k] < si[0])) {
+        sv[0] = sv[k];
+        si[0] = si[k];
+      }
+  }
+  __syncthreads();
+  v = sv[0];
+  idx = si[0];
+  __syncthreads();
+}
+
+__device__ __forceinline__ float block_sum(float v, float* sv) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (lane == 0) sv[w] = v;
+  __syncthreads();
+  float s = 0.f;
+  for (int k = 0; k < kAcaThreads / 32; ++k) s += sv[k];
+  __syncthreads();
+  return s;
+}
+
+// One CTA per far block: adaptive cross approximation with partial pivoting.
+__global__ void __launch_bounds__(kAcaThreads)
+hm_aca_kernel(Geometry g, const int32_t* __restrict__ perm, const int4* __restrict__ far,
+              const int64_t* __restrict__ uw_off, const int64_t* __restrict__ used_off,
+              float kr, float ki, OpCoef op, float eps, int rmax, float2* __restrict__ uw,
+              uint8_t* __restrict__ used, int32_t* __restrict__ rank) {
+  __shared__ float sv[kAcaThreads / 32];
+  __shared__ int si[kAcaThreads / 32];
+  __shared__ float2 ui[kMaxRank], wj[kMaxRank], au[kMaxRank], aw[kMaxRank];
+  __shared__ float2 piv;
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const int4 f = far[b];
+  const int m = f.y - f.x, n = f.w - f.z;
+  float2* U = uw + uw_off[b];
+  float2* W = U + (int64_t)m * rmax;
+  uint8_t* fl = used + used_off[b];
+  const bool general = !op_single(op);
+  for (int i = tid; i < m; i += kAcaThreads) fl[i] = 0;
+  const int rcap = min(rmax, min(m, n));
+  int k = 0, istar = 0, guard = 0;
+  float norm2 = 0.f;
+  __syncthreads();
+  while (k < rcap && guard++ < m + rcap) {
+    if (tid == 0) fl[istar] = 1;
+    for (int p = tid; p < k; p += kAcaThreads) ui[p] = U[istar + (int64_t)p * m];
+    __syncthreads();
+    // residual row i* into W[:, k]
+    const int64_t gi = perm[f.x + istar];
+    float best = -1.f;
+    int bj = 0x7fffffff;
+    for (int l = tid; l < n; l += kAcaThreads) {
+      float2 v = hm_entry(g, gi, perm[f.z + l], kr, ki, op, general);
+      for (int p = 0; p < k; ++p) {
+        const float2 a = ui[p], w = W[l + (int64_t)p * n];
+        v.x -= a.x * w.x - a.y * w.y;
+        v.y -= a.x * w.y + a.y * w.x;
+      }
+      W[l + (int64_t)k * n] = v;
+      const float mag = v.x * v.x + v.y * v.y;
+      if (mag > best) {
+        best = mag;
+        bj = l;
+      }
+    }
+    block_argmax(best, bj, sv, si);
+    if (!(best > 0.f)) {   // a zero residual row: the next unused row, if any
+      float fv = -1.f;
+      int fi = 0x7fffffff;
+      for (int i = tid; i < m; i += kAcaThreads)
+        if (!fl[i] && fv < 0.f) {
+          fv = 0.f;
+          fi = i;
+        }
+      block_argmax(fv, fi, sv, si);
+      if (fv < 0.f) break;
+      istar = fi;
+      continue;
+    }
+    if (tid == 0) piv = W[bj + (int64_t)k * n];
+    __syncthreads();
+    const float2 pv = piv;
+    const float pd = pv.x * pv.x + pv.y * pv.y;
+    float nw = 0.f;
+    for (int l = tid; l < n; l += kAcaThreads) {   // w_k = r / r[j*]
+      const float2 v = W[l + (int64_t)k * n];
+      const float2 q = make_float2((v.x * pv.x + v.y * pv.y) / pd, (v.y * pv.x - v.x * pv.y) / pd);
+      W[l + (int64_t)k * n] = q;
+      nw += q.x * q.x + q.y * q.y;
+    }
+    for (int p = tid; p < k; p += kAcaThreads) wj[p] = W[bj + (int64_t)p * n];
+    __syncthreads();
+    // residual column j* into U[:, k]
+    const int64_t gl = perm[f.z + bj];
+    float nu2 = 0.f;
+    for (int i = tid; i < m; i += kAcaThreads) {
+      float2 v = hm_entry(g, perm[f.x + i], gl, kr, ki, op, general);
+      for (int p = 0; p < k; ++p) {
+        const float2 a = U[i + (int64_t)p * m], w = wj[p];
+        v.x -= a.x * w.x - a.y * w.y;
+        v.y -= a.x * w.y + a.y * w.x;
+      }
+      U[i + (int64_t)k * m] = v;
+      nu2 += v.x * v.x + v.y * v.y;
+    }
+    __syncthreads();
+    nu2 = block_sum(nu2, sv);
+    nw = block_sum(nw, sv);
+    // (U^H u)_p and (W^H w)_p for p < k: warps take p in turn, lanes sum over the rows
+    {
+      const int wp = tid / 32, lane = tid % 32;
+      for (int p = wp; p < k; p += kAcaThreads / 32) {
+        float2 a = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+        for (int i = lane; i < m; i += 32) {
+          const float2 x = U[i + (int64_t)p * m], y = U[i + (int64_t)k * m];
+          a.x += x.x * y.x + x.y * y.y;
+          a.y += x.x * y.y - x.y * y.x;
+        }
+        for (int l = lane; l < n; l += 32) {
+          const float2 x = W[l + (int64_t)p * n], y = W[l + (int64_t)k * n];
+          c.x += x.x * y.x + x.y * y.y;
+          c.y += x.x * y.y - x.y * y.x;
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+          a.x += __shfl_down_sync(0xffffffffu, a.x, off);
+          a.y += __shfl_down_sync(0xffffffffu, a.y, off);
+          c.x += __shfl_down_sync(0xffffffffu, c.x, off);
+          c.y += __shfl_down_sync(0xffffffffu, c.y, off);
+        }
+        if (lane == 0) {
+          au[p] = a;
+          aw[p] = c;
+        }
+      }
+    }
+    __syncthreads();
+    float cross = 0.f;
+    for (int p = 0; p < k; ++p) cross += au[p].x * aw[p].x - au[p].y * aw[p].y;
+    norm2 += 2.f * cross + nu2 * nw;
+    ++k;
+    if (sqrtf(nu2 * nw) <= eps * sqrtf(fmaxf(norm2, 0.f))) break;
+    // next row: the largest |u_k| among the unused rows
+    float bv = -1.f;
+    int bi = 0x7fffffff;
+    for (int i = tid; i < m; i += kAcaThreads) {
+      if (fl[i]) continue;
+      const float2 v = U[i + (int64_t)(k - 1) * m];
+      const float mag = v.x * v.x + v.y * v.y;
+      if (mag > bv) {
+        bv = mag;
+        bi = i;
+      }
+    }
+    block_argmax(bv, bi, sv, si);
+    if (bv < 0.f) break;
+    istar = bi;
+  }
+  if (tid == 0) rank[b] = k;
+}
+
+// T_b = W_b^T V_sigma (rank x nu, row-major) per far block; vp is V in cluster order,
+// row-major (nu per panel), FP32.
+__global__ void __launch_bounds__(256)
+hm_wtv_kernel(const int4* __restrict__ far, const int64_t* __restrict__ uw_off,
+              const int32_t* __restrict__ rank, const int64_t* __restrict__ toff, int rmax,
+              const float2* __restrict__ uw, const float2* __restrict__ vp, int nu,
+              float2* __restrict__ T) {
+  const int b = blockIdx.x;
+  const int4 f = far[b];
+  const int m = f.y - f.x, n = f.w - f.z;
+  const int r = rank[b];
+  const float2* W = uw + uw_off[b] + (int64_t)m * rmax;
+  float2* Tb = T + toff[b];
+  for (int idx = threadIdx.x; idx < r * nu; idx += blockDim.x) {
+    const int p = idx / nu, c = idx % nu;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int l = 0; l < n; ++l) {
+      const float2 w = W[l + (int64_t)p * n], v = vp[(int64_t)(f.z + l) * nu + c];
+      acc.x += w.x * v.x - w.y * v.y;
+      acc.y += w.x * v.y + w.y * v.x;
+    }
+    Tb[idx] = acc;
+  }
+}
+
+constexpr int kLeafMax = 32;   // rows of a leaf (the leaf size is capped to it)
+constexpr int kLeafCols = 64;  // basis columns per CTA
+
+// Y_j for the rows of one leaf and 64 basis columns: its dense blocks, then U_b T_b of every
+// far block above it, in the lists' order.
+__global__ void __launch_bounds__(256)
+hm_leaf_kernel(Geometry g, const int32_t* __restrict__ perm, const int4* __restrict__ leaves,
+               const int2* __restrict__ near, const int32_t* __restrict__ leaf_far_ptr,
+               const int32_t* __restrict__ leaf_far, const int4* __restrict__ far,
+               const int64_t* __restrict__ uw_off, const int32_t* __restrict__ rank,
+               const int64_t* __restrict__ toff, int rmax, const float2* __restrict__ uw,
+               const float2* __restrict__ T, const float2* __restrict__ vp, int nu,
+               const float2* __restrict__ self32, float kr, float ki, OpCoef op,
+               double* __restrict__ Y) {
+  __shared__ float2 sA[kLeafMax][kLeafMax + 1];
+  __shared__ float2 sV[kLeafMax][kLeafCols];
+  const int L = blockIdx.x;
+  const int c0 = blockIdx.y * kLeafCols;
+  const int4 lf = leaves[L];   // rows [x, y), dense blocks [z, w)
+  const int mL = lf.y - lf.x;
+  const int tid = threadIdx.x;
+  const int row = tid % kLeafMax, cg = tid / kLeafMax;   // columns c0 + cg + 8 q
+  const int64_t n = g.n;
+  const bool general = !op_single(op);
+  float2 acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
+  for (int nb = lf.z; nb < lf.w; ++nb) {
+    const int2 sg = near[nb];
+    const int ns = sg.y - sg.x;
+    __syncthreads();
+    for (int t = tid; t < kLeafMax * kLeafMax; t += 256) {
+      const int rr = t % kLeafMax, ll = t / kLeafMax;
+      float2 a = make_float2(0.f, 0.f);
+      if (rr < mL && ll < ns) {
+        const int64_t i = perm[lf.x + rr], l = perm[sg.x + ll];
+        a = (i == l) ? self32[l] : hm_entry(g, i, l, kr, ki, op, general);
+      }
+      sA[rr][ll] = a;
+    }
+    for (int t = tid; t < kLeafMax * kLeafCols; t += 256) {
+      const int ll = t / kLeafCols, c = t % kLeafCols;
+      sV[ll][c] = (ll < ns && c0 + c < nu) ? vp[(int64_t)(sg.x + ll) * nu + c0 + c]
+                                            : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int ll = 0; ll < ns; ++ll) {
+      const float2 a = sA[row][ll];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float2 v = sV[ll][cg + 8 * q];
+        acc[q].x += a.x * v.x - a.y * v.y;
+        acc[q].y += a.x * v.y + a.y * v.x;
+      }
+    }
+  }
+  if (row < mL) {
+    for (int e = leaf_far_ptr[L]; e < leaf_far_ptr[L + 1]; ++e) {
+      const int b = leaf_far[e];
+      const int4 f = far[b];
+      const int m = f.y - f.x;
+      const int o = lf.x - f.x + row;
+      const float2* U = uw + uw_off[b];
+      const float2* Tb = T + toff[b];
+      const int r = rank[b];
+      for (int p = 0; p < r; ++p) {
+        const float2 u = U[o + (int64_t)p * m];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int c = c0 + cg + 8 * q;
+          if (c < nu) {
+            const float2 t = Tb[(int64_t)p * nu + c];
+            acc[q].x += u.x * t.x - u.y * t.y;
+            acc[q].y += u.x * t.y + u.y * t.x;
+          }
+        }
+      }
+    }
+    const int64_t i = perm[lf.x + row];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int c = c0 + cg + 8 * q;
+      if (c < nu) {
+        Y[2 * ((int64_t)c * n + i)] = (double)acc[q].x;
+        Y[2 * ((int64_t)c * n + i) + 1] = (double)acc[q].y;
+      }
+    }
+  }
+}
+
+// vp[t][c] = V[perm[t], c] in FP32 (cluster order, row-major)
+__global__ void hm_vperm_kernel(const double2* __restrict__ V, int64_t ldv, int64_t n, int nu,
+                                const int32_t* __restrict__ perm, float2* __restrict__ vp) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * nu) return;
+  const int64_t row = t / nu;
+  const int c = (int)(t % nu);
+  const double2 v = V[(int64_t)c * ldv + perm[row]];
+  vp[t] = make_float2((float)v.x, (float)v.y);
+}
+
+}  // namespace
+
+namespace {
+
+template <typename T>
+bem_status upload(bem_ctx* ctx, T*& dst, const std::vector<T>& src) {
+  cudaFree(dst);
+  dst = nullptr;
+  const size_t bytes = std::max<size_t>(1, src.size()) * sizeof(T);
+  if (cudaMalloc(&dst, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, BEM_ENOMEM, "low-rank far field: device allocation failed");
+  }
+  if (!src.empty())
+    return cuda_check(ctx, cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice),
+                      "low-rank far field copy");
+  return BEM_OK;
+}
+
+template <typename T>
+bem_status grow(bem_ctx* ctx, T*& p, size_t& cap, size_t bytes) {
+  if (bytes <= cap) return BEM_OK;
+  cudaFree(p);
+  p = nullptr;
+  cap = 0;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, BEM_ENOMEM, "low-rank far field: device allocation failed");
+  }
+  cap = bytes;
+  return BEM_OK;
+}
+
+// The cluster tree, the block partition and the per-leaf lists of the current mesh.
+bem_status build_structure(bem_ctx* ctx) {
+  HMatrix& h = *ctx->hm;
+  const int64_t n = ctx->geo.n;
+  const std::vector<double>& xyz = ctx->h_xyz;
+  const std::vector<int32_t>& tri = ctx->h_tri;
+  std::vector<double> cen(3 * n);
+  for (int64_t l = 0; l < n; ++l)
+    for (int d = 0; d < 3; ++d)
+      cen[3 * l + d] = (xyz[3 * (int64_t)tri[3 * l] + d] + xyz[3 * (int64_t)tri[3 * l + 1] + d] +
+                        xyz[3 * (int64_t)tri[3 * l + 2] + d]) / 3.0;
+  h.perm.resize(n);
+  std::iota(h.perm.begin(), h.perm.end(), 0);
+  h.cl.clear();
+  build_cluster(h, cen, xyz, tri, 0, (int32_t)n);
+  std::vector<int2> far_cl, near_cl;
+  build_blocks(h, 0, 0, far_cl, near_cl);
+  // far blocks and their storage
+  h.far.clear();
+  h.uw_off.clear();
+  h.used_off.clear();
+  h.uw_total = h.used_total = 0;
+  double far_entries = 0.0;
+  for (const int2& fb : far_cl) {
+    const HMatrix::Cl& A = h.cl[fb.x];
+    const HMatrix::Cl& B = h.cl[fb.y];
+    h.far.push_back(make_int4(A.b, A.e, B.b, B.e));
+    h.uw_off.push_back(h.uw_total);
+    h.uw_total += (int64_t)(A.e - A.b + B.e - B.b) * h.rmax;
+    h.used_off.push_back(h.used_total);
+    h.used_total += A.e - A.b;
+    far_entries += (double)(A.e - A.b) * (B.e - B.b);
+  }
+  h.far_fraction = far_entries / ((double)n * n);
+  // leaves in cluster order, their dense blocks and the far blocks above them
+  std::vector<int> leaf_id(h.cl.size(), -1);
+  h.leaves.clear();
+  for (size_t c = 0; c < h.cl.size(); ++c)
+    if (h.cl[c].c0 < 0) leaf_id[c] = 0;
+  std::vector<int> leaf_cl;
+  for (size_t c = 0; c < h.cl.size(); ++c)
+    if (h.cl[c].c0 < 0) leaf_cl.push_back((int)c);
+  std::sort(leaf_cl.begin(), leaf_cl.end(), [&](int a, int b) { return h.cl[a].b < h.cl[b].b; });
+  for (size_t t = 0; t < leaf_cl.size(); ++t) leaf_id[leaf_cl[t]] = (int)t;
+  std::vector<std::vector<int2>> lnear(leaf_cl.size());
+  for (const int2& nb : near_cl)
+    lnear[leaf_id[nb.x]].push_back(make_int2(h.cl[nb.y].b, h.cl[nb.y].e));
+  std::vector<std::vector<int32_t>> lfar(leaf_cl.size());
+  // the leaves inside a far block's row cluster are consecutive (leaves sorted by start)
+  std::vector<int32_t> leaf_start(leaf_cl.size());
+  for (size_t t = 0; t < leaf_cl.size(); ++t) leaf_start[t] = h.cl[leaf_cl[t]].b;
+  for (size_t b = 0; b < h.far.size(); ++b) {
+    const int4 f = h.far[b];
+    size_t t = std::lower_bound(leaf_start.begin(), leaf_start.end(), f.x) - leaf_start.begin();
+    for (; t < leaf_cl.size() && h.cl[leaf_cl[t]].e <= f.y; ++t) lfar[t].push_back((int32_t)b);
+  }
+  h.near.clear();
+  h.leaf_far.clear();
+  h.leaf_far_ptr.assign(1, 0);
+  for (size_t t = 0; t < leaf_cl.size(); ++t) {
+    const HMatrix::Cl& Lc = h.cl[leaf_cl[t]];
+    const int nb0 = (int)h.near.size();
+    for (const int2& s : lnear[t]) h.near.push_back(s);
+    h.leaves.push_back(make_int4(Lc.b, Lc.e, nb0, (int)h.near.size()));
+    for (int32_t b : lfar[t]) h.leaf_far.push_back(b);
+    h.leaf_far_ptr.push_back((int32_t)h.leaf_far.size());
+  }
+  bem_status st = upload(ctx, h.d_perm, h.perm);
+  if (st == BEM_OK) st = upload(ctx, h.d_far, h.far);
+  if (st == BEM_OK) st = upload(ctx, h.d_uw_off, h.uw_off);
+  if (st == BEM_OK) st = upload(ctx, h.d_used_off, h.used_off);
+  if (st == BEM_OK) st = upload(ctx, h.d_leaves, h.leaves);
+  if (st == BEM_OK) st = upload(ctx, h.d_leaf_far_ptr, h.leaf_far_ptr);
+  if (st == BEM_OK) st = upload(ctx, h.d_leaf_far, h.leaf_far);
+  if (st == BEM_OK) st = upload(ctx, h.d_near, h.near);
+  if (st != BEM_OK) return st;
+  h.mesh_version = ctx->mesh_version;
+  return BEM_OK;
+}
+
+unsigned nblocks(int64_t count, int t = 256) { return (unsigned)((count + t - 1) / t); }
+
+}  // namespace
+
+void free_hmatrix(bem_ctx* ctx) {
+  if (!ctx->hm) return;
+  free_dev(*ctx->hm);
+  free_work(*ctx->hm);
+  delete ctx->hm;
+  ctx->hm = nullptr;
+}
+
+bem_status project_hmatrix(bem_ctx* ctx, const double* V, int64_t ldv, int nu, double* Bhat,
+                           double* AV, cudaStream_t s) {
+  if (!ctx->hm) return fail(ctx, BEM_ESTATE, "bem_project: no low-rank far field set (bem_set_hmatrix)");
+  HMatrix& h = *ctx->hm;
+  const int64_t n = ctx->geo.n;
+  const int N = ctx->con.N;
+  if (ctx->h_xyz.empty()) return fail(ctx, BEM_ESTATE, "bem_project: no mesh set");
+  bem_status st = BEM_OK;
+  if (h.mesh_version != ctx->mesh_version && (st = build_structure(ctx)) != BEM_OK) return st;
+  if ((st = ensure_self32(ctx, s)) != BEM_OK) return st;
+  const size_t nfar = h.far.size();
+  if ((st = grow(ctx, h.d_uw, h.uw_bytes, std::max<size_t>(1, h.uw_total) * sizeof(float2))) != BEM_OK ||
+      (st = grow(ctx, h.d_used, h.used_bytes, std::max<size_t>(1, h.used_total))) != BEM_OK ||
+      (st = grow(ctx, h.d_vp, h.vp_bytes, (size_t)n * nu * sizeof(float2))) != BEM_OK)
+    return st;
+  size_t rc = h.rank_cap, tc = h.rank_cap;
+  if ((st = grow(ctx, h.d_rank, rc, std::max<size_t>(1, nfar) * sizeof(int32_t))) != BEM_OK ||
+      (st = grow(ctx, h.d_toff, tc, std::max<size_t>(1, nfar) * sizeof(int64_t))) != BEM_OK)
+    return st;
+  h.rank_cap = std::min(rc, tc);
+  double* Y = AV;
+  if (!Y) {
+    if ((st = grow(ctx, h.d_y, h.y_bytes, (size_t)N * n * nu * 2 * sizeof(double))) != BEM_OK) return st;
+    Y = h.d_y;
+  }
+  hm_vperm_kernel<<<nblocks(n * nu), 256, 0, s>>>(reinterpret_cast<const double2*>(V), ldv, n, nu,
+                                                  h.d_perm, h.d_vp);
+  ctx->launches++;
+  std::vector<int32_t> ranks(nfar);
+  std::vector<int64_t> toff(nfar);
+  double rank_sum = 0.0;
+  int rank_max = 0;
+  for (int j = 0; j < N; ++j) {
+    const float kr = (float)ctx->con.z_host[2 * j], ki = (float)ctx->con.z_host[2 * j + 1];
+    if (nfar) {
+      hm_aca_kernel<<<(unsigned)nfar, kAcaThreads, 0, s>>>(
+          ctx->geo, h.d_perm, h.d_far, h.d_uw_off, h.d_used_off, kr, ki, ctx->op, (float)h.eps,
+          h.rmax, h.d_uw, h.d_used, h.d_rank);
+      ctx->launches++;
+      st = cuda_check(ctx, cudaMemcpyAsync(ranks.data(), h.d_rank, nfar * sizeof(int32_t),
+                                           cudaMemcpyDeviceToHost, s), "rank copy");
+      if (st == BEM_OK) st = cuda_check(ctx, cudaStreamSynchronize(s), "rank copy");
+      if (st != BEM_OK) return st;
+      int64_t tot = 0;
+      for (size_t b = 0; b < nfar; ++b) {
+        toff[b] = tot;
+        tot += (int64_t)ranks[b] * nu;
+        rank_sum += ranks[b];
+        rank_max = std::max(rank_max, ranks[b]);
+      }
+      if ((st = grow(ctx, h.d_t, h.t_bytes, std::max<int64_t>(1, tot) * sizeof(float2))) != BEM_OK) return st;
+      st = cuda_check(ctx, cudaMemcpyAsync(h.d_toff, toff.data(), nfar * sizeof(int64_t),
+                                           cudaMemcpyHostToDevice, s), "offset copy");
+      if (st != BEM_OK) return st;
+      hm_wtv_kernel<<<(unsigned)nfar, 256, 0, s>>>(h.d_far, h.d_uw_off, h.d_rank, h.d_toff, h.rmax,
+                                                   h.d_uw, h.d_vp, nu, h.d_t);
+      ctx->launches++;
+    }
+    const dim3 grid((unsigned)h.leaves.size(), (unsigned)((nu + kLeafCols - 1) / kLeafCols));
+    hm_leaf_kernel<<<grid, 256, 0, s>>>(
+        ctx->geo, h.d_perm, h.d_leaves, h.d_near, h.d_leaf_far_ptr, h.d_leaf_far, h.d_far,
+        h.d_uw_off, h.d_rank, h.d_toff, h.rmax, h.d_uw, h.d_t, h.d_vp, nu,
+        reinterpret_cast<const float2*>(ctx->con.self32) + (int64_t)j * n, kr, ki, ctx->op,
+        Y + 2 * (int64_t)j * n * nu);
+    ctx->launches++;
+    if ((st = cuda_check(ctx, cudaGetLastError(), "low-rank far field kernels")) != BEM_OK) return st;
+  }
+  h.mean_rank = nfar ? rank_sum / ((double)nfar * N) : 0.0;
+  h.max_rank = rank_max;
+  if (near_active(ctx) && (st = near_apply64(ctx, V, ldv, nu, Y, s)) != BEM_OK) return st;
+  return cuda_check(ctx, launch_xhy_fp64(ctx, V, ldv, nu, Y, n, n * nu, nu, n, N, ctx->con.w, Bhat, s),
+                    "projection kernel");
+}
+
+}  // namespace bem
+
+using namespace bem;
+
+extern "C" bem_status bem_set_hmatrix(bem_ctx* ctx, int leaf, double eta, double eps, int rmax) {
+  if (!ctx) return BEM_EINVAL;
+  if (leaf < 1 || leaf > kLeafMax || !(eta > 0.0) || !(eps > 0.0) || eps >= 1.0 || rmax < 1 ||
+      rmax > kMaxRank)
+    return fail(ctx, BEM_EINVAL,
+                "bem_set_hmatrix: need 1 <= leaf <= 32, eta > 0, 0 < eps < 1, 1 <= rmax <= 128");
+  if (!ctx->hm) ctx->hm = new HMatrix();
+  HMatrix& h = *ctx->hm;
+  h.leaf = leaf;
+  h.eta = eta;
+  h.eps = eps;
+  h.rmax = rmax;
+  h.mesh_version = -1;   // rebuilt (and its storage re-laid out) by the next projection
+  free_work(h);
+  return BEM_OK;
+}
+
+extern "C" bem_status bem_hmatrix_stats(const bem_ctx* ctx, int64_t* far_blocks,
+                                        int64_t* dense_blocks, double* far_fraction,
+                                        double* mean_rank, int* max_rank) {
+  if (!ctx) return BEM_EINVAL;
+  if (!ctx->hm) return BEM_ESTATE;
+  const HMatrix& h = *ctx->hm;
+  if (far_blocks) *far_blocks = (int64_t)h.far.size();
+  if (dense_blocks) *dense_blocks = (int64_t)h.near.size();
+  if (far_fraction) *far_fraction = h.far_fraction;
+  if (mean_rank) *mean_rank = h.mean_rank;
+  if (max_rank) *max_rank = h.max_rank;
+  return BEM_OK;
+}

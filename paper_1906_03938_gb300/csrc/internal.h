@@ -85,6 +85,10 @@ constexpr int kNodeMask = kTwinBit - 1;
 
 }  // namespace bem
 
+namespace bem {
+struct HMatrix;   // low-rank far field (hmatrix.cu)
+}  // namespace bem
+
 struct bem_ctx {
   int device = 0;
   std::string err;
@@ -130,6 +134,11 @@ struct bem_ctx {
   // the boundary operator T = c_G G + c_H (1/2 I + K) (single layer by default)
   bem::OpCoef op;
   int64_t op_version = 0;   // bumped by every bem_set_operator
+  // host copy of the mesh (the cluster tree of the low-rank far field is built from it)
+  std::vector<double> h_xyz;
+  std::vector<int32_t> h_tri;
+  // low-rank far field (hmatrix.cu); null until bem_set_hmatrix
+  bem::HMatrix* hm = nullptr;
 };
 
 namespace bem {
@@ -224,6 +233,10 @@ size_t gmres_sum_work_bytes(bem_ctx* ctx, int nu, int restart);
 bem_status gmres_sum32(bem_ctx* ctx, const double* coef_host, const float2* B, float2* X, int nu,
                        double tol, int max_iter, int restart, void* work, cudaStream_t s,
                        int* iters_out, double* relres_host);
+// Projection with the low-rank far field (hmatrix.cu); BEM_ESTATE without bem_set_hmatrix.
+bem_status project_hmatrix(bem_ctx* ctx, const double* V, int64_t ldv, int nu, double* Bhat,
+                           double* AV, cudaStream_t s);
+void free_hmatrix(bem_ctx* ctx);
 // mixed-precision fused projection (tcgen05); defined in project_mixed.cu
 bem_status project_mixed(bem_ctx* ctx, const double* V, int64_t ldv, int nu, double* Bhat,
                          double* AV, cudaStream_t s);
