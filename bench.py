@@ -44,7 +44,7 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    p.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "hmatrix"])
     p.add_argument("--plain-steps", type=int, default=2,
                    help="steps of the plain FP64 path timed for the speedup (0: skip)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -384,7 +384,8 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     prob, mesh, V = problem(args.workload)
     n, N, nu = mesh.n, prob.N, prob.nu
-    prec = bem.PREC_MIXED if args.precision == "mixed" else bem.PREC_FP64
+    prec = {"mixed": bem.PREC_MIXED, "fp64": bem.PREC_FP64,
+            "hmatrix": bem.PREC_HMATRIX}[args.precision]
     c = prob.contour
     ctx = bem.Context(local)
     stream = torch.cuda.current_stream()
@@ -395,6 +396,8 @@ def run_ours(args):
         ctx.surrogate_set(surrogate["params"])
     OPS = {"single": (1.0, 0.0), "neumann": (0.0, 1.0), "robin": (0.5, 1.0)}
     ctx.set_operator(*OPS[args.operator])
+    if prec == bem.PREC_HMATRIX:   # low-rank far field: leaves of 32, eta 1, eps 1e-6
+        ctx.set_hmatrix(leaf=32, eta=1.0, eps=1e-6, rmax=64)
     if near_mode:
         ctx.set_mesh(mesh.xyz, mesh.tri)
         ctx.set_near_field(near_mode)
@@ -487,7 +490,15 @@ def run_ours(args):
 
     # roofline of the dominant kernel
     kern_avg = statistics.mean(kern_ms) if kern_ms else float("nan")
-    if prec == bem.PREC_FP64:
+    if prec == bem.PREC_HMATRIX:
+        # the H-matrix evaluates a fraction of the entries: there is no single-kernel roof;
+        # "achieved" counts the n^2 N entries of the dense operator it replaces
+        st = ctx.hmatrix_stats()
+        roof = {"bound": "effective", "achieved": entries / (t_total / args.steps),
+                "peak": None, "unit": "entries/s", "frac": None,
+                "hmatrix": st, "note": "whole step; far blocks by adaptive cross approximation "
+                                       "(eps 1e-6), dense leaf blocks and products in FP32"}
+    elif prec == bem.PREC_FP64:
         # plain path: FP64 pipe; algorithmic work = the complex MAC of every entry with
         # every basis column, 8 nu flops per entry
         flops = entries * 8 * nu
@@ -511,9 +522,10 @@ def run_ours(args):
                                + f"; per entry and quadrature point: ex2 per node, sin + cos "
                                f"per node or per twin pair ({twins} of {N // 2} possible), "
                                f"rsqrt per {G} nodes"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+    if roof.get("peak"):
+        roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = measured_traffic(args.workload, args.precision)
-    roof["kernel_ms"] = kern_avg
+    roof["kernel_ms"] = kern_avg if kern_ms else None
     roof["launches_timed"] = len(kern_ms)
 
     plain = None
@@ -542,7 +554,7 @@ def run_ours(args):
     eig = None
     golden = os.path.join(ROOT, "tests", "golden", f"eigs_{args.workload}.txt")
     if not args.no_eig_check and os.path.exists(golden) and not near_mode and \
-            args.operator == "single":
+            args.operator == "single" and args.precision != "hmatrix":
         t0 = time.perf_counter()
         lam, X, rel = ctx.solve(V_res, q=10, precision=prec, tol=1e-14)
         torch.cuda.synchronize()
@@ -579,7 +591,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == bem.PREC_FP64 else "f32+bf16x3", "data": "synthetic",
+        "dtype": {bem.PREC_FP64: "f64", bem.PREC_MIXED: "f32+bf16x3",
+                  bem.PREC_HMATRIX: "f32"}[prec], "data": "synthetic",
         "config": {"workload": args.workload, "mesh": mesh.name, "n": n, "N": N, "nu": nu,
                    "contour": f"{c.kind} c={c.centre.real:g} a={c.a:g} b={c.b:g}",
                    "precision": args.precision,

@@ -11,9 +11,11 @@ ones, written out plainly:
 * Geometry of a cluster: the axis-aligned box of all vertices of its panels; diam = the box
   diagonal, dist = the distance between two boxes.
 * Block partition, from (root, root): a pair is admissible (far) when
-  max(diam(tau), diam(sigma)) <= eta dist(tau, sigma); a pair of leaves that is not
-  admissible is dense (near); otherwise the pair is split into the pairs of children (a
-  leaf stays as it is). The blocks cover every (i, l) exactly once.
+  max(diam(tau), diam(sigma)) <= eta dist(tau, sigma) (and, when a leaf size is given,
+  both clusters hold more than two leaves of panels: smaller admissible blocks are cheaper
+  dense); a pair of leaves that is not admissible is dense (near); otherwise the pair is
+  split into the pairs of children (a leaf stays as it is). The blocks cover every (i, l)
+  exactly once.
 * Adaptive cross approximation with partial pivoting on a far block, entries A_il(k) of
   the 7-point rule: from row i* (first row of tau), residual row
   r = A[i*, sigma] - sum_p u_p[i*] w_p, pivot column j* = argmax |r|, w_k = r / r[j*],
@@ -65,13 +67,15 @@ def _dist(a, b):
     return float(np.linalg.norm(gap))
 
 
-def blocks(clusters, eta=1.0):
-    """Block list: (tau, sigma, far) cluster numbers."""
+def blocks(clusters, eta=1.0, leaf=None):
+    """Block list: (tau, sigma, far) cluster numbers. With ``leaf``, an admissible pair is
+    far only when both clusters hold more than 2 leaf panels (smaller ones stay dense)."""
     out = []
 
     def split(t, s):
         A, B = clusters[t], clusters[s]
-        if max(_diam(A), _diam(B)) <= eta * _dist(A, B):
+        big = leaf is None or min(A[0].size, B[0].size) > 2 * leaf
+        if max(_diam(A), _diam(B)) <= eta * _dist(A, B) and big:
             out.append((t, s, True))
             return
         if not A[1] and not B[1]:

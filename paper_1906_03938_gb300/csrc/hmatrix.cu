@@ -5,8 +5,9 @@
 // Host: a cluster tree of the panels (split at the middle of their order along the longest
 // axis of the centroids' box, ties by index, down to `leaf` panels; a cluster's geometry is
 // the box of its panels' vertices) and the block partition from (root, root): a pair is far
-// when max(diam tau, diam sigma) <= eta dist(tau, sigma), a pair of leaves that is not far
-// is dense, any other pair splits into its children's pairs.
+// when max(diam tau, diam sigma) <= eta dist(tau, sigma) and both hold more than two leaves
+// of panels, a pair of leaves that is not far is dense, any other pair splits into its
+// children's pairs.
 // Device, node by node:
 //   hm_aca_kernel        one CTA per far block: adaptive cross approximation with partial
 //                        pivoting on FP32 entries (block ~ U W^T, ranks up to rmax, stop at
@@ -14,8 +15,10 @@
 //   hm_wtv_kernel        T_b = W_b^T V_sigma (rank x nu) per far block;
 //   hm_leaf_kernel       per leaf row range and 64 basis columns: the dense blocks of the
 //                        leaf evaluated and multiplied at once, then U_b T_b of every far
-//                        block above the leaf, in a fixed order (no atomics), into Y_j (FP64).
-// Then the near-field corrections (if enabled) and B_j = w_j V^H Y_j in FP64.
+//                        block above the leaf, in a fixed order (no atomics), into the mixed
+//                        path's FP32 partials of Y_j.
+// The mixed path then adds the FP32 near-field corrections (if enabled) and forms
+// B_j = w_j V^H Y_j (tensor-core contraction for nu <= 128).
 #include <math.h>
 
 #include <algorithm>
@@ -159,7 +162,10 @@ void build_blocks(HMatrix& h, int t, int s, std::vector<int2>& far_cl,
                   std::vector<int2>& near_cl) {
   const HMatrix::Cl& A = h.cl[t];
   const HMatrix::Cl& B = h.cl[s];
-  if (std::max(box_diam(A), box_diam(B)) <= h.eta * box_dist(A, B)) {
+  // far: admissible and larger than two leaves both ways (smaller admissible blocks are
+  // cheaper evaluated densely, leaf by leaf)
+  if (std::max(box_diam(A), box_diam(B)) <= h.eta * box_dist(A, B) &&
+      std::min(A.e - A.b, B.e - B.b) > 2 * h.leaf) {
     far_cl.push_back(make_int2(t, s));
     return;
   }
@@ -443,7 +449,7 @@ hm_leaf_kernel(Geometry g, const int32_t* __restrict__ perm, const int4* __restr
                const int64_t* __restrict__ toff, int rmax, const float2* __restrict__ uw,
                const float2* __restrict__ T, const float2* __restrict__ vp, int nu,
                const float2* __restrict__ self32, float kr, float ki, OpCoef op,
-               double* __restrict__ Y) {
+               float* __restrict__ Yp, int acc_cols, int C, int n_pad) {
   __shared__ float2 sA[kLeafMax][kLeafMax + 1];
   __shared__ float2 sV[kLeafMax][kLeafCols];
   const int L = blockIdx.x;
@@ -512,9 +518,10 @@ hm_leaf_kernel(Geometry g, const int32_t* __restrict__ perm, const int4* __restr
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int c = c0 + cg + 8 * q;
-      if (c < nu) {
-        Y[2 * ((int64_t)c * n + i)] = (double)acc[q].x;
-        Y[2 * ((int64_t)c * n + i) + 1] = (double)acc[q].y;
+      if (c < nu) {   // real part at column (c / C) 2 C + c % C, imaginary part C further
+        const int colr = (c / C) * 2 * C + c % C;
+        Yp[(int64_t)colr * n_pad + i] = acc[q].x;
+        Yp[(int64_t)(colr + C) * n_pad + i] = acc[q].y;
       }
     }
   }
@@ -676,10 +683,15 @@ bem_status project_hmatrix(bem_ctx* ctx, const double* V, int64_t ldv, int nu, d
       (st = grow(ctx, h.d_toff, tc, std::max<size_t>(1, nfar) * sizeof(int64_t))) != BEM_OK)
     return st;
   h.rank_cap = std::min(rc, tc);
-  double* Y = AV;
-  if (!Y) {
-    if ((st = grow(ctx, h.d_y, h.y_bytes, (size_t)N * n * nu * 2 * sizeof(double))) != BEM_OK) return st;
-    Y = h.d_y;
+  // the mixed path's FP32 partials (slice 0 of one column split), zeroed: the leaf kernels
+  // write every row < n and column < nu
+  ExtFrame fr;
+  if ((st = external_begin(ctx, V, ldv, nu, fr, s)) != BEM_OK) return st;
+  st = cuda_check(ctx, cudaMemsetAsync(fr.Yp, 0, (size_t)N * fr.acc_cols * fr.n_pad * sizeof(float), s),
+                  "partials clear");
+  if (st != BEM_OK) {
+    external_release(fr);
+    return st;
   }
   hm_vperm_kernel<<<nblocks(n * nu), 256, 0, s>>>(reinterpret_cast<const double2*>(V), ldv, n, nu,
                                                   h.d_perm, h.d_vp);
@@ -698,7 +710,10 @@ bem_status project_hmatrix(bem_ctx* ctx, const double* V, int64_t ldv, int nu, d
       st = cuda_check(ctx, cudaMemcpyAsync(ranks.data(), h.d_rank, nfar * sizeof(int32_t),
                                            cudaMemcpyDeviceToHost, s), "rank copy");
       if (st == BEM_OK) st = cuda_check(ctx, cudaStreamSynchronize(s), "rank copy");
-      if (st != BEM_OK) return st;
+      if (st != BEM_OK) {
+        external_release(fr);
+        return st;
+      }
       int64_t tot = 0;
       for (size_t b = 0; b < nfar; ++b) {
         toff[b] = tot;
@@ -706,10 +721,16 @@ bem_status project_hmatrix(bem_ctx* ctx, const double* V, int64_t ldv, int nu, d
         rank_sum += ranks[b];
         rank_max = std::max(rank_max, ranks[b]);
       }
-      if ((st = grow(ctx, h.d_t, h.t_bytes, std::max<int64_t>(1, tot) * sizeof(float2))) != BEM_OK) return st;
+      if ((st = grow(ctx, h.d_t, h.t_bytes, std::max<int64_t>(1, tot) * sizeof(float2))) != BEM_OK) {
+        external_release(fr);
+        return st;
+      }
       st = cuda_check(ctx, cudaMemcpyAsync(h.d_toff, toff.data(), nfar * sizeof(int64_t),
                                            cudaMemcpyHostToDevice, s), "offset copy");
-      if (st != BEM_OK) return st;
+      if (st != BEM_OK) {
+        external_release(fr);
+        return st;
+      }
       hm_wtv_kernel<<<(unsigned)nfar, 256, 0, s>>>(h.d_far, h.d_uw_off, h.d_rank, h.d_toff, h.rmax,
                                                    h.d_uw, h.d_vp, nu, h.d_t);
       ctx->launches++;
@@ -719,15 +740,16 @@ bem_status project_hmatrix(bem_ctx* ctx, const double* V, int64_t ldv, int nu, d
         ctx->geo, h.d_perm, h.d_leaves, h.d_near, h.d_leaf_far_ptr, h.d_leaf_far, h.d_far,
         h.d_uw_off, h.d_rank, h.d_toff, h.rmax, h.d_uw, h.d_t, h.d_vp, nu,
         reinterpret_cast<const float2*>(ctx->con.self32) + (int64_t)j * n, kr, ki, ctx->op,
-        Y + 2 * (int64_t)j * n * nu);
+        fr.Yp + (int64_t)j * fr.acc_cols * fr.n_pad, fr.acc_cols, fr.C, fr.n_pad);
     ctx->launches++;
-    if ((st = cuda_check(ctx, cudaGetLastError(), "low-rank far field kernels")) != BEM_OK) return st;
+    if ((st = cuda_check(ctx, cudaGetLastError(), "low-rank far field kernels")) != BEM_OK) {
+      external_release(fr);
+      return st;
+    }
   }
   h.mean_rank = nfar ? rank_sum / ((double)nfar * N) : 0.0;
   h.max_rank = rank_max;
-  if (near_active(ctx) && (st = near_apply64(ctx, V, ldv, nu, Y, s)) != BEM_OK) return st;
-  return cuda_check(ctx, launch_xhy_fp64(ctx, V, ldv, nu, Y, n, n * nu, nu, n, N, ctx->con.w, Bhat, s),
-                    "projection kernel");
+  return external_end(ctx, fr, nu, Bhat, AV, s);
 }
 
 }  // namespace bem

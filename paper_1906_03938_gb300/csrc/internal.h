@@ -233,6 +233,19 @@ size_t gmres_sum_work_bytes(bem_ctx* ctx, int nu, int restart);
 bem_status gmres_sum32(bem_ctx* ctx, const double* coef_host, const float2* B, float2* X, int nu,
                        double tol, int max_iter, int restart, void* work, cudaStream_t s,
                        int* iters_out, double* relres_host);
+// Products formed outside the fused kernel, finished by the mixed path (project_mixed.cu):
+// Yp is slice 0 of the FP32 partials [slice][N][acc_cols][n_pad], basis column c's real part
+// at column (c / C) 2 C + c % C, its imaginary part C further; every entry must be written.
+struct ExtFrame {
+  float* Yp = nullptr;
+  int acc_cols = 0, C = 0, n_pad = 0;
+  void* impl = nullptr;
+};
+bem_status external_begin(bem_ctx* ctx, const double* V, int64_t ldv, int nu, ExtFrame& f,
+                          cudaStream_t s);
+bem_status external_end(bem_ctx* ctx, ExtFrame& f, int nu, double* Bhat, double* AV,
+                        cudaStream_t s);
+void external_release(ExtFrame& f);   // on an error between begin and end
 // Projection with the low-rank far field (hmatrix.cu); BEM_ESTATE without bem_set_hmatrix.
 bem_status project_hmatrix(bem_ctx* ctx, const double* V, int64_t ldv, int nu, double* Bhat,
                            double* AV, cudaStream_t s);

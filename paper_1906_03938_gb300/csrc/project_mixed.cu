@@ -1462,6 +1462,50 @@ bem_status mixed_sum_apply(bem_ctx* ctx, const float2* X, int64_t ldx, int64_t n
   return cuda_check(ctx, cudaGetLastError(), "node-summed apply");
 }
 
+// A projection whose products Y_j = T(z_j) V are formed elsewhere (the low-rank far field)
+// into the mixed path's FP32 partials, one column split: begin plans the scratch, prepares
+// the basis planes and hands out slice 0; end adds the FP32 near-field corrections (slice
+// 1) and forms B_j = w_j V^H Y_j (and Y_j on request) exactly as the mixed projection.
+bem_status external_begin(bem_ctx* ctx, const double* V, int64_t ldv, int nu, ExtFrame& f,
+                          cudaStream_t s) {
+  MixedPlan* plan = new MixedPlan();
+  bem_status st = mixed_plan(ctx, V, ldv, nu, 1, 0, *plan, s);
+  if (st != BEM_OK) {
+    delete plan;
+    return st;
+  }
+  if ((st = set_mixed_smem(ctx, plan->L.total)) != BEM_OK) {   // the V^H Y kernels' smem
+    delete plan;
+    return st;
+  }
+  mixed_pre(ctx, *plan, s);
+  f.impl = plan;
+  f.Yp = plan->p.Yp;
+  f.acc_cols = 2 * plan->p.nup;
+  f.C = plan->p.C;
+  f.n_pad = plan->p.n_pad;
+  return cuda_check(ctx, cudaGetLastError(), "external projection set-up");
+}
+
+void external_release(ExtFrame& f) {
+  delete static_cast<MixedPlan*>(f.impl);
+  f.impl = nullptr;
+}
+
+bem_status external_end(bem_ctx* ctx, ExtFrame& f, int nu, double* Bhat, double* AV,
+                        cudaStream_t s) {
+  MixedPlan* plan = static_cast<MixedPlan*>(f.impl);
+  bem_status st = BEM_OK;
+  if (plan->slices > plan->p.S)
+    st = near_apply32(ctx, plan->V32, nu, plan->p.nup, plan->p.C, plan->p.n_pad, plan->p.Yp,
+                      plan->p.S, s);
+  if (st == BEM_OK) mixed_post(ctx, *plan, Bhat, AV, s);
+  delete plan;
+  f.impl = nullptr;
+  if (st != BEM_OK) return st;
+  return cuda_check(ctx, cudaGetLastError(), "external projection kernels");
+}
+
 bem_status project_mixed(bem_ctx* ctx, const double* V, int64_t ldv, int nu, double* Bhat,
                          double* AV, cudaStream_t s) {
   MixedPlan plan;

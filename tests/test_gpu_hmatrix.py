@@ -52,7 +52,7 @@ def test_hmatrix_projection_matches_fp64(bem, level, op, near):
     spec = synth.ContourSpec("circle", 4.0 + 0j, 1.0, 1.0)
     N, nu = 8, 24
     ctx, z, w = _ctx(bem, mesh, spec, N, op, near)
-    ctx.set_hmatrix(leaf=32, eta=1.0, eps=1e-6, rmax=64)
+    ctx.set_hmatrix(leaf=16 if level == 3 else 32, eta=1.0, eps=1e-6, rmax=64)
     V = _dev(synth.complex_gaussian(mesh.n, nu, 3))
     B64, Y64 = ctx.project(V, bem.PREC_FP64, AV=True)
     Bh, Yh = ctx.project(V, bem.PREC_HMATRIX, AV=True)
@@ -70,12 +70,13 @@ def test_structure_and_products_match_oracle(bem):
     mesh = synth.icosphere(3)
     spec = synth.ContourSpec("circle", 4.0 + 0j, 1.0, 1.0)
     ctx, z, w = _ctx(bem, mesh, spec, 2)
-    ctx.set_hmatrix(leaf=32, eta=1.0, eps=1e-6, rmax=64)
+    ctx.set_hmatrix(leaf=16, eta=1.0, eps=1e-6, rmax=64)
     V = synth.complex_gaussian(mesh.n, 8, 4)
     _, Yh = ctx.project(_dev(V), bem.PREC_HMATRIX, AV=True)
     st = ctx.hmatrix_stats()
-    cl = ohm.cluster_tree(mesh, leaf=32)
-    bl = ohm.blocks(cl, eta=1.0)
+    cl = ohm.cluster_tree(mesh, leaf=16)
+    bl = ohm.blocks(cl, eta=1.0, leaf=16)
+    assert st["far_blocks"] > 0
     assert st["far_blocks"] == sum(1 for b in bl if b[2])
     assert st["dense_blocks"] == sum(1 for b in bl if not b[2])
     for j in range(2):
