@@ -12,11 +12,14 @@
 //   hm_aca_kernel        one CTA per far block: adaptive cross approximation with partial
 //                        pivoting on FP32 entries (block ~ U W^T, ranks up to rmax, stop at
 //                        ||u_k|| ||w_k|| <= eps ||S_k||_F with the exact norm update);
-//   hm_wtv_kernel        T_b = W_b^T V_sigma (rank x nu) per far block;
-//   hm_leaf_kernel       per leaf row range and 64 basis columns: the dense blocks of the
-//                        leaf evaluated and multiplied at once, then U_b T_b of every far
-//                        block above the leaf, in a fixed order (no atomics), into the mixed
-//                        path's FP32 partials of Y_j.
+//   hm_wtv_kernel        T_b = W_b^T V_sigma (rank x nu) per far block, as panel products in
+//                        shared memory;
+//   hm_leaf_kernel       one CTA per leaf row range: the leaf's dense column ranges evaluated
+//                        32 panels at a time from geometry staged in shared memory and
+//                        multiplied with every basis column, then the rank-1 terms of every
+//                        far block above the leaf, 32 at a time, in a fixed order (no
+//                        atomics), into the mixed path's FP32 partials of Y_j.
+// Geometry, basis and T_b are kept in cluster order, so that a cluster is a contiguous range.
 // The mixed path then adds the FP32 near-field corrections (if enabled) and forms
 // B_j = w_j V^H Y_j (tensor-core contraction for nu <= 128).
 #include <math.h>
@@ -48,8 +51,9 @@ struct HMatrix {
   std::vector<int64_t> used_off;
   std::vector<int4> leaves;    // leaf row range, then [near_begin, near_end) in `near`
   std::vector<int32_t> leaf_far_ptr, leaf_far;   // CSR: far blocks above each leaf
-  std::vector<int2> near;      // dense blocks of a leaf: sigma range
+  std::vector<int2> near;      // dense column ranges of a leaf (contiguous in cluster order)
   std::vector<int32_t> near_ptr;
+  int64_t dense_blocks = 0;    // leaf-leaf dense blocks of the partition
   // device copies
   int32_t* d_perm = nullptr;
   int4* d_far = nullptr;
@@ -60,6 +64,9 @@ struct HMatrix {
   int32_t* d_leaf_far = nullptr;
   int2* d_near = nullptr;
   int32_t* d_near_ptr = nullptr;
+  float4* d_gq = nullptr;      // geometry in cluster order: 7 n points, n normals, n centroids
+  float4* d_gn = nullptr;
+  float4* d_gc = nullptr;
   // per-node work (grown on demand)
   float2* d_uw = nullptr;
   size_t uw_bytes = 0;
@@ -70,7 +77,7 @@ struct HMatrix {
   size_t rank_cap = 0;
   float2* d_t = nullptr;
   size_t t_bytes = 0;
-  float2* d_vp = nullptr;      // V in cluster order, row-major (nu per panel), FP32
+  float2* d_vp = nullptr;      // V in cluster order, row-major (CW per panel, zero-padded), FP32
   size_t vp_bytes = 0;
   double* d_y = nullptr;       // Y_j, FP64, column-major per node
   size_t y_bytes = 0;
@@ -85,7 +92,8 @@ namespace {
 void free_dev(HMatrix& h) {
   cudaFree(h.d_perm); cudaFree(h.d_far); cudaFree(h.d_uw_off); cudaFree(h.d_used_off);
   cudaFree(h.d_leaves); cudaFree(h.d_leaf_far_ptr); cudaFree(h.d_leaf_far); cudaFree(h.d_near);
-  cudaFree(h.d_near_ptr);
+  cudaFree(h.d_near_ptr); cudaFree(h.d_gq);
+  h.d_gq = h.d_gn = h.d_gc = nullptr;
   h.d_perm = nullptr; h.d_far = nullptr; h.d_uw_off = nullptr; h.d_used_off = nullptr;
   h.d_leaves = nullptr; h.d_leaf_far_ptr = nullptr; h.d_leaf_far = nullptr; h.d_near = nullptr;
   h.d_near_ptr = nullptr;
@@ -185,40 +193,59 @@ void build_blocks(HMatrix& h, int t, int s, std::vector<int2>& far_cl,
 
 namespace {
 
+// Geometry in cluster order (structure of arrays, coalesced for consecutive panels of a
+// cluster): the 7 quadrature points (x, y, z, W/4pi) of cluster panel t at q * n + t, the
+// unit normal at t, the centroid (x, y, z, panel index as int bits) at t. FP32 values of the
+// mixed path's geometry, permuted once per block structure.
+struct HmGeom {
+  const float4* q;
+  const float4* nrm;
+  const float4* cen;
+  int64_t n;
+};
+
+__global__ void hm_geom_kernel(Geometry g, const int32_t* __restrict__ perm, float4* __restrict__ q,
+                               float4* __restrict__ nrm, float4* __restrict__ cen) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t n = g.n;
+  if (t >= n) return;
+  const int64_t l = perm[t];
+#pragma unroll
+  for (int k = 0; k < 7; ++k)
+    q[k * n + t] = make_float4(g.qp32[k * n + l], g.qp32[(7 + k) * n + l], g.qp32[(14 + k) * n + l],
+                               g.qw32[k * n + l]);
+  const float* pk = g.pack32 + l * 64;
+  nrm[t] = make_float4(pk[56], pk[57], pk[58], 0.f);
+  cen[t] = make_float4(g.cx32[l], g.cx32[n + l], g.cx32[2 * n + l], __int_as_float((int)l));
+}
+
 __device__ __forceinline__ float hm_ex2(float x) {
   float r;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
 
-// T_il(z) in FP32 for i != l (7-point rule; the general operator's factor when op is not
-// the single layer); coordinates relative to x_i.
-__device__ __forceinline__ float2 hm_entry(const Geometry& g, int64_t i, int64_t l, float kr,
-                                           float ki, const OpCoef& op, bool general) {
-  const int64_t n = g.n;
-  const float xi = g.cx32[i], yi = g.cx32[n + i], zi = g.cx32[2 * n + i];
-  float nx = 0.f, ny = 0.f, nz = 0.f;
-  if (general) {
-    const float* pk = g.pack32 + l * 64;
-    nx = pk[56];
-    ny = pk[57];
-    nz = pk[58];
-  }
+// T_il(z) in FP32 for i != l: the 7-point rule at collocation point x_i over the points
+// q[k * stride] (k = 0..6) of panel l, with the general operator's factor (normal nl) when
+// op is not the single layer; coordinates relative to x_i.
+__device__ __forceinline__ float2 hm_eval(float xi, float yi, float zi, const float4* q,
+                                          int64_t stride, float4 nl, float kr, float ki,
+                                          const OpCoef& op, bool general) {
   const float kmi = -ki * 1.4426950408889634f;
   float sr = 0.f, si = 0.f;
 #pragma unroll
-  for (int q = 0; q < 7; ++q) {
-    const float dx = g.qp32[q * n + l] - xi, dy = g.qp32[(7 + q) * n + l] - yi,
-                dz = g.qp32[(14 + q) * n + l] - zi;
+  for (int k = 0; k < 7; ++k) {
+    const float4 y = q[k * stride];
+    const float dx = y.x - xi, dy = y.y - yi, dz = y.z - zi;
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const float rs = rsqrtf(r2);
     const float r = r2 * rs;
-    const float a = g.qw32[q * n + l] * rs * hm_ex2(kmi * r);
+    const float a = y.w * rs * hm_ex2(kmi * r);
     float sn, cs;
     __sincosf(kr * r, &sn, &cs);
     if (general) {
       float fr, fi;
-      op_factor(op, (dx * nx + dy * ny + dz * nz) * rs * rs, kr * r, ki * r, fr, fi);
+      op_factor(op, (dx * nl.x + dy * nl.y + dz * nl.z) * rs * rs, kr * r, ki * r, fr, fi);
       sr += a * (cs * fr - sn * fi);
       si += a * (cs * fi + sn * fr);
     } else {
@@ -227,6 +254,14 @@ __device__ __forceinline__ float2 hm_entry(const Geometry& g, int64_t i, int64_t
     }
   }
   return make_float2(sr, si);
+}
+
+// Entry of cluster row t against cluster column u (t != u as panels).
+__device__ __forceinline__ float2 hm_entry(const HmGeom& g, int64_t t, int64_t u, float kr,
+                                           float ki, const OpCoef& op, bool general) {
+  const float4 x = g.cen[t];
+  const float4 nl = general ? g.nrm[u] : make_float4(0.f, 0.f, 0.f, 0.f);
+  return hm_eval(x.x, x.y, x.z, g.q + u, g.n, nl, kr, ki, op, general);
 }
 
 constexpr int kAcaThreads = 128;
@@ -274,7 +309,7 @@ __device__ __forceinline__ float block_sum(float v, float* sv) {
 
 // One CTA per far block: adaptive cross approximation with partial pivoting.
 __global__ void __launch_bounds__(kAcaThreads)
-hm_aca_kernel(Geometry g, const int32_t* __restrict__ perm, const int4* __restrict__ far,
+hm_aca_kernel(HmGeom g, const int4* __restrict__ far,
               const int64_t* __restrict__ uw_off, const int64_t* __restrict__ used_off,
               float kr, float ki, OpCoef op, float eps, int rmax, float2* __restrict__ uw,
               uint8_t* __restrict__ used, int32_t* __restrict__ rank) {
@@ -299,11 +334,10 @@ hm_aca_kernel(Geometry g, const int32_t* __restrict__ perm, const int4* __restri
     for (int p = tid; p < k; p += kAcaThreads) ui[p] = U[istar + (int64_t)p * m];
     __syncthreads();
     // residual row i* into W[:, k]
-    const int64_t gi = perm[f.x + istar];
     float best = -1.f;
     int bj = 0x7fffffff;
     for (int l = tid; l < n; l += kAcaThreads) {
-      float2 v = hm_entry(g, gi, perm[f.z + l], kr, ki, op, general);
+      float2 v = hm_entry(g, f.x + istar, f.z + l, kr, ki, op, general);
       for (int p = 0; p < k; ++p) {
         const float2 a = ui[p], w = W[l + (int64_t)p * n];
         v.x -= a.x * w.x - a.y * w.y;
@@ -344,10 +378,9 @@ hm_aca_kernel(Geometry g, const int32_t* __restrict__ perm, const int4* __restri
     for (int p = tid; p < k; p += kAcaThreads) wj[p] = W[bj + (int64_t)p * n];
     __syncthreads();
     // residual column j* into U[:, k]
-    const int64_t gl = perm[f.z + bj];
     float nu2 = 0.f;
     for (int i = tid; i < m; i += kAcaThreads) {
-      float2 v = hm_entry(g, perm[f.x + i], gl, kr, ki, op, general);
+      float2 v = hm_entry(g, f.x + i, f.z + bj, kr, ki, op, general);
       for (int p = 0; p < k; ++p) {
         const float2 a = U[i + (int64_t)p * m], w = wj[p];
         v.x -= a.x * w.x - a.y * w.y;
@@ -411,131 +444,248 @@ hm_aca_kernel(Geometry g, const int32_t* __restrict__ perm, const int4* __restri
   if (tid == 0) rank[b] = k;
 }
 
-// T_b = W_b^T V_sigma (rank x nu, row-major) per far block; vp is V in cluster order,
-// row-major (nu per panel), FP32.
-__global__ void __launch_bounds__(256)
+constexpr int kLeafMax = 32;   // rows of a leaf (the leaf size is capped to it)
+constexpr int kPanelK = 32;    // depth of a staged panel
+constexpr int kHmThreads = 256;
+
+// Panel products on 256 threads: A (up to 32 rows x K, in shared memory as a[row][k], row
+// stride kPanelK + 1) times B (K rows x CW = 64 NCH complex columns, row-major in shared
+// memory) accumulated into acc. Thread t owns rows t / GP + RP k (k < NCH) and the column
+// pairs cg + GP e (e < 4), cg = t % GP, GP = 8 NCH, RP = 32 / NCH: columns 2 (cg + GP e) and
+// one more, so that the lanes of a warp read consecutive 16-byte pairs of B.
+template <int NCH>
+struct Panel {
+  static constexpr int CW = 64 * NCH;
+  static constexpr int GP = 8 * NCH;
+  static constexpr int RP = kHmThreads / GP;
+  static __device__ __forceinline__ int row(int k) { return (int)threadIdx.x / GP + RP * k; }
+  static __device__ __forceinline__ int col(int e, int h) {
+    return 2 * ((int)threadIdx.x % GP + GP * e) + h;
+  }
+  static __device__ __forceinline__ void zero(float2 (&acc)[NCH][8]) {
+#pragma unroll
+    for (int k = 0; k < NCH; ++k)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[k][e] = make_float2(0.f, 0.f);
+  }
+  static __device__ __forceinline__ void mac(const float2 (*a)[kPanelK + 1], const float2* b, int K,
+                                             int rows, float2 (&acc)[NCH][8]) {
+    const int cg = (int)threadIdx.x % GP;
+    for (int kk = 0; kk < K; ++kk) {
+      float4 v[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        v[e] = *reinterpret_cast<const float4*>(b + (int64_t)kk * CW + 2 * (cg + GP * e));
+#pragma unroll
+      for (int k = 0; k < NCH; ++k) {
+        const int r = row(k);
+        if (r < rows) {
+          const float2 x = a[r][kk];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            float2& p = acc[k][2 * e];
+            float2& q = acc[k][2 * e + 1];
+            p.x = fmaf(x.x, v[e].x, fmaf(-x.y, v[e].y, p.x));
+            p.y = fmaf(x.x, v[e].y, fmaf(x.y, v[e].x, p.y));
+            q.x = fmaf(x.x, v[e].z, fmaf(-x.y, v[e].w, q.x));
+            q.y = fmaf(x.x, v[e].w, fmaf(x.y, v[e].z, q.y));
+          }
+        }
+      }
+    }
+  }
+  // B rows [0, K) from rows src + kk * CW (16-byte aligned, CW complex each)
+  static __device__ __forceinline__ void stage_b(float2* b, const float2* __restrict__ src, int K) {
+    const float4* s = reinterpret_cast<const float4*>(src);
+    float4* d = reinterpret_cast<float4*>(b);
+    for (int t = threadIdx.x; t < K * (CW / 2); t += kHmThreads) d[t] = s[t];
+  }
+  static constexpr size_t smem_bytes() {
+    return (size_t)kPanelK * CW * sizeof(float2) + kLeafMax * (kPanelK + 1) * sizeof(float2) +
+           kPanelK * 8 * sizeof(float4) + kLeafMax * sizeof(float4) + kPanelK * sizeof(int2) +
+           (kFarGroup + 1) * sizeof(int);
+  }
+  static constexpr int kFarGroup = 128;
+};
+
+// Y_j for the rows of one leaf and every basis column (one CTA per leaf):
+//   dense part: the leaf's dense column ranges (contiguous in cluster order), 32 panels at a
+//   time: their quadrature points staged, the block T(z_j)[leaf, panels] evaluated into
+//   shared memory (self entries from the FP32 self terms), times the staged basis rows;
+//   far part: the rank-1 terms u_p w_p^T of every far block above the leaf, as rows of
+//   [U_b | ...] (the leaf's rows of U_b) and [T_b; ...] (T_b = W_b^T V), 32 terms a panel;
+// in a fixed order (deterministic), then written into the FP32 partials of the mixed path.
+// vp: V in cluster order, row-major with CW columns (zero beyond nu); T rows CW wide too.
+template <int NCH>
+__global__ void __launch_bounds__(kHmThreads, NCH >= 4 ? 2 : 3)
+hm_leaf_kernel(HmGeom g, const int4* __restrict__ leaves, const int2* __restrict__ near,
+               const int32_t* __restrict__ leaf_far_ptr, const int32_t* __restrict__ leaf_far,
+               const int4* __restrict__ far, const int64_t* __restrict__ uw_off,
+               const int32_t* __restrict__ rank, const int64_t* __restrict__ toff,
+               const float2* __restrict__ uw, const float2* __restrict__ T,
+               const float2* __restrict__ vp, int nu, const float2* __restrict__ self32,
+               float kr, float ki, OpCoef op, float* __restrict__ Yp, int C, int64_t n_pad) {
+  using P = Panel<NCH>;
+  extern __shared__ float4 hm_smem[];
+  float2* sB = reinterpret_cast<float2*>(hm_smem);
+  float2(*sA)[kPanelK + 1] = reinterpret_cast<float2(*)[kPanelK + 1]>(sB + kPanelK * P::CW);
+  float4* sQ = reinterpret_cast<float4*>(&sA[kLeafMax][0]);   // [kk][8]: 7 points, normal
+  float4* sX = sQ + kPanelK * 8;
+  int2* sMap = reinterpret_cast<int2*>(sX + kLeafMax);
+  int* sPre = reinterpret_cast<int*>(sMap + kPanelK);
+  const int L = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int4 lf = leaves[L];   // rows [x, y), dense ranges [z, w)
+  const int mL = lf.y - lf.x;
+  const int64_t n = g.n;
+  const bool general = !op_single(op);
+  if (tid < kLeafMax) sX[tid] = tid < mL ? g.cen[lf.x + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
+  float2 acc[NCH][8];
+  P::zero(acc);
+  for (int nb = lf.z; nb < lf.w; ++nb) {
+    const int2 sg = near[nb];
+    for (int k0 = sg.x; k0 < sg.y; k0 += kPanelK) {
+      const int K = min(kPanelK, sg.y - k0);
+      __syncthreads();
+      for (int t = tid; t < 8 * kPanelK; t += kHmThreads) {
+        const int kk = t % kPanelK, q = t / kPanelK;
+        if (kk < K)
+          sQ[kk * 8 + q] = q < 7 ? g.q[q * n + k0 + kk]
+                                 : (general ? g.nrm[k0 + kk] : make_float4(0.f, 0.f, 0.f, 0.f));
+      }
+      P::stage_b(sB, vp + (int64_t)k0 * P::CW, K);
+      __syncthreads();
+      for (int t = tid; t < mL * K; t += kHmThreads) {
+        const int rr = t % mL, kk = t / mL;
+        const float4 x = sX[rr];
+        sA[rr][kk] = (lf.x + rr == k0 + kk)
+                         ? self32[__float_as_int(x.w)]
+                         : hm_eval(x.x, x.y, x.z, sQ + kk * 8, 1, sQ[kk * 8 + 7], kr, ki, op, general);
+      }
+      __syncthreads();
+      P::mac(sA, sB, K, mL, acc);
+    }
+  }
+  const int fe = leaf_far_ptr[L + 1];
+  for (int g0 = leaf_far_ptr[L]; g0 < fe; g0 += P::kFarGroup) {
+    const int gn = min(P::kFarGroup, fe - g0);
+    __syncthreads();
+    if (tid == 0) {   // term offsets of the group's far blocks
+      int s = 0;
+      for (int e = 0; e < gn; ++e) {
+        sPre[e] = s;
+        s += rank[leaf_far[g0 + e]];
+      }
+      sPre[gn] = s;
+    }
+    __syncthreads();
+    const int Kt = sPre[gn];
+    for (int k0 = 0; k0 < Kt; k0 += kPanelK) {
+      const int K = min(kPanelK, Kt - k0);
+      if (tid < K) {   // term k0 + tid: far block and rank index
+        const int want = k0 + tid;
+        int lo = 0, hi = gn - 1;   // the last e with sPre[e] <= want
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) / 2;
+          if (sPre[mid] <= want) lo = mid; else hi = mid - 1;
+        }
+        sMap[tid] = make_int2(leaf_far[g0 + lo], want - sPre[lo]);
+      }
+      __syncthreads();
+      for (int t = tid; t < K * (P::CW / 2); t += kHmThreads) {
+        const int kk = t / (P::CW / 2), c = t % (P::CW / 2);
+        const int2 bp = sMap[kk];
+        reinterpret_cast<float4*>(sB)[t] =
+            reinterpret_cast<const float4*>(T + toff[bp.x] + (int64_t)bp.y * P::CW)[c];
+      }
+      for (int t = tid; t < K * mL; t += kHmThreads) {
+        const int rr = t % mL, kk = t / mL;
+        const int2 bp = sMap[kk];
+        const int4 f = far[bp.x];
+        sA[rr][kk] = uw[uw_off[bp.x] + (lf.x - f.x + rr) + (int64_t)bp.y * (f.y - f.x)];
+      }
+      __syncthreads();
+      P::mac(sA, sB, K, mL, acc);
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NCH; ++k) {
+    const int r = P::row(k);
+    if (r >= mL) continue;
+    const int64_t i = __float_as_int(sX[r].w);
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = P::col(e, h);
+        if (c < nu) {   // real part at column (c / C) 2 C + c % C, imaginary part C further
+          const int64_t colr = (int64_t)(c / C) * 2 * C + c % C;
+          Yp[colr * n_pad + i] = acc[k][2 * e + h].x;
+          Yp[(colr + C) * n_pad + i] = acc[k][2 * e + h].y;
+        }
+      }
+  }
+}
+
+// T_b = W_b^T V_sigma (rank x CW, row-major) per far block (one CTA each), 32 ranks and 32
+// panels of sigma per panel product.
+template <int NCH>
+__global__ void __launch_bounds__(kHmThreads, NCH >= 4 ? 2 : 3)
 hm_wtv_kernel(const int4* __restrict__ far, const int64_t* __restrict__ uw_off,
               const int32_t* __restrict__ rank, const int64_t* __restrict__ toff, int rmax,
-              const float2* __restrict__ uw, const float2* __restrict__ vp, int nu,
+              const float2* __restrict__ uw, const float2* __restrict__ vp,
               float2* __restrict__ T) {
-  const int b = blockIdx.x;
+  using P = Panel<NCH>;
+  extern __shared__ float4 hm_smem[];
+  float2* sB = reinterpret_cast<float2*>(hm_smem);
+  float2(*sA)[kPanelK + 1] = reinterpret_cast<float2(*)[kPanelK + 1]>(sB + kPanelK * P::CW);
+  const int b = blockIdx.x, tid = threadIdx.x;
   const int4 f = far[b];
   const int m = f.y - f.x, n = f.w - f.z;
   const int r = rank[b];
   const float2* W = uw + uw_off[b] + (int64_t)m * rmax;
   float2* Tb = T + toff[b];
-  for (int idx = threadIdx.x; idx < r * nu; idx += blockDim.x) {
-    const int p = idx / nu, c = idx % nu;
-    float2 acc = make_float2(0.f, 0.f);
-    for (int l = 0; l < n; ++l) {
-      const float2 w = W[l + (int64_t)p * n], v = vp[(int64_t)(f.z + l) * nu + c];
-      acc.x += w.x * v.x - w.y * v.y;
-      acc.y += w.x * v.y + w.y * v.x;
-    }
-    Tb[idx] = acc;
-  }
-}
-
-constexpr int kLeafMax = 32;   // rows of a leaf (the leaf size is capped to it)
-constexpr int kLeafCols = 64;  // basis columns per CTA
-
-// Y_j for the rows of one leaf and 64 basis columns: its dense blocks, then U_b T_b of every
-// far block above it, in the lists' order.
-__global__ void __launch_bounds__(256)
-hm_leaf_kernel(Geometry g, const int32_t* __restrict__ perm, const int4* __restrict__ leaves,
-               const int2* __restrict__ near, const int32_t* __restrict__ leaf_far_ptr,
-               const int32_t* __restrict__ leaf_far, const int4* __restrict__ far,
-               const int64_t* __restrict__ uw_off, const int32_t* __restrict__ rank,
-               const int64_t* __restrict__ toff, int rmax, const float2* __restrict__ uw,
-               const float2* __restrict__ T, const float2* __restrict__ vp, int nu,
-               const float2* __restrict__ self32, float kr, float ki, OpCoef op,
-               float* __restrict__ Yp, int acc_cols, int C, int n_pad) {
-  __shared__ float2 sA[kLeafMax][kLeafMax + 1];
-  __shared__ float2 sV[kLeafMax][kLeafCols];
-  const int L = blockIdx.x;
-  const int c0 = blockIdx.y * kLeafCols;
-  const int4 lf = leaves[L];   // rows [x, y), dense blocks [z, w)
-  const int mL = lf.y - lf.x;
-  const int tid = threadIdx.x;
-  const int row = tid % kLeafMax, cg = tid / kLeafMax;   // columns c0 + cg + 8 q
-  const int64_t n = g.n;
-  const bool general = !op_single(op);
-  float2 acc[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
-  for (int nb = lf.z; nb < lf.w; ++nb) {
-    const int2 sg = near[nb];
-    const int ns = sg.y - sg.x;
-    __syncthreads();
-    for (int t = tid; t < kLeafMax * kLeafMax; t += 256) {
-      const int rr = t % kLeafMax, ll = t / kLeafMax;
-      float2 a = make_float2(0.f, 0.f);
-      if (rr < mL && ll < ns) {
-        const int64_t i = perm[lf.x + rr], l = perm[sg.x + ll];
-        a = (i == l) ? self32[l] : hm_entry(g, i, l, kr, ki, op, general);
+  for (int p0 = 0; p0 < r; p0 += kLeafMax) {
+    const int rows = min(kLeafMax, r - p0);
+    float2 acc[NCH][8];
+    P::zero(acc);
+    for (int l0 = 0; l0 < n; l0 += kPanelK) {
+      const int K = min(kPanelK, n - l0);
+      __syncthreads();
+      for (int t = tid; t < rows * kPanelK; t += kHmThreads) {
+        const int kk = t % kPanelK, pp = t / kPanelK;
+        if (kk < K) sA[pp][kk] = W[(l0 + kk) + (int64_t)(p0 + pp) * n];
       }
-      sA[rr][ll] = a;
+      P::stage_b(sB, vp + (int64_t)(f.z + l0) * P::CW, K);
+      __syncthreads();
+      P::mac(sA, sB, K, rows, acc);
     }
-    for (int t = tid; t < kLeafMax * kLeafCols; t += 256) {
-      const int ll = t / kLeafCols, c = t % kLeafCols;
-      sV[ll][c] = (ll < ns && c0 + c < nu) ? vp[(int64_t)(sg.x + ll) * nu + c0 + c]
-                                            : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    for (int ll = 0; ll < ns; ++ll) {
-      const float2 a = sA[row][ll];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float2 v = sV[ll][cg + 8 * q];
-        acc[q].x += a.x * v.x - a.y * v.y;
-        acc[q].y += a.x * v.y + a.y * v.x;
-      }
-    }
-  }
-  if (row < mL) {
-    for (int e = leaf_far_ptr[L]; e < leaf_far_ptr[L + 1]; ++e) {
-      const int b = leaf_far[e];
-      const int4 f = far[b];
-      const int m = f.y - f.x;
-      const int o = lf.x - f.x + row;
-      const float2* U = uw + uw_off[b];
-      const float2* Tb = T + toff[b];
-      const int r = rank[b];
-      for (int p = 0; p < r; ++p) {
-        const float2 u = U[o + (int64_t)p * m];
+    for (int k = 0; k < NCH; ++k) {
+      const int pr = P::row(k);
+      if (pr >= rows) continue;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int c = c0 + cg + 8 * q;
-          if (c < nu) {
-            const float2 t = Tb[(int64_t)p * nu + c];
-            acc[q].x += u.x * t.x - u.y * t.y;
-            acc[q].y += u.x * t.y + u.y * t.x;
-          }
-        }
-      }
-    }
-    const int64_t i = perm[lf.x + row];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int c = c0 + cg + 8 * q;
-      if (c < nu) {   // real part at column (c / C) 2 C + c % C, imaginary part C further
-        const int colr = (c / C) * 2 * C + c % C;
-        Yp[(int64_t)colr * n_pad + i] = acc[q].x;
-        Yp[(int64_t)(colr + C) * n_pad + i] = acc[q].y;
-      }
+      for (int e = 0; e < 4; ++e)
+        reinterpret_cast<float4*>(Tb + (int64_t)(p0 + pr) * P::CW)[P::col(e, 0) / 2] =
+            make_float4(acc[k][2 * e].x, acc[k][2 * e].y, acc[k][2 * e + 1].x, acc[k][2 * e + 1].y);
     }
   }
 }
 
-// vp[t][c] = V[perm[t], c] in FP32 (cluster order, row-major)
+// vp[t][c] = V[perm[t], c] in FP32 (cluster order, row-major, cw columns, zero beyond nu)
 __global__ void hm_vperm_kernel(const double2* __restrict__ V, int64_t ldv, int64_t n, int nu,
-                                const int32_t* __restrict__ perm, float2* __restrict__ vp) {
+                                int cw, const int32_t* __restrict__ perm, float2* __restrict__ vp) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= n * nu) return;
-  const int64_t row = t / nu;
-  const int c = (int)(t % nu);
-  const double2 v = V[(int64_t)c * ldv + perm[row]];
-  vp[t] = make_float2((float)v.x, (float)v.y);
+  if (t >= n * cw) return;
+  const int64_t row = t / cw;
+  const int c = (int)(t % cw);
+  float2 o = make_float2(0.f, 0.f);
+  if (c < nu) {
+    const double2 v = V[(int64_t)c * ldv + perm[row]];
+    o = make_float2((float)v.x, (float)v.y);
+  }
+  vp[t] = o;
 }
 
 }  // namespace
@@ -572,7 +722,7 @@ bem_status grow(bem_ctx* ctx, T*& p, size_t& cap, size_t bytes) {
 }
 
 // The cluster tree, the block partition and the per-leaf lists of the current mesh.
-bem_status build_structure(bem_ctx* ctx) {
+bem_status build_structure(bem_ctx* ctx, cudaStream_t s) {
   HMatrix& h = *ctx->hm;
   const int64_t n = ctx->geo.n;
   const std::vector<double>& xyz = ctx->h_xyz;
@@ -618,6 +768,16 @@ bem_status build_structure(bem_ctx* ctx) {
   std::vector<std::vector<int2>> lnear(leaf_cl.size());
   for (const int2& nb : near_cl)
     lnear[leaf_id[nb.x]].push_back(make_int2(h.cl[nb.y].b, h.cl[nb.y].e));
+  h.dense_blocks = (int64_t)near_cl.size();
+  for (std::vector<int2>& r : lnear) {   // ranges sorted, adjacent ones merged
+    std::sort(r.begin(), r.end(), [](int2 a, int2 b) { return a.x < b.x; });
+    size_t w = 0;
+    for (size_t e = 0; e < r.size(); ++e) {
+      if (w && r[w - 1].y == r[e].x) r[w - 1].y = r[e].y;
+      else r[w++] = r[e];
+    }
+    r.resize(w);
+  }
   std::vector<std::vector<int32_t>> lfar(leaf_cl.size());
   // the leaves inside a far block's row cluster are consecutive (leaves sorted by start)
   std::vector<int32_t> leaf_start(leaf_cl.size());
@@ -647,11 +807,46 @@ bem_status build_structure(bem_ctx* ctx) {
   if (st == BEM_OK) st = upload(ctx, h.d_leaf_far, h.leaf_far);
   if (st == BEM_OK) st = upload(ctx, h.d_near, h.near);
   if (st != BEM_OK) return st;
+  cudaFree(h.d_gq);
+  h.d_gq = h.d_gn = h.d_gc = nullptr;
+  if (cudaMalloc(&h.d_gq, (size_t)n * 9 * sizeof(float4)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, BEM_ENOMEM, "low-rank far field: device allocation failed");
+  }
+  h.d_gn = h.d_gq + 7 * n;
+  h.d_gc = h.d_gq + 8 * n;
+  hm_geom_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctx->geo, h.d_perm, h.d_gq, h.d_gn, h.d_gc);
+  ctx->launches++;
   h.mesh_version = ctx->mesh_version;
   return BEM_OK;
 }
 
 unsigned nblocks(int64_t count, int t = 256) { return (unsigned)((count + t - 1) / t); }
+
+// The W^T V and leaf kernels for CW = 64 NCH basis columns (the dynamic shared memory of
+// NCH = 4 exceeds the default 48 KB and is opted in).
+template <int NCH>
+bem_status hm_apply_kernels(bem_ctx* ctx, HMatrix& h, bool wtv, int j, int nu, float kr, float ki,
+                            const ExtFrame& fr, cudaStream_t s) {
+  const size_t smem = Panel<NCH>::smem_bytes();
+  if (cudaFuncSetAttribute(hm_leaf_kernel<NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaFuncSetAttribute(hm_wtv_kernel<NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return cuda_check(ctx, cudaGetLastError(), "low-rank far field kernel attributes");
+  const int64_t n = ctx->geo.n;
+  const HmGeom g{h.d_gq, h.d_gn, h.d_gc, n};
+  if (wtv) {
+    hm_wtv_kernel<NCH><<<(unsigned)h.far.size(), kHmThreads, smem, s>>>(
+        h.d_far, h.d_uw_off, h.d_rank, h.d_toff, h.rmax, h.d_uw, h.d_vp, h.d_t);
+    ctx->launches++;
+  }
+  hm_leaf_kernel<NCH><<<(unsigned)h.leaves.size(), kHmThreads, smem, s>>>(
+      g, h.d_leaves, h.d_near, h.d_leaf_far_ptr, h.d_leaf_far, h.d_far, h.d_uw_off, h.d_rank,
+      h.d_toff, h.d_uw, h.d_t, h.d_vp, nu,
+      reinterpret_cast<const float2*>(ctx->con.self32) + (int64_t)j * n, kr, ki, ctx->op,
+      fr.Yp + (int64_t)j * fr.acc_cols * fr.n_pad, fr.C, fr.n_pad);
+  ctx->launches++;
+  return cuda_check(ctx, cudaGetLastError(), "low-rank far field kernels");
+}
 
 }  // namespace
 
@@ -671,13 +866,15 @@ bem_status project_hmatrix(bem_ctx* ctx, const double* V, int64_t ldv, int nu, d
   const int N = ctx->con.N;
   if (ctx->h_xyz.empty()) return fail(ctx, BEM_ESTATE, "bem_project: no mesh set");
   bem_status st = BEM_OK;
-  if (h.mesh_version != ctx->mesh_version && (st = build_structure(ctx)) != BEM_OK) return st;
+  if (h.mesh_version != ctx->mesh_version && (st = build_structure(ctx, s)) != BEM_OK) return st;
   if ((st = ensure_self32(ctx, s)) != BEM_OK) return st;
   const size_t nfar = h.far.size();
   if ((st = grow(ctx, h.d_uw, h.uw_bytes, std::max<size_t>(1, h.uw_total) * sizeof(float2))) != BEM_OK ||
       (st = grow(ctx, h.d_used, h.used_bytes, std::max<size_t>(1, h.used_total))) != BEM_OK ||
-      (st = grow(ctx, h.d_vp, h.vp_bytes, (size_t)n * nu * sizeof(float2))) != BEM_OK)
+      (st = grow(ctx, h.d_vp, h.vp_bytes, (size_t)n * 256 * sizeof(float2))) != BEM_OK)
     return st;
+  const int nch = nu <= 64 ? 1 : nu <= 128 ? 2 : 4;   // basis columns padded to CW = 64 nch
+  const int cw = 64 * nch;
   size_t rc = h.rank_cap, tc = h.rank_cap;
   if ((st = grow(ctx, h.d_rank, rc, std::max<size_t>(1, nfar) * sizeof(int32_t))) != BEM_OK ||
       (st = grow(ctx, h.d_toff, tc, std::max<size_t>(1, nfar) * sizeof(int64_t))) != BEM_OK)
@@ -693,8 +890,8 @@ bem_status project_hmatrix(bem_ctx* ctx, const double* V, int64_t ldv, int nu, d
     external_release(fr);
     return st;
   }
-  hm_vperm_kernel<<<nblocks(n * nu), 256, 0, s>>>(reinterpret_cast<const double2*>(V), ldv, n, nu,
-                                                  h.d_perm, h.d_vp);
+  hm_vperm_kernel<<<nblocks(n * cw), 256, 0, s>>>(reinterpret_cast<const double2*>(V), ldv, n, nu,
+                                                  cw, h.d_perm, h.d_vp);
   ctx->launches++;
   std::vector<int32_t> ranks(nfar);
   std::vector<int64_t> toff(nfar);
@@ -704,7 +901,7 @@ bem_status project_hmatrix(bem_ctx* ctx, const double* V, int64_t ldv, int nu, d
     const float kr = (float)ctx->con.z_host[2 * j], ki = (float)ctx->con.z_host[2 * j + 1];
     if (nfar) {
       hm_aca_kernel<<<(unsigned)nfar, kAcaThreads, 0, s>>>(
-          ctx->geo, h.d_perm, h.d_far, h.d_uw_off, h.d_used_off, kr, ki, ctx->op, (float)h.eps,
+          HmGeom{h.d_gq, h.d_gn, h.d_gc, n}, h.d_far, h.d_uw_off, h.d_used_off, kr, ki, ctx->op, (float)h.eps,
           h.rmax, h.d_uw, h.d_used, h.d_rank);
       ctx->launches++;
       st = cuda_check(ctx, cudaMemcpyAsync(ranks.data(), h.d_rank, nfar * sizeof(int32_t),
@@ -717,7 +914,7 @@ bem_status project_hmatrix(bem_ctx* ctx, const double* V, int64_t ldv, int nu, d
       int64_t tot = 0;
       for (size_t b = 0; b < nfar; ++b) {
         toff[b] = tot;
-        tot += (int64_t)ranks[b] * nu;
+        tot += (int64_t)ranks[b] * cw;
         rank_sum += ranks[b];
         rank_max = std::max(rank_max, ranks[b]);
       }
@@ -731,18 +928,11 @@ bem_status project_hmatrix(bem_ctx* ctx, const double* V, int64_t ldv, int nu, d
         external_release(fr);
         return st;
       }
-      hm_wtv_kernel<<<(unsigned)nfar, 256, 0, s>>>(h.d_far, h.d_uw_off, h.d_rank, h.d_toff, h.rmax,
-                                                   h.d_uw, h.d_vp, nu, h.d_t);
-      ctx->launches++;
     }
-    const dim3 grid((unsigned)h.leaves.size(), (unsigned)((nu + kLeafCols - 1) / kLeafCols));
-    hm_leaf_kernel<<<grid, 256, 0, s>>>(
-        ctx->geo, h.d_perm, h.d_leaves, h.d_near, h.d_leaf_far_ptr, h.d_leaf_far, h.d_far,
-        h.d_uw_off, h.d_rank, h.d_toff, h.rmax, h.d_uw, h.d_t, h.d_vp, nu,
-        reinterpret_cast<const float2*>(ctx->con.self32) + (int64_t)j * n, kr, ki, ctx->op,
-        fr.Yp + (int64_t)j * fr.acc_cols * fr.n_pad, fr.acc_cols, fr.C, fr.n_pad);
-    ctx->launches++;
-    if ((st = cuda_check(ctx, cudaGetLastError(), "low-rank far field kernels")) != BEM_OK) {
+    st = nch == 1   ? hm_apply_kernels<1>(ctx, h, nfar > 0, j, nu, kr, ki, fr, s)
+         : nch == 2 ? hm_apply_kernels<2>(ctx, h, nfar > 0, j, nu, kr, ki, fr, s)
+                    : hm_apply_kernels<4>(ctx, h, nfar > 0, j, nu, kr, ki, fr, s);
+    if (st != BEM_OK) {
       external_release(fr);
       return st;
     }
@@ -780,7 +970,7 @@ extern "C" bem_status bem_hmatrix_stats(const bem_ctx* ctx, int64_t* far_blocks,
   if (!ctx->hm) return BEM_ESTATE;
   const HMatrix& h = *ctx->hm;
   if (far_blocks) *far_blocks = (int64_t)h.far.size();
-  if (dense_blocks) *dense_blocks = (int64_t)h.near.size();
+  if (dense_blocks) *dense_blocks = h.dense_blocks;
   if (far_fraction) *far_fraction = h.far_fraction;
   if (mean_rank) *mean_rank = h.mean_rank;
   if (max_rank) *max_rank = h.max_rank;
