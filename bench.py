@@ -204,18 +204,21 @@ def mufu_seconds_per_entry(rates, N, G, twins):
 
 
 def measured_traffic(workload, precision):
-    """DRAM bytes (read + write) per launch of the fused kernel from the committed ncu
-    summary of this workload, or None when there is none or the kernel's source has changed
-    since the counters were taken (the summary records the source's SHA-256)."""
+    """DRAM bytes (read + write) per launch of the dominant kernel (the fused kernel, or the
+    far field's leaf kernel) from the committed ncu summary of this workload, or None when
+    there is none or the kernel's source has changed since the counters were taken (the
+    summary records the source's SHA-256)."""
     import hashlib
-    if precision != "mixed":
+    names = {"mixed": ("mixed_apply", "project_mixed.cu"), "hmatrix": ("hm_leaf", "hmatrix.cu")}
+    if precision not in names:
         return None
-    path = os.path.join(ROOT, "profiles", f"mixed_apply_{workload}_traffic.json")
+    kernel, source = names[precision]
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         rec = json.load(f)
-    src = os.path.join(ROOT, "paper_1906_03938_gb300", "csrc", "project_mixed.cu")
+    src = os.path.join(ROOT, "paper_1906_03938_gb300", "csrc", source)
     with open(src, "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()
     if rec.get("source_sha256") != sha:
@@ -491,13 +494,22 @@ def run_ours(args):
     # roofline of the dominant kernel
     kern_avg = statistics.mean(kern_ms) if kern_ms else float("nan")
     if prec == bem.PREC_HMATRIX:
-        # the H-matrix evaluates a fraction of the entries: there is no single-kernel roof;
-        # "achieved" counts the n^2 N entries of the dense operator it replaces
+        # low-rank far field: the leaf kernel (dense blocks and the U_b T_b products, one
+        # launch per node) dominates. Its algorithmic work is one complex multiply-add per
+        # basis column for every dense entry and every rank-1 term of a row: 8 nu flops each,
+        # on the FP32 pipe (the entries' own evaluation, 7 points each, goes to the MUFU unit
+        # and is not counted). "value" above counts the n^2 N entries of the dense operator
+        # that the H-matrix replaces.
         st = ctx.hmatrix_stats()
-        roof = {"bound": "effective", "achieved": entries / (t_total / args.steps),
-                "peak": None, "unit": "entries/s", "frac": None,
-                "hmatrix": st, "note": "whole step; far blocks by adaptive cross approximation "
-                                       "(eps 1e-6), dense leaf blocks and products in FP32"}
+        work = ctx.hmatrix_work()
+        flops = 8.0 * nu * (work["dense_entries"] + work["far_row_terms"])
+        peak = ctx.microbench("fp32_fma")
+        roof = {"bound": "alu", "pipe": "fp32", "kernel": "hm_leaf_kernel",
+                "achieved": flops / (kern_avg * 1e-3) / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "peak_source": "measured FP32 FMA microbenchmark (bem_microbench)",
+                "flops_per_launch": flops, "hmatrix": st, "work_per_node": work,
+                "note": "far blocks by adaptive cross approximation (eps 1e-6), dense blocks "
+                        "and products in FP32"}
     elif prec == bem.PREC_FP64:
         # plain path: FP64 pipe; algorithmic work = the complex MAC of every entry with
         # every basis column, 8 nu flops per entry

@@ -131,18 +131,26 @@ bem_status bem_set_operator(bem_ctx* ctx, double cg_re, double cg_im, double ch_
  *     both clusters are leaves, else split into the children's pairs;
  *   far blocks: adaptive cross approximation with partial pivoting on FP32 entries, per
  *     node, to relative accuracy eps (stop at ||u_k|| ||w_k|| <= eps ||S_k||_F, at most
- *     rmax terms, 1..128); dense blocks evaluated in FP32; products in FP32; the near-field
- *     corrections (bem_set_near_field) and V^H Y in FP64.
+ *     rmax terms, 1..128); dense blocks evaluated in FP32; products in FP32; then the
+ *     mixed path's finish: FP32 near-field corrections (bem_set_near_field) and
+ *     B_j = w_j V^H Y_j (BF16x3 tensor-core contraction for nu <= 128).
  * The structure is built on the host at the first projection after a mesh change (from a
  * host copy of the mesh kept by bem_set_mesh) and reused; the compression runs at every
  * projection. The AV output holds the H-matrix products. Synchronises the stream (once per
  * node). bem_hmatrix_stats: far and dense block counts, the fraction of entries in far
  * blocks, mean and largest rank of the last projection (host; BEM_ESTATE before
- * bem_set_hmatrix).
+ * bem_set_hmatrix). bem_hmatrix_work: the algorithmic work of one node of the last
+ * projection, averaged over its nodes: dense entries (each evaluated once and multiplied
+ * into nu columns), sum over far blocks of rank x rows (the U_b T_b products) and of
+ * rank x columns (the W_b^T V products); any pointer may be NULL (host; BEM_ESTATE before
+ * bem_set_hmatrix). With bem_set_timing on, each node's leaf kernel (dense blocks and
+ * U_b T_b) is timed by bem_kernel_times.
  */
 bem_status bem_set_hmatrix(bem_ctx* ctx, int leaf, double eta, double eps, int rmax);
 bem_status bem_hmatrix_stats(const bem_ctx* ctx, int64_t* far_blocks, int64_t* dense_blocks,
                              double* far_fraction, double* mean_rank, int* max_rank);
+bem_status bem_hmatrix_work(const bem_ctx* ctx, double* dense_entries, double* far_row_terms,
+                            double* far_col_terms);
 
 /*
  * Node schedule of the mixed projection (an implementation detail of Eq. RR_approx's
@@ -365,7 +373,8 @@ int64_t bem_kernel_launches(const bem_ctx* ctx);
 /*
  * Diagnostics for roofline accounting (no counterpart in the paper).
  * bem_set_timing: when enable != 0, every bem_project records CUDA events on its stream
- *   around its main kernel (the fused evaluation + contraction); resets the record.
+ *   around its main kernel (the fused evaluation + contraction; with BEM_PREC_HMATRIX the
+ *   leaf kernel of every node); resets the record.
  * bem_kernel_times: durations in ms of up to max_out recorded launches (in call order),
  *   synchronising on their stop events; *count receives how many; resets the record.
  *   At most 256 launches are kept between resets.

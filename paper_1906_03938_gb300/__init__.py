@@ -47,6 +47,7 @@ SIGNATURES = {
     "bem_set_operator": (_I, [_P, _D, _D, _D, _D]),
     "bem_set_hmatrix": (_I, [_P, _I, _D, _D, _I]),
     "bem_hmatrix_stats": (_I, [_P, _P, _P, _P, _P, _P]),
+    "bem_hmatrix_work": (_I, [_P, _P, _P, _P]),
     "bem_apply_sum": (_I, [_P, _P, _P, _I64, _I, _I, _P, _P]),
     "bem_solve_sum": (_I, [_P, _P, _P, _I64, _I, _D, _I, _P, _I64, ctypes.POINTER(_I), _P, _P]),
     "bem_inverse_power_mf": (_I, [_P, _P, _I64, _I, _I, _D, _D, _D, _I, ctypes.POINTER(_I), _P]),
@@ -371,6 +372,14 @@ class Context:
             ctypes.byref(xr)))
         return {"far_blocks": fb.value, "dense_blocks": db.value, "far_fraction": ff.value,
                 "mean_rank": mr.value, "max_rank": xr.value}
+
+    def hmatrix_work(self):
+        """Algorithmic work of one node of the last far-field projection (node average):
+        dense entries, far rank x rows, far rank x columns."""
+        d, r, c = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+        self._chk("bem_hmatrix_work", self._lib.bem_hmatrix_work(
+            self._h, ctypes.byref(d), ctypes.byref(r), ctypes.byref(c)))
+        return {"dense_entries": d.value, "far_row_terms": r.value, "far_col_terms": c.value}
 
     def set_async(self, on=True):
         """Asynchronous mode: cholqr2 leaves its status check to check()."""

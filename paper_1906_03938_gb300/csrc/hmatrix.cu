@@ -85,6 +85,9 @@ struct HMatrix {
   double mean_rank = 0.0;
   int max_rank = 0;
   double far_fraction = 0.0;
+  // algorithmic work per node (averaged over the nodes of the last projection): dense
+  // entries evaluated and multiplied, rank-1 terms times rows (U T) and times columns (W^T V)
+  double dense_entries = 0.0, far_row_terms = 0.0, far_col_terms = 0.0;
 };
 
 namespace {
@@ -228,9 +231,10 @@ __device__ __forceinline__ float hm_ex2(float x) {
 // T_il(z) in FP32 for i != l: the 7-point rule at collocation point x_i over the points
 // q[k * stride] (k = 0..6) of panel l, with the general operator's factor (normal nl) when
 // op is not the single layer; coordinates relative to x_i.
+template <bool general>
 __device__ __forceinline__ float2 hm_eval(float xi, float yi, float zi, const float4* q,
                                           int64_t stride, float4 nl, float kr, float ki,
-                                          const OpCoef& op, bool general) {
+                                          const OpCoef& op) {
   const float kmi = -ki * 1.4426950408889634f;
   float sr = 0.f, si = 0.f;
 #pragma unroll
@@ -243,7 +247,7 @@ __device__ __forceinline__ float2 hm_eval(float xi, float yi, float zi, const fl
     const float a = y.w * rs * hm_ex2(kmi * r);
     float sn, cs;
     __sincosf(kr * r, &sn, &cs);
-    if (general) {
+    if constexpr (general) {
       float fr, fi;
       op_factor(op, (dx * nl.x + dy * nl.y + dz * nl.z) * rs * rs, kr * r, ki * r, fr, fi);
       sr += a * (cs * fr - sn * fi);
@@ -257,11 +261,12 @@ __device__ __forceinline__ float2 hm_eval(float xi, float yi, float zi, const fl
 }
 
 // Entry of cluster row t against cluster column u (t != u as panels).
+template <bool general>
 __device__ __forceinline__ float2 hm_entry(const HmGeom& g, int64_t t, int64_t u, float kr,
-                                           float ki, const OpCoef& op, bool general) {
+                                           float ki, const OpCoef& op) {
   const float4 x = g.cen[t];
   const float4 nl = general ? g.nrm[u] : make_float4(0.f, 0.f, 0.f, 0.f);
-  return hm_eval(x.x, x.y, x.z, g.q + u, g.n, nl, kr, ki, op, general);
+  return hm_eval<general>(x.x, x.y, x.z, g.q + u, g.n, nl, kr, ki, op);
 }
 
 constexpr int kAcaThreads = 128;
@@ -296,24 +301,34 @@ __device__ __forceinline__ void block_argmax(float& v, int& idx, float* sv, int*
   __syncthreads();
 }
 
-__device__ __forceinline__ float block_sum(float v, float* sv) {
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+// Block-wide sums of a and b (warp partials in sa, sb; the same order on every thread).
+__device__ __forceinline__ void block_sum2(float& a, float& b, float* sa, float* sb) {
+  for (int off = 16; off > 0; off >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, off);
+    b += __shfl_down_sync(0xffffffffu, b, off);
+  }
   const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
-  if (lane == 0) sv[w] = v;
+  if (lane == 0) {
+    sa[w] = a;
+    sb[w] = b;
+  }
   __syncthreads();
-  float s = 0.f;
-  for (int k = 0; k < kAcaThreads / 32; ++k) s += sv[k];
+  a = b = 0.f;
+  for (int k = 0; k < kAcaThreads / 32; ++k) {
+    a += sa[k];
+    b += sb[k];
+  }
   __syncthreads();
-  return s;
 }
 
 // One CTA per far block: adaptive cross approximation with partial pivoting.
+template <bool general>
 __global__ void __launch_bounds__(kAcaThreads)
 hm_aca_kernel(HmGeom g, const int4* __restrict__ far,
               const int64_t* __restrict__ uw_off, const int64_t* __restrict__ used_off,
               float kr, float ki, OpCoef op, float eps, int rmax, float2* __restrict__ uw,
               uint8_t* __restrict__ used, int32_t* __restrict__ rank) {
-  __shared__ float sv[kAcaThreads / 32];
+  __shared__ float sv[kAcaThreads / 32], sv2[kAcaThreads / 32];
   __shared__ int si[kAcaThreads / 32];
   __shared__ float2 ui[kMaxRank], wj[kMaxRank], au[kMaxRank], aw[kMaxRank];
   __shared__ float2 piv;
@@ -323,7 +338,6 @@ hm_aca_kernel(HmGeom g, const int4* __restrict__ far,
   float2* U = uw + uw_off[b];
   float2* W = U + (int64_t)m * rmax;
   uint8_t* fl = used + used_off[b];
-  const bool general = !op_single(op);
   for (int i = tid; i < m; i += kAcaThreads) fl[i] = 0;
   const int rcap = min(rmax, min(m, n));
   int k = 0, istar = 0, guard = 0;
@@ -337,7 +351,7 @@ hm_aca_kernel(HmGeom g, const int4* __restrict__ far,
     float best = -1.f;
     int bj = 0x7fffffff;
     for (int l = tid; l < n; l += kAcaThreads) {
-      float2 v = hm_entry(g, f.x + istar, f.z + l, kr, ki, op, general);
+      float2 v = hm_entry<general>(g, f.x + istar, f.z + l, kr, ki, op);
       for (int p = 0; p < k; ++p) {
         const float2 a = ui[p], w = W[l + (int64_t)p * n];
         v.x -= a.x * w.x - a.y * w.y;
@@ -367,11 +381,11 @@ hm_aca_kernel(HmGeom g, const int4* __restrict__ far,
     if (tid == 0) piv = W[bj + (int64_t)k * n];
     __syncthreads();
     const float2 pv = piv;
-    const float pd = pv.x * pv.x + pv.y * pv.y;
+    const float ipd = 1.f / (pv.x * pv.x + pv.y * pv.y);
     float nw = 0.f;
     for (int l = tid; l < n; l += kAcaThreads) {   // w_k = r / r[j*]
       const float2 v = W[l + (int64_t)k * n];
-      const float2 q = make_float2((v.x * pv.x + v.y * pv.y) / pd, (v.y * pv.x - v.x * pv.y) / pd);
+      const float2 q = make_float2((v.x * pv.x + v.y * pv.y) * ipd, (v.y * pv.x - v.x * pv.y) * ipd);
       W[l + (int64_t)k * n] = q;
       nw += q.x * q.x + q.y * q.y;
     }
@@ -380,7 +394,7 @@ hm_aca_kernel(HmGeom g, const int4* __restrict__ far,
     // residual column j* into U[:, k]
     float nu2 = 0.f;
     for (int i = tid; i < m; i += kAcaThreads) {
-      float2 v = hm_entry(g, f.x + i, f.z + bj, kr, ki, op, general);
+      float2 v = hm_entry<general>(g, f.x + i, f.z + bj, kr, ki, op);
       for (int p = 0; p < k; ++p) {
         const float2 a = U[i + (int64_t)p * m], w = wj[p];
         v.x -= a.x * w.x - a.y * w.y;
@@ -390,8 +404,7 @@ hm_aca_kernel(HmGeom g, const int4* __restrict__ far,
       nu2 += v.x * v.x + v.y * v.y;
     }
     __syncthreads();
-    nu2 = block_sum(nu2, sv);
-    nw = block_sum(nw, sv);
+    block_sum2(nu2, nw, sv, sv2);
     // (U^H u)_p and (W^H w)_p for p < k: warps take p in turn, lanes sum over the rows
     {
       const int wp = tid / 32, lane = tid % 32;
@@ -468,29 +481,42 @@ struct Panel {
 #pragma unroll
       for (int e = 0; e < 8; ++e) acc[k][e] = make_float2(0.f, 0.f);
   }
-  static __device__ __forceinline__ void mac(const float2 (*a)[kPanelK + 1], const float2* b, int K,
-                                             int rows, float2 (&acc)[NCH][8]) {
-    const int cg = (int)threadIdx.x % GP;
+  // the products for the first NA of the thread's rows (all of them below the row count)
+  template <int NA>
+  static __device__ __forceinline__ void mac_rows(const float2 (*a)[kPanelK + 1], const float2* b,
+                                                  int K, float2 (&acc)[NCH][8]) {
+    const int cg = (int)threadIdx.x % GP, r0 = (int)threadIdx.x / GP;
+#pragma unroll 2
     for (int kk = 0; kk < K; ++kk) {
       float4 v[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e)
         v[e] = *reinterpret_cast<const float4*>(b + (int64_t)kk * CW + 2 * (cg + GP * e));
 #pragma unroll
-      for (int k = 0; k < NCH; ++k) {
-        const int r = row(k);
-        if (r < rows) {
-          const float2 x = a[r][kk];
+      for (int k = 0; k < NA; ++k) {
+        const float2 x = a[r0 + RP * k][kk];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            float2& p = acc[k][2 * e];
-            float2& q = acc[k][2 * e + 1];
-            p.x = fmaf(x.x, v[e].x, fmaf(-x.y, v[e].y, p.x));
-            p.y = fmaf(x.x, v[e].y, fmaf(x.y, v[e].x, p.y));
-            q.x = fmaf(x.x, v[e].z, fmaf(-x.y, v[e].w, q.x));
-            q.y = fmaf(x.x, v[e].w, fmaf(x.y, v[e].z, q.y));
-          }
+        for (int e = 0; e < 4; ++e) {
+          float2& p = acc[k][2 * e];
+          float2& q = acc[k][2 * e + 1];
+          p.x = fmaf(x.x, v[e].x, fmaf(-x.y, v[e].y, p.x));
+          p.y = fmaf(x.x, v[e].y, fmaf(x.y, v[e].x, p.y));
+          q.x = fmaf(x.x, v[e].z, fmaf(-x.y, v[e].w, q.x));
+          q.y = fmaf(x.x, v[e].w, fmaf(x.y, v[e].z, q.y));
         }
+      }
+    }
+  }
+  static __device__ __forceinline__ void mac(const float2 (*a)[kPanelK + 1], const float2* b, int K,
+                                             int rows, float2 (&acc)[NCH][8]) {
+    const int r0 = (int)threadIdx.x / GP;   // the thread's rows r0 + RP k increase with k
+    const int na = r0 >= rows ? 0 : min(NCH, (rows - r0 + RP - 1) / RP);
+    if (na == NCH) mac_rows<NCH>(a, b, K, acc);
+    else if constexpr (NCH >= 2) {
+      if (na == 1) mac_rows<1>(a, b, K, acc);
+      else if constexpr (NCH >= 4) {
+        if (na == 2) mac_rows<2>(a, b, K, acc);
+        else if (na == 3) mac_rows<3>(a, b, K, acc);
       }
     }
   }
@@ -516,8 +542,8 @@ struct Panel {
 //   [U_b | ...] (the leaf's rows of U_b) and [T_b; ...] (T_b = W_b^T V), 32 terms a panel;
 // in a fixed order (deterministic), then written into the FP32 partials of the mixed path.
 // vp: V in cluster order, row-major with CW columns (zero beyond nu); T rows CW wide too.
-template <int NCH>
-__global__ void __launch_bounds__(kHmThreads, NCH >= 4 ? 2 : 3)
+template <int NCH, bool general>
+__global__ void __launch_bounds__(kHmThreads, NCH >= 4 ? 2 : 4)
 hm_leaf_kernel(HmGeom g, const int4* __restrict__ leaves, const int2* __restrict__ near,
                const int32_t* __restrict__ leaf_far_ptr, const int32_t* __restrict__ leaf_far,
                const int4* __restrict__ far, const int64_t* __restrict__ uw_off,
@@ -538,7 +564,6 @@ hm_leaf_kernel(HmGeom g, const int4* __restrict__ leaves, const int2* __restrict
   const int4 lf = leaves[L];   // rows [x, y), dense ranges [z, w)
   const int mL = lf.y - lf.x;
   const int64_t n = g.n;
-  const bool general = !op_single(op);
   if (tid < kLeafMax) sX[tid] = tid < mL ? g.cen[lf.x + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
   float2 acc[NCH][8];
   P::zero(acc);
@@ -560,7 +585,7 @@ hm_leaf_kernel(HmGeom g, const int4* __restrict__ leaves, const int2* __restrict
         const float4 x = sX[rr];
         sA[rr][kk] = (lf.x + rr == k0 + kk)
                          ? self32[__float_as_int(x.w)]
-                         : hm_eval(x.x, x.y, x.z, sQ + kk * 8, 1, sQ[kk * 8 + 7], kr, ki, op, general);
+                         : hm_eval<general>(x.x, x.y, x.z, sQ + kk * 8, 1, sQ[kk * 8 + 7], kr, ki, op);
       }
       __syncthreads();
       P::mac(sA, sB, K, mL, acc);
@@ -788,6 +813,7 @@ bem_status build_structure(bem_ctx* ctx, cudaStream_t s) {
     for (; t < leaf_cl.size() && h.cl[leaf_cl[t]].e <= f.y; ++t) lfar[t].push_back((int32_t)b);
   }
   h.near.clear();
+  h.dense_entries = 0.0;
   h.leaf_far.clear();
   h.leaf_far_ptr.assign(1, 0);
   for (size_t t = 0; t < leaf_cl.size(); ++t) {
@@ -795,6 +821,7 @@ bem_status build_structure(bem_ctx* ctx, cudaStream_t s) {
     const int nb0 = (int)h.near.size();
     for (const int2& s : lnear[t]) h.near.push_back(s);
     h.leaves.push_back(make_int4(Lc.b, Lc.e, nb0, (int)h.near.size()));
+    for (const int2& r : lnear[t]) h.dense_entries += (double)(Lc.e - Lc.b) * (r.y - r.x);
     for (int32_t b : lfar[t]) h.leaf_far.push_back(b);
     h.leaf_far_ptr.push_back((int32_t)h.leaf_far.size());
   }
@@ -825,11 +852,11 @@ unsigned nblocks(int64_t count, int t = 256) { return (unsigned)((count + t - 1)
 
 // The W^T V and leaf kernels for CW = 64 NCH basis columns (the dynamic shared memory of
 // NCH = 4 exceeds the default 48 KB and is opted in).
-template <int NCH>
+template <int NCH, bool general>
 bem_status hm_apply_kernels(bem_ctx* ctx, HMatrix& h, bool wtv, int j, int nu, float kr, float ki,
                             const ExtFrame& fr, cudaStream_t s) {
   const size_t smem = Panel<NCH>::smem_bytes();
-  if (cudaFuncSetAttribute(hm_leaf_kernel<NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+  if (cudaFuncSetAttribute(hm_leaf_kernel<NCH, general>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
       cudaFuncSetAttribute(hm_wtv_kernel<NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return cuda_check(ctx, cudaGetLastError(), "low-rank far field kernel attributes");
   const int64_t n = ctx->geo.n;
@@ -839,11 +866,13 @@ bem_status hm_apply_kernels(bem_ctx* ctx, HMatrix& h, bool wtv, int j, int nu, f
         h.d_far, h.d_uw_off, h.d_rank, h.d_toff, h.rmax, h.d_uw, h.d_vp, h.d_t);
     ctx->launches++;
   }
-  hm_leaf_kernel<NCH><<<(unsigned)h.leaves.size(), kHmThreads, smem, s>>>(
+  timing_begin(ctx, s);
+  hm_leaf_kernel<NCH, general><<<(unsigned)h.leaves.size(), kHmThreads, smem, s>>>(
       g, h.d_leaves, h.d_near, h.d_leaf_far_ptr, h.d_leaf_far, h.d_far, h.d_uw_off, h.d_rank,
       h.d_toff, h.d_uw, h.d_t, h.d_vp, nu,
       reinterpret_cast<const float2*>(ctx->con.self32) + (int64_t)j * n, kr, ki, ctx->op,
       fr.Yp + (int64_t)j * fr.acc_cols * fr.n_pad, fr.C, fr.n_pad);
+  timing_end(ctx, s);
   ctx->launches++;
   return cuda_check(ctx, cudaGetLastError(), "low-rank far field kernels");
 }
@@ -895,14 +924,21 @@ bem_status project_hmatrix(bem_ctx* ctx, const double* V, int64_t ldv, int nu, d
   ctx->launches++;
   std::vector<int32_t> ranks(nfar);
   std::vector<int64_t> toff(nfar);
-  double rank_sum = 0.0;
+  const bool single = op_single(ctx->op);
+  double rank_sum = 0.0, row_terms = 0.0, col_terms = 0.0;
   int rank_max = 0;
   for (int j = 0; j < N; ++j) {
     const float kr = (float)ctx->con.z_host[2 * j], ki = (float)ctx->con.z_host[2 * j + 1];
     if (nfar) {
-      hm_aca_kernel<<<(unsigned)nfar, kAcaThreads, 0, s>>>(
-          HmGeom{h.d_gq, h.d_gn, h.d_gc, n}, h.d_far, h.d_uw_off, h.d_used_off, kr, ki, ctx->op, (float)h.eps,
-          h.rmax, h.d_uw, h.d_used, h.d_rank);
+      const HmGeom hg{h.d_gq, h.d_gn, h.d_gc, n};
+      if (single)
+        hm_aca_kernel<false><<<(unsigned)nfar, kAcaThreads, 0, s>>>(
+            hg, h.d_far, h.d_uw_off, h.d_used_off, kr, ki, ctx->op, (float)h.eps, h.rmax, h.d_uw,
+            h.d_used, h.d_rank);
+      else
+        hm_aca_kernel<true><<<(unsigned)nfar, kAcaThreads, 0, s>>>(
+            hg, h.d_far, h.d_uw_off, h.d_used_off, kr, ki, ctx->op, (float)h.eps, h.rmax, h.d_uw,
+            h.d_used, h.d_rank);
       ctx->launches++;
       st = cuda_check(ctx, cudaMemcpyAsync(ranks.data(), h.d_rank, nfar * sizeof(int32_t),
                                            cudaMemcpyDeviceToHost, s), "rank copy");
@@ -916,6 +952,8 @@ bem_status project_hmatrix(bem_ctx* ctx, const double* V, int64_t ldv, int nu, d
         toff[b] = tot;
         tot += (int64_t)ranks[b] * cw;
         rank_sum += ranks[b];
+        row_terms += (double)ranks[b] * (h.far[b].y - h.far[b].x);
+        col_terms += (double)ranks[b] * (h.far[b].w - h.far[b].z);
         rank_max = std::max(rank_max, ranks[b]);
       }
       if ((st = grow(ctx, h.d_t, h.t_bytes, std::max<int64_t>(1, tot) * sizeof(float2))) != BEM_OK) {
@@ -929,9 +967,14 @@ bem_status project_hmatrix(bem_ctx* ctx, const double* V, int64_t ldv, int nu, d
         return st;
       }
     }
-    st = nch == 1   ? hm_apply_kernels<1>(ctx, h, nfar > 0, j, nu, kr, ki, fr, s)
-         : nch == 2 ? hm_apply_kernels<2>(ctx, h, nfar > 0, j, nu, kr, ki, fr, s)
-                    : hm_apply_kernels<4>(ctx, h, nfar > 0, j, nu, kr, ki, fr, s);
+    if (single)
+      st = nch == 1   ? hm_apply_kernels<1, false>(ctx, h, nfar > 0, j, nu, kr, ki, fr, s)
+           : nch == 2 ? hm_apply_kernels<2, false>(ctx, h, nfar > 0, j, nu, kr, ki, fr, s)
+                      : hm_apply_kernels<4, false>(ctx, h, nfar > 0, j, nu, kr, ki, fr, s);
+    else
+      st = nch == 1   ? hm_apply_kernels<1, true>(ctx, h, nfar > 0, j, nu, kr, ki, fr, s)
+           : nch == 2 ? hm_apply_kernels<2, true>(ctx, h, nfar > 0, j, nu, kr, ki, fr, s)
+                      : hm_apply_kernels<4, true>(ctx, h, nfar > 0, j, nu, kr, ki, fr, s);
     if (st != BEM_OK) {
       external_release(fr);
       return st;
@@ -939,6 +982,8 @@ bem_status project_hmatrix(bem_ctx* ctx, const double* V, int64_t ldv, int nu, d
   }
   h.mean_rank = nfar ? rank_sum / ((double)nfar * N) : 0.0;
   h.max_rank = rank_max;
+  h.far_row_terms = row_terms / N;
+  h.far_col_terms = col_terms / N;
   return external_end(ctx, fr, nu, Bhat, AV, s);
 }
 
@@ -960,6 +1005,17 @@ extern "C" bem_status bem_set_hmatrix(bem_ctx* ctx, int leaf, double eta, double
   h.rmax = rmax;
   h.mesh_version = -1;   // rebuilt (and its storage re-laid out) by the next projection
   free_work(h);
+  return BEM_OK;
+}
+
+extern "C" bem_status bem_hmatrix_work(const bem_ctx* ctx, double* dense_entries,
+                                       double* far_row_terms, double* far_col_terms) {
+  if (!ctx) return BEM_EINVAL;
+  if (!ctx->hm) return BEM_ESTATE;
+  const HMatrix& h = *ctx->hm;
+  if (dense_entries) *dense_entries = h.dense_entries;
+  if (far_row_terms) *far_row_terms = h.far_row_terms;
+  if (far_col_terms) *far_col_terms = h.far_col_terms;
   return BEM_OK;
 }
 
