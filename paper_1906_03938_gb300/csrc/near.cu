@@ -361,8 +361,99 @@ near_apply64_kernel(Geometry g, const int32_t* __restrict__ ptr, const int32_t* 
   }
 }
 
+// Row of every pair of the list (rows[e] = i for e in [ptr[i], ptr[i + 1])).
+__global__ void near_rows_kernel(const int32_t* __restrict__ ptr, int64_t n, int32_t* __restrict__ rows) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) rows[e] = (int32_t)i;
+}
+
+constexpr int kNearNodes = 8;   // contour nodes per thread of the value kernel
+
+// C[j][e] = (A_near - A_7)(z_j) of pair e (single layer, FP32): one thread per pair and
+// group of up to 8 nodes. The pair's frame (FP64, rounded to FP32 relative to x_i) and the
+// 71 points' distances are formed once and shared by the group's nodes, whose kernel
+// values take one ex2 and one sine / cosine each (MUFU approximations, as the fused
+// kernel's; the FP64 path and the residuals keep the exact functions).
+__global__ void __launch_bounds__(256, 3)
+near_values32_kernel(Geometry g, const int32_t* __restrict__ rows, const int32_t* __restrict__ cols,
+                     int64_t nnz, const double* __restrict__ z, int N, GL8 gl,
+                     float2* __restrict__ Cv) {
+  __shared__ float s_x[8], s_w[64];
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      s_x[p] = (float)gl.x[p];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s_w[8 * p + q] = (float)(gl.w[p] * gl.w[q]);
+    }
+  }
+  __syncthreads();
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int groups = (N + kNearNodes - 1) / kNearNodes;
+  if (t >= nnz * groups) return;
+  const int64_t e = t % nnz;
+  const int j0 = (int)(t / nnz) * kNearNodes;
+  const int cnt = min(kNearNodes, N - j0);
+  const int64_t n = g.n;
+  const int64_t i = rows[e], l = cols[e];
+  const double x[3] = {g.cx[i], g.cx[n + i], g.cx[2 * n + i]};
+  NearFrame F;
+  near_frame(g, l, x, F);
+  const float ax = (float)(F.a[0] - x[0]), ay = (float)(F.a[1] - x[1]), az = (float)(F.a[2] - x[2]);
+  const float abx = (float)F.ab[0], aby = (float)F.ab[1], abz = (float)F.ab[2];
+  const float bcx = (float)F.bc[0], bcy = (float)F.bc[1], bcz = (float)F.bc[2];
+  const float scale = (float)F.scale;
+  float kr[kNearNodes], km[kNearNodes];   // Re k, -Im k log2(e)
+  float2 acc[kNearNodes];
+#pragma unroll
+  for (int u = 0; u < kNearNodes; ++u) {
+    const int j = j0 + (u < cnt ? u : 0);
+    kr[u] = (float)z[2 * j];
+    km[u] = -(float)z[2 * j + 1] * 1.4426950408889634f;
+    acc[u] = make_float2(0.f, 0.f);
+  }
+  // amp = W / r at distance r, added for every node of the group
+  auto add = [&](float amp, float r) {
+#pragma unroll
+    for (int u = 0; u < kNearNodes; ++u) {
+      float sn, cs, ex;
+      asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex) : "f"(km[u] * r));
+      __sincosf(kr[u] * r, &sn, &cs);
+      const float a = amp * ex;
+      acc[u].x = fmaf(a, cs, acc[u].x);
+      acc[u].y = fmaf(a, sn, acc[u].y);
+    }
+  };
+#pragma unroll 1
+  for (int p = 0; p < 8; ++p) {
+    const float sp = s_x[p];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float st = sp * s_x[q];
+      const float dx = ax + sp * abx + st * bcx, dy = ay + sp * aby + st * bcy,
+                  dz = az + sp * abz + st * bcz;
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      const float rs = rsqrtf(r2);
+      add(s_w[8 * p + q] * sp * scale * rs, r2 * rs);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    const float dx = (float)(g.qp[q * n + l] - x[0]), dy = (float)(g.qp[(7 + q) * n + l] - x[1]),
+                dz = (float)(g.qp[(14 + q) * n + l] - x[2]);
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const float rs = rsqrtf(r2);
+    add(-(float)g.qw[q * n + l] * rs, r2 * rs);
+  }
+#pragma unroll
+  for (int u = 0; u < kNearNodes; ++u)
+    if (u < cnt) Cv[(int64_t)(j0 + u) * nnz + e] = acc[u];
+}
+
 // Slice `slice` of the mixed path's partials := C(z_j) V in FP32 (every row < n_pad and
-// every column < nu written); one warp per (row i, node j).
+// every column < nu written); one warp per (row i, node j), the pair values evaluated here
+// (the surrogate network and the general operator).
 __global__ void __launch_bounds__(256)
 near_apply32_kernel(Geometry g, const int32_t* __restrict__ ptr, const int32_t* __restrict__ cols,
                     const double* __restrict__ z, int N, const float2* __restrict__ Vt, int nu,
@@ -402,6 +493,62 @@ near_apply32_kernel(Geometry g, const int32_t* __restrict__ ptr, const int32_t* 
             const float2 v = vr[c];
             acc[cg].x += cx * v.x - cy * v.y;
             acc[cg].y += cx * v.y + cy * v.x;
+          }
+        }
+      }
+    }
+  }
+  const int acc_cols = 2 * nup;
+  float* base = Yp + ((size_t)slice * N + node) * acc_cols * (size_t)n_pad;
+#pragma unroll
+  for (int cg = 0; cg < kMaxColGroups; ++cg) {
+    const int c = lane + 32 * cg;
+    if (c < nu) {
+      const int colr = (c / C) * 2 * C + (c % C);
+      base[(size_t)colr * n_pad + i] = acc[cg].x;
+      base[(size_t)(colr + C) * n_pad + i] = acc[cg].y;
+    }
+  }
+}
+
+// The same slice from stored pair values Cv (node-major, nnz per node): one warp per
+// (row i, node j); lanes load 32 pairs' values and columns, then sweep the basis columns.
+__global__ void __launch_bounds__(256)
+near_spmm32_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ cols, int64_t n,
+                   int64_t nnz, int N, const float2* __restrict__ Cv, const float2* __restrict__ Vt,
+                   int nu, int nup, int C, int n_pad, float* __restrict__ Yp, int slice) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x % 32;
+  if (w >= (int64_t)n_pad * N) return;
+  const int64_t i = w % n_pad;
+  const int node = (int)(w / n_pad);
+  float2 acc[kMaxColGroups];
+#pragma unroll
+  for (int t = 0; t < kMaxColGroups; ++t) acc[t] = make_float2(0.f, 0.f);
+  if (i < n) {
+    const int32_t e0 = ptr[i], e1 = ptr[i + 1];
+    const float2* Cj = Cv + (int64_t)node * nnz;
+    for (int32_t eb = e0; eb < e1; eb += 32) {
+      const int32_t e = eb + lane;
+      float2 cval = make_float2(0.f, 0.f);
+      int32_t l = 0;
+      if (e < e1) {
+        l = cols[e];
+        cval = Cj[e];
+      }
+      const int cnt = min(32, e1 - eb);
+      for (int t = 0; t < cnt; ++t) {
+        const float cx = __shfl_sync(0xffffffffu, cval.x, t);
+        const float cy = __shfl_sync(0xffffffffu, cval.y, t);
+        const int32_t lt = __shfl_sync(0xffffffffu, l, t);
+        const float2* vr = Vt + (int64_t)lt * nu;
+#pragma unroll
+        for (int cg = 0; cg < kMaxColGroups; ++cg) {
+          const int c = lane + 32 * cg;
+          if (c < nu) {
+            const float2 v = vr[c];
+            acc[cg].x = fmaf(cx, v.x, fmaf(-cy, v.y, acc[cg].x));
+            acc[cg].y = fmaf(cx, v.y, fmaf(cy, v.x, acc[cg].y));
           }
         }
       }
@@ -622,17 +769,39 @@ bem_status near_apply64(bem_ctx* ctx, const double* V, int64_t ldv, int nu, doub
 bem_status near_apply32(bem_ctx* ctx, const float2* V32, int nu, int nup, int C, int n_pad,
                         float* Yp, int slice, cudaStream_t s) {
   const int64_t n = ctx->geo.n;
-  bem_status st = ensure_near_work(ctx, (size_t)n * nu * sizeof(float2));
+  const int N = ctx->con.N;
+  const int64_t nnz = ctx->near_nnz;
+  // the inference copy of the network (BF16-rounded weights) follows the master weights
+  const float* net = (ctx->near_mode == 2 && ctx->net_ready) ? ctx->d_net + kNetFloats : nullptr;
+  // single layer with the 64-point rule: the pair values of every node first (work buffer:
+  // the row-major basis, then N x nnz values, then the pairs' rows)
+  const bool values = !net && op_single(ctx->op) && nnz > 0;
+  const size_t vt_bytes = (size_t)n * nu * sizeof(float2);
+  const size_t cv_bytes = values ? (size_t)N * nnz * sizeof(float2) : 0;
+  bem_status st = ensure_near_work(ctx, vt_bytes + cv_bytes + (values ? (size_t)nnz * sizeof(int32_t) : 0));
   if (st != BEM_OK) return st;
   float2* Vt = reinterpret_cast<float2*>(ctx->d_near_work);
   transpose32_kernel<<<(unsigned)((n * nu + 255) / 256), 256, 0, s>>>(V32, n, nu, Vt);
-  const int N = ctx->con.N;
-  // the inference copy of the network (BF16-rounded weights) follows the master weights
-  const float* net = (ctx->near_mode == 2 && ctx->net_ready) ? ctx->d_net + kNetFloats : nullptr;
-  near_apply32_kernel<<<(unsigned)((32 * (int64_t)n_pad * N + 255) / 256), 256, 0, s>>>(
-      ctx->geo, ctx->d_near_ptr, ctx->d_near_cols, ctx->con.z, N, Vt, nu, nup, C, n_pad, Yp, slice,
-      gl8(), net, ctx->op);
-  ctx->launches += 2;
+  ctx->launches++;
+  float2* Cv = nullptr;
+  if (values) {
+    Cv = reinterpret_cast<float2*>(static_cast<char*>(ctx->d_near_work) + vt_bytes);
+    int32_t* rows = reinterpret_cast<int32_t*>(static_cast<char*>(ctx->d_near_work) + vt_bytes + cv_bytes);
+    near_rows_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctx->d_near_ptr, n, rows);
+    const int64_t threads = nnz * ((N + kNearNodes - 1) / kNearNodes);
+    near_values32_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+        ctx->geo, rows, ctx->d_near_cols, nnz, ctx->con.z, N, gl8(), Cv);
+    ctx->launches += 2;
+  }
+  const unsigned blocks = (unsigned)((32 * (int64_t)n_pad * N + 255) / 256);
+  if (Cv)
+    near_spmm32_kernel<<<blocks, 256, 0, s>>>(ctx->d_near_ptr, ctx->d_near_cols, n, nnz, N, Cv, Vt,
+                                              nu, nup, C, n_pad, Yp, slice);
+  else
+    near_apply32_kernel<<<blocks, 256, 0, s>>>(
+        ctx->geo, ctx->d_near_ptr, ctx->d_near_cols, ctx->con.z, N, Vt, nu, nup, C, n_pad, Yp,
+        slice, gl8(), net, ctx->op);
+  ctx->launches++;
   return cuda_check(ctx, cudaGetLastError(), "near field kernels");
 }
 
