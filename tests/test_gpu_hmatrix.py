@@ -66,6 +66,30 @@ def test_hmatrix_projection_matches_fp64(bem, level, op, near):
     ctx.close()
 
 
+@pytest.mark.parametrize("nu", [100, 200], ids=["nu100-two-chunks", "nu200-four-chunks"])
+def test_hmatrix_wide_bases(bem, nu):
+    """Basis widths of two and four 64-column chunks (ragged: zero-padded columns)."""
+    mesh = synth.icosphere(4)
+    spec = synth.ContourSpec("circle", 4.0 + 0j, 1.0, 1.0)
+    N = 4
+    ctx, z, w = _ctx(bem, mesh, spec, N)
+    ctx.set_hmatrix(leaf=32, eta=1.0, eps=1e-6, rmax=64)
+    V = _dev(synth.complex_gaussian(mesh.n, nu, 7))
+    B64, Y64 = ctx.project(V, bem.PREC_FP64, AV=True)
+    Bh, Yh = ctx.project(V, bem.PREC_HMATRIX, AV=True)
+    ctx.check()
+    eb = max(_relerr(Bh[j].cpu().numpy(), B64[j].cpu().numpy()) for j in range(N))
+    ey = max(_relerr(Yh[j].cpu().numpy(), Y64[j].cpu().numpy()) for j in range(N))
+    st, work = ctx.hmatrix_stats(), ctx.hmatrix_work()
+    print(f"nu={nu}: Bhat {eb:.1e}, AV {ey:.1e}, {work}")
+    assert eb < 1e-4 and ey < 1e-4
+    # the dense work is every entry outside the far blocks, evaluated once
+    n2 = float(mesh.n) ** 2
+    assert abs(work["dense_entries"] - (1.0 - st["far_fraction"]) * n2) <= 1e-9 * n2
+    assert work["far_row_terms"] > 0 and work["far_col_terms"] > 0
+    ctx.close()
+
+
 def test_structure_and_products_match_oracle(bem):
     mesh = synth.icosphere(3)
     spec = synth.ContourSpec("circle", 4.0 + 0j, 1.0, 1.0)
