@@ -54,6 +54,7 @@ struct HMatrix {
   std::vector<int2> near;      // dense column ranges of a leaf (contiguous in cluster order)
   std::vector<int32_t> near_ptr;
   int64_t dense_blocks = 0;    // leaf-leaf dense blocks of the partition
+  int nbig = 0;                // far blocks (the first ones) of at least kAcaBig rows + columns
   // device copies
   int32_t* d_perm = nullptr;
   int4* d_far = nullptr;
@@ -269,10 +270,13 @@ __device__ __forceinline__ float2 hm_entry(const HmGeom& g, int64_t t, int64_t u
   return hm_eval<general>(x.x, x.y, x.z, g.q + u, g.n, nl, kr, ki, op);
 }
 
-constexpr int kAcaThreads = 128;
+constexpr int kAcaThreads = 128;      // threads per far block
+constexpr int kAcaThreadsBig = 256;   // for blocks of at least kAcaBig rows + columns
+constexpr int kAcaBig = 1024;
 constexpr int kMaxRank = 128;
 
-// Block-wide argmax of (v, i): the largest v, the smallest i among equals.
+// Block-wide argmax of (v, i) over NT threads: the largest v, the smallest i among equals.
+template <int NT>
 __device__ __forceinline__ void block_argmax(float& v, int& idx, float* sv, int* si) {
   for (int off = 16; off > 0; off >>= 1) {
     const float ov = __shfl_down_sync(0xffffffffu, v, off);
@@ -289,7 +293,7 @@ __device__ __forceinline__ void block_argmax(float& v, int& idx, float* sv, int*
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int k = 1; k < kAcaThreads / 32; ++k)
+    for (int k = 1; k < NT / 32; ++k)
       if (sv[k] > sv[0] || (sv[k] == sv[0] && si[k] < si[0])) {
         sv[0] = sv[k];
         si[0] = si[k];
@@ -301,7 +305,9 @@ __device__ __forceinline__ void block_argmax(float& v, int& idx, float* sv, int*
   __syncthreads();
 }
 
-// Block-wide sums of a and b (warp partials in sa, sb; the same order on every thread).
+// Block-wide sums of a and b over NT threads (warp partials in sa, sb; the same order on
+// every thread).
+template <int NT>
 __device__ __forceinline__ void block_sum2(float& a, float& b, float* sa, float* sb) {
   for (int off = 16; off > 0; off >>= 1) {
     a += __shfl_down_sync(0xffffffffu, a, off);
@@ -314,7 +320,7 @@ __device__ __forceinline__ void block_sum2(float& a, float& b, float* sa, float*
   }
   __syncthreads();
   a = b = 0.f;
-  for (int k = 0; k < kAcaThreads / 32; ++k) {
+  for (int k = 0; k < NT / 32; ++k) {
     a += sa[k];
     b += sb[k];
   }
@@ -322,35 +328,35 @@ __device__ __forceinline__ void block_sum2(float& a, float& b, float* sa, float*
 }
 
 // One CTA per far block: adaptive cross approximation with partial pivoting.
-template <bool general>
-__global__ void __launch_bounds__(kAcaThreads)
-hm_aca_kernel(HmGeom g, const int4* __restrict__ far,
+template <bool general, int NT>
+__global__ void __launch_bounds__(NT)
+hm_aca_kernel(int base, HmGeom g, const int4* __restrict__ far,
               const int64_t* __restrict__ uw_off, const int64_t* __restrict__ used_off,
               float kr, float ki, OpCoef op, float eps, int rmax, float2* __restrict__ uw,
               uint8_t* __restrict__ used, int32_t* __restrict__ rank) {
-  __shared__ float sv[kAcaThreads / 32], sv2[kAcaThreads / 32];
-  __shared__ int si[kAcaThreads / 32];
+  __shared__ float sv[NT / 32], sv2[NT / 32];
+  __shared__ int si[NT / 32];
   __shared__ float2 ui[kMaxRank], wj[kMaxRank], au[kMaxRank], aw[kMaxRank];
   __shared__ float2 piv;
-  const int b = blockIdx.x, tid = threadIdx.x;
+  const int b = base + (int)blockIdx.x, tid = threadIdx.x;
   const int4 f = far[b];
   const int m = f.y - f.x, n = f.w - f.z;
   float2* U = uw + uw_off[b];
   float2* W = U + (int64_t)m * rmax;
   uint8_t* fl = used + used_off[b];
-  for (int i = tid; i < m; i += kAcaThreads) fl[i] = 0;
+  for (int i = tid; i < m; i += NT) fl[i] = 0;
   const int rcap = min(rmax, min(m, n));
   int k = 0, istar = 0, guard = 0;
   float norm2 = 0.f;
   __syncthreads();
   while (k < rcap && guard++ < m + rcap) {
     if (tid == 0) fl[istar] = 1;
-    for (int p = tid; p < k; p += kAcaThreads) ui[p] = U[istar + (int64_t)p * m];
+    for (int p = tid; p < k; p += NT) ui[p] = U[istar + (int64_t)p * m];
     __syncthreads();
     // residual row i* into W[:, k]
     float best = -1.f;
     int bj = 0x7fffffff;
-    for (int l = tid; l < n; l += kAcaThreads) {
+    for (int l = tid; l < n; l += NT) {
       float2 v = hm_entry<general>(g, f.x + istar, f.z + l, kr, ki, op);
       for (int p = 0; p < k; ++p) {
         const float2 a = ui[p], w = W[l + (int64_t)p * n];
@@ -364,16 +370,16 @@ hm_aca_kernel(HmGeom g, const int4* __restrict__ far,
         bj = l;
       }
     }
-    block_argmax(best, bj, sv, si);
+    block_argmax<NT>(best, bj, sv, si);
     if (!(best > 0.f)) {   // a zero residual row: the next unused row, if any
       float fv = -1.f;
       int fi = 0x7fffffff;
-      for (int i = tid; i < m; i += kAcaThreads)
+      for (int i = tid; i < m; i += NT)
         if (!fl[i] && fv < 0.f) {
           fv = 0.f;
           fi = i;
         }
-      block_argmax(fv, fi, sv, si);
+      block_argmax<NT>(fv, fi, sv, si);
       if (fv < 0.f) break;
       istar = fi;
       continue;
@@ -383,17 +389,17 @@ hm_aca_kernel(HmGeom g, const int4* __restrict__ far,
     const float2 pv = piv;
     const float ipd = 1.f / (pv.x * pv.x + pv.y * pv.y);
     float nw = 0.f;
-    for (int l = tid; l < n; l += kAcaThreads) {   // w_k = r / r[j*]
+    for (int l = tid; l < n; l += NT) {   // w_k = r / r[j*]
       const float2 v = W[l + (int64_t)k * n];
       const float2 q = make_float2((v.x * pv.x + v.y * pv.y) * ipd, (v.y * pv.x - v.x * pv.y) * ipd);
       W[l + (int64_t)k * n] = q;
       nw += q.x * q.x + q.y * q.y;
     }
-    for (int p = tid; p < k; p += kAcaThreads) wj[p] = W[bj + (int64_t)p * n];
+    for (int p = tid; p < k; p += NT) wj[p] = W[bj + (int64_t)p * n];
     __syncthreads();
     // residual column j* into U[:, k]
     float nu2 = 0.f;
-    for (int i = tid; i < m; i += kAcaThreads) {
+    for (int i = tid; i < m; i += NT) {
       float2 v = hm_entry<general>(g, f.x + i, f.z + bj, kr, ki, op);
       for (int p = 0; p < k; ++p) {
         const float2 a = U[i + (int64_t)p * m], w = wj[p];
@@ -404,11 +410,11 @@ hm_aca_kernel(HmGeom g, const int4* __restrict__ far,
       nu2 += v.x * v.x + v.y * v.y;
     }
     __syncthreads();
-    block_sum2(nu2, nw, sv, sv2);
+    block_sum2<NT>(nu2, nw, sv, sv2);
     // (U^H u)_p and (W^H w)_p for p < k: warps take p in turn, lanes sum over the rows
     {
       const int wp = tid / 32, lane = tid % 32;
-      for (int p = wp; p < k; p += kAcaThreads / 32) {
+      for (int p = wp; p < k; p += NT / 32) {
         float2 a = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
         for (int i = lane; i < m; i += 32) {
           const float2 x = U[i + (int64_t)p * m], y = U[i + (int64_t)k * m];
@@ -441,7 +447,7 @@ hm_aca_kernel(HmGeom g, const int4* __restrict__ far,
     // next row: the largest |u_k| among the unused rows
     float bv = -1.f;
     int bi = 0x7fffffff;
-    for (int i = tid; i < m; i += kAcaThreads) {
+    for (int i = tid; i < m; i += NT) {
       if (fl[i]) continue;
       const float2 v = U[i + (int64_t)(k - 1) * m];
       const float mag = v.x * v.x + v.y * v.y;
@@ -450,7 +456,7 @@ hm_aca_kernel(HmGeom g, const int4* __restrict__ far,
         bi = i;
       }
     }
-    block_argmax(bv, bi, sv, si);
+    block_argmax<NT>(bv, bi, sv, si);
     if (bv < 0.f) break;
     istar = bi;
   }
@@ -463,40 +469,43 @@ constexpr int kHmThreads = 256;
 
 // Panel products on 256 threads: A (up to 32 rows x K, in shared memory as a[row][k], row
 // stride kPanelK + 1) times B (K rows x CW = 64 NCH complex columns, row-major in shared
-// memory) accumulated into acc. Thread t owns rows t / GP + RP k (k < NCH) and the column
-// pairs cg + GP e (e < 4), cg = t % GP, GP = 8 NCH, RP = 32 / NCH: columns 2 (cg + GP e) and
-// one more, so that the lanes of a warp read consecutive 16-byte pairs of B.
+// memory) accumulated into acc. A warp owns one row per item: thread t owns rows
+// t / 32 + 8 k (k < 4) and the column pairs cg + 32 e (e < NCH), cg = t % 32: columns
+// 2 (cg + 32 e) and one more, so that the lanes of a warp read consecutive 16-byte pairs of
+// B and one element of A.
 template <int NCH>
 struct Panel {
   static constexpr int CW = 64 * NCH;
-  static constexpr int GP = 8 * NCH;
+  static constexpr int GP = 32;
   static constexpr int RP = kHmThreads / GP;
+  static constexpr int NI = kLeafMax / RP;   // rows (items) per thread
+  static constexpr int NE = 2 * NCH;         // columns per thread and row
   static __device__ __forceinline__ int row(int k) { return (int)threadIdx.x / GP + RP * k; }
   static __device__ __forceinline__ int col(int e, int h) {
     return 2 * ((int)threadIdx.x % GP + GP * e) + h;
   }
-  static __device__ __forceinline__ void zero(float2 (&acc)[NCH][8]) {
+  static __device__ __forceinline__ void zero(float2 (&acc)[NI][NE]) {
 #pragma unroll
-    for (int k = 0; k < NCH; ++k)
+    for (int k = 0; k < NI; ++k)
 #pragma unroll
-      for (int e = 0; e < 8; ++e) acc[k][e] = make_float2(0.f, 0.f);
+      for (int e = 0; e < NE; ++e) acc[k][e] = make_float2(0.f, 0.f);
   }
   // the products for the first NA of the thread's rows (all of them below the row count)
   template <int NA>
   static __device__ __forceinline__ void mac_rows(const float2 (*a)[kPanelK + 1], const float2* b,
-                                                  int K, float2 (&acc)[NCH][8]) {
+                                                  int K, float2 (&acc)[NI][NE]) {
     const int cg = (int)threadIdx.x % GP, r0 = (int)threadIdx.x / GP;
 #pragma unroll 2
     for (int kk = 0; kk < K; ++kk) {
-      float4 v[4];
+      float4 v[NCH];
 #pragma unroll
-      for (int e = 0; e < 4; ++e)
+      for (int e = 0; e < NCH; ++e)
         v[e] = *reinterpret_cast<const float4*>(b + (int64_t)kk * CW + 2 * (cg + GP * e));
 #pragma unroll
       for (int k = 0; k < NA; ++k) {
         const float2 x = a[r0 + RP * k][kk];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
+        for (int e = 0; e < NCH; ++e) {
           float2& p = acc[k][2 * e];
           float2& q = acc[k][2 * e + 1];
           p.x = fmaf(x.x, v[e].x, fmaf(-x.y, v[e].y, p.x));
@@ -508,17 +517,14 @@ struct Panel {
     }
   }
   static __device__ __forceinline__ void mac(const float2 (*a)[kPanelK + 1], const float2* b, int K,
-                                             int rows, float2 (&acc)[NCH][8]) {
+                                             int rows, float2 (&acc)[NI][NE]) {
     const int r0 = (int)threadIdx.x / GP;   // the thread's rows r0 + RP k increase with k
-    const int na = r0 >= rows ? 0 : min(NCH, (rows - r0 + RP - 1) / RP);
-    if (na == NCH) mac_rows<NCH>(a, b, K, acc);
-    else if constexpr (NCH >= 2) {
-      if (na == 1) mac_rows<1>(a, b, K, acc);
-      else if constexpr (NCH >= 4) {
-        if (na == 2) mac_rows<2>(a, b, K, acc);
-        else if (na == 3) mac_rows<3>(a, b, K, acc);
-      }
-    }
+    const int na = r0 >= rows ? 0 : min(NI, (rows - r0 + RP - 1) / RP);
+    static_assert(NI == 4, "four rows per thread");
+    if (na == 4) mac_rows<4>(a, b, K, acc);
+    else if (na == 3) mac_rows<3>(a, b, K, acc);
+    else if (na == 2) mac_rows<2>(a, b, K, acc);
+    else if (na == 1) mac_rows<1>(a, b, K, acc);
   }
   // B rows [0, K) from rows src + kk * CW (16-byte aligned, CW complex each)
   static __device__ __forceinline__ void stage_b(float2* b, const float2* __restrict__ src, int K) {
@@ -565,7 +571,7 @@ hm_leaf_kernel(HmGeom g, const int4* __restrict__ leaves, const int2* __restrict
   const int mL = lf.y - lf.x;
   const int64_t n = g.n;
   if (tid < kLeafMax) sX[tid] = tid < mL ? g.cen[lf.x + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
-  float2 acc[NCH][8];
+  float2 acc[P::NI][P::NE];
   P::zero(acc);
   for (int nb = lf.z; nb < lf.w; ++nb) {
     const int2 sg = near[nb];
@@ -635,12 +641,12 @@ hm_leaf_kernel(HmGeom g, const int4* __restrict__ leaves, const int2* __restrict
     }
   }
 #pragma unroll
-  for (int k = 0; k < NCH; ++k) {
+  for (int k = 0; k < P::NI; ++k) {
     const int r = P::row(k);
     if (r >= mL) continue;
     const int64_t i = __float_as_int(sX[r].w);
 #pragma unroll
-    for (int e = 0; e < 4; ++e)
+    for (int e = 0; e < NCH; ++e)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int c = P::col(e, h);
@@ -673,7 +679,7 @@ hm_wtv_kernel(const int4* __restrict__ far, const int64_t* __restrict__ uw_off,
   float2* Tb = T + toff[b];
   for (int p0 = 0; p0 < r; p0 += kLeafMax) {
     const int rows = min(kLeafMax, r - p0);
-    float2 acc[NCH][8];
+    float2 acc[P::NI][P::NE];
     P::zero(acc);
     for (int l0 = 0; l0 < n; l0 += kPanelK) {
       const int K = min(kPanelK, n - l0);
@@ -687,11 +693,11 @@ hm_wtv_kernel(const int4* __restrict__ far, const int64_t* __restrict__ uw_off,
       P::mac(sA, sB, K, rows, acc);
     }
 #pragma unroll
-    for (int k = 0; k < NCH; ++k) {
+    for (int k = 0; k < P::NI; ++k) {
       const int pr = P::row(k);
       if (pr >= rows) continue;
 #pragma unroll
-      for (int e = 0; e < 4; ++e)
+      for (int e = 0; e < NCH; ++e)
         reinterpret_cast<float4*>(Tb + (int64_t)(p0 + pr) * P::CW)[P::col(e, 0) / 2] =
             make_float4(acc[k][2 * e].x, acc[k][2 * e].y, acc[k][2 * e + 1].x, acc[k][2 * e + 1].y);
     }
@@ -763,6 +769,14 @@ bem_status build_structure(bem_ctx* ctx, cudaStream_t s) {
   build_cluster(h, cen, xyz, tri, 0, (int32_t)n);
   std::vector<int2> far_cl, near_cl;
   build_blocks(h, 0, 0, far_cl, near_cl);
+  // far blocks largest first (rows + columns; ties keep the partition's order)
+  auto fsize = [&](const int2& fb) {
+    return (h.cl[fb.x].e - h.cl[fb.x].b) + (h.cl[fb.y].e - h.cl[fb.y].b);
+  };
+  std::stable_sort(far_cl.begin(), far_cl.end(),
+                   [&](const int2& a, const int2& b) { return fsize(a) > fsize(b); });
+  h.nbig = 0;
+  while (h.nbig < (int)far_cl.size() && fsize(far_cl[h.nbig]) >= kAcaBig) ++h.nbig;
   // far blocks and their storage
   h.far.clear();
   h.uw_off.clear();
@@ -930,15 +944,24 @@ bem_status project_hmatrix(bem_ctx* ctx, const double* V, int64_t ldv, int nu, d
   for (int j = 0; j < N; ++j) {
     const float kr = (float)ctx->con.z_host[2 * j], ki = (float)ctx->con.z_host[2 * j + 1];
     if (nfar) {
+      // the far blocks are ordered by size, largest first: those of at least kAcaBig rows +
+      // columns take the wider kernel
       const HmGeom hg{h.d_gq, h.d_gn, h.d_gc, n};
-      if (single)
-        hm_aca_kernel<false><<<(unsigned)nfar, kAcaThreads, 0, s>>>(
-            hg, h.d_far, h.d_uw_off, h.d_used_off, kr, ki, ctx->op, (float)h.eps, h.rmax, h.d_uw,
-            h.d_used, h.d_rank);
-      else
-        hm_aca_kernel<true><<<(unsigned)nfar, kAcaThreads, 0, s>>>(
-            hg, h.d_far, h.d_uw_off, h.d_used_off, kr, ki, ctx->op, (float)h.eps, h.rmax, h.d_uw,
-            h.d_used, h.d_rank);
+      const int nbig = h.nbig, nsmall = (int)nfar - h.nbig;
+#define HM_ACA(GEN, NT, BASE, COUNT)                                                          \
+  hm_aca_kernel<GEN, NT><<<(unsigned)(COUNT), NT, 0, s>>>(BASE, hg, h.d_far, h.d_uw_off,      \
+                                                        h.d_used_off, kr, ki, ctx->op,        \
+                                                        (float)h.eps, h.rmax, h.d_uw, h.d_used, \
+                                                        h.d_rank)
+      if (single) {
+        if (nbig) HM_ACA(false, kAcaThreadsBig, 0, nbig);
+        if (nsmall) HM_ACA(false, kAcaThreads, nbig, nsmall);
+      } else {
+        if (nbig) HM_ACA(true, kAcaThreadsBig, 0, nbig);
+        if (nsmall) HM_ACA(true, kAcaThreads, nbig, nsmall);
+      }
+#undef HM_ACA
+      ctx->launches += (nbig > 0) + (nsmall > 0) - 1;
       ctx->launches++;
       st = cuda_check(ctx, cudaMemcpyAsync(ranks.data(), h.d_rank, nfar * sizeof(int32_t),
                                            cudaMemcpyDeviceToHost, s), "rank copy");
