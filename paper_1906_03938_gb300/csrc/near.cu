@@ -370,14 +370,16 @@ __global__ void near_rows_kernel(const int32_t* __restrict__ ptr, int64_t n, int
 
 constexpr int kNearNodes = 8;   // contour nodes per thread of the value kernel
 
-// C[j][e] = (A_near - A_7)(z_j) of pair e (single layer, FP32): one thread per pair and
+// C[j][e] = (A_near - A_7)(z_j) of pair e (FP32; with the general operator, T's point
+// terms with the factor c_G + c_H s (i k r - 1), s = (d . n) / r^2): one thread per pair and
 // group of up to 8 nodes. The pair's frame (FP64, rounded to FP32 relative to x_i) and the
 // 71 points' distances are formed once and shared by the group's nodes, whose kernel
 // values take one ex2 and one sine / cosine each (MUFU approximations, as the fused
 // kernel's; the FP64 path and the residuals keep the exact functions).
+template <bool general>
 __global__ void __launch_bounds__(256, 3)
 near_values32_kernel(Geometry g, const int32_t* __restrict__ rows, const int32_t* __restrict__ cols,
-                     int64_t nnz, const double* __restrict__ z, int N, GL8 gl,
+                     int64_t nnz, const double* __restrict__ z, int N, GL8 gl, OpCoef op,
                      float2* __restrict__ Cv) {
   __shared__ float s_x[8], s_w[64];
   if (threadIdx.x == 0) {
@@ -404,25 +406,39 @@ near_values32_kernel(Geometry g, const int32_t* __restrict__ rows, const int32_t
   const float abx = (float)F.ab[0], aby = (float)F.ab[1], abz = (float)F.ab[2];
   const float bcx = (float)F.bc[0], bcy = (float)F.bc[1], bcz = (float)F.bc[2];
   const float scale = (float)F.scale;
-  float kr[kNearNodes], km[kNearNodes];   // Re k, -Im k log2(e)
+  float nx = 0.f, ny = 0.f, nz = 0.f;
+  if constexpr (general) {
+    nx = (float)g.nrm[l];
+    ny = (float)g.nrm[n + l];
+    nz = (float)g.nrm[2 * n + l];
+  }
+  float kr[kNearNodes], ki[kNearNodes];
   float2 acc[kNearNodes];
 #pragma unroll
   for (int u = 0; u < kNearNodes; ++u) {
     const int j = j0 + (u < cnt ? u : 0);
     kr[u] = (float)z[2 * j];
-    km[u] = -(float)z[2 * j + 1] * 1.4426950408889634f;
+    ki[u] = (float)z[2 * j + 1];
     acc[u] = make_float2(0.f, 0.f);
   }
-  // amp = W / r at distance r, added for every node of the group
-  auto add = [&](float amp, float r) {
+  // amp = W / r at distance r (sr = (d . n) / r^2 for the general operator), added for every
+  // node of the group
+  auto add = [&](float amp, float r, float sr) {
 #pragma unroll
     for (int u = 0; u < kNearNodes; ++u) {
       float sn, cs, ex;
-      asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex) : "f"(km[u] * r));
+      asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex) : "f"(-ki[u] * 1.4426950408889634f * r));
       __sincosf(kr[u] * r, &sn, &cs);
       const float a = amp * ex;
-      acc[u].x = fmaf(a, cs, acc[u].x);
-      acc[u].y = fmaf(a, sn, acc[u].y);
+      if constexpr (general) {
+        float fr, fi;
+        op_factor(op, sr, kr[u] * r, ki[u] * r, fr, fi);
+        acc[u].x += a * (cs * fr - sn * fi);
+        acc[u].y += a * (cs * fi + sn * fr);
+      } else {
+        acc[u].x = fmaf(a, cs, acc[u].x);
+        acc[u].y = fmaf(a, sn, acc[u].y);
+      }
     }
   };
 #pragma unroll 1
@@ -435,7 +451,7 @@ near_values32_kernel(Geometry g, const int32_t* __restrict__ rows, const int32_t
                   dz = az + sp * abz + st * bcz;
       const float r2 = dx * dx + dy * dy + dz * dz;
       const float rs = rsqrtf(r2);
-      add(s_w[8 * p + q] * sp * scale * rs, r2 * rs);
+      add(s_w[8 * p + q] * sp * scale * rs, r2 * rs, (dx * nx + dy * ny + dz * nz) * rs * rs);
     }
   }
 #pragma unroll
@@ -444,7 +460,7 @@ near_values32_kernel(Geometry g, const int32_t* __restrict__ rows, const int32_t
                 dz = (float)(g.qp[(14 + q) * n + l] - x[2]);
     const float r2 = dx * dx + dy * dy + dz * dz;
     const float rs = rsqrtf(r2);
-    add(-(float)g.qw[q * n + l] * rs, r2 * rs);
+    add(-(float)g.qw[q * n + l] * rs, r2 * rs, (dx * nx + dy * ny + dz * nz) * rs * rs);
   }
 #pragma unroll
   for (int u = 0; u < kNearNodes; ++u)
@@ -453,7 +469,7 @@ near_values32_kernel(Geometry g, const int32_t* __restrict__ rows, const int32_t
 
 // Slice `slice` of the mixed path's partials := C(z_j) V in FP32 (every row < n_pad and
 // every column < nu written); one warp per (row i, node j), the pair values evaluated here
-// (the surrogate network and the general operator).
+// (the surrogate network).
 __global__ void __launch_bounds__(256)
 near_apply32_kernel(Geometry g, const int32_t* __restrict__ ptr, const int32_t* __restrict__ cols,
                     const double* __restrict__ z, int N, const float2* __restrict__ Vt, int nu,
@@ -773,9 +789,9 @@ bem_status near_apply32(bem_ctx* ctx, const float2* V32, int nu, int nup, int C,
   const int64_t nnz = ctx->near_nnz;
   // the inference copy of the network (BF16-rounded weights) follows the master weights
   const float* net = (ctx->near_mode == 2 && ctx->net_ready) ? ctx->d_net + kNetFloats : nullptr;
-  // single layer with the 64-point rule: the pair values of every node first (work buffer:
-  // the row-major basis, then N x nnz values, then the pairs' rows)
-  const bool values = !net && op_single(ctx->op) && nnz > 0;
+  // the 64-point rule: the pair values of every node first (work buffer: the row-major
+  // basis, then N x nnz values, then the pairs' rows)
+  const bool values = !net && nnz > 0;
   const size_t vt_bytes = (size_t)n * nu * sizeof(float2);
   const size_t cv_bytes = values ? (size_t)N * nnz * sizeof(float2) : 0;
   bem_status st = ensure_near_work(ctx, vt_bytes + cv_bytes + (values ? (size_t)nnz * sizeof(int32_t) : 0));
@@ -789,8 +805,12 @@ bem_status near_apply32(bem_ctx* ctx, const float2* V32, int nu, int nup, int C,
     int32_t* rows = reinterpret_cast<int32_t*>(static_cast<char*>(ctx->d_near_work) + vt_bytes + cv_bytes);
     near_rows_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctx->d_near_ptr, n, rows);
     const int64_t threads = nnz * ((N + kNearNodes - 1) / kNearNodes);
-    near_values32_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-        ctx->geo, rows, ctx->d_near_cols, nnz, ctx->con.z, N, gl8(), Cv);
+    if (op_single(ctx->op))
+      near_values32_kernel<false><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+          ctx->geo, rows, ctx->d_near_cols, nnz, ctx->con.z, N, gl8(), ctx->op, Cv);
+    else
+      near_values32_kernel<true><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+          ctx->geo, rows, ctx->d_near_cols, nnz, ctx->con.z, N, gl8(), ctx->op, Cv);
     ctx->launches += 2;
   }
   const unsigned blocks = (unsigned)((32 * (int64_t)n_pad * N + 255) / 256);
