@@ -90,6 +90,28 @@ def test_hmatrix_wide_bases(bem, nu):
     ctx.close()
 
 
+@pytest.mark.parametrize("level", [0, 1], ids=["root-leaf", "no-far-blocks"])
+def test_hmatrix_without_far_blocks(bem, level):
+    """A mesh of one leaf (20 panels) and one whose admissible blocks are all too small to be
+    far (80 panels): every entry dense, the leaf kernel alone (no cross approximation)."""
+    mesh = synth.icosphere(level)
+    spec = synth.ContourSpec("circle", 4.0 + 0j, 1.0, 1.0)
+    N, nu = 5, 3
+    ctx, z, w = _ctx(bem, mesh, spec, N)
+    ctx.set_hmatrix(leaf=32, eta=1.0, eps=1e-6, rmax=64)
+    V = _dev(synth.complex_gaussian(mesh.n, nu, 9))
+    B64, Y64 = ctx.project(V, bem.PREC_FP64, AV=True)
+    Bh, Yh = ctx.project(V, bem.PREC_HMATRIX, AV=True)
+    ctx.check()
+    st, work = ctx.hmatrix_stats(), ctx.hmatrix_work()
+    assert st["far_blocks"] == 0 and st["far_fraction"] == 0.0
+    assert work["dense_entries"] == float(mesh.n) ** 2 and work["far_row_terms"] == 0.0
+    eb = max(_relerr(Bh[j].cpu().numpy(), B64[j].cpu().numpy()) for j in range(N))
+    ey = max(_relerr(Yh[j].cpu().numpy(), Y64[j].cpu().numpy()) for j in range(N))
+    assert eb < 1e-4 and ey < 1e-4
+    ctx.close()
+
+
 def test_structure_and_products_match_oracle(bem):
     mesh = synth.icosphere(3)
     spec = synth.ContourSpec("circle", 4.0 + 0j, 1.0, 1.0)
