@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -467,43 +468,128 @@ constexpr int kLeafMax = 32;   // rows of a leaf (the leaf size is capped to it)
 constexpr int kPanelK = 32;    // depth of a staged panel
 constexpr int kHmThreads = 256;
 
-// Panel products on 256 threads: A (up to 32 rows x K, in shared memory as a[row][k], row
-// stride kPanelK + 1) times B (K rows x CW = 64 NCH complex columns, row-major in shared
-// memory) accumulated into acc. A warp owns one row per item: thread t owns rows
-// t / 32 + 8 k (k < 4) and the column pairs cg + 32 e (e < NCH), cg = t % 32: columns
-// 2 (cg + 32 e) and one more, so that the lanes of a warp read consecutive 16-byte pairs of
-// B and one element of A.
+// Panel products on 256 threads: A (up to 32 rows x K) times B (K rows x CW = 64 NCH complex
+// columns, row-major in shared memory) accumulated into acc. Two thread mappings with one
+// interface (accumulator NR x NC per thread, its rows row(i) and columns col(e), the A slot
+// aidx(row, k)); PanelFor picks the faster one per width (measured).
+//
+// PanelTile (CW = 256): warp w covers the 32 column
+// pairs 32 (w % NCH) + lane (columns 2 p and 2 p + 1) for the rows rg + RG i (i < RPT) of
+// its row group rg = w / NCH, RG = 8 / NCH, RPT = 32 / RG. A is kept in shared memory as
+// a[k][slot], slot = (row % RG) RPT + row / RG, so that a thread's rows are contiguous: one
+// broadcast 16-byte read gives two of them, and a warp reads B once for all its rows.
 template <int NCH>
-struct Panel {
+struct PanelTile {
   static constexpr int CW = 64 * NCH;
-  static constexpr int GP = 32;
-  static constexpr int RP = kHmThreads / GP;
-  static constexpr int NI = kLeafMax / RP;   // rows (items) per thread
-  static constexpr int NE = 2 * NCH;         // columns per thread and row
-  static __device__ __forceinline__ int row(int k) { return (int)threadIdx.x / GP + RP * k; }
-  static __device__ __forceinline__ int col(int e, int h) {
-    return 2 * ((int)threadIdx.x % GP + GP * e) + h;
+  static constexpr int RG = 8 / NCH;         // row groups
+  static constexpr int RPT = kLeafMax / RG;  // rows per thread (even)
+  static constexpr int kAS = kLeafMax + 2;   // A row stride (float2; even, 16-byte rows)
+  static_assert(RPT % 2 == 0, "row pairs");
+  static __device__ __forceinline__ int aidx(int row, int kk) {
+    return kk * kAS + (row % RG) * RPT + row / RG;
   }
-  static __device__ __forceinline__ void zero(float2 (&acc)[NI][NE]) {
-#pragma unroll
-    for (int k = 0; k < NI; ++k)
-#pragma unroll
-      for (int e = 0; e < NE; ++e) acc[k][e] = make_float2(0.f, 0.f);
+  static __device__ __forceinline__ int rg() { return ((int)threadIdx.x / 32) / NCH; }
+  static __device__ __forceinline__ int pair() {
+    return 32 * (((int)threadIdx.x / 32) % NCH) + (int)threadIdx.x % 32;
   }
-  // the products for the first NA of the thread's rows (all of them below the row count)
+  static constexpr int NR = RPT, NC = 2;   // accumulator: rows x columns per thread
+  static constexpr int ASZ = kPanelK * kAS;  // A tile, float2
+  static __device__ __forceinline__ int row(int i) { return rg() + RG * i; }
+  static __device__ __forceinline__ int col(int e) { return 2 * pair() + e; }
+  // the products for the thread's first 2 NP rows (those beyond the row count are computed
+  // on whatever A holds there and never written out)
+  template <int NP>
+  static __device__ __forceinline__ void mac_rows(const float2* a, const float2* b, int K,
+                                                  float2 (&acc)[RPT][2]) {
+    const float2* ab = a + rg() * RPT;
+    const float2* bb = b + 2 * pair();
+#pragma unroll 2
+    for (int kk = 0; kk < K; ++kk) {
+      const float4 v = *reinterpret_cast<const float4*>(bb + kk * CW);
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        const float4 x = *reinterpret_cast<const float4*>(ab + kk * kAS + 2 * j);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float xr = h ? x.z : x.x, xi = h ? x.w : x.y;
+          float2& p = acc[2 * j + h][0];
+          float2& q = acc[2 * j + h][1];
+          p.x = fmaf(xr, v.x, fmaf(-xi, v.y, p.x));
+          p.y = fmaf(xr, v.y, fmaf(xi, v.x, p.y));
+          q.x = fmaf(xr, v.z, fmaf(-xi, v.w, q.x));
+          q.y = fmaf(xr, v.w, fmaf(xi, v.z, q.y));
+        }
+      }
+    }
+  }
+  static __device__ __forceinline__ void mac(const float2* a, const float2* b, int K, int rows,
+                                             float2 (&acc)[RPT][2]) {
+    const int g = rg();   // the thread's rows g + RG i, active while below the row count
+    const int na = g >= rows ? 0 : min(RPT, (rows - g + RG - 1) / RG);
+    const int np = (na + 1) / 2;
+    if (np == RPT / 2) mac_rows<RPT / 2>(a, b, K, acc);
+    else if (np == 1) mac_rows<1>(a, b, K, acc);
+    else if constexpr (RPT >= 6) {
+      if (np == 2) mac_rows<2>(a, b, K, acc);
+      else if constexpr (RPT >= 8) {
+        if (np == 3) mac_rows<3>(a, b, K, acc);
+        else if constexpr (RPT >= 16) {
+          if (np == 4) mac_rows<4>(a, b, K, acc);
+          else if (np == 5) mac_rows<5>(a, b, K, acc);
+          else if (np == 6) mac_rows<6>(a, b, K, acc);
+          else if (np == 7) mac_rows<7>(a, b, K, acc);
+        }
+      }
+    }
+  }
+  template <int R, int C2>
+  static __device__ __forceinline__ void zero(float2 (&acc)[R][C2]) {
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int e = 0; e < C2; ++e) acc[i][e] = make_float2(0.f, 0.f);
+  }
+  // B rows [0, K) from rows src + kk * CW (16-byte aligned, CW complex each)
+  static __device__ __forceinline__ void stage_b(float2* b, const float2* __restrict__ src, int K) {
+    const float4* s = reinterpret_cast<const float4*>(src);
+    float4* d = reinterpret_cast<float4*>(b);
+    for (int t = threadIdx.x; t < K * (CW / 2); t += kHmThreads) d[t] = s[t];
+  }
+  static constexpr size_t smem_bytes() {
+    return (size_t)kPanelK * CW * sizeof(float2) + kPanelK * (kLeafMax + 2) * sizeof(float2) +
+           kPanelK * 8 * sizeof(float4) + kLeafMax * sizeof(float4) + kPanelK * sizeof(int2) +
+           (kFarGroup + 1) * sizeof(int);
+  }
+  static constexpr int kFarGroup = 128;
+};
+
+// PanelRows (CW = 64, 128): a warp owns one row per item: thread t owns rows t / 32 + 8 k
+// (k < 4) and the column pairs lane + 32 e (e < NCH); A kept as a[row][k] (row stride
+// kPanelK + 1). Reads B once per row, but its warps stay busy on short leaves.
+template <int NCH>
+struct PanelRows : PanelTile<NCH> {
+  using Base = PanelTile<NCH>;
+  static constexpr int CW = Base::CW;
+  static constexpr int NR = 4, NC = 2 * NCH;
+  static constexpr int ASZ = kLeafMax * (kPanelK + 1);
+  static __device__ __forceinline__ int aidx(int row, int kk) { return row * (kPanelK + 1) + kk; }
+  static __device__ __forceinline__ int row(int k) { return (int)threadIdx.x / 32 + 8 * k; }
+  static __device__ __forceinline__ int col(int e) {
+    return 2 * ((int)threadIdx.x % 32 + 32 * (e / 2)) + e % 2;
+  }
   template <int NA>
-  static __device__ __forceinline__ void mac_rows(const float2 (*a)[kPanelK + 1], const float2* b,
-                                                  int K, float2 (&acc)[NI][NE]) {
-    const int cg = (int)threadIdx.x % GP, r0 = (int)threadIdx.x / GP;
+  static __device__ __forceinline__ void mac_rows(const float2* a, const float2* b, int K,
+                                                  float2 (&acc)[NR][NC]) {
+    const int cg = (int)threadIdx.x % 32, r0 = (int)threadIdx.x / 32;
 #pragma unroll 2
     for (int kk = 0; kk < K; ++kk) {
       float4 v[NCH];
 #pragma unroll
       for (int e = 0; e < NCH; ++e)
-        v[e] = *reinterpret_cast<const float4*>(b + (int64_t)kk * CW + 2 * (cg + GP * e));
+        v[e] = *reinterpret_cast<const float4*>(b + (int64_t)kk * CW + 2 * (cg + 32 * e));
 #pragma unroll
       for (int k = 0; k < NA; ++k) {
-        const float2 x = a[r0 + RP * k][kk];
+        const float2 x = a[(r0 + 8 * k) * (kPanelK + 1) + kk];
 #pragma unroll
         for (int e = 0; e < NCH; ++e) {
           float2& p = acc[k][2 * e];
@@ -516,29 +602,19 @@ struct Panel {
       }
     }
   }
-  static __device__ __forceinline__ void mac(const float2 (*a)[kPanelK + 1], const float2* b, int K,
-                                             int rows, float2 (&acc)[NI][NE]) {
-    const int r0 = (int)threadIdx.x / GP;   // the thread's rows r0 + RP k increase with k
-    const int na = r0 >= rows ? 0 : min(NI, (rows - r0 + RP - 1) / RP);
-    static_assert(NI == 4, "four rows per thread");
+  static __device__ __forceinline__ void mac(const float2* a, const float2* b, int K, int rows,
+                                             float2 (&acc)[NR][NC]) {
+    const int r0 = (int)threadIdx.x / 32;   // the thread's rows r0 + 8 k increase with k
+    const int na = r0 >= rows ? 0 : min(NR, (rows - r0 + 7) / 8);
     if (na == 4) mac_rows<4>(a, b, K, acc);
     else if (na == 3) mac_rows<3>(a, b, K, acc);
     else if (na == 2) mac_rows<2>(a, b, K, acc);
     else if (na == 1) mac_rows<1>(a, b, K, acc);
   }
-  // B rows [0, K) from rows src + kk * CW (16-byte aligned, CW complex each)
-  static __device__ __forceinline__ void stage_b(float2* b, const float2* __restrict__ src, int K) {
-    const float4* s = reinterpret_cast<const float4*>(src);
-    float4* d = reinterpret_cast<float4*>(b);
-    for (int t = threadIdx.x; t < K * (CW / 2); t += kHmThreads) d[t] = s[t];
-  }
-  static constexpr size_t smem_bytes() {
-    return (size_t)kPanelK * CW * sizeof(float2) + kLeafMax * (kPanelK + 1) * sizeof(float2) +
-           kPanelK * 8 * sizeof(float4) + kLeafMax * sizeof(float4) + kPanelK * sizeof(int2) +
-           (kFarGroup + 1) * sizeof(int);
-  }
-  static constexpr int kFarGroup = 128;
 };
+
+template <int NCH>
+using PanelFor = typename std::conditional<NCH >= 4, PanelTile<NCH>, PanelRows<NCH>>::type;
 
 // Y_j for the rows of one leaf and every basis column (one CTA per leaf):
 //   dense part: the leaf's dense column ranges (contiguous in cluster order), 32 panels at a
@@ -557,11 +633,11 @@ hm_leaf_kernel(HmGeom g, const int4* __restrict__ leaves, const int2* __restrict
                const float2* __restrict__ uw, const float2* __restrict__ T,
                const float2* __restrict__ vp, int nu, const float2* __restrict__ self32,
                float kr, float ki, OpCoef op, float* __restrict__ Yp, int C, int64_t n_pad) {
-  using P = Panel<NCH>;
+  using P = PanelFor<NCH>;
   extern __shared__ float4 hm_smem[];
   float2* sB = reinterpret_cast<float2*>(hm_smem);
-  float2(*sA)[kPanelK + 1] = reinterpret_cast<float2(*)[kPanelK + 1]>(sB + kPanelK * P::CW);
-  float4* sQ = reinterpret_cast<float4*>(&sA[kLeafMax][0]);   // [kk][8]: 7 points, normal
+  float2* sA = sB + kPanelK * P::CW;                          // A tile, slots P::aidx
+  float4* sQ = reinterpret_cast<float4*>(sA + kPanelK * (kLeafMax + 2));   // [kk][8]: 7 points, normal
   float4* sX = sQ + kPanelK * 8;
   int2* sMap = reinterpret_cast<int2*>(sX + kLeafMax);
   int* sPre = reinterpret_cast<int*>(sMap + kPanelK);
@@ -571,7 +647,7 @@ hm_leaf_kernel(HmGeom g, const int4* __restrict__ leaves, const int2* __restrict
   const int mL = lf.y - lf.x;
   const int64_t n = g.n;
   if (tid < kLeafMax) sX[tid] = tid < mL ? g.cen[lf.x + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
-  float2 acc[P::NI][P::NE];
+  float2 acc[P::NR][P::NC];
   P::zero(acc);
   for (int nb = lf.z; nb < lf.w; ++nb) {
     const int2 sg = near[nb];
@@ -589,7 +665,7 @@ hm_leaf_kernel(HmGeom g, const int4* __restrict__ leaves, const int2* __restrict
       for (int t = tid; t < mL * K; t += kHmThreads) {
         const int rr = t % mL, kk = t / mL;
         const float4 x = sX[rr];
-        sA[rr][kk] = (lf.x + rr == k0 + kk)
+        sA[P::aidx(rr, kk)] = (lf.x + rr == k0 + kk)
                          ? self32[__float_as_int(x.w)]
                          : hm_eval<general>(x.x, x.y, x.z, sQ + kk * 8, 1, sQ[kk * 8 + 7], kr, ki, op);
       }
@@ -633,7 +709,7 @@ hm_leaf_kernel(HmGeom g, const int4* __restrict__ leaves, const int2* __restrict
         const int rr = t % mL, kk = t / mL;
         const int2 bp = sMap[kk];
         const int4 f = far[bp.x];
-        sA[rr][kk] = uw[uw_off[bp.x] + (lf.x - f.x + rr) + (int64_t)bp.y * (f.y - f.x)];
+        sA[P::aidx(rr, kk)] = uw[uw_off[bp.x] + (lf.x - f.x + rr) + (int64_t)bp.y * (f.y - f.x)];
       }
       __syncthreads();
       P::mac(sA, sB, K, mL, acc);
@@ -641,21 +717,19 @@ hm_leaf_kernel(HmGeom g, const int4* __restrict__ leaves, const int2* __restrict
     }
   }
 #pragma unroll
-  for (int k = 0; k < P::NI; ++k) {
+  for (int k = 0; k < P::NR; ++k) {
     const int r = P::row(k);
     if (r >= mL) continue;
     const int64_t i = __float_as_int(sX[r].w);
 #pragma unroll
-    for (int e = 0; e < NCH; ++e)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int c = P::col(e, h);
-        if (c < nu) {   // real part at column (c / C) 2 C + c % C, imaginary part C further
-          const int64_t colr = (int64_t)(c / C) * 2 * C + c % C;
-          Yp[colr * n_pad + i] = acc[k][2 * e + h].x;
-          Yp[(colr + C) * n_pad + i] = acc[k][2 * e + h].y;
-        }
+    for (int e = 0; e < P::NC; ++e) {
+      const int c = P::col(e);
+      if (c < nu) {   // real part at column (c / C) 2 C + c % C, imaginary part C further
+        const int64_t colr = (int64_t)(c / C) * 2 * C + c % C;
+        Yp[colr * n_pad + i] = acc[k][e].x;
+        Yp[(colr + C) * n_pad + i] = acc[k][e].y;
       }
+    }
   }
 }
 
@@ -667,10 +741,10 @@ hm_wtv_kernel(const int4* __restrict__ far, const int64_t* __restrict__ uw_off,
               const int32_t* __restrict__ rank, const int64_t* __restrict__ toff, int rmax,
               const float2* __restrict__ uw, const float2* __restrict__ vp,
               float2* __restrict__ T) {
-  using P = Panel<NCH>;
+  using P = PanelFor<NCH>;
   extern __shared__ float4 hm_smem[];
   float2* sB = reinterpret_cast<float2*>(hm_smem);
-  float2(*sA)[kPanelK + 1] = reinterpret_cast<float2(*)[kPanelK + 1]>(sB + kPanelK * P::CW);
+  float2* sA = sB + kPanelK * P::CW;   // A tile, slots P::aidx
   const int b = blockIdx.x, tid = threadIdx.x;
   const int4 f = far[b];
   const int m = f.y - f.x, n = f.w - f.z;
@@ -679,27 +753,27 @@ hm_wtv_kernel(const int4* __restrict__ far, const int64_t* __restrict__ uw_off,
   float2* Tb = T + toff[b];
   for (int p0 = 0; p0 < r; p0 += kLeafMax) {
     const int rows = min(kLeafMax, r - p0);
-    float2 acc[P::NI][P::NE];
+    float2 acc[P::NR][P::NC];
     P::zero(acc);
     for (int l0 = 0; l0 < n; l0 += kPanelK) {
       const int K = min(kPanelK, n - l0);
       __syncthreads();
       for (int t = tid; t < rows * kPanelK; t += kHmThreads) {
         const int kk = t % kPanelK, pp = t / kPanelK;
-        if (kk < K) sA[pp][kk] = W[(l0 + kk) + (int64_t)(p0 + pp) * n];
+        if (kk < K) sA[P::aidx(pp, kk)] = W[(l0 + kk) + (int64_t)(p0 + pp) * n];
       }
       P::stage_b(sB, vp + (int64_t)(f.z + l0) * P::CW, K);
       __syncthreads();
       P::mac(sA, sB, K, rows, acc);
     }
 #pragma unroll
-    for (int k = 0; k < P::NI; ++k) {
+    for (int k = 0; k < P::NR; ++k) {
       const int pr = P::row(k);
       if (pr >= rows) continue;
 #pragma unroll
-      for (int e = 0; e < NCH; ++e)
-        reinterpret_cast<float4*>(Tb + (int64_t)(p0 + pr) * P::CW)[P::col(e, 0) / 2] =
-            make_float4(acc[k][2 * e].x, acc[k][2 * e].y, acc[k][2 * e + 1].x, acc[k][2 * e + 1].y);
+      for (int e = 0; e < P::NC; e += 2)   // columns col(e), col(e) + 1
+        reinterpret_cast<float4*>(Tb + (int64_t)(p0 + pr) * P::CW)[P::col(e) / 2] =
+            make_float4(acc[k][e].x, acc[k][e].y, acc[k][e + 1].x, acc[k][e + 1].y);
     }
   }
 }
@@ -869,7 +943,7 @@ unsigned nblocks(int64_t count, int t = 256) { return (unsigned)((count + t - 1)
 template <int NCH, bool general>
 bem_status hm_apply_kernels(bem_ctx* ctx, HMatrix& h, bool wtv, int j, int nu, float kr, float ki,
                             const ExtFrame& fr, cudaStream_t s) {
-  const size_t smem = Panel<NCH>::smem_bytes();
+  const size_t smem = PanelFor<NCH>::smem_bytes();
   if (cudaFuncSetAttribute(hm_leaf_kernel<NCH, general>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
       cudaFuncSetAttribute(hm_wtv_kernel<NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return cuda_check(ctx, cudaGetLastError(), "low-rank far field kernel attributes");
