@@ -432,7 +432,10 @@ bem_status bem_solve_chebyshev(bem_ctx* ctx, const double* B_dev, int nu, double
  * Algorithm 1 operator of bem_inverse_power keeps the 7-point rule. It is kept across
  * bem_set_mesh (the pair list is rebuilt for the new mesh at first use). Building the list
  * synchronises `stream`. Contexts with a near-field mode are not accepted by the batched
- * projection.
+ * projection. Precision: the FP64 projection, residuals and refinement evaluate the rule in
+ * FP64 with the exact functions; the mixed projection evaluates it in FP32 with the
+ * hardware approximations of exp2, sine, cosine and reciprocal square root (pair geometry
+ * shared by eight contour nodes; N x nnz FP32 values held in the context's work memory).
  * bem_near_pairs: the pair list of the current mesh (builds it if needed): *nnz pairs;
  *   row_ptr_host (n + 1 int32, nullable) and cols_host (nnz int32, nullable, increasing
  *   within each row). BEM_ESTATE when the mode is 0. Synchronous.
