@@ -91,14 +91,16 @@ def blocks(clusters, eta=1.0, leaf=None):
     return out
 
 
-def aca(entry_rows, entry_cols, m, n, eps, rmax):
+def aca(entry_rows, entry_cols, m, n, eps, rmax, history=False):
     """ACA with partial pivoting. entry_rows(i) -> row i (n values), entry_cols(j) -> column j
-    (m values), local indices. Returns U (m x r), W (n x r)."""
+    (m values), local indices. Returns U (m x r), W (n x r); with history, also the updated
+    squared norms ||S_k||_F^2 after each step."""
     U = np.zeros((m, 0), complex)
     W = np.zeros((n, 0), complex)
     used = np.zeros(m, bool)
     i = 0
     norm2 = 0.0
+    hist = []
     while U.shape[1] < min(rmax, m, n):
         used[i] = True
         r = entry_rows(i) - U[i, :] @ W.T
@@ -114,6 +116,7 @@ def aca(entry_rows, entry_cols, m, n, eps, rmax):
         cross = 2.0 * np.real(np.sum((U.conj().T @ u) * (W.conj().T @ w)))
         nu, nw = np.linalg.norm(u), np.linalg.norm(w)
         norm2 += cross + (nu * nw) ** 2
+        hist.append(norm2)
         U = np.hstack([U, u[:, None]])
         W = np.hstack([W, w[:, None]])
         if nu * nw <= eps * np.sqrt(max(norm2, 0.0)):
@@ -123,7 +126,7 @@ def aca(entry_rows, entry_cols, m, n, eps, rmax):
         if cand.max() < 0.0:
             break
         i = int(np.argmax(cand))
-    return U, W
+    return (U, W, hist) if history else (U, W)
 
 
 def compress(mesh, k, clusters, blist, eps=1e-6, rmax=64, op=None):

@@ -5,6 +5,8 @@ fix independently of its code:
   admissibility condition it was chosen by;
 * adaptive cross approximation recovers an exactly rank-3 matrix to rounding in 3 steps
   (plus at most the one that finds the zero residual);
+* the squared Frobenius norm that the stopping test uses, updated step by step (cross
+  terms included), equals ||U_k W_k^T||_F^2 formed explicitly after every step;
 * the assembled H-matrix differs from the dense A(k) by less than the requested tolerance
   (relative Frobenius norm), for the single layer and the double layer, and the error falls
   with the tolerance.
@@ -38,6 +40,19 @@ def test_aca_recovers_a_rank3_matrix():
     U, W = hm.aca(lambda i: M[i].copy(), lambda j: M[:, j].copy(), m, n, 1e-12, 20)
     assert U.shape[1] <= 4
     assert np.max(np.abs(U @ W.T - M)) < 1e-12 * np.max(np.abs(M))
+
+
+def test_aca_norm_update_is_exact():
+    rng = np.random.default_rng(5)
+    m, n = 50, 37
+    M = sum(np.outer(rng.normal(size=m) + 1j * rng.normal(size=m),
+                     rng.normal(size=n) + 1j * rng.normal(size=n)) * 0.5 ** p for p in range(12))
+    U, W, hist = hm.aca(lambda i: M[i].copy(), lambda j: M[:, j].copy(), m, n, 1e-14, 30,
+                        history=True)
+    assert len(hist) == U.shape[1] >= 8
+    for k, h in enumerate(hist, start=1):
+        ref = np.linalg.norm(U[:, :k] @ W[:, :k].T, "fro") ** 2
+        assert abs(h - ref) <= 1e-12 * ref, (k, h, ref)
 
 
 @pytest.mark.parametrize("op", [None, (0.0, 1.0)], ids=["single", "double"])
