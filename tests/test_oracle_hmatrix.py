@@ -3,6 +3,8 @@ fix independently of its code:
 
 * the block partition covers every (i, l) exactly once, and every far block satisfies the
   admissibility condition it was chosen by;
+* two unit squares a distance D apart form one far block exactly when sqrt(2) <= D - 1
+  (the vertex boxes' diagonal against their gap, eta = 1);
 * adaptive cross approximation recovers an exactly rank-3 matrix to rounding in 3 steps
   (plus at most the one that finds the zero residual);
 * the squared Frobenius norm that the stopping test uses, updated step by step (cross
@@ -29,6 +31,37 @@ def test_partition_covers_every_entry_once():
             assert max(hm._diam(cl[t]), hm._diam(cl[s])) <= hm._dist(cl[t], cl[s])
     assert np.all(count == 1)
     assert any(f for _, _, f in bl) and any(not f for _, _, f in bl)
+
+
+class _Mesh:
+    def __init__(self, xyz, tri):
+        self.xyz, self.tri, self.n = np.asarray(xyz, float), np.asarray(tri), len(tri)
+
+
+def _two_squares(D):
+    """Two unit squares in the plane z = 0, the second shifted by D along x, each split into
+    two triangles."""
+    xyz, tri = [], []
+    for x0 in (0.0, D):
+        b = len(xyz)
+        xyz += [(x0, 0, 0), (x0 + 1, 0, 0), (x0 + 1, 1, 0), (x0, 1, 0)]
+        tri += [(b, b + 1, b + 2), (b, b + 2, b + 3)]
+    return _Mesh(xyz, tri)
+
+
+@pytest.mark.parametrize("D,far", [(1.0 + np.sqrt(2.0) + 1e-3, True),
+                                   (1.0 + np.sqrt(2.0) - 1e-3, False)])
+def test_admissibility_of_two_squares(D, far):
+    """Each square's box (of its vertices) has diagonal sqrt(2); the gap between the boxes is
+    D - 1, so the squares form one far block exactly when sqrt(2) <= D - 1 (eta = 1); the
+    boxes of the triangles' centroids would give a diagonal of sqrt(2) / 3."""
+    mesh = _two_squares(D)
+    cl = hm.cluster_tree(mesh, leaf=2)
+    assert sorted(map(sorted, (cl[c][0].tolist() for c in cl[0][1]))) == [[0, 1], [2, 3]]
+    bl = hm.blocks(cl, eta=1.0)
+    a, b = cl[0][1]
+    assert ((a, b, True) in bl) == far and ((b, a, True) in bl) == far
+    assert not any(f for t, s, f in bl if t == s)
 
 
 def test_aca_recovers_a_rank3_matrix():
