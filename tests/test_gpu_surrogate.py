@@ -108,7 +108,7 @@ def test_training_and_gain_on_held_out_mesh(bem):
     assert np.all(np.isfinite(losses)) and losses[-1] < losses[0] / 10, losses
     params = trainer.surrogate_params(which=0)
     trainer.close()
-    # held out: pairs of a finer sphere; the network against the 8 x 8 rule (the judge)
+    # held out: pairs of a finer sphere; the network against the 8 x 8 rule (the reference)
     mesh = synth.icosphere(5)
     ctx = _ctx(bem, mesh)
     ctx.surrogate_set(params)
