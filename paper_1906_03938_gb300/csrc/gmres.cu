@@ -6,7 +6,7 @@
 // Arnoldi vectors are FP32; each new vector is orthogonalised against its column's
 // previous ones by classical Gram-Schmidt run twice (dot products accumulated in FP64),
 // the small Hessenberg least-squares problems are solved on the host by Givens rotations
-// (FP64), and convergence is judged on the true residual ||B - S X|| / ||B|| per column
+// (FP64), and convergence is tested on the true residual ||B - S X|| / ||B|| per column
 // at every restart.
 #include <math.h>
 

@@ -649,7 +649,7 @@ __device__ __forceinline__ double u01(uint64_t seed, uint64_t idx) {
 // Training samples of the surrogate network: sample t takes the near pair
 // e = floor(u * nnz) of the current mesh and k uniform in the box, u from SplitMix64 of
 // (seed, 3t, 3t+1, 3t+2); features as near_features32, target (A_near - A_7)(k) / h from
-// the FP64 8 x 8 rule (the plain quadrature judges the network). Optionally the pair
+// the FP64 8 x 8 rule (the plain quadrature is the network's reference). Optionally the pair
 // (row, column) and k of each sample.
 __global__ void surrogate_samples_kernel(Geometry g, const int32_t* __restrict__ ptr,
                                          const int32_t* __restrict__ cols, int64_t nnz,
