@@ -1,7 +1,10 @@
 """Pins of the oracle's Rayleigh-Ritz layer: orthonormalisation, projection, the reduced
 linearisation (Eq. EVP_red) and the inverse power / subspace iteration (Algorithms 1, 3),
 against problems whose eigenvalues are known by construction or by a textbook
-companion linearisation that uses none of the Cauchy machinery."""
+companion linearisation that uses none of the Cauchy machinery. Algorithm 1 in its
+Schur-complement form is also pinned against plain inverse iteration on the explicit
+(N + 1) n linearisation (a sign error in its v-update or the extra u^(j) term of the
+printed listing fail it)."""
 import numpy as np
 import scipy.linalg as sla
 import pytest
@@ -104,6 +107,40 @@ def _linear_nlevp(n, lam_in, lam_out, seed):
     D = np.concatenate([lam_in, lam_out])
     K = X @ np.diag(D) @ np.linalg.inv(X)
     return lambda t: K - t * np.eye(n)
+
+
+def test_inverse_power_is_inverse_iteration_on_the_linearisation():
+    """Algorithm 1 in Schur-complement form (reading of its right-hand side: no u^(j) term)
+    against plain inverse iteration w <- (A - s M)^{-1} M w on the explicit Cauchy
+    linearisation of sum_j B_j / (z_j - z): unknowns (v_1 .. v_N, x), rows
+    z_j v_j - x = lambda v_j and sum_j B_j v_j = 0, M = diag(I, .., I, 0). After q steps the
+    x-part is parallel to the oracle's u (both iterations scale by scalars only)."""
+    rng = np.random.default_rng(21)
+    n, N, nu, q, s = 9, 6, 3, 4, 0.3 + 0.2j
+    z = 2.0 * np.exp(2j * np.pi * (np.arange(N) + 0.5) / N)
+    B = rng.normal(size=(N, n, n)) + 1j * rng.normal(size=(N, n, n))
+    V0 = synth.complex_gaussian(n, nu, 22)
+    u = rr.inverse_power(B, z, s, V0, q)
+    dim = (N + 1) * n
+    A = np.zeros((dim, dim), complex)
+    M = np.zeros((dim, dim), complex)
+    for j in range(N):
+        blk = slice(j * n, (j + 1) * n)
+        A[blk, blk] = z[j] * np.eye(n)
+        A[blk, N * n:] = -np.eye(n)
+        A[N * n:, blk] = B[j]
+        M[blk, blk] = np.eye(n)
+    K = np.linalg.solve(A - s * M, M)
+    for c in range(nu):
+        w = np.zeros(dim, complex)
+        for j in range(N):
+            w[j * n:(j + 1) * n] = V0[:, c] / (z[j] - s)
+        for _ in range(q):
+            w = K @ w
+            w = w / np.linalg.norm(w)
+        x = w[N * n:]
+        cos = abs(np.vdot(x, u[:, c])) / (np.linalg.norm(x) * np.linalg.norm(u[:, c]))
+        assert abs(cos - 1.0) < 1e-12, (c, cos)
 
 
 def test_subspace_iteration_finds_known_eigenvalues():
