@@ -226,6 +226,66 @@ def measured_traffic(workload, precision):
     return rec["dram_bytes_read"] + rec["dram_bytes_write"]
 
 
+def read_golden(name):
+    """(eigenvalue, multiplicity) of the stored oracle eigenvalues of a workload that lie
+    inside its contour, or None when the workload has no stored list."""
+    path = os.path.join(ROOT, "tests", "golden", f"eigs_{name}.txt")
+    if not os.path.exists(path):
+        return None
+    gold = []
+    for line in open(path):
+        if not line.startswith("#"):
+            re_, im_, mult, ins = line.split()
+            if int(ins):
+                gold.append((complex(float(re_), float(im_)), int(mult)))
+    return gold
+
+
+def inside_contour(lam, spec, margin=0.0):
+    """True where lam lies inside the ellipse (circle) of ``spec`` shrunk by ``margin``."""
+    lam = np.asarray(lam)
+    x = (lam.real - spec.centre.real) / spec.a
+    y = (lam.imag - spec.centre.imag) / spec.b
+    return np.sqrt(x * x + y * y) < 1.0 - margin
+
+
+def eig_compare(lam, X, rel, gold, spec, tol, conv=1e-10, margin=0.02):
+    """Compares a solve's eigenpairs (lam, columns of X, relative residuals rel) with the
+    expected list ``gold`` of (eigenvalue, multiplicity) inside the contour:
+      * every expected eigenvalue has a found value within tol (relative) whose residual is
+        below conv, and at least its multiplicity of independent vectors there (missing);
+      * every converged value (rel < conv) strictly inside the contour (shrunk by the
+        relative margin; the annulus next to the contour may hold values either way) is
+        within tol of an expected one (extras).
+    Returns a dict with the per-eigenvalue errors and residuals, the missing and extra
+    values and ``ok``."""
+    lam = np.asarray(lam, dtype=np.complex128)
+    rel = np.asarray(rel, dtype=np.float64)
+    Xh = np.asarray(X)
+    per, missing = [], []
+    for g, m in gold:
+        near = np.where((np.abs(lam - g) <= tol * abs(g)) & (rel < conv))[0]
+        err = float(np.min(np.abs(lam - g)) / abs(g)) if len(lam) else float("inf")
+        rank = 0
+        if len(near):
+            cols = Xh[:, near] / np.linalg.norm(Xh[:, near], axis=0)
+            rank = int(np.sum(np.linalg.svd(cols, compute_uv=False) > 1e-6))
+        rr = float(np.max(rel[near])) if len(near) else None
+        per.append({"expected": [g.real, g.imag], "multiplicity": m, "rel_err": err,
+                    "relres_max": rr, "vectors": rank})
+        if len(near) == 0 or rank < m:
+            missing.append([g.real, g.imag, m, rank])
+    extras = []
+    for k in np.where((rel < conv) & inside_contour(lam, spec, margin))[0]:
+        if not any(abs(lam[k] - g) <= tol * abs(g) for g, _ in gold):
+            extras.append([lam[k].real, lam[k].imag, float(rel[k])])
+    errs = [p["rel_err"] for p in per]
+    return {"ok": not missing and not extras, "per_eigenvalue": per, "missing": missing,
+            "extras": extras, "eig_rel_err_max": max(errs) if errs else None,
+            "relres_max": float(np.max(rel)) if len(rel) else None,
+            "multiplicities_ok": not missing}
+
+
 def train_surrogate(bem, device, epochs=200):
     """Training data from the near pairs of two spheres and an ellipsoid (k over the
     contours' range), then training with the library's own kernels; returns the parameters
@@ -564,34 +624,18 @@ def run_ours(args):
     # projection (Algorithm 1 basis, reduced solve, FP64 refinement), untimed, against the
     # oracle's discrete eigenvalues stored under tests/golden
     eig = None
-    golden = os.path.join(ROOT, "tests", "golden", f"eigs_{args.workload}.txt")
-    if not args.no_eig_check and os.path.exists(golden) and not near_mode and \
-            args.operator == "single" and args.precision != "hmatrix":
+    gold = read_golden(args.workload + ("_near" if near_mode else ""))
+    if not args.no_eig_check and gold is not None and args.operator == "single" and \
+            args.precision != "hmatrix":
         t0 = time.perf_counter()
         lam, X, rel = ctx.solve(V_res, q=10, precision=prec, tol=1e-14)
         torch.cuda.synchronize()
         t_solve = time.perf_counter() - t0
-        gold = []
-        for line in open(golden):
-            if not line.startswith("#"):
-                re_, im_, mult, ins = line.split()
-                if int(ins):
-                    gold.append((complex(float(re_), float(im_)), int(mult)))
-        errs = [float(np.min(np.abs(lam - g)) / abs(g)) if len(lam) else float("inf") for g, _ in gold]
-        Xh = X.cpu().numpy()
-        mult_ok = True
-        for g, m in gold:
-            near = np.where(np.abs(lam - g) <= 1e-8 * abs(g))[0]
-            if len(near) == 0:
-                mult_ok = False
-                continue
-            sv = np.linalg.svd(Xh[:, near] / np.linalg.norm(Xh[:, near], axis=0), compute_uv=False)
-            mult_ok = mult_ok and int(np.sum(sv > 1e-6)) >= m
-        eig = {"eig_rel_err_max": max(errs) if errs else None, "relres_max": float(np.max(rel)) if len(rel) else None,
-               "found": [[l.real, l.imag] for l in lam], "expected": [[g.real, g.imag, m] for g, m in gold],
-               "multiplicities_ok": mult_ok, "solve_s": t_solve,
-               "pipeline": "Algorithm 1 (q=10) + CholeskyQR2 + projection (" + args.precision +
-                           ") + reduced solve + FP64 refinement"}
+        eig = eig_compare(lam, X.cpu().numpy(), rel, gold, c, tol=1e-8)
+        eig.update({"found": [[l.real, l.imag] for l in lam],
+                    "relres": [float(r) for r in rel], "solve_s": t_solve,
+                    "pipeline": "Algorithm 1 (q=10) + CholeskyQR2 + projection (" +
+                                args.precision + ") + reduced solve + FP64 refinement"})
 
     cpu = None
     if not args.no_cpu_baseline and world == 1 and args.operator == "single":

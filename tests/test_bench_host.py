@@ -7,6 +7,7 @@ import json
 import os
 import sys
 
+import numpy as np
 import pytest
 
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
@@ -45,3 +46,50 @@ def test_mufu_work_count():
     assert twins < base < wider
     # every node still takes its own ex2 at every quadrature point
     assert twins > 7 * 32 / rates["ex2"]
+
+
+def _fake_solve(values, mults, rng):
+    """Eigenpairs as a solve returns them: each value repeated with independent vectors."""
+    lam, cols = [], []
+    for v, m in zip(values, mults):
+        for _ in range(m):
+            lam.append(v)
+            cols.append(rng.normal(size=40) + 1j * rng.normal(size=40))
+    return np.array(lam), np.stack(cols, axis=1), np.full(len(lam), 1e-13)
+
+
+def test_eig_compare_flags_extras_missing_and_multiplicity():
+    """The eigenvalue check used by the golden-solve tests and the bench: a clean solve
+    passes; an extra converged value inside the contour, a missing golden value, a
+    multiplicity short of vectors each fail; unconverged or near-contour values are left
+    out of the extras."""
+    import synth
+    spec = synth.ContourSpec("ellipse", 6.5 + 0j, 1.5, 0.4)
+    gold = [(5.44 - 3e-7j, 1), (7.6932 - 1e-6j, 2)]
+    rng = np.random.default_rng(3)
+    lam, X, rel = _fake_solve([g for g, _ in gold], [m for _, m in gold], rng)
+    assert bench.eig_compare(lam, X, rel, gold, spec, 1e-10)["ok"]
+    # an injected extra converged eigenvalue strictly inside the contour
+    lam2 = np.append(lam, 6.1 + 0.01j)
+    X2 = np.concatenate([X, rng.normal(size=(40, 1)) + 0j], axis=1)
+    r = bench.eig_compare(lam2, X2, np.append(rel, 1e-12), gold, spec, 1e-10)
+    assert not r["ok"] and len(r["extras"]) == 1 and not r["missing"]
+    # the same value unconverged, or in the annulus next to the contour, is not an extra
+    assert bench.eig_compare(lam2, X2, np.append(rel, 1e-3), gold, spec, 1e-10)["ok"]
+    lam3 = np.append(lam, 7.99 + 0j)
+    assert bench.eig_compare(lam3, X2, np.append(rel, 1e-12), gold, spec, 1e-10)["ok"]
+    # a golden value missing from the solve (or the golden list short of a found value)
+    r = bench.eig_compare(lam[1:], X[:, 1:], rel[1:], gold, spec, 1e-10)
+    assert not r["ok"] and r["missing"][0][:2] == [5.44, -3e-7]
+    r = bench.eig_compare(lam, X, rel, gold[1:], spec, 1e-10)
+    assert not r["ok"] and len(r["extras"]) == 1
+    # a double eigenvalue found twice with the same vector: multiplicity not met
+    X4 = X.copy()
+    X4[:, 2] = 2.0 * X4[:, 1]
+    r = bench.eig_compare(lam, X4, rel, gold, spec, 1e-10)
+    assert not r["ok"] and r["missing"] == [[7.6932, -1e-6, 2, 1]]
+    # a value off by more than the tolerance is both missing and extra
+    lam5 = lam.copy()
+    lam5[0] *= 1 + 1e-8
+    r = bench.eig_compare(lam5, X, rel, gold, spec, 1e-10)
+    assert not r["ok"] and len(r["missing"]) == 1 and len(r["extras"]) == 1

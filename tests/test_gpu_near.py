@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 import torch
 
+import bench
 import synth
 from oracle import assembly as oasm, rr as orr
 
@@ -118,11 +119,6 @@ def test_near_solve_sphere320_against_golden(bem, precision):
     V0 = _dev(synth.complex_gaussian(mesh.n, prob.nu, prob.seed))
     prec = bem.PREC_FP64 if precision == "fp64" else bem.PREC_MIXED
     lam, X, rel = ctx.solve(V0, q=10, precision=prec, tol=1e-14)
-    Xh = X.cpu().numpy()
-    for lg, mult in _golden("sphere320_near"):
-        near = np.where(np.abs(lam - lg) <= 1e-10 * abs(lg))[0]
-        assert len(near) >= 1, (lg, lam)
-        sv = np.linalg.svd(Xh[:, near] / np.linalg.norm(Xh[:, near], axis=0), compute_uv=False)
-        assert np.sum(sv > 1e-6) >= mult, (lg, sv)
-        assert np.all(rel[near] < 1e-10)
+    res = bench.eig_compare(lam, X.cpu().numpy(), rel, _golden("sphere320_near"), spec, 1e-10)
+    assert not res["missing"] and not res["extras"], res
     ctx.close()

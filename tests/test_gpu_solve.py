@@ -9,6 +9,7 @@ import pytest
 import scipy.linalg as sla
 import torch
 
+import bench
 import synth
 from oracle import contour as ocon, rr as orr
 
@@ -84,33 +85,14 @@ def test_reduced_solve_sphere320_matches_oracle_pencil(bem):
     ctx.close()
 
 
-def _golden(name):
-    import os
-    rows = []
-    path = os.path.join(os.path.dirname(__file__), "golden", f"eigs_{name}.txt")
-    for line in open(path):
-        if line.startswith("#"):
-            continue
-        re_, im_, mult, ins = line.split()
-        if int(ins):
-            rows.append((complex(float(re_), float(im_)), int(mult)))
-    return rows
-
-
-def _check_against_golden(name, lam, X, rel, tol):
-    gold = _golden(name)
-    Xh = X.cpu().numpy()
+def _check_against_golden(name, lam, X, rel, tol, spec):
+    """Every golden eigenvalue found (with its multiplicity of independent vectors and a
+    converged residual) and no converged extra strictly inside the contour."""
+    res = bench.eig_compare(lam, X.cpu().numpy(), rel, bench.read_golden(name), spec, tol)
     print(name, "found", lam, "relres", rel)
-    for lg, mult in gold:
-        near = np.where(np.abs(lam - lg) <= tol * abs(lg))[0]
-        assert len(near) >= 1, (lg, lam)
-        # independent vectors at this eigenvalue: at least its multiplicity
-        sv = np.linalg.svd(Xh[:, near] / np.linalg.norm(Xh[:, near], axis=0), compute_uv=False)
-        assert np.sum(sv > 1e-6) >= mult, (lg, sv)
-        assert np.all(rel[near] < 1e-10)
-    # nothing converged inside the contour that is not an eigenvalue of the golden list
-    for l in lam[rel < 1e-10]:
-        assert min(abs(l - g) for g, _ in gold) <= tol * abs(l) or True
+    assert not res["missing"], res
+    assert not res["extras"], res
+    assert res["ok"]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -123,7 +105,7 @@ def test_solve_sphere320_against_golden(bem, precision):
     V0 = bem.fortran(torch.from_numpy(synth.complex_gaussian(mesh.n, prob.nu, prob.seed)).to("cuda:0"))
     prec = bem.PREC_FP64 if precision == "fp64" else bem.PREC_MIXED
     lam, X, rel = ctx.solve(V0, q=10, precision=prec, tol=1e-14)
-    _check_against_golden("sphere320", lam, X, rel, 1e-10)
+    _check_against_golden("sphere320", lam, X, rel, 1e-10, spec)
     ctx.close()
 
 
@@ -140,5 +122,5 @@ def test_solve_cube3072_mixed_against_golden(bem):
     t0 = time.perf_counter()
     lam, X, rel = ctx.solve(V0, q=10, precision=bem.PREC_MIXED, tol=1e-14)
     print("cube3072 solve seconds", time.perf_counter() - t0)
-    _check_against_golden("cube3072", lam, X, rel, 1e-10)
+    _check_against_golden("cube3072", lam, X, rel, 1e-10, spec)
     ctx.close()

@@ -4,6 +4,8 @@ machinery: the smallest singular value of A at the eigenvalue, the argument-prin
 count of det A(z) around the contour, and the closed-form Dirichlet eigenvalues of the
 unit sphere (zeros of spherical Bessel functions, Table 3 of the paper) and unit cube
 (pi sqrt(n1^2 + n2^2 + n3^2), Table 1 of the paper) approached at O(h^2)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -57,3 +59,21 @@ def test_cube_richardson_to_closed_form(oracle_mod):
     assert 3.0 < e[0] / e[1] < 6.0
     rich = vals[1] + (vals[1] - vals[0]) / 3.0
     assert abs(rich - CUBE[0]) < 2e-3 * CUBE[0]
+
+
+@pytest.mark.slow
+def test_cube3072_golden_list_is_complete(oracle_mod):
+    """The stored cube3072 eigenvalues (tests/golden/eigs_cube3072.txt: 5.44004 and the
+    split pair 7.69320 / 7.69325 x 2) are every eigenvalue inside the ellipse, counted with
+    multiplicity by the argument principle, (1 / 2 pi i) \\oint tr(A^{-1} A') dz, which uses
+    none of the refinement that produced the list. The trapezoid rule in the angle converges
+    geometrically (the nearest eigenvalue sits at Im(theta) ~ 0.27 from the contour: error
+    ~ e^{-0.27 M}), so on 48 points the count is an integer to well within 1e-3."""
+    prob = synth.workload("cube3072").problems[0]
+    m = prob.mesh()
+    gold = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "eigs_cube3072.txt"),
+                      ndmin=2)
+    expected = int(np.sum(gold[gold[:, 3] == 1, 2]))
+    assert expected == 4
+    count = refine.winding_count(m, prob.contour, M=48)
+    assert abs(count - expected) < 1e-3, count
