@@ -366,6 +366,30 @@ bem_status bem_check(bem_ctx* ctx, void* stream);
  * next call that synchronises). Off by default.
  */
 bem_status bem_set_async(bem_ctx* ctx, int on);
+/*
+ * Bound of the pipeline-stage waits of the fused mixed-precision projection kernel
+ * (operational; the paper has no counterpart): each wait of a block on its shared-memory
+ * pipeline (copies landed, entries evaluated, tensor-core products done) polls an mbarrier
+ * at most `polls` times, with 64 ns sleeps after the first 64 (default 1 << 24, about a
+ * second), then records BEM_ETIMEOUT in the device status word, raises the block's abort
+ * flag and returns. The waits that drain copies and tensor-core products still in flight
+ * before a block frees its shared memory and tensor memory keep the default bound whatever
+ * this value is, so an aborted block leaves no asynchronous work behind and the context
+ * stays usable. polls = 0 makes every stage wait give up at once (a way to exercise the
+ * timeout path). Applies to projections planned after the call (bem_project,
+ * bem_apply_sum, batches created afterwards).
+ */
+bem_status bem_set_wait_limit(bem_ctx* ctx, uint32_t polls);
+/*
+ * Split of the fused mixed-precision kernel's transcendental work between two pipes
+ * (tuning; the paper has no counterpart). Each entry of A(z_j) sums 7 quadrature points,
+ * each needing e^{i Re(z_j) r}: for the first poly_points of them (0..4) its cosine and
+ * sine come from minimax polynomials on the FP32 FMA pipe (phase reduced in half
+ * revolutions; error below 2e-7), for the rest from the MUFU sin/cos unit, so that neither
+ * pipe idles while the other binds. -1 (the default) selects the measured best split for
+ * the unit shape. Applies to later bem_project calls. BEM_EINVAL outside -1..4.
+ */
+bem_status bem_set_eval_split(bem_ctx* ctx, int poly_points);
 
 /* Number of CUDA kernels this context has launched since creation (diagnostics). */
 int64_t bem_kernel_launches(const bem_ctx* ctx);
@@ -380,7 +404,9 @@ int64_t bem_kernel_launches(const bem_ctx* ctx);
  *   At most 256 launches are kept between resets.
  * bem_microbench: measured throughput (operations per second over the whole device) of
  *   one pipe: kind 0 FP64 FMA (2 flops each), 1 FP32 FMA (2 flops each), 2 MUFU ex2,
- *   3 MUFU sin, 4 MUFU cos, 5 MUFU rsqrt. Synchronous; runs on the legacy default stream.
+ *   3 MUFU sin, 4 MUFU cos, 5 MUFU rsqrt, 6 paired FP32 FMA (fma.rn.f32x2, 2 flops per
+ *   lane), 7 the fused kernel's polynomial sine-and-cosine on the FMA pipe (phases per
+ *   second, each giving both). Synchronous; runs on the legacy default stream.
  */
 bem_status bem_set_timing(bem_ctx* ctx, int enable);
 bem_status bem_kernel_times(bem_ctx* ctx, double* ms_out, int max_out, int* count);
@@ -576,17 +602,25 @@ bem_status bem_project_batched(bem_ctx* const* ctxs, int nprob, const double* co
  * library holds until the process exits; nothing is allocated or freed by this call.
  * Limit: 372*nt + 16*nt*N + 16*nt*nu + 32*N bytes (plus alignment) must fit in 64 MiB,
  * otherwise BEM_EINVAL (e.g. nt = 3072, N = 32, nu = 64 fits; the nodes are processed in
- * groups that fit). The first call on a device looks up the array's device address (with
- * that device current); make that first call before any stream capture. All calls share
- * the array and it keeps the last call's contents: calls that overlap on the GPU (other
- * streams or threads) race and must be serialised by the caller. Returns BEM_EINVAL for a
- * bad argument or a vertex index out of range, BEM_ECUDA on a CUDA error. Synchronises the
- * stream once (after the geometry checks); the rest is asynchronous on `stream`.
+ * groups that fit). Every call looks up the array's device address on `device` (with that
+ * device current; this allocates nothing, and a primary context that was reset and
+ * re-created in between is handled); the first call on a device may load the module, so
+ * make it before any stream capture. All calls share the array and it keeps the last
+ * call's contents: calls that overlap on the GPU (other streams or threads) race and must
+ * be serialised by the caller. Returns BEM_EINVAL for a bad argument, a problem beyond the
+ * limit or a vertex index out of range, BEM_ECUDA on a CUDA error; the reason is kept per
+ * host thread for bem_noalloc_last_error. Synchronises the stream once (after the geometry
+ * checks); the rest is asynchronous on `stream`.
  */
 bem_status bem_project_fp64_noalloc(int device, int64_t nv, const double* xyz_dev, int64_t nt,
                                     const int32_t* tri_dev, int kind, double c_re, double c_im,
                                     double a, double b, int N, const double* V_dev,
                                     int64_t ldv, int nu, double* Bhat_dev, void* stream);
+/*
+ * Message of the calling host thread's last failed bem_project_fp64_noalloc call (empty
+ * after a successful one). The string stays valid until the thread's next call.
+ */
+const char* bem_noalloc_last_error(void);
 
 #ifdef __cplusplus
 }

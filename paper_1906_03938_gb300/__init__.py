@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libbem_gb300.so")
 BEM_OK = 0
 STATUS = {0: "BEM_OK", -1: "BEM_EINVAL", -2: "BEM_ENOMEM", -3: "BEM_ECUDA", -4: "BEM_EKERNEL",
           -5: "BEM_ETIMEOUT", -6: "BEM_ENOCONV", -7: "BEM_ESTATE"}
+STATUS_CODES = {v: k for k, v in STATUS.items()}
 PREC_FP64 = 0
 PREC_MIXED = 1
 PREC_HMATRIX = 2
@@ -44,6 +45,8 @@ SIGNATURES = {
     "bem_project": (_I, [_P, _P, _I64, _I, _P, _P, _I, _P]),
     "bem_node_order": (_I, [_P, _P, _P]),
     "bem_set_async": (_I, [_P, _I]),
+    "bem_set_wait_limit": (_I, [_P, ctypes.c_uint32]),
+    "bem_set_eval_split": (_I, [_P, _I]),
     "bem_set_operator": (_I, [_P, _D, _D, _D, _D]),
     "bem_set_hmatrix": (_I, [_P, _I, _D, _D, _I]),
     "bem_hmatrix_stats": (_I, [_P, _P, _P, _P, _P, _P]),
@@ -67,6 +70,7 @@ SIGNATURES = {
     "bem_microbench": (_I, [_P, _I, ctypes.POINTER(_D)]),
     "bem_project_fp64_noalloc": (_I, [_I, _I64, _P, _I64, _P, _I, _D, _D, _D, _D, _I, _P,
                                       _I64, _I, _P, _P]),
+    "bem_noalloc_last_error": (ctypes.c_char_p, []),
     "bem_chebyshev_coeffs": (_I, [_P, _P, _I, _P, _P]),
     "bem_solve_chebyshev": (_I, [_P, _P, _I, _D, _D, _I, _I, _D, _P, _P, _P, ctypes.POINTER(_I),
                                  _P]),
@@ -211,9 +215,11 @@ class Context:
         return ms[:cnt.value]
 
     def microbench(self, kind):
-        """Measured device throughput in ops/s: 'fp64_fma', 'fp32_fma' (flops), 'ex2',
-        'sin', 'cos', 'rsqrt' (MUFU operations)."""
-        kinds = {"fp64_fma": 0, "fp32_fma": 1, "ex2": 2, "sin": 3, "cos": 4, "rsqrt": 5}
+        """Measured device throughput in ops/s: 'fp64_fma', 'fp32_fma', 'fp32x2_fma'
+        (flops), 'ex2', 'sin', 'cos', 'rsqrt' (MUFU operations), 'sincos_poly' (phases
+        whose sine and cosine the FMA-pipe polynomials give)."""
+        kinds = {"fp64_fma": 0, "fp32_fma": 1, "ex2": 2, "sin": 3, "cos": 4, "rsqrt": 5,
+                 "fp32x2_fma": 6, "sincos_poly": 7}
         r = _D(0.0)
         self._chk("bem_microbench", self._lib.bem_microbench(self._h, kinds[kind], ctypes.byref(r)))
         return r.value
@@ -384,6 +390,16 @@ class Context:
     def set_async(self, on=True):
         """Asynchronous mode: cholqr2 leaves its status check to check()."""
         self._chk("bem_set_async", self._lib.bem_set_async(self._h, 1 if on else 0))
+
+    def set_wait_limit(self, polls):
+        """Polls of each pipeline-stage wait of the fused kernel before it gives up with
+        BEM_ETIMEOUT (0: at once); the default is 1 << 24."""
+        self._chk("bem_set_wait_limit", self._lib.bem_set_wait_limit(self._h, int(polls)))
+
+    def set_eval_split(self, poly_points=-1):
+        """Quadrature points (0..4 of 7) per entry whose sine and cosine the fused kernel
+        takes from the FMA-pipe polynomials; -1: the measured default."""
+        self._chk("bem_set_eval_split", self._lib.bem_set_eval_split(self._h, int(poly_points)))
 
     def node_order(self):
         """(order, twins): the mixed kernel's node schedule (slot -> node) and the number

@@ -260,6 +260,19 @@ bem_status bem_set_async(bem_ctx* ctx, int on) {
   return BEM_OK;
 }
 
+bem_status bem_set_wait_limit(bem_ctx* ctx, uint32_t polls) {
+  if (!ctx) return BEM_EINVAL;
+  ctx->stage_wait_limit = polls;
+  return BEM_OK;
+}
+
+bem_status bem_set_eval_split(bem_ctx* ctx, int poly_points) {
+  if (!ctx || poly_points < -1 || poly_points > 4)
+    return fail(ctx, BEM_EINVAL, "bem_set_eval_split: poly_points must be -1 or 0..4");
+  ctx->poly_points = poly_points;
+  return BEM_OK;
+}
+
 bem_status bem_check(bem_ctx* ctx, void* stream) {
   if (!ctx) return BEM_EINVAL;
   cudaSetDevice(ctx->device);

@@ -30,6 +30,9 @@ enum : int {
   kStatusNonFinite = 8,    // a non-finite value where a finite one is required
   kStatusTimeout = 16,     // a bounded device wait gave up (the kernel aborted cleanly)
 };
+// polls (with 64 ns sleeps after the first 64: about a second) of a bounded device wait
+constexpr uint32_t kStageWaitDefault = 1u << 24;
+
 
 // Device geometry, structure-of-arrays, FP64 (plain path) and FP32 (mixed path).
 // Quadrature arrays are q-major: element (q, l) at q * n + l, so that consecutive
@@ -131,6 +134,12 @@ struct bem_ctx {
   cudaEvent_t con_ev = nullptr;
   // asynchronous mode: bem_cholqr2 does not wait for its status word (bem_check reports it)
   bool async = false;
+  // polls of each pipeline-stage wait of the fused projection kernel before it gives up
+  // (bem_set_wait_limit); the drains before a block releases its memory keep the full bound
+  uint32_t stage_wait_limit = bem::kStageWaitDefault;
+  // quadrature points per entry whose sine and cosine the fused kernel takes from the FMA-
+  // pipe polynomials (bem_set_eval_split); -1: the measured default of the unit shape
+  int poly_points = -1;
   // the boundary operator T = c_G G + c_H (1/2 I + K) (single layer by default)
   bem::OpCoef op;
   int64_t op_version = 0;   // bumped by every bem_set_operator

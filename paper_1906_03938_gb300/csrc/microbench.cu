@@ -4,6 +4,7 @@
 // FP32 FMA and the MUFU transcendental unit for the mixed path).
 #include <vector>
 
+#include "f32x2.cuh"
 #include "internal.h"
 
 namespace bem {
@@ -68,13 +69,59 @@ __global__ void __launch_bounds__(kThreads) mufu_kernel(float* out, float seed) 
   if (s == 12345.678f) out[0] = s;
 }
 
+// paired FP32 FMA (fma.rn.f32x2): 4 flops per instruction and thread
+__global__ void __launch_bounds__(kThreads) fma32x2_kernel(float* out, float seed) {
+  f2_t a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = f2(seed + threadIdx.x + k, seed - k);
+  const f2_t m = f2dup(0.9999f), c = f2dup(1e-4f);
+#pragma unroll 4
+  for (int it = 0; it < kIters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma2(a[k], m, c);
+  }
+  float s = 0, x, y;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    f2split(a[k], x, y);
+    s += x + y;
+  }
+  if (s == 12345.678f) out[0] = s;
+}
+
+// the fused kernel's polynomial e^{i phi} (sincos_poly2), two phases per call; the next
+// phases depend on the results (one extra paired FMA per call)
+__global__ void __launch_bounds__(kThreads) sincos_poly_kernel(float* out, float seed) {
+  f2_t a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = f2(1e-3f * (seed + threadIdx.x + k), 0.5f + k);
+  const f2_t m = f2dup(3.0f);
+#pragma unroll 2
+  for (int it = 0; it < kIters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      f2_t c, s, sg;
+      sincos_poly2(a[k], c, s, sg);
+      a[k] = fma2(c ^ sg, m, s);
+    }
+  }
+  float s = 0, x, y;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    f2split(a[k], x, y);
+    s += x + y;
+  }
+  if (s == 12345.678f) out[0] = s;
+}
+
 }  // namespace
 }  // namespace bem
 
 using namespace bem;
 
 extern "C" bem_status bem_microbench(bem_ctx* ctx, int kind, double* ops_per_s) {
-  if (!ctx || !ops_per_s || kind < 0 || kind > 5) return fail(ctx, BEM_EINVAL, "bem_microbench: bad argument");
+  if (!ctx || !ops_per_s || kind < 0 || kind > 7)
+    return fail(ctx, BEM_EINVAL, "bem_microbench: bad argument");
   cudaSetDevice(ctx->device);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
@@ -93,7 +140,9 @@ extern "C" bem_status bem_microbench(bem_ctx* ctx, int kind, double* ops_per_s) 
       case 2: mufu_kernel<0><<<blocks, kThreads>>>(reinterpret_cast<float*>(ctx->d_small), 1.0f); break;
       case 3: mufu_kernel<1><<<blocks, kThreads>>>(reinterpret_cast<float*>(ctx->d_small), 1.0f); break;
       case 4: mufu_kernel<2><<<blocks, kThreads>>>(reinterpret_cast<float*>(ctx->d_small), 1.0f); break;
-      default: mufu_kernel<3><<<blocks, kThreads>>>(reinterpret_cast<float*>(ctx->d_small), 1.0f); break;
+      case 5: mufu_kernel<3><<<blocks, kThreads>>>(reinterpret_cast<float*>(ctx->d_small), 1.0f); break;
+      case 6: fma32x2_kernel<<<blocks, kThreads>>>(reinterpret_cast<float*>(ctx->d_small), 1.0f); break;
+      default: sincos_poly_kernel<<<blocks, kThreads>>>(reinterpret_cast<float*>(ctx->d_small), 1.0f); break;
     }
     cudaEventRecord(e1, 0);
     ctx->launches++;
@@ -106,7 +155,10 @@ extern "C" bem_status bem_microbench(bem_ctx* ctx, int kind, double* ops_per_s) 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != BEM_OK) return st;
-  const double ops = (double)blocks * kThreads * kIters * 8 * ((kind <= 1) ? 2.0 : 1.0);
+  // flops for the FMA kinds (2 per FMA lane), operations for the MUFU kinds, phases for
+  // the polynomial sine / cosine
+  const double per = kind <= 1 ? 2.0 : (kind == 6 ? 4.0 : (kind == 7 ? 2.0 : 1.0));
+  const double ops = (double)blocks * kThreads * kIters * 8 * per;
   *ops_per_s = ops / (best * 1e-3);
   return BEM_OK;
 }

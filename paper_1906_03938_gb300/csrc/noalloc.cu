@@ -9,16 +9,20 @@
 // anything it calls allocates.
 //
 // The array is a __device__ symbol: in host code its name is only a host-side stand-in, so
-// its device address is obtained with cudaGetSymbolAddress once per device (with that
-// device current) on the first call on that device, and that address is what the kernels
-// receive. Every GPU that loads this library holds the array until the process exits.
+// its device address is obtained with cudaGetSymbolAddress (with the device current) and
+// that address is what the kernels receive. The lookup is repeated on every call, so a
+// device whose primary context was reset and re-created in between gets the array's new
+// address; it allocates nothing (the first lookup on a device may load the module, which
+// is why the first call should come before any stream capture). Every GPU that loads this
+// library holds the array until the process exits. The message of the last failure on the
+// calling thread is kept for bem_noalloc_last_error.
 // All calls share it and it keeps the last call's contents; calls whose work overlaps on
 // the GPU (other streams, other host threads) race on it and must be serialised by the
 // caller.
 #include <math.h>
 
 #include <algorithm>
-#include <mutex>
+#include <string>
 
 #include "internal.h"
 
@@ -30,8 +34,12 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
-std::mutex g_setup_mutex;
-void* g_scratch_addr[kMaxDevices] = {};
+thread_local std::string g_last_error;   // message of the calling thread's last failure
+
+bem_status noalloc_fail(bem_status st, const std::string& msg) {
+  g_last_error = "bem_project_fp64_noalloc: " + msg;
+  return st;
+}
 
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -52,35 +60,33 @@ extern "C" bem_status bem_project_fp64_noalloc(int device, int64_t nv, const dou
                                                double c_re, double c_im, double a, double b,
                                                int N, const double* V_dev, int64_t ldv, int nu,
                                                double* Bhat_dev, void* stream) {
+  g_last_error.clear();
   if (!xyz_dev || !tri_dev || !V_dev || !Bhat_dev || nv < 3 || nt < 1 || nu < 1 ||
       nu > kMaxNu || ldv < nt || N < 1 || N > kMaxNodes || device < 0 || device >= kMaxDevices)
-    return BEM_EINVAL;
-  if (kind != BEM_CONTOUR_CIRCLE && kind != BEM_CONTOUR_ELLIPSE) return BEM_EINVAL;
+    return noalloc_fail(BEM_EINVAL, "bad argument (null pointer, size or device out of range)");
+  if (kind != BEM_CONTOUR_CIRCLE && kind != BEM_CONTOUR_ELLIPSE)
+    return noalloc_fail(BEM_EINVAL, "unknown contour kind");
   if (kind == BEM_CONTOUR_CIRCLE) b = a;
   if (!(a > 0.0) || !(b > 0.0) || !isfinite(a) || !isfinite(b) || !isfinite(c_re) ||
       !isfinite(c_im))
-    return BEM_EINVAL;
+    return noalloc_fail(BEM_EINVAL, "contour centre and semi-axes must be finite, axes > 0");
   // size limit: the fixed parts plus the products of at least one node must fit
   const size_t fixed = fixed_bytes(nt, N);
   const size_t per_node = round256((size_t)2 * nt * nu * sizeof(double));
-  if (fixed + per_node > kNoallocBytes) return BEM_EINVAL;
+  if (fixed + per_node > kNoallocBytes)
+    return noalloc_fail(BEM_EINVAL, "problem too large for the fixed " +
+                                        std::to_string(kNoallocBytes >> 20) + " MiB array");
 
   int cur = -1;
-  if (cudaGetDevice(&cur) != cudaSuccess) return BEM_ECUDA;
-  if (cur != device && cudaSetDevice(device) != cudaSuccess) return BEM_ECUDA;
+  if (cudaGetDevice(&cur) != cudaSuccess) return noalloc_fail(BEM_ECUDA, "cudaGetDevice failed");
+  if (cur != device && cudaSetDevice(device) != cudaSuccess)
+    return noalloc_fail(BEM_ECUDA, "cudaSetDevice failed");
   void* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[device]) {
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-        cudaGetLastError();
-        if (cur != device) cudaSetDevice(cur);
-        return BEM_ECUDA;
-      }
-      g_scratch_addr[device] = p;
-    }
-    base = g_scratch_addr[device];
+  const cudaError_t ge = cudaGetSymbolAddress(&base, g_noalloc_scratch);
+  if (ge != cudaSuccess || !base) {
+    cudaGetLastError();
+    if (cur != device) cudaSetDevice(cur);
+    return noalloc_fail(BEM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(ge));
   }
 
   // carve the array: status | FP64 geometry | FP32 geometry | z | w | self | Y chunk
@@ -137,5 +143,9 @@ extern "C" bem_status bem_project_fp64_noalloc(int device, int64_t nv, const dou
     ctx.con = c;
   }
   if (cur != device) cudaSetDevice(cur);
+  if (st != BEM_OK)
+    noalloc_fail(st, ctx.err.empty() ? std::string("CUDA error on a launch") : ctx.err);
   return st;
 }
+
+extern "C" const char* bem_noalloc_last_error(void) { return g_last_error.c_str(); }

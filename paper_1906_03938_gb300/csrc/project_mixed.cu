@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "f32x2.cuh"
 #include "internal.h"
 #include "sm100.cuh"
 
@@ -45,8 +46,14 @@ constexpr int kEvalThreads = 32 * kEvalWarps;
 constexpr int kThreads = 32 * (2 + kEvalWarps);
 constexpr int kMaxG = 4;
 constexpr int kPlaneBytes = kBM * kBK * 2;   // one BF16 plane of a 128 x 16 block: 4 KB
-constexpr uint32_t kWaitLimit = 1u << 24;    // polls (with 64 ns sleeps) before giving up
+constexpr uint32_t kWaitLimit = kStageWaitDefault;   // polls (64 ns sleeps) before giving up
 constexpr float kLog2e = 1.4426950408889634f;
+// Quadrature points (of 7) per entry whose sine and cosine the fused kernel evaluates by
+// the FMA-pipe polynomials rather than on the MUFU unit, by unit shape: units of several
+// nodes (shared rsqrt, twin nodes sharing sine and cosine) and units of one node.
+constexpr int kPolyPointsMulti = 1;
+constexpr int kPolyPointsSingle = 1;
+constexpr int kPolyPointsMax = 4;
 
 struct MixedParams {
   int64_t n;          // unknowns
@@ -78,6 +85,7 @@ struct MixedParams {
   const __nv_bfloat16* Bp;   // prepared basis planes, tile-native
   float* Yp;          // FP32 partial products [S][N][2 nup][n_pad]
   int* status;
+  uint32_t wait_limit;   // polls of each pipeline-stage wait (the drains keep kWaitLimit)
 };
 
 struct SmemLayout {
@@ -121,35 +129,6 @@ __device__ __forceinline__ float cosf_mufu(float x) {
 __device__ __forceinline__ float rsqrtf_mufu(float x) {
   float r;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-
-// Packed FP32 pairs: the evaluation handles two entries of a row at once (its two columns
-// of the 16-wide K-block), so their identical arithmetic goes through the paired FP32
-// instructions (one instruction per two lanes' worth of work; same rounding as the scalar
-// operations).
-typedef unsigned long long f2_t;
-__device__ __forceinline__ f2_t f2(float a, float b) {
-  f2_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void f2split(f2_t v, float& a, float& b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ f2_t mul2(f2_t a, f2_t b) {
-  f2_t r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ f2_t sub2(f2_t a, f2_t b) {
-  f2_t r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c) {
-  f2_t r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
   return r;
 }
 
@@ -212,8 +191,9 @@ __device__ __forceinline__ void put_entries(f2_t sr2, f2_t si2, const float2* se
 
 // bounded wait that also watches the block's abort flag
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
-                                              volatile int* abort_flag, int* status) {
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+                                              volatile int* abort_flag, int* status,
+                                              uint32_t limit = kWaitLimit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
     if (it > 64) __nanosleep(64);
@@ -230,7 +210,9 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
 constexpr uint32_t kNoTmem = 0xffffffffu;
 // kSum: the node-summed mode (p.sum is set accordingly by the host); kOp: the general
 // operator c_G G + c_H (1/2 I + K) (else the single layer, c_G = 1, c_H = 0)
-template <bool kSum, bool kOp = false>
+// kNP: quadrature points (the first kNP of 7) whose sine and cosine come from the FMA-pipe
+// polynomials (sincos_poly2) instead of the MUFU unit, which balances the two pipes.
+template <bool kSum, bool kOp = false, int kNP = 0>
 __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int u,
                                                  const uint32_t tmem_given) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -328,8 +310,8 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
       const int Gvi = kSum ? min(p.G, p.N - j0i) : Gv;
       int ok = 1;
       if (lane == 0)
-        ok = early ? wait_or_abort(&afull[s], par ^ 1, abort_flag, p.status)
-                   : wait_or_abort(&empty[s], par ^ 1, abort_flag, p.status);
+        ok = early ? wait_or_abort(&afull[s], par ^ 1, abort_flag, p.status, p.wait_limit)
+                   : wait_or_abort(&empty[s], par ^ 1, abort_flag, p.status, p.wait_limit);
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
       auto issue_b = [&]() {
@@ -355,7 +337,7 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
       }
       ++issued_g;
       // tile-relative FP32 coordinates from the hi/lo pairs: (y_hi - o_hi) + (y_lo - o_lo)
-      if (!wait_or_abort(&gready[s], par, abort_flag, p.status)) break;
+      if (!wait_or_abort(&gready[s], par, abort_flag, p.status, p.wait_limit)) break;
       const float* graw = sGraw + s * (kBK * 64);
       float4* sCol = sColAll + s * (kBK * 7);
       for (int x = lane; x < kBK * 7; x += 32) {
@@ -376,7 +358,7 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
       }
       mbar_arrive(&gfull[s]);   // release: the staged values are visible to the waiters
       if (early) {
-        if (lane == 0) ok = wait_or_abort(&empty[s], par ^ 1, abort_flag, p.status);
+        if (lane == 0) ok = wait_or_abort(&empty[s], par ^ 1, abort_flag, p.status, p.wait_limit);
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) break;
         issue_b();
@@ -400,8 +382,8 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
       for (int it = 0; it < nit; ++it) {
         const int s = it % kStages;
         const uint32_t par = (it / kStages) & 1;
-        if (!wait_or_abort(&afull[s], par, abort_flag, p.status)) break;
-        if (!wait_or_abort(&bfull[s], par, abort_flag, p.status)) break;
+        if (!wait_or_abort(&afull[s], par, abort_flag, p.status, p.wait_limit)) break;
+        if (!wait_or_abort(&bfull[s], par, abort_flag, p.status, p.wait_limit)) break;
         tc_fence_after();
         const uint32_t a_base = smem_u32(sA + s * L.a_stage_bytes);
         const uint32_t b_base = smem_u32(sB + s * L.b_stage_bytes);
@@ -472,9 +454,10 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
       // the column geometry, and the stage's A planes free of the MMAs of its last round
       // (one lane per warp observes the MMAs' completion; the warp synchronises on it)
       int free_ok = 1;
-      if (p.G < kMaxG && lane == 0) free_ok = wait_or_abort(&empty[s], par ^ 1, abort_flag, p.status);
+      if (p.G < kMaxG && lane == 0)
+        free_ok = wait_or_abort(&empty[s], par ^ 1, abort_flag, p.status, p.wait_limit);
       free_ok = __shfl_sync(0xffffffffu, free_ok, 0);
-      const bool ready = wait_or_abort(&gfull[s], par, abort_flag, p.status) && free_ok;
+      const bool ready = wait_or_abort(&gfull[s], par, abort_flag, p.status, p.wait_limit) && free_ok;
       const float4* sCol = sColAll + s * (kBK * 7);
       const float2* sSelf = sSelfAll + s * (kBK * kMaxG);
       unsigned char* a_stage = sA + s * L.a_stage_bytes;
@@ -525,15 +508,24 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
             const f2_t kr2 = f2(kr[g], kr[g]);
 #pragma unroll
             for (int q = 0; q < 7; ++q) {
-              float e0, e1, e2, e3, p0, p1;
+              float e0, e1, e2, e3;
               f2split(mul2(kma, rr2[q]), e0, e1);
               f2split(mul2(kmb, rr2[q]), e2, e3);
-              const f2_t aa = mul2(am2[q], f2(ex2f(e0), ex2f(e1)));
-              const f2_t ab = mul2(am2[q], f2(ex2f(e2), ex2f(e3)));
+              f2_t aa = mul2(am2[q], f2(ex2f(e0), ex2f(e1)));
+              f2_t ab = mul2(am2[q], f2(ex2f(e2), ex2f(e3)));
               const f2_t ph2 = mul2(kr2, rr2[q]);
-              f2split(ph2, p0, p1);
-              const f2_t cs = f2(cosf_mufu(p0), cosf_mufu(p1));
-              const f2_t sn = f2(sinf_mufu(p0), sinf_mufu(p1));
+              f2_t cs, sn;
+              if (q < kNP) {   // FMA pipe: e^{i ph} = (-1)^n e^{i pi f}, the sign into aa, ab
+                f2_t sg;
+                sincos_poly2(ph2, cs, sn, sg);
+                aa ^= sg;
+                ab ^= sg;
+              } else {
+                float p0, p1;
+                f2split(ph2, p0, p1);
+                cs = f2(cosf_mufu(p0), cosf_mufu(p1));
+                sn = f2(sinf_mufu(p0), sinf_mufu(p1));
+              }
               if constexpr (kOp) {
                 op_acc2(sa, ia, aa, cs, sn, s2[q], ph2,
                         mul2(f2(kim[g], kim[g]), rr2[q]), cgr2, cgi2, chr2, chi2, nchi2, m1);
@@ -561,20 +553,29 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
               for (int q = 0; q < 7; ++q) {
                 float e0, e1;
                 f2split(mul2(kmi2, rr2[q]), e0, e1);
-                const f2_t a = mul2(am2[q], f2(ex2f(e0), ex2f(e1)));
-                // the MUFU sine and cosine reduce their argument in revolutions themselves;
-                // that reduction's error (half an FP32 ulp of ph / 2 pi) is of the order of
-                // the rounding of ph itself, so no explicit reduction precedes them
-                float p0, p1;
+                f2_t a = mul2(am2[q], f2(ex2f(e0), ex2f(e1)));
                 const f2_t ph2 = mul2(kr2, rr2[q]);
-                f2split(ph2, p0, p1);
-                if constexpr (kOp) {
-                  op_acc2(sr2, si2, a, f2(cosf_mufu(p0), cosf_mufu(p1)),
-                          f2(sinf_mufu(p0), sinf_mufu(p1)), s2[q], ph2,
-                          mul2(f2(kim[h], kim[h]), rr2[q]), cgr2, cgi2, chr2, chi2, nchi2, m1);
+                f2_t cs, sn;
+                if (q < kNP) {   // FMA pipe: e^{i ph} = (-1)^n e^{i pi f}, the sign into a
+                  f2_t sg;
+                  sincos_poly2(ph2, cs, sn, sg);
+                  a ^= sg;
                 } else {
-                  sr2 = fma2(a, f2(cosf_mufu(p0), cosf_mufu(p1)), sr2);
-                  si2 = fma2(a, f2(sinf_mufu(p0), sinf_mufu(p1)), si2);
+                  // the MUFU sine and cosine reduce their argument in revolutions
+                  // themselves; that reduction's error (half an FP32 ulp of ph / 2 pi) is
+                  // of the order of the rounding of ph itself, so no explicit reduction
+                  // precedes them
+                  float p0, p1;
+                  f2split(ph2, p0, p1);
+                  cs = f2(cosf_mufu(p0), cosf_mufu(p1));
+                  sn = f2(sinf_mufu(p0), sinf_mufu(p1));
+                }
+                if constexpr (kOp) {
+                  op_acc2(sr2, si2, a, cs, sn, s2[q], ph2, mul2(f2(kim[h], kim[h]), rr2[q]), cgr2,
+                          cgi2, chr2, chi2, nchi2, m1);
+                } else {
+                  sr2 = fma2(a, cs, sr2);
+                  si2 = fma2(a, sn, si2);
                 }
               }
               put_entries(sr2, si2, selfk + h, i, l0, p.n, a_stage + h * 4 * kPlaneBytes + off,
@@ -589,7 +590,7 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
     }
 
     // ---------------- epilogue: TMEM -> FP32 partial Y ----------------
-    const bool ok = !*abort_flag && wait_or_abort(accfull, 0, abort_flag, p.status);
+    const bool ok = !*abort_flag && wait_or_abort(accfull, 0, abort_flag, p.status, p.wait_limit);
     if (__all_sync(0xffffffffu, ok)) {   // tcgen05.ld is warp-collective
       tc_fence_after();
       const int quarter = warp % 4;              // TMEM lanes this warp may read
@@ -624,16 +625,16 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
   }
 }
 
-template <bool kOp>
+template <bool kOp, int kNP>
 __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p) {
-  mixed_apply_unit<false, kOp>(p, blockIdx.x, kNoTmem);
+  mixed_apply_unit<false, kOp, kNP>(p, blockIdx.x, kNoTmem);
 }
 
 // Node-summed form: Y = sum_j c_j A(z_j) X_j (the right-hand side of an inverse power
 // step, X_j per node) or (sum_j c_j A(z_j)) X (one X: the Schur complement S applied).
 template <bool kOp>
 __global__ void __launch_bounds__(kThreads, 1) mixed_sum_kernel(MixedParams p) {
-  mixed_apply_unit<true, kOp>(p, blockIdx.x, kNoTmem);
+  mixed_apply_unit<true, kOp, kPolyPointsMulti>(p, blockIdx.x, kNoTmem);
 }
 
 // Persistent grouped kernel over several problems: one CTA per SM takes work units from a
@@ -667,7 +668,7 @@ mixed_apply_grouped_kernel(const MixedParams* __restrict__ plist, const int* __r
       if (unit_start[mid] <= b) lo = mid; else hi = mid - 1;
     }
     const MixedParams p = plist[lo];
-    mixed_apply_unit<false>(p, b - unit_start[lo], tmem_base);
+    mixed_apply_unit<false, false, kPolyPointsMulti>(p, b - unit_start[lo], tmem_base);
     __syncthreads();   // the unit's barriers, shared memory and accumulators are free again
   }
   tc_fence_before();
@@ -681,9 +682,11 @@ mixed_apply_grouped_kernel(const MixedParams* __restrict__ plist, const int* __r
 // 8 rows x 8 bf16, row stride 16 B, at ng * 256 + kg * 128 bytes.
 __global__ void prep_basis_planes_kernel(const double* __restrict__ V, int64_t ldv, int64_t n,
                                          int nu, int nup, int C, int nK,
-                                         __nv_bfloat16* __restrict__ Bp, float2* __restrict__ V32) {
+                                         __nv_bfloat16* __restrict__ Bp, float2* __restrict__ V32,
+                                         int* status) {
   // one thread per source element (panel l, column col); the split is formed in FP32
-  // (hi + lo carries 16 significant bits, far above FP32's own rounding)
+  // (hi + lo carries 16 significant bits, far above FP32's own rounding). A non-finite
+  // basis entry is recorded in the status word (the projection is then invalid).
   const int64_t rows = (int64_t)nK * kBK;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= rows * nup) return;
@@ -692,6 +695,7 @@ __global__ void prep_basis_planes_kernel(const double* __restrict__ V, int64_t l
   float vr = 0.f, vi = 0.f;
   if (l < n && col < nu) {
     const double2 v = reinterpret_cast<const double2*>(V)[(int64_t)col * ldv + l];
+    if (!isfinite(v.x) || !isfinite(v.y)) atomicOr(status, kStatusNonFinite);
     vr = (float)v.x;
     vi = (float)v.y;
     V32[(int64_t)col * n + l] = make_float2(vr, vi);
@@ -1220,6 +1224,7 @@ bem_status mixed_plan(bem_ctx* ctx, const double* V, int64_t ldv, int nu, int S,
   p.z = ctx->con.z;
   p.order = ctx->con.order;
   p.status = ctx->d_status;
+  p.wait_limit = ctx->stage_wait_limit;
   p.op = ctx->op;
   plan.V = V;
   plan.ldv = ldv;
@@ -1234,7 +1239,7 @@ void mixed_pre(bem_ctx* ctx, const MixedPlan& plan, cudaStream_t s) {
   const MixedParams& p = plan.p;
   const int64_t prep_total = (int64_t)p.nK * kBK * p.nup;
   prep_basis_planes_kernel<<<(unsigned)((prep_total + 255) / 256), 256, 0, s>>>(
-      plan.V, plan.ldv, p.n, p.nu, p.nup, p.C, p.nK, plan.Bp, plan.V32);
+      plan.V, plan.ldv, p.n, p.nu, p.nup, p.C, p.nK, plan.Bp, plan.V32, p.status);
   ctx->launches++;
 }
 
@@ -1266,16 +1271,38 @@ void mixed_post(bem_ctx* ctx, const MixedPlan& plan, double* Bhat, double* AV, c
   }
 }
 
+using MixedKernel = void (*)(MixedParams);
+
+// The fused kernel with np polynomial points (0..kPolyPointsMax), single layer or general
+// operator.
+MixedKernel mixed_kernel(bool general, int np) {
+  static const MixedKernel single[kPolyPointsMax + 1] = {
+      mixed_apply_kernel<false, 0>, mixed_apply_kernel<false, 1>, mixed_apply_kernel<false, 2>,
+      mixed_apply_kernel<false, 3>, mixed_apply_kernel<false, 4>};
+  static const MixedKernel op[kPolyPointsMax + 1] = {
+      mixed_apply_kernel<true, 0>, mixed_apply_kernel<true, 1>, mixed_apply_kernel<true, 2>,
+      mixed_apply_kernel<true, 3>, mixed_apply_kernel<true, 4>};
+  np = std::max(0, std::min(np, kPolyPointsMax));
+  return general ? op[np] : single[np];
+}
+
+// Polynomial points of a projection with G nodes per unit: the context's override, else the
+// measured default of the unit shape.
+int poly_points(const bem_ctx* ctx, int G) {
+  if (ctx->poly_points >= 0) return std::min(ctx->poly_points, kPolyPointsMax);
+  return G > 1 ? kPolyPointsMulti : kPolyPointsSingle;
+}
+
 bem_status set_mixed_smem(bem_ctx* ctx, uint32_t bytes) {
-  bem_status st = cuda_check(ctx, cudaFuncSetAttribute(mixed_apply_kernel<false>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)bytes),
-                             "mixed kernel attribute");
-  if (st != BEM_OK) return st;
-  st = cuda_check(ctx, cudaFuncSetAttribute(mixed_apply_kernel<true>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes),
-                  "mixed kernel attribute");
-  if (st != BEM_OK) return st;
+  bem_status st = BEM_OK;
+  for (int np = 0; np <= kPolyPointsMax && st == BEM_OK; ++np)
+    for (bool general : {false, true}) {
+      st = cuda_check(ctx, cudaFuncSetAttribute(mixed_kernel(general, np),
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)bytes),
+                      "mixed kernel attribute");
+      if (st != BEM_OK) return st;
+    }
   for (const void* f : {(const void*)mixed_vhy_tc_kernel<1>, (const void*)mixed_vhy_tc_kernel<2>,
                         (const void*)mixed_vhy_tc_kernel<4>}) {
     st = cuda_check(ctx, cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1438,6 +1465,7 @@ bem_status mixed_sum_apply(bem_ctx* ctx, const float2* X, int64_t ldx, int64_t n
   p.z = ctx->con.z;
   p.order = ctx->con.order;
   p.status = ctx->d_status;
+  p.wait_limit = ctx->stage_wait_limit;
   p.op = ctx->op;
   bem_status st = ensure_self32(ctx, s);
   if (st != BEM_OK) return st;
@@ -1514,10 +1542,8 @@ bem_status project_mixed(bem_ctx* ctx, const double* V, int64_t ldv, int nu, dou
   mixed_pre(ctx, plan, s);
   if ((st = set_mixed_smem(ctx, plan.L.total)) != BEM_OK) return st;
   timing_begin(ctx, s);
-  if (op_single(ctx->op))
-    mixed_apply_kernel<false><<<(unsigned)plan.units, kThreads, plan.L.total, s>>>(plan.p);
-  else
-    mixed_apply_kernel<true><<<(unsigned)plan.units, kThreads, plan.L.total, s>>>(plan.p);
+  mixed_kernel(!op_single(ctx->op), poly_points(ctx, plan.p.G))
+      <<<(unsigned)plan.units, kThreads, plan.L.total, s>>>(plan.p);
   timing_end(ctx, s);
   ctx->launches++;
   st = cuda_check(ctx, cudaGetLastError(), "mixed apply kernel");

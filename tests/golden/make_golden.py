@@ -9,8 +9,12 @@ refinement reveals. "sphere320_near" is the same sphere with the near-field vari
 (8 x 8 conical rule on near panel pairs). "sphere320_neumann" is the sphere with the
 operator T = 1/2 I + K (the double layer with its jump: the interior Neumann problem, the
 paper's T = A H - B G with B = 0), started from the zeros of j_1' and j_2' (2.0816,
-3.3421) inside the circle of centre 2.75 and radius 0.9. Usage:
+3.3421) inside the circle of centre 2.75 and radius 0.9. "sphere20480_near" is the icosphere
+of level 5 with the near-field variant inside the circle of centre 7 and radius 1, started
+from the zeros of j_0, j_3 and j_1 there (6.2832, 6.9879, 7.7253; about two hours on eight
+cores: every step factorises the dense n = 20480 matrix). Usage:
 python tests/golden/make_golden.py [sphere320] [cube3072] [sphere320_near] [sphere320_neumann]
+                                   [sphere20480_near]
 """
 import os
 import sys
@@ -28,6 +32,7 @@ STARTS = {
     "cube3072": [5.441398, 7.695299],
     "sphere320_near": [3.141593, 4.493409],
     "sphere320_neumann": [2.081576, 3.342094],
+    "sphere20480_near": [6.283185, 6.987932, 7.725252],
 }
 OPERATOR = {"sphere320_neumann": (0.0, 1.0)}
 CONTOUR = {"sphere320_neumann": synth.ContourSpec("circle", 2.75 + 0j, 0.9, 0.9)}

@@ -145,3 +145,28 @@ def test_node_order(bem, kind, N, twins):
         assert np.float32(a.real) == np.float32(b.real)
         assert a.real == b.real and a.imag == -b.imag
     ctx.close()
+
+
+@pytest.mark.parametrize("np_poly", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("case", ["twins_g4", "single_g1"])
+def test_mixed_eval_split_matches_oracle(bem, case, np_poly):
+    """Every split of the sines and cosines between the MUFU unit and the FMA-pipe
+    polynomials (bem_set_eval_split) meets the mixed path's bar against the oracle, for
+    units of four nodes with twin pairs (ellipse) and units of one node (nu = 130)."""
+    if case == "twins_g4":
+        mesh, spec, N, nu = synth.cube_grid(4), synth.ContourSpec("ellipse", 6.5 + 0j, 1.5, 0.4), 8, 24
+    else:
+        mesh, spec, N, nu = synth.icosphere(2), synth.ContourSpec("circle", 9.0 + 0j, 1.5, 1.5), 4, 130
+    V = synth.complex_gaussian(mesh.n, nu, 31)
+    ctx = bem.Context(0)
+    ctx.set_mesh(mesh.xyz, mesh.tri)
+    z, w = ctx.set_contour(spec.kind, spec.centre, spec.a, spec.b, N)
+    ctx.set_eval_split(np_poly)
+    B, Y = ctx.project(_dev(V), bem.PREC_MIXED, AV=True)
+    ctx.check()
+    P, Yo = orr.project(mesh, z, V)
+    Bh, Yh = B.cpu().numpy(), Y.cpu().numpy()
+    worst = max(max(_relerr(Yh[j], Yo[j]), _relerr(Bh[j], w[j] * P[j])) for j in range(N))
+    print(f"{case} poly points {np_poly}: worst rel err {worst:.2e}")
+    assert worst < TOL
+    ctx.close()

@@ -82,3 +82,5 @@ def test_noalloc_rejects_sizes_beyond_its_array(bem):
                   out)
     assert st == -1                                       # BEM_EINVAL, nothing launched
     assert torch.count_nonzero(out).item() == 0
+    # the reason is kept for the calling thread
+    assert b"too large" in bem.load().bem_noalloc_last_error()
