@@ -1,18 +1,25 @@
 """Benchmark of the fused BEM assembly + Rayleigh-Ritz projection on one GB300 per rank.
 
-One step is one pass of the hot path over the unit-cube workload (3072 triangles, 16 x 16
-squares per face; ellipse contour centre 6.5, semi-axes 1.5 and 0.4, N = 32 trapezoid
-nodes; Ritz basis of 64 complex Gaussian columns):
+One step is one pass of the hot path over the largest single-GPU workload, the ellipsoid
+of semi-axes (1.0, 0.7, 0.5) meshed by 98304 flat triangles (circle contour centre 9.0,
+radius 1.5, N = 64 trapezoid nodes; Ritz basis of 256 complex Gaussian columns; near
+panel pairs by the 8 x 8 rule):
   geometry set-up -> contour nodes, weights and self terms -> CholeskyQR2 of the basis ->
-  fused assembly + projection Bhat_j = w_j V^H A(z_j) V for all 32 nodes.
-The metric counts n^2 N matrix entries assembled and projected per step.
+  fused assembly + projection Bhat_j = w_j V^H A(z_j) V for all 64 nodes.
+The metric counts n^2 N matrix entries assembled and projected per step. The accuracy
+qualifier (untimed) solves the eigenproblem from the same basis (Algorithm 1, CholeskyQR2,
+mixed projection, reduced solve, refinement) and reports every eigenpair inside the
+contour with its FP64 residual; where the oracle's eigenvalues are stored (tests/golden)
+it also compares against them.
 
-``--workload`` selects another of the synthetic workloads for a separate line (the
-default line is the unit cube): ``sphere20480`` (icosphere level 5, circle centre 7 radius
-1, N = 32, nu = 128; ``--near`` 0/1/2 selects no near-field treatment, the 8 x 8 rule, or
-the surrogate network, trained beforehand, untimed), ``ellipsoid98304`` (98304 triangles,
-circle centre 9 radius 1.5, N = 64, nu = 256) and ``batch48`` (48 ellipsoids of uneven size
-through the grouped persistent launch replayed as a CUDA graph; a step is one replay).
+``--workload`` selects another of the synthetic workloads for a separate line:
+``cube3072`` (unit cube, 16 x 16 squares per face, ellipse centre 6.5 semi-axes 1.5 and
+0.4, N = 32, nu = 64), ``sphere20480`` (icosphere level 5, circle centre 7 radius 1,
+N = 32, nu = 128; ``--near`` 0/1/2 selects no near-field treatment, the 8 x 8 rule, or the
+surrogate network, trained beforehand, untimed), ``batch48`` (48 ellipsoids of uneven size
+through the grouped persistent launch replayed as a CUDA graph; a step is one replay) and
+``ellipsoid24576`` (the level-5 mesh of the default ellipsoid, N = 16: a small case of the
+same kernel shape for profiler captures).
 
 Ranks (torchrun) run independent replicas of the step (the path has no exchange step) and
 the reported value is the sum over ranks (weak scaling). ``--impl reference`` times the
@@ -34,14 +41,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = "BEM entries assembled+projected/s at eig rel err ≤1e-8; % of roofline"
 UNIT = "entries/s"
-WORKLOAD = "cube3072"
+WORKLOAD = "ellipsoid98304"
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "hmatrix"])
@@ -50,12 +57,17 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-eig-check", action="store_true")
     p.add_argument("--workload", default=WORKLOAD,
-                   choices=["cube3072", "sphere20480", "ellipsoid98304", "batch48"])
+                   choices=["cube3072", "sphere20480", "ellipsoid98304", "batch48",
+                            "ellipsoid24576"])
     p.add_argument("--near", type=int, default=None, choices=[0, 1, 2],
                    help="near-field mode (default: 1 for sphere20480 and ellipsoid98304, else 0)")
     p.add_argument("--operator", default="single", choices=["single", "neumann", "robin"],
                    help="boundary operator: single layer (default), double layer with its jump "
                         "(Neumann), or Robin 0.5 G + (1/2 I + K)")
+    p.add_argument("--sweep-eval-split", action="store_true",
+                   help="instead of the projection bench: time the fused kernel at every split "
+                        "of its sines and cosines between the MUFU unit and the FMA-pipe "
+                        "polynomials (0..4 of the 7 quadrature points), with the pipe rates")
     p.add_argument("--inverse-power", type=int, default=0, metavar="Q",
                    help="instead of the projection bench: time Q steps of Algorithm 1 on the "
                         "workload, dense (FP32 LU of S) against matrix-free (GMRES)")
@@ -411,6 +423,35 @@ def run_batch(args):
     if not args.no_cpu_baseline and world == 1:
         cpu = oracle_sample(probs[0], meshes[0], synth.complex_gaussian(meshes[0].n, probs[0].nu,
                                                                         probs[0].seed))
+    # accuracy qualifier (untimed): every problem of this rank solved from its own basis
+    # (Algorithm 1, CholeskyQR2, mixed projection, reduced solve, refinement), each
+    # eigenpair with its FP64 residual; problems with stored oracle eigenvalues compared
+    eig = None
+    if not args.no_eig_check:
+        t0 = time.perf_counter()
+        per = []
+        for k, i_prob in enumerate(mine):
+            spec = probs_all[i_prob].contour
+            r = eig_check(ctxs[k], Vd[k], bem.PREC_MIXED, spec, read_golden(f"batch48_p{i_prob}"),
+                          "mixed")
+            entry = {"problem": i_prob, "n": meshes[k].n, "N": probs_all[i_prob].N,
+                     "centre": spec.centre.real, "found": len(r.get("found", [])),
+                     "converged": r.get("converged_inside"),
+                     "relres_max_converged": r.get("relres_max_converged"),
+                     "solve_s": r.get("solve_s")}
+            if "error" in r:
+                entry["error"] = r["error"]
+            if "ok" in r:
+                entry.update({"golden_ok": r["ok"], "eig_rel_err_max": r["eig_rel_err_max"],
+                              "missing": r["missing"], "extras": r["extras"]})
+            per.append(entry)
+        conv = [p["relres_max_converged"] for p in per if p["relres_max_converged"] is not None]
+        eig = {"problems": per, "relres_max_converged": max(conv) if conv else None,
+               "with_golden": [p["problem"] for p in per if "golden_ok" in p],
+               "golden_ok": all(p.get("golden_ok", True) for p in per),
+               "total_s": time.perf_counter() - t0,
+               "pipeline": "per problem: Algorithm 1 (q=10) + CholeskyQR2 + projection (mixed) "
+                           "+ reduced solve + refinement (FP64 residuals)"}
     bi = sum(v.numel() * 16 for v in Vh)
     bo = sum(b.numel() * 16 for b in Bh)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -427,12 +468,105 @@ def run_batch(args):
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": entries * args.steps / e2e_total, "unit": UNIT,
                     "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
-            "gpu_launches": launches, "clocks": clk}
+            "gpu_launches": launches, "clocks": clk, "eig_check": eig}
     print(json.dumps(line), flush=True)
     batch.close()
     for c in ctxs:
         c.close()
     return 0
+
+
+def sustained_bf16_tflops():
+    """(peak, source): the sustained dense BF16 rate of MEASURED_PEAKS.json, else the
+    profiling recipe's fallback of 1.7 PFLOP/s."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops_sustained"]), "of measured (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 1700.0, "of fallback (1.7 PFLOP/s sustained)"
+
+
+def plain_fp64_speedup(bem, ctx, args, prob, mesh, V_res, V_work, B_dev, flush, stream, mixed_rate):
+    """The plain FP64 GPU path, for the speedup of the mixed form. Its cost per entry (the
+    FP64 evaluation of the 7 points and the 8 nu flops of the contraction) does not depend
+    on n; up to n = 20000 it is timed on the workload itself, above that on the workload's
+    contour and basis width with the mesh one level coarser cut to 4 nodes (the full FP64
+    projection at n = 98304 takes about an hour), beside the mixed path on the same sample."""
+    import torch
+    c = prob.contour
+    n, N, nu = mesh.n, prob.N, prob.nu
+
+    def timed(cx, Vw, Vsrc, prec, B, steps):
+        ms = []
+        for _ in range(steps):
+            flush.fill_(0.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            Vw.copy_(Vsrc, non_blocking=True)
+            cx.cholqr2(Vw, want_R=False)
+            cx.project(Vw, prec, Bhat=B)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.mean(ms)
+
+    if n <= 20000:
+        ms = timed(ctx, V_work, V_res, bem.PREC_FP64, B_dev, args.plain_steps)
+        return {"value": n * n * N / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                "steps": args.plain_steps, "speedup_of_mixed": mixed_rate / (n * n * N / (ms * 1e-3)),
+                "sample": "the workload itself"}
+    import synth
+    coarse = {"ellipsoid98304": lambda: synth.tetrakis_sphere(4, (1.0, 0.7, 0.5)),
+              "sphere20480": lambda: synth.icosphere(4)}[args.workload]()
+    Ns = min(4, N)
+    sc = bem.Context(torch.cuda.current_device())
+    sc.set_mesh(coarse.xyz, coarse.tri)
+    sc.set_contour(c.kind, c.centre, c.a, c.b, Ns)
+    Vs = bem.fortran(torch.from_numpy(synth.complex_gaussian(coarse.n, nu, prob.seed)).to(V_res.device))
+    Vw = bem.fortran(torch.empty_like(Vs))
+    Bs = torch.empty((Ns, nu, nu), dtype=torch.complex128, device=V_res.device)
+    timed(sc, Vw, Vs, bem.PREC_FP64, Bs, 1)
+    ms64 = timed(sc, Vw, Vs, bem.PREC_FP64, Bs, args.plain_steps)
+    timed(sc, Vw, Vs, bem.PREC_MIXED, Bs, 1)
+    msmx = timed(sc, Vw, Vs, bem.PREC_MIXED, Bs, max(2, args.plain_steps))
+    sc.close()
+    ent = float(coarse.n) ** 2 * Ns
+    rate64 = ent / (ms64 * 1e-3)
+    return {"value": rate64, "unit": UNIT, "ms_per_step": ms64, "steps": args.plain_steps,
+            "speedup_of_mixed": mixed_rate / rate64,
+            "speedup_of_mixed_same_sample": ms64 / msmx,
+            "sample": f"{coarse.name} (n = {coarse.n}), the workload's contour, {Ns} of its "
+                      f"{N} nodes, nu = {nu}: FP64 and mixed steps timed on it; "
+                      "speedup_of_mixed = the full-size mixed rate over this FP64 rate"}
+
+
+def eig_check(ctx, V_res, prec, spec, gold, precision):
+    """Solves from V_res and reports every eigenpair inside the contour with its FP64
+    residual, and, with a stored oracle list, the per-eigenvalue errors (eig_compare). A
+    failure of the solve is reported in the line, not raised."""
+    import torch
+    t0 = time.perf_counter()
+    try:
+        lam, X, rel = ctx.solve(V_res, q=10, precision=prec, tol=1e-14)
+        torch.cuda.synchronize()
+    except Exception as exc:   # the bench line still prints
+        return {"error": str(exc), "solve_s": time.perf_counter() - t0}
+    t_solve = time.perf_counter() - t0
+    conv = [k for k in range(len(lam)) if rel[k] <= 1e-8]
+    out = {"found": [[l.real, l.imag] for l in lam], "relres": [float(r) for r in rel],
+           "converged_inside": len(conv), "relres_max_converged":
+               max((float(rel[k]) for k in conv), default=None),
+           "solve_s": t_solve,
+           "pipeline": "Algorithm 1 (q=10) + CholeskyQR2 + projection (" + precision +
+                       ") + reduced solve + refinement (double-FP32 iterations, FP64 residuals)"}
+    if gold is not None:
+        out.update(eig_compare(lam, X.cpu().numpy(), rel, gold, spec, tol=1e-8))
+    else:
+        out["oracle"] = ("no stored oracle eigenvalues for this mesh (the CPU oracle's dense "
+                         "FP64 solve is out of reach at this n); each pair is certified by "
+                         "its FP64 residual ||A(lambda) x|| / ||x||")
+    return out
 
 
 def run_ours(args):
@@ -600,42 +734,27 @@ def run_ours(args):
     roof["kernel_ms"] = kern_avg if kern_ms else None
     roof["launches_timed"] = len(kern_ms)
 
-    plain = None
-    if prec != bem.PREC_FP64 and args.plain_steps > 0 and args.workload == "cube3072":
-        # the plain FP64 GPU path on the same workload, for the speedup of the mixed form
-        ms = []
-        for _ in range(args.plain_steps):
-            flush.fill_(0.0)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            ctx.set_mesh(mesh.xyz, mesh.tri)
-            ctx.set_contour(c.kind, c.centre, c.a, c.b, N)
-            V_work.copy_(V_res, non_blocking=True)
-            ctx.cholqr2(V_work, want_R=False)
-            ctx.project(V_work, bem.PREC_FP64, Bhat=B_dev)
-            b.record(stream)
-            torch.cuda.synchronize()
-            ms.append(a.elapsed_time(b))
-        plain = {"value": entries / (statistics.mean(ms) * 1e-3), "unit": UNIT,
-                 "ms_per_step": statistics.mean(ms), "steps": len(ms),
-                 "speedup_of_mixed": statistics.mean(ms) / (1e3 * t_total / args.steps)}
+    if prec == bem.PREC_MIXED:
+        # the tensor pipe: BF16x3 complex contraction, 6 BF16 MMAs of 2 x (2 C) columns per
+        # node and 16 K -> 24 nu real flops per entry and node (physical work)
+        tflops = 24.0 * nu * entries / (kern_avg * 1e-3) / 1e12
+        tpeak, tsrc = sustained_bf16_tflops()
+        roof["tensor"] = {"achieved_tflops": tflops, "peak_tflops": tpeak,
+                          "frac": tflops / tpeak, "peak_source": "sustained dense BF16 " + tsrc}
 
-    # accuracy qualifier of the metric: the eigenvalues inside the contour from this
-    # projection (Algorithm 1 basis, reduced solve, FP64 refinement), untimed, against the
-    # oracle's discrete eigenvalues stored under tests/golden
+    plain = None
+    if prec != bem.PREC_FP64 and args.plain_steps > 0:
+        plain = plain_fp64_speedup(bem, ctx, args, prob, mesh, V_res, V_work, B_dev, flush,
+                                   stream, entries / (t_total / args.steps))
+
+    # accuracy qualifier of the metric (untimed): the eigenpairs inside the contour from
+    # this basis (Algorithm 1 basis, CholeskyQR2, projection in the bench's precision,
+    # reduced solve, refinement), each with its FP64 residual; against the oracle's discrete
+    # eigenvalues where tests/golden stores them
     eig = None
-    gold = read_golden(args.workload + ("_near" if near_mode else ""))
-    if not args.no_eig_check and gold is not None and args.operator == "single" and \
-            args.precision != "hmatrix":
-        t0 = time.perf_counter()
-        lam, X, rel = ctx.solve(V_res, q=10, precision=prec, tol=1e-14)
-        torch.cuda.synchronize()
-        t_solve = time.perf_counter() - t0
-        eig = eig_compare(lam, X.cpu().numpy(), rel, gold, c, tol=1e-8)
-        eig.update({"found": [[l.real, l.imag] for l in lam],
-                    "relres": [float(r) for r in rel], "solve_s": t_solve,
-                    "pipeline": "Algorithm 1 (q=10) + CholeskyQR2 + projection (" +
-                                args.precision + ") + reduced solve + FP64 refinement"})
+    if not args.no_eig_check and args.operator == "single" and args.precision != "hmatrix":
+        eig = eig_check(ctx, V_res, prec, c, read_golden(args.workload + ("_near" if near_mode else "")),
+                        args.precision)
 
     cpu = None
     if not args.no_cpu_baseline and world == 1 and args.operator == "single":
@@ -723,8 +842,50 @@ def run_inverse_power(args):
     return 0
 
 
+def run_sweep_eval_split(args):
+    """The fused kernel's time at each split of e^{i phi} between the MUFU sin/cos and the
+    FMA-pipe polynomials (bem_set_eval_split 0..4), near field off, mixed precision; the
+    measured pipe rates beside it. One JSON line."""
+    import torch
+    import paper_1906_03938_gb300 as bem
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    prob, mesh, V = problem(args.workload)
+    c = prob.contour
+    ctx = bem.Context(local)
+    ctx.set_mesh(mesh.xyz, mesh.tri)
+    ctx.set_contour(c.kind, c.centre, c.a, c.b, prob.N)
+    Vd = bem.fortran(torch.from_numpy(V).to(torch.device("cuda", local)))
+    B = torch.empty((prob.N, prob.nu, prob.nu), dtype=torch.complex128, device=Vd.device)
+    out = {"metric": "fused kernel time by eval split", "workload": args.workload, "n": mesh.n,
+           "N": prob.N, "nu": prob.nu, "rates": {k: ctx.microbench(k) for k in (
+               "fp32_fma", "fp32x2_fma", "ex2", "sin", "cos", "rsqrt", "sincos_poly")},
+           "split": {}}
+    for npoly in range(5):
+        ctx.set_eval_split(npoly)
+        for _ in range(max(1, args.warmup)):
+            ctx.project(Vd, bem.PREC_MIXED, Bhat=B)
+        torch.cuda.synchronize()
+        ctx.set_timing(True)
+        for _ in range(args.steps):
+            ctx.project(Vd, bem.PREC_MIXED, Bhat=B)
+        torch.cuda.synchronize()
+        kt = list(ctx.kernel_times())
+        ctx.set_timing(False)
+        ms = statistics.mean(kt)
+        out["split"][npoly] = {"kernel_ms": ms, "entries_per_s": mesh.n ** 2 * prob.N / (ms * 1e-3)}
+    ctx.check()
+    ctx.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.sweep_eval_split:
+        return run_sweep_eval_split(args)
     if args.inverse_power > 0:
         return run_inverse_power(args)
     if args.impl == "reference":

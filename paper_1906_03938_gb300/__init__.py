@@ -56,6 +56,7 @@ SIGNATURES = {
     "bem_inverse_power_mf": (_I, [_P, _P, _I64, _I, _I, _D, _D, _D, _I, ctypes.POINTER(_I), _P]),
     "bem_cholqr2": (_I, [_P, _P, _I64, _I64, _I, _P, _P]),
     "bem_residual": (_I, [_P, _I, _P, _P, _I64, _P, _P, _P]),
+    "bem_residual_arith": (_I, [_P, _I, _P, _P, _I64, _P, _P, _P, _I, _P]),
     "bem_kernel_launches": (_I64, [_P]),
     "bem_check": (_I, [_P, _P]),
     "bem_solve_reduced": (_I, [_P, _P, _I, _D, _D, _I, _I, _D, _P, _P, _P,
@@ -583,6 +584,21 @@ class Context:
             self._h, m, _ptr(lam.view(np.float64)), _ptr(X), X.stride(1), _ptr(R), _ptr(rel),
             _stream(stream)))
         return (rel, R.transpose(0, 1)) if want_R else rel
+
+    def residual_arith(self, lam, X, arith=1, deriv=False, stream=None):
+        """(relres, R, Rd): residuals of the columns of X at lam in FP64 (arith 0) or
+        double-FP32 (arith 1), R = A(lam) x and, with deriv, Rd = A'(lam) x."""
+        import torch
+        _check_fortran(X, "X")
+        n, m = X.shape
+        lam = np.ascontiguousarray(np.asarray(lam, dtype=np.complex128).reshape(m))
+        rel = np.zeros(m)
+        R = torch.empty((m, n), dtype=torch.complex128, device=X.device)
+        Rd = torch.empty((m, n), dtype=torch.complex128, device=X.device) if deriv else None
+        self._chk("bem_residual_arith", self._lib.bem_residual_arith(
+            self._h, m, _ptr(lam.view(np.float64)), _ptr(X), X.stride(1), _ptr(R), _ptr(Rd), _ptr(rel),
+            int(arith), _stream(stream)))
+        return rel, R.transpose(0, 1), (Rd.transpose(0, 1) if deriv else None)
 
 
 def _batch_arrays(ctxs, Vs, Bhats):

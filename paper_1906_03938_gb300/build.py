@@ -52,7 +52,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+        run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcublas"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -212,6 +212,10 @@ void bem_destroy(bem_ctx* ctx) {
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_scratch);
   cudaFree(ctx->d_small);
+  cudaFree(ctx->d_piv_val);
+  cudaFree(ctx->d_piv_idx);
+  cudaFree(ctx->d_lu_work);
+  release_cublas(ctx);
   cudaFree(ctx->d_solve);
   cudaFree(ctx->d_near_ptr);
   cudaFree(ctx->d_near_cols);

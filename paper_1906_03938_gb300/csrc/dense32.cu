@@ -6,15 +6,23 @@
 //   the matrix the residual-inverse refinement factorises; with the contour nodes and
 //   c_j = w_j / (z_j - s) it is the Schur complement S = sum_j B_j / (z_j - s) of the
 //   inverse power step (Algorithm 1, Eq. linsyssim).
-// * lu32: right-looking blocked LU with partial pivoting (panel width 32): panel
-//   factorisation in one block, row interchanges, triangular solve for the block row,
-//   complex GEMM update of the trailing matrix. lu32_solve applies it to a block of
-//   right-hand sides. FP32 is enough here: both users only need an approximate inverse
+// * lu32: right-looking blocked LU with partial pivoting in two levels. Panels of 256
+//   columns are factorised 32 columns at a time: each column's pivot is searched by all
+//   blocks (partial maxima, then one block picks the row, swaps it in and publishes it),
+//   the multipliers and the rank-1 update of the 32-column sub-panel run over all rows;
+//   the rest of the 256-column panel gets the sub-panel's interchanges, a triangular solve
+//   and a CUDA-core complex GEMM (k = 32). Then the panel's interchanges go to the other
+//   columns, U12 = L11^{-1} A12 is solved in 32-row blocks and the trailing matrix is
+//   updated with k = 256 by cuBLAS (a plain complex FP32 GEMM, FP32 emulated on the
+//   tensor cores where the library offers it). lu32_solve applies the factors to a block
+//   of right-hand sides. FP32 is enough here: both users only need an approximate inverse
 //   (the refinement's fixed point is defined by FP64 residuals).
+#include <cublas_v2.h>
 #include <cuda_bf16.h>
 #include <math.h>
 
 #include <algorithm>
+#include <climits>
 #include <vector>
 
 #include "internal.h"
@@ -122,68 +130,106 @@ __device__ __forceinline__ float2 cdivf(float2 a, float2 b) {
   return make_float2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
 
-constexpr int kNB = 32;   // panel width
+constexpr int kNB = 32;       // sub-panel width (and block size of the triangular solves)
+constexpr int kPanel = 256;   // panel width of the trailing updates
+constexpr int kPivBlock = 256;
+constexpr int kPivParts = 1024;   // most blocks of a pivot search
 
-// Factor the panel A[k0:n, k0:k0+kb] in place (one block, 1024 threads).
-__global__ void __launch_bounds__(1024)
-lu_panel_kernel(float2* A, int64_t n, int64_t k0, int kb, int* ipiv, int* status) {
-  __shared__ float bval[32];
-  __shared__ int bidx[32];
-  __shared__ int piv;
-  __shared__ float2 prow[kNB];
-  const int tid = threadIdx.x, lane = tid % 32, w = tid / 32;
-  for (int c = 0; c < kb; ++c) {
-    const int64_t col = k0 + c;
-    float bv = -1.f;
-    int64_t bi = col;
-    for (int64_t r = col + tid; r < n; r += blockDim.x) {
-      const float2 v = A[col * n + r];
-      const float a = fabsf(v.x) + fabsf(v.y);
-      if (a > bv) { bv = a; bi = r; }
-    }
-    int bii = (int)bi;
-    for (int off = 16; off > 0; off >>= 1) {
-      const float ov = __shfl_down_sync(0xffffffffu, bv, off);
-      const int oi = __shfl_down_sync(0xffffffffu, bii, off);
-      if (ov > bv || (ov == bv && oi < bii)) { bv = ov; bii = oi; }
-    }
-    if (lane == 0) { bval[w] = bv; bidx[w] = bii; }
-    __syncthreads();
-    if (tid == 0) {
-      float b = -1.f;
-      int bj = (int)col;
-      for (int q = 0; q < (int)(blockDim.x / 32); ++q)
-        if (bval[q] > b || (bval[q] == b && bidx[q] < bj)) { b = bval[q]; bj = bidx[q]; }
-      piv = bj;
-      ipiv[col] = bj;
-      if (!(b > 0.f)) atomicOr(status, kStatusNotSPD);
-    }
-    __syncthreads();
-    const int64_t pr = piv;
-    // swap rows col and pr inside the panel
-    if (pr != col && tid < kb) {
-      const float2 a = A[(k0 + tid) * n + col], b = A[(k0 + tid) * n + pr];
-      A[(k0 + tid) * n + col] = b;
-      A[(k0 + tid) * n + pr] = a;
-    }
-    __syncthreads();
-    if (tid < kb) prow[tid] = A[(k0 + tid) * n + col];
-    __syncthreads();
-    const float2 dinv = cdivf(make_float2(1.f, 0.f), prow[c]);
-    // multipliers and the rank-1 update of the rest of the panel
-    for (int64_t r = col + 1 + tid; r < n; r += blockDim.x) {
-      const float2 m = cmulf(A[col * n + r], dinv);
-      A[col * n + r] = m;
-      for (int j = c + 1; j < kb; ++j) {
-        const float2 u = prow[j];
-        float2 v = A[(k0 + j) * n + r];
-        v.x -= m.x * u.x - m.y * u.y;
-        v.y -= m.x * u.y + m.y * u.x;
-        A[(k0 + j) * n + r] = v;
-      }
-    }
-    __syncthreads();
+// Blocks of a pivot search over rows [r0, n): one per 256 rows, at most kPivParts.
+inline int piv_parts(int64_t rows) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(kPivParts, (rows + kPivBlock - 1) / kPivBlock));
+}
+
+__device__ __forceinline__ void piv_better(float& bv, int& bi, float v, int i) {
+  if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+}
+
+// block-wide arg-max (largest |re| + |im|, smallest row on ties) -> partials[blockIdx.x]
+__device__ __forceinline__ void piv_block_reduce(float bv, int bi, float* pval, int* pidx) {
+  __shared__ float sv[kPivBlock / 32];
+  __shared__ int si[kPivBlock / 32];
+  for (int off = 16; off > 0; off >>= 1) {
+    const float ov = __shfl_down_sync(0xffffffffu, bv, off);
+    const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+    piv_better(bv, bi, ov, oi);
   }
+  const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (lane == 0) { sv[w] = bv; si[w] = bi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float b = sv[0];
+    int j = si[0];
+    for (int q = 1; q < kPivBlock / 32; ++q) piv_better(b, j, sv[q], si[q]);
+    pval[blockIdx.x] = b;
+    pidx[blockIdx.x] = j;
+  }
+}
+
+// partial maxima of column col over rows [col, n) (the first column of a sub-panel)
+__global__ void __launch_bounds__(kPivBlock)
+lu_colmax_kernel(const float2* __restrict__ A, int64_t n, int64_t col, float* pval, int* pidx) {
+  float bv = -1.f;
+  int bi = INT_MAX;
+  for (int64_t r = col + blockIdx.x * (int64_t)kPivBlock + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * kPivBlock) {
+    const float2 v = A[col * n + r];
+    piv_better(bv, bi, fabsf(v.x) + fabsf(v.y), (int)r);
+  }
+  piv_block_reduce(bv, bi, pval, pidx);
+}
+
+// One block: the pivot row p of column col from the partial maxima; ipiv[col] = p; rows col
+// and p exchanged in the sub-panel's columns [j0, jend).
+__global__ void __launch_bounds__(32)
+lu_pivot_kernel(float2* A, int64_t n, int64_t col, int64_t j0, int64_t jend,
+                const float* __restrict__ pval, const int* __restrict__ pidx, int parts,
+                int* ipiv, int* status) {
+  float bv = -1.f;
+  int bi = INT_MAX;
+  for (int q = threadIdx.x; q < parts; q += 32) piv_better(bv, bi, pval[q], pidx[q]);
+  for (int off = 16; off > 0; off >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+    piv_better(bv, bi, ov, oi);
+  }
+  const int64_t p = (bi == INT_MAX) ? col : bi;
+  if (threadIdx.x == 0) {
+    ipiv[col] = (int)p;
+    if (!(bv > 0.f)) atomicOr(status, kStatusNotSPD);   // exactly singular column
+  }
+  if (p != col)
+    for (int64_t c = j0 + threadIdx.x; c < jend; c += 32) {
+      const float2 a = A[c * n + col], b = A[c * n + p];
+      A[c * n + col] = b;
+      A[c * n + p] = a;
+    }
+}
+
+// Rows r > col: multiplier l = A[r, col] / A[col, col] stored in place, columns (col, jend)
+// updated by -l * A[col, c]; then the partial maxima of the updated column col + 1.
+__global__ void __launch_bounds__(kPivBlock)
+lu_colupdate_kernel(float2* A, int64_t n, int64_t col, int64_t jend, float* pval, int* pidx) {
+  __shared__ float2 prow[kNB];
+  const int w = (int)(jend - col);   // columns col .. jend-1 of the pivot row
+  if (threadIdx.x < w) prow[threadIdx.x] = A[(col + threadIdx.x) * n + col];
+  __syncthreads();
+  const float2 dinv = cdivf(make_float2(1.f, 0.f), prow[0]);
+  float bv = -1.f;
+  int bi = INT_MAX;
+  for (int64_t r = col + 1 + blockIdx.x * (int64_t)kPivBlock + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * kPivBlock) {
+    const float2 m = cmulf(A[col * n + r], dinv);
+    A[col * n + r] = m;
+    for (int j = 1; j < w; ++j) {
+      const float2 u = prow[j];
+      float2 v = A[(col + j) * n + r];
+      v.x -= m.x * u.x - m.y * u.y;
+      v.y -= m.x * u.y + m.y * u.x;
+      A[(col + j) * n + r] = v;
+      if (j == 1) piv_better(bv, bi, fabsf(v.x) + fabsf(v.y), (int)r);
+    }
+  }
+  if (w > 1) piv_block_reduce(bv, bi, pval, pidx);
 }
 
 // Apply the interchanges ipiv[k0 .. k0+kb) to the columns outside [k0, k0+kb) (one thread
@@ -291,6 +337,37 @@ cgemm_sub_kernel(int64_t m, int64_t n, int k, const float2* __restrict__ A, int6
   }
 }
 
+// Real representation of the complex panel L (m x k, column-major, leading dimension ld):
+// Ah (2m x 2k, leading dimension 2m) with rows (2i, 2i+1) = (Re, Im) of row i and columns
+// [Re L | -Im L] over [Im L | Re L], so that Ah [Re B; Im B] gives the interleaved
+// (Re, Im) rows of L B.
+__global__ void lu_real_rep_kernel(const float2* __restrict__ L, int64_t ld, int64_t m, int k,
+                                   float* __restrict__ Ah) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= m * k) return;
+  const int64_t i = t % m;
+  const int l = (int)(t / m);
+  const float2 v = L[(int64_t)l * ld + i];
+  const int64_t m2 = 2 * m;
+  Ah[(int64_t)l * m2 + 2 * i] = v.x;
+  Ah[(int64_t)l * m2 + 2 * i + 1] = v.y;
+  Ah[(int64_t)(k + l) * m2 + 2 * i] = -v.y;
+  Ah[(int64_t)(k + l) * m2 + 2 * i + 1] = v.x;
+}
+
+// Planar copy of the complex block U (k x nc, leading dimension ld): Bp (2k x nc, leading
+// dimension 2k) = [Re U; Im U].
+__global__ void lu_planar_kernel(const float2* __restrict__ U, int64_t ld, int k, int64_t nc,
+                                 float* __restrict__ Bp) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)k * nc) return;
+  const int l = (int)(t % k);
+  const int64_t j = t / k;
+  const float2 v = U[j * ld + l];
+  Bp[j * 2 * k + l] = v.x;
+  Bp[j * 2 * k + k + l] = v.y;
+}
+
 }  // namespace
 
 bem_status assemble32(bem_ctx* ctx, int nk, const double* kz_host, const double* coef_host,
@@ -322,21 +399,135 @@ bem_status assemble32(bem_ctx* ctx, int nk, const double* kz_host, const double*
   return cuda_check(ctx, cudaGetLastError(), "assemble32 kernel");
 }
 
+void release_cublas(bem_ctx* ctx) {
+  if (ctx->cublas) cublasDestroy(static_cast<cublasHandle_t>(ctx->cublas));
+  ctx->cublas = nullptr;
+}
+
+namespace {
+
+// C[m x nc] -= A[m x k] B[k x nc] (complex FP32, column-major) by cuBLAS on stream s: the
+// complex product as one real GEMM of the real representation of A (2m x 2k) with the
+// planar [Re B; Im B] (2k x nc) into the interleaved rows of C (2m x nc, leading dimension
+// 2 ldc), the same 8 flops per complex multiply-add, FP32 products emulated on the tensor
+// cores by BF16x9 (FP32 accuracy); the plain FP32 GEMM where the library lacks the
+// emulation. work: (2m + nc) 2k floats.
+bem_status cublas_update(bem_ctx* ctx, int64_t m, int64_t nc, int k, const float2* A,
+                         int64_t lda, const float2* B, int64_t ldb, float2* C, int64_t ldc,
+                         float* work, cudaStream_t s) {
+  if (!ctx->cublas) {
+    cublasHandle_t h = nullptr;
+    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS)
+      return fail(ctx, BEM_ECUDA, "lu32: cublasCreate failed");
+    cublasSetEmulationStrategy(h, CUBLAS_EMULATION_STRATEGY_EAGER);
+    ctx->cublas = h;
+  }
+  cublasHandle_t h = static_cast<cublasHandle_t>(ctx->cublas);
+  if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS)
+    return fail(ctx, BEM_ECUDA, "lu32: cublasSetStream failed");
+  float* Ah = work;
+  float* Bp = work + 4 * m * (int64_t)k;
+  lu_real_rep_kernel<<<(unsigned)((m * k + 255) / 256), 256, 0, s>>>(A, lda, m, k, Ah);
+  lu_planar_kernel<<<(unsigned)((k * nc + 255) / 256), 256, 0, s>>>(B, ldb, k, nc, Bp);
+  ctx->launches += 2;
+  const float alpha = -1.f, beta = 1.f;
+  cublasStatus_t cs = cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)(2 * m), (int)nc, 2 * k,
+                                   &alpha, Ah, CUDA_R_32F, (int)(2 * m), Bp, CUDA_R_32F, 2 * k,
+                                   &beta, reinterpret_cast<float*>(C), CUDA_R_32F,
+                                   (int)(2 * ldc), CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
+                                   CUBLAS_GEMM_DEFAULT);
+  if (cs == CUBLAS_STATUS_NOT_SUPPORTED || cs == CUBLAS_STATUS_INVALID_VALUE)
+    cs = cublasSgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)(2 * m), (int)nc, 2 * k, &alpha, Ah,
+                     (int)(2 * m), Bp, 2 * k, &beta, reinterpret_cast<float*>(C), (int)(2 * ldc));
+  if (cs != CUBLAS_STATUS_SUCCESS)
+    return fail(ctx, BEM_ECUDA, "lu32: GEMM failed (cuBLAS status " + std::to_string((int)cs) + ")");
+  return BEM_OK;
+}
+
+}  // namespace
+
 bem_status lu32(bem_ctx* ctx, float2* A, int64_t n, int* ipiv, cudaStream_t s) {
-  for (int64_t k0 = 0; k0 < n; k0 += kNB) {
-    const int kb = (int)std::min<int64_t>(kNB, n - k0);
-    lu_panel_kernel<<<1, 1024, 0, s>>>(A, n, k0, kb, ipiv, ctx->d_status);
-    lu_swap_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A, n, n, k0, kb, ipiv, k0, k0 + kb);
-    ctx->launches += 2;
-    const int64_t rest = n - k0 - kb;
+  if (!ctx->d_piv_val) {
+    if (cudaMalloc(&ctx->d_piv_val, kPivParts * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_piv_idx, kPivParts * sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, BEM_ENOMEM, "lu32: pivot workspace allocation failed");
+    }
+  }
+  float* pval = ctx->d_piv_val;
+  int* pidx = ctx->d_piv_idx;
+  // GEMM operands in real form: (2 n + n) 2 kPanel floats at most
+  const size_t lu_work = (size_t)3 * n * 2 * kPanel * sizeof(float);
+  if (lu_work > ctx->lu_work_bytes) {
+    cudaFree(ctx->d_lu_work);
+    ctx->d_lu_work = nullptr;
+    ctx->lu_work_bytes = 0;
+    if (cudaMalloc(&ctx->d_lu_work, lu_work) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, BEM_ENOMEM, "lu32: GEMM workspace allocation failed");
+    }
+    ctx->lu_work_bytes = lu_work;
+  }
+  for (int64_t K0 = 0; K0 < n; K0 += kPanel) {
+    const int kb = (int)std::min<int64_t>(kPanel, n - K0);
+    for (int64_t J0 = K0; J0 < K0 + kb; J0 += kNB) {
+      const int jb = (int)std::min<int64_t>(kNB, K0 + kb - J0);
+      const int64_t jend = J0 + jb;
+      // the sub-panel A[J0:n, J0:jend), one column at a time
+      int parts = piv_parts(n - J0);
+      lu_colmax_kernel<<<parts, kPivBlock, 0, s>>>(A, n, J0, pval, pidx);
+      ctx->launches++;
+      for (int64_t col = J0; col < jend; ++col) {
+        lu_pivot_kernel<<<1, 32, 0, s>>>(A, n, col, J0, jend, pval, pidx, parts, ipiv,
+                                          ctx->d_status);
+        const int next = piv_parts(n - col - 1);
+        lu_colupdate_kernel<<<next, kPivBlock, 0, s>>>(A, n, col, jend, pval, pidx);
+        parts = next;
+        ctx->launches += 2;
+      }
+      // the rest of the panel: interchanges, block row, update (k = 32)
+      if (kb > jb)
+        lu_swap_kernel<<<(unsigned)((kb + 127) / 128), 128, 0, s>>>(A + K0 * n, n, kb, J0, jb, ipiv,
+                                                                  J0 - K0, jend - K0);
+      const int64_t rin = K0 + kb - jend;
+      if (rin > 0) {
+        lu_trsm_lower_kernel<<<(unsigned)((rin + 127) / 128), 128, 0, s>>>(A, n, J0, jb,
+                                                                           A + jend * n, n, rin);
+        const int64_t below = n - jend;
+        if (below > 0) {
+          dim3 grid((unsigned)((below + kGB - 1) / kGB), (unsigned)((rin + kGB - 1) / kGB));
+          cgemm_sub_kernel<<<grid, 256, 0, s>>>(below, rin, jb, A + J0 * n + jend, n,
+                                                 A + jend * n + J0, n, A + jend * n + jend, n);
+        }
+        ctx->launches += 2;
+      }
+      if (kb > jb) ctx->launches++;
+    }
+    // the panel's interchanges in every other column
+    lu_swap_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A, n, n, K0, kb, ipiv, K0, K0 + kb);
+    ctx->launches++;
+    const int64_t rest = n - K0 - kb;
     if (rest > 0) {
-      lu_trsm_lower_kernel<<<(unsigned)((rest + 127) / 128), 128, 0, s>>>(
-          A, n, k0, kb, A + (k0 + kb) * n, n, rest);
-      dim3 grid((unsigned)((rest + kGB - 1) / kGB), (unsigned)((rest + kGB - 1) / kGB));
-      cgemm_sub_kernel<<<grid, 256, 0, s>>>(rest, rest, kb, A + k0 * n + k0 + kb, n,
-                                             A + (k0 + kb) * n + k0, n,
-                                             A + (k0 + kb) * n + k0 + kb, n);
-      ctx->launches += 2;
+      // U12 = L11^{-1} A12, 32 rows at a time
+      for (int64_t b0 = K0; b0 < K0 + kb; b0 += kNB) {
+        const int bb = (int)std::min<int64_t>(kNB, K0 + kb - b0);
+        lu_trsm_lower_kernel<<<(unsigned)((rest + 127) / 128), 128, 0, s>>>(
+            A, n, b0, bb, A + (K0 + kb) * n, n, rest);
+        ctx->launches++;
+        const int64_t below = K0 + kb - (b0 + bb);
+        if (below > 0) {
+          dim3 grid((unsigned)((below + kGB - 1) / kGB), (unsigned)((rest + kGB - 1) / kGB));
+          cgemm_sub_kernel<<<grid, 256, 0, s>>>(below, rest, bb, A + b0 * n + b0 + bb, n,
+                                                 A + (K0 + kb) * n + b0, n,
+                                                 A + (K0 + kb) * n + b0 + bb, n);
+          ctx->launches++;
+        }
+      }
+      // trailing matrix, k = kb
+      const bem_status st = cublas_update(ctx, rest, rest, kb, A + K0 * n + K0 + kb, n,
+                                          A + (K0 + kb) * n + K0, n, A + (K0 + kb) * n + K0 + kb,
+                                          n, ctx->d_lu_work, s);
+      if (st != BEM_OK) return st;
     }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(ctx, e, "lu32");

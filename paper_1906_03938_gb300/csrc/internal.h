@@ -101,6 +101,11 @@ struct bem_ctx {
   double* d_scratch = nullptr;   // reusable FP64 workspace
   size_t scratch_bytes = 0;
   double* d_small = nullptr;     // small FP64 workspace (Gram / Cholesky / norms)
+  void* cublas = nullptr;        // cuBLAS handle of the dense LU's trailing updates (lazy)
+  float* d_piv_val = nullptr;    // LU pivot search: per-block partial maxima and their rows
+  int* d_piv_idx = nullptr;
+  float* d_lu_work = nullptr;    // the LU's trailing-update operands in real form
+  size_t lu_work_bytes = 0;
   size_t small_bytes = 0;
   int64_t launches = 0;
   int64_t mesh_version = 0;         // bumped by every successful bem_set_mesh
@@ -159,6 +164,7 @@ bem_status cuda_check(bem_ctx* ctx, cudaError_t e, const char* what);
 // Make sure the context's scratch holds at least `bytes`.
 bem_status ensure_scratch(bem_ctx* ctx, size_t bytes);
 bem_status ensure_small(bem_ctx* ctx, size_t bytes);
+void release_cublas(bem_ctx* ctx);
 // Events around the main kernel of a projection (no-ops unless timing is enabled).
 inline void timing_begin(bem_ctx* ctx, cudaStream_t s) {
   if (ctx->timing && ctx->n_timed < kMaxTimed) cudaEventRecord(ctx->ev[2 * ctx->n_timed], s);
@@ -180,6 +186,13 @@ cudaError_t launch_self32(bem_ctx* ctx, int nk, const double* kz, float* out, cu
 // R has leading dimension n. lam_dev: m complex on the device.
 cudaError_t launch_apply_percol64(bem_ctx* ctx, int m, const double* lam_dev, const double* X,
                                   int64_t ldx, double* R, bool deriv, cudaStream_t s);
+// R = A(lambda_c) x_c and, if Rd, Rd = A'(lambda_c) x_c in double-FP32 arithmetic (entries
+// to ~1e-13; single layer; the general operator uses the FP64 kernels), near field added
+cudaError_t launch_apply_ff(bem_ctx* ctx, int m, const double* lam_dev, const double* X,
+                            int64_t ldx, double* R, double* Rd, cudaStream_t s);
+// R_c[i] = the self entry of T(lambda_c) (or of its k-derivative)
+cudaError_t launch_self_at(bem_ctx* ctx, int m, const double* lam_dev, double* R, bool deriv,
+                           cudaStream_t s);
 // out[2c] = ||R[:, c]||^2, out[2c+1] = ||X[:, c]||^2 (fixed-order sums)
 cudaError_t launch_colnorms(bem_ctx* ctx, const double* R, int64_t ldr, const double* X,
                             int64_t ldx, int64_t n, int m, double* out, cudaStream_t s);

@@ -6,6 +6,7 @@
 // reduction (deterministic).
 #include <math.h>
 
+#include <string>
 #include <vector>
 
 #include "internal.h"
@@ -164,6 +165,15 @@ cudaError_t launch_apply_percol64(bem_ctx* ctx, int m, const double* lam_dev, co
   return cudaGetLastError();
 }
 
+cudaError_t launch_self_at(bem_ctx* ctx, int m, const double* lam_dev, double* R, bool deriv,
+                           cudaStream_t s) {
+  static const GL16 gl = make_gl16();
+  dim3 g1((unsigned)((ctx->geo.n + 127) / 128), (unsigned)m);
+  self_at_kernel<<<g1, 128, 0, s>>>(ctx->geo, lam_dev, gl, R, deriv, ctx->op);
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_colnorms(bem_ctx* ctx, const double* R, int64_t ldr, const double* X,
                             int64_t ldx, int64_t n, int m, double* out, cudaStream_t s) {
   (void)ldr;
@@ -176,15 +186,20 @@ cudaError_t launch_colnorms(bem_ctx* ctx, const double* R, int64_t ldr, const do
 
 using namespace bem;
 
-extern "C" bem_status bem_residual(bem_ctx* ctx, int m, const double* lam_host, const double* X_dev,
-                                   int64_t ldx, double* R_dev, double* relres_host, void* stream) {
+namespace {
+
+bem_status residual_impl(bem_ctx* ctx, int m, const double* lam_host, const double* X_dev,
+                         int64_t ldx, double* R_dev, double* Rd_dev, double* relres_host,
+                         int arith, void* stream, const char* name) {
   if (!ctx) return BEM_EINVAL;
-  if (ctx->geo.n == 0) return fail(ctx, BEM_ESTATE, "bem_residual: no mesh set");
+  if (ctx->geo.n == 0) return fail(ctx, BEM_ESTATE, std::string(name) + ": no mesh set");
   const int64_t n = ctx->geo.n;
-  if (m < 1 || m > 65535 || !lam_host || !X_dev || !relres_host || ldx < n)
-    return fail(ctx, BEM_EINVAL, "bem_residual: need 1 <= m <= 65535, lam, X, relres, ldx >= n");
+  if (m < 1 || m > 65535 || !lam_host || !X_dev || !relres_host || ldx < n ||
+      (arith != 0 && arith != 1))
+    return fail(ctx, BEM_EINVAL, std::string(name) +
+                                     ": need 1 <= m <= 65535, lam, X, relres, ldx >= n, arith 0/1");
   for (int c = 0; c < 2 * m; ++c)
-    if (!isfinite(lam_host[c])) return fail(ctx, BEM_EINVAL, "bem_residual: non-finite lambda");
+    if (!isfinite(lam_host[c])) return fail(ctx, BEM_EINVAL, std::string(name) + ": non-finite lambda");
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   bem_status st = ensure_near(ctx, s);
@@ -202,19 +217,41 @@ extern "C" bem_status bem_residual(bem_ctx* ctx, int m, const double* lam_host, 
   double* dlam = ctx->d_small;
   double* dnorm = ctx->d_small + 2 * m;
   st = cuda_check(ctx, cudaMemcpyAsync(dlam, lam_host, 2 * m * sizeof(double),
-                                       cudaMemcpyHostToDevice, s), "bem_residual copy");
+                                       cudaMemcpyHostToDevice, s), name);
   if (st != BEM_OK) return st;
-  st = cuda_check(ctx, launch_apply_percol64(ctx, m, dlam, X_dev, ldx, R, false, s),
-                  "residual kernels");
+  cudaError_t e;
+  if (arith == 1) {
+    e = launch_apply_ff(ctx, m, dlam, X_dev, ldx, R, Rd_dev, s);
+  } else {
+    e = launch_apply_percol64(ctx, m, dlam, X_dev, ldx, R, false, s);
+    if (e == cudaSuccess && Rd_dev) e = launch_apply_percol64(ctx, m, dlam, X_dev, ldx, Rd_dev, true, s);
+  }
+  st = cuda_check(ctx, e, name);
   if (st != BEM_OK) return st;
-  st = cuda_check(ctx, launch_colnorms(ctx, R, n, X_dev, ldx, n, m, dnorm, s), "residual kernels");
+  st = cuda_check(ctx, launch_colnorms(ctx, R, n, X_dev, ldx, n, m, dnorm, s), name);
   if (st != BEM_OK) return st;
   std::vector<double> h(2 * m);
   st = cuda_check(ctx, cudaMemcpyAsync(h.data(), dnorm, 2 * m * sizeof(double),
-                                       cudaMemcpyDeviceToHost, s), "bem_residual copy");
-  if (st == BEM_OK) st = cuda_check(ctx, cudaStreamSynchronize(s), "bem_residual sync");
+                                       cudaMemcpyDeviceToHost, s), name);
+  if (st == BEM_OK) st = cuda_check(ctx, cudaStreamSynchronize(s), name);
   if (st != BEM_OK) return st;
   for (int c = 0; c < m; ++c)
     relres_host[c] = h[2 * c + 1] > 0.0 ? sqrt(h[2 * c]) / sqrt(h[2 * c + 1]) : INFINITY;
   return BEM_OK;
+}
+
+}  // namespace
+
+extern "C" bem_status bem_residual(bem_ctx* ctx, int m, const double* lam_host, const double* X_dev,
+                                   int64_t ldx, double* R_dev, double* relres_host, void* stream) {
+  return residual_impl(ctx, m, lam_host, X_dev, ldx, R_dev, nullptr, relres_host, 0, stream,
+                       "bem_residual");
+}
+
+extern "C" bem_status bem_residual_arith(bem_ctx* ctx, int m, const double* lam_host,
+                                         const double* X_dev, int64_t ldx, double* R_dev,
+                                         double* Rd_dev, double* relres_host, int arith,
+                                         void* stream) {
+  return residual_impl(ctx, m, lam_host, X_dev, ldx, R_dev, Rd_dev, relres_host, arith, stream,
+                       "bem_residual_arith");
 }

@@ -14,6 +14,10 @@ conditions, Section 4) at the sizes this project measures:
 5. ``ellipsoid98304``: tetrakis sphere level 6 scaled to semi-axes (1.0, 0.7, 0.5); circle
    centre 9.0 radius 1.5, N = 64, nu = 256.
 
+``ellipsoid24576`` (level 5 of the same ellipsoid, same contour, N = 16, nu = 256) is the
+small case of workload 5's kernel shape (one node per work unit, 256 basis columns), sized
+for profiler captures.
+
 A contour is described by data only (kind, centre, semi-axes); its nodes and weights are
 computed by each side on its own. Seeds: problem p of a workload uses 20190609 + p.
 """
@@ -88,6 +92,10 @@ def _make():
                                    [Problem(lambda: tetrakis_sphere(6, (1.0, 0.7, 0.5)),
                                             _circle(9.0, 1.5), 64, 256, BASE_SEED,
                                             "tetrakis_L6")]),
+        "ellipsoid24576": Workload("ellipsoid24576",
+                                   [Problem(lambda: tetrakis_sphere(5, (1.0, 0.7, 0.5)),
+                                            _circle(9.0, 1.5), 16, 256, BASE_SEED,
+                                            "tetrakis_L5")]),
     }
 
 

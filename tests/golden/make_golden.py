@@ -12,9 +12,11 @@ paper's T = A H - B G with B = 0), started from the zeros of j_1' and j_2' (2.08
 3.3421) inside the circle of centre 2.75 and radius 0.9. "sphere20480_near" is the icosphere
 of level 5 with the near-field variant inside the circle of centre 7 and radius 1, started
 from the zeros of j_0, j_3 and j_1 there (6.2832, 6.9879, 7.7253; about two hours on eight
-cores: every step factorises the dense n = 20480 matrix). Usage:
+cores: every step factorises the dense n = 20480 matrix). "batch48_p<i>" is problem i of
+the 48-ellipsoid sweep (no closed form: started from a grid of points inside its circle).
+Usage:
 python tests/golden/make_golden.py [sphere320] [cube3072] [sphere320_near] [sphere320_neumann]
-                                   [sphere20480_near]
+                                   [sphere20480_near] [batch48_p9] [batch48_p14]
 """
 import os
 import sys
@@ -38,15 +40,28 @@ OPERATOR = {"sphere320_neumann": (0.0, 1.0)}
 CONTOUR = {"sphere320_neumann": synth.ContourSpec("circle", 2.75 + 0j, 0.9, 0.9)}
 
 
+def _batch_starts(spec):
+    """Starts for an ellipsoid of the 48-problem sweep (no closed form): the circle's
+    centre, six points at half its radius and two on the real axis at 0.85 of it."""
+    c, r = spec.centre, spec.a
+    pts = [c] + [c + 0.5 * r * np.exp(2j * np.pi * k / 6) for k in range(6)]
+    return pts + [c - 0.85 * r, c + 0.85 * r]
+
+
 def main(names):
     for name in names:
         near = name.endswith("_near")
         base = name.split("_")[0]
-        prob = synth.workload(base).problems[0]
+        if base == "batch48":   # batch48_p<i>: problem i of the sweep
+            prob = synth.workload(base).problems[int(name.split("_p")[1])]
+            starts, radius = _batch_starts(prob.contour), prob.contour.a
+        else:
+            prob = synth.workload(base).problems[0]
+            starts, radius = STARTS[name], 0.2
         mesh = prob.mesh()
         spec = CONTOUR.get(name, prob.contour)
         op = OPERATOR.get(name)
-        found = refine.discrete_eigs(mesh, STARTS[name], radius=0.2,
+        found = refine.discrete_eigs(mesh, starts, radius=radius,
                                      keep=lambda l: bool(contour.inside(l, spec, -0.05)),
                                      near=near, op=op)
         path = os.path.join(HERE, f"eigs_{name}.txt")
