@@ -84,3 +84,51 @@ def shift_invert_apply(B, sigma, Wblk):
     """(A - sigma M)^{-1} M W, the plain definition (dense solve)."""
     A, M = pencil(B)
     return np.linalg.solve(A - sigma * M, M @ Wblk)
+
+
+def cheb_at_zero(m):
+    """T_i(0), i = 0..m-1: 1, 0, -1, 0, 1, ..."""
+    return np.array([np.cos(i * np.pi / 2) for i in range(m)]).round()
+
+
+def inverse_power_step(B, W):
+    """One step of Algorithm 2 (inverse power for the Chebyshev interpolant, the shift at the
+    interval's centre, zeta = 0): w' = A^{-1} M w for the colleague pencil of ``pencil``,
+    w = [v_0; ..; v_{m-1}] (blocks of n rows, any number of columns).
+
+    Steps in the paper's order: y = M w (block diagonal: y_0 = v_0, y_r = 2 v_r,
+    y_{m-1} = 2 B_m v_{m-1}); the block rows 0..m-2 of A w' = y give the recurrence
+    v'_1 = y_0, v'_{r+1} = y_r - v'_{r-1} (Eq. reccurenceCheb_odd / _even), so that every
+    v'_i = E_i + T_i(0) u with u = v'_0 and E from the recurrence started at E_0 = 0; the
+    last block row then leaves G u = b with G = sum_i T_i(0) L_i and b = y_{m-1} - sum_i
+    L_i E_i, L_i the blocks of that row (Eq. Gmtx, Eq. bodd / beven: here derived from the
+    block row, whatever the parity of m). Returns w'."""
+    B = np.asarray(B)
+    m = B.shape[0] - 1
+    n = B.shape[1]
+    W = np.asarray(W).reshape(m, n, -1)
+    y = [W[0]] + [2 * W[r] for r in range(1, m - 1)] + [2 * B[m] @ W[m - 1]]
+    E = [np.zeros_like(W[0]), y[0]]
+    for r in range(1, m - 1):
+        E.append(y[r] - E[r - 1])
+    L = [-B[i] for i in range(m - 2)] + [B[m] - B[m - 2], -B[m - 1]]
+    s = cheb_at_zero(m)
+    G = sum(s[i] * L[i] for i in range(m))
+    b = y[m - 1] - sum(L[i] @ E[i] for i in range(m))
+    u = np.linalg.solve(G, b)
+    return np.concatenate([E[i] + s[i] * u for i in range(m)], axis=0)
+
+
+def inverse_power(B, V0, q):
+    """q steps of Algorithm 2 from the blocks v_i = T_i(0) V0 (the eigenvector form at the
+    shift), each step's columns rescaled to unit norm (direction only); returns the u-parts
+    (the y-part of the linearisation, v_0) after q steps."""
+    B = np.asarray(B)
+    m = B.shape[0] - 1
+    s = cheb_at_zero(m)
+    V0 = np.asarray(V0, dtype=np.complex128)
+    W = np.concatenate([s[i] * V0 for i in range(m)], axis=0)
+    for _ in range(q):
+        W = inverse_power_step(B, W)
+        W = W / np.linalg.norm(W, axis=0)
+    return W[:V0.shape[0]]

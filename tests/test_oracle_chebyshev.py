@@ -3,6 +3,7 @@ at the nodes and any polynomial of degree < N exactly; the colleague linearisati
 scalar Chebyshev series has the roots numpy's Chebyshev module finds, and that of a matrix
 polynomial the eigenvalues of its textbook companion pencil."""
 import numpy as np
+import pytest
 import scipy.linalg as sla
 
 from oracle import chebyshev as och
@@ -60,3 +61,32 @@ def test_shift_invert_is_inverse_of_pencil():
     sigma = 0.3 - 0.1j
     X = och.shift_invert_apply(B, sigma, W)
     assert np.max(np.abs((A - sigma * M) @ X - M @ W)) < 1e-12 * np.max(np.abs(M @ W))
+
+
+@pytest.mark.parametrize("m", [5, 6])
+def test_algorithm2_step_is_inverse_iteration_on_the_pencil(m):
+    """Algorithm 2's step (recurrence on the block rows, then G u = b) equals one step of
+    plain inverse iteration A^{-1} M w on the explicit colleague pencil, for an odd and an
+    even number of blocks (the paper prints b separately for each parity)."""
+    rng = np.random.default_rng(m)
+    n = 7
+    B = rng.normal(size=(m + 1, n, n)) + 1j * rng.normal(size=(m + 1, n, n))
+    W = rng.normal(size=(m * n, 3)) + 1j * rng.normal(size=(m * n, 3))
+    got = och.inverse_power_step(B, W)
+    ref = och.shift_invert_apply(B, 0.0, W)
+    assert np.max(np.abs(got - ref)) <= 1e-10 * np.max(np.abs(ref))
+
+
+def test_algorithm2_converges_to_eigenvector_nearest_centre():
+    """q steps of Algorithm 2 on a matrix polynomial with known eigenvalues: the u-part
+    aligns with the eigenvector of the eigenvalue nearest the interval's centre."""
+    rng = np.random.default_rng(4)
+    n = 6
+    lam = np.array([0.05, 0.6, -0.7, 1.5, -1.8, 2.2])
+    Q, _ = np.linalg.qr(rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n)))
+    # T(zeta) = Q diag(zeta - lam) Q^H: degree 1, interpolated exactly by m = 4
+    x = np.cos(np.pi * (np.arange(5) + 0.5) / 5)
+    B = och.coefficients([Q @ np.diag(xx - lam) @ Q.conj().T for xx in x])
+    U = och.inverse_power(B, rng.normal(size=(n, 1)) + 0j, 30)
+    u = U[:, 0] / np.linalg.norm(U[:, 0])
+    assert 1 - abs(np.vdot(Q[:, 0], u)) < 1e-10
