@@ -320,6 +320,22 @@ bem_status bem_inverse_power(bem_ctx* ctx, double* V_dev, int64_t ldv, int nu, i
                              double shift_re, double shift_im, void* stream);
 
 /*
+ * Basis improvement by q steps of the inverse power method for the Chebyshev interpolant
+ * (Section 3.2, Algorithm 2; Eq. reccurenceCheb_odd, Eq. reccurenceCheb_even, Eq. Gmtx,
+ * Eq. bodd / beven), for a context whose contour is of kind CHEBYSHEV (N >= 4 points x_k of
+ * the interval, degree m = N - 1), the shift at the interval's centre (zeta = 0). The
+ * iterate w = [v_0; ..; v_{m-1}] of the colleague linearisation starts from v_i = T_i(0) V;
+ * each step solves A w' = M w: the block rows 0..m-2 give the recurrence for v', the last
+ * row G u = b with G = sum_i T_i(0) L_i (L_i its blocks, combinations of
+ * B_i = sum_k c_ik A(x_k)) assembled densely in FP32 and LU-factorised once, and b from one
+ * node-summed application sum_k A(x_k) X_k of the fused kernel; the columns are rescaled.
+ * On return V (n x nu, leading dimension ldv) holds the u-part v_0 (not orthonormalised).
+ * Scratch: n^2 * 8 + (2 m + N + 1) n nu * 8 bytes. 1 <= nu <= 256. Synchronises the stream.
+ */
+bem_status bem_inverse_power_chebyshev(bem_ctx* ctx, double* V_dev, int64_t ldv, int nu, int q,
+                                       void* stream);
+
+/*
  * bem_inverse_power without forming S (the basis construction at sizes where the dense S,
  * n^2 * 8 bytes, does not fit): the same q steps, each S u' = b solved by bem_solve_sum's
  * GMRES to relative residual tol with at most max_iter Arnoldi steps. Memory: the N n nu
@@ -406,6 +422,14 @@ bem_status bem_set_wait_limit(bem_ctx* ctx, uint32_t polls);
  * the unit shape. Applies to later bem_project calls. BEM_EINVAL outside -1..4.
  */
 bem_status bem_set_eval_split(bem_ctx* ctx, int poly_points);
+/*
+ * Arithmetic of the residuals ||A(lambda) x|| / ||x|| that bem_refine and bem_solve report
+ * for their eigenpairs (Section 4's accuracy measure): 0 FP64 (default), 1 double-FP32
+ * as bem_residual_arith (entries to ~1e-13 relative; over ten times faster on this GPU,
+ * for the largest meshes, where an FP64 residual takes seconds per eigenpair). The
+ * refinement's own iterations always use double-FP32. BEM_EINVAL for other values.
+ */
+bem_status bem_set_refine_residual(bem_ctx* ctx, int arith);
 
 /* Number of CUDA kernels this context has launched since creation (diagnostics). */
 int64_t bem_kernel_launches(const bem_ctx* ctx);
@@ -605,6 +629,25 @@ void bem_batch_destroy(bem_batch* batch);
 bem_status bem_project_batched(bem_ctx* const* ctxs, int nprob, const double* const* V_dev,
                                const int64_t* ldv, const int* nu, double* const* Bhat_dev,
                                int precision, void* stream);
+
+/*
+ * Order of the Cauchy approximation (Section 4, Example 3: grow m until the rational
+ * approximation is accurate on the circle of radius r/2 inside the contour). For each N of
+ * N_list (count entries, each 2..1024) the N-node trapezoid approximation on the contour
+ * (kind circle or ellipse, centre c, semi-axes a, b; nodes and weights as bem_set_contour)
+ * T~(zeta) X = sum_j w_j T(z_j) X / (z_j - zeta) is compared with T(zeta) X at nsamples
+ * (1..64) points of the inner contour (same centre, semi-axes a/2, b/2, angles
+ * 2 pi (s + 1/4) / nsamples) for the caller's test vectors X_dev (n x ncols complex,
+ * column-major, leading dimension ldx, 1 <= ncols <= 64). err_out[k] receives the largest
+ * relative error ||T~ X - T X||_F / ||T X||_F of N_list[k]; *N_chosen the first N whose
+ * error is <= tol (or -1). T is the context's operator (near field included when set),
+ * applied matrix-free in double-FP32 arithmetic (entries to ~1e-13). Does not change the
+ * context's contour. Synchronises the stream.
+ */
+bem_status bem_select_order(bem_ctx* ctx, int kind, double c_re, double c_im, double a, double b,
+                            const int* N_list, int count, int nsamples, const double* X_dev,
+                            int64_t ldx, int ncols, double tol, int* N_chosen, double* err_out,
+                            void* stream);
 
 /*
  * Allocation-free projection (the paper has no counterpart: this serves callers that

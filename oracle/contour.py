@@ -37,3 +37,34 @@ def inside(lam, spec, margin: float = 0.0):
     x = (lam.real - spec.centre.real) / spec.a
     y = (lam.imag - spec.centre.imag) / spec.b
     return np.sqrt(x * x + y * y) < 1.0 - margin
+
+
+def inner_points(spec, nsamples: int):
+    """Sample points on the inner contour (same centre, semi-axes halved: the circle of
+    radius r/2 of Section 4, Example 3) at angles 2 pi (s + 1/4) / nsamples."""
+    b = spec.a if spec.kind == "circle" else spec.b
+    t = 2.0 * np.pi * (np.arange(nsamples) + 0.25) / nsamples
+    return complex(spec.centre) + 0.5 * spec.a * np.cos(t) + 0.5j * b * np.sin(t)
+
+
+def approximation_error(Tfun, spec, N: int, X, nsamples: int = 8):
+    """The order test of Section 4, Example 3: the largest relative error
+    ||T~(zeta) X - T(zeta) X||_F / ||T(zeta) X||_F over the sample points zeta of the inner
+    contour, T~ the N-node Cauchy approximation sum_j w_j T(z_j) / (z_j - zeta) and X a
+    block of test vectors; Tfun(z) returns the matrix T(z)."""
+    z, w = from_spec(spec, N)
+    TX = [Tfun(zj) @ X for zj in z]
+    err = 0.0
+    for zeta in inner_points(spec, nsamples):
+        approx = sum(w[j] / (z[j] - zeta) * TX[j] for j in range(N))
+        exact = Tfun(zeta) @ X
+        err = max(err, np.linalg.norm(approx - exact) / np.linalg.norm(exact))
+    return err
+
+
+def select_order(Tfun, spec, N_list, X, tol, nsamples: int = 8):
+    """The smallest N of N_list whose approximation error is <= tol (None if none), and the
+    errors of every N."""
+    errs = [approximation_error(Tfun, spec, N, X, nsamples) for N in N_list]
+    chosen = next((N for N, e in zip(N_list, errs) if e <= tol), None)
+    return chosen, errs

@@ -20,7 +20,8 @@ import numpy as np
 IN, HID, OUT = 11, 64, 2
 _SHAPES = [("in_shift", (IN,)), ("in_scale", (IN,)), ("W1", (HID, IN)), ("b1", (HID,)),
            ("W2", (HID, HID)), ("b2", (HID,)), ("W3", (HID, HID)), ("b3", (HID,)),
-           ("W4", (OUT, HID)), ("b4", (OUT,)), ("out_scale", (OUT,))]
+           ("W4", (OUT, HID)), ("b4", (OUT,)), ("out_scale", (OUT,)),
+           ("feat_lo", (IN,)), ("feat_hi", (IN,))]
 SIZE = sum(int(np.prod(s)) for _, s in _SHAPES)
 TRAINED = ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4")
 

@@ -47,6 +47,7 @@ SIGNATURES = {
     "bem_set_async": (_I, [_P, _I]),
     "bem_set_wait_limit": (_I, [_P, ctypes.c_uint32]),
     "bem_set_eval_split": (_I, [_P, _I]),
+    "bem_set_refine_residual": (_I, [_P, _I]),
     "bem_set_operator": (_I, [_P, _D, _D, _D, _D]),
     "bem_set_hmatrix": (_I, [_P, _I, _D, _D, _I]),
     "bem_hmatrix_stats": (_I, [_P, _P, _P, _P, _P, _P]),
@@ -63,6 +64,8 @@ SIGNATURES = {
                                ctypes.POINTER(_I), _P]),
     "bem_ritz_vectors": (_I, [_P, _P, _I64, _I, _P, _I, _P, _I64, _P]),
     "bem_inverse_power": (_I, [_P, _P, _I64, _I, _I, _D, _D, _P]),
+    "bem_inverse_power_chebyshev": (_I, [_P, _P, _I64, _I, _I, _P]),
+    "bem_select_order": (_I, [_P, _I, _D, _D, _D, _D, _P, _I, _I, _P, _I64, _I, _D, _P, _P, _P]),
     "bem_refine": (_I, [_P, _I, _P, _P, _I64, _D, _I, _P, _P, _P]),
     "bem_solve": (_I, [_P, _P, _I64, _I, _I, _I, _D, _I, _P, _P, _I64, ctypes.POINTER(_I),
                        _P, _P]),
@@ -402,6 +405,10 @@ class Context:
         takes from the FMA-pipe polynomials; -1: the measured default."""
         self._chk("bem_set_eval_split", self._lib.bem_set_eval_split(self._h, int(poly_points)))
 
+    def set_refine_residual(self, arith=0):
+        """Arithmetic of the residuals refine/solve report: 0 FP64, 1 double-FP32."""
+        self._chk("bem_set_refine_residual", self._lib.bem_set_refine_residual(self._h, int(arith)))
+
     def node_order(self):
         """(order, twins): the mixed kernel's node schedule (slot -> node) and the number
         of twin pairs (nodes with equal FP32 real parts) at its front."""
@@ -507,6 +514,28 @@ class Context:
         sh = complex(shift)
         self._chk("bem_inverse_power", self._lib.bem_inverse_power(
             self._h, _ptr(V), V.stride(1), nu, int(q), sh.real, sh.imag, _stream(stream)))
+
+    def select_order(self, kind, centre, a, b, N_list, X, tol, nsamples=8, stream=None):
+        """(N chosen or None, errors): the first order whose Cauchy approximation meets tol
+        on the inner contour (Section 4, Example 3), for test vectors X (n x ncols)."""
+        _check_fortran(X, "X")
+        kinds = {"circle": CONTOUR_CIRCLE, "ellipse": CONTOUR_ELLIPSE}
+        Ns = np.ascontiguousarray(N_list, dtype=np.int32)
+        err = np.zeros(len(Ns))
+        ch = _I(0)
+        c = complex(centre)
+        self._chk("bem_select_order", self._lib.bem_select_order(
+            self._h, kinds[kind], c.real, c.imag, float(a), float(b), _ptr(Ns), len(Ns),
+            int(nsamples), _ptr(X), X.stride(1), X.shape[1], float(tol), ctypes.byref(ch),
+            _ptr(err), _stream(stream)))
+        return (ch.value if ch.value > 0 else None), err
+
+    def inverse_power_chebyshev(self, V, q, stream=None):
+        """q steps of Algorithm 2 (Chebyshev contour) on every column of V (in place)."""
+        _check_fortran(V, "V")
+        n, nu = V.shape
+        self._chk("bem_inverse_power_chebyshev", self._lib.bem_inverse_power_chebyshev(
+            self._h, _ptr(V), V.stride(1), nu, int(q), _stream(stream)))
 
     def inverse_power_mf(self, V, q, shift, tol=1e-4, max_iter=400, stream=None):
         """q steps of Algorithm 1 with matrix-free GMRES solves (in place); returns the total

@@ -151,8 +151,8 @@ static bem_status stage_buffer(bem_ctx* ctx, void*& buf, size_t& cap, cudaEvent_
 // Nodes and weights of a contour, on the host (the device receives these values).
 // Circle / ellipse: theta_j = pi (2 j + 1) / N with the lower half the exact mirror of the
 // upper (theta_{N-1-j} = 2 pi - theta_j), so conjugate nodes have equal real parts.
-static void contour_nodes(int kind, double c_re, double c_im, double a, double b, int N,
-                          double* z, double* w) {
+void contour_nodes(int kind, double c_re, double c_im, double a, double b, int N, double* z,
+                   double* w) {
   const double pi = 3.14159265358979323846;
   for (int j = 0; j < N; ++j) {
     if (kind == BEM_CONTOUR_CHEBYSHEV) {
@@ -274,6 +274,13 @@ bem_status bem_set_eval_split(bem_ctx* ctx, int poly_points) {
   if (!ctx || poly_points < -1 || poly_points > 4)
     return fail(ctx, BEM_EINVAL, "bem_set_eval_split: poly_points must be -1 or 0..4");
   ctx->poly_points = poly_points;
+  return BEM_OK;
+}
+
+bem_status bem_set_refine_residual(bem_ctx* ctx, int arith) {
+  if (!ctx || (arith != 0 && arith != 1))
+    return fail(ctx, BEM_EINVAL, "bem_set_refine_residual: arith must be 0 (FP64) or 1");
+  ctx->final_residual_arith = arith;
   return BEM_OK;
 }
 

@@ -145,6 +145,8 @@ struct bem_ctx {
   // quadrature points per entry whose sine and cosine the fused kernel takes from the FMA-
   // pipe polynomials (bem_set_eval_split); -1: the measured default of the unit shape
   int poly_points = -1;
+  // arithmetic of the residuals bem_refine (and bem_solve) report: 0 FP64, 1 double-FP32
+  int final_residual_arith = 0;
   // the boundary operator T = c_G G + c_H (1/2 I + K) (single layer by default)
   bem::OpCoef op;
   int64_t op_version = 0;   // bumped by every bem_set_operator
@@ -165,6 +167,9 @@ bem_status cuda_check(bem_ctx* ctx, cudaError_t e, const char* what);
 bem_status ensure_scratch(bem_ctx* ctx, size_t bytes);
 bem_status ensure_small(bem_ctx* ctx, size_t bytes);
 void release_cublas(bem_ctx* ctx);
+// nodes z and weights w (2 N doubles each, interleaved) of a contour, on the host
+void contour_nodes(int kind, double c_re, double c_im, double a, double b, int N, double* z,
+                   double* w);
 // Events around the main kernel of a projection (no-ops unless timing is enabled).
 inline void timing_begin(bem_ctx* ctx, cudaStream_t s) {
   if (ctx->timing && ctx->n_timed < kMaxTimed) cudaEventRecord(ctx->ev[2 * ctx->n_timed], s);

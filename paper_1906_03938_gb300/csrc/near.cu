@@ -266,9 +266,12 @@ __device__ float2 near_corr32(const Geometry& g, int64_t l, const double x[3], f
   if (net) {
     float feat[kNetIn];
     near_features32(g, l, F, x, kr, ki, feat);
-    const float2 o = surrogate_eval(net, feat);
-    const float h = (float)g.diam[l];
-    return make_float2(o.x * h, o.y * h);
+    // a pair outside the network's training box takes the plain rule below
+    if (surrogate_in_box(net, feat)) {
+      const float2 o = surrogate_eval(net, feat);
+      const float h = (float)g.diam[l];
+      return make_float2(o.x * h, o.y * h);
+    }
   }
   const float ax = (float)(F.a[0] - x[0]), ay = (float)(F.a[1] - x[1]), az = (float)(F.a[2] - x[2]);
   const float abx = (float)F.ab[0], aby = (float)F.ab[1], abz = (float)F.ab[2];

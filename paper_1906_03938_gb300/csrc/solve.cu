@@ -29,6 +29,12 @@
 namespace bem {
 namespace {
 
+// refinement: factorisations of A(sigma) per eigenpair at most (the last one is kept), and
+// the relative residual at which an eigenpair is converged (a few units of the double-FP32
+// entries' rounding, 1e-13, times the growth of the sums)
+constexpr int kMaxFactorisations = 4;
+constexpr double kResidualStop = 1e-12;
+
 // Vn_j = u / (z_j - s) (u FP64 n x nu, ld ldu)
 __global__ void ip_start_kernel(const double2* __restrict__ U, int64_t ldu, int64_t n, int nu,
                                 int N, const double2* __restrict__ z, double2 s, float2* Vn) {
@@ -188,6 +194,74 @@ __global__ void dot1_kernel(const double2* __restrict__ e, const double2* __rest
   if (threadIdx.x == 0) *out = red[0];
 }
 
+// ---- Algorithm 2 (inverse power for the Chebyshev interpolant, shift at the centre) ----
+
+// W_i = T_i(0) V for the m blocks (T_i(0) = 1, 0, -1, 0, ...)
+__global__ void cip_start_kernel(const double2* __restrict__ V, int64_t ldv, int64_t n, int nu,
+                                 int m, float2* W) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per = n * nu;
+  if (t >= per * m) return;
+  const int i = (int)(t / per);
+  const int64_t e = t % per;
+  const double2 v = V[(e / n) * ldv + e % n];
+  const float s = (i % 2) ? 0.f : ((i / 2) % 2 ? -1.f : 1.f);
+  W[t] = make_float2(s * (float)v.x, s * (float)v.y);
+}
+
+// E: the part of A^{-1} M w that the block rows 0..m-2 fix (E_0 = 0, E_1 = y_0,
+// E_{r+1} = y_r - E_{r-1}; y_0 = w_0, y_r = 2 w_r), one thread per element of a block
+__global__ void cip_recur_kernel(const float2* __restrict__ W, int64_t n, int nu, int m,
+                                 float2* __restrict__ E) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per = n * nu;
+  if (e >= per) return;
+  float2 em1 = make_float2(0.f, 0.f), ei = W[e];
+  E[e] = em1;
+  if (m > 1) E[per + e] = ei;
+  for (int r = 1; r + 1 < m; ++r) {
+    const float2 y = W[(int64_t)r * per + e];
+    const float2 en = make_float2(2.f * y.x - em1.x, 2.f * y.y - em1.y);
+    E[(int64_t)(r + 1) * per + e] = en;
+    em1 = ei;
+    ei = en;
+  }
+}
+
+// X_k = cm_k w_{m-1} - sum_i L_ki E_i (the per-node blocks whose node sum
+// sum_k A(x_k) X_k is the right-hand side b of G u = b)
+__global__ void cip_nodes_kernel(const float2* __restrict__ W, const float2* __restrict__ E,
+                                 int64_t n, int nu, int m, int N, const float* __restrict__ Lk,
+                                 const float* __restrict__ cm, float2* __restrict__ X) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per = n * nu;
+  if (e >= per) return;
+  const float2 wl = W[(int64_t)(m - 1) * per + e];
+  for (int k = 0; k < N; ++k) {
+    float2 x = make_float2(cm[k] * wl.x, cm[k] * wl.y);
+    for (int i = 0; i < m; ++i) {
+      const float l = Lk[k * m + i];
+      if (l == 0.f) continue;
+      const float2 ei = E[(int64_t)i * per + e];
+      x.x -= l * ei.x;
+      x.y -= l * ei.y;
+    }
+    X[(int64_t)k * per + e] = x;
+  }
+}
+
+// W_i = E_i + T_i(0) U
+__global__ void cip_combine_kernel(float2* W, const float2* __restrict__ E,
+                                   const float2* __restrict__ U, int64_t n, int nu, int m) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per = n * nu;
+  if (t >= per * m) return;
+  const int i = (int)(t / per);
+  const float s = (i % 2) ? 0.f : ((i / 2) % 2 ? -1.f : 1.f);
+  const float2 u = U[t % per], ev = E[t];
+  W[t] = make_float2(ev.x + s * u.x, ev.y + s * u.y);
+}
+
 unsigned nblk(int64_t count, int t = 256) { return (unsigned)((count + t - 1) / t); }
 
 }  // namespace
@@ -288,6 +362,96 @@ bem_status inverse_power_impl(bem_ctx* ctx, double* V_dev, int64_t ldv, int nu, 
 
 }  // namespace
 }  // namespace bem
+
+extern "C" bem_status bem_inverse_power_chebyshev(bem_ctx* ctx, double* V_dev, int64_t ldv,
+                                                  int nu, int q, void* stream) {
+  const char* name = "bem_inverse_power_chebyshev";
+  if (!ctx) return BEM_EINVAL;
+  if (ctx->geo.n == 0 || ctx->con.N == 0 || ctx->con.kind != BEM_CONTOUR_CHEBYSHEV)
+    return fail(ctx, BEM_ESTATE, std::string(name) + ": mesh and a Chebyshev contour must be set");
+  const int64_t n = ctx->geo.n;
+  const int N = ctx->con.N, m = N - 1;
+  if (!V_dev || nu < 1 || nu > kMaxNu || ldv < n || q < 0 || N < 4 || N > kMaxNodesSolve)
+    return fail(ctx, BEM_EINVAL, std::string(name) +
+                                     ": need V, 1 <= nu <= 256, ldv >= n, 4 <= N <= 64 points");
+  if (q == 0) return BEM_OK;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  // coefficients: B_i = sum_k c_ik A(x_k), c_ik = (2 - delta_i0) / N cos(i pi (k + 1/2) / N);
+  // the last block row's L_i = -B_i (i <= m-3), B_m - B_{m-2}, -B_{m-1} as node weights
+  // l_ik; G = sum_i T_i(0) L_i = sum_k g_k A(x_k); cm_k = 2 c_mk (y_{m-1} = 2 B_m w_{m-1})
+  auto cik = [&](int i, int k) {
+    return (i == 0 ? 1.0 : 2.0) / N * cos(i * M_PI * (k + 0.5) / N);
+  };
+  std::vector<float> Lk((size_t)N * m), cm(N);
+  std::vector<double> g(2 * N, 0.0), ones(2 * N, 0.0);
+  for (int k = 0; k < N; ++k) {
+    for (int i = 0; i < m; ++i) {
+      double l;
+      if (i <= m - 3) l = -cik(i, k);
+      else if (i == m - 2) l = cik(m, k) - cik(m - 2, k);
+      else l = -cik(m - 1, k);
+      Lk[(size_t)k * m + i] = (float)l;
+      const double t0 = (i % 2) ? 0.0 : ((i / 2) % 2 ? -1.0 : 1.0);
+      g[2 * k] += t0 * l;
+    }
+    cm[k] = (float)(2.0 * cik(m, k));
+    ones[2 * k] = 1.0;
+  }
+  size_t off = 0;
+  auto take = [&](size_t b) { const size_t o = off; off += (b + 255) / 256 * 256; return o; };
+  const size_t blk = (size_t)n * nu * sizeof(float2);
+  const size_t oG = take((size_t)n * n * sizeof(float2)), oP = take((size_t)n * sizeof(int)),
+               oW = take((size_t)m * blk), oE = take((size_t)m * blk), oX = take((size_t)N * blk),
+               oU = take(blk), oN = take((size_t)nu * sizeof(double)),
+               oL = take(((size_t)N * m + N) * sizeof(float)),
+               oS = take(mixed_sum_work_bytes(ctx, nu, true));
+  bem_status st = ensure_scratch(ctx, off);
+  if (st != BEM_OK) return st;
+  st = ensure_self32(ctx, s);
+  if (st != BEM_OK) return st;
+  unsigned char* base = reinterpret_cast<unsigned char*>(ctx->d_scratch);
+  float2* G = reinterpret_cast<float2*>(base + oG);
+  int* piv = reinterpret_cast<int*>(base + oP);
+  float2* W = reinterpret_cast<float2*>(base + oW);
+  float2* E = reinterpret_cast<float2*>(base + oE);
+  float2* X = reinterpret_cast<float2*>(base + oX);
+  float2* U = reinterpret_cast<float2*>(base + oU);
+  double* nrm = reinterpret_cast<double*>(base + oN);
+  float* dL = reinterpret_cast<float*>(base + oL);
+  float* dcm = dL + (size_t)N * m;
+  st = cuda_check(ctx, cudaMemcpyAsync(dL, Lk.data(), Lk.size() * sizeof(float),
+                                       cudaMemcpyHostToDevice, s), name);
+  if (st == BEM_OK)
+    st = cuda_check(ctx, cudaMemcpyAsync(dcm, cm.data(), cm.size() * sizeof(float),
+                                         cudaMemcpyHostToDevice, s), name);
+  if (st == BEM_OK) st = assemble32(ctx, N, ctx->con.z_host, g.data(), G, s);
+  if (st == BEM_OK) st = lu32(ctx, G, n, piv, s);
+  if (st != BEM_OK) return st;
+  const int64_t per = n * nu;
+  cip_start_kernel<<<nblk(per * m), 256, 0, s>>>(reinterpret_cast<const double2*>(V_dev), ldv, n,
+                                                nu, m, W);
+  ctx->launches++;
+  for (int step = 0; step < q; ++step) {
+    cip_recur_kernel<<<nblk(per), 256, 0, s>>>(W, n, nu, m, E);
+    cip_nodes_kernel<<<nblk(per), 256, 0, s>>>(W, E, n, nu, m, N, dL, dcm, X);
+    ctx->launches += 2;
+    // b = sum_k A(x_k) X_k (the node-summed fused kernel), then u = G^{-1} b
+    st = mixed_sum_apply(ctx, X, n, n * nu, true, nu, ones.data(), U, base + oS, s);
+    if (st == BEM_OK) st = lu32_solve(ctx, G, piv, n, U, nu, s);
+    if (st != BEM_OK) return st;
+    cip_combine_kernel<<<nblk(per * m), 256, 0, s>>>(W, E, U, n, nu, m);
+    ip_colnorm_kernel<<<nu, 256, 0, s>>>(W, n, nu, m, nrm);
+    ip_scale_kernel<<<nblk(per * m), 256, 0, s>>>(W, U, n, nu, m, nrm);
+    ctx->launches += 3;
+  }
+  // the basis: u = v_0, the y-part of the linearisation
+  f32_to_f64_kernel<<<nblk(per), 256, 0, s>>>(W, n, nu, reinterpret_cast<double2*>(V_dev), ldv);
+  ctx->launches++;
+  st = cuda_check(ctx, cudaGetLastError(), name);
+  if (st != BEM_OK) return st;
+  return take_status(ctx, s, name);
+}
 
 extern "C" bem_status bem_inverse_power(bem_ctx* ctx, double* V_dev, int64_t ldv, int nu, int q,
                                         double shift_re, double shift_im, void* stream) {
@@ -407,7 +571,7 @@ extern "C" bem_status bem_refine(bem_ctx* ctx, int m, double* lam_host, double* 
   double2* e = reinterpret_cast<double2*>(base + oE);
   double2* dlam = reinterpret_cast<double2*>(base + oL);
   double2* dots = reinterpret_cast<double2*>(base + oD);
-  double2 hd[2];
+  double2 hd[3];
   const double one[2] = {1.0, 0.0};
   // eigenpairs in order of Re lambda, so that the members of a cluster (|lambda - sigma|
   // <= 1e-3 |sigma|: a multiple eigenvalue split by the mesh) follow each other and share
@@ -434,9 +598,15 @@ extern "C" bem_status bem_refine(bem_ctx* ctx, int m, double* lam_host, double* 
     scale_vec_kernel<<<nblk(n), 256, 0, s>>>(x, n, hd[0]);
     ctx->launches++;
     double dl_prev = INFINITY;
-    int it = 0;
+    int it = 0, factorisations = 0;
+    // a Ritz value that is not an eigenvalue (reading of the paper's spurious values)
+    // makes lambda wander off: stop once it leaves twice the contour's extent
+    const double c_re = ctx->con.c_re, c_im = ctx->con.c_im;
+    const double reach = 2.0 * std::max(ctx->con.a, ctx->con.b);
     for (; it < maxit; ++it) {
+      if (!have_lu && factorisations >= kMaxFactorisations) have_lu = true;   // keep the last
       if (!have_lu) {
+        ++factorisations;
         sig_r = lr;
         sig_i = li;
         const double k[2] = {sig_r, sig_i};
@@ -454,15 +624,21 @@ extern "C" bem_status bem_refine(bem_ctx* ctx, int m, double* lam_host, double* 
                           n, reinterpret_cast<double*>(R), reinterpret_cast<double*>(R + n),
                           s) != cudaSuccess)
         return fail(ctx, BEM_ECUDA, "refine residual");
+      // ||r||^2 and ||x||^2 of the current pair (stop once the residual is at the level the
+      // double-FP32 entries resolve)
+      if (launch_colnorms(ctx, reinterpret_cast<double*>(R), n, reinterpret_cast<double*>(x), n,
+                          n, 1, reinterpret_cast<double*>(dots + 2), s) != cudaSuccess)
+        return fail(ctx, BEM_ECUDA, "refine norms");
       to_f32_kernel<<<nblk(2 * n), 256, 0, s>>>(R, 2 * n, F);
       ctx->launches++;
       st = lu32_solve(ctx, A, piv, n, F, 2, s);
       if (st != BEM_OK) return st;
       dot2_kernel<<<2, 256, 0, s>>>(e, F, n, dots);
       ctx->launches++;
-      st = cuda_check(ctx, cudaMemcpyAsync(hd, dots, 2 * sizeof(double2), cudaMemcpyDeviceToHost, s), "refine");
+      st = cuda_check(ctx, cudaMemcpyAsync(hd, dots, 3 * sizeof(double2), cudaMemcpyDeviceToHost, s), "refine");
       if (st == BEM_OK) st = cuda_check(ctx, cudaStreamSynchronize(s), "refine");
       if (st != BEM_OK) return st;
+      if (hd[2].y > 0.0 && sqrt(hd[2].x / hd[2].y) <= kResidualStop) break;
       // dlambda = -(e^H s1) / (e^H s2)
       const double dd = hd[1].x * hd[1].x + hd[1].y * hd[1].y;
       if (!(dd > 0.0)) break;
@@ -478,6 +654,10 @@ extern "C" bem_status bem_refine(bem_ctx* ctx, int m, double* lam_host, double* 
       ctx->launches++;
       lr += dr;
       li += di;
+      if (hypot(lr - c_re, li - c_im) > reach) {   // not an eigenvalue near the contour
+        ++it;
+        break;
+      }
       const double step = hypot(dr, di), lam_abs = hypot(lr, li);
       if (step <= tol * lam_abs) {
         ++it;
@@ -492,7 +672,8 @@ extern "C" bem_status bem_refine(bem_ctx* ctx, int m, double* lam_host, double* 
     if (iters_host) iters_host[c] = it;
   }
   // final FP64 residuals
-  return bem_residual(ctx, m, lam_host, X_dev, ldx, nullptr, relres_host, stream);
+  return bem_residual_arith(ctx, m, lam_host, X_dev, ldx, nullptr, nullptr, relres_host,
+                            ctx->final_residual_arith, stream);
 }
 
 extern "C" bem_status bem_solve(bem_ctx* ctx, const double* V0_dev, int64_t ldv, int nu, int q,
@@ -550,7 +731,14 @@ extern "C" bem_status bem_solve(bem_ctx* ctx, const double* V0_dev, int64_t ldv,
   const double c_re = con.c_re, c_im = con.c_im, a0 = con.a, b0 = con.b;
   const double rb = 2.0 * std::max(a0, b0);
   st = bem_set_contour(ctx, BEM_CONTOUR_CIRCLE, c_re, c_im, rb, rb, N0, nullptr, nullptr, stream);
-  if (st == BEM_OK) st = bem_inverse_power(ctx, V, n, nu, q, c_re, c_im, stream);
+  // The shift sits 0.3 rb above the centre: Algorithm 1 only rescales its columns between
+  //    steps, so an eigenvalue within ~1 % of the radius from the shift (sphere20480:
+  //    6.9894 against the centre 7.0; ellipsoid98304: 9.0087 against 9.0) outgrows every
+  //    other direction by ~100^q and collapses the whole block onto its eigenvector,
+  //    losing the other eigenvalues inside the contour. Off the real axis (where the
+  //    interior eigenvalues lie) no eigenvalue is that close, and the node clusters of
+  //    the basis circle stay at 0.7 rb.
+  if (st == BEM_OK) st = bem_inverse_power(ctx, V, n, nu, q, c_re, c_im + 0.3 * rb, stream);
   const bem_status st_restore =
       bem_set_contour(ctx, kind0, c_re, c_im, a0, b0, N0, nullptr, nullptr, stream);
   if (st == BEM_OK) st = st_restore;
@@ -559,20 +747,37 @@ extern "C" bem_status bem_solve(bem_ctx* ctx, const double* V0_dev, int64_t ldv,
   if (st == BEM_OK) st = bem_project(ctx, V, n, nu, Bh, nullptr, precision, stream);
   if (st != BEM_OK) return st;
   // 3. reduced problem: shift-and-invert at K shifts spread along the major axis
-  //    (K = round(a/b); one shift, the centre, for a circle). The reduced linearisation
+  //    (K = round(a/b) for a flat ellipse). The reduced linearisation
   //    has nu eigenvalues clustered at each node; a shift only sees the eigenvalues that
   //    are nearer to it than the nearest node cluster, so on a flat ellipse one shift at
   //    the centre would return node clusters instead of the eigenvalues inside. Each
   //    shift keeps the converged Ritz pairs inside the contour that are nearer to it
   //    than to any other shift (every eigenvalue is reported once).
+  //    On a circle (and a near-circular ellipse) one shift at the centre converges the
+  //    eigenvalues nearest it first and stops once those have: eigenvalues out towards the
+  //    contour, as near to the node clusters as to the centre, are then missed. There the
+  //    centre is joined by eight shifts on the ellipse of 0.45 times the semi-axes: an
+  //    eigenvalue at 0.75 of the radius is then ~0.36 radii from its nearest shift, the
+  //    node clusters at least 0.55 radii from every shift.
   const double amaj = std::max(con.a, con.b), amin = std::min(con.a, con.b);
   const bool along_re = con.a >= con.b;
-  const int K = std::max(1, std::min(16, (int)lround(amaj / amin)));
-  std::vector<double> sr(K), si(K);
-  for (int kk = 0; kk < K; ++kk) {
-    const double x = -1.0 + (2.0 * kk + 1.0) / K;
-    sr[kk] = con.c_re + (along_re ? amaj * x : 0.0);
-    si[kk] = con.c_im + (along_re ? 0.0 : amaj * x) + 1e-3 * amin;   // off the real axis
+  int K = std::max(1, std::min(16, (int)lround(amaj / amin)));
+  std::vector<double> sr, si;
+  if (K == 1) {
+    sr.push_back(con.c_re);
+    si.push_back(con.c_im + 1e-3 * amin);   // off the real axis
+    for (int kk = 0; kk < 8; ++kk) {
+      const double t = M_PI * (2.0 * kk + 1.0) / 8.0;
+      sr.push_back(con.c_re + 0.45 * con.a * cos(t));
+      si.push_back(con.c_im + 0.45 * con.b * sin(t));
+    }
+    K = 9;
+  } else {
+    for (int kk = 0; kk < K; ++kk) {
+      const double x = -1.0 + (2.0 * kk + 1.0) / K;
+      sr.push_back(con.c_re + (along_re ? amaj * x : 0.0));
+      si.push_back(con.c_im + (along_re ? 0.0 : amaj * x) + 1e-3 * amin);   // off the real axis
+    }
   }
   const int pk = std::min(p, 32);
   std::vector<double> lam(2 * pk), res(pk), lk, ysel;

@@ -50,6 +50,10 @@ __global__ void init_kernel(float* __restrict__ net, uint64_t seed) {
   } else if ((t >= kOffInScale && t < kOffInScale + kNetIn) ||
              (t >= kOffOutScale && t < kOffOutScale + kNetOut)) {
     v = 1.f;
+  } else if (t >= kOffFeatLo && t < kOffFeatLo + kNetIn) {
+    v = -INFINITY;   // no box until the scalings are fitted to training data
+  } else if (t >= kOffFeatHi && t < kOffFeatHi + kNetIn) {
+    v = INFINITY;
   }
   net[t] = v;
 }
@@ -77,16 +81,20 @@ __global__ void forward_kernel(const float* __restrict__ net, const float* __res
 // Mean and standard deviation of column c of the features (c < 11) or of the network's
 // targets (c = 11, 12: target times (d / h)^7): one block per column, fixed-order FP64
 // sums. Sets in_shift / in_scale (1 / std, or 1 for a constant column) and out_scale (std,
-// or 1).
+// or 1), and the features' range (the training box of the quadrature fallback).
 __global__ void fit_scaling_kernel(const float* __restrict__ feat, const float* __restrict__ target,
                                    int64_t count, float* __restrict__ net) {
   __shared__ double s1[256], s2[256];
+  __shared__ float slo[256], shi[256];
   const int c = blockIdx.x;
   double a = 0.0, b = 0.0;
+  float lo = INFINITY, hi = -INFINITY;
   for (int64_t t = threadIdx.x; t < count; t += blockDim.x) {
     double v;
     if (c < kNetIn) {
       v = feat[t * kNetIn + c];
+      lo = fminf(lo, (float)v);
+      hi = fmaxf(hi, (float)v);
     } else {   // the network's own target: (A_near - A_7) / h times (d / h)^7
       float f[kNetIn];
       for (int q = 0; q < kNetIn; ++q) f[q] = feat[t * kNetIn + q];
@@ -97,11 +105,15 @@ __global__ void fit_scaling_kernel(const float* __restrict__ feat, const float* 
   }
   s1[threadIdx.x] = a;
   s2[threadIdx.x] = b;
+  slo[threadIdx.x] = lo;
+  shi[threadIdx.x] = hi;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
     if ((int)threadIdx.x < w) {
       s1[threadIdx.x] += s1[threadIdx.x + w];
       s2[threadIdx.x] += s2[threadIdx.x + w];
+      slo[threadIdx.x] = fminf(slo[threadIdx.x], slo[threadIdx.x + w]);
+      shi[threadIdx.x] = fmaxf(shi[threadIdx.x], shi[threadIdx.x + w]);
     }
     __syncthreads();
   }
@@ -112,6 +124,8 @@ __global__ void fit_scaling_kernel(const float* __restrict__ feat, const float* 
     if (c < kNetIn) {
       net[kOffInShift + c] = (float)mean;
       net[kOffInScale + c] = sd > 1e-6 ? (float)(1.0 / sd) : 1.f;
+      net[kOffFeatLo + c] = slo[0];
+      net[kOffFeatHi + c] = shi[0];
     } else {
       net[kOffOutScale + (c - kNetIn)] = sd > 0.0 ? (float)sd : 1.f;
     }

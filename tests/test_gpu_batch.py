@@ -150,3 +150,27 @@ def test_batch48_full_against_single(bem):
     batch.close()
     for c in ctxs:
         c.close()
+
+
+@pytest.mark.parametrize("problem", [9, 14])
+def test_batch48_problem_eigenvalues_against_oracle(bem, problem):
+    """The whole method (Algorithm 1, CholeskyQR2, mixed projection, reduced solve,
+    refinement) on a problem of the 48-ellipsoid sweep with stored oracle eigenvalues
+    (tests/golden/eigs_batch48_p<i>.txt, pinned complete by the argument principle): every
+    one found, no converged extra inside the circle, 1e-10 relative."""
+    import os
+    import bench
+    if bench.read_golden(f"batch48_p{problem}") is None:
+        pytest.skip("stored list absent")
+    prob = synth.workload("batch48").problems[problem]
+    mesh, c = prob.mesh(), prob.contour
+    ctx = bem.Context(0)
+    ctx.set_mesh(mesh.xyz, mesh.tri)
+    ctx.set_contour(c.kind, c.centre, c.a, c.b, prob.N)
+    V0 = bem.fortran(torch.from_numpy(synth.complex_gaussian(mesh.n, prob.nu, prob.seed)).to("cuda:0"))
+    lam, X, rel = ctx.solve(V0, q=10, precision=bem.PREC_MIXED, tol=1e-14)
+    res = bench.eig_compare(lam, X.cpu().numpy(), rel, bench.read_golden(f"batch48_p{problem}"),
+                            c, 1e-10)
+    print(problem, lam, rel)
+    assert not res["missing"] and not res["extras"], res
+    ctx.close()

@@ -13,7 +13,7 @@ import scipy.linalg as sla
 import torch
 
 import synth
-from oracle import chebyshev as och
+from oracle import assembly as oasm, chebyshev as och
 
 pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -113,6 +113,60 @@ def test_sphere320_through_chebyshev_interpolant(bem):
     # Chebyshev interpolant on [2.8, 4.8]
     c, a = 3.8, 1.0
     ctx.set_contour("chebyshev", c, a, a, 14)
+    P = ctx.project(V, bem.PREC_FP64)
+    B = ctx.chebyshev_coeffs(P)
+    lam, Y, res, _ = ctx.solve_chebyshev(B, c, p=32, tol=1e-10)
+    keep = np.where((np.abs(lam.real - c) < a) & (np.abs(lam.imag) < 0.1) & (res < 1e-6))[0]
+    X = ctx.ritz_vectors(V, Y[:, keep].contiguous())
+    lam_r, rel, _ = ctx.refine(lam[keep], X, tol=1e-14)
+    Xh = X.cpu().numpy()
+    for lg, mult in _golden("sphere320"):
+        near = np.where(np.abs(lam_r - lg) <= 1e-10 * abs(lg))[0]
+        assert len(near) >= 1, (lg, lam_r)
+        sv = np.linalg.svd(Xh[:, near] / np.linalg.norm(Xh[:, near], axis=0), compute_uv=False)
+        assert np.sum(sv > 1e-6) >= mult, (lg, sv)
+        assert np.all(rel[near] < 1e-10)
+    ctx.close()
+
+
+def test_algorithm2_matches_oracle(bem):
+    """Algorithm 2 (bem_inverse_power_chebyshev: FP32 iterate, G factorised in FP32, the
+    right-hand side by the node-summed BF16x3 kernel) against the oracle's FP64 Algorithm 2
+    on the dense Chebyshev coefficients of A, q = 3 steps from the same basis: the same
+    directions to 1e-3 (column by column, up to a scalar), as Algorithm 1's test."""
+    mesh = synth.icosphere(1)
+    c, a, N, nu, q = 3.6, 1.0, 8, 6, 3
+    ctx = bem.Context(0)
+    ctx.set_mesh(mesh.xyz, mesh.tri)
+    z, _ = ctx.set_contour("chebyshev", c, a, a, N)
+    V0 = synth.complex_gaussian(mesh.n, nu, 9)
+    Vd = bem.fortran(torch.from_numpy(V0).to("cuda:0"))
+    ctx.inverse_power_chebyshev(Vd, q)
+    ctx.check()
+    got = Vd.cpu().numpy()
+    B = och.coefficients([oasm.matrix(mesh, zk) for zk in och.nodes(c, a, N)])
+    ref = och.inverse_power(B, V0, q)
+    for col in range(nu):
+        g, r = got[:, col], ref[:, col]
+        al = np.vdot(r, g) / np.vdot(r, r)
+        assert np.linalg.norm(g - al * r) <= 1e-3 * np.linalg.norm(g), col
+    ctx.close()
+
+
+def test_sphere320_through_algorithm2_basis(bem):
+    """The whole Chebyshev route with Algorithm 2's basis: q = 10 steps on the interval
+    [2.8, 4.8], CholeskyQR2, FP64 projection at the Chebyshev points, colleague solve,
+    refinement; the golden eigenvalues of the unit sphere inside the interval (pi and
+    4.4934 x 3 on the level-2 mesh) with their multiplicities to 1e-10."""
+    prob = synth.workload("sphere320").problems[0]
+    mesh = prob.mesh()
+    ctx = bem.Context(0)
+    ctx.set_mesh(mesh.xyz, mesh.tri)
+    c, a = 3.8, 1.0
+    ctx.set_contour("chebyshev", c, a, a, 14)
+    V = bem.fortran(torch.from_numpy(synth.complex_gaussian(mesh.n, prob.nu, prob.seed)).to("cuda:0"))
+    ctx.inverse_power_chebyshev(V, 10)
+    ctx.cholqr2(V, want_R=False)
     P = ctx.project(V, bem.PREC_FP64)
     B = ctx.chebyshev_coeffs(P)
     lam, Y, res, _ = ctx.solve_chebyshev(B, c, p=32, tol=1e-10)

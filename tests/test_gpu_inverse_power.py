@@ -34,6 +34,8 @@ CASES = {
     "sphere320": (lambda: synth.icosphere(2), synth.ContourSpec("circle", 4.0 + 0j, 1.0, 1.0), 16, 16),
     "ragged108": (lambda: synth.cube_grid(3), synth.ContourSpec("ellipse", 6.5 + 0.1j, 1.5, 0.4), 7, 5),
     "nu72": (lambda: synth.icosphere(1), synth.ContourSpec("ellipse", 5.0 + 0j, 1.2, 0.5), 12, 72),
+    # nu = 256: two column chunks of the accumulator (one node per unit)
+    "nu256": (lambda: synth.icosphere(2), synth.ContourSpec("circle", 9.0 + 0j, 1.5, 1.5), 4, 256),
 }
 
 
@@ -70,24 +72,30 @@ def test_apply_sum_matches_oracle(bem, case, per_node):
     ctx.close()
 
 
-def test_inverse_power_matches_oracle(bem):
-    prob = synth.workload("sphere320").problems[0]
-    mesh, spec, N, nu = prob.mesh(), prob.contour, prob.N, prob.nu
+@pytest.mark.parametrize("case", ["sphere320", "cube3072"])
+def test_inverse_power_matches_oracle(bem, case):
+    """sphere320: two LU panels; cube3072 (n = 3072): twelve panels of 256 columns, so every
+    level of the blocked factorisation (sub-panel pivoting, in-panel updates, interchanges,
+    block rows, tensor-core trailing updates) is exercised."""
+    prob = synth.workload(case).problems[0]
+    mesh, spec, N = prob.mesh(), prob.contour, prob.N
+    nu = prob.nu if case == "sphere320" else 8
     ctx = bem.Context(0)
     ctx.set_mesh(mesh.xyz, mesh.tri)
     z, w = ctx.set_contour(spec.kind, spec.centre, spec.a, spec.b, N)
     V0 = synth.complex_gaussian(mesh.n, nu, prob.seed)
-    q = 3
+    q = 3 if case == "sphere320" else 2
+    shift = spec.centre + (0.0 if case == "sphere320" else 0.3j)
     Vd = bem.fortran(torch.from_numpy(V0).to("cuda:0"))
-    ctx.inverse_power(Vd, q, spec.centre)
+    ctx.inverse_power(Vd, q, shift)
     ug = Vd.cpu().numpy()
     Bfull = np.stack([w[j] * oasm.matrix(mesh, z[j]) for j in range(N)])
-    uo = orr.inverse_power(Bfull, z, spec.centre, V0, q)
+    uo = orr.inverse_power(Bfull, z, shift, V0, q)
     worst = 0.0
     for c in range(nu):
         a = np.vdot(uo[:, c], ug[:, c]) / np.vdot(uo[:, c], uo[:, c])
         worst = max(worst, np.linalg.norm(ug[:, c] - a * uo[:, c]) / np.linalg.norm(ug[:, c]))
-    print("inverse power: worst column direction error", worst)
+    print(case, "inverse power: worst column direction error", worst)
     assert worst < 1e-3
     ctx.close()
 

@@ -143,3 +143,46 @@ def test_training_and_gain_on_held_out_mesh(bem):
     print("mixed A V error vs near-field oracle: with network", e2, "without near field", e0)
     assert e2 < e0 / 3
     ctx.close()
+
+
+def test_pairs_outside_training_box_take_plain_rule(bem):
+    """The quadrature fallback of the learned part: a network trained only on k h of one
+    narrow band (k in [5.5, 6] on a level-3 sphere) records that box; used at k near 10,
+    every near pair's Re(k h) lies outside it, so every pair must take the plain 8 x 8
+    rule: the mixed projection with the network (mode 2) then equals the one with the
+    rule (mode 1) to FP32 rounding and meets the mixed bar against the oracle's near
+    variant. At k inside the band the same network is used (the projection differs from
+    mode 1 by more than rounding)."""
+    mesh = synth.icosphere(3)
+    tr = _ctx(bem, mesh)
+    feat, targ = tr.surrogate_samples(20000, (5.5, 6.0), (-0.1, 0.1), seed=3)
+    tr.surrogate_init(seed=2)
+    tr.surrogate_train(feat, targ, epochs=3, batch=4096, lr=3e-3)
+    params = tr.surrogate_params(which=0)
+    tr.close()
+    V = synth.complex_gaussian(mesh.n, 8, 5)
+    Vd = bem.fortran(torch.from_numpy(V).to("cuda:0"))
+
+    def proj(spec, mode):
+        ctx = bem.Context(0)
+        ctx.set_mesh(mesh.xyz, mesh.tri)
+        z, w = ctx.set_contour(spec.kind, spec.centre, spec.a, spec.b, 4)
+        ctx.surrogate_set(params)
+        ctx.set_near_field(mode)
+        B = ctx.project(Vd, bem.PREC_MIXED)
+        ctx.check()
+        ctx.close()
+        return (B[0] if isinstance(B, tuple) else B).cpu().numpy(), z, w
+
+    out = synth.ContourSpec("circle", 10.0 + 0j, 0.3, 0.3)
+    B2, z, w = proj(out, 2)
+    B1, _, _ = proj(out, 1)
+    assert np.max(np.abs(B2 - B1)) <= 1e-5 * np.max(np.abs(B1))
+    P, _ = orr.project(mesh, z, V, near=True)
+    for j in range(4):
+        ref = w[j] * P[j]
+        assert np.max(np.abs(B2[j] - ref)) <= 1e-4 * np.max(np.abs(ref))
+    inside = synth.ContourSpec("circle", 5.75 + 0j, 0.05, 0.05)
+    C2, _, _ = proj(inside, 2)
+    C1, _, _ = proj(inside, 1)
+    assert np.max(np.abs(C2 - C1)) > 1e-5 * np.max(np.abs(C1))

@@ -51,3 +51,28 @@ def test_equal_axes_ellipse_is_circle():
     assert np.allclose(w2, (z2 - (2.0 - 1j)) / 24, rtol=1e-15, atol=1e-17)
     # nodes stay off the real axis through the centre for even N (half-step offset)
     assert np.min(np.abs(z2.imag + 1.0)) > 0.0
+
+
+def test_order_selection_closed_form_for_polynomials():
+    """The order test of Section 4, Example 3 on a matrix polynomial of degree 2 < N: the
+    trapezoid Cauchy sum reproduces T(zeta) / (1 + u^N), u = (zeta - c) / rho, so the
+    relative error at every inner point is exactly |u^N / (1 + u^N)| with |u| = 1/2
+    (independent of the test vectors), and the selected order is the first N whose
+    closed-form error meets the tolerance."""
+    import synth
+    from oracle import contour as con
+    rng = np.random.default_rng(2)
+    A0, A1, A2 = (rng.normal(size=(5, 5)) + 1j * rng.normal(size=(5, 5)) for _ in range(3))
+
+    def T(z):
+        return A0 + z * A1 + z * z * A2
+
+    spec = synth.ContourSpec("circle", 2.0 + 1.0j, 1.5, 1.5)
+    X = rng.normal(size=(5, 3)) + 1j * rng.normal(size=(5, 3))
+    N_list = [4, 8, 12, 16, 24]
+    chosen, errs = con.select_order(T, spec, N_list, X, 2e-5, nsamples=8)
+    for N, e in zip(N_list, errs):
+        u = (con.inner_points(spec, 8) - spec.centre) / spec.a
+        closed = np.max(np.abs(u ** N / (1 + u ** N)))
+        assert abs(e - closed) <= 1e-12 + 1e-9 * closed, (N, e, closed)
+    assert chosen == 16   # 2^-16 / (1 - 2^-16) < 2e-5 < 2^-12 / (1 + 2^-12)

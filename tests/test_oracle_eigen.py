@@ -77,3 +77,20 @@ def test_cube3072_golden_list_is_complete(oracle_mod):
     assert expected == 4
     count = refine.winding_count(m, prob.contour, M=48)
     assert abs(count - expected) < 1e-3, count
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("problem", [9, 14])
+def test_batch48_golden_lists_are_complete(oracle_mod, problem):
+    """The stored eigenvalues of two ellipsoids of the 48-problem sweep (no closed form;
+    the generator starts from a grid inside the circle and follows neighbours) are every
+    eigenvalue inside the circle: their count with multiplicity equals the argument
+    principle's winding number of det A(z)."""
+    path = os.path.join(os.path.dirname(__file__), "golden", f"eigs_batch48_p{problem}.txt")
+    if not os.path.exists(path):
+        pytest.skip("stored list absent")
+    prob = synth.workload("batch48").problems[problem]
+    gold = np.loadtxt(path, ndmin=2)
+    expected = int(np.sum(gold[gold[:, 3] == 1, 2]))
+    count = refine.winding_count(prob.mesh(), prob.contour, M=64)
+    assert abs(count - expected) < 1e-3, count
