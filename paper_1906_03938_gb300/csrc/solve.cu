@@ -573,9 +573,11 @@ extern "C" bem_status bem_refine(bem_ctx* ctx, int m, double* lam_host, double* 
   double2* dots = reinterpret_cast<double2*>(base + oD);
   double2 hd[3];
   const double one[2] = {1.0, 0.0};
-  // eigenpairs in order of Re lambda, so that the members of a cluster (|lambda - sigma|
-  // <= 1e-3 |sigma|: a multiple eigenvalue split by the mesh) follow each other and share
-  // the factorisation of A(sigma); the dense LU is the refinement's dominant cost at large n
+  // eigenpairs in order of Re lambda, so that the Ritz values of one multiple eigenvalue
+  // (equal to ~1e-7 relative) follow each other and share the factorisation of A(sigma),
+  // the refinement's dominant cost at large n. Distinct eigenvalues, even those a mesh
+  // splits by 1e-5 (sphere20480: 6.989352 x 3 and 6.989424 x 4), each get their own: a
+  // shift nearer to the neighbour pulls the iteration onto the neighbour's eigenspace.
   std::vector<int> order(m);
   for (int c = 0; c < m; ++c) order[c] = c;
   std::stable_sort(order.begin(), order.end(),
@@ -586,7 +588,7 @@ extern "C" bem_status bem_refine(bem_ctx* ctx, int m, double* lam_host, double* 
     const int c = order[oc];
     double2* x = reinterpret_cast<double2*>(X_dev) + (int64_t)c * ldx;
     double lr = lam_host[2 * c], li = lam_host[2 * c + 1];
-    if (have_lu && hypot(lr - sig_r, li - sig_i) > 1e-3 * hypot(sig_r, sig_i)) have_lu = false;
+    if (have_lu && hypot(lr - sig_r, li - sig_i) > 1e-7 * hypot(sig_r, sig_i)) have_lu = false;
     // e = x0, x normalised so that e^H x = 1
     st = cuda_check(ctx, cudaMemcpyAsync(e, x, n * sizeof(double2), cudaMemcpyDeviceToDevice, s), "refine");
     if (st != BEM_OK) return st;

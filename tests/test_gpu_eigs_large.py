@@ -3,8 +3,9 @@ basis, CholeskyQR2, mixed projection, reduced solve, refinement), through the C 
 
 * sphere20480 with the near-field rule (icosphere level 5, circle 7 / 1, N = 32, nu = 128):
   against the oracle's eigenvalues of the same discrete operator
-  (tests/golden/eigs_sphere20480_near.txt, six of them distinct: 6.2889 and the level-5
-  splits of 6.9879 (3 + 4) and 7.7253 (x 3)), every one found with its multiplicity, no
+  (tests/golden/eigs_sphere20480_near.txt: 6.28451 x 1, the level-5 split of the zero
+  6.9879 of j_3 into 6.989352 x 3 and 6.989424 x 4, and 7.72688 x 3), every one found with
+  its multiplicity, no
   converged extra inside the circle, relative error <= 1e-8 and FP64 residual <= 1e-8
   (the metric's accuracy qualifier).
 * ellipsoid98304 (98304 panels, circle 9 / 1.5, N = 64, nu = 256): the oracle cannot

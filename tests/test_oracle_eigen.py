@@ -94,3 +94,24 @@ def test_batch48_golden_lists_are_complete(oracle_mod, problem):
     expected = int(np.sum(gold[gold[:, 3] == 1, 2]))
     count = refine.winding_count(prob.mesh(), prob.contour, M=64)
     assert abs(count - expected) < 1e-3, count
+
+
+def test_sphere20480_golden_list_matches_continuum_multiplicities():
+    """The stored eigenvalues of the level-5 icosphere with the near field
+    (tests/golden/eigs_sphere20480_near.txt) against the closed forms inside the circle of
+    centre 7 and radius 1: zeros of j_0 (6.283185, x1), j_3 (6.987932, x7) and j_1
+    (7.725252, x3) (Table 3 of the paper). The sphere's exterior single-layer resonances
+    lie below Im k = -1.8 there, so nothing else is inside: each group of discrete values
+    must sit just above its zero (O(h^2), a few 1e-3 relative at level 5) and carry the
+    zero's multiplicity (the icosahedral mesh splits the 7 into 3 + 4)."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "eigs_sphere20480_near.txt")
+    if not os.path.exists(path):
+        pytest.skip("stored list absent")
+    gold = np.loadtxt(path, ndmin=2)
+    gold = gold[gold[:, 3] == 1]
+    assert int(np.sum(gold[:, 2])) == 11
+    for zero, mult in ((6.283185, 1), (6.987932, 7), (7.725252, 3)):
+        near = gold[np.abs(gold[:, 0] - zero) < 0.01 * zero]
+        assert int(np.sum(near[:, 2])) == mult, (zero, near)
+        assert np.all(near[:, 0] > zero) and np.all(near[:, 0] - zero < 3e-3 * zero)
+        assert np.all(np.abs(near[:, 1]) < 1e-6)
