@@ -73,6 +73,8 @@ def main(names):
             f.write("# written by tests/golden/make_golden.py (oracle only)\n")
             f.write("# re im multiplicity inside\n")
             for lam, mult in found:
+                if not contour.inside(lam, spec, -0.05):   # a start that wandered off
+                    continue
                 ins = int(bool(contour.inside(lam, spec)))
                 f.write(f"{lam.real:.17g} {lam.imag:.17g} {mult} {ins}\n")
         print(name, found)
