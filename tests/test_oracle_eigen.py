@@ -92,8 +92,11 @@ def test_batch48_golden_lists_are_complete(oracle_mod, problem):
     prob = synth.workload("batch48").problems[problem]
     gold = np.loadtxt(path, ndmin=2)
     expected = int(np.sum(gold[gold[:, 3] == 1, 2]))
-    count = refine.winding_count(prob.mesh(), prob.contour, M=64)
-    assert abs(count - expected) < 1e-3, count
+    # problem 14 has an eigenvalue at 0.93 of the radius (2.916 in the circle of centre
+    # 2.169, radius 0.8): the trapezoid sum converges slowly there, so the count is taken
+    # on 96 points and compared with the stored multiplicities to 0.05 (an integer apart)
+    count = refine.winding_count(prob.mesh(), prob.contour, M=96)
+    assert abs(count - expected) < 0.05, count
 
 
 def test_sphere20480_golden_list_matches_continuum_multiplicities():
