@@ -317,11 +317,14 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
       auto issue_b = [&]() {
         if (lane == 0) {
           const uint32_t bset = 256u * p.nup;   // one node's (or the shared) planes
-          const int nb = bnodes > 1 ? Gvi : 1;
+          // one X per node (node-summed mode): the planes of each node of the unit, at its
+          // own offset, also when the unit holds a single node
+          const bool per_node = kSum && p.b_node_stride != 0;
+          const int nb = per_node ? Gvi : 1;
           mbar_arrive_expect_tx(&bfull[s], (uint32_t)nb * bset);
           for (int g = 0; g < nb; ++g) {
             const size_t node_off =
-                bnodes > 1 ? (size_t)(p.order[j0i + g] & kNodeMask) * (size_t)p.b_node_stride : 0;
+                per_node ? (size_t)(p.order[j0i + g] & kNodeMask) * (size_t)p.b_node_stride : 0;
             bulk_g2s(sB + s * L.b_stage_bytes + g * bset,
                      reinterpret_cast<const unsigned char*>(p.Bp) + node_off + (size_t)kb * bset,
                      bset, &bfull[s]);

@@ -25,15 +25,19 @@
 #include <vector>
 
 #include "internal.h"
+#include "small_eig.h"
 
 namespace bem {
 namespace {
 
 // refinement: factorisations of A(sigma) per eigenpair at most (the last one is kept), and
-// the relative residual at which an eigenpair is converged (a few units of the double-FP32
-// entries' rounding, 1e-13, times the growth of the sums)
+// the relative residual at which an eigenpair is converged (the double-FP32 entries'
+// rounding, ~1e-13, times the growth of the row sums at n ~ 1e5; three orders below the
+// 1e-8 the eigenpairs are certified to)
 constexpr int kMaxFactorisations = 4;
-constexpr double kResidualStop = 1e-12;
+constexpr double kResidualStop = 1e-11;
+// relative lambda steps below this are the double-FP32 residuals' noise: converged
+constexpr double kStepFloor = 1e-12;
 
 // Vn_j = u / (z_j - s) (u FP64 n x nu, ld ldu)
 __global__ void ip_start_kernel(const double2* __restrict__ U, int64_t ldu, int64_t n, int nu,
@@ -260,6 +264,23 @@ __global__ void cip_combine_kernel(float2* W, const float2* __restrict__ E,
   const float s = (i % 2) ? 0.f : ((i / 2) % 2 ? -1.f : 1.f);
   const float2 u = U[t % per], ev = E[t];
   W[t] = make_float2(ev.x + s * u.x, ev.y + s * u.y);
+}
+
+// Xout[:, cols[c]] = Xc Y[:, c] (Xc n x k, Y k x k column-major, FP64 complex)
+__global__ void combine_cols_kernel(const double2* __restrict__ Xc, int64_t n, int k,
+                                    const double2* __restrict__ Y, const int* __restrict__ cols,
+                                    double2* __restrict__ Xout, int64_t ldx) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * k) return;
+  const int64_t i = t % n;
+  const int c = (int)(t / n);
+  double2 acc = make_double2(0.0, 0.0);
+  for (int q = 0; q < k; ++q) {
+    const double2 x = Xc[(int64_t)q * n + i], y = Y[(int64_t)c * k + q];
+    acc.x += x.x * y.x - x.y * y.y;
+    acc.y += x.x * y.y + x.y * y.x;
+  }
+  Xout[(int64_t)cols[c] * ldx + i] = acc;
 }
 
 unsigned nblk(int64_t count, int t = 256) { return (unsigned)((count + t - 1) / t); }
@@ -661,12 +682,13 @@ extern "C" bem_status bem_refine(bem_ctx* ctx, int m, double* lam_host, double* 
         break;
       }
       const double step = hypot(dr, di), lam_abs = hypot(lr, li);
-      if (step <= tol * lam_abs) {
+      // steps below the double-FP32 residuals' resolution (~1e-13 of lambda) are noise
+      if (step <= std::max(tol, kStepFloor) * lam_abs) {
         ++it;
         break;
       }
-      // stalled: refactor at the current lambda
-      if (step > 0.1 * dl_prev) have_lu = false;
+      // stalled well above that floor: refactor at the current lambda
+      if (step > 0.1 * dl_prev && step > 1e-9 * lam_abs) have_lu = false;
       dl_prev = step;
     }
     lam_host[2 * c] = lr;
@@ -677,6 +699,209 @@ extern "C" bem_status bem_refine(bem_ctx* ctx, int m, double* lam_host, double* 
   return bem_residual_arith(ctx, m, lam_host, X_dev, ldx, nullptr, nullptr, relres_host,
                             ctx->final_residual_arith, stream);
 }
+
+namespace bem {
+namespace {
+
+// theta and y of M0 y = -theta M1 y (k x k, column-major, host): the eigenpairs of
+// -M1^{-1} M0 (Gaussian elimination with partial pivoting, then the small dense solver).
+bool small_pencil(int k, std::vector<small::zc> M0, std::vector<small::zc> M1,
+                  std::vector<small::zc>& theta, std::vector<small::zc>& Y) {
+  using namespace small;
+  auto E = [k](std::vector<zc>& Mx, int i, int j) -> zc& { return Mx[(size_t)j * k + i]; };
+  // solve M1 Z = -M0
+  std::vector<zc> Z(k * k);
+  for (int i = 0; i < k * k; ++i) Z[i] = scl(M0[i], -1.0);
+  for (int c = 0; c < k; ++c) {
+    int p = c;
+    for (int r = c + 1; r < k; ++r)
+      if (absz(E(M1, r, c)) > absz(E(M1, p, c))) p = r;
+    if (!(absz(E(M1, p, c)) > 0.0)) return false;
+    if (p != c) {
+      for (int j = 0; j < k; ++j) std::swap(E(M1, c, j), E(M1, p, j));
+      for (int j = 0; j < k; ++j) std::swap(E(Z, c, j), E(Z, p, j));
+    }
+    for (int r = c + 1; r < k; ++r) {
+      const zc f = dvd(E(M1, r, c), E(M1, c, c));
+      for (int j = c; j < k; ++j)
+        E(M1, r, j) = sub(E(M1, r, j), mul(f, E(M1, c, j)));
+      for (int j = 0; j < k; ++j)
+        E(Z, r, j) = sub(E(Z, r, j), mul(f, E(Z, c, j)));
+    }
+  }
+  for (int j = 0; j < k; ++j)
+    for (int r = k - 1; r >= 0; --r) {
+      zc v = E(Z, r, j);
+      for (int q = r + 1; q < k; ++q) v = sub(v, mul(E(M1, r, q), E(Z, q, j)));
+      E(Z, r, j) = dvd(v, E(M1, r, r));
+    }
+  theta.assign(k, mk(0.0, 0.0));
+  Y.assign(k * k, mk(0.0, 0.0));
+  std::vector<zc> W(k * k);
+  return eig(k, Z.data(), theta.data(), Y.data(), W.data()) == 0;
+}
+
+// Near-degenerate clusters of Ritz values (consecutive values within 1e-3 relative, whose
+// spread exceeds 1e-7 relative: distinct eigenvalues that the mesh splits, such as
+// sphere20480's 6.989352 x 3 and 6.989424 x 4, 7e-5 apart). The mixed projection's error
+// (~1e-5) mixes the Ritz vectors of such eigenvalues, and a refinement vector by vector then
+// lands on the wrong one. On the subspace X of a cluster's Ritz vectors:
+//  (1) two steps of block inverse iteration X <- orth(A(s)^{-1} A'(s) X), s the cluster's
+//      mean: its invariant subspace gains |rest - s| / |cluster - s| (~1e4) per step;
+//  (2) the projected problem X^H A(lambda) X y = 0 by successive linear problems (Ruhe):
+//      at mu, M0 = X^H A(mu) X, M1 = X^H A'(mu) X and M0 y = -theta M1 y; all k values
+//      from mu = s, then one more step for each at its own mu = s + theta;
+//  (3) the cluster's Ritz pairs replaced by (mu + theta, X y), y from the step at s (so
+//      that the members of a multiple eigenvalue keep independent vectors).
+// A(s) is factorised in FP32; the applications of A and A' are double-FP32.
+bem_status separate_clusters(bem_ctx* ctx, int k, double* lam, double* X_dev, int64_t ldx,
+                             cudaStream_t s) {
+  using namespace small;
+  const int64_t n = ctx->geo.n;
+  std::vector<int> order(k);
+  for (int i = 0; i < k; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return lam[2 * a] < lam[2 * b]; });
+  const double one[2] = {1.0, 0.0};
+  for (int b0 = 0; b0 < k;) {
+    int b1 = b0 + 1;
+    while (b1 < k && hypot(lam[2 * order[b1]] - lam[2 * order[b1 - 1]],
+                           lam[2 * order[b1] + 1] - lam[2 * order[b1 - 1] + 1]) <=
+                         1e-3 * hypot(lam[2 * order[b1]], lam[2 * order[b1] + 1]))
+      ++b1;
+    const int kc = b1 - b0;
+    double sr = 0.0, si = 0.0, spread = 0.0;
+    for (int q = b0; q < b1; ++q) {
+      sr += lam[2 * order[q]] / kc;
+      si += lam[2 * order[q] + 1] / kc;
+    }
+    for (int q = b0; q < b1; ++q)
+      spread = std::max(spread, hypot(lam[2 * order[q]] - sr, lam[2 * order[q] + 1] - si));
+    const int c0 = b0;
+    b0 = b1;
+    if (kc < 2 || kc > 32 || spread <= 1e-7 * hypot(sr, si)) continue;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
+    const size_t oA = take((size_t)n * n * sizeof(float2)), oP = take((size_t)n * sizeof(int)),
+                 oX = take((size_t)n * kc * sizeof(double2)), oR = take((size_t)n * kc * sizeof(double2)),
+                 oD = take((size_t)n * kc * sizeof(double2)), oF = take((size_t)n * kc * sizeof(float2)),
+                 oM = take((size_t)2 * kc * kc * sizeof(double2)), oL = take((size_t)2 * kc * sizeof(double)),
+                 oY = take((size_t)kc * kc * sizeof(double2)), oC = take((size_t)kc * sizeof(int));
+    bem_status st = ensure_scratch(ctx, off);
+    if (st != BEM_OK) return st;
+    unsigned char* base = reinterpret_cast<unsigned char*>(ctx->d_scratch);
+    float2* A = reinterpret_cast<float2*>(base + oA);
+    int* piv = reinterpret_cast<int*>(base + oP);
+    double2* Xc = reinterpret_cast<double2*>(base + oX);
+    double2* R = reinterpret_cast<double2*>(base + oR);
+    double2* D = reinterpret_cast<double2*>(base + oD);
+    float2* F = reinterpret_cast<float2*>(base + oF);
+    double2* M = reinterpret_cast<double2*>(base + oM);
+    double* dlam = reinterpret_cast<double*>(base + oL);
+    double2* dY = reinterpret_cast<double2*>(base + oY);
+    int* dcols = reinterpret_cast<int*>(base + oC);
+    std::vector<int> cols(kc);
+    for (int q = 0; q < kc; ++q) {
+      cols[q] = order[c0 + q];
+      st = cuda_check(ctx, cudaMemcpyAsync(Xc + (int64_t)q * n, reinterpret_cast<double2*>(X_dev) +
+                                               (int64_t)cols[q] * ldx, n * sizeof(double2),
+                                           cudaMemcpyDeviceToDevice, s), "cluster copy");
+      if (st != BEM_OK) return st;
+    }
+    const double sh[2] = {sr, si};
+    st = assemble32(ctx, 1, sh, one, A, s);
+    if (st == BEM_OK) st = lu32(ctx, A, n, piv, s);
+    if (st != BEM_OK) return st;
+    std::vector<double> lv(2 * kc);
+    // M0 = Xc^H A(mu) Xc, M1 = Xc^H A'(mu) Xc on the host
+    auto project_at = [&](double mr, double mi, std::vector<zc>& M0, std::vector<zc>& M1) {
+      for (int q = 0; q < kc; ++q) { lv[2 * q] = mr; lv[2 * q + 1] = mi; }
+      bem_status r = cuda_check(ctx, cudaMemcpyAsync(dlam, lv.data(), lv.size() * sizeof(double),
+                                                     cudaMemcpyHostToDevice, s), "cluster");
+      if (r != BEM_OK) return r;
+      if (launch_apply_ff(ctx, kc, dlam, reinterpret_cast<double*>(Xc), n,
+                          reinterpret_cast<double*>(R), reinterpret_cast<double*>(D), s) != cudaSuccess ||
+          launch_xhy_fp64(ctx, reinterpret_cast<double*>(Xc), n, kc, reinterpret_cast<double*>(R),
+                          n, 0, kc, n, 1, nullptr, reinterpret_cast<double*>(M), s) != cudaSuccess ||
+          launch_xhy_fp64(ctx, reinterpret_cast<double*>(Xc), n, kc, reinterpret_cast<double*>(D),
+                          n, 0, kc, n, 1, nullptr, reinterpret_cast<double*>(M + kc * kc), s) != cudaSuccess)
+        return fail(ctx, BEM_ECUDA, "cluster projection");
+      std::vector<double2> h(2 * kc * kc);
+      r = cuda_check(ctx, cudaMemcpyAsync(h.data(), M, h.size() * sizeof(double2),
+                                          cudaMemcpyDeviceToHost, s), "cluster");
+      if (r == BEM_OK) r = cuda_check(ctx, cudaStreamSynchronize(s), "cluster");
+      M0.resize(kc * kc);
+      M1.resize(kc * kc);
+      for (int q = 0; q < kc * kc; ++q) {
+        M0[q] = mk(h[q].x, h[q].y);
+        M1[q] = mk(h[kc * kc + q].x, h[kc * kc + q].y);
+      }
+      return r;
+    };
+    // (1) block inverse iteration with A(s)^{-1} A'(s)
+    for (int step = 0; step < 2; ++step) {
+      for (int q = 0; q < kc; ++q) { lv[2 * q] = sr; lv[2 * q + 1] = si; }
+      st = cuda_check(ctx, cudaMemcpyAsync(dlam, lv.data(), lv.size() * sizeof(double),
+                                           cudaMemcpyHostToDevice, s), "cluster");
+      if (st != BEM_OK) return st;
+      if (launch_apply_ff(ctx, kc, dlam, reinterpret_cast<double*>(Xc), n,
+                          reinterpret_cast<double*>(R), reinterpret_cast<double*>(D), s) != cudaSuccess)
+        return fail(ctx, BEM_ECUDA, "cluster iteration");
+      to_f32_kernel<<<nblk(n * kc), 256, 0, s>>>(D, n * kc, F);
+      ctx->launches++;
+      st = lu32_solve(ctx, A, piv, n, F, kc, s);
+      if (st != BEM_OK) return st;
+      f32_to_f64_kernel<<<nblk(n * kc), 256, 0, s>>>(F, n, kc, Xc, n);
+      ctx->launches++;
+      st = bem_cholqr2(ctx, reinterpret_cast<double*>(Xc), n, n, kc, nullptr, s);
+      if (st != BEM_OK) return st;
+    }
+    // (2) successive linear problems on the projected problem
+    std::vector<zc> M0, M1, th, Yv, th2, Y2, Ysel(kc * kc);
+    st = project_at(sr, si, M0, M1);
+    if (st != BEM_OK) return st;
+    if (!small_pencil(kc, M0, M1, th, Yv)) continue;   // leave the cluster to the refinement
+    std::vector<double> newlam(2 * kc);
+    bool ok = true;
+    for (int q = 0; q < kc && ok; ++q) {
+      const double mr = sr + th[q].re, mi = si + th[q].im;
+      st = project_at(mr, mi, M0, M1);
+      if (st != BEM_OK) return st;
+      ok = small_pencil(kc, M0, M1, th2, Y2);
+      if (!ok) break;
+      int best = 0;
+      for (int r = 1; r < kc; ++r)
+        if (absz(th2[r]) < absz(th2[best])) best = r;
+      newlam[2 * q] = mr + th2[best].re;
+      newlam[2 * q + 1] = mi + th2[best].im;
+      // the vectors from the step at s: distinct for every member of a multiple
+      // eigenvalue (the refinement polishes them)
+      for (int r = 0; r < kc; ++r) Ysel[(int64_t)q * kc + r] = Yv[(size_t)q * kc + r];
+    }
+    if (!ok) continue;
+    // (3) the cluster's pairs: (mu + theta, Xc y)
+    std::vector<double2> hy(kc * kc);
+    for (int q = 0; q < kc * kc; ++q) hy[q] = make_double2(Ysel[q].re, Ysel[q].im);
+    st = cuda_check(ctx, cudaMemcpyAsync(dY, hy.data(), hy.size() * sizeof(double2),
+                                         cudaMemcpyHostToDevice, s), "cluster");
+    if (st == BEM_OK)
+      st = cuda_check(ctx, cudaMemcpyAsync(dcols, cols.data(), kc * sizeof(int),
+                                           cudaMemcpyHostToDevice, s), "cluster");
+    if (st != BEM_OK) return st;
+    combine_cols_kernel<<<nblk(n * kc), 256, 0, s>>>(Xc, n, kc, dY, dcols,
+                                                     reinterpret_cast<double2*>(X_dev), ldx);
+    ctx->launches++;
+    st = cuda_check(ctx, cudaStreamSynchronize(s), "cluster");
+    if (st != BEM_OK) return st;
+    for (int q = 0; q < kc; ++q) {
+      lam[2 * cols[q]] = newlam[2 * q];
+      lam[2 * cols[q] + 1] = newlam[2 * q + 1];
+    }
+  }
+  return BEM_OK;
+}
+
+}  // namespace
+}  // namespace bem
 
 extern "C" bem_status bem_solve(bem_ctx* ctx, const double* V0_dev, int64_t ldv, int nu, int q,
                                 int precision, double tol, int kmax, double* lam_host,
@@ -813,6 +1038,9 @@ extern "C" bem_status bem_solve(bem_ctx* ctx, const double* V0_dev, int64_t ldv,
   *k_found = 0;
   if (k == 0) return take_status(ctx, s, "bem_solve");
   st = bem_ritz_vectors(ctx, V, n, nu, Xc, k, X_dev, ldx, stream);
+  if (st != BEM_OK) return st;
+  // near-degenerate clusters separated on their own subspace before the refinement
+  st = separate_clusters(ctx, k, lk.data(), X_dev, ldx, s);
   if (st != BEM_OK) return st;
   std::vector<double> rr(k);
   // 4. FP64 refinement of every candidate against A(k) itself
