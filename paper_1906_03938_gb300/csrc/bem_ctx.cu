@@ -215,6 +215,7 @@ void bem_destroy(bem_ctx* ctx) {
   cudaFree(ctx->d_piv_val);
   cudaFree(ctx->d_piv_idx);
   cudaFree(ctx->d_lu_work);
+  cudaFree(ctx->d_zgemm);
   release_cublas(ctx);
   cudaFree(ctx->d_solve);
   cudaFree(ctx->d_near_ptr);

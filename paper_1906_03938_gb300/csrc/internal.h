@@ -104,6 +104,8 @@ struct bem_ctx {
   void* cublas = nullptr;        // cuBLAS handle of the dense LU's trailing updates (lazy)
   float* d_piv_val = nullptr;    // LU pivot search: per-block partial maxima and their rows
   int* d_piv_idx = nullptr;
+  double* d_zgemm = nullptr;     // split-k partial products of the small complex GEMMs
+  size_t zgemm_bytes = 0;
   float* d_lu_work = nullptr;    // the LU's trailing-update operands in real form
   size_t lu_work_bytes = 0;
   size_t small_bytes = 0;

@@ -134,9 +134,12 @@ __global__ void __launch_bounds__(1024) gauss_jordan_kernel(double2* M, double2*
 constexpr int kZT = 32;
 // C = A B (complex FP64): A m x k (lda), B k x n (ldb), C m x n (ldc); 32 x 32 tiles,
 // fixed-order sums.
+// With gridDim.z > 1 block z sums the k-range [z kc, (z + 1) kc) and writes its partial
+// product at C + z * ldc * n (the caller sums the partials in z order).
 __global__ void __launch_bounds__(256)
 zgemm_kernel(int m, int n, int k, const double2* __restrict__ A, int64_t lda,
-             const double2* __restrict__ B, int64_t ldb, double2* __restrict__ C, int64_t ldc) {
+             const double2* __restrict__ B, int64_t ldb, double2* __restrict__ C, int64_t ldc,
+             int kc) {
   __shared__ double2 sA[kZT][kZT + 1];
   __shared__ double2 sB[kZT][kZT + 1];
   const int i0 = blockIdx.x * kZT, j0 = blockIdx.y * kZT;
@@ -144,12 +147,14 @@ zgemm_kernel(int m, int n, int k, const double2* __restrict__ A, int64_t lda,
   double2 acc[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) acc[q] = make_double2(0.0, 0.0);
-  for (int k0 = 0; k0 < k; k0 += kZT) {
+  const int kb = blockIdx.z * kc, ke = min(k, kb + kc);
+  C += (int64_t)blockIdx.z * ldc * n;
+  for (int k0 = kb; k0 < ke; k0 += kZT) {
     __syncthreads();
     for (int t = threadIdx.x; t < kZT * kZT; t += 256) {
       const int r = t % kZT, c = t / kZT;
-      sA[r][c] = (i0 + r < m && k0 + c < k) ? A[(int64_t)(k0 + c) * lda + i0 + r] : make_double2(0.0, 0.0);
-      sB[r][c] = (k0 + r < k && j0 + c < n) ? B[(int64_t)(j0 + c) * ldb + k0 + r] : make_double2(0.0, 0.0);
+      sA[r][c] = (i0 + r < m && k0 + c < ke) ? A[(int64_t)(k0 + c) * lda + i0 + r] : make_double2(0.0, 0.0);
+      sB[r][c] = (k0 + r < ke && j0 + c < n) ? B[(int64_t)(j0 + c) * ldb + k0 + r] : make_double2(0.0, 0.0);
     }
     __syncthreads();
 #pragma unroll 8
@@ -444,12 +449,57 @@ __global__ void cheb_residual_kernel(const double2* __restrict__ B, const double
 
 }  // namespace
 
+// C = sum_z P_z (m x n each, packed with leading dimension m), fixed order
+__global__ void zsum_parts_kernel(const double2* __restrict__ P, int parts, int m, int n,
+                                  double2* __restrict__ C, int64_t ldc) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)m * n) return;
+  const int i = (int)(t % m), j = (int)(t / m);
+  double2 acc = make_double2(0.0, 0.0);
+  for (int z = 0; z < parts; ++z) {
+    const double2 v = P[(int64_t)z * m * n + t];
+    acc.x += v.x;
+    acc.y += v.y;
+  }
+  C[(int64_t)j * ldc + i] = acc;
+}
+
 cudaError_t launch_zgemm(bem_ctx* ctx, int m, int n, int k, const double* A, int64_t lda,
                          const double* B, int64_t ldb, double* C, int64_t ldc, cudaStream_t s) {
   dim3 grid((unsigned)((m + kZT - 1) / kZT), (unsigned)((n + kZT - 1) / kZT));
+  // few output tiles and a long k (the reduced problem's [C_0 .. C_{N-1}] W, k = N nu):
+  // split k so that the device fills, partial products summed in a fixed order
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  const int tiles = (int)(grid.x * grid.y);
+  int parts = 1;
+  if (tiles < 2 * sms && k >= 8 * kZT)
+    parts = std::min((2 * sms + tiles - 1) / tiles, k / (4 * kZT));
+  if (parts > 1) {
+    const int kc = ((k + parts - 1) / parts + kZT - 1) / kZT * kZT;
+    parts = (k + kc - 1) / kc;
+    const size_t bytes = (size_t)parts * m * n * sizeof(double2);
+    if (bytes > ctx->zgemm_bytes) {
+      cudaFree(ctx->d_zgemm);
+      ctx->d_zgemm = nullptr;
+      ctx->zgemm_bytes = 0;
+      cudaError_t e = cudaMalloc(&ctx->d_zgemm, bytes);
+      if (e != cudaSuccess) return e;
+      ctx->zgemm_bytes = bytes;
+    }
+    grid.z = (unsigned)parts;
+    zgemm_kernel<<<grid, 256, 0, s>>>(m, n, k, reinterpret_cast<const double2*>(A), lda,
+                                      reinterpret_cast<const double2*>(B), ldb,
+                                      reinterpret_cast<double2*>(ctx->d_zgemm), m, kc);
+    zsum_parts_kernel<<<(unsigned)(((int64_t)m * n + 255) / 256), 256, 0, s>>>(
+        reinterpret_cast<const double2*>(ctx->d_zgemm), parts, m, n,
+        reinterpret_cast<double2*>(C), ldc);
+    ctx->launches += 2;
+    return cudaGetLastError();
+  }
   zgemm_kernel<<<grid, 256, 0, s>>>(m, n, k, reinterpret_cast<const double2*>(A), lda,
                                     reinterpret_cast<const double2*>(B), ldb,
-                                    reinterpret_cast<double2*>(C), ldc);
+                                    reinterpret_cast<double2*>(C), ldc, k);
   ctx->launches++;
   return cudaGetLastError();
 }
