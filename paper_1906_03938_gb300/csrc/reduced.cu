@@ -215,15 +215,37 @@ __global__ void scale_columns_kernel(double2* Y, int64_t rows, int cols, const d
 
 // Reduced residuals ||sum_j B^_j y_i / (lambda_i - z_j)|| / (||y_i|| sum_j ||B^_j||_1 /
 // |lambda_i - z_j|), one block per column i (fixed-order sums).
+// bnorm[j] = max column sum of |B^_j| (the size of B^_j in the residual's scale), one block
+// per node, fixed-order sums
+__global__ void bnorm_kernel(const double2* __restrict__ Bhat, int nu, double* __restrict__ bnorm) {
+  __shared__ double red[256];
+  const double2* B = Bhat + (int64_t)blockIdx.x * nu * nu;
+  double mx = 0.0;
+  for (int k = threadIdx.x; k < nu; k += blockDim.x) {
+    double cs = 0.0;
+    for (int a = 0; a < nu; ++a) cs += hypot(B[(int64_t)k * nu + a].x, B[(int64_t)k * nu + a].y);
+    mx = fmax(mx, cs);
+  }
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bnorm[blockIdx.x] = red[0];
+}
+
+// ||sum_j B^_j y / (lambda - z_j)|| / (||y|| sum_j ||B^_j|| / |lambda - z_j|) per Ritz pair,
+// one block per pair; bnorm from bnorm_kernel.
 __global__ void reduced_residual_kernel(const double2* __restrict__ Bhat, const double2* __restrict__ z,
                                         const double2* __restrict__ lam, const double2* __restrict__ Y,
-                                        int N, int nu, double* __restrict__ res) {
-  __shared__ double red[256];
-  __shared__ double sden;
+                                        int N, int nu, const double* __restrict__ bnorm,
+                                        double* __restrict__ res) {
+  __shared__ double red[256], ry[256];
   const int i = blockIdx.x;
   const double2 l = lam[i];
   const double2* y = Y + (int64_t)i * nu;
-  double part = 0.0;
+  double part = 0.0, yn = 0.0;
   for (int a = threadIdx.x; a < nu; a += blockDim.x) {
     double2 acc = make_double2(0.0, 0.0);
     for (int j = 0; j < N; ++j) {
@@ -239,28 +261,22 @@ __global__ void reduced_residual_kernel(const double2* __restrict__ Bhat, const 
       acc.y += q.y;
     }
     part += acc.x * acc.x + acc.y * acc.y;
+    yn += y[a].x * y[a].x + y[a].y * y[a].y;
   }
   red[threadIdx.x] = part;
+  ry[threadIdx.x] = yn;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    if ((int)threadIdx.x < w) {
+      red[threadIdx.x] += red[threadIdx.x + w];
+      ry[threadIdx.x] += ry[threadIdx.x + w];
+    }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    double yn = 0.0, den = 0.0;
-    for (int k = 0; k < nu; ++k) yn += y[k].x * y[k].x + y[k].y * y[k].y;
-    for (int j = 0; j < N; ++j) {
-      // max column sum of |B^_j| as the size of B^_j
-      double bmax = 0.0;
-      const double2* B = Bhat + (int64_t)j * nu * nu;
-      for (int k = 0; k < nu; ++k) {
-        double cs = 0.0;
-        for (int a = 0; a < nu; ++a) cs += hypot(B[(int64_t)k * nu + a].x, B[(int64_t)k * nu + a].y);
-        bmax = fmax(bmax, cs);
-      }
-      den += bmax / hypot(l.x - z[j].x, l.y - z[j].y);
-    }
-    sden = den * sqrt(yn);
+    double den = 0.0;
+    for (int j = 0; j < N; ++j) den += bnorm[j] / hypot(l.x - z[j].x, l.y - z[j].y);
+    const double sden = den * sqrt(ry[0]);
     res[i] = sden > 0.0 ? sqrt(red[0]) / sden : INFINITY;
   }
 }
@@ -535,7 +551,8 @@ extern "C" bem_status bem_solve_reduced(bem_ctx* ctx, const double* Bhat_dev, in
   const size_t oC = take(nC * z2), oS = take(nS * z2), oSi = take(nS * z2), oW = take(nW * z2),
                oHW = take(nW * z2), oT = take(nT * z2), oU = take(nT * z2), oG = take(nG * z2),
                oZ = take(nG * z2), oVs = take(nG * z2), oMu = take((size_t)p * z2),
-               oRes = take((size_t)p * sizeof(double)), oCq = take(cq);
+               oRes = take((size_t)p * sizeof(double)), oBn = take((size_t)N * sizeof(double)),
+               oCq = take(cq);
   bem_status st = ensure_scratch(ctx, off);
   if (st != BEM_OK) return st;
   unsigned char* base = reinterpret_cast<unsigned char*>(ctx->d_scratch);
@@ -551,6 +568,7 @@ extern "C" bem_status bem_solve_reduced(bem_ctx* ctx, const double* Bhat_dev, in
   double2* Vs = reinterpret_cast<double2*>(base + oVs);
   double2* mu = reinterpret_cast<double2*>(base + oMu);
   double* res = reinterpret_cast<double*>(base + oRes);
+  double* bnorm = reinterpret_cast<double*>(base + oBn);
   void* cqw = base + oCq;
   const double2* z = reinterpret_cast<const double2*>(ctx->con.z);
 
@@ -558,7 +576,8 @@ extern "C" bem_status bem_solve_reduced(bem_ctx* ctx, const double* Bhat_dev, in
       reinterpret_cast<const double2*>(Bhat_dev), z, shift, N, nu, C, S);
   gauss_jordan_kernel<<<1, 1024, 0, s>>>(S, Si, nu, ctx->d_status);
   random_block_kernel<<<(unsigned)((nW + 255) / 256), 256, 0, s>>>(W, (int64_t)nW, 20190609ull);
-  ctx->launches += 3;
+  bnorm_kernel<<<N, 256, 0, s>>>(reinterpret_cast<const double2*>(Bhat_dev), nu, bnorm);
+  ctx->launches += 4;
   st = cuda_check(ctx, cudaGetLastError(), "reduced setup");
   if (st != BEM_OK) return st;
   st = cholqr2_impl(ctx, reinterpret_cast<double*>(W), rows, rows, p, nullptr, cqw, s, 77);
@@ -616,7 +635,8 @@ extern "C" bem_status bem_solve_reduced(bem_ctx* ctx, const double* Bhat_dev, in
                                            cudaMemcpyHostToDevice, s), "reduced copy");
       if (st != BEM_OK) return st;
       reduced_residual_kernel<<<p, 256, 0, s>>>(reinterpret_cast<const double2*>(Bhat_dev), z, mu,
-                                                reinterpret_cast<const double2*>(Y_dev), N, nu, res);
+                                                reinterpret_cast<const double2*>(Y_dev), N, nu,
+                                                bnorm, res);
       ctx->launches++;
       st = cuda_check(ctx, cudaMemcpyAsync(hres.data(), res, p * sizeof(double),
                                            cudaMemcpyDeviceToHost, s), "reduced copy");
