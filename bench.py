@@ -64,6 +64,9 @@ def parse():
     p.add_argument("--operator", default="single", choices=["single", "neumann", "robin"],
                    help="boundary operator: single layer (default), double layer with its jump "
                         "(Neumann), or Robin 0.5 G + (1/2 I + K)")
+    p.add_argument("--twin-clusters", type=int, default=1, choices=[0, 1],
+                   help="units of one node (nu > 128): twin pairs on two-CTA clusters (1, "
+                        "default) or one node per CTA (0)")
     p.add_argument("--sweep-eval-split", action="store_true",
                    help="instead of the projection bench: time the fused kernel at every split "
                         "of its sines and cosines between the MUFU unit and the FMA-pipe "
@@ -200,10 +203,16 @@ def unit_nodes(N, nu, cap):
     return max(1, min(g, 512 // (2 * nup)))
 
 
-def mufu_seconds_per_entry(rates, N, G, twins):
+def mufu_seconds_per_entry(rates, N, G, twins, clusters=False):
     """MUFU time of one entry of A for all N nodes at the measured rates: per quadrature
     point (7) one ex2 per node, one sin and one cos per node or per twin pair evaluated
-    together (the pair in one unit, starting at an even slot), one rsqrt per unit."""
+    together (the pair in one unit, starting at an even slot), one rsqrt per unit.
+    clusters: units of one node whose twin pairs run on two-CTA clusters, each entry of a
+    pair evaluated once for both nodes (one rsqrt, sin and cos per pair)."""
+    if clusters:
+        phases = N - twins
+        return 7 * (N / rates["ex2"] + phases * (1 / rates["sin"] + 1 / rates["cos"] +
+                                                 1 / rates["rsqrt"]))
     paired = 0
     for P in range(twins):
         s0 = 2 * P
@@ -578,7 +587,7 @@ def eig_check(ctx, V_res, prec, spec, gold, precision):
         out["fp64_spot_check"] = {"lambda": [lam[k].real, lam[k].imag],
                                   "relres_fp64": float(r64[0]), "relres_double_fp32": float(rel[k])}
     if gold is not None:
-        out.update(eig_compare(lam, X.cpu().numpy(), rel, gold, spec, tol=1e-8))
+        out.update(eig_compare(lam, X.cpu().numpy(), rel, gold, spec, tol=1e-8, conv=1e-8))
     else:
         out["oracle"] = ("no stored oracle eigenvalues for this mesh (the CPU oracle's dense "
                          "FP64 solve is out of reach at this n); each pair is certified by "
@@ -602,6 +611,7 @@ def run_ours(args):
             "hmatrix": bem.PREC_HMATRIX}[args.precision]
     c = prob.contour
     ctx = bem.Context(local)
+    ctx.set_twin_clusters(bool(args.twin_clusters))
     stream = torch.cuda.current_stream()
     near_mode = args.near if args.near is not None else (1 if n > 10000 else 0)
     surrogate = None
@@ -704,6 +714,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel
     kern_avg = statistics.mean(kern_ms) if kern_ms else float("nan")
+    shape = ctx.mixed_shape()
     if prec == bem.PREC_HMATRIX:
         # low-rank far field: the leaf kernel (dense blocks and the U_b T_b products, one
         # launch per node) dominates. Its algorithmic work is one complex multiply-add per
@@ -737,14 +748,16 @@ def run_ours(args):
         rates = {k: ctx.microbench(k) for k in ("ex2", "sin", "cos", "rsqrt")}
         G = unit_nodes(N, nu, 0)
         twins = ctx.node_order()[1]
-        t_entry = mufu_seconds_per_entry(rates, N, G, twins) / N
+        clusters = shape["paired"]
+        t_entry = mufu_seconds_per_entry(rates, N, G, twins, clusters) / N
         roof = {"bound": "alu", "pipe": "mufu", "achieved": entries / (kern_avg * 1e-3),
                 "peak": 1.0 / t_entry, "unit": "entries/s",
                 "peak_source": "measured MUFU rates (bem_microbench): "
                                + ", ".join(f"{k} {v:.3e}/s" for k, v in rates.items())
                                + f"; per entry and quadrature point: ex2 per node, sin + cos "
                                f"per node or per twin pair ({twins} of {N // 2} possible), "
-                               f"rsqrt per {G} nodes"}
+                               + (f"rsqrt per twin pair (two-CTA clusters)" if clusters
+                                  else f"rsqrt per {G} nodes")}
     if roof.get("peak"):
         roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = measured_traffic(args.workload, args.precision)
@@ -789,6 +802,7 @@ def run_ours(args):
                    "contour": f"{c.kind} c={c.centre.real:g} a={c.a:g} b={c.b:g}",
                    "precision": args.precision,
                    "near_field": ["off", "8x8 rule", "surrogate network"][near_mode],
+                   "units": shape if prec == bem.PREC_MIXED else None,
                    "operator": args.operator,
                    "parallelism": f"replicas{world}", "l2": "flushed between steps (512 MB write)",
                    "wall_s_timed": wall},

@@ -430,6 +430,26 @@ bem_status bem_set_eval_split(bem_ctx* ctx, int poly_points);
  * refinement's own iterations always use double-FP32. BEM_EINVAL for other values.
  */
 bem_status bem_set_refine_residual(bem_ctx* ctx, int arith);
+/*
+ * Twin pairs across thread-block clusters in the fused mixed-precision kernel (scheduling;
+ * the paper has no counterpart). When one node's [Re Y | Im Y] accumulator fills a whole
+ * SM's tensor memory (bases of more than 128 columns) and the contour has twin nodes (equal
+ * real parts, as the conjugate nodes of a contour symmetric about the real axis), on != 0
+ * (the default) runs each twin pair on a cluster of two CTAs: each evaluates half of every
+ * 128 x 16 block of entries for both nodes, sharing the distance, sine and cosine of each
+ * quadrature point, and sends the other node's half to its partner through distributed
+ * shared memory. on = 0 keeps one node per CTA. The results agree to the rounding of the
+ * FP32 evaluation (the same operations on the same values, so normally bit for bit).
+ * Applies to later bem_project calls. BEM_EINVAL for other values than 0 and 1.
+ */
+bem_status bem_set_twin_clusters(bem_ctx* ctx, int on);
+/*
+ * Work decomposition of the last mixed-precision bem_project on this context: nodes per
+ * work unit (1..4), whether twin pairs ran on two-CTA clusters (0/1), column splits S and
+ * CTAs launched. Zeros before the first such projection. Any pointer may be NULL.
+ */
+bem_status bem_mixed_shape(const bem_ctx* ctx, int* nodes_per_unit, int* paired, int* splits,
+                           int64_t* ctas);
 
 /* Number of CUDA kernels this context has launched since creation (diagnostics). */
 int64_t bem_kernel_launches(const bem_ctx* ctx);

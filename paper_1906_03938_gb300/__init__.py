@@ -48,6 +48,8 @@ SIGNATURES = {
     "bem_set_wait_limit": (_I, [_P, ctypes.c_uint32]),
     "bem_set_eval_split": (_I, [_P, _I]),
     "bem_set_refine_residual": (_I, [_P, _I]),
+    "bem_set_twin_clusters": (_I, [_P, _I]),
+    "bem_mixed_shape": (_I, [_P, _P, _P, _P, _P]),
     "bem_set_operator": (_I, [_P, _D, _D, _D, _D]),
     "bem_set_hmatrix": (_I, [_P, _I, _D, _D, _I]),
     "bem_hmatrix_stats": (_I, [_P, _P, _P, _P, _P, _P]),
@@ -408,6 +410,21 @@ class Context:
     def set_refine_residual(self, arith=0):
         """Arithmetic of the residuals refine/solve report: 0 FP64, 1 double-FP32."""
         self._chk("bem_set_refine_residual", self._lib.bem_set_refine_residual(self._h, int(arith)))
+
+    def set_twin_clusters(self, on=True):
+        """Twin pairs on two-CTA clusters when a unit of the fused kernel holds one node
+        (bases of more than 128 columns); on by default."""
+        self._chk("bem_set_twin_clusters", self._lib.bem_set_twin_clusters(self._h, 1 if on else 0))
+
+    def mixed_shape(self):
+        """Work decomposition of the last mixed projection: nodes per unit, whether twin
+        pairs ran on clusters, column splits, CTAs launched."""
+        g, pr, sp = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        u = ctypes.c_int64(0)
+        self._chk("bem_mixed_shape", self._lib.bem_mixed_shape(
+            self._h, ctypes.byref(g), ctypes.byref(pr), ctypes.byref(sp), ctypes.byref(u)))
+        return {"nodes_per_unit": g.value, "paired": bool(pr.value), "splits": sp.value,
+                "ctas": u.value}
 
     def node_order(self):
         """(order, twins): the mixed kernel's node schedule (slot -> node) and the number

@@ -278,6 +278,23 @@ bem_status bem_set_eval_split(bem_ctx* ctx, int poly_points) {
   return BEM_OK;
 }
 
+bem_status bem_set_twin_clusters(bem_ctx* ctx, int on) {
+  if (!ctx || (on != 0 && on != 1))
+    return fail(ctx, BEM_EINVAL, "bem_set_twin_clusters: on must be 0 or 1");
+  ctx->twin_clusters = on;
+  return BEM_OK;
+}
+
+bem_status bem_mixed_shape(const bem_ctx* ctx, int* nodes_per_unit, int* paired, int* splits,
+                           int64_t* ctas) {
+  if (!ctx) return BEM_EINVAL;
+  if (nodes_per_unit) *nodes_per_unit = ctx->last_mixed_G;
+  if (paired) *paired = ctx->last_mixed_pair;
+  if (splits) *splits = ctx->last_mixed_S;
+  if (ctas) *ctas = ctx->last_mixed_ctas;
+  return BEM_OK;
+}
+
 bem_status bem_set_refine_residual(bem_ctx* ctx, int arith) {
   if (!ctx || (arith != 0 && arith != 1))
     return fail(ctx, BEM_EINVAL, "bem_set_refine_residual: arith must be 0 (FP64) or 1");

@@ -147,6 +147,11 @@ struct bem_ctx {
   // quadrature points per entry whose sine and cosine the fused kernel takes from the FMA-
   // pipe polynomials (bem_set_eval_split); -1: the measured default of the unit shape
   int poly_points = -1;
+  // twin pairs on two-CTA clusters when a unit holds one node (bem_set_twin_clusters)
+  int twin_clusters = 1;
+  // work decomposition of the last mixed projection (bem_mixed_shape)
+  int last_mixed_G = 0, last_mixed_pair = 0, last_mixed_S = 0;
+  int64_t last_mixed_ctas = 0;
   // arithmetic of the residuals bem_refine (and bem_solve) report: 0 FP64, 1 double-FP32
   int final_residual_arith = 0;
   // the boundary operator T = c_G G + c_H (1/2 I + K) (single layer by default)

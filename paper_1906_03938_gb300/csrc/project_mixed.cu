@@ -156,7 +156,8 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
 // at ag; self points at the staged self term of column l0 (that of l0 + 1 is kMaxG later).
 __device__ __forceinline__ void put_entries(f2_t sr2, f2_t si2, const float2* self, int64_t i,
                                             int64_t l0, int64_t n, unsigned char* ag,
-                                            bool scaled = false, float2 cf = float2()) {
+                                            bool scaled = false, float2 cf = float2(),
+                                            uint32_t plane_bytes = kPlaneBytes) {
   float re[2], im[2];
   f2split(sr2, re[0], re[1]);
   f2split(si2, im[0], im[1]);
@@ -183,10 +184,10 @@ __device__ __forceinline__ void put_entries(f2_t sr2, f2_t si2, const float2* se
                                 re[1] - __uint_as_float(hr & 0xFFFF0000u));
   const uint32_t li = pack_bf16(im[0] - __uint_as_float(hi << 16),
                                 im[1] - __uint_as_float(hi & 0xFFFF0000u));
-  *reinterpret_cast<uint32_t*>(ag + 0 * kPlaneBytes) = hr;
-  *reinterpret_cast<uint32_t*>(ag + 1 * kPlaneBytes) = lr;
-  *reinterpret_cast<uint32_t*>(ag + 2 * kPlaneBytes) = hi;
-  *reinterpret_cast<uint32_t*>(ag + 3 * kPlaneBytes) = li;
+  *reinterpret_cast<uint32_t*>(ag + 0 * plane_bytes) = hr;
+  *reinterpret_cast<uint32_t*>(ag + 1 * plane_bytes) = lr;
+  *reinterpret_cast<uint32_t*>(ag + 2 * plane_bytes) = hi;
+  *reinterpret_cast<uint32_t*>(ag + 3 * plane_bytes) = li;
 }
 
 // bounded wait that also watches the block's abort flag
@@ -631,6 +632,427 @@ __device__ __forceinline__ void mixed_apply_unit(const MixedParams& p, const int
 template <bool kOp, int kNP>
 __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p) {
   mixed_apply_unit<false, kOp, kNP>(p, blockIdx.x, kNoTmem);
+}
+
+// ---------------------------------------------------------------------------------------
+// Twin pairs across a cluster of two CTAs, for units of one node (bases of more than 128
+// columns, whose [Yr | Yi] accumulator fills the 512 TMEM columns of an SM).
+// CTA r of the cluster holds the accumulator of node r of a twin pair (two nodes with the
+// same FP32 real part, so the same phase Re(z) r at every quadrature point). Per 128 x 16
+// K-block each CTA evaluates columns 8 r .. 8 r + 7 for BOTH nodes: one rsqrt, one sine and
+// one cosine per quadrature point serve two nodes, against one node per point in the
+// unpaired unit. It writes node r's entries into its own A stage and the other node's into
+// an export buffer, which one bulk copy moves into the peer's A stage (distributed shared
+// memory, completing on the peer's xin mbarrier). A node's A stage is laid out as two
+// contiguous 8 KB column halves, each with the four planes (Re hi, Re lo, Im hi, Im lo) of
+// 128 rows x 8 columns, so that a half is one copy. Each MMA warp's commit arrives on the
+// stage-free barriers of both CTAs (multicast): a stage, its export buffer and the copy's
+// target are rewritten only once both CTAs' MMAs are done with them. Pairs whose first
+// slot carries no twin flag run unpaired, each CTA evaluating its own node (the second
+// idles when N is odd). Every wait is bounded; the CTAs leave the cluster together, after
+// any copy still addressed to them has landed.
+constexpr uint32_t kHalfPlane = kBM * (kBK / 2) * 2;   // one plane of a column half: 2 KB
+constexpr uint32_t kHalfBytes = 4 * kHalfPlane;        // the four planes of a half: 8 KB
+
+struct PairLayout {
+  uint32_t a_off, x_off, b_off, graw_off, row_off, col_off, self_off, bar_off, misc_off, total;
+  uint32_t b_stage_bytes;
+};
+__host__ __device__ inline PairLayout pair_layout(int nup) {
+  PairLayout L;
+  L.b_stage_bytes = 256u * nup;
+  L.a_off = 0;
+  L.x_off = L.a_off + kStages * 2 * kHalfBytes;
+  L.b_off = L.x_off + kStages * kHalfBytes;
+  L.graw_off = L.b_off + kStages * L.b_stage_bytes;
+  L.row_off = L.graw_off + kStages * kGeoBlockBytes;
+  L.col_off = L.row_off + kBM * 4 * 4;
+  L.self_off = L.col_off + kStages * kBK * 7 * 16;
+  L.bar_off = L.self_off + kStages * kBK * kMaxG * 8;
+  L.misc_off = L.bar_off + 16 * 8;   // 13 mbarriers (+3 pad)
+  L.total = L.misc_off + 16;         // tmem slot, abort flag, halves sent by the peer
+  return L;
+}
+
+template <bool kOp, int kNP>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+    mixed_pair_kernel(MixedParams p) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const PairLayout L = pair_layout(p.nup);
+  unsigned char* sA = smem + L.a_off;
+  unsigned char* sX = smem + L.x_off;
+  unsigned char* sB = smem + L.b_off;
+  float4* sRow = reinterpret_cast<float4*>(smem + L.row_off);
+  const float* sGraw = reinterpret_cast<const float*>(smem + L.graw_off);
+  float4* sColAll = reinterpret_cast<float4*>(smem + L.col_off);
+  float2* sSelfAll = reinterpret_cast<float2*>(smem + L.self_off);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
+  uint64_t* afull = bars;        // [2] this CTA's evaluation warps -> MMA
+  uint64_t* bfull = bars + 2;    // [2] basis bulk copy -> MMA
+  uint64_t* empty = bars + 4;    // [2] the MMAs (both CTAs' when paired) done with the stage
+  uint64_t* accfull = bars + 6;  // accumulator final
+  uint64_t* gfull = bars + 7;    // [2] column geometry / self terms staged -> evaluation
+  uint64_t* gready = bars + 9;   // [2] packed geometry bulk copy landed -> producer
+  uint64_t* xin = bars + 11;     // [2] the peer's half of the A stage landed -> MMA
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.misc_off);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.misc_off + 4);
+  volatile uint32_t* peer_sent = reinterpret_cast<volatile uint32_t*>(smem + L.misc_off + 8);
+
+  const int warp = threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  const uint32_t rank = cluster_ctarank();
+  const uint32_t peer = rank ^ 1u;
+
+  // cluster -> (row tile, pair of schedule slots, column split)
+  const int npairs = (p.N + 1) / 2;
+  const int cl = blockIdx.x / 2;
+  const int split = cl % p.S;
+  const int t = cl / p.S;
+  const int pr = t % npairs;
+  const int rt = t / npairs;
+  const int slot0 = 2 * pr;
+  const bool paired = (p.order[slot0] & kTwinBit) != 0 && slot0 + 1 < p.N;
+  const int myslot = slot0 + (int)rank;
+  const bool has_node = myslot < p.N;
+  const int64_t row0 = (int64_t)rt * kBM;
+  const int kb0 = (int)((int64_t)p.nK * split / p.S);
+  const int kb1 = (int)((int64_t)p.nK * (split + 1) / p.S);
+  const int nit = kb1 - kb0;
+  const int ev0 = paired ? slot0 : myslot;   // evaluated nodes: the pair, or this CTA's own
+  const int nev = paired ? 2 : 1;
+  const uint32_t acc_cols = 2u * p.nup;
+  uint32_t tmem_cols = 32;
+  while (tmem_cols < acc_cols) tmem_cols <<= 1;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&afull[s], kEvalThreads);
+      mbar_init(&bfull[s], 1);
+      mbar_init(&empty[s], paired ? 2 : 1);
+      mbar_init(&gfull[s], 32);
+      mbar_init(&gready[s], 1);
+      mbar_init(&xin[s], 1);
+    }
+    mbar_init(accfull, 1);
+    // the first round of each stage expects the peer's half before the peer can send it
+    if (paired)
+      for (int s = 0; s < kStages && s < nit; ++s) mbar_arrive_expect_tx(&xin[s], kHalfBytes);
+    *abort_flag = 0;
+    *peer_sent = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1 && has_node) {
+    tmem_alloc(tmem_slot, tmem_cols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();   // both CTAs' barriers exist before any copy or arrival reaches them
+  tc_fence_after();
+  if (!has_node) {      // the idle second CTA of an unpaired last slot (N odd)
+    cluster_sync_all();
+    cluster_sync_all();
+    return;
+  }
+  const uint32_t tmem_base = *tmem_slot;
+  int consumed = 0, sent = 0;   // (MMA thread) peer halves consumed, halves sent
+
+  if (warp == 0) {
+    // ---------------- producer: column geometry, self terms, basis planes ----------------
+    const int64_t i_org = row0 < p.n ? row0 : p.n - 1;
+    const double ox = p.cx[i_org], oy = p.cx[p.n + i_org], oz = p.cx[2 * p.n + i_org];
+    const float oxh = (float)ox, oyh = (float)oy, ozh = (float)oz;
+    const float oxl = (float)(ox - oxh), oyl = (float)(oy - oyh), ozl = (float)(oz - ozh);
+    for (int r = lane; r < kBM; r += 32) {
+      const int64_t i = row0 + r;
+      float4 v = make_float4(2.0f, 2.0f, 2.0f, 0.f);
+      if (i < p.n)
+        v = make_float4((float)(p.cx[i] - ox), (float)(p.cx[p.n + i] - oy),
+                        (float)(p.cx[2 * p.n + i] - oz), 1.f);
+      sRow[r] = v;
+    }
+    const uint32_t bset = 256u * p.nup;
+    int issued_g = 0, issued_b = 0;
+    for (int it = 0; it < nit; ++it) {
+      const int s = it % kStages;
+      const uint32_t par = (it / kStages) & 1;
+      const int kb = kb0 + it;
+      // the geometry once the evaluation warps are done with the stage
+      int ok = 1;
+      if (lane == 0) ok = wait_or_abort(&afull[s], par ^ 1, abort_flag, p.status, p.wait_limit);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      if (lane == 0) {
+        mbar_arrive_expect_tx(&gready[s], kGeoBlockBytes);
+        bulk_g2s(smem + L.graw_off + s * kGeoBlockBytes, p.pack32 + (size_t)kb * kBK * 64,
+                 kGeoBlockBytes, &gready[s]);
+      }
+      ++issued_g;
+      if (!wait_or_abort(&gready[s], par, abort_flag, p.status, p.wait_limit)) break;
+      const float* graw = sGraw + s * (kBK * 64);
+      float4* sCol = sColAll + s * (kBK * 7);
+      for (int x = lane; x < kBK * 7; x += 32) {
+        const int k = x / 7, q = x % 7;
+        const float4 hi = *reinterpret_cast<const float4*>(graw + k * 64 + 4 * q);
+        const float4 lo = *reinterpret_cast<const float4*>(graw + k * 64 + 28 + 4 * q);
+        sCol[x] = make_float4((hi.x - oxh) + (lo.x - oxl), (hi.y - oyh) + (lo.y - oyl),
+                              (hi.z - ozh) + (lo.z - ozl), hi.w);
+      }
+      float2* sSelf = sSelfAll + s * (kBK * kMaxG);
+      for (int x = lane; x < kBK * kMaxG; x += 32) {
+        const int k = x / kMaxG, g = x % kMaxG;
+        const int64_t l = (int64_t)kb * kBK + k;
+        float2 v = make_float2(0.f, 0.f);
+        if (l < p.n && g < nev && l >= row0 && l < row0 + kBM)
+          v = p.self32[(int64_t)(p.order[ev0 + g] & kNodeMask) * p.n + l];
+        sSelf[x] = v;
+      }
+      mbar_arrive(&gfull[s]);
+      // the basis planes once the MMAs are done with the stage
+      if (lane == 0) ok = wait_or_abort(&empty[s], par ^ 1, abort_flag, p.status, p.wait_limit);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      if (lane == 0) {
+        mbar_arrive_expect_tx(&bfull[s], bset);
+        bulk_g2s(sB + s * L.b_stage_bytes,
+                 reinterpret_cast<const unsigned char*>(p.Bp) + (size_t)kb * bset, bset, &bfull[s]);
+      }
+      ++issued_b;
+    }
+    if (lane == 0 && *abort_flag) {
+      for (int it = max(0, issued_b - kStages); it < issued_b; ++it)
+        mbar_wait(&bfull[it % kStages], (it / kStages) & 1, kWaitLimit);
+      for (int it = max(0, issued_g - kStages); it < issued_g; ++it)
+        mbar_wait(&gready[it % kStages], (it / kStages) & 1, kWaitLimit);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer (and sender of the evaluated half to the peer) ----------
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(kBM, 2 * p.C);
+      const int pa[6] = {0, 0, 1, 2, 2, 3};
+      const int pb[6] = {0, 1, 0, 2, 3, 2};
+      const uint32_t bplane = 2u * p.C * kBK * 2;
+      for (int it = 0; it < nit; ++it) {
+        const int s = it % kStages;
+        const uint32_t par = (it / kStages) & 1;
+        if (!wait_or_abort(&afull[s], par, abort_flag, p.status, p.wait_limit)) break;
+        if (*abort_flag) break;
+        if (paired) {
+          // this CTA's half of the other node's block -> the same half of the peer's stage
+          bulk_s2peer(mapa_shared(smem_u32(sA + s * 2 * kHalfBytes + rank * kHalfBytes), peer),
+                      sX + s * kHalfBytes, kHalfBytes, mapa_shared(smem_u32(&xin[s]), peer));
+          ++sent;
+          if (!wait_or_abort(&xin[s], par, abort_flag, p.status, p.wait_limit)) break;
+          ++consumed;
+          // the stage's next round expects its half before these MMAs release the peer
+          if (it + kStages < nit) mbar_arrive_expect_tx(&xin[s], kHalfBytes);
+        }
+        if (!wait_or_abort(&bfull[s], par, abort_flag, p.status, p.wait_limit)) break;
+        tc_fence_after();
+        const uint32_t a_base = smem_u32(sA + s * 2 * kHalfBytes);
+        const uint32_t b_base = smem_u32(sB + s * L.b_stage_bytes);
+        for (int c = 0; c < p.nchunks; ++c) {
+          const uint32_t d = tmem_base + c * 2 * p.C;
+#pragma unroll
+          for (int q = 0; q < 6; ++q) {
+            // column halves kHalfBytes apart along K, 8-row groups 128 bytes apart
+            const uint64_t ad = smem_desc(a_base + pa[q] * kHalfPlane, kHalfBytes, 128);
+            const uint64_t bd = smem_desc(b_base + (c * 4 + pb[q]) * bplane, 128, 256);
+            mma_bf16(d, ad, bd, idesc, (it == 0 && q == 0) ? 0u : 1u);
+          }
+        }
+        if (paired) mma_commit_mc(&empty[s], (uint16_t)0x3);
+        else mma_commit(&empty[s]);
+      }
+      mma_commit(accfull);
+      // the number of halves sent, read by the peer after the first end-of-unit sync
+      if (paired) st_peer_u32(mapa_shared(smem_u32((const void*)peer_sent), peer), (uint32_t)sent);
+    }
+  } else {
+    // ---------------- evaluation warps ----------------
+    const int e = warp - 2;
+    float kr[2], kmi[2], kim[2];
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      const int j = p.order[ev0 + (g < nev ? g : 0)] & kNodeMask;
+      kr[g] = (float)p.z[2 * j];
+      kmi[g] = (float)(-p.z[2 * j + 1]) * kLog2e;
+      kim[g] = (float)p.z[2 * j + 1];
+    }
+    const f2_t m1 = f2(-1.f, -1.f);
+    const f2_t cgr2 = f2((float)p.op.cgr, (float)p.op.cgr), cgi2 = f2((float)p.op.cgi, (float)p.op.cgi);
+    const f2_t chr2 = f2((float)p.op.chr, (float)p.op.chr), chi2 = f2((float)p.op.chi, (float)p.op.chi);
+    const f2_t nchi2 = f2(-(float)p.op.chi, -(float)p.op.chi);
+    const int r8 = lane / 4, kp = lane % 4;
+    const int row = 8 * e + r8;
+    const int64_t i = row0 + row;
+    // paired: the column half kg = rank for both nodes; unpaired: both halves, own node
+    const int kg_lo = paired ? (int)rank : 0;
+    const int kg_hi = paired ? (int)rank + 1 : 2;
+
+    for (int it = 0; it < nit; ++it) {
+      const int s = it % kStages;
+      const uint32_t par = (it / kStages) & 1;
+      const int kb = kb0 + it;
+      int free_ok = 1;
+      if (lane == 0) free_ok = wait_or_abort(&empty[s], par ^ 1, abort_flag, p.status, p.wait_limit);
+      free_ok = __shfl_sync(0xffffffffu, free_ok, 0);
+      const bool ready = wait_or_abort(&gfull[s], par, abort_flag, p.status, p.wait_limit) && free_ok;
+      const float4* sCol = sColAll + s * (kBK * 7);
+      const float2* sSelf = sSelfAll + s * (kBK * kMaxG);
+      unsigned char* a_stage = sA + s * 2 * kHalfBytes;
+      unsigned char* x_stage = sX + s * kHalfBytes;
+      const float4 xr = sRow[row];
+#pragma unroll 1
+      for (int kg = kg_lo; kg < (ready ? kg_hi : kg_lo); ++kg) {
+        const int k0 = 8 * kg + 2 * kp;
+        const int64_t l0 = (int64_t)kb * kBK + k0;
+        f2_t rr2[7], am2[7];
+        f2_t s2[kOp ? 7 : 1];
+        {
+          const float4* c0 = sCol + k0 * 7;
+          const float4* c1 = c0 + 7;
+          const f2_t xx = f2(xr.x, xr.x), xy = f2(xr.y, xr.y), xz = f2(xr.z, xr.z);
+          f2_t nnx = f2(0.f, 0.f), nny = nnx, nnz = nnx;
+          if (kOp) {
+            const float* gk = sGraw + s * (kBK * 64) + k0 * 64;
+            nnx = f2(-gk[56], -gk[64 + 56]);
+            nny = f2(-gk[57], -gk[64 + 57]);
+            nnz = f2(-gk[58], -gk[64 + 58]);
+          }
+#pragma unroll
+          for (int q = 0; q < 7; ++q) {
+            const float4 y0 = c0[q], y1 = c1[q];
+            const f2_t dx = sub2(xx, f2(y0.x, y1.x)), dy = sub2(xy, f2(y0.y, y1.y)),
+                       dz = sub2(xz, f2(y0.z, y1.z));
+            const f2_t r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+            float r20, r21;
+            f2split(r2, r20, r21);
+            const f2_t rs = f2(rsqrtf_mufu(r20), rsqrtf_mufu(r21));
+            rr2[q] = mul2(r2, rs);
+            am2[q] = mul2(f2(y0.w, y1.w), rs);
+            if (kOp)
+              s2[kOp ? q : 0] = mul2(fma2(dx, nnx, fma2(dy, nny, mul2(dz, nnz))), mul2(rs, rs));
+          }
+        }
+        const uint32_t off = e * 128 + r8 * 16 + kp * 4;   // within a column half
+        const float2* selfk = sSelf + k0 * kMaxG;
+        if (paired) {
+          f2_t sa = f2(0.f, 0.f), ia = f2(0.f, 0.f), sb = f2(0.f, 0.f), ib = f2(0.f, 0.f);
+          const f2_t kma = f2(kmi[0], kmi[0]), kmb = f2(kmi[1], kmi[1]);
+          const f2_t kr2 = f2(kr[0], kr[0]);
+#pragma unroll
+          for (int q = 0; q < 7; ++q) {
+            float e0, e1, e2, e3;
+            f2split(mul2(kma, rr2[q]), e0, e1);
+            f2split(mul2(kmb, rr2[q]), e2, e3);
+            f2_t aa = mul2(am2[q], f2(ex2f(e0), ex2f(e1)));
+            f2_t ab = mul2(am2[q], f2(ex2f(e2), ex2f(e3)));
+            const f2_t ph2 = mul2(kr2, rr2[q]);
+            f2_t cs, sn;
+            if (q < kNP) {
+              f2_t sg;
+              sincos_poly2(ph2, cs, sn, sg);
+              aa ^= sg;
+              ab ^= sg;
+            } else {
+              float p0, p1;
+              f2split(ph2, p0, p1);
+              cs = f2(cosf_mufu(p0), cosf_mufu(p1));
+              sn = f2(sinf_mufu(p0), sinf_mufu(p1));
+            }
+            if constexpr (kOp) {
+              op_acc2(sa, ia, aa, cs, sn, s2[q], ph2, mul2(f2(kim[0], kim[0]), rr2[q]), cgr2,
+                      cgi2, chr2, chi2, nchi2, m1);
+              op_acc2(sb, ib, ab, cs, sn, s2[q], ph2, mul2(f2(kim[1], kim[1]), rr2[q]), cgr2,
+                      cgi2, chr2, chi2, nchi2, m1);
+            } else {
+              sa = fma2(aa, cs, sa);
+              ia = fma2(aa, sn, ia);
+              sb = fma2(ab, cs, sb);
+              ib = fma2(ab, sn, ib);
+            }
+          }
+          // node `rank` into this CTA's stage, the other into the export buffer
+          unsigned char* own = a_stage + kg * kHalfBytes + off;
+          unsigned char* other = x_stage + off;
+          put_entries(sa, ia, selfk, i, l0, p.n, rank == 0 ? own : other, false, float2(),
+                      kHalfPlane);
+          put_entries(sb, ib, selfk + 1, i, l0, p.n, rank == 0 ? other : own, false, float2(),
+                      kHalfPlane);
+        } else {
+          f2_t sr2 = f2(0.f, 0.f), si2 = f2(0.f, 0.f);
+          const f2_t kmi2 = f2(kmi[0], kmi[0]), kr2 = f2(kr[0], kr[0]);
+#pragma unroll
+          for (int q = 0; q < 7; ++q) {
+            float e0, e1;
+            f2split(mul2(kmi2, rr2[q]), e0, e1);
+            f2_t a = mul2(am2[q], f2(ex2f(e0), ex2f(e1)));
+            const f2_t ph2 = mul2(kr2, rr2[q]);
+            f2_t cs, sn;
+            if (q < kNP) {
+              f2_t sg;
+              sincos_poly2(ph2, cs, sn, sg);
+              a ^= sg;
+            } else {
+              float p0, p1;
+              f2split(ph2, p0, p1);
+              cs = f2(cosf_mufu(p0), cosf_mufu(p1));
+              sn = f2(sinf_mufu(p0), sinf_mufu(p1));
+            }
+            if constexpr (kOp) {
+              op_acc2(sr2, si2, a, cs, sn, s2[q], ph2, mul2(f2(kim[0], kim[0]), rr2[q]), cgr2,
+                      cgi2, chr2, chi2, nchi2, m1);
+            } else {
+              sr2 = fma2(a, cs, sr2);
+              si2 = fma2(a, sn, si2);
+            }
+          }
+          put_entries(sr2, si2, selfk, i, l0, p.n, a_stage + kg * kHalfBytes + off, false,
+                      float2(), kHalfPlane);
+        }
+      }
+      fence_proxy_async_smem();
+      mbar_arrive(&afull[s]);
+      if (!ready) break;
+    }
+
+    // ---------------- epilogue: TMEM -> FP32 partial Y of this CTA's node ----------------
+    const bool ok = !*abort_flag && wait_or_abort(accfull, 0, abort_flag, p.status, p.wait_limit);
+    if (__all_sync(0xffffffffu, ok)) {
+      tc_fence_after();
+      const int quarter = warp % 4;
+      const int part = (warp - 2) / 4;
+      const int erow = quarter * 32 + lane;
+      const int64_t ei = row0 + erow;
+      const size_t slot = (size_t)split * p.N + (p.order[myslot] & kNodeMask);
+      for (uint32_t c0 = part * 16; c0 < acc_cols; c0 += 64) {
+        float v[16];
+        tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + c0, v);
+        float* dst = p.Yp + (slot * acc_cols + c0) * p.n_pad + ei;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) dst[(size_t)k * p.n_pad] = v[k];
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  // this CTA's MMAs, and with them their arrivals on the peer's barriers, complete (bounded)
+  if (warp == 1 && lane == 0) mbar_wait(accfull, 0, kWaitLimit);
+  cluster_sync_all();   // neither CTA issues anything more; peer_sent is visible
+  if (warp == 1) {
+    if (lane == 0 && paired) {
+      // halves the peer sent that an aborted loop did not consume: let them land (bounded)
+      const int sentp = min((int)*peer_sent, nit);
+      for (int it = consumed; it < sentp; ++it)
+        mbar_wait(&xin[it % kStages], (it / kStages) & 1, kWaitLimit);
+    }
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem_base, tmem_cols);
+  }
+  cluster_sync_all();   // no copy into either CTA is still in flight
 }
 
 // Node-summed form: Y = sum_j c_j A(z_j) X_j (the right-hand side of an inverse power
@@ -1147,6 +1569,8 @@ struct MixedPlan {
   int vtiles = 0;
   int64_t vparts = 0, rows_per_vpart = 0;
   bool vhy_tc = false;        // V^H Y on the tensor core (one column chunk)
+  bool pair = false;          // twin pairs across CTA clusters (mixed_pair_kernel)
+  uint32_t smem = 0;          // dynamic shared memory of the main kernel
   const double* V = nullptr;
   int64_t ldv = 0;
   float2* V32 = nullptr;
@@ -1157,9 +1581,10 @@ struct MixedPlan {
 
 // Parameters, scratch and FP32 self terms of one projection; S > 0 forces the number of
 // column splits (else the fewest that fill the device's waves), Gmax > 0 caps the nodes per
-// work unit (else up to kMaxG).
+// work unit (else up to kMaxG); allow_pair lets units of one node run as twin pairs across
+// two-CTA clusters when the contour has twin nodes.
 bem_status mixed_plan(bem_ctx* ctx, const double* V, int64_t ldv, int nu, int S, int Gmax,
-                      MixedPlan& plan, cudaStream_t s) {
+                      MixedPlan& plan, cudaStream_t s, bool allow_pair = false) {
   const int64_t n = ctx->geo.n;
   const int N = ctx->con.N;
   MixedParams& p = plan.p;
@@ -1179,9 +1604,12 @@ bem_status mixed_plan(bem_ctx* ctx, const double* V, int64_t ldv, int nu, int S,
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
   const int64_t rtiles = p.n_pad / kBM;
+  plan.pair = allow_pair && p.G == 1 && N >= 2 && ctx->con.twins > 0 && ctx->twin_clusters;
+  // CTAs per column split: one per (row tile, node), or two per (row tile, pair of slots)
+  const int64_t units1 = plan.pair ? rtiles * 2 * ((N + 1) / 2) : rtiles * p.nG;
   p.S = S > 0 ? std::max(1, std::min(S, std::max(1, p.nK / 4)))
-              : choose_splits(rtiles * p.nG, p.nK, std::max(1, sms));
-  plan.units = rtiles * p.nG * p.S;
+              : choose_splits(units1, p.nK, std::max(1, sms));
+  plan.units = units1 * p.S;
 
   // scratch: basis planes, FP32 partials, FP32 copy of V, V^H Y partials
   const size_t bp_bytes = (size_t)p.nK * 256 * p.nup;
@@ -1234,6 +1662,7 @@ bem_status mixed_plan(bem_ctx* ctx, const double* V, int64_t ldv, int nu, int S,
   plan.V32 = reinterpret_cast<float2*>(scr + v32_off);
   plan.vpart = reinterpret_cast<double*>(scr + vp_off);
   plan.L = smem_layout(p.G, p.nup);
+  plan.smem = plan.pair ? pair_layout(p.nup).total : plan.L.total;
   return BEM_OK;
 }
 
@@ -1289,6 +1718,17 @@ MixedKernel mixed_kernel(bool general, int np) {
   return general ? op[np] : single[np];
 }
 
+MixedKernel mixed_pair(bool general, int np) {
+  static const MixedKernel single[kPolyPointsMax + 1] = {
+      mixed_pair_kernel<false, 0>, mixed_pair_kernel<false, 1>, mixed_pair_kernel<false, 2>,
+      mixed_pair_kernel<false, 3>, mixed_pair_kernel<false, 4>};
+  static const MixedKernel op[kPolyPointsMax + 1] = {
+      mixed_pair_kernel<true, 0>, mixed_pair_kernel<true, 1>, mixed_pair_kernel<true, 2>,
+      mixed_pair_kernel<true, 3>, mixed_pair_kernel<true, 4>};
+  np = std::max(0, std::min(np, kPolyPointsMax));
+  return general ? op[np] : single[np];
+}
+
 // Polynomial points of a projection with G nodes per unit: the context's override, else the
 // measured default of the unit shape.
 int poly_points(const bem_ctx* ctx, int G) {
@@ -1301,6 +1741,11 @@ bem_status set_mixed_smem(bem_ctx* ctx, uint32_t bytes) {
   for (int np = 0; np <= kPolyPointsMax && st == BEM_OK; ++np)
     for (bool general : {false, true}) {
       st = cuda_check(ctx, cudaFuncSetAttribute(mixed_kernel(general, np),
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)bytes),
+                      "mixed kernel attribute");
+      if (st != BEM_OK) return st;
+      st = cuda_check(ctx, cudaFuncSetAttribute(mixed_pair(general, np),
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                 (int)bytes),
                       "mixed kernel attribute");
@@ -1540,13 +1985,18 @@ bem_status external_end(bem_ctx* ctx, ExtFrame& f, int nu, double* Bhat, double*
 bem_status project_mixed(bem_ctx* ctx, const double* V, int64_t ldv, int nu, double* Bhat,
                          double* AV, cudaStream_t s) {
   MixedPlan plan;
-  bem_status st = mixed_plan(ctx, V, ldv, nu, 0, 0, plan, s);
+  bem_status st = mixed_plan(ctx, V, ldv, nu, 0, 0, plan, s, true);
   if (st != BEM_OK) return st;
   mixed_pre(ctx, plan, s);
-  if ((st = set_mixed_smem(ctx, plan.L.total)) != BEM_OK) return st;
+  if ((st = set_mixed_smem(ctx, plan.smem)) != BEM_OK) return st;
+  const int np = poly_points(ctx, plan.pair ? 2 : plan.p.G);
+  ctx->last_mixed_G = plan.p.G;
+  ctx->last_mixed_pair = plan.pair ? 1 : 0;
+  ctx->last_mixed_S = plan.p.S;
+  ctx->last_mixed_ctas = plan.units;
   timing_begin(ctx, s);
-  mixed_kernel(!op_single(ctx->op), poly_points(ctx, plan.p.G))
-      <<<(unsigned)plan.units, kThreads, plan.L.total, s>>>(plan.p);
+  (plan.pair ? mixed_pair : mixed_kernel)(!op_single(ctx->op), np)
+      <<<(unsigned)plan.units, kThreads, plan.smem, s>>>(plan.p);
   timing_end(ctx, s);
   ctx->launches++;
   st = cuda_check(ctx, cudaGetLastError(), "mixed apply kernel");

@@ -57,8 +57,10 @@ def _check_against_oracle(ctx, bem, mesh, z, w, V):
         assert _relerr(Bh[j], w[j] * P[j]) < TOL
 
 
-@pytest.mark.parametrize("nu", [16, 72])
+@pytest.mark.parametrize("nu", [16, 72, 136])
 def test_stage_wait_runs_out_and_context_recovers(bem, nu):
+    """nu = 136: units of one node, twin pairs on two-CTA clusters; the partners leave the
+    cluster together after any half sent between them has landed."""
     ctx, mesh, z, w = _setup(bem)
     V = synth.complex_gaussian(mesh.n, nu, 9)
     ctx.set_wait_limit(0)
@@ -70,6 +72,8 @@ def test_stage_wait_runs_out_and_context_recovers(bem, nu):
     # the status word was cleared by the check; the default bound restores normal service
     ctx.set_wait_limit(1 << 24)
     _check_against_oracle(ctx, bem, mesh, z, w, V)
+    if nu > 128:
+        assert ctx.mixed_shape()["paired"]
     ctx.close()
 
 

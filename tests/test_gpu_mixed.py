@@ -170,3 +170,45 @@ def test_mixed_eval_split_matches_oracle(bem, case, np_poly):
     print(f"{case} poly points {np_poly}: worst rel err {worst:.2e}")
     assert worst < TOL
     ctx.close()
+
+
+@pytest.mark.parametrize("case", ["ellipse_nu136", "odd_circle_nu130", "robin_ellipse_nu200"])
+def test_twin_clusters_match_single_node_units(bem, case):
+    """Units of one node (nu > 128) run each twin pair on a two-CTA cluster, every entry of
+    a pair evaluated once for both nodes and half of each block sent to the partner through
+    distributed shared memory. The same FP32 operations act on the same values as with one
+    node per CTA, so the projected matrices and A(z_j)V agree bit for bit; both meet the
+    mixed path's bar against the oracle. A circle with an odd node count leaves its real
+    node unpaired (its cluster partner idles); the Robin operator covers the general kernel."""
+    op = None
+    if case == "ellipse_nu136":
+        mesh, spec, N, nu = synth.cube_grid(4), synth.ContourSpec("ellipse", 6.5 + 0j, 1.5, 0.4), 8, 136
+    elif case == "odd_circle_nu130":
+        mesh, spec, N, nu = synth.icosphere(2), synth.ContourSpec("circle", 5.0 + 0j, 1.0, 1.0), 5, 130
+    else:
+        mesh, spec, N, nu = synth.cube_grid(3), synth.ContourSpec("ellipse", 6.0 + 0j, 1.5, 0.4), 6, 200
+        op = (0.5 + 0.0j, 1.0 + 0.0j)
+    V = synth.complex_gaussian(mesh.n, nu, 41)
+    ctx = bem.Context(0)
+    ctx.set_mesh(mesh.xyz, mesh.tri)
+    z, w = ctx.set_contour(spec.kind, spec.centre, spec.a, spec.b, N)
+    if op is not None:
+        ctx.set_operator(*op)
+    twins = ctx.node_order()[1]
+    assert twins == N // 2
+    out = {}
+    for on in (True, False):
+        ctx.set_twin_clusters(on)
+        B, Y = ctx.project(_dev(V), bem.PREC_MIXED, AV=True)
+        ctx.check()
+        shape = ctx.mixed_shape()
+        assert shape["nodes_per_unit"] == 1 and shape["paired"] == on
+        out[on] = (B.cpu().numpy(), Y.cpu().numpy())
+    assert np.array_equal(out[True][0], out[False][0])
+    assert np.array_equal(out[True][1], out[False][1])
+    P, Yo = orr.project(mesh, z, V, op=op)
+    Bh, Yh = out[True]
+    worst = max(max(_relerr(Yh[j], Yo[j]), _relerr(Bh[j], w[j] * P[j])) for j in range(N))
+    print(f"{case}: twin clusters bit-identical to single-node units; worst rel err {worst:.2e}")
+    assert worst < TOL
+    ctx.close()
