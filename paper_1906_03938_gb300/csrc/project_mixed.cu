@@ -651,8 +651,17 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
 // slot carries no twin flag run unpaired, each CTA evaluating its own node (the second
 // idles when N is odd). Every wait is bounded; the CTAs leave the cluster together, after
 // any copy still addressed to them has landed.
+// Pipeline: three A stages (the evaluated blocks, their export buffers, column geometry)
+// and two basis stages (64 KB each at 256 columns), with the basis copies in a warp of
+// their own: the evaluation runs up to two K-blocks ahead of the MMAs, which hides the
+// exchange between the partners and the MMAs' own duration behind it (with two stages
+// the evaluation warps waited for a free stage a sixth of the time).
 constexpr uint32_t kHalfPlane = kBM * (kBK / 2) * 2;   // one plane of a column half: 2 KB
 constexpr uint32_t kHalfBytes = 4 * kHalfPlane;        // the four planes of a half: 8 KB
+constexpr int kPA = 3;                                 // A stages
+constexpr int kPB = 2;                                 // basis stages
+constexpr int kPairWarps = 3 + kEvalWarps;   // geometry producer, MMA, basis producer, evaluation
+constexpr int kPairThreads = 32 * kPairWarps;
 
 struct PairLayout {
   uint32_t a_off, x_off, b_off, graw_off, row_off, col_off, self_off, bar_off, misc_off, total;
@@ -662,20 +671,20 @@ __host__ __device__ inline PairLayout pair_layout(int nup) {
   PairLayout L;
   L.b_stage_bytes = 256u * nup;
   L.a_off = 0;
-  L.x_off = L.a_off + kStages * 2 * kHalfBytes;
-  L.b_off = L.x_off + kStages * kHalfBytes;
-  L.graw_off = L.b_off + kStages * L.b_stage_bytes;
-  L.row_off = L.graw_off + kStages * kGeoBlockBytes;
+  L.x_off = L.a_off + kPA * 2 * kHalfBytes;
+  L.b_off = L.x_off + kPA * kHalfBytes;
+  L.graw_off = L.b_off + kPB * L.b_stage_bytes;
+  L.row_off = L.graw_off + kPA * kGeoBlockBytes;
   L.col_off = L.row_off + kBM * 4 * 4;
-  L.self_off = L.col_off + kStages * kBK * 7 * 16;
-  L.bar_off = L.self_off + kStages * kBK * kMaxG * 8;
-  L.misc_off = L.bar_off + 16 * 8;   // 13 mbarriers (+3 pad)
+  L.self_off = L.col_off + kPA * kBK * 7 * 16;
+  L.bar_off = L.self_off + kPA * kBK * kMaxG * 8;
+  L.misc_off = L.bar_off + 24 * 8;   // 20 mbarriers (+4 pad)
   L.total = L.misc_off + 16;         // tmem slot, abort flag, halves sent by the peer
   return L;
 }
 
 template <bool kOp, int kNP>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
     mixed_pair_kernel(MixedParams p) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const PairLayout L = pair_layout(p.nup);
@@ -687,13 +696,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   float4* sColAll = reinterpret_cast<float4*>(smem + L.col_off);
   float2* sSelfAll = reinterpret_cast<float2*>(smem + L.self_off);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
-  uint64_t* afull = bars;        // [2] this CTA's evaluation warps -> MMA
-  uint64_t* bfull = bars + 2;    // [2] basis bulk copy -> MMA
-  uint64_t* empty = bars + 4;    // [2] the MMAs (both CTAs' when paired) done with the stage
-  uint64_t* accfull = bars + 6;  // accumulator final
-  uint64_t* gfull = bars + 7;    // [2] column geometry / self terms staged -> evaluation
-  uint64_t* gready = bars + 9;   // [2] packed geometry bulk copy landed -> producer
-  uint64_t* xin = bars + 11;     // [2] the peer's half of the A stage landed -> MMA
+  uint64_t* afull = bars;         // [kPA] this CTA's evaluation warps -> MMA
+  uint64_t* empty = bars + 3;     // [kPA] the MMAs (both CTAs' when paired) done with the A stage
+  uint64_t* gfull = bars + 6;     // [kPA] column geometry / self terms staged -> evaluation
+  uint64_t* gready = bars + 9;    // [kPA] packed geometry bulk copy landed -> producer
+  uint64_t* xin = bars + 12;      // [kPA] the peer's half of the A stage landed -> MMA
+  uint64_t* bfull = bars + 15;    // [kPB] basis bulk copy -> MMA
+  uint64_t* bempty = bars + 17;   // [kPB] this CTA's MMAs done with the basis stage
+  uint64_t* accfull = bars + 19;  // accumulator final
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.misc_off);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.misc_off + 4);
   volatile uint32_t* peer_sent = reinterpret_cast<volatile uint32_t*>(smem + L.misc_off + 8);
@@ -725,18 +735,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   while (tmem_cols < acc_cols) tmem_cols <<= 1;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < kPA; ++s) {
       mbar_init(&afull[s], kEvalThreads);
-      mbar_init(&bfull[s], 1);
       mbar_init(&empty[s], paired ? 2 : 1);
       mbar_init(&gfull[s], 32);
       mbar_init(&gready[s], 1);
       mbar_init(&xin[s], 1);
     }
+    for (int s = 0; s < kPB; ++s) {
+      mbar_init(&bfull[s], 1);
+      mbar_init(&bempty[s], 1);
+    }
     mbar_init(accfull, 1);
     // the first round of each stage expects the peer's half before the peer can send it
     if (paired)
-      for (int s = 0; s < kStages && s < nit; ++s) mbar_arrive_expect_tx(&xin[s], kHalfBytes);
+      for (int s = 0; s < kPA && s < nit; ++s) mbar_arrive_expect_tx(&xin[s], kHalfBytes);
     *abort_flag = 0;
     *peer_sent = 0;
     fence_mbar_init();
@@ -758,7 +771,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   int consumed = 0, sent = 0;   // (MMA thread) peer halves consumed, halves sent
 
   if (warp == 0) {
-    // ---------------- producer: column geometry, self terms, basis planes ----------------
+    // ---------------- geometry producer: column geometry and self terms per A stage ------
     const int64_t i_org = row0 < p.n ? row0 : p.n - 1;
     const double ox = p.cx[i_org], oy = p.cx[p.n + i_org], oz = p.cx[2 * p.n + i_org];
     const float oxh = (float)ox, oyh = (float)oy, ozh = (float)oz;
@@ -771,11 +784,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                         (float)(p.cx[2 * p.n + i] - oz), 1.f);
       sRow[r] = v;
     }
-    const uint32_t bset = 256u * p.nup;
-    int issued_g = 0, issued_b = 0;
+    int issued_g = 0;
     for (int it = 0; it < nit; ++it) {
-      const int s = it % kStages;
-      const uint32_t par = (it / kStages) & 1;
+      const int s = it % kPA;
+      const uint32_t par = (it / kPA) & 1;
       const int kb = kb0 + it;
       // the geometry once the evaluation warps are done with the stage
       int ok = 1;
@@ -808,22 +820,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         sSelf[x] = v;
       }
       mbar_arrive(&gfull[s]);
-      // the basis planes once the MMAs are done with the stage
-      if (lane == 0) ok = wait_or_abort(&empty[s], par ^ 1, abort_flag, p.status, p.wait_limit);
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) break;
-      if (lane == 0) {
+    }
+    if (lane == 0 && *abort_flag)   // let geometry copies in flight land (bounded)
+      for (int it = max(0, issued_g - kPA); it < issued_g; ++it)
+        mbar_wait(&gready[it % kPA], (it / kPA) & 1, kWaitLimit);
+  } else if (warp == 2) {
+    // ---------------- basis producer: one K-block of the basis planes per basis stage ----
+    if (lane == 0) {
+      const uint32_t bset = 256u * p.nup;
+      int issued_b = 0;
+      for (int it = 0; it < nit; ++it) {
+        const int s = it % kPB;
+        const uint32_t par = (it / kPB) & 1;
+        if (!wait_or_abort(&bempty[s], par ^ 1, abort_flag, p.status, p.wait_limit)) break;
         mbar_arrive_expect_tx(&bfull[s], bset);
         bulk_g2s(sB + s * L.b_stage_bytes,
-                 reinterpret_cast<const unsigned char*>(p.Bp) + (size_t)kb * bset, bset, &bfull[s]);
+                 reinterpret_cast<const unsigned char*>(p.Bp) + (size_t)(kb0 + it) * bset, bset,
+                 &bfull[s]);
+        ++issued_b;
       }
-      ++issued_b;
-    }
-    if (lane == 0 && *abort_flag) {
-      for (int it = max(0, issued_b - kStages); it < issued_b; ++it)
-        mbar_wait(&bfull[it % kStages], (it / kStages) & 1, kWaitLimit);
-      for (int it = max(0, issued_g - kStages); it < issued_g; ++it)
-        mbar_wait(&gready[it % kStages], (it / kStages) & 1, kWaitLimit);
+      if (*abort_flag)   // let basis copies in flight land (bounded)
+        for (int it = max(0, issued_b - kPB); it < issued_b; ++it)
+          mbar_wait(&bfull[it % kPB], (it / kPB) & 1, kWaitLimit);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer (and sender of the evaluated half to the peer) ----------
@@ -833,8 +851,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       const int pb[6] = {0, 1, 0, 2, 3, 2};
       const uint32_t bplane = 2u * p.C * kBK * 2;
       for (int it = 0; it < nit; ++it) {
-        const int s = it % kStages;
-        const uint32_t par = (it / kStages) & 1;
+        const int s = it % kPA;
+        const uint32_t par = (it / kPA) & 1;
+        const int sb = it % kPB;
+        const uint32_t parb = (it / kPB) & 1;
         if (!wait_or_abort(&afull[s], par, abort_flag, p.status, p.wait_limit)) break;
         if (*abort_flag) break;
         if (paired) {
@@ -845,12 +865,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
           if (!wait_or_abort(&xin[s], par, abort_flag, p.status, p.wait_limit)) break;
           ++consumed;
           // the stage's next round expects its half before these MMAs release the peer
-          if (it + kStages < nit) mbar_arrive_expect_tx(&xin[s], kHalfBytes);
+          if (it + kPA < nit) mbar_arrive_expect_tx(&xin[s], kHalfBytes);
         }
-        if (!wait_or_abort(&bfull[s], par, abort_flag, p.status, p.wait_limit)) break;
+        if (!wait_or_abort(&bfull[sb], parb, abort_flag, p.status, p.wait_limit)) break;
         tc_fence_after();
         const uint32_t a_base = smem_u32(sA + s * 2 * kHalfBytes);
-        const uint32_t b_base = smem_u32(sB + s * L.b_stage_bytes);
+        const uint32_t b_base = smem_u32(sB + sb * L.b_stage_bytes);
         for (int c = 0; c < p.nchunks; ++c) {
           const uint32_t d = tmem_base + c * 2 * p.C;
 #pragma unroll
@@ -863,6 +883,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         }
         if (paired) mma_commit_mc(&empty[s], (uint16_t)0x3);
         else mma_commit(&empty[s]);
+        mma_commit(&bempty[sb]);
       }
       mma_commit(accfull);
       // the number of halves sent, read by the peer after the first end-of-unit sync
@@ -870,7 +891,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     }
   } else {
     // ---------------- evaluation warps ----------------
-    const int e = warp - 2;
+    const int e = warp - 3;
     float kr[2], kmi[2], kim[2];
 #pragma unroll
     for (int g = 0; g < 2; ++g) {
@@ -891,8 +912,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const int kg_hi = paired ? (int)rank + 1 : 2;
 
     for (int it = 0; it < nit; ++it) {
-      const int s = it % kStages;
-      const uint32_t par = (it / kStages) & 1;
+      const int s = it % kPA;
+      const uint32_t par = (it / kPA) & 1;
       const int kb = kb0 + it;
       int free_ok = 1;
       if (lane == 0) free_ok = wait_or_abort(&empty[s], par ^ 1, abort_flag, p.status, p.wait_limit);
@@ -1021,8 +1042,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const bool ok = !*abort_flag && wait_or_abort(accfull, 0, abort_flag, p.status, p.wait_limit);
     if (__all_sync(0xffffffffu, ok)) {
       tc_fence_after();
-      const int quarter = warp % 4;
-      const int part = (warp - 2) / 4;
+      const int quarter = warp % 4;   // TMEM lanes this warp may read
+      const int part = (warp - 3) / 4;
       const int erow = quarter * 32 + lane;
       const int64_t ei = row0 + erow;
       const size_t slot = (size_t)split * p.N + (p.order[myslot] & kNodeMask);
@@ -1046,7 +1067,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       // halves the peer sent that an aborted loop did not consume: let them land (bounded)
       const int sentp = min((int)*peer_sent, nit);
       for (int it = consumed; it < sentp; ++it)
-        mbar_wait(&xin[it % kStages], (it / kStages) & 1, kWaitLimit);
+        mbar_wait(&xin[it % kPA], (it / kPA) & 1, kWaitLimit);
     }
     __syncwarp();
     tc_fence_after();
@@ -1996,7 +2017,7 @@ bem_status project_mixed(bem_ctx* ctx, const double* V, int64_t ldv, int nu, dou
   ctx->last_mixed_ctas = plan.units;
   timing_begin(ctx, s);
   (plan.pair ? mixed_pair : mixed_kernel)(!op_single(ctx->op), np)
-      <<<(unsigned)plan.units, kThreads, plan.smem, s>>>(plan.p);
+      <<<(unsigned)plan.units, plan.pair ? kPairThreads : kThreads, plan.smem, s>>>(plan.p);
   timing_end(ctx, s);
   ctx->launches++;
   st = cuda_check(ctx, cudaGetLastError(), "mixed apply kernel");
