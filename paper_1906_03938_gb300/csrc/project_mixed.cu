@@ -20,8 +20,8 @@
 //    is bounded and a timeout aborts the block cleanly with an error status);
 //  * the evaluation warps finally read the accumulators from TMEM and store the FP32
 //    partial Y of the unit.
-// mixed_vhy_tc_kernel (one column chunk: BF16x3 on the tensor core, reading the same basis
-// planes) or mixed_vhy_part_kernel (FP32 CUDA cores, nu > 128), then mixed_vhy_reduce_kernel,
+// mixed_vhy_tc_kernel (BF16x3 on the tensor core, reading the same basis planes, one CTA
+// per node, row part and quadrant of column chunks), then mixed_vhy_reduce_kernel,
 // form Bhat_j = w_j V^H (sum over column splits of Y_j) with a fixed summation order.
 #include <cuda_bf16.h>
 #include <math.h>
@@ -1170,112 +1170,9 @@ __global__ void prep_basis_planes_kernel(const double* __restrict__ V, int64_t l
     }
 }
 
-// Partial products P_r,j = V^H Y_j over the row range of part r, Y_j = sum over column
-// splits of the FP32 partials: FP32 products of the FP32 copy of V summed over 32-row
-// chunks, chunk sums added with compensation (the inputs carry ~1e-5 relative error, so
-// FP32 products lose nothing; the FP64 pipe of this GPU is ~70x slower than its FP32 pipe).
-constexpr int kT = 64;    // output tile (64 x 64 of the nu x nu matrix)
-constexpr int kTR = 32;   // rows per chunk
-__global__ void __launch_bounds__(256, 2)
-mixed_vhy_part_kernel(const float2* __restrict__ V32, int nu, int64_t n, int n_pad,
-                      int N, int S, int acc_cols, int C, const float* __restrict__ Yp,
-                      int64_t rows_per_part, double* __restrict__ part) {
-  __shared__ float2 sX[kTR][kT + 1];   // +1: the row-major fill below is then 2-way at most
-  __shared__ float2 sY[kTR][kT + 1];
-  const int tiles_a = (nu + kT - 1) / kT;
-  const int ta = blockIdx.x % tiles_a, tb = blockIdx.x / tiles_a;
-  const int j = blockIdx.y;
-  const int64_t r_begin = (int64_t)blockIdx.z * rows_per_part;
-  const int64_t r_end = min(n, r_begin + rows_per_part);
-  const int tid = threadIdx.x;
-  const int oa = tid % 16, ob = tid / 16;   // outputs (oa + 16 i, ob + 16 m)
-  float2 acc[4][4], comp[4][4];   // running sums of the chunk sums and their compensation
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int m = 0; m < 4; ++m) acc[i][m] = comp[i][m] = make_float2(0.f, 0.f);
-  for (int64_t r0 = r_begin; r0 < r_end; r0 += kTR) {
-    __syncthreads();
-    for (int x = tid; x < kTR * kT; x += 256) {
-      const int rr = x % kTR, cc = x / kTR;
-      const int64_t r = r0 + rr;
-      const int a = ta * kT + cc;
-      sX[rr][cc] = (r < r_end && a < nu) ? V32[(int64_t)a * n + r] : make_float2(0.f, 0.f);
-    }
-    // Y rows four at a time (rows_per_part and the chunk start are multiples of 4; rows
-    // past n are the zero padding rows of the last tile, rows past r_end are masked)
-    for (int x = tid; x < (kTR / 4) * kT; x += 256) {
-      const int q4 = x % (kTR / 4), cc = x / (kTR / 4);
-      const int64_t r = r0 + 4 * q4;
-      const int b = tb * kT + cc;
-      float4 yr = make_float4(0.f, 0.f, 0.f, 0.f), yi = yr;
-      if (r < r_end && b < nu) {
-        const int colr = (b / C) * 2 * C + (b % C);
-        for (int s = 0; s < S; ++s) {
-          const float* base = Yp + ((size_t)s * N + j) * acc_cols * (size_t)n_pad;
-          const float4 a4 = *reinterpret_cast<const float4*>(base + (size_t)colr * n_pad + r);
-          const float4 b4 = *reinterpret_cast<const float4*>(base + (size_t)(colr + C) * n_pad + r);
-          yr.x += a4.x; yr.y += a4.y; yr.z += a4.z; yr.w += a4.w;
-          yi.x += b4.x; yi.y += b4.y; yi.z += b4.z; yi.w += b4.w;
-        }
-      }
-      sY[4 * q4 + 0][cc] = (r + 0 < r_end) ? make_float2(yr.x, yi.x) : make_float2(0.f, 0.f);
-      sY[4 * q4 + 1][cc] = (r + 1 < r_end) ? make_float2(yr.y, yi.y) : make_float2(0.f, 0.f);
-      sY[4 * q4 + 2][cc] = (r + 2 < r_end) ? make_float2(yr.z, yi.z) : make_float2(0.f, 0.f);
-      sY[4 * q4 + 3][cc] = (r + 3 < r_end) ? make_float2(yr.w, yi.w) : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    float2 c[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int m = 0; m < 4; ++m) c[i][m] = make_float2(0.f, 0.f);
-#pragma unroll 4
-    for (int rr = 0; rr < kTR; ++rr) {
-      float2 x[4], y[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) x[i] = sX[rr][oa + 16 * i];
-#pragma unroll
-      for (int m = 0; m < 4; ++m) y[m] = sY[rr][ob + 16 * m];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {   // conj(x) * y
-          c[i][m].x = fmaf(x[i].x, y[m].x, fmaf(x[i].y, y[m].y, c[i][m].x));
-          c[i][m].y = fmaf(x[i].x, y[m].y, fmaf(-x[i].y, y[m].x, c[i][m].y));
-        }
-    }
-    // compensated (Kahan) addition of the chunk sums: the error stays at FP32 rounding
-    // however many chunks a part holds
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const float yx = c[i][m].x - comp[i][m].x, yy = c[i][m].y - comp[i][m].y;
-        const float tx = acc[i][m].x + yx, ty = acc[i][m].y + yy;
-        comp[i][m].x = (tx - acc[i][m].x) - yx;
-        comp[i][m].y = (ty - acc[i][m].y) - yy;
-        acc[i][m].x = tx;
-        acc[i][m].y = ty;
-      }
-  }
-  double2* P = reinterpret_cast<double2*>(part) + ((int64_t)blockIdx.z * N + j) * nu * nu;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int a = ta * kT + oa + 16 * i;
-    if (a >= nu) continue;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const int b = tb * kT + ob + 16 * m;
-      if (b < nu)
-        P[(int64_t)b * nu + a] = make_double2((double)acc[i][m].x - (double)comp[i][m].x,
-                                              (double)acc[i][m].y - (double)comp[i][m].y);
-    }
-  }
-}
-
-// Partial products P_r,j = V^H Y_j on the tensor core (one chunk of columns, nup <= 128,
-// C = nup): a CTA takes node j and the rows of part r, 32 rows per stage.
+// Partial products P_r,j = V^H Y_j on the tensor core: a CTA takes node j, the rows of
+// part r (32 rows per stage) and one quadrant (ca, cb) of P_j: the basis columns of chunk ca
+// against the Y columns of chunk cb (C columns each; one quadrant when nup <= 128).
 //  * the A operand is the prepared basis planes [Vr | Vi] (hi and lo) of the main kernel,
 //    split into two M = 128 halves (Vr rows in half 0, Vi rows in half 1, zero rows above C)
 //    so that each output's real and imaginary combinations meet in one TMEM lane;
@@ -1316,7 +1213,7 @@ __host__ __device__ inline VhyLayout vhy_layout(int C) {
 template <int TPT>
 __global__ void __launch_bounds__(kVThreads, 2)
 mixed_vhy_tc_kernel(const __nv_bfloat16* __restrict__ Bp, const float* __restrict__ Yp,
-                    int64_t n, int n_pad, int nu, int C, int N, int nK, int slices,
+                    int64_t n, int n_pad, int nu, int C, int nchunks, int N, int nK, int slices,
                     int64_t rows_per_part, double* __restrict__ part, int* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const VhyLayout L = vhy_layout(C);
@@ -1333,8 +1230,11 @@ mixed_vhy_tc_kernel(const __nv_bfloat16* __restrict__ Bp, const float* __restric
   const int64_t r_end = min(n, r_begin + rows_per_part);
   const int nst = (int)((r_end - r_begin + kVRows - 1) / kVRows);
   const int twoC = 2 * C;
-  const uint32_t plane_bytes = (uint32_t)twoC * 32;   // one prepared plane of a K-block
+  const uint32_t plane_bytes = (uint32_t)twoC * 32;   // one prepared plane of a chunk and K-block
   const uint32_t half_bytes = (uint32_t)C * 32;       // its Vr or Vi rows
+  const int ca = (int)blockIdx.z / nchunks;           // basis chunk (rows of P_j)
+  const int cb = (int)blockIdx.z % nchunks;           // Y chunk (columns of P_j)
+  const int acc_cols = nchunks * twoC;                // FP32 partial columns per node
 
   // zero the A blocks once: rows C..127 of each half stay zero (the copies fill rows < C)
   for (uint32_t x = threadIdx.x; x < kVStages * L.a_stage / 16; x += blockDim.x)
@@ -1372,8 +1272,10 @@ mixed_vhy_tc_kernel(const __nv_bfloat16* __restrict__ Bp, const float* __restric
         mbar_arrive_expect_tx(&afull[st], (uint32_t)nkb * 4u * half_bytes);
         unsigned char* a_st = smem + st * L.a_stage;
         for (int kb = 0; kb < nkb; ++kb) {
+          // K-block sets of nchunks x 4 planes; chunk ca's [Vr|Vi] hi and lo planes
           const unsigned char* src = reinterpret_cast<const unsigned char*>(Bp) +
-                                     (size_t)(kbg0 + kb) * (2u * plane_bytes * 2u);
+                                     (size_t)(kbg0 + kb) * (4u * plane_bytes * nchunks) +
+                                     (size_t)ca * 4u * plane_bytes;
           for (int pl = 0; pl < 2; ++pl)
             for (int h = 0; h < 2; ++h)
               bulk_g2s(a_st + ((kb * 2 + pl) * 2 + h) * kVHalfBytes,
@@ -1447,8 +1349,8 @@ mixed_vhy_tc_kernel(const __nv_bfloat16* __restrict__ Bp, const float* __restric
             if (s0 + g2 < slices && t < tasks) {
               const int nn = t % twoC, g = t / twoC;
               const float* src =
-                  Yp + (((size_t)(s0 + g2) * N + j) * (size_t)twoC + nn) * (size_t)n_pad + r0 +
-                  8 * g;
+                  Yp + (((size_t)(s0 + g2) * N + j) * (size_t)acc_cols + (size_t)cb * twoC + nn) *
+                           (size_t)n_pad + r0 + 8 * g;
               u[g2][q][0] = *reinterpret_cast<const float4*>(src);
               u[g2][q][1] = *reinterpret_cast<const float4*>(src + 4);
             }
@@ -1493,7 +1395,7 @@ mixed_vhy_tc_kernel(const __nv_bfloat16* __restrict__ Bp, const float* __restric
     // ---------------- epilogue: TMEM -> FP64 partial ----------------
     const bool ok = !*abort_flag && wait_or_abort(accfull, 0, abort_flag, status);
     const int quarter = warp % 4;
-    const int a = quarter * 32 + lane;
+    const int a = ca * C + quarter * 32 + lane;   // row of P_j
     if (__all_sync(0xffffffffu, ok) && quarter * 32 < C) {
       tc_fence_after();
       const int side = (warp - 2) / 4;   // two warps per lane quarter split the columns
@@ -1508,7 +1410,7 @@ mixed_vhy_tc_kernel(const __nv_bfloat16* __restrict__ Bp, const float* __restric
         if (a < nu) {
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
-            const int b = b0 + k;
+            const int b = cb * C + b0 + k;   // column of P_j
             if (b < nu)
               P[(int64_t)b * nu + a] = make_double2((double)d0r[k] + (double)d1i[k],
                                                     (double)d0i[k] - (double)d1r[k]);
@@ -1587,9 +1489,7 @@ struct MixedPlan {
   int64_t units = 0;          // work units of the main kernel
   int slices = 0;             // slices of the FP32 partials: the S column splits, then the
                               // near-field correction when it is active
-  int vtiles = 0;
   int64_t vparts = 0, rows_per_vpart = 0;
-  bool vhy_tc = false;        // V^H Y on the tensor core (one column chunk)
   bool pair = false;          // twin pairs across CTA clusters (mixed_pair_kernel)
   uint32_t smem = 0;          // dynamic shared memory of the main kernel
   const double* V = nullptr;
@@ -1638,21 +1538,13 @@ bem_status mixed_plan(bem_ctx* ctx, const double* V, int64_t ldv, int nu, int S,
   const size_t yp_off = (bp_bytes + 255) / 256 * 256;
   plan.slices = p.S + (near_active(ctx) ? 1 : 0);
   const size_t yp_bytes = (size_t)plan.slices * N * acc_cols * p.n_pad * sizeof(float);
-  // V^H Y partials: enough row ranges to fill the device, at least 128 rows each
-  plan.vtiles = ((nu + kT - 1) / kT) * ((nu + kT - 1) / kT);
-  int64_t vparts = std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128,
-                                                          (4 * (int64_t)sms + plan.vtiles * N - 1) /
-                                                              ((int64_t)plan.vtiles * N)));
-  plan.rows_per_vpart = ((n + vparts - 1) / vparts + kTR - 1) / kTR * kTR;
-  plan.vparts = (n + plan.rows_per_vpart - 1) / plan.rows_per_vpart;
-  plan.vhy_tc = p.nchunks == 1;
-  if (plan.vhy_tc) {
-    // one wave of (node, row part) CTAs, 32-row stages
-    // two CTAs per SM when their shared memory and TMEM columns both fit twice
+  // V^H Y partials on the tensor core: one wave of (node, row part, chunk quadrant) CTAs,
+  // 32-row stages; two CTAs per SM when their shared memory and TMEM columns both fit twice
+  {
     const VhyLayout VL = vhy_layout(p.C);
     const int per_sm = (VL.total <= 110 * 1024 && VL.tmem_cols <= 256) ? 2 : 1;
     const int64_t slots = (int64_t)std::max(1, sms) * per_sm;
-    const int64_t tparts = std::max<int64_t>(1, slots / N);
+    const int64_t tparts = std::max<int64_t>(1, slots / ((int64_t)N * p.nchunks * p.nchunks));
     plan.rows_per_vpart = ((n + tparts - 1) / tparts + kVRows - 1) / kVRows * kVRows;
     plan.vparts = (n + plan.rows_per_vpart - 1) / plan.rows_per_vpart;
   }
@@ -1700,17 +1592,14 @@ void mixed_pre(bem_ctx* ctx, const MixedPlan& plan, cudaStream_t s) {
 void mixed_post(bem_ctx* ctx, const MixedPlan& plan, double* Bhat, double* AV, cudaStream_t s) {
   const MixedParams& p = plan.p;
   const int acc_cols = 2 * p.nup;
-  if (plan.vhy_tc) {
-    const dim3 grid((unsigned)p.N, (unsigned)plan.vparts);
+  {
+    const dim3 grid((unsigned)p.N, (unsigned)plan.vparts, (unsigned)(p.nchunks * p.nchunks));
     const uint32_t sm = vhy_layout(p.C).total;
     auto* kern = p.C <= 32 ? mixed_vhy_tc_kernel<1>
                            : (p.C <= 64 ? mixed_vhy_tc_kernel<2> : mixed_vhy_tc_kernel<4>);
-    kern<<<grid, kVThreads, sm, s>>>(plan.Bp, p.Yp, p.n, p.n_pad, p.nu, p.C, p.N, p.nK,
-                                     plan.slices, plan.rows_per_vpart, plan.vpart, p.status);
-  } else
-    mixed_vhy_part_kernel<<<dim3((unsigned)plan.vtiles, (unsigned)p.N, (unsigned)plan.vparts),
-                            256, 0, s>>>(plan.V32, p.nu, p.n, p.n_pad, p.N, plan.slices, acc_cols,
-                                         p.C, p.Yp, plan.rows_per_vpart, plan.vpart);
+    kern<<<grid, kVThreads, sm, s>>>(plan.Bp, p.Yp, p.n, p.n_pad, p.nu, p.C, p.nchunks, p.N,
+                                     p.nK, plan.slices, plan.rows_per_vpart, plan.vpart, p.status);
+  }
   const int64_t outs = (int64_t)p.N * p.nu * p.nu;
   mixed_vhy_reduce_kernel<<<(unsigned)((outs + 255) / 256), 256, 0, s>>>(
       plan.vpart, (int)plan.vparts, p.N, p.nu, ctx->con.w, Bhat);
