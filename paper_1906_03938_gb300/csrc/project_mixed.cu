@@ -46,6 +46,7 @@ constexpr int kEvalThreads = 32 * kEvalWarps;
 constexpr int kThreads = 32 * (2 + kEvalWarps);
 constexpr int kMaxG = 4;
 constexpr int kPlaneBytes = kBM * kBK * 2;   // one BF16 plane of a 128 x 16 block: 4 KB
+constexpr uint32_t kHalfPlane = kBM * (kBK / 2) * 2;   // its 8-column half: 2 KB
 constexpr uint32_t kWaitLimit = kStageWaitDefault;   // polls (64 ns sleeps) before giving up
 constexpr float kLog2e = 1.4426950408889634f;
 // Quadrature points (of 7) per entry whose sine and cosine the fused kernel evaluates by
@@ -188,6 +189,43 @@ __device__ __forceinline__ void put_entries(f2_t sr2, f2_t si2, const float2* se
   *reinterpret_cast<uint32_t*>(ag + 1 * plane_bytes) = lr;
   *reinterpret_cast<uint32_t*>(ag + 2 * plane_bytes) = hi;
   *reinterpret_cast<uint32_t*>(ag + 3 * plane_bytes) = li;
+}
+
+// Two entries of one node in one column l: rows i0 and i1 = i0 + 64 in the FFMA2 lanes (the
+// self term on the diagonal, zero in the padding), split into BF16 hi/lo and stored as
+// 16-bit values into the four planes of a column half (kHalfPlane apart) at ag (row i0)
+// and ag + 1024 (row i1: eight 8-row groups of 128 bytes further); self points at the
+// staged self term of column l.
+__device__ __forceinline__ void put_rows(f2_t sr2, f2_t si2, const float2* self, int64_t i0,
+                                         int64_t i1, int64_t l, int64_t n, unsigned char* ag) {
+  float re[2], im[2];
+  f2split(sr2, re[0], re[1]);
+  f2split(si2, im[0], im[1]);
+  const int64_t ii[2] = {i0, i1};
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    if (ii[d] == l) {   // diagonal: the self term
+      const float2 sv = *self;
+      re[d] = sv.x;
+      im[d] = sv.y;
+    }
+    if (ii[d] >= n || l >= n) {   // padding rows / columns of the tile
+      re[d] = 0.f;
+      im[d] = 0.f;
+    }
+  }
+  const uint32_t hr = pack_bf16(re[0], re[1]);
+  const uint32_t hi = pack_bf16(im[0], im[1]);
+  const uint32_t lr = pack_bf16(re[0] - __uint_as_float(hr << 16),
+                                re[1] - __uint_as_float(hr & 0xFFFF0000u));
+  const uint32_t li = pack_bf16(im[0] - __uint_as_float(hi << 16),
+                                im[1] - __uint_as_float(hi & 0xFFFF0000u));
+  const uint32_t v[4] = {hr, lr, hi, li};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    *reinterpret_cast<uint16_t*>(ag + q * kHalfPlane) = (uint16_t)(v[q] & 0xFFFFu);
+    *reinterpret_cast<uint16_t*>(ag + 1024 + q * kHalfPlane) = (uint16_t)(v[q] >> 16);
+  }
 }
 
 // bounded wait that also watches the block's abort flag
@@ -656,7 +694,6 @@ __global__ void __launch_bounds__(kThreads, 1) mixed_apply_kernel(MixedParams p)
 // their own: the evaluation runs up to two K-blocks ahead of the MMAs, which hides the
 // exchange between the partners and the MMAs' own duration behind it (with two stages
 // the evaluation warps waited for a free stage a sixth of the time).
-constexpr uint32_t kHalfPlane = kBM * (kBK / 2) * 2;   // one plane of a column half: 2 KB
 constexpr uint32_t kHalfBytes = 4 * kHalfPlane;        // the four planes of a half: 8 KB
 constexpr int kPA = 3;                                 // A stages
 constexpr int kPB = 2;                                 // basis stages
@@ -904,12 +941,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
     const f2_t cgr2 = f2((float)p.op.cgr, (float)p.op.cgr), cgi2 = f2((float)p.op.cgi, (float)p.op.cgi);
     const f2_t chr2 = f2((float)p.op.chr, (float)p.op.chr), chi2 = f2((float)p.op.chi, (float)p.op.chi);
     const f2_t nchi2 = f2(-(float)p.op.chi, -(float)p.op.chi);
-    const int r8 = lane / 4, kp = lane % 4;
-    const int row = 8 * e + r8;
-    const int64_t i = row0 + row;
+    // this thread's entries: rows r and r + 64 of one column (r = 4 e + lane / 8, column
+    // 8 kg + lane % 8), paired in the FFMA2 lanes. A warp reads eight columns' geometry per
+    // load (one 128-byte wavefront per quarter-warp, no bank conflicts) and writes 16-bit
+    // entries of four rows x eight columns (64 contiguous bytes per store); against a pair
+    // of columns of one row this halves the column-geometry loads, the bulk of the shared-
+    // memory traffic besides the tensor core's operand reads.
+    const int cq8 = lane % 8;
+    const int rr = 4 * e + lane / 8;                       // 0 .. 63
+    const int64_t i0 = row0 + rr, i1 = i0 + 64;
+    const uint32_t off = (uint32_t)(rr / 8) * 128 + (rr % 8) * 16 + cq8 * 2;   // row r; r + 64 at + 1024
     // paired: the column half kg = rank for both nodes; unpaired: both halves, own node
     const int kg_lo = paired ? (int)rank : 0;
     const int kg_hi = paired ? (int)rank + 1 : 2;
+    float4 xa = make_float4(0.f, 0.f, 0.f, 0.f), xb = xa;
 
     for (int it = 0; it < nit; ++it) {
       const int s = it % kPA;
@@ -923,41 +968,42 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
       const float2* sSelf = sSelfAll + s * (kBK * kMaxG);
       unsigned char* a_stage = sA + s * 2 * kHalfBytes;
       unsigned char* x_stage = sX + s * kHalfBytes;
-      const float4 xr = sRow[row];
+      if (it == 0) {   // the rows, staged by the producer before its first release
+        xa = sRow[rr];
+        xb = sRow[rr + 64];
+      }
 #pragma unroll 1
       for (int kg = kg_lo; kg < (ready ? kg_hi : kg_lo); ++kg) {
-        const int k0 = 8 * kg + 2 * kp;
-        const int64_t l0 = (int64_t)kb * kBK + k0;
+        const int k = 8 * kg + cq8;
+        const int64_t l = (int64_t)kb * kBK + k;
         f2_t rr2[7], am2[7];
         f2_t s2[kOp ? 7 : 1];
         {
-          const float4* c0 = sCol + k0 * 7;
-          const float4* c1 = c0 + 7;
-          const f2_t xx = f2(xr.x, xr.x), xy = f2(xr.y, xr.y), xz = f2(xr.z, xr.z);
+          const float4* cq = sCol + k * 7;
+          const f2_t xx = f2(xa.x, xb.x), xy = f2(xa.y, xb.y), xz = f2(xa.z, xb.z);
           f2_t nnx = f2(0.f, 0.f), nny = nnx, nnz = nnx;
-          if (kOp) {
-            const float* gk = sGraw + s * (kBK * 64) + k0 * 64;
-            nnx = f2(-gk[56], -gk[64 + 56]);
-            nny = f2(-gk[57], -gk[64 + 57]);
-            nnz = f2(-gk[58], -gk[64 + 58]);
+          if (kOp) {   // the column's normal, negated (d = x - y here)
+            const float* gk = sGraw + s * (kBK * 64) + k * 64;
+            nnx = f2(-gk[56], -gk[56]);
+            nny = f2(-gk[57], -gk[57]);
+            nnz = f2(-gk[58], -gk[58]);
           }
 #pragma unroll
           for (int q = 0; q < 7; ++q) {
-            const float4 y0 = c0[q], y1 = c1[q];
-            const f2_t dx = sub2(xx, f2(y0.x, y1.x)), dy = sub2(xy, f2(y0.y, y1.y)),
-                       dz = sub2(xz, f2(y0.z, y1.z));
+            const float4 y = cq[q];
+            const f2_t dx = sub2(xx, f2(y.x, y.x)), dy = sub2(xy, f2(y.y, y.y)),
+                       dz = sub2(xz, f2(y.z, y.z));
             const f2_t r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
             float r20, r21;
             f2split(r2, r20, r21);
             const f2_t rs = f2(rsqrtf_mufu(r20), rsqrtf_mufu(r21));
             rr2[q] = mul2(r2, rs);
-            am2[q] = mul2(f2(y0.w, y1.w), rs);
+            am2[q] = mul2(f2(y.w, y.w), rs);
             if (kOp)
               s2[kOp ? q : 0] = mul2(fma2(dx, nnx, fma2(dy, nny, mul2(dz, nnz))), mul2(rs, rs));
           }
         }
-        const uint32_t off = e * 128 + r8 * 16 + kp * 4;   // within a column half
-        const float2* selfk = sSelf + k0 * kMaxG;
+        const float2* selfk = sSelf + k * kMaxG;
         if (paired) {
           f2_t sa = f2(0.f, 0.f), ia = f2(0.f, 0.f), sb = f2(0.f, 0.f), ib = f2(0.f, 0.f);
           const f2_t kma = f2(kmi[0], kmi[0]), kmb = f2(kmi[1], kmi[1]);
@@ -997,10 +1043,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
           // node `rank` into this CTA's stage, the other into the export buffer
           unsigned char* own = a_stage + kg * kHalfBytes + off;
           unsigned char* other = x_stage + off;
-          put_entries(sa, ia, selfk, i, l0, p.n, rank == 0 ? own : other, false, float2(),
-                      kHalfPlane);
-          put_entries(sb, ib, selfk + 1, i, l0, p.n, rank == 0 ? other : own, false, float2(),
-                      kHalfPlane);
+          put_rows(sa, ia, selfk, i0, i1, l, p.n, rank == 0 ? own : other);
+          put_rows(sb, ib, selfk + 1, i0, i1, l, p.n, rank == 0 ? other : own);
         } else {
           f2_t sr2 = f2(0.f, 0.f), si2 = f2(0.f, 0.f);
           const f2_t kmi2 = f2(kmi[0], kmi[0]), kr2 = f2(kr[0], kr[0]);
@@ -1029,8 +1073,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
               si2 = fma2(a, sn, si2);
             }
           }
-          put_entries(sr2, si2, selfk, i, l0, p.n, a_stage + kg * kHalfBytes + off, false,
-                      float2(), kHalfPlane);
+          put_rows(sr2, si2, selfk, i0, i1, l, p.n, a_stage + kg * kHalfBytes + off);
         }
       }
       fence_proxy_async_smem();
