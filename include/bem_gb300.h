@@ -543,7 +543,11 @@ bem_status bem_near_pairs(bem_ctx* ctx, int64_t* nnz, int32_t* row_ptr_host, int
  * out_scale * (W4 h3 + b4) on features standardised as (f - in_shift) * in_scale.
  * The context keeps FP32 master weights (trained) and an inference copy with the weights
  * rounded to BF16 (used by bem_surrogate_forward and by the mixed projection in near-field
- * mode 2). Device arrays are row-major: features count x 11, targets and outputs count x 2.
+ * mode 2). In the projection the network runs on the tensor core: tiles of 128 (pair,
+ * node) samples, the three 64-wide layers as BF16 tcgen05 MMAs on activations split into
+ * BF16 hi + lo (FP32 accumulation), tanh by the MUFU's approximation; a sample whose
+ * features leave the training box (widened by 2 % of its width) takes the 8 x 8 rule.
+ * Device arrays are row-major: features count x 11, targets and outputs count x 2.
  *
  * bem_surrogate_init: Xavier-uniform weights from `seed`, zero biases, identity scalings.
  * bem_surrogate_set / _get: copy the parameters from / to the host (which: 0 master, 1
@@ -567,6 +571,14 @@ bem_status bem_near_pairs(bem_ctx* ctx, int64_t* nnz, int32_t* row_ptr_host, int
  * Errors: BEM_EINVAL for bad arguments, BEM_ESTATE without a network (init or set first).
  */
 int bem_surrogate_size(void);
+/*
+ * bem_surrogate_usage: samples (near pair x contour node) whose correction the network gave
+ * (*network) and whose features fell outside its training box so that the plain 8 x 8 rule
+ * gave it (*rule), summed over the mixed projections with near-field mode 2 since the
+ * previous call; the counters are reset. Synchronises the stream. Zeros before the first
+ * such projection.
+ */
+bem_status bem_surrogate_usage(bem_ctx* ctx, int64_t* network, int64_t* rule, void* stream);
 bem_status bem_surrogate_init(bem_ctx* ctx, uint64_t seed, void* stream);
 bem_status bem_surrogate_set(bem_ctx* ctx, const float* params_host, int64_t count, void* stream);
 bem_status bem_surrogate_get(bem_ctx* ctx, int which, float* params_host, int64_t count,

@@ -87,6 +87,7 @@ SIGNATURES = {
     "bem_surrogate_init": (_I, [_P, ctypes.c_uint64, _P]),
     "bem_surrogate_set": (_I, [_P, _P, _I64, _P]),
     "bem_surrogate_get": (_I, [_P, _I, _P, _I64, _P]),
+    "bem_surrogate_usage": (_I, [_P, _P, _P, _P]),
     "bem_surrogate_samples": (_I, [_P, _D, _D, _D, _D, _I64, ctypes.c_uint64, _P, _P, _P, _P,
                                    _P]),
     "bem_surrogate_forward": (_I, [_P, _P, _I64, _P, _P]),
@@ -262,6 +263,15 @@ class Context:
     def surrogate_set(self, params):
         p = np.ascontiguousarray(params, dtype=np.float32)
         self._chk("bem_surrogate_set", self._lib.bem_surrogate_set(self._h, _ptr(p), p.size, None))
+
+    def surrogate_usage(self, stream=None):
+        """(network, rule): samples of the near-field projections since the last call whose
+        correction came from the network, and from the plain 8 x 8 rule (features outside
+        the training box); resets the counters."""
+        a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+        self._chk("bem_surrogate_usage", self._lib.bem_surrogate_usage(
+            self._h, ctypes.byref(a), ctypes.byref(b), _stream(stream)))
+        return a.value, b.value
 
     def surrogate_samples(self, count, k_re, k_im, seed=1, with_pairs=False, stream=None):
         """(features (count, 11), targets (count, 2)[, pairs (count, 2), k (count,)])."""

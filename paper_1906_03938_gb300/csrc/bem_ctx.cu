@@ -221,6 +221,7 @@ void bem_destroy(bem_ctx* ctx) {
   cudaFree(ctx->d_near_ptr);
   cudaFree(ctx->d_near_cols);
   cudaFree(ctx->d_near_work);
+  cudaFree(ctx->d_sur_usage);
   cudaFree(ctx->d_net);
   free_hmatrix(ctx);
   for (auto& e : ctx->ev) cudaEventDestroy(e);

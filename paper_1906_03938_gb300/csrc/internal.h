@@ -125,6 +125,7 @@ struct bem_ctx {
   int32_t* d_near_ptr = nullptr;    // n + 1
   int32_t* d_near_cols = nullptr;   // nnz
   int64_t near_cap_n = 0, near_cap_nnz = 0;
+  unsigned long long* d_sur_usage = nullptr;   // (network, plain rule) samples since the last read
   void* d_near_work = nullptr;      // row-major copy of the basis for the near products
   size_t near_work_bytes = 0;
   // surrogate network of the near field (weights on the device, see surrogate.cu)

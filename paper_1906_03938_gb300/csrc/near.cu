@@ -15,16 +15,20 @@
 //     R[:, c] += C(lam_c) X[:, c] (values or k-derivatives) for residuals and refinement.
 // One warp per (row, node) or (row, column): its lanes evaluate the row's pair corrections,
 // then sweep the basis columns with them (fixed order: deterministic).
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include <algorithm>
 #include <vector>
 
 #include "internal.h"
+#include "sm100.cuh"
 #include "surrogate.cuh"
 
 namespace bem {
 namespace {
+
+using namespace sm100;
 
 constexpr double kPi = 3.141592653589793238462643383279502884;
 
@@ -251,27 +255,15 @@ __device__ void near_features32(const Geometry& g, int64_t l, const NearFrame& F
   feat[10] = (float)(ki * h);
 }
 
-// (A_near - A_7)(k) of the pair, FP32 with coordinates relative to x (formed in FP64), or
-// from the surrogate network when net is non-null (the 7-point part is then h times its
-// output's complement: the network predicts the whole correction divided by h).
+// (A_near - A_7)(k) of the pair by the 8 x 8 rule, FP32 with coordinates relative to x
+// (formed in FP64): the surrogate's value for pairs outside its training box.
 __device__ float2 near_corr32(const Geometry& g, int64_t l, const double x[3], float kr,
-                              float ki, const GL8& gl, const float* __restrict__ net,
-                              const OpCoef& op) {
+                              float ki, const GL8& gl, const OpCoef& op) {
   NearFrame F;
   near_frame(g, l, x, F);
   if (!op_single(op)) {   // the general operator: the FP64 correction, rounded
     const double2 c = near_corr64(g, l, x, (double)kr, (double)ki, false, gl, op);
     return make_float2((float)c.x, (float)c.y);
-  }
-  if (net) {
-    float feat[kNetIn];
-    near_features32(g, l, F, x, kr, ki, feat);
-    // a pair outside the network's training box takes the plain rule below
-    if (surrogate_in_box(net, feat)) {
-      const float2 o = surrogate_eval(net, feat);
-      const float h = (float)g.diam[l];
-      return make_float2(o.x * h, o.y * h);
-    }
   }
   const float ax = (float)(F.a[0] - x[0]), ay = (float)(F.a[1] - x[1]), az = (float)(F.a[2] - x[2]);
   const float abx = (float)F.ab[0], aby = (float)F.ab[1], abz = (float)F.ab[2];
@@ -471,67 +463,9 @@ near_values32_kernel(Geometry g, const int32_t* __restrict__ rows, const int32_t
 }
 
 // Slice `slice` of the mixed path's partials := C(z_j) V in FP32 (every row < n_pad and
-// every column < nu written); one warp per (row i, node j), the pair values evaluated here
-// (the surrogate network).
-__global__ void __launch_bounds__(256)
-near_apply32_kernel(Geometry g, const int32_t* __restrict__ ptr, const int32_t* __restrict__ cols,
-                    const double* __restrict__ z, int N, const float2* __restrict__ Vt, int nu,
-                    int nup, int C, int n_pad, float* __restrict__ Yp, int slice, GL8 gl,
-                    const float* __restrict__ net, OpCoef op) {
-  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
-  const int lane = threadIdx.x % 32;
-  const int64_t n = g.n;
-  if (w >= (int64_t)n_pad * N) return;
-  const int64_t i = w % n_pad;
-  const int node = (int)(w / n_pad);
-  float2 acc[kMaxColGroups];
-#pragma unroll
-  for (int t = 0; t < kMaxColGroups; ++t) acc[t] = make_float2(0.f, 0.f);
-  if (i < n) {
-    const float kr = (float)z[2 * node], ki = (float)z[2 * node + 1];
-    const double x[3] = {g.cx[i], g.cx[n + i], g.cx[2 * n + i]};
-    const int32_t e0 = ptr[i], e1 = ptr[i + 1];
-    for (int32_t eb = e0; eb < e1; eb += 32) {
-      const int32_t e = eb + lane;
-      float2 cval = make_float2(0.f, 0.f);
-      int32_t l = 0;
-      if (e < e1) {
-        l = cols[e];
-        cval = near_corr32(g, l, x, kr, ki, gl, net, op);
-      }
-      const int cnt = min(32, e1 - eb);
-      for (int t = 0; t < cnt; ++t) {
-        const float cx = __shfl_sync(0xffffffffu, cval.x, t);
-        const float cy = __shfl_sync(0xffffffffu, cval.y, t);
-        const int32_t lt = __shfl_sync(0xffffffffu, l, t);
-        const float2* vr = Vt + (int64_t)lt * nu;
-#pragma unroll
-        for (int cg = 0; cg < kMaxColGroups; ++cg) {
-          const int c = lane + 32 * cg;
-          if (c < nu) {
-            const float2 v = vr[c];
-            acc[cg].x += cx * v.x - cy * v.y;
-            acc[cg].y += cx * v.y + cy * v.x;
-          }
-        }
-      }
-    }
-  }
-  const int acc_cols = 2 * nup;
-  float* base = Yp + ((size_t)slice * N + node) * acc_cols * (size_t)n_pad;
-#pragma unroll
-  for (int cg = 0; cg < kMaxColGroups; ++cg) {
-    const int c = lane + 32 * cg;
-    if (c < nu) {
-      const int colr = (c / C) * 2 * C + (c % C);
-      base[(size_t)colr * n_pad + i] = acc[cg].x;
-      base[(size_t)(colr + C) * n_pad + i] = acc[cg].y;
-    }
-  }
-}
-
-// The same slice from stored pair values Cv (node-major, nnz per node): one warp per
-// (row i, node j); lanes load 32 pairs' values and columns, then sweep the basis columns.
+// every column < nu written) from stored pair values Cv (node-major, nnz per node; the 8 x 8
+// rule's or the surrogate network's): one warp per (row i, node j); lanes load 32 pairs'
+// values and columns, then sweep the basis columns.
 __global__ void __launch_bounds__(256)
 near_spmm32_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ cols, int64_t n,
                    int64_t nnz, int N, const float2* __restrict__ Cv, const float2* __restrict__ Vt,
@@ -583,6 +517,252 @@ near_spmm32_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ 
       base[(size_t)colr * n_pad + i] = acc[cg].x;
       base[(size_t)(colr + C) * n_pad + i] = acc[cg].y;
     }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Surrogate inference on the tensor core: the network's per-(pair, node) values C_j(e) into
+// the same node-major array as the 8 x 8 rule's values, then the same sparse product.
+// A CTA takes tiles of 128 samples t = j nnz + e (sample = TMEM lane = thread). The three
+// 64-wide layers are tcgen05 kind::f16 MMAs (M = 128, N = 64, K = 16 per instruction): the
+// weights, rounded to BF16 for inference, sit in shared memory as the B operands; each
+// layer's input activations are split into BF16 hi + lo planes (two MMAs per K step, FP32
+// accumulation in 64 TMEM columns), so the products carry ~16 bits of each activation
+// against the BF16 weights, as the per-thread FP32 evaluation does to the rounding of its
+// sums. Biases, tanh (the MUFU's tanh.approx) and the 64 -> 2 output layer run per thread
+// on the accumulator rows read back with tcgen05.ld. Samples whose features leave the
+// training box take the plain 8 x 8 rule (near_corr32 without a network).
+constexpr int kSurTile = 128;
+constexpr int kSurK1 = 16;   // the 11 inputs padded to one MMA K step
+
+// shared memory: A1 (hi/lo planes of 128 x 16), A (hi/lo planes of 128 x 64), W1 (64 x 16),
+// W2 and W3 (64 x 64), all BF16 K-major; then the FP32 constants (input shift, scale and
+// box, biases, output layer, output scale); then the mbarrier, TMEM slot and abort flag
+constexpr uint32_t kSurA1 = 0;
+constexpr uint32_t kSurA = kSurA1 + 2u * kSurTile * kSurK1 * 2u;
+constexpr uint32_t kSurW1 = kSurA + 2u * kSurTile * kNetHid * 2u;
+constexpr uint32_t kSurW2 = kSurW1 + (uint32_t)kNetHid * kSurK1 * 2u;
+constexpr uint32_t kSurW3 = kSurW2 + (uint32_t)kNetHid * kNetHid * 2u;
+constexpr uint32_t kSurCst = kSurW3 + (uint32_t)kNetHid * kNetHid * 2u;
+constexpr int kCShift = 0, kCScale = 11, kCLo = 22, kCHi = 33, kCB1 = 44, kCB2 = 108,
+              kCB3 = 172, kCW4 = 236, kCB4 = 364, kCOut = 366, kCFloats = 368;
+constexpr uint32_t kSurBar = kSurCst + kCFloats * 4u;
+constexpr uint32_t kSurSmem = kSurBar + 16u;
+
+// Byte offset of element (row r, k) in a K-major canonical (no swizzle) BF16 operand with
+// K columns: 8-row x 16-byte core matrices, 128 bytes apart along K, 8-row groups
+// (K / 8) x 128 bytes apart.
+__device__ __forceinline__ uint32_t kmaj_off(int r, int k, int K) {
+  return (uint32_t)(r / 8) * (uint32_t)(K / 8) * 128u + (uint32_t)(k / 8) * 128u +
+         (uint32_t)(r % 8) * 16u + (uint32_t)(k % 8) * 2u;
+}
+
+__device__ __forceinline__ float tanh_mufu(float x) {
+  float r;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Per pair: the nine frame features (the triangle's vertices in the pair's frame over h),
+// h, and the output factor h / (d / h)^7 (SoA, 11 x nnz floats).
+__global__ void __launch_bounds__(256)
+surrogate_pair_features_kernel(Geometry g, const int32_t* __restrict__ rows,
+                               const int32_t* __restrict__ cols, int64_t nnz,
+                               float* __restrict__ pf) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nnz) return;
+  const int64_t n = g.n;
+  const int64_t i = rows[e], l = cols[e];
+  const double x[3] = {g.cx[i], g.cx[n + i], g.cx[2 * n + i]};
+  NearFrame F;
+  near_frame(g, l, x, F);
+  float feat[kNetIn];
+  near_features32(g, l, F, x, 0.f, 0.f, feat);
+  for (int c = 0; c < 9; ++c) pf[c * nnz + e] = feat[c];
+  const float h = (float)g.diam[l];
+  pf[9 * nnz + e] = h;
+  pf[10 * nnz + e] = h / surrogate_decay(feat);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16_pair(float lo_elem, float hi_elem) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(lo_elem, hi_elem);   // .x -> low 16 bits
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// One row of a layer's input (K values) as BF16 hi and lo planes of a K-major operand.
+template <int K>
+__device__ __forceinline__ void put_act_row(unsigned char* hi_plane, unsigned char* lo_plane, int r,
+                                            const float* v) {
+#pragma unroll
+  for (int c = 0; c < K / 8; ++c) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float a = v[8 * c + 2 * q], b = v[8 * c + 2 * q + 1];
+      h[q] = pack_bf16_pair(a, b);
+      l[q] = pack_bf16_pair(a - __uint_as_float(h[q] << 16), b - __uint_as_float(h[q] & 0xFFFF0000u));
+    }
+    const uint32_t off = kmaj_off(r, 8 * c, K);
+    *reinterpret_cast<uint4*>(hi_plane + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(lo_plane + off) = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+}
+
+__global__ void __launch_bounds__(kSurTile)
+surrogate_values_tc_kernel(Geometry g, const int32_t* __restrict__ rows,
+                           const int32_t* __restrict__ cols, int64_t nnz,
+                           const double* __restrict__ z, int N, const float* __restrict__ pf,
+                           const float* __restrict__ net, GL8 gl, OpCoef op,
+                           float2* __restrict__ Cv, int* status, uint32_t wait_limit,
+                           unsigned long long* __restrict__ usage) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  float* cst = reinterpret_cast<float*>(smem + kSurCst);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kSurBar);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + kSurBar + 8);
+  const int tid = threadIdx.x, warp = tid / 32;
+
+  // the BF16 weights as K-major B operands (rows = output units), the FP32 constants
+  for (int x = tid; x < kNetHid * kSurK1; x += kSurTile) {
+    const int o = x / kSurK1, k = x % kSurK1;
+    const float w = k < kNetIn ? net[kOffW1 + o * kNetIn + k] : 0.f;
+    *reinterpret_cast<__nv_bfloat16*>(smem + kSurW1 + kmaj_off(o, k, kSurK1)) = __float2bfloat16_rn(w);
+  }
+  for (int x = tid; x < kNetHid * kNetHid; x += kSurTile) {
+    const int o = x / kNetHid, k = x % kNetHid;
+    *reinterpret_cast<__nv_bfloat16*>(smem + kSurW2 + kmaj_off(o, k, kNetHid)) =
+        __float2bfloat16_rn(net[kOffW2 + x]);
+    *reinterpret_cast<__nv_bfloat16*>(smem + kSurW3 + kmaj_off(o, k, kNetHid)) =
+        __float2bfloat16_rn(net[kOffW3 + x]);
+  }
+  for (int x = tid; x < kNetIn; x += kSurTile) {
+    cst[kCShift + x] = net[kOffInShift + x];
+    cst[kCScale + x] = net[kOffInScale + x];
+    const float lo = net[kOffFeatLo + x], hi = net[kOffFeatHi + x], m = 0.02f * (hi - lo);
+    cst[kCLo + x] = lo - m;   // the training box widened by 2 % of its width
+    cst[kCHi + x] = hi + m;
+  }
+  for (int x = tid; x < kNetHid; x += kSurTile) {
+    cst[kCB1 + x] = net[kOffB1 + x];
+    cst[kCB2 + x] = net[kOffB2 + x];
+    cst[kCB3 + x] = net[kOffB3 + x];
+  }
+  for (int x = tid; x < kNetOut * kNetHid; x += kSurTile) cst[kCW4 + x] = net[kOffW4 + x];
+  if (tid < kNetOut) {
+    cst[kCB4 + tid] = net[kOffB4 + tid];
+    cst[kCOut + tid] = net[kOffOutScale + tid];
+  }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(slot, kNetHid);
+    tmem_relinquish();
+  }
+  fence_proxy_async_smem();   // the weight planes -> the tensor core
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  const uint32_t lanes = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's TMEM lanes
+  const uint32_t idesc = idesc_bf16(kSurTile, kNetHid);
+  const uint32_t a1 = smem_u32(smem + kSurA1), a = smem_u32(smem + kSurA);
+  const uint32_t a1_lo = kSurTile * kSurK1 * 2u, a_lo = kSurTile * kNetHid * 2u;
+  const int64_t total = nnz * N;
+  const int64_t tiles = (total + kSurTile - 1) / kSurTile;
+  uint32_t phase = 0;
+  bool ok = true;
+  // one layer's MMAs (thread 0) and the wait for them (every thread, bounded; the block
+  // agrees on the outcome)
+  auto layer = [&](uint32_t a_base, uint32_t a_lo_off, uint32_t w, int K) {
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+      for (int kk = 0; kk < K / 16; ++kk) {
+        const uint64_t bd = smem_desc(w + kk * 256u, 128, sbo);
+        mma_bf16(tmem, smem_desc(a_base + kk * 256u, 128, sbo), bd, idesc, kk > 0 ? 1u : 0u);
+        mma_bf16(tmem, smem_desc(a_base + a_lo_off + kk * 256u, 128, sbo), bd, idesc, 1u);
+      }
+      mma_commit(bar);
+    }
+    const bool done = mbar_wait(bar, phase, wait_limit);
+    phase ^= 1u;
+    ok = __syncthreads_and(done) != 0;
+    tc_fence_after();
+  };
+  auto read_act = [&](int boff, float* v) {   // tanh(accumulator row + bias)
+#pragma unroll
+    for (int c0 = 0; c0 < kNetHid; c0 += 16) {
+      float r[16];
+      tmem_ld16(lanes + c0, r);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[c0 + k] = tanh_mufu(r[k] + cst[boff + c0 + k]);
+    }
+  };
+
+  for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+    const int64_t t = tile * kSurTile + tid;
+    const bool valid = t < total;
+    const int64_t e = valid ? t % nnz : 0;
+    const int j = valid ? (int)(t / nnz) : 0;
+    const float kr = (float)z[2 * j], ki = (float)z[2 * j + 1];
+    const float h = pf[9 * nnz + e], fac = pf[10 * nnz + e];
+    float x[kSurK1];
+    bool inbox = true;
+#pragma unroll
+    for (int c = 0; c < kNetIn; ++c) {
+      const float f = c < 9 ? pf[c * nnz + e] : (c == 9 ? kr * h : ki * h);
+      inbox = inbox && f >= cst[kCLo + c] && f <= cst[kCHi + c];
+      x[c] = valid ? (f - cst[kCShift + c]) * cst[kCScale + c] : 0.f;
+    }
+#pragma unroll
+    for (int c = kNetIn; c < kSurK1; ++c) x[c] = 0.f;
+    put_act_row<kSurK1>(smem + kSurA1, smem + kSurA1 + a1_lo, tid, x);
+    layer(a1, a1_lo, smem_u32(smem + kSurW1), kSurK1);
+    if (!ok) break;
+    float v[kNetHid];
+    read_act(kCB1, v);
+    put_act_row<kNetHid>(smem + kSurA, smem + kSurA + a_lo, tid, v);
+    layer(a, a_lo, smem_u32(smem + kSurW2), kNetHid);
+    if (!ok) break;
+    read_act(kCB2, v);
+    put_act_row<kNetHid>(smem + kSurA, smem + kSurA + a_lo, tid, v);
+    layer(a, a_lo, smem_u32(smem + kSurW3), kNetHid);
+    if (!ok) break;
+    read_act(kCB3, v);
+    float o0 = cst[kCB4], o1 = cst[kCB4 + 1];
+#pragma unroll
+    for (int k = 0; k < kNetHid; ++k) {
+      o0 = fmaf(cst[kCW4 + k], v[k], o0);
+      o1 = fmaf(cst[kCW4 + kNetHid + k], v[k], o1);
+    }
+    float2 val = make_float2(o0 * cst[kCOut] * fac, o1 * cst[kCOut + 1] * fac);
+    // samples served by the network and by the plain rule (one atomic per warp)
+    const unsigned in_net = __ballot_sync(0xffffffffu, valid && inbox);
+    const unsigned in_rule = __ballot_sync(0xffffffffu, valid && !inbox);
+    if (tid % 32 == 0) {
+      if (in_net) atomicAdd(&usage[0], (unsigned long long)__popc(in_net));
+      if (in_rule) atomicAdd(&usage[1], (unsigned long long)__popc(in_rule));
+    }
+    if (valid && !inbox) {   // outside the training box: the plain 8 x 8 rule
+      const int64_t n = g.n, i = rows[e], l = cols[e];
+      const double xc[3] = {g.cx[i], g.cx[n + i], g.cx[2 * n + i]};
+      val = near_corr32(g, l, xc, kr, ki, gl, op);
+    }
+    if (valid) Cv[t] = val;
+  }
+  if (!ok && tid == 0) atomicOr(status, kStatusTimeout);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    // the last commit has completed on the normal path; bounded on an aborted one
+    if (tid == 0 && !ok) mbar_wait(bar, phase ^ 1u, kStageWaitDefault);
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, kNetHid);
   }
 }
 
@@ -792,38 +972,64 @@ bem_status near_apply32(bem_ctx* ctx, const float2* V32, int nu, int nup, int C,
   const int64_t nnz = ctx->near_nnz;
   // the inference copy of the network (BF16-rounded weights) follows the master weights
   const float* net = (ctx->near_mode == 2 && ctx->net_ready) ? ctx->d_net + kNetFloats : nullptr;
-  // the 64-point rule: the pair values of every node first (work buffer: the row-major
-  // basis, then N x nnz values, then the pairs' rows)
-  const bool values = !net && nnz > 0;
+  // the pair values of every node first, by the 64-point rule or the network (work buffer:
+  // the row-major basis, N x nnz values, the pairs' rows, the network's pair features)
+  const bool values = nnz > 0;
   const size_t vt_bytes = (size_t)n * nu * sizeof(float2);
   const size_t cv_bytes = values ? (size_t)N * nnz * sizeof(float2) : 0;
-  bem_status st = ensure_near_work(ctx, vt_bytes + cv_bytes + (values ? (size_t)nnz * sizeof(int32_t) : 0));
+  const size_t rows_bytes = values ? ((size_t)nnz * sizeof(int32_t) + 15) / 16 * 16 : 0;
+  const size_t pf_bytes = (values && net) ? (size_t)11 * nnz * sizeof(float) : 0;
+  bem_status st = ensure_near_work(ctx, vt_bytes + cv_bytes + rows_bytes + pf_bytes);
   if (st != BEM_OK) return st;
   float2* Vt = reinterpret_cast<float2*>(ctx->d_near_work);
   transpose32_kernel<<<(unsigned)((n * nu + 255) / 256), 256, 0, s>>>(V32, n, nu, Vt);
   ctx->launches++;
   float2* Cv = nullptr;
   if (values) {
-    Cv = reinterpret_cast<float2*>(static_cast<char*>(ctx->d_near_work) + vt_bytes);
-    int32_t* rows = reinterpret_cast<int32_t*>(static_cast<char*>(ctx->d_near_work) + vt_bytes + cv_bytes);
+    char* wk = static_cast<char*>(ctx->d_near_work);
+    Cv = reinterpret_cast<float2*>(wk + vt_bytes);
+    int32_t* rows = reinterpret_cast<int32_t*>(wk + vt_bytes + cv_bytes);
     near_rows_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctx->d_near_ptr, n, rows);
-    const int64_t threads = nnz * ((N + kNearNodes - 1) / kNearNodes);
-    if (op_single(ctx->op))
-      near_values32_kernel<false><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-          ctx->geo, rows, ctx->d_near_cols, nnz, ctx->con.z, N, gl8(), ctx->op, Cv);
-    else
-      near_values32_kernel<true><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-          ctx->geo, rows, ctx->d_near_cols, nnz, ctx->con.z, N, gl8(), ctx->op, Cv);
-    ctx->launches += 2;
+    ctx->launches++;
+    if (net) {
+      float* pf = reinterpret_cast<float*>(wk + vt_bytes + cv_bytes + rows_bytes);
+      surrogate_pair_features_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, s>>>(
+          ctx->geo, rows, ctx->d_near_cols, nnz, pf);
+      st = cuda_check(ctx, cudaFuncSetAttribute(surrogate_values_tc_kernel,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)kSurSmem),
+                      "surrogate kernel attribute");
+      if (st != BEM_OK) return st;
+      int sms = 0;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+      const int64_t tiles = (nnz * N + kSurTile - 1) / kSurTile;
+      const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, 3 * (int64_t)std::max(1, sms)));
+      if (!ctx->d_sur_usage) {
+        st = cuda_check(ctx, cudaMalloc(&ctx->d_sur_usage, 2 * sizeof(unsigned long long)),
+                        "surrogate usage counters");
+        if (st != BEM_OK) return st;
+        st = cuda_check(ctx, cudaMemsetAsync(ctx->d_sur_usage, 0, 2 * sizeof(unsigned long long), s),
+                        "surrogate usage counters");
+        if (st != BEM_OK) return st;
+      }
+      surrogate_values_tc_kernel<<<grid, kSurTile, kSurSmem, s>>>(
+          ctx->geo, rows, ctx->d_near_cols, nnz, ctx->con.z, N, pf, net, gl8(), ctx->op, Cv,
+          ctx->d_status, ctx->stage_wait_limit, ctx->d_sur_usage);
+      ctx->launches += 2;
+    } else {
+      const int64_t threads = nnz * ((N + kNearNodes - 1) / kNearNodes);
+      if (op_single(ctx->op))
+        near_values32_kernel<false><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+            ctx->geo, rows, ctx->d_near_cols, nnz, ctx->con.z, N, gl8(), ctx->op, Cv);
+      else
+        near_values32_kernel<true><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+            ctx->geo, rows, ctx->d_near_cols, nnz, ctx->con.z, N, gl8(), ctx->op, Cv);
+      ctx->launches++;
+    }
   }
   const unsigned blocks = (unsigned)((32 * (int64_t)n_pad * N + 255) / 256);
-  if (Cv)
-    near_spmm32_kernel<<<blocks, 256, 0, s>>>(ctx->d_near_ptr, ctx->d_near_cols, n, nnz, N, Cv, Vt,
-                                              nu, nup, C, n_pad, Yp, slice);
-  else
-    near_apply32_kernel<<<blocks, 256, 0, s>>>(
-        ctx->geo, ctx->d_near_ptr, ctx->d_near_cols, ctx->con.z, N, Vt, nu, nup, C, n_pad, Yp,
-        slice, gl8(), net, ctx->op);
+  near_spmm32_kernel<<<blocks, 256, 0, s>>>(ctx->d_near_ptr, ctx->d_near_cols, n, nnz, N, Cv, Vt,
+                                            nu, nup, C, n_pad, Yp, slice);
   ctx->launches++;
   return cuda_check(ctx, cudaGetLastError(), "near field kernels");
 }
@@ -861,6 +1067,26 @@ extern "C" bem_status bem_set_near_field(bem_ctx* ctx, int mode, void* stream) {
   ctx->near_mesh_version = -1;
   if (mode == 0 || ctx->geo.n == 0) return BEM_OK;
   return ensure_near(ctx, (cudaStream_t)stream);
+}
+
+extern "C" bem_status bem_surrogate_usage(bem_ctx* ctx, int64_t* network, int64_t* rule,
+                                          void* stream) {
+  if (!ctx || !network || !rule) return BEM_EINVAL;
+  *network = 0;
+  *rule = 0;
+  if (!ctx->d_sur_usage) return BEM_OK;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long h[2] = {0, 0};
+  bem_status st = cuda_check(ctx, cudaMemcpyAsync(h, ctx->d_sur_usage, sizeof(h),
+                                                  cudaMemcpyDeviceToHost, s),
+                             "bem_surrogate_usage copy");
+  if (st == BEM_OK)
+    st = cuda_check(ctx, cudaMemsetAsync(ctx->d_sur_usage, 0, sizeof(h), s), "bem_surrogate_usage reset");
+  if (st == BEM_OK) st = cuda_check(ctx, cudaStreamSynchronize(s), "bem_surrogate_usage");
+  *network = (int64_t)h[0];
+  *rule = (int64_t)h[1];
+  return st;
 }
 
 extern "C" bem_status bem_near_pairs(bem_ctx* ctx, int64_t* nnz, int32_t* row_ptr_host,

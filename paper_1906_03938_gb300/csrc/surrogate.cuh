@@ -9,6 +9,7 @@
 //   out_scale[2]                 the output is out_scale * (W4 h3 + b4) / (d / h)^7
 //   feat_lo[11], feat_hi[11]     the training data's box: a pair whose features leave it
 //                                (widened by 2 % of its width) takes the plain 8 x 8 rule
+//                                (the inference kernel in near.cu checks it)
 // d / h is the distance from the collocation point to the triangle's centroid in units of
 // h, read off the features: the 7-point rule's error on a smooth integrand falls like
 // (h / d)^7 (measured slope -7.5 over near pairs), so the network itself only has to
@@ -47,20 +48,6 @@ __device__ __forceinline__ float surrogate_decay(const float feat[kNetIn]) {
   const float cz = (feat[2] + feat[5] + feat[8]) * (1.f / 3.f);
   const float d2 = cx * cx + cy * cy + cz * cz;
   return d2 * d2 * d2 * sqrtf(d2);
-}
-
-// True when every feature lies in the training box widened by 2 % of its width on each
-// side (an untrained network's box is the whole line).
-__device__ __forceinline__ bool surrogate_in_box(const float* __restrict__ net,
-                                                 const float feat[kNetIn]) {
-  bool in = true;
-#pragma unroll
-  for (int i = 0; i < kNetIn; ++i) {
-    const float lo = __ldg(net + kOffFeatLo + i), hi = __ldg(net + kOffFeatHi + i);
-    const float m = 0.02f * (hi - lo);
-    in = in && feat[i] >= lo - m && feat[i] <= hi + m;
-  }
-  return in;
 }
 
 // One evaluation per thread; every lane of a warp reads the same weight at the same time

@@ -135,6 +135,11 @@ def test_training_and_gain_on_held_out_mesh(bem):
     Vd = bem.fortran(torch.from_numpy(V).to("cuda:0"))
     ctx.set_near_field(2)
     _, Y2 = ctx.project(Vd, bem.PREC_MIXED, AV=True)
+    # every (pair, node) sample inside the training box goes through the network
+    net_s, rule_s = ctx.surrogate_usage()
+    nnz = len(ctx.near_pairs()[1])
+    print("samples through the network", net_s, "through the plain rule", rule_s)
+    assert net_s + rule_s == 6 * nnz and net_s >= 0.9 * (net_s + rule_s)
     ctx.set_near_field(0)
     _, Y0 = ctx.project(Vd, bem.PREC_MIXED, AV=True)
     _, Yo = orr.project(m, z, V, near=True)
@@ -171,18 +176,21 @@ def test_pairs_outside_training_box_take_plain_rule(bem):
         ctx.set_near_field(mode)
         B = ctx.project(Vd, bem.PREC_MIXED)
         ctx.check()
+        usage = ctx.surrogate_usage()
         ctx.close()
-        return (B[0] if isinstance(B, tuple) else B).cpu().numpy(), z, w
+        return (B[0] if isinstance(B, tuple) else B).cpu().numpy(), z, w, usage
 
     out = synth.ContourSpec("circle", 10.0 + 0j, 0.3, 0.3)
-    B2, z, w = proj(out, 2)
-    B1, _, _ = proj(out, 1)
+    B2, z, w, (net_s, rule_s) = proj(out, 2)
+    assert net_s == 0 and rule_s > 0   # every sample outside the box: the plain rule
+    B1, _, _, _ = proj(out, 1)
     assert np.max(np.abs(B2 - B1)) <= 1e-5 * np.max(np.abs(B1))
     P, _ = orr.project(mesh, z, V, near=True)
     for j in range(4):
         ref = w[j] * P[j]
         assert np.max(np.abs(B2[j] - ref)) <= 1e-4 * np.max(np.abs(ref))
     inside = synth.ContourSpec("circle", 5.75 + 0j, 0.05, 0.05)
-    C2, _, _ = proj(inside, 2)
-    C1, _, _ = proj(inside, 1)
+    C2, _, _, (net_s, rule_s) = proj(inside, 2)
+    assert net_s > 0
+    C1, _, _, _ = proj(inside, 1)
     assert np.max(np.abs(C2 - C1)) > 1e-5 * np.max(np.abs(C1))
