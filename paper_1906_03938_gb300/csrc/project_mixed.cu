@@ -1230,6 +1230,7 @@ __global__ void prep_basis_planes_kernel(const double* __restrict__ V, int64_t l
 constexpr int kVStages = 2;
 constexpr int kVKB = 2;                       // 16-row K-blocks per stage
 constexpr int kVRows = 16 * kVKB;             // rows per stage
+constexpr int64_t kVMaxRows = 4096;           // rows per CTA (row part) at most
 constexpr int kVConvWarps = 8;
 constexpr int kVConvThreads = 32 * kVConvWarps;
 constexpr int kVThreads = 32 * (2 + kVConvWarps);
@@ -1589,6 +1590,9 @@ bem_status mixed_plan(bem_ctx* ctx, const double* V, int64_t ldv, int nu, int S,
     const int64_t slots = (int64_t)std::max(1, sms) * per_sm;
     const int64_t tparts = std::max<int64_t>(1, slots / ((int64_t)N * p.nchunks * p.nchunks));
     plan.rows_per_vpart = ((n + tparts - 1) / tparts + kVRows - 1) / kVRows * kVRows;
+    // at most kVMaxRows rows per FP32 TMEM accumulation: its rounding error grows with the
+    // number of accumulated 16-row steps (up to 256 u32 here); the parts are summed in FP64
+    plan.rows_per_vpart = std::min<int64_t>(plan.rows_per_vpart, kVMaxRows);
     plan.vparts = (n + plan.rows_per_vpart - 1) / plan.rows_per_vpart;
   }
   const size_t v32_off = (yp_off + yp_bytes + 255) / 256 * 256;
