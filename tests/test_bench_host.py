@@ -1,7 +1,8 @@
 """Host logic of bench.py that needs no GPU: the DRAM-traffic record of the dominant kernel is
 used only while the kernel's source is the one the counters were taken from (its SHA-256),
 for the mixed path's fused kernel and the far field's leaf kernel alike; and the MUFU
-roof's work count falls with twin pairs and with more nodes per unit."""
+roof's work count falls with twin pairs, with more nodes per unit and with twin pairs on
+two-CTA clusters."""
 import hashlib
 import json
 import os
@@ -46,6 +47,14 @@ def test_mufu_work_count():
     assert twins < base < wider
     # every node still takes its own ex2 at every quadrature point
     assert twins > 7 * 32 / rates["ex2"]
+    # units of one node on two-CTA clusters: each twin pair shares its rsqrt, sine and
+    # cosine, so 32 nodes in 16 pairs cost 16 (rsqrt, sin, cos) and 32 ex2 per point
+    clus = bench.mufu_seconds_per_entry(rates, 32, 1, 16, clusters=True)
+    expect = 7 * (32 / rates["ex2"] + 16 * (1 / rates["sin"] + 1 / rates["cos"] + 1 / rates["rsqrt"]))
+    assert np.isclose(clus, expect) and clus < wider
+    # unpaired nodes on clusters pay their own rsqrt, sine and cosine
+    solo = bench.mufu_seconds_per_entry(rates, 5, 1, 2, clusters=True)
+    assert np.isclose(solo, 7 * (5 / rates["ex2"] + 3 * (1 / rates["sin"] + 1 / rates["cos"] + 1 / rates["rsqrt"])))
 
 
 def _fake_solve(values, mults, rng):
