@@ -224,6 +224,13 @@ def mufu_seconds_per_entry(rates, N, G, twins, clusters=False):
                 units / rates["rsqrt"])
 
 
+def mufu_seconds_method(rates, N):
+    """The method's own evaluation work per entry for all N nodes, at the measured rates:
+    7 quadrature points, each one complex exponential per node (ex2, sin, cos) and one
+    rsqrt shared by all N nodes; no work shared between nodes beyond that."""
+    return 7 * (N * (1 / rates["ex2"] + 1 / rates["sin"] + 1 / rates["cos"]) + 1 / rates["rsqrt"])
+
+
 def measured_traffic(workload, precision):
     """DRAM bytes (read + write) per launch of the dominant kernel (the fused kernel, or the
     far field's leaf kernel) from the committed ncu summary of this workload, or None when
@@ -775,6 +782,17 @@ def run_ours(args):
         tpeak, tsrc = sustained_bf16_tflops()
         roof["tensor"] = {"achieved_tflops": tflops, "peak_tflops": tpeak,
                           "frac": tflops / tpeak, "peak_source": "sustained dense BF16 " + tsrc}
+        # against the method's own work count (no twin sharing credited) and the smaller of
+        # that evaluation bound and the tensor bound (24 nu physical flops per entry and node)
+        eval_peak = N / mufu_seconds_method(rates, N)
+        tensor_peak = tpeak * 1e12 / (24.0 * nu)
+        roof["method_count"] = {
+            "eval_peak": eval_peak, "tensor_peak": tensor_peak,
+            "frac_eval": roof["achieved"] / eval_peak,
+            "frac_min": roof["achieved"] / min(eval_peak, tensor_peak), "unit": "entries/s",
+            "peak_source": "per entry and node 7 x (ex2, sin, cos), one rsqrt per quadrature "
+                           "point for all N nodes, at the measured MUFU rates; tensor: sustained "
+                           "BF16 / (24 nu)"}
 
     plain = None
     if prec != bem.PREC_FP64 and args.plain_steps > 0:

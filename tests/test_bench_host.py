@@ -67,6 +67,19 @@ def _fake_solve(values, mults, rng):
     return np.array(lam), np.stack(cols, axis=1), np.full(len(lam), 1e-13)
 
 
+def test_method_count_roof():
+    """The method's evaluation bound: at the measured GB300 rates (ex2 1e13/s, sin, cos,
+    rsqrt 5e12/s) and 64 nodes, 7 x (ex2, sin, cos) per entry and node plus one rsqrt per
+    quadrature point for all nodes gives 2.84e11 entries/s; one node alone pays the rsqrt."""
+    rates = {"ex2": 1e13, "sin": 5e12, "cos": 5e12, "rsqrt": 5e12}
+    peak = 64 / bench.mufu_seconds_method(rates, 64)
+    assert abs(peak - 2.8369e11) / 2.8369e11 < 1e-3
+    assert np.isclose(bench.mufu_seconds_method(rates, 1), 7 * (1e-13 + 2e-13 + 2e-13 + 2e-13))
+    # the kernel's own count with twin clusters is below the method's (sin, cos shared)
+    assert bench.mufu_seconds_per_entry(rates, 64, 1, 32, clusters=True) < \
+        bench.mufu_seconds_method(rates, 64)
+
+
 def test_eig_compare_flags_extras_missing_and_multiplicity():
     """The eigenvalue check used by the golden-solve tests and the bench: a clean solve
     passes; an extra converged value inside the contour, a missing golden value, a
