@@ -11,10 +11,14 @@
 //   * the pair list (CSR, columns increasing within a row), decided in FP64 with the
 //     criterion rounded step by step exactly as written, after an FP32 prefilter;
 //   * Y_j += C(z_j) V for the FP64 projection, the same in FP32 into a slice of the mixed
-//     path's partial products (optionally from the surrogate network), and
-//     R[:, c] += C(lam_c) X[:, c] (values or k-derivatives) for residuals and refinement.
-// One warp per (row, node) or (row, column): its lanes evaluate the row's pair corrections,
-// then sweep the basis columns with them (fixed order: deterministic).
+//     path's partial products, and R[:, c] += C(lam_c) X[:, c] (values or k-derivatives)
+//     for residuals and refinement.
+// FP64 and residual paths: one warp per (row, node) or (row, column), whose lanes evaluate
+// the row's pair corrections and then sweep the basis columns with them. FP32 path: the
+// values of every (pair, node) first, by the 8 x 8 rule (a thread per pair and 8 nodes) or
+// by the surrogate network on the tensor core (128-sample tiles), then one warp per (row,
+// node) sweeps the basis columns with them. Every sum runs in a fixed order, so the results
+// are deterministic.
 #include <cuda_bf16.h>
 #include <math.h>
 
