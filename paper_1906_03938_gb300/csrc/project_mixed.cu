@@ -20,6 +20,9 @@
 //    is bounded and a timeout aborts the block cleanly with an error status);
 //  * the evaluation warps finally read the accumulators from TMEM and store the FP32
 //    partial Y of the unit.
+// mixed_pair_kernel is the same evaluation and contraction for units of one node (bases of
+// more than 128 columns) whose nodes come in twin pairs: a cluster of two CTAs per twin
+// pair, each evaluating half of every block for both nodes (see its own description).
 // mixed_vhy_tc_kernel (BF16x3 on the tensor core, reading the same basis planes, one CTA
 // per node, row part and quadrant of column chunks), then mixed_vhy_reduce_kernel,
 // form Bhat_j = w_j V^H (sum over column splits of Y_j) with a fixed summation order.
